@@ -1,0 +1,271 @@
+"""CPU oracle (plain C, FP64) for the patch-AMR wave-propagation method.
+
+TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and
+the CPU-baseline leg of ``bench.py`` may import this package.  It shares no
+code with the CUDA path; the two meet only in the seeded inputs of ``synth``.
+
+The C sources are compiled here with gcc (``-ffp-contract=off`` so that the
+arithmetic is the same on every host) into ``oracle/liboracle.so``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+from typing import Optional, Sequence
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SO = os.path.join(_HERE, "liboracle.so")
+_SRC = ["forest.c", "ghost.c", "claw.c", "drive.c"]
+_HDR = ["oracle.h", "internal.h"]
+
+WALLS, PERIODIC, SPHERE = 0, 1, 2
+VEL_CONST, VEL_SWIRL = 0, 1
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle into liboracle.so (skipped when up to date)."""
+    srcs = [os.path.join(_HERE, s) for s in _SRC]
+    deps = srcs + [os.path.join(_HERE, h) for h in _HDR]
+    if not force and os.path.exists(_SO):
+        so_t = os.path.getmtime(_SO)
+        if all(os.path.getmtime(d) <= so_t for d in deps):
+            return _SO
+    tmp = _SO + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-std=gnu11", "-ffp-contract=off", "-fPIC", "-shared",
+           "-Wall", *srcs, "-lm", "-o", tmp]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _SO)
+    return _SO
+
+
+class _Params(ctypes.Structure):
+    _fields_ = [
+        ("domain", ctypes.c_int), ("nforests", ctypes.c_int),
+        ("mx", ctypes.c_int), ("mbc", ctypes.c_int),
+        ("lmin", ctypes.c_int), ("lmax", ctypes.c_int),
+        ("vel_kind", ctypes.c_int), ("vel", ctypes.c_double * 4),
+        ("order", ctypes.c_int), ("limiter", ctypes.c_int),
+        ("transverse", ctypes.c_int),
+    ]
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is not None:
+        return _lib
+    build()
+    L = ctypes.CDLL(_SO)
+    vp, ip, dp = ctypes.c_void_p, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)
+    L.or_create.restype = vp
+    L.or_create.argtypes = [ctypes.POINTER(_Params), ctypes.c_int, ip]
+    L.or_destroy.argtypes = [vp]
+    L.or_num_leaves.argtypes = [vp]
+    L.or_get_leaves.argtypes = [vp, ip]
+    for f in ("or_set_q", "or_get_q", "or_get_q_full", "or_set_q_full"):
+        getattr(L, f).argtypes = [vp, dp]
+    L.or_fill_ghosts.argtypes = [vp]
+    L.or_step_global.argtypes = [vp, ctypes.c_double, ctypes.c_double]
+    L.or_step_multirate.argtypes = [vp, ctypes.c_double, ctypes.c_double]
+    L.or_tag.argtypes = [vp, dp]
+    L.or_regrid.argtypes = [vp, ctypes.c_double, ctypes.c_double, ip, ip]
+    L.or_mass.argtypes = [vp, dp]
+    L.or_single_grid_periodic.argtypes = [ctypes.POINTER(_Params), ctypes.c_int, dp,
+                                          ctypes.c_double, ctypes.c_double, ctypes.c_int]
+    L.or_mc_phi.restype = ctypes.c_double
+    L.or_mc_phi.argtypes = [ctypes.c_double]
+    L.or_minmod.restype = ctypes.c_double
+    L.or_minmod.argtypes = [ctypes.c_double, ctypes.c_double]
+    L.or_last_error.restype = ctypes.c_char_p
+    _lib = L
+    return L
+
+
+def _dptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _iptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
+
+
+class OracleError(RuntimeError):
+    pass
+
+
+def _check(rc: int):
+    if rc != 0:
+        raise OracleError(lib().or_last_error().decode())
+
+
+def params(domain: int, mx: int, mbc: int, lmin: int, lmax: int, velocity,
+           order: int = 2, limiter: int = 1, transverse: int = 2,
+           nforests: int = 1) -> _Params:
+    p = _Params()
+    p.domain, p.nforests, p.mx, p.mbc, p.lmin, p.lmax = domain, nforests, mx, mbc, lmin, lmax
+    if velocity[0] == "const":
+        p.vel_kind = VEL_CONST
+        p.vel[0], p.vel[1] = float(velocity[1]), float(velocity[2])
+    elif velocity[0] == "swirl":
+        p.vel_kind = VEL_SWIRL
+        p.vel[0] = float(velocity[1])
+    else:
+        raise ValueError(velocity)
+    p.order, p.limiter, p.transverse = order, limiter, transverse
+    return p
+
+
+def uniform_leaves(level: int, nforests: int = 1) -> np.ndarray:
+    n = 1 << level
+    out = [(f, 0, level, x, y) for f in range(nforests) for y in range(n) for x in range(n)]
+    return np.asarray(out, dtype=np.int32).reshape(-1, 5)
+
+
+class Forest:
+    """One oracle forest (owner of a C handle)."""
+
+    def __init__(self, prm: _Params, leaves: np.ndarray):
+        self.prm = prm
+        leaves = np.ascontiguousarray(leaves, dtype=np.int32).reshape(-1, 5)
+        h = lib().or_create(ctypes.byref(prm), len(leaves), _iptr(leaves))
+        if not h:
+            raise OracleError(lib().or_last_error().decode())
+        self.h = h
+
+    def __del__(self):
+        h = getattr(self, "h", None)
+        if h:
+            lib().or_destroy(h)
+            self.h = None
+
+    @property
+    def mx(self) -> int:
+        return self.prm.mx
+
+    @property
+    def S(self) -> int:
+        return self.prm.mx + 2 * self.prm.mbc
+
+    def __len__(self) -> int:
+        return lib().or_num_leaves(self.h)
+
+    def leaves(self) -> np.ndarray:
+        out = np.zeros((len(self), 5), dtype=np.int32)
+        lib().or_get_leaves(self.h, _iptr(out))
+        return out
+
+    def set_q(self, q: np.ndarray):
+        q = np.ascontiguousarray(q, dtype=np.float64).reshape(len(self), self.mx, self.mx)
+        lib().or_set_q(self.h, _dptr(q))
+
+    def get_q(self) -> np.ndarray:
+        out = np.zeros((len(self), self.mx, self.mx))
+        lib().or_get_q(self.h, _dptr(out))
+        return out
+
+    def get_q_full(self) -> np.ndarray:
+        out = np.zeros((len(self), self.S, self.S))
+        lib().or_get_q_full(self.h, _dptr(out))
+        return out
+
+    def set_q_full(self, q: np.ndarray):
+        q = np.ascontiguousarray(q, dtype=np.float64).reshape(len(self), self.S, self.S)
+        lib().or_set_q_full(self.h, _dptr(q))
+
+    def fill_ghosts(self):
+        _check(lib().or_fill_ghosts(self.h))
+
+    def step_global(self, t: float, dt: float):
+        _check(lib().or_step_global(self.h, t, dt))
+
+    def step_multirate(self, t: float, dt_coarse: float):
+        _check(lib().or_step_multirate(self.h, t, dt_coarse))
+
+    def tag(self) -> np.ndarray:
+        out = np.zeros(len(self))
+        _check(lib().or_tag(self.h, _dptr(out)))
+        return out
+
+    def regrid(self, tau_r: float, tau_c: float,
+               lmax_f: Optional[Sequence[int]] = None) -> int:
+        changed = np.zeros(1, dtype=np.int32)
+        lm = None
+        if lmax_f is not None:
+            lm_arr = np.ascontiguousarray(lmax_f, dtype=np.int32)
+            lm = _iptr(lm_arr)
+        _check(lib().or_regrid(self.h, tau_r, tau_c, lm, _iptr(changed)))
+        return int(changed[0])
+
+    def mass(self) -> np.ndarray:
+        out = np.zeros(self.prm.nforests)
+        lib().or_mass(self.h, _dptr(out))
+        return out
+
+
+def single_grid_periodic(prm: _Params, q: np.ndarray, t0: float, dt: float,
+                         nsteps: int) -> np.ndarray:
+    q = np.ascontiguousarray(q, dtype=np.float64).copy()
+    N = q.shape[0]
+    _check(lib().or_single_grid_periodic(ctypes.byref(prm), N, _dptr(q), t0, dt, nsteps))
+    return q
+
+
+def mc_phi(theta: float) -> float:
+    return lib().or_mc_phi(float(theta))
+
+
+def minmod(a: float, b: float) -> float:
+    return lib().or_minmod(float(a), float(b))
+
+
+# ---------------------------------------------------------------- workloads
+
+_DOMAIN = {"walls": WALLS, "periodic": PERIODIC, "sphere": SPHERE}
+_LIMITER = {"none": (2, 0), "lw": (2, 0), "mc": (2, 1), "first": (1, 0)}
+
+
+def params_for(w, nforests: int = 1, lmax: Optional[int] = None) -> _Params:
+    order, lim = _LIMITER[w.limiter]
+    return params(_DOMAIN[w.domain], w.mx, w.mbc, w.lmin,
+                  w.lmax if lmax is None else lmax, w.velocity, order=order,
+                  limiter=lim, transverse=w.transverse, nforests=nforests)
+
+
+def initial_forest(workloads, lmax: Optional[int] = None) -> Forest:
+    """Build the initial adaptive forest of one or more workloads.
+
+    Start every forest uniformly at lmin, then (lmax_f - lmin) times: set the
+    analytic field at the cell centres, tag, refine/coarsen/balance; finally
+    set the analytic field on the final layout.
+    """
+    import synth
+    if not isinstance(workloads, (list, tuple)):
+        workloads = [workloads]
+    w0 = workloads[0]
+    nf = len(workloads)
+    lmax_all = max(w.lmax for w in workloads) if lmax is None else lmax
+    prm = params_for(w0, nforests=nf, lmax=lmax_all)
+    leaves = np.concatenate([uniform_leaves(w0.lmin) + np.array([f, 0, 0, 0, 0], np.int32)
+                             for f in range(nf)])
+    F = Forest(prm, leaves)
+    lmax_f = [w.lmax for w in workloads]
+
+    def set_analytic():
+        lv = F.leaves()
+        x, y = synth.cell_centres(lv, w0.mx)
+        q = np.empty(x.shape)
+        for f, w in enumerate(workloads):
+            sel = lv[:, 0] == f
+            q[sel] = synth.evaluate(w, x[sel], y[sel])
+        F.set_q(q)
+
+    for _ in range(lmax_all - w0.lmin):
+        set_analytic()
+        F.regrid(w0.tau_refine, w0.tau_coarsen, lmax_f)
+    set_analytic()
+    return F

@@ -1,0 +1,316 @@
+/*
+ * Oracle: time stepping, tagging, regridding and mass.
+ * Test infrastructure only (see oracle.h).
+ *
+ * Global time stepping (Sec. 5.1 runs): one time step for every grid, ghost
+ * fill of all levels by Alg. 1 before each step.
+ *
+ * Multirate stepping (Sec. 4, local time stepping): 2^(lmax-lmin) steps of
+ * the finest level per coarse step.  Reading used here: recursive order,
+ * coarse level first; before each substep of level L, Alg. 1 restricted to
+ * levels L-1 and L, with level L-1 data linearly interpolated in time between
+ * its state before and after its own last step.
+ *
+ * Regridding (Sec. 3.1): a grid is tagged for refinement when its indicator
+ * exceeds tau_r; a family of four sibling leaves is tagged for coarsening
+ * when all four indicators are below tau_c.  The indicator is the largest
+ * undivided gradient magnitude over the interior,
+ *   delta = max 1/2 sqrt((q(i+1,j)-q(i-1,j))^2 + (q(i,j+1)-q(i,j-1))^2).
+ * The new layout: tagged grids refined, then 2:1 balance by refinement only
+ * (Sec. 2: face and corner neighbours differ by at most one level), then each
+ * tagged family coarsened if its parent is balanced against that layout.
+ * New fine grids are filled by the ghost-fill interpolation (Eq. ghost_fine
+ * in the parent's index space), new coarse grids by averaging (Eq.
+ * ghost_coarse), unchanged grids are copied.
+ */
+#include "internal.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+static double cell_h(const or_forest* F, int l) { return 1.0 / ldexp((double)F->P.mx, l); }
+
+static void advance_leaf(or_forest* F, int p, double t, double dt) {
+  const or_leaf* a = &F->lv[p];
+  size_t S2 = (size_t)F->S * F->S;
+  or_claw_step(&F->P, F->q + p * S2, F->P.mx, F->P.mbc, cell_h(F, a->l), dt, t,
+               (long)a->x * F->P.mx, (long)a->y * F->P.mx);
+}
+
+int or_fill_ghosts(or_forest* F) { return or_fill_all(F); }
+
+int or_step_global(or_forest* F, double t, double dt) {
+  if (or_fill_all(F)) return -1;
+  for (int p = 0; p < F->n; ++p) advance_leaf(F, p, t, dt);
+  return 0;
+}
+
+static int mr_level(or_forest* F, int L, double t, double dt, double alpha) {
+  size_t S2 = (size_t)F->S * F->S;
+  if (or_fill_level(F, L, alpha)) return -1;
+  for (int p = 0; p < F->n; ++p)
+    if (F->lv[p].l == L) {
+      memcpy(F->qold + p * S2, F->q + p * S2, sizeof(double) * S2);
+      advance_leaf(F, p, t, dt);
+    }
+  if (L < F->P.lmax) {
+    if (mr_level(F, L + 1, t, 0.5 * dt, 0.0)) return -1;
+    if (mr_level(F, L + 1, t + 0.5 * dt, 0.5 * dt, 0.5)) return -1;
+  }
+  return 0;
+}
+
+int or_step_multirate(or_forest* F, double t, double dt_coarse) {
+  return mr_level(F, F->P.lmin, t, dt_coarse, 0.0);
+}
+
+int or_tag(or_forest* F, double* delta) {
+  if (or_fill_all(F)) return -1;
+  size_t S2 = (size_t)F->S * F->S;
+  int mx = F->P.mx;
+  for (int p = 0; p < F->n; ++p) {
+    const double* Q = F->q + p * S2;
+    double m = 0.0;
+    for (int j = 0; j < mx; ++j)
+      for (int i = 0; i < mx; ++i) {
+        double gx = Q[OR_IDX(F, i + 1, j)] - Q[OR_IDX(F, i - 1, j)];
+        double gy = Q[OR_IDX(F, i, j + 1)] - Q[OR_IDX(F, i, j - 1)];
+        double d = 0.5 * sqrt(gx * gx + gy * gy);
+        if (d > m) m = d;
+      }
+    delta[p] = m;
+  }
+  return 0;
+}
+
+/* ---- new layout ---- */
+
+typedef struct {
+  or_leaf* a;
+  int n, cap;
+} leafvec;
+
+static void push(leafvec* v, or_leaf x) {
+  if (v->n == v->cap) {
+    v->cap = v->cap ? 2 * v->cap : 64;
+    v->a = (or_leaf*)realloc(v->a, sizeof(or_leaf) * (size_t)v->cap);
+  }
+  v->a[v->n++] = x;
+}
+
+static void push_children(leafvec* v, const or_leaf* p) {
+  for (int c = 0; c < 4; ++c) {
+    or_leaf k = {p->f, p->b, p->l + 1, 2 * p->x + (c & 1), 2 * p->y + (c >> 1)};
+    push(v, k);
+  }
+}
+
+/* refine (once) every leaf that touches a leaf two or more levels finer, until none */
+static void balance(const or_forest* F, leafvec* v) {
+  for (;;) {
+    char* mark = (char*)calloc((size_t)(v->n > 0 ? v->n : 1), 1);
+    int any = 0;
+    for (int a = 0; a < v->n; ++a)
+      for (int c = 0; c < v->n; ++c) {
+        if (a == c) continue;
+        if (v->a[c].l >= v->a[a].l + 2 && or_touch(F, &v->a[a], &v->a[c])) {
+          mark[a] = 1;
+          any = 1;
+          break;
+        }
+      }
+    if (!any) {
+      free(mark);
+      return;
+    }
+    leafvec w = {0, 0, 0};
+    for (int a = 0; a < v->n; ++a) {
+      if (mark[a]) push_children(&w, &v->a[a]);
+      else push(&w, v->a[a]);
+    }
+    free(mark);
+    free(v->a);
+    *v = w;
+  }
+}
+
+static int is_first_child(const or_leaf* a) { return (a->x % 2 == 0) && (a->y % 2 == 0); }
+
+int or_regrid(or_forest* F, double tau_r, double tau_c, const int* lmax_f, int* changed) {
+  int n = F->n, mx = F->P.mx;
+  size_t S2 = (size_t)F->S * F->S;
+  double* delta = (double*)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+  if (or_tag(F, delta)) {
+    free(delta);
+    return -1;
+  }
+  char* refine = (char*)calloc((size_t)(n > 0 ? n : 1), 1);
+  for (int p = 0; p < n; ++p) {
+    int lm = lmax_f ? lmax_f[F->lv[p].f] : F->P.lmax;
+    refine[p] = (delta[p] > tau_r) && (F->lv[p].l < lm);
+  }
+  /* candidate families: four sibling leaves, none tagged to refine, all below tau_c */
+  int* fam = (int*)malloc(sizeof(int) * 4 * (size_t)(n > 0 ? n : 1));
+  int nfam = 0;
+  for (int p = 0; p < n; ++p) {
+    const or_leaf* a = &F->lv[p];
+    if (a->l <= F->P.lmin || !is_first_child(a)) continue;
+    int s[4], ok = 1;
+    for (int c = 0; c < 4 && ok; ++c) {
+      s[c] = or_find(F, a->f, a->b, a->l, a->x + (c & 1), a->y + (c >> 1));
+      if (s[c] < 0 || refine[s[c]] || !(delta[s[c]] < tau_c)) ok = 0;
+    }
+    if (!ok) continue;
+    for (int c = 0; c < 4; ++c) fam[4 * nfam + c] = s[c];
+    ++nfam;
+  }
+  /* refine, then balance */
+  leafvec v = {0, 0, 0};
+  for (int p = 0; p < n; ++p) {
+    if (refine[p]) push_children(&v, &F->lv[p]);
+    else push(&v, F->lv[p]);
+  }
+  balance(F, &v);
+  /* coarsen families whose parent is balanced against the refined layout */
+  char* gone = (char*)calloc((size_t)(v.n > 0 ? v.n : 1), 1);
+  leafvec parents = {0, 0, 0};
+  for (int k = 0; k < nfam; ++k) {
+    const or_leaf* c0 = &F->lv[fam[4 * k]];
+    int idx[4], ok = 1;
+    for (int c = 0; c < 4; ++c) {
+      const or_leaf* s = &F->lv[fam[4 * k + c]];
+      idx[c] = -1;
+      for (int m = 0; m < v.n; ++m)
+        if (v.a[m].f == s->f && v.a[m].b == s->b && v.a[m].l == s->l && v.a[m].x == s->x &&
+            v.a[m].y == s->y) {
+          idx[c] = m;
+          break;
+        }
+      if (idx[c] < 0) ok = 0; /* a sibling was refined by balance */
+    }
+    if (!ok) continue;
+    or_leaf par = {c0->f, c0->b, c0->l - 1, c0->x / 2, c0->y / 2};
+    for (int m = 0; m < v.n && ok; ++m) {
+      if (m == idx[0] || m == idx[1] || m == idx[2] || m == idx[3]) continue;
+      if (v.a[m].l > par.l + 1 && or_touch(F, &par, &v.a[m])) ok = 0;
+    }
+    if (!ok) continue;
+    for (int c = 0; c < 4; ++c) gone[idx[c]] = 1;
+    push(&parents, par);
+  }
+  leafvec nw = {0, 0, 0};
+  for (int m = 0; m < v.n; ++m)
+    if (!gone[m]) push(&nw, v.a[m]);
+  for (int k = 0; k < parents.n; ++k) push(&nw, parents.a[k]);
+  or_sort_leaves(nw.a, nw.n);
+
+  /* remap data onto the new layout */
+  double* q2 = (double*)malloc(sizeof(double) * S2 * (size_t)(nw.n > 0 ? nw.n : 1));
+  for (size_t c = 0; c < S2 * (size_t)nw.n; ++c) q2[c] = NAN;
+  int status = 0, nchanged = 0;
+  for (int m = 0; m < nw.n && status == 0; ++m) {
+    const or_leaf* a = &nw.a[m];
+    double* D = q2 + m * S2;
+    int old = or_find(F, a->f, a->b, a->l, a->x, a->y);
+    if (old >= 0) {
+      for (int j = 0; j < mx; ++j)
+        for (int i = 0; i < mx; ++i) D[OR_IDX(F, i, j)] = F->q[old * S2 + OR_IDX(F, i, j)];
+      continue;
+    }
+    ++nchanged;
+    int par = (a->l > 0) ? or_find(F, a->f, a->b, a->l - 1, a->x / 2, a->y / 2) : -1;
+    if (par >= 0) {
+      const double* Q = F->q + par * S2;
+      int cx = a->x & 1, cy = a->y & 1;
+      for (int j = 0; j < mx; ++j)
+        for (int i = 0; i < mx; ++i) {
+          int ic = cx * mx / 2 + i / 2, jc = cy * mx / 2 + j / 2;
+          double dx = (i & 1) ? 1.0 : -1.0, dy = (j & 1) ? 1.0 : -1.0;
+          double q0 = Q[OR_IDX(F, ic, jc)];
+          double sx = or_minmod(Q[OR_IDX(F, ic + 1, jc)] - q0, q0 - Q[OR_IDX(F, ic - 1, jc)]);
+          double sy = or_minmod(Q[OR_IDX(F, ic, jc + 1)] - q0, q0 - Q[OR_IDX(F, ic, jc - 1)]);
+          D[OR_IDX(F, i, j)] = q0 + 0.25 * (sx * dx + sy * dy);
+        }
+      continue;
+    }
+    int ch[4], ok = 1;
+    for (int c = 0; c < 4; ++c) {
+      ch[c] = or_find(F, a->f, a->b, a->l + 1, 2 * a->x + (c & 1), 2 * a->y + (c >> 1));
+      if (ch[c] < 0) ok = 0;
+    }
+    if (!ok) {
+      or_set_error("regrid: new leaf (%d,%d,%d,%d,%d) has neither an old parent nor four old "
+                   "children", a->f, a->b, a->l, a->x, a->y);
+      status = -1;
+      break;
+    }
+    for (int j = 0; j < mx; ++j)
+      for (int i = 0; i < mx; ++i) {
+        int cx = (2 * i >= mx), cy = (2 * j >= mx);
+        const double* C = F->q + ch[cx + 2 * cy] * S2;
+        int fi = 2 * i - cx * mx, fj = 2 * j - cy * mx;
+        double a0 = C[OR_IDX(F, fi, fj)], a1 = C[OR_IDX(F, fi + 1, fj)];
+        double a2 = C[OR_IDX(F, fi, fj + 1)], a3 = C[OR_IDX(F, fi + 1, fj + 1)];
+        D[OR_IDX(F, i, j)] = 0.25 * (((a0 + a1) + a2) + a3);
+      }
+  }
+  if (status == 0) {
+    /* new leaves plus the old leaves that disappeared */
+    nchanged += n - (nw.n - nchanged);
+    free(F->lv);
+    F->lv = nw.a;
+    F->n = nw.n;
+    free(F->q);
+    F->q = q2;
+    free(F->qold);
+    free(F->qT);
+    F->qold = (double*)malloc(sizeof(double) * S2 * (size_t)(nw.n > 0 ? nw.n : 1));
+    F->qT = (double*)malloc(sizeof(double) * S2 * (size_t)(nw.n > 0 ? nw.n : 1));
+    for (size_t c = 0; c < S2 * (size_t)nw.n; ++c) F->qold[c] = F->qT[c] = NAN;
+    or_build_index(F);
+    or_drop_cache(F);
+    if (changed) *changed = nchanged;
+  } else {
+    free(nw.a);
+    free(q2);
+  }
+  free(v.a);
+  free(parents.a);
+  free(gone);
+  free(fam);
+  free(refine);
+  free(delta);
+  return status;
+}
+
+void or_mass(const or_forest* F, double* per_forest) {
+  size_t S2 = (size_t)F->S * F->S;
+  int mx = F->P.mx;
+  for (int f = 0; f < F->P.nforests; ++f) per_forest[f] = 0.0;
+  for (int p = 0; p < F->n; ++p) {
+    double h = cell_h(F, F->lv[p].l), s = 0.0;
+    for (int j = 0; j < mx; ++j)
+      for (int i = 0; i < mx; ++i) s += F->q[p * S2 + OR_IDX(F, i, j)];
+    per_forest[F->lv[p].f] += h * h * s;
+  }
+}
+
+int or_single_grid_periodic(const or_params* P, int N, double* q, double t0, double dt,
+                            int nsteps) {
+  int mbc = P->mbc, S = N + 2 * mbc;
+  double* a = (double*)malloc(sizeof(double) * (size_t)S * S);
+  double h = 1.0 / N;
+  for (int n = 0; n < nsteps; ++n) {
+    for (int j = -mbc; j < N + mbc; ++j)
+      for (int i = -mbc; i < N + mbc; ++i) {
+        int ii = ((i % N) + N) % N, jj = ((j % N) + N) % N;
+        a[(i + mbc) + S * (j + mbc)] = q[ii + N * jj];
+      }
+    or_claw_step(P, a, N, mbc, h, dt, t0 + n * dt, 0, 0);
+    for (int j = 0; j < N; ++j)
+      for (int i = 0; i < N; ++i) q[i + N * j] = a[(i + mbc) + S * (j + mbc)];
+  }
+  free(a);
+  return 0;
+}

@@ -1,0 +1,53 @@
+/* Oracle internals (test infrastructure only; see oracle.h). */
+#ifndef FC_ORACLE_INTERNAL_H
+#define FC_ORACLE_INTERNAL_H
+
+#include "oracle.h"
+#include <stdint.h>
+
+typedef struct {
+  int f, b, l, x, y;   /* forest, block, level, quadrant coordinates */
+} or_leaf;
+
+struct or_forest {
+  or_params P;
+  int n;
+  int S;             /* mx + 2 mbc */
+  or_leaf* lv;       /* leaves in (forest, block, Morton) order */
+  int* byKey;        /* leaf indices sorted by (f, b, l, x, y) */
+  double* q;         /* n * S * S, current solution with ghosts */
+  double* qold;      /* state saved before a leaf's last advance (multirate) */
+  double* qT;        /* time-interpolated coarse data (multirate) */
+  void* gcache;      /* memoised ghost-cell holders of the current mesh */
+};
+
+/* relation of the leaf that holds a ghost cell to the ghost's owner */
+enum { REL_SAME = 0, REL_FINE = 1, REL_COARSE = -1, REL_EXTERIOR = -100,
+       REL_CORNER3 = -101, REL_NONE = -102 };
+
+#define OR_IDX(F, i, j) (((i) + (F)->P.mbc) + (F)->S * ((j) + (F)->P.mbc))
+
+void or_set_error(const char* fmt, ...);
+
+/* forest.c */
+int or_find(const or_forest* F, int f, int b, int l, int x, int y);
+/* locate the leaf of forest f holding block point (x, y) of block b.
+ * Returns the leaf index, or -1.  May move the point into another block
+ * (periodic wrap, cube-face crossing); *b, *x, *y are updated.
+ * Returns -2 for a point outside the physical domain (walls) and -3 for a
+ * point beyond a three-valent cube corner. */
+int or_locate(const or_forest* F, int f, int* b, double* x, double* y);
+void or_sort_leaves(or_leaf* lv, int n);
+void or_build_index(or_forest* F);
+int or_touch(const or_forest* F, const or_leaf* a, const or_leaf* c);
+
+/* claw.c */
+void or_claw_step(const or_params* P, double* q, int mx, int mbc, double h,
+                  double dt, double t, long gx0, long gy0);
+
+/* ghost.c */
+int or_fill_all(or_forest* F);
+int or_fill_level(or_forest* F, int level, double alpha);
+void or_drop_cache(or_forest* F);
+
+#endif

@@ -1,0 +1,76 @@
+/*
+ * CPU oracle for the patch-AMR wave-propagation method (ForestClaw,
+ * Calhoun & Burstedde, arXiv 1703.03116).
+ *
+ * TEST INFRASTRUCTURE ONLY.  This code is a plain, slow, FP64 restatement of
+ * the method used to check the CUDA path.  Only the test-suite, the smoke
+ * check and the CPU-baseline leg of the benchmark may load it.  It shares no
+ * code, header, table or constant with the CUDA path.
+ *
+ * Geometry is done by brute force: every ghost cell is located by searching
+ * the leaf set for the quadrant that contains its centre (Sec. 2.2 "Ghost
+ * regions"), instead of using a precomputed neighbour list.
+ *
+ * Parity unpinned (checked only against the same stated reading): the
+ * multirate time interpolation of coarse data, the fill of the corner ghost
+ * block at three-valent cube corners, and the capacity form on the sphere.
+ */
+#ifndef FC_ORACLE_H
+#define FC_ORACLE_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum { OR_WALLS = 0, OR_PERIODIC = 1, OR_SPHERE = 2 };
+enum { OR_VEL_CONST = 0, OR_VEL_SWIRL = 1 };
+
+#define OR_MAXLEV 18
+
+typedef struct {
+  int domain;      /* OR_WALLS, OR_PERIODIC, OR_SPHERE */
+  int nforests;    /* independent forests (one block each for the square) */
+  int mx, mbc;     /* interior cells per side, ghost layers */
+  int lmin, lmax;  /* level range of the whole run */
+  int vel_kind;    /* OR_VEL_CONST (vel[0]=u, vel[1]=v) or OR_VEL_SWIRL (vel[0]=T) */
+  double vel[4];
+  int order;       /* 1: first order, 2: second-order corrections */
+  int limiter;     /* 0: unlimited (Lax-Wendroff), 1: MC */
+  int transverse;  /* 0: none, 1: fluctuations, 2: fluctuations + corrections */
+} or_params;
+
+typedef struct or_forest or_forest;
+
+/* leaves: n rows of (forest, block, level, ix, iy) */
+or_forest* or_create(const or_params* P, int n, const int* leaves);
+void or_destroy(or_forest* F);
+int or_num_leaves(const or_forest* F);
+void or_get_leaves(const or_forest* F, int* out);
+/* interior data, [leaf][j][i], leaves in the order of or_get_leaves */
+void or_set_q(or_forest* F, const double* q);
+void or_get_q(const or_forest* F, double* q);
+/* full arrays with ghosts, [leaf][j][i] over (mx+2mbc)^2 */
+void or_get_q_full(const or_forest* F, double* q);
+void or_set_q_full(or_forest* F, const double* q);
+
+int or_fill_ghosts(or_forest* F);                       /* Alg. 1 */
+int or_step_global(or_forest* F, double t, double dt);  /* global time stepping */
+int or_step_multirate(or_forest* F, double t, double dt_coarse);
+int or_tag(or_forest* F, double* delta);                /* ghost fill + per-leaf indicator */
+int or_regrid(or_forest* F, double tau_r, double tau_c, const int* lmax_f, int* changed);
+void or_mass(const or_forest* F, double* per_forest);
+
+/* one uniform periodic N x N grid, used to check the forest against it */
+int or_single_grid_periodic(const or_params* P, int N, double* q, double t0,
+                            double dt, int nsteps);
+
+/* scalar building blocks, exposed for table checks */
+double or_mc_phi(double theta);
+double or_minmod(double a, double b);
+
+const char* or_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,225 @@
+"""Seeded synthetic inputs for the patch-AMR advection workloads.
+
+This module is the one piece shared by the CPU oracle and the CUDA path.  It
+holds no arithmetic of the method: it draws seeded parameters (numpy PCG64)
+and evaluates the analytic initial fields at points that the caller supplies.
+Every workload is synthetic; the paper's own runs also start from analytic
+tracer fields (a piecewise-constant disc pattern in the replicated-domain test,
+a slotted disk on the sphere), so nothing here stands in for a dataset.
+
+Workloads (unit square = one block; cubed sphere = six blocks):
+
+* ``uniform_periodic``: one periodic tree refined uniformly to level 3,
+  16x16 patches (a 128^2 grid), constant velocity (1, 0.5), MC limiter with
+  transverse corrections, CFL 0.9, 100 steps.  q0 = four Gaussians
+  (amplitude U[0.5,1], width U[0.03,0.08], centre U[0,1]^2, periodic distance)
+  plus a square pulse of value 1 (side 0.25, corner U[0,0.75]^2).
+* ``swirl``: one walled tree, levels 2..6, 32x32 patches, swirl velocity with
+  period T=4, q0 = 1 inside a radius-0.2 disc (centre U[0.2,0.8]^2), else 0.
+* ``ensemble``: many independent swirl forests, each with its own disc and a
+  maximum level drawn from {4,5,6}.
+* ``adjoint``: the swirl forest plus a target field from a disc whose centre is
+  shifted by a seeded offset of at most 0.05.
+"""
+from __future__ import annotations
+
+import dataclasses
+from typing import List, Optional
+
+import numpy as np
+
+__all__ = [
+    "Gaussians", "Disc", "SquarePulse", "Workload", "uniform_periodic",
+    "swirl", "ensemble", "adjoint_target", "smooth_periodic", "cell_centres",
+    "evaluate", "random_field", "time_step",
+]
+
+
+@dataclasses.dataclass
+class Gaussians:
+    amp: np.ndarray      # (k,)
+    width: np.ndarray    # (k,)
+    centre: np.ndarray   # (k, 2)
+    periodic: bool = True
+
+
+@dataclasses.dataclass
+class SquarePulse:
+    corner: np.ndarray   # (2,)
+    side: float = 0.25
+    periodic: bool = True
+
+
+@dataclasses.dataclass
+class Disc:
+    centre: np.ndarray   # (2,)
+    radius: float = 0.2
+
+
+@dataclasses.dataclass
+class Workload:
+    """One forest's problem description (parameters only, no numerics)."""
+    name: str
+    domain: str          # "periodic" | "walls" | "sphere"
+    mx: int
+    mbc: int
+    lmin: int
+    lmax: int
+    velocity: tuple      # ("const", u, v) | ("swirl", T)
+    limiter: str         # "none" | "mc" | "lw"
+    transverse: int      # 0, 1 (fluctuations), 2 (fluctuations + corrections)
+    cfl: float
+    parts: list          # list of Gaussians / SquarePulse / Disc
+    steps: Optional[int] = None
+    t_final: Optional[float] = None
+    regrid_every: int = 0
+    tau_refine: float = 0.05
+    tau_coarsen: float = 0.0125
+    seed: int = 0
+
+
+def _rng(seed: int) -> np.random.Generator:
+    return np.random.Generator(np.random.PCG64(seed))
+
+
+def uniform_periodic(seed: int = 0, level: int = 3, mx: int = 16,
+                     steps: int = 100) -> Workload:
+    g = _rng(seed)
+    k = 4
+    amp = g.uniform(0.5, 1.0, k)
+    width = g.uniform(0.03, 0.08, k)
+    centre = g.uniform(0.0, 1.0, (k, 2))
+    corner = g.uniform(0.0, 0.75, 2)
+    return Workload(
+        name=f"uniform periodic level {level} mx={mx}", domain="periodic",
+        mx=mx, mbc=2, lmin=level, lmax=level, velocity=("const", 1.0, 0.5),
+        limiter="mc", transverse=2, cfl=0.9,
+        parts=[Gaussians(amp, width, centre), SquarePulse(corner)],
+        steps=steps, seed=seed)
+
+
+def smooth_periodic(seed: int = 0, level: int = 2, mx: int = 16,
+                    velocity=("const", 1.0, 0.5), limiter="none") -> Workload:
+    """Gaussians only (smooth), for convergence studies."""
+    g = _rng(seed)
+    k = 4
+    amp = g.uniform(0.5, 1.0, k)
+    width = g.uniform(0.08, 0.12, k)
+    centre = g.uniform(0.0, 1.0, (k, 2))
+    return Workload(
+        name="smooth periodic", domain="periodic", mx=mx, mbc=2, lmin=level,
+        lmax=level, velocity=velocity, limiter=limiter, transverse=2, cfl=0.9,
+        parts=[Gaussians(amp, width, centre)], seed=seed)
+
+
+def swirl(seed: int = 0, lmin: int = 2, lmax: int = 6, mx: int = 32,
+          period: float = 4.0, regrid_every: int = 4) -> Workload:
+    g = _rng(seed)
+    centre = g.uniform(0.2, 0.8, 2)
+    return Workload(
+        name=f"swirl levels {lmin}-{lmax} mx={mx}", domain="walls", mx=mx,
+        mbc=2, lmin=lmin, lmax=lmax, velocity=("swirl", period),
+        limiter="mc", transverse=2, cfl=0.9, parts=[Disc(centre)],
+        t_final=period, regrid_every=regrid_every, seed=seed)
+
+
+def ensemble(n: int = 256, seed: int = 0, lmin: int = 2, mx: int = 32,
+             levels=(4, 5, 6)) -> List[Workload]:
+    """n independent swirl forests with seeded discs and maximum levels."""
+    g = _rng(seed)
+    out = []
+    sub_seeds = g.integers(0, 2**31 - 1, n)
+    lmaxes = g.choice(np.asarray(levels), n)
+    for f in range(n):
+        out.append(swirl(int(sub_seeds[f]), lmin=lmin, lmax=int(lmaxes[f]),
+                         mx=mx))
+    return out
+
+
+def adjoint_target(w: Workload, seed: int = 0, max_shift: float = 0.05) -> Workload:
+    """The same workload with its disc centre moved by a seeded offset."""
+    g = _rng(seed + 7919)
+    ang = g.uniform(0.0, 2 * np.pi)
+    r = g.uniform(0.0, max_shift)
+    parts = []
+    for p in w.parts:
+        if isinstance(p, Disc):
+            parts.append(Disc(p.centre + r * np.array([np.cos(ang), np.sin(ang)]),
+                              p.radius))
+        else:
+            parts.append(p)
+    return dataclasses.replace(w, parts=parts, name=w.name + " (target)")
+
+
+def evaluate(w: Workload, x: np.ndarray, y: np.ndarray) -> np.ndarray:
+    """Initial field of workload ``w`` at points (x, y) (unit-square coords)."""
+    x = np.asarray(x, dtype=np.float64)
+    y = np.asarray(y, dtype=np.float64)
+    q = np.zeros(np.broadcast(x, y).shape)
+    for p in w.parts:
+        if isinstance(p, Gaussians):
+            for a, s, c in zip(p.amp, p.width, p.centre):
+                dx = x - c[0]
+                dy = y - c[1]
+                if p.periodic:
+                    dx = dx - np.round(dx)
+                    dy = dy - np.round(dy)
+                q = q + a * np.exp(-(dx * dx + dy * dy) / (s * s))
+        elif isinstance(p, SquarePulse):
+            dx = x - p.corner[0]
+            dy = y - p.corner[1]
+            if p.periodic:
+                dx = np.mod(dx, 1.0)
+                dy = np.mod(dy, 1.0)
+            inside = (dx >= 0) & (dx < p.side) & (dy >= 0) & (dy < p.side)
+            q = q + inside.astype(np.float64)
+        elif isinstance(p, Disc):
+            dx = x - p.centre[0]
+            dy = y - p.centre[1]
+            q = q + ((dx * dx + dy * dy) < p.radius * p.radius).astype(np.float64)
+        else:
+            raise TypeError(type(p))
+    return q
+
+
+def cell_centres(leaves: np.ndarray, mx: int):
+    """Cell-centre coordinates of every interior cell of every leaf.
+
+    ``leaves`` is an (n, >=5) integer array whose columns 2..4 are
+    (level, ix, iy) of a quadrant in a unit block.  Returns x, y of shape
+    (n, mx, mx) indexed [leaf][j][i].
+    """
+    leaves = np.asarray(leaves)
+    lev = leaves[:, 2].astype(np.float64)
+    ix = leaves[:, 3].astype(np.float64)
+    iy = leaves[:, 4].astype(np.float64)
+    h = 1.0 / (mx * np.exp2(lev))
+    i = np.arange(mx, dtype=np.float64) + 0.5
+    x = (ix[:, None, None] * mx + i[None, None, :]) * h[:, None, None]
+    y = (iy[:, None, None] * mx + i[None, :, None]) * h[:, None, None]
+    x = np.broadcast_to(x, (len(leaves), mx, mx))
+    y = np.broadcast_to(y, (len(leaves), mx, mx))
+    return np.ascontiguousarray(x), np.ascontiguousarray(y)
+
+
+def time_step(w: Workload, lmax: Optional[int] = None):
+    """(number of coarse steps, coarse dt) landing exactly on ``w.t_final``.
+
+    dt_CFL = cfl * h_finest / (largest speed; 1 for the swirl).  A coarse step
+    is 2^(lmax - lmin) steps of the finest level.  This is a parameter choice
+    shared by both implementations, not part of either.
+    """
+    L = w.lmax if lmax is None else lmax
+    h_f = 1.0 / (w.mx * 2 ** L)
+    if w.velocity[0] == "const":
+        smax = max(abs(w.velocity[1]), abs(w.velocity[2]))
+    else:
+        smax = 1.0
+    dt_cfl = w.cfl * h_f / smax
+    ratio = 2 ** (L - w.lmin)
+    n = int(np.ceil(w.t_final / (ratio * dt_cfl)))
+    return n, w.t_final / n
+
+
+def random_field(shape, seed: int = 0, lo: float = 0.0, hi: float = 1.0):
+    return _rng(seed).uniform(lo, hi, shape)
