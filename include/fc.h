@@ -1,0 +1,190 @@
+/*
+ * fc.h -- C ABI of the GB300 patch-AMR wave-propagation library.
+ *
+ * The library advances a scalar tracer, q_t + (u q)_x + (v q)_y = 0, on a
+ * forest of quadtrees whose leaves carry fixed-size mx x mx patches with mbc
+ * ghost layers (Calhoun & Burstedde, arXiv 1703.03116, Sec. 2: "A quadtree
+ * layout").  One device store holds every patch of every forest; all
+ * numerical work runs in CUDA kernels on the device.
+ *
+ * Conventions common to every call:
+ *  - Every call returns an fc_status; no exception or abort crosses the ABI.
+ *    On failure fc_last_error() returns a thread-local message.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  Calls enqueue work on it and return without synchronising,
+ *    unless stated otherwise.  An asynchronous device error is reported as
+ *    FC_ERR_CUDA by the next call that synchronises.
+ *  - Pointers marked "host" are read or written before the call returns.
+ *    Pointers marked "device" must stay valid until the stream reaches the
+ *    call's work.  The caller keeps ownership of every buffer it passes; the
+ *    library owns the forest and all device storage it allocates.
+ *  - Field layout for get/set: interior cells only, [leaf][j][i] (i fastest),
+ *    leaves in the order of fc_forest_leaves (forest, block, Morton order).
+ *    Element type is the forest's dtype (float for FC_F32, double for FC_F64).
+ *  - A forest handle is not thread-safe; use one host thread per handle.
+ */
+#ifndef FC_H
+#define FC_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct fc_forest fc_forest;
+
+typedef enum {
+  FC_OK = 0,
+  FC_ERR_INVALID_ARG = 1,   /* bad pointer, size, level or enum value            */
+  FC_ERR_PRECONDITION = 2,  /* layout not 2:1 balanced, not covering, mbc > mx/4 */
+  FC_ERR_OOM = 3,           /* device or host allocation failed                  */
+  FC_ERR_CUDA = 4,          /* a CUDA call or kernel failed                      */
+  FC_ERR_TIMEOUT = 5,       /* a bounded device wait gave up                     */
+  FC_ERR_STATE = 6          /* call not valid in the forest's current state      */
+} fc_status;
+
+typedef enum { FC_F32 = 0, FC_F64 = 1 } fc_dtype;
+typedef enum { FC_DOMAIN_WALLS = 0, FC_DOMAIN_PERIODIC = 1, FC_DOMAIN_SPHERE = 2 } fc_domain;
+typedef enum { FC_VEL_CONST = 0, FC_VEL_SWIRL = 1 } fc_velocity;
+
+/* Problem description (Sec. 2; Sec. 5.1 "Problem setup").
+ *   domain      unit square with walls, periodic unit square, or cubed sphere.
+ *   nforests    independent forests in one store (a batched ensemble); each
+ *               forest of a square domain is one block.
+ *   mx, mbc     interior cells per side (power of two, 8..64) and ghost layers
+ *               (Proposition 1 requires mbc <= mx/4; only mbc = 2 is built).
+ *   lmin, lmax  level range; a level-l leaf has edge 2^-l of its block.
+ *   dtype       FC_F32 or FC_F64 for the stored field and the update.
+ *   vel_kind    FC_VEL_CONST: (u, v) = (vel[0], vel[1]);
+ *               FC_VEL_SWIRL: streamfunction sin^2(pi x) sin^2(pi y)
+ *               cos(pi t / T) / pi with T = vel[0].
+ *   order       1 (first order) or 2 (second-order wave corrections).
+ *   limiter     0 unlimited, 1 MC.
+ *   transverse  0 none, 1 fluctuations, 2 fluctuations and corrections. */
+typedef struct {
+  int domain;
+  int nforests;
+  int mx, mbc;
+  int lmin, lmax;
+  int dtype;
+  int vel_kind;
+  double vel[4];
+  int order;
+  int limiter;
+  int transverse;
+} fc_forest_desc;
+
+/* Create a forest from an explicit leaf list (Sec. 2: quadrants identified
+ * by tree coordinates and level; only leaves are stored).
+ *   leaves   host, nleaves rows of 5 ints (forest, block, level, ix, iy),
+ *            0 <= ix, iy < 2^level; any order.
+ * The leaves of each forest must tile its blocks exactly and be 2:1 balanced
+ * across faces and corners (FC_ERR_PRECONDITION otherwise).  The field is
+ * allocated but undefined until fc_forest_set_q.  Synchronous. */
+fc_status fc_forest_create(const fc_forest_desc* desc, int nleaves, const int* leaves,
+                           fc_forest** out);
+fc_status fc_forest_destroy(fc_forest* forest);
+
+/* Number of leaves, and the leaf list (host, n x 5 ints) in field order. */
+fc_status fc_forest_num_leaves(const fc_forest* forest, int* n);
+fc_status fc_forest_leaves(const fc_forest* forest, int* out);
+
+/* Copy the interior field in or out (layout in the header comment).
+ *   on_device  nonzero: `q` is a device pointer (async on `stream`);
+ *              zero: `q` is a host pointer (the call synchronises `stream`). */
+fc_status fc_forest_set_q(fc_forest* forest, const void* q, int on_device, void* stream);
+fc_status fc_forest_get_q(const fc_forest* forest, void* q, int on_device, void* stream);
+/* Whole patch arrays with ghosts, (mx+2mbc)^2 per leaf, [leaf][j][i]. */
+fc_status fc_forest_get_q_full(const fc_forest* forest, void* q, int on_device, void* stream);
+
+/* Alg. 1 (update_ghost, Sec. 2.3) on every level: copy from same-size
+ * neighbours (Eq. transform), average from fine neighbours (Eq.
+ * ghost_coarse), physical boundary conditions, interpolation from coarse
+ * neighbours (Eq. ghost_fine), physical boundary conditions again.
+ * All levels must hold data at the same time. */
+fc_status fc_fill_ghosts(fc_forest* forest, void* stream);
+
+/* One multirate substep of one level (Sec. 4, local time stepping): fill the
+ * ghosts of `level` at time t -- data of level-1 are linearly interpolated in
+ * time between its states before and after its own last step -- then advance
+ * every level-`level` patch from t to t+dt with the wave-propagation update.
+ * Levels are driven coarse-first: level+1 takes two substeps of dt/2 after
+ * each substep of `level`.  `level` must hold patches' time t. */
+fc_status fc_advance_level(fc_forest* forest, int level, double t, double dt, void* stream);
+
+/* One global time step (every level advanced by dt after one Alg. 1 fill). */
+fc_status fc_step_global(fc_forest* forest, double t, double dt, void* stream);
+
+/* One coarse multirate step: the coarse-first recursion of fc_advance_level
+ * over all levels, 2^(lmax-lmin) substeps of the finest level. */
+fc_status fc_step_multirate(fc_forest* forest, double t, double dt_coarse, void* stream);
+
+/* Tag and regrid (Sec. 3.1).  Fills ghosts, computes on the device the
+ * per-leaf indicator max 1/2 |(q(i+1,j)-q(i-1,j), q(i,j+1)-q(i,j-1))| (FP64),
+ * refines leaves above tau_refine (below their forest's maximum level
+ * lmax_per_forest[f], or desc.lmax when NULL), 2:1 balances by refinement,
+ * coarsens families of four leaves all below tau_coarsen whose parent stays
+ * balanced, and remaps the field on the device (copy; Eq. ghost_fine
+ * interpolation for new children; Eq. ghost_coarse averaging for new
+ * parents).  *changed (host) receives the number of leaves created plus
+ * removed.  Synchronous. */
+fc_status fc_tag_regrid(fc_forest* forest, double tau_refine, double tau_coarsen,
+                        const int* lmax_per_forest, int* changed, void* stream);
+
+/* The per-leaf indicator alone, into a host array of nleaves doubles. */
+fc_status fc_tag(fc_forest* forest, double* delta_host, void* stream);
+
+/* Total mass per forest, sum over leaves of h^2 sum(q), accumulated in FP64
+ * on the device in a fixed order.  out: host, nforests doubles.  Synchronous. */
+fc_status fc_forest_mass(const fc_forest* forest, double* out, void* stream);
+
+/* Host-only layout services (no device work; usable without a GPU).
+ *
+ * fc_layout_check: validate a leaf list against `desc` (tiling, levels, 2:1
+ * balance across faces and corners).  Returns FC_OK or FC_ERR_PRECONDITION.
+ *
+ * fc_layout_neighbours: the face/corner neighbour table of Sec. 2.2-2.4 for
+ * a valid leaf list.  out: host, nleaves * 8 rows of 6 ints
+ *   (kind, n0, n1, a, fx, fy)
+ * in the leaves' field order, regions (-x, +x, -y, +y, (-,-), (+,-), (-,+),
+ * (+,+)); kind 0 exterior, 1 same size, 2 finer, 3 coarser; n0/n1 are field
+ * indices of the neighbour leaves; (a, fx, fy) encode Eq. (transform)
+ * I' = A I + F on level-l global cell indices (a: bit 0 swaps axes, bits 1
+ * and 2 negate the first and second output).
+ *
+ * fc_layout_regrid: the layout that fc_tag_regrid builds from per-leaf
+ * indicators `delta` (host, nleaves doubles, field order).  out_leaves:
+ * host, capacity `cap` rows of 5 ints; *nout receives the new count
+ * (FC_ERR_INVALID_ARG when cap is too small). */
+fc_status fc_layout_check(const fc_forest_desc* desc, int nleaves, const int* leaves);
+fc_status fc_layout_neighbours(const fc_forest_desc* desc, int nleaves, const int* leaves,
+                               int* out);
+fc_status fc_layout_regrid(const fc_forest_desc* desc, int nleaves, const int* leaves,
+                           const double* delta, double tau_refine, double tau_coarsen,
+                           const int* lmax_per_forest, int cap, int* out_leaves, int* nout);
+
+/* Per-phase device timers (the paper's run-time breakdown, Sec. 5: advance,
+ * ghost fill, regrid).  While enabled, every kernel launch of a phase is
+ * bracketed by CUDA events on its stream.
+ *   phase: 0 advance, 1 ghost fill, 2 regrid/tag/remap, 3 other.
+ * fc_timers_read synchronises the forest's pending timed work and returns,
+ * for one phase, the summed kernel time in ms, the number of timed launches
+ * and the algorithmic bytes those launches must move (advance: every patch
+ * array read once with ghosts, every interior written once; fill: every
+ * filled ghost cell written once and its source read once).  reset != 0
+ * clears the phase afterwards. */
+fc_status fc_timers_enable(fc_forest* forest, int enable);
+fc_status fc_timers_read(fc_forest* forest, int phase, double* ms, int64_t* launches,
+                         double* bytes, int reset);
+
+/* Thread-local description of the last failure. */
+const char* fc_last_error(void);
+
+/* Kernel launches issued by this thread since the last reset. */
+uint64_t fc_launch_count(int reset);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FC_H */

@@ -1,0 +1,90 @@
+"""ctypes declarations of the C ABI in include/fc.h (argument marshalling only)."""
+from __future__ import annotations
+
+import ctypes
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libfc.so")
+
+FC_OK = 0
+STATUS = {0: "FC_OK", 1: "FC_ERR_INVALID_ARG", 2: "FC_ERR_PRECONDITION", 3: "FC_ERR_OOM",
+          4: "FC_ERR_CUDA", 5: "FC_ERR_TIMEOUT", 6: "FC_ERR_STATE"}
+F32, F64 = 0, 1
+WALLS, PERIODIC, SPHERE = 0, 1, 2
+VEL_CONST, VEL_SWIRL = 0, 1
+
+# every function that include/fc.h declares, with (restype, argtypes)
+_vp, _ip, _dp = ctypes.c_void_p, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)
+
+
+class Desc(ctypes.Structure):
+    """Mirror of fc_forest_desc."""
+    _fields_ = [
+        ("domain", ctypes.c_int), ("nforests", ctypes.c_int),
+        ("mx", ctypes.c_int), ("mbc", ctypes.c_int),
+        ("lmin", ctypes.c_int), ("lmax", ctypes.c_int),
+        ("dtype", ctypes.c_int), ("vel_kind", ctypes.c_int),
+        ("vel", ctypes.c_double * 4),
+        ("order", ctypes.c_int), ("limiter", ctypes.c_int),
+        ("transverse", ctypes.c_int),
+    ]
+
+
+_DP = ctypes.POINTER(Desc)
+SIGNATURES = {
+    "fc_forest_create": (ctypes.c_int, [_DP, ctypes.c_int, _ip, ctypes.POINTER(_vp)]),
+    "fc_forest_destroy": (ctypes.c_int, [_vp]),
+    "fc_forest_num_leaves": (ctypes.c_int, [_vp, _ip]),
+    "fc_forest_leaves": (ctypes.c_int, [_vp, _ip]),
+    "fc_forest_set_q": (ctypes.c_int, [_vp, _vp, ctypes.c_int, _vp]),
+    "fc_forest_get_q": (ctypes.c_int, [_vp, _vp, ctypes.c_int, _vp]),
+    "fc_forest_get_q_full": (ctypes.c_int, [_vp, _vp, ctypes.c_int, _vp]),
+    "fc_fill_ghosts": (ctypes.c_int, [_vp, _vp]),
+    "fc_advance_level": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_double, ctypes.c_double, _vp]),
+    "fc_step_global": (ctypes.c_int, [_vp, ctypes.c_double, ctypes.c_double, _vp]),
+    "fc_step_multirate": (ctypes.c_int, [_vp, ctypes.c_double, ctypes.c_double, _vp]),
+    "fc_tag_regrid": (ctypes.c_int, [_vp, ctypes.c_double, ctypes.c_double, _ip, _ip, _vp]),
+    "fc_tag": (ctypes.c_int, [_vp, _dp, _vp]),
+    "fc_forest_mass": (ctypes.c_int, [_vp, _dp, _vp]),
+    "fc_layout_check": (ctypes.c_int, [_DP, ctypes.c_int, _ip]),
+    "fc_layout_neighbours": (ctypes.c_int, [_DP, ctypes.c_int, _ip, _ip]),
+    "fc_layout_regrid": (ctypes.c_int, [_DP, ctypes.c_int, _ip, _dp, ctypes.c_double,
+                                        ctypes.c_double, _ip, ctypes.c_int, _ip, _ip]),
+    "fc_timers_enable": (ctypes.c_int, [_vp, ctypes.c_int]),
+    "fc_timers_read": (ctypes.c_int, [_vp, ctypes.c_int, _dp, ctypes.POINTER(ctypes.c_int64),
+                                      _dp, ctypes.c_int]),
+    "fc_last_error": (ctypes.c_char_p, []),
+    "fc_launch_count": (ctypes.c_uint64, [ctypes.c_int]),
+}
+
+_lib = None
+
+
+class FcError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+def load() -> ctypes.CDLL:
+    """Load libfc.so; raise if it has not been built (no fallback exists)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(
+            f"{LIB_PATH} is missing: build it with `python -c 'import __graft_entry__ as g; "
+            "g.build()'` (nvcc, sm_103a).  There is no CPU fallback.")
+    L = ctypes.CDLL(LIB_PATH)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(L, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = L
+    return L
+
+
+def check(status: int):
+    if status != FC_OK:
+        raise FcError(status, load().fc_last_error().decode())

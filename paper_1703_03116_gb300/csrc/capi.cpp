@@ -1,0 +1,740 @@
+// C ABI (include/fc.h): forest lifetime, device store, and the time-stepping
+// scheduler (Alg. 1 fills, global and multirate level substeps, regrid).
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "fc_internal.hpp"
+
+using namespace fc;
+
+namespace {
+
+thread_local std::string g_err;
+
+fc_status fail(fc_status s, const std::string& msg) {
+  g_err = msg;
+  return s;
+}
+
+fc_status cuda_fail(cudaError_t e, const char* where) {
+  return fail(FC_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define FC_CUDA(call)                                  \
+  do {                                                 \
+    cudaError_t e_ = (call);                           \
+    if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
+  } while (0)
+
+template <typename T>
+cudaError_t dmalloc(T** p, size_t n) {
+  *p = nullptr;
+  if (n == 0) n = 1;
+  return cudaMalloc((void**)p, n * sizeof(T));
+}
+
+template <typename T>
+void dfree(T*& p) {
+  if (p) cudaFree((void*)p);
+  p = nullptr;
+}
+
+}  // namespace
+
+struct fc_forest {
+  HostForest host;
+  size_t esize = 8;
+  void* buf[2] = {nullptr, nullptr};
+  void* qT = nullptr;
+  void* stage = nullptr;  // device staging for host copies
+  PatchMeta* d_meta = nullptr;
+  NbrEntry* d_nbr = nullptr;
+  int* d_lists = nullptr;  // all work lists, concatenated
+  size_t off_all = 0, off_coarse_all = 0, off_a[kMaxLevel + 1] = {0}, off_b[kMaxLevel + 1] = {0};
+  int* d_api_to_dev = nullptr;
+  int* d_fstart = nullptr;
+  double* d_patch_sums = nullptr;
+  double* d_mass = nullptr;
+  double* d_delta = nullptr;
+  RemapEntry* d_remap = nullptr;
+  int cur[kMaxLevel + 1] = {0};
+  bool has_old[kMaxLevel + 1] = {false};
+  double t_start[kMaxLevel + 1] = {0};
+  double dt_last[kMaxLevel + 1] = {0};
+  // per-phase CUDA-event timers
+  struct Phase {
+    std::vector<cudaEvent_t> ev;  // start/stop pairs
+    std::vector<double> bytes;    // algorithmic bytes of each pending pair
+    size_t used = 0;
+    double ms = 0.0, total_bytes = 0.0;
+    int64_t launches = 0;
+  };
+  bool timing = false;
+  Phase ph[4];
+};
+
+namespace {
+
+// Brackets one launch with a pair of events when the forest's timers are on.
+class Timed {
+ public:
+  Timed(fc_forest* F, int phase, cudaStream_t s, double bytes) : F_(F), s_(s) {
+    if (!F->timing) return;
+    fc_forest::Phase& P = F->ph[phase];
+    if (P.used * 2 + 2 > P.ev.size()) {
+      for (int k = 0; k < 2; ++k) {
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) return;
+        P.ev.push_back(e);
+      }
+    }
+    P_ = &P;
+    idx_ = P.used++;
+    if (P.bytes.size() < P.used) P.bytes.resize(P.used);
+    P.bytes[idx_] = bytes;
+    cudaEventRecord(P.ev[2 * idx_], s_);
+  }
+  ~Timed() {
+    if (P_) cudaEventRecord(P_->ev[2 * idx_ + 1], s_);
+  }
+
+ private:
+  fc_forest* F_;
+  cudaStream_t s_;
+  fc_forest::Phase* P_ = nullptr;
+  size_t idx_ = 0;
+};
+
+void destroy_timers(fc_forest* F) {
+  for (auto& P : F->ph) {
+    for (cudaEvent_t e : P.ev) cudaEventDestroy(e);
+    P.ev.clear();
+    P.used = 0;
+  }
+}
+
+void free_device(fc_forest* F) {
+  dfree(F->buf[0]);
+  dfree(F->buf[1]);
+  dfree(F->qT);
+  dfree(F->stage);
+  dfree(F->d_meta);
+  dfree(F->d_nbr);
+  dfree(F->d_lists);
+  dfree(F->d_api_to_dev);
+  dfree(F->d_fstart);
+  dfree(F->d_patch_sums);
+  dfree(F->d_mass);
+  dfree(F->d_delta);
+  dfree(F->d_remap);
+}
+
+// upload tables (and allocate a store) for the current host layout
+fc_status upload(fc_forest* F, bool alloc_store) {
+  const HostForest& H = F->host;
+  const int n = H.npatch();
+  const size_t S = (size_t)H.desc.mx + 2 * kMbc;
+  const size_t cells = (size_t)n * S * S;
+  if (alloc_store) {
+    for (int b = 0; b < 2; ++b) {
+      dfree(F->buf[b]);
+      if (cudaMalloc(&F->buf[b], std::max<size_t>(cells, 1) * F->esize) != cudaSuccess)
+        return fail(FC_ERR_OOM, "device store allocation failed");
+      FC_CUDA(cudaMemset(F->buf[b], 0, std::max<size_t>(cells, 1) * F->esize));
+    }
+    dfree(F->qT);
+    dfree(F->stage);
+    if (cudaMalloc(&F->qT, std::max<size_t>(cells, 1) * F->esize) != cudaSuccess ||
+        cudaMalloc(&F->stage, std::max<size_t>(cells, 1) * F->esize) != cudaSuccess)
+      return fail(FC_ERR_OOM, "device store allocation failed");
+    FC_CUDA(cudaMemset(F->qT, 0, std::max<size_t>(cells, 1) * F->esize));
+  }
+  dfree(F->d_meta);
+  dfree(F->d_nbr);
+  dfree(F->d_lists);
+  dfree(F->d_api_to_dev);
+  dfree(F->d_fstart);
+  dfree(F->d_patch_sums);
+  dfree(F->d_mass);
+  dfree(F->d_delta);
+  FC_CUDA(dmalloc(&F->d_meta, n));
+  FC_CUDA(dmalloc(&F->d_nbr, (size_t)n * 8));
+  FC_CUDA(cudaMemcpy(F->d_meta, H.meta.data(), sizeof(PatchMeta) * n, cudaMemcpyHostToDevice));
+  FC_CUDA(cudaMemcpy(F->d_nbr, H.nbr.data(), sizeof(NbrEntry) * n * 8, cudaMemcpyHostToDevice));
+  std::vector<int> lists;
+  F->off_all = lists.size();
+  lists.insert(lists.end(), H.list_all.begin(), H.list_all.end());
+  F->off_coarse_all = lists.size();
+  lists.insert(lists.end(), H.list_coarse_all.begin(), H.list_coarse_all.end());
+  for (int l = 0; l <= kMaxLevel; ++l) {
+    F->off_a[l] = lists.size();
+    lists.insert(lists.end(), H.list_a[l].begin(), H.list_a[l].end());
+    F->off_b[l] = lists.size();
+    lists.insert(lists.end(), H.list_b[l].begin(), H.list_b[l].end());
+  }
+  FC_CUDA(dmalloc(&F->d_lists, lists.size()));
+  if (!lists.empty())
+    FC_CUDA(cudaMemcpy(F->d_lists, lists.data(), sizeof(int) * lists.size(), cudaMemcpyHostToDevice));
+  FC_CUDA(dmalloc(&F->d_api_to_dev, n));
+  FC_CUDA(cudaMemcpy(F->d_api_to_dev, H.dev_of.data(), sizeof(int) * n, cudaMemcpyHostToDevice));
+  FC_CUDA(dmalloc(&F->d_fstart, H.forest_start.size()));
+  FC_CUDA(cudaMemcpy(F->d_fstart, H.forest_start.data(), sizeof(int) * H.forest_start.size(),
+                     cudaMemcpyHostToDevice));
+  FC_CUDA(dmalloc(&F->d_patch_sums, n));
+  FC_CUDA(dmalloc(&F->d_mass, H.desc.nforests));
+  FC_CUDA(dmalloc(&F->d_delta, n));
+  return FC_OK;
+}
+
+template <typename real>
+DevForest<real> dev(const fc_forest* F) {
+  DevForest<real> D{};
+  const HostForest& H = F->host;
+  D.mx = H.desc.mx;
+  D.S = H.desc.mx + 2 * kMbc;
+  D.npatch = H.npatch();
+  D.domain = H.desc.domain;
+  D.meta = F->d_meta;
+  D.nbr = F->d_nbr;
+  D.buf[0] = static_cast<real*>(F->buf[0]);
+  D.buf[1] = static_cast<real*>(F->buf[1]);
+  D.qT = static_cast<real*>(F->qT);
+  for (int l = 0; l <= kMaxLevel; ++l) D.cur[l] = F->cur[l];
+  D.vel_kind = H.desc.vel_kind;
+  for (int k = 0; k < 4; ++k) D.vel[k] = H.desc.vel[k];
+  D.order = H.desc.order;
+  D.limiter = H.desc.limiter;
+  D.transverse = H.desc.transverse;
+  return D;
+}
+
+// algorithmic bytes of filling one patch's ghost ring (source read + write)
+double ghost_bytes(const fc_forest* F) {
+  const int mx = F->host.desc.mx;
+  return 2.0 * (4.0 * (mx + 4) + 4.0 * mx) * (double)F->esize;
+}
+
+// algorithmic bytes of advancing n patches: read (mx+4)^2, write mx^2 each
+double advance_bytes(const fc_forest* F, int n) {
+  const double mx = F->host.desc.mx;
+  return (double)n * ((mx + 4) * (mx + 4) + mx * mx) * (double)F->esize;
+}
+
+template <typename real>
+fc_status fill_all_t(fc_forest* F, cudaStream_t s) {
+  DevForest<real> D = dev<real>(F);
+  const HostForest& H = F->host;
+  const double gb = ghost_bytes(F);
+  FillArgs A{F->d_lists + F->off_all, (int)H.list_all.size(), -1, 0.0};
+  {
+    Timed tm(F, 1, s, gb * A.ntargets);
+    FC_CUDA(launch_fill_coarse(D, A, s));
+  }
+  FillArgs B{F->d_lists + F->off_coarse_all, (int)H.list_coarse_all.size(), -1, 0.0};
+  {
+    Timed tm(F, 1, s, gb * B.ntargets);
+    FC_CUDA(launch_fill_fine(D, B, s));
+  }
+  return FC_OK;
+}
+
+fc_status fill_all(fc_forest* F, cudaStream_t s) {
+  return F->esize == 4 ? fill_all_t<float>(F, s) : fill_all_t<double>(F, s);
+}
+
+template <typename real>
+fc_status advance_level_t(fc_forest* F, int L, double t, double dt, cudaStream_t s) {
+  const HostForest& H = F->host;
+  const int p0 = H.lev_start[L], p1 = H.lev_start[L + 1];
+  int tlevel = -1;
+  double alpha = 0.0;
+  if (L > H.desc.lmin && F->has_old[L - 1] && F->dt_last[L - 1] > 0.0) {
+    tlevel = L - 1;
+    alpha = (t - F->t_start[L - 1]) / F->dt_last[L - 1];
+    alpha = std::min(1.0, std::max(0.0, alpha));
+  }
+  DevForest<real> D = dev<real>(F);
+  if (p1 > p0) {
+    const double gb = ghost_bytes(F);
+    FillArgs A{F->d_lists + F->off_a[L], (int)H.list_a[L].size(), tlevel, alpha};
+    {
+      Timed tm(F, 1, s, gb * A.ntargets);
+      FC_CUDA(launch_fill_coarse(D, A, s));
+    }
+    FillArgs B{F->d_lists + F->off_b[L], (int)H.list_b[L].size(), tlevel, alpha};
+    {
+      Timed tm(F, 1, s, gb * B.ntargets);
+      FC_CUDA(launch_fill_fine(D, B, s));
+    }
+    {
+      Timed tm(F, 0, s, advance_bytes(F, p1 - p0));
+      FC_CUDA(launch_advance(D, L, p0, p1, t, dt, s));
+    }
+    F->cur[L] ^= 1;
+  }
+  F->has_old[L] = true;
+  F->t_start[L] = t;
+  F->dt_last[L] = dt;
+  return FC_OK;
+}
+
+fc_status advance_level(fc_forest* F, int L, double t, double dt, cudaStream_t s) {
+  return F->esize == 4 ? advance_level_t<float>(F, L, t, dt, s)
+                       : advance_level_t<double>(F, L, t, dt, s);
+}
+
+fc_status multirate(fc_forest* F, int L, double t, double dt, cudaStream_t s) {
+  fc_status st = advance_level(F, L, t, dt, s);
+  if (st != FC_OK) return st;
+  if (L < F->host.desc.lmax) {
+    if ((st = multirate(F, L + 1, t, 0.5 * dt, s)) != FC_OK) return st;
+    if ((st = multirate(F, L + 1, t + 0.5 * dt, 0.5 * dt, s)) != FC_OK) return st;
+  }
+  return FC_OK;
+}
+
+void reset_times(fc_forest* F) {
+  for (int l = 0; l <= kMaxLevel; ++l) {
+    F->has_old[l] = false;
+    F->t_start[l] = 0.0;
+    F->dt_last[l] = 0.0;
+  }
+}
+
+fc_status check_desc(const fc_forest_desc* d) {
+  if (!d) return fail(FC_ERR_INVALID_ARG, "null descriptor");
+  if (d->mx != 8 && d->mx != 16 && d->mx != 32)
+    return fail(FC_ERR_INVALID_ARG, "mx must be 8, 16 or 32");
+  if (d->mbc != kMbc) return fail(FC_ERR_INVALID_ARG, "only mbc = 2 is built");
+  if (4 * d->mbc > d->mx) return fail(FC_ERR_PRECONDITION, "Proposition 1 needs mbc <= mx/4");
+  if (d->lmin < 0 || d->lmax > 16 || d->lmin > d->lmax)
+    return fail(FC_ERR_INVALID_ARG, "level range must satisfy 0 <= lmin <= lmax <= 16");
+  if (d->nforests < 1 || d->nforests > 65535) return fail(FC_ERR_INVALID_ARG, "bad nforests");
+  if (d->dtype != FC_F32 && d->dtype != FC_F64) return fail(FC_ERR_INVALID_ARG, "bad dtype");
+  if (d->domain != FC_DOMAIN_WALLS && d->domain != FC_DOMAIN_PERIODIC)
+    return fail(FC_ERR_INVALID_ARG, "domain not supported by this build");
+  if (d->vel_kind != FC_VEL_CONST && d->vel_kind != FC_VEL_SWIRL)
+    return fail(FC_ERR_INVALID_ARG, "bad velocity kind");
+  if (d->vel_kind == FC_VEL_SWIRL && !(d->vel[0] != 0.0))
+    return fail(FC_ERR_INVALID_ARG, "swirl period must be nonzero");
+  if (d->order < 1 || d->order > 2 || d->limiter < 0 || d->limiter > 1 || d->transverse < 0 ||
+      d->transverse > 2)
+    return fail(FC_ERR_INVALID_ARG, "bad scheme options");
+  return FC_OK;
+}
+
+cudaStream_t as_stream(void* s) { return static_cast<cudaStream_t>(s); }
+
+}  // namespace
+
+extern "C" {
+
+const char* fc_last_error(void) { return g_err.c_str(); }
+
+uint64_t fc_launch_count(int reset) {
+  uint64_t v = launch_counter();
+  if (reset) launch_counter() = 0;
+  return v;
+}
+
+fc_status fc_forest_create(const fc_forest_desc* desc, int nleaves, const int* leaves,
+                           fc_forest** out) {
+  if (!out) return fail(FC_ERR_INVALID_ARG, "null output handle");
+  *out = nullptr;
+  fc_status st = check_desc(desc);
+  if (st != FC_OK) return st;
+  if (nleaves < 1 || !leaves) return fail(FC_ERR_INVALID_ARG, "empty leaf list");
+  fc_forest* F = new (std::nothrow) fc_forest();
+  if (!F) return fail(FC_ERR_OOM, "host allocation failed");
+  F->host.desc = *desc;
+  F->esize = desc->dtype == FC_F32 ? 4 : 8;
+  F->host.leaves.resize(nleaves);
+  for (int k = 0; k < nleaves; ++k)
+    F->host.leaves[k] = Leaf{leaves[5 * k], leaves[5 * k + 1], leaves[5 * k + 2],
+                             leaves[5 * k + 3], leaves[5 * k + 4]};
+  std::string err = F->host.build();
+  if (!err.empty()) {
+    delete F;
+    return fail(FC_ERR_PRECONDITION, err);
+  }
+  st = upload(F, true);
+  if (st != FC_OK) {
+    free_device(F);
+    delete F;
+    return st;
+  }
+  *out = F;
+  return FC_OK;
+}
+
+fc_status fc_forest_destroy(fc_forest* F) {
+  if (!F) return FC_OK;
+  cudaDeviceSynchronize();
+  destroy_timers(F);
+  free_device(F);
+  delete F;
+  return FC_OK;
+}
+
+fc_status fc_timers_enable(fc_forest* F, int enable) {
+  if (!F) return fail(FC_ERR_INVALID_ARG, "null forest");
+  F->timing = enable != 0;
+  return FC_OK;
+}
+
+fc_status fc_timers_read(fc_forest* F, int phase, double* ms, int64_t* launches, double* bytes,
+                         int reset) {
+  if (!F || phase < 0 || phase > 3) return fail(FC_ERR_INVALID_ARG, "bad phase");
+  fc_forest::Phase& P = F->ph[phase];
+  for (size_t k = 0; k < P.used; ++k) {
+    FC_CUDA(cudaEventSynchronize(P.ev[2 * k + 1]));
+    float t = 0.f;
+    FC_CUDA(cudaEventElapsedTime(&t, P.ev[2 * k], P.ev[2 * k + 1]));
+    P.ms += t;
+    P.total_bytes += P.bytes[k];
+    P.launches += 1;
+  }
+  P.used = 0;
+  if (ms) *ms = P.ms;
+  if (launches) *launches = P.launches;
+  if (bytes) *bytes = P.total_bytes;
+  if (reset) {
+    P.ms = 0.0;
+    P.total_bytes = 0.0;
+    P.launches = 0;
+  }
+  return FC_OK;
+}
+
+fc_status fc_forest_num_leaves(const fc_forest* F, int* n) {
+  if (!F || !n) return fail(FC_ERR_INVALID_ARG, "null argument");
+  *n = F->host.npatch();
+  return FC_OK;
+}
+
+fc_status fc_forest_leaves(const fc_forest* F, int* out) {
+  if (!F || !out) return fail(FC_ERR_INVALID_ARG, "null argument");
+  for (int k = 0; k < F->host.npatch(); ++k) {
+    const Leaf& a = F->host.leaves[k];
+    out[5 * k] = a.f;
+    out[5 * k + 1] = a.b;
+    out[5 * k + 2] = a.l;
+    out[5 * k + 3] = a.x;
+    out[5 * k + 4] = a.y;
+  }
+  return FC_OK;
+}
+
+fc_status fc_forest_set_q(fc_forest* F, const void* q, int on_device, void* stream) {
+  if (!F || !q) return fail(FC_ERR_INVALID_ARG, "null argument");
+  cudaStream_t s = as_stream(stream);
+  const size_t bytes = (size_t)F->host.npatch() * F->host.desc.mx * F->host.desc.mx * F->esize;
+  const void* src = q;
+  if (!on_device) {
+    FC_CUDA(cudaMemcpyAsync(F->stage, q, bytes, cudaMemcpyHostToDevice, s));
+    src = F->stage;
+  }
+  cudaError_t e = F->esize == 4
+                      ? launch_unpack(dev<float>(F), F->d_api_to_dev, (const float*)src, s)
+                      : launch_unpack(dev<double>(F), F->d_api_to_dev, (const double*)src, s);
+  if (e != cudaSuccess) return cuda_fail(e, "unpack");
+  if (!on_device) FC_CUDA(cudaStreamSynchronize(s));
+  reset_times(F);
+  return FC_OK;
+}
+
+static fc_status get_q_impl(const fc_forest* F, void* q, int on_device, void* stream, int full) {
+  if (!F || !q) return fail(FC_ERR_INVALID_ARG, "null argument");
+  cudaStream_t s = as_stream(stream);
+  const size_t per = full ? (size_t)(F->host.desc.mx + 4) * (F->host.desc.mx + 4)
+                          : (size_t)F->host.desc.mx * F->host.desc.mx;
+  const size_t bytes = (size_t)F->host.npatch() * per * F->esize;
+  void* dst = on_device ? q : F->stage;
+  cudaError_t e = F->esize == 4
+                      ? launch_pack(dev<float>(F), F->d_api_to_dev, (float*)dst, full, s)
+                      : launch_pack(dev<double>(F), F->d_api_to_dev, (double*)dst, full, s);
+  if (e != cudaSuccess) return cuda_fail(e, "pack");
+  if (!on_device) {
+    FC_CUDA(cudaMemcpyAsync(q, F->stage, bytes, cudaMemcpyDeviceToHost, s));
+    FC_CUDA(cudaStreamSynchronize(s));
+  }
+  return FC_OK;
+}
+
+fc_status fc_forest_get_q(const fc_forest* F, void* q, int on_device, void* stream) {
+  return get_q_impl(F, q, on_device, stream, 0);
+}
+
+fc_status fc_forest_get_q_full(const fc_forest* F, void* q, int on_device, void* stream) {
+  return get_q_impl(F, q, on_device, stream, 1);
+}
+
+fc_status fc_fill_ghosts(fc_forest* F, void* stream) {
+  if (!F) return fail(FC_ERR_INVALID_ARG, "null forest");
+  return fill_all(F, as_stream(stream));
+}
+
+fc_status fc_advance_level(fc_forest* F, int level, double t, double dt, void* stream) {
+  if (!F) return fail(FC_ERR_INVALID_ARG, "null forest");
+  if (level < F->host.desc.lmin || level > F->host.desc.lmax)
+    return fail(FC_ERR_INVALID_ARG, "level outside [lmin, lmax]");
+  if (!(dt > 0.0)) return fail(FC_ERR_INVALID_ARG, "dt must be positive");
+  return advance_level(F, level, t, dt, as_stream(stream));
+}
+
+fc_status fc_step_global(fc_forest* F, double t, double dt, void* stream) {
+  if (!F) return fail(FC_ERR_INVALID_ARG, "null forest");
+  if (!(dt > 0.0)) return fail(FC_ERR_INVALID_ARG, "dt must be positive");
+  cudaStream_t s = as_stream(stream);
+  fc_status st = fill_all(F, s);
+  if (st != FC_OK) return st;
+  const HostForest& H = F->host;
+  cudaError_t e;
+  {
+    Timed tm(F, 0, s, advance_bytes(F, H.npatch()));
+    e = F->esize == 4 ? launch_advance(dev<float>(F), -1, 0, H.npatch(), t, dt, s)
+                      : launch_advance(dev<double>(F), -1, 0, H.npatch(), t, dt, s);
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "advance");
+  for (int l = 0; l <= kMaxLevel; ++l) F->cur[l] ^= 1;
+  reset_times(F);
+  return FC_OK;
+}
+
+fc_status fc_step_multirate(fc_forest* F, double t, double dt_coarse, void* stream) {
+  if (!F) return fail(FC_ERR_INVALID_ARG, "null forest");
+  if (!(dt_coarse > 0.0)) return fail(FC_ERR_INVALID_ARG, "dt must be positive");
+  return multirate(F, F->host.desc.lmin, t, dt_coarse, as_stream(stream));
+}
+
+fc_status fc_tag(fc_forest* F, double* delta_host, void* stream) {
+  if (!F || !delta_host) return fail(FC_ERR_INVALID_ARG, "null argument");
+  cudaStream_t s = as_stream(stream);
+  fc_status st = fill_all(F, s);
+  if (st != FC_OK) return st;
+  const int n = F->host.npatch();
+  cudaError_t e;
+  {
+    Timed tm(F, 2, s, (double)n * F->host.desc.mx * F->host.desc.mx * F->esize);
+    e = F->esize == 4 ? launch_tag(dev<float>(F), F->d_delta, s)
+                      : launch_tag(dev<double>(F), F->d_delta, s);
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "tag");
+  std::vector<double> dd(n);
+  FC_CUDA(cudaMemcpyAsync(dd.data(), F->d_delta, sizeof(double) * n, cudaMemcpyDeviceToHost, s));
+  FC_CUDA(cudaStreamSynchronize(s));
+  for (int k = 0; k < n; ++k) delta_host[k] = dd[F->host.dev_of[k]];
+  return FC_OK;
+}
+
+fc_status fc_tag_regrid(fc_forest* F, double tau_refine, double tau_coarsen,
+                        const int* lmax_per_forest, int* changed, void* stream) {
+  if (!F) return fail(FC_ERR_INVALID_ARG, "null forest");
+  cudaStream_t s = as_stream(stream);
+  const int n = F->host.npatch();
+  std::vector<double> delta(n);
+  fc_status st = fc_tag(F, delta.data(), stream);
+  if (st != FC_OK) return st;
+  std::vector<int> lmax_f;
+  if (lmax_per_forest) lmax_f.assign(lmax_per_forest, lmax_per_forest + F->host.desc.nforests);
+  std::vector<Leaf> nl;
+  std::string err = regrid_layout(F->host, delta, tau_refine, tau_coarsen, lmax_f, &nl);
+  if (!err.empty()) return fail(FC_ERR_STATE, err);
+  // unchanged layout?
+  bool same = (int)nl.size() == n;
+  for (int k = 0; same && k < n; ++k) {
+    const Leaf& a = nl[k];
+    const Leaf& b = F->host.leaves[k];
+    same = a.f == b.f && a.b == b.b && a.l == b.l && a.x == b.x && a.y == b.y;
+  }
+  if (same) {
+    if (changed) *changed = 0;
+    return FC_OK;
+  }
+  fc_forest* G = new (std::nothrow) fc_forest();
+  if (!G) return fail(FC_ERR_OOM, "host allocation failed");
+  G->host.desc = F->host.desc;
+  G->esize = F->esize;
+  G->host.leaves = nl;
+  err = G->host.build();
+  if (!err.empty()) {
+    delete G;
+    return fail(FC_ERR_STATE, "regrid produced an invalid layout: " + err);
+  }
+  st = upload(G, true);
+  if (st != FC_OK) {
+    free_device(G);
+    delete G;
+    return st;
+  }
+  // remap list in G's device order
+  const HostForest& O = F->host;
+  const HostForest& N = G->host;
+  std::vector<RemapEntry> rm(N.npatch());
+  int created = 0, kept = 0;
+  for (int p = 0; p < N.npatch(); ++p) {
+    const Leaf& a = N.leaves[N.api_of[p]];
+    RemapEntry e{RM_COPY, {-1, -1, -1, -1}, 0, 0};
+    int o = O.find(a.f, a.b, a.l, a.x, a.y);
+    if (o >= 0) {
+      e.src[0] = O.dev_of[o];
+      ++kept;
+    } else {
+      ++created;
+      int par = a.l > 0 ? O.find(a.f, a.b, a.l - 1, a.x >> 1, a.y >> 1) : -1;
+      if (par >= 0) {
+        e.kind = RM_INTERP;
+        e.src[0] = O.dev_of[par];
+        e.cx = a.x & 1;
+        e.cy = a.y & 1;
+      } else {
+        e.kind = RM_AVERAGE;
+        for (int c = 0; c < 4; ++c) {
+          int ch = O.find(a.f, a.b, a.l + 1, 2 * a.x + (c & 1), 2 * a.y + (c >> 1));
+          if (ch < 0) {
+            free_device(G);
+            delete G;
+            return fail(FC_ERR_STATE, "regrid: new leaf has neither an old parent nor children");
+          }
+          e.src[c] = O.dev_of[ch];
+        }
+      }
+    }
+    rm[p] = e;
+  }
+  dfree(G->d_remap);
+  if (dmalloc(&G->d_remap, rm.size()) != cudaSuccess) {
+    free_device(G);
+    delete G;
+    return fail(FC_ERR_OOM, "remap list allocation failed");
+  }
+  FC_CUDA(cudaMemcpyAsync(G->d_remap, rm.data(), sizeof(RemapEntry) * rm.size(),
+                          cudaMemcpyHostToDevice, s));
+  cudaError_t e;
+  {
+    Timed tm(F, 2, s, 2.0 * (double)N.npatch() * N.desc.mx * N.desc.mx * F->esize);
+    e = F->esize == 4 ? launch_remap(dev<float>(F), dev<float>(G), G->d_remap, s)
+                      : launch_remap(dev<double>(F), dev<double>(G), G->d_remap, s);
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "remap");
+  FC_CUDA(cudaStreamSynchronize(s));
+  // swap contents: F takes G's layout and store
+  free_device(F);
+  F->host = std::move(G->host);
+  std::memcpy(F->buf, G->buf, sizeof F->buf);
+  F->qT = G->qT;
+  F->stage = G->stage;
+  F->d_meta = G->d_meta;
+  F->d_nbr = G->d_nbr;
+  F->d_lists = G->d_lists;
+  F->off_all = G->off_all;
+  F->off_coarse_all = G->off_coarse_all;
+  std::memcpy(F->off_a, G->off_a, sizeof F->off_a);
+  std::memcpy(F->off_b, G->off_b, sizeof F->off_b);
+  F->d_api_to_dev = G->d_api_to_dev;
+  F->d_fstart = G->d_fstart;
+  F->d_patch_sums = G->d_patch_sums;
+  F->d_mass = G->d_mass;
+  F->d_delta = G->d_delta;
+  F->d_remap = G->d_remap;
+  for (int l = 0; l <= kMaxLevel; ++l) F->cur[l] = 0;
+  reset_times(F);
+  delete G;  // its device pointers now belong to F
+  if (changed) *changed = created + (n - kept);
+  return FC_OK;
+}
+
+static fc_status host_layout(const fc_forest_desc* desc, int nleaves, const int* leaves,
+                             HostForest* H) {
+  fc_status st = check_desc(desc);
+  if (st != FC_OK) return st;
+  if (nleaves < 1 || !leaves) return fail(FC_ERR_INVALID_ARG, "empty leaf list");
+  H->desc = *desc;
+  H->leaves.resize(nleaves);
+  for (int k = 0; k < nleaves; ++k)
+    H->leaves[k] = Leaf{leaves[5 * k], leaves[5 * k + 1], leaves[5 * k + 2], leaves[5 * k + 3],
+                        leaves[5 * k + 4]};
+  std::string err = H->build();
+  if (!err.empty()) return fail(FC_ERR_PRECONDITION, err);
+  return FC_OK;
+}
+
+fc_status fc_layout_check(const fc_forest_desc* desc, int nleaves, const int* leaves) {
+  HostForest H;
+  return host_layout(desc, nleaves, leaves, &H);
+}
+
+fc_status fc_layout_neighbours(const fc_forest_desc* desc, int nleaves, const int* leaves,
+                               int* out) {
+  if (!out) return fail(FC_ERR_INVALID_ARG, "null output");
+  HostForest H;
+  fc_status st = host_layout(desc, nleaves, leaves, &H);
+  if (st != FC_OK) return st;
+  for (int k = 0; k < nleaves; ++k) {
+    const int p = H.dev_of[k];
+    for (int d = 0; d < 8; ++d) {
+      const NbrEntry& e = H.nbr[(size_t)p * 8 + d];
+      int* o = out + ((size_t)k * 8 + d) * 6;
+      o[0] = e.kind;
+      o[1] = e.n0 >= 0 ? H.api_of[e.n0] : -1;
+      o[2] = e.n1 >= 0 ? H.api_of[e.n1] : -1;
+      o[3] = e.a;
+      o[4] = e.fx;
+      o[5] = e.fy;
+    }
+  }
+  return FC_OK;
+}
+
+fc_status fc_layout_regrid(const fc_forest_desc* desc, int nleaves, const int* leaves,
+                           const double* delta, double tau_refine, double tau_coarsen,
+                           const int* lmax_per_forest, int cap, int* out_leaves, int* nout) {
+  if (!delta || !out_leaves || !nout) return fail(FC_ERR_INVALID_ARG, "null argument");
+  HostForest H;
+  fc_status st = host_layout(desc, nleaves, leaves, &H);
+  if (st != FC_OK) return st;
+  // delta arrives in the caller's leaf order; H sorted its leaves
+  std::vector<double> d(nleaves);
+  for (int k = 0; k < nleaves; ++k) {
+    const int* a = leaves + 5 * k;
+    d[H.find(a[0], a[1], a[2], a[3], a[4])] = delta[k];
+  }
+  std::vector<int> lmax_f;
+  if (lmax_per_forest) lmax_f.assign(lmax_per_forest, lmax_per_forest + desc->nforests);
+  std::vector<Leaf> nl;
+  std::string err = regrid_layout(H, d, tau_refine, tau_coarsen, lmax_f, &nl);
+  if (!err.empty()) return fail(FC_ERR_STATE, err);
+  *nout = (int)nl.size();
+  if ((int)nl.size() > cap) return fail(FC_ERR_INVALID_ARG, "output capacity too small");
+  for (size_t k = 0; k < nl.size(); ++k) {
+    int* o = out_leaves + 5 * k;
+    o[0] = nl[k].f;
+    o[1] = nl[k].b;
+    o[2] = nl[k].l;
+    o[3] = nl[k].x;
+    o[4] = nl[k].y;
+  }
+  return FC_OK;
+}
+
+fc_status fc_forest_mass(const fc_forest* F, double* out, void* stream) {
+  if (!F || !out) return fail(FC_ERR_INVALID_ARG, "null argument");
+  cudaStream_t s = as_stream(stream);
+  const int nf = F->host.desc.nforests;
+  cudaError_t e =
+      F->esize == 4
+          ? launch_mass(dev<float>(F), F->d_api_to_dev, F->d_fstart, nf, F->d_patch_sums,
+                        F->d_mass, s)
+          : launch_mass(dev<double>(F), F->d_api_to_dev, F->d_fstart, nf, F->d_patch_sums,
+                        F->d_mass, s);
+  if (e != cudaSuccess) return cuda_fail(e, "mass");
+  FC_CUDA(cudaMemcpyAsync(out, F->d_mass, sizeof(double) * nf, cudaMemcpyDeviceToHost, s));
+  FC_CUDA(cudaStreamSynchronize(s));
+  return FC_OK;
+}
+
+}  // extern "C"

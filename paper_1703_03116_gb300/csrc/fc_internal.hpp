@@ -1,0 +1,136 @@
+// Internal declarations shared by the host forest, the scheduler and the
+// CUDA kernels.  Nothing here crosses the C ABI (include/fc.h).
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <string>
+#include <unordered_map>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "fc.h"
+
+namespace fc {
+
+constexpr int kMaxLevel = 20;
+constexpr int kMbc = 2;  // ghost layers built into the kernels
+
+// Neighbour relation of one face or corner region of a patch (Sec. 2.2):
+// same-size neighbour (copy), finer neighbour(s) (average), coarser neighbour
+// (interpolate), or outside the physical domain (boundary condition).
+enum NbrKind : int { NB_EXTERIOR = 0, NB_SAME = 1, NB_FINE = 2, NB_COARSE = 3 };
+
+// Region order: faces -x, +x, -y, +y, then corners (-,-), (+,-), (-,+), (+,+).
+constexpr int kDirX[8] = {-1, 1, 0, 0, -1, 1, -1, 1};
+constexpr int kDirY[8] = {0, 0, -1, 1, -1, -1, 1, 1};
+
+// Index transform of Eq. (transform): I' = A I + F maps the owner's level-l
+// global cell index I into the neighbour block's level-l global index I'.
+// A is a signed permutation: bit 0 swaps the axes, bits 1 and 2 negate the
+// first and second output component.
+struct NbrEntry {
+  int kind;
+  int n0, n1;  // device patch indices; n1 only for a face with two fine patches
+  int a;       // orientation code of A
+  int fx, fy;  // F
+};
+
+struct PatchMeta {
+  int level, x, y, block, forest, flags;  // flags bit 0: has a coarser neighbour
+};
+
+struct Leaf {
+  int f, b, l, x, y;
+};
+
+inline uint64_t leaf_key(int f, int b, int l, int x, int y) {
+  return ((uint64_t)(uint32_t)f << 48) | ((uint64_t)(uint32_t)b << 45) |
+         ((uint64_t)(uint32_t)l << 40) | ((uint64_t)(uint32_t)x << 20) | (uint64_t)(uint32_t)y;
+}
+
+// Remap entry for regridding (Sec. 3.1).
+enum RemapKind : int { RM_COPY = 0, RM_INTERP = 1, RM_AVERAGE = 2 };
+struct RemapEntry {
+  int kind;
+  int src[4];  // old device patches: COPY/INTERP use src[0]; AVERAGE uses 4 children
+  int cx, cy;  // INTERP: position of the new child inside the old parent
+};
+
+// Host-side forest: leaves, lookup, neighbour tables, level work lists.
+struct HostForest {
+  fc_forest_desc desc{};
+  std::vector<Leaf> leaves;              // field order (forest, block, Morton)
+  std::unordered_map<uint64_t, int> idx; // key -> index in `leaves`
+  std::vector<int> dev_of;               // leaves index -> device patch index
+  std::vector<int> api_of;               // device patch index -> leaves index
+  std::vector<PatchMeta> meta;           // device order
+  std::vector<NbrEntry> nbr;             // device order, 8 per patch
+  int lev_start[kMaxLevel + 2] = {0};    // device patches of level l: [lev_start[l], lev_start[l+1])
+  std::vector<int> list_all, list_coarse_all;
+  std::vector<int> list_a[kMaxLevel + 1], list_b[kMaxLevel + 1];
+  std::vector<int> forest_start;         // leaves of forest f: [forest_start[f], forest_start[f+1])
+
+  // Build everything from `leaves`; returns an empty string or an error.
+  std::string build();
+  int find(int f, int b, int l, int x, int y) const {
+    auto it = idx.find(leaf_key(f, b, l, x, y));
+    return it == idx.end() ? -1 : it->second;
+  }
+  int npatch() const { return (int)leaves.size(); }
+};
+
+// Regrid: new leaf list and remap list (in the new field order).
+std::string regrid_layout(const HostForest& F, const std::vector<double>& delta, double tau_r,
+                          double tau_c, const std::vector<int>& lmax_f,
+                          std::vector<Leaf>* out_leaves);
+void sort_leaves(std::vector<Leaf>* v);
+
+// ---------------------------------------------------------------- device side
+
+template <typename real>
+struct DevForest {
+  int mx, S, npatch, domain;
+  const PatchMeta* meta;
+  const NbrEntry* nbr;
+  real* buf[2];
+  real* qT;
+  int cur[kMaxLevel + 1];
+  int vel_kind;
+  double vel[4];
+  int order, limiter, transverse;
+};
+
+struct FillArgs {
+  const int* targets;
+  int ntargets;
+  int tlevel;    // level read/written through the time-interpolated buffer, -1 none
+  double alpha;  // time-interpolation weight of the newer state
+};
+
+template <typename real>
+cudaError_t launch_fill_coarse(const DevForest<real>& D, const FillArgs& A, cudaStream_t s);
+template <typename real>
+cudaError_t launch_fill_fine(const DevForest<real>& D, const FillArgs& A, cudaStream_t s);
+template <typename real>
+cudaError_t launch_advance(const DevForest<real>& D, int level, int p0, int p1, double t,
+                           double dt, cudaStream_t s);
+template <typename real>
+cudaError_t launch_tag(const DevForest<real>& D, double* delta, cudaStream_t s);
+template <typename real>
+cudaError_t launch_mass(const DevForest<real>& D, const int* api_to_dev, const int* fstart,
+                        int nforests, double* patch_sums, double* out, cudaStream_t s);
+template <typename real>
+cudaError_t launch_pack(const DevForest<real>& D, const int* api_to_dev, real* out, int full,
+                        cudaStream_t s);
+template <typename real>
+cudaError_t launch_unpack(const DevForest<real>& D, const int* api_to_dev, const real* in,
+                          cudaStream_t s);
+template <typename real>
+cudaError_t launch_remap(const DevForest<real>& Old, const DevForest<real>& New,
+                         const RemapEntry* rm, cudaStream_t s);
+
+uint64_t& launch_counter();
+
+}  // namespace fc

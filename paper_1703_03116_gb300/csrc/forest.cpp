@@ -1,0 +1,341 @@
+// Host-side forest of quadtrees: leaf lookup, face/corner neighbour tables
+// with index transforms, level work lists, and the regrid layout (refine,
+// 2:1 balance, coarsen).
+//
+// Sec. 2 (quadtree layout): a level-l quadrant of a unit block has edge 2^-l;
+// only leaves hold patches; leaves are enumerated in Morton order; any two
+// leaves sharing a face or corner differ by at most one level.
+// Sec. 2.2/2.4: each face or corner region of a patch is filled from one
+// same-size neighbour, two (face) or one (corner) finer neighbours, or one
+// coarser neighbour; Eq. (transform) I_n = A I_c + F maps indices between
+// the two patches.
+// Sec. 3.1: tagged grids are refined, quiet families of four siblings are
+// coarsened, and 2:1 balancing may add refinement.
+#include <algorithm>
+#include <cstdio>
+
+#include "fc_internal.hpp"
+
+namespace fc {
+
+static uint64_t spread_bits(uint32_t v) {
+  uint64_t x = v;
+  x = (x | (x << 16)) & 0x0000FFFF0000FFFFull;
+  x = (x | (x << 8)) & 0x00FF00FF00FF00FFull;
+  x = (x | (x << 4)) & 0x0F0F0F0F0F0F0F0Full;
+  x = (x | (x << 2)) & 0x3333333333333333ull;
+  x = (x | (x << 1)) & 0x5555555555555555ull;
+  return x;
+}
+
+static uint64_t morton_key(const Leaf& a) {
+  const int sh = kMaxLevel - a.l;
+  return spread_bits((uint32_t)a.x << sh) | (spread_bits((uint32_t)a.y << sh) << 1);
+}
+
+void sort_leaves(std::vector<Leaf>* v) {
+  std::sort(v->begin(), v->end(), [](const Leaf& a, const Leaf& b) {
+    if (a.f != b.f) return a.f < b.f;
+    if (a.b != b.b) return a.b < b.b;
+    uint64_t ka = morton_key(a), kb = morton_key(b);
+    if (ka != kb) return ka < kb;
+    return a.l < b.l;
+  });
+}
+
+static int nblocks(const fc_forest_desc& d) { return d.domain == FC_DOMAIN_SPHERE ? 6 : 1; }
+
+namespace {
+
+// Where does quadrant (b, l, x, y) of a forest lie once moved across the
+// block boundary?  For the square domains the neighbour lies in the same
+// block (periodic) or outside the domain (walls).  Returns false for the
+// exterior.  *fx, *fy: shift of level-l cell indices into the new frame.
+struct Moved {
+  int b, x, y, a, fx, fy;
+};
+
+bool move_quadrant(const fc_forest_desc& d, int b, int l, int x, int y, int mx, Moved* m) {
+  const int N = 1 << l;
+  m->b = b;
+  m->x = x;
+  m->y = y;
+  m->a = 0;
+  m->fx = 0;
+  m->fy = 0;
+  if (x >= 0 && x < N && y >= 0 && y < N) return true;
+  if (d.domain == FC_DOMAIN_WALLS) return false;
+  if (d.domain == FC_DOMAIN_PERIODIC) {
+    if (x < 0) { m->x = x + N; m->fx = N * mx; }
+    if (x >= N) { m->x = x - N; m->fx = -N * mx; }
+    if (y < 0) { m->y = y + N; m->fy = N * mx; }
+    if (y >= N) { m->y = y - N; m->fy = -N * mx; }
+    return true;
+  }
+  return false;  // cubed sphere: not in this build
+}
+
+}  // namespace
+
+std::string HostForest::build() {
+  const fc_forest_desc& d = desc;
+  const int mx = d.mx;
+  const int nb = nblocks(d);
+  sort_leaves(&leaves);
+  idx.clear();
+  idx.reserve(leaves.size() * 2);
+  for (size_t k = 0; k < leaves.size(); ++k) {
+    const Leaf& a = leaves[k];
+    if (a.f < 0 || a.f >= d.nforests || a.b < 0 || a.b >= nb || a.l < d.lmin || a.l > d.lmax ||
+        a.x < 0 || a.y < 0 || a.x >= (1 << a.l) || a.y >= (1 << a.l))
+      return "leaf out of range";
+    if (!idx.emplace(leaf_key(a.f, a.b, a.l, a.x, a.y), (int)k).second) return "duplicate leaf";
+  }
+  // exact tiling: areas of each block sum to one and no leaf has a leaf ancestor
+  std::vector<double> area((size_t)d.nforests * nb, 0.0);
+  for (const Leaf& a : leaves) {
+    area[(size_t)a.f * nb + a.b] += std::ldexp(1.0, -2 * a.l);
+    for (int l = a.l - 1; l >= d.lmin; --l)
+      if (find(a.f, a.b, l, a.x >> (a.l - l), a.y >> (a.l - l)) >= 0)
+        return "overlapping leaves";
+  }
+  for (double s : area)
+    if (s != 1.0) return "leaves do not tile every block";
+
+  // device order: (level, field order)
+  const int n = (int)leaves.size();
+  std::vector<int> order(n);
+  for (int k = 0; k < n; ++k) order[k] = k;
+  std::stable_sort(order.begin(), order.end(),
+                   [&](int a, int b) { return leaves[a].l < leaves[b].l; });
+  api_of = order;
+  dev_of.assign(n, 0);
+  for (int p = 0; p < n; ++p) dev_of[api_of[p]] = p;
+  for (int l = 0; l <= kMaxLevel + 1; ++l) lev_start[l] = 0;
+  for (int p = 0; p < n; ++p) lev_start[leaves[api_of[p]].l + 1]++;
+  for (int l = 1; l <= kMaxLevel + 1; ++l) lev_start[l] += lev_start[l - 1];
+
+  forest_start.assign(d.nforests + 1, 0);
+  for (const Leaf& a : leaves) forest_start[a.f + 1]++;
+  for (int f = 0; f < d.nforests; ++f) forest_start[f + 1] += forest_start[f];
+
+  meta.assign(n, PatchMeta{});
+  nbr.assign((size_t)n * 8, NbrEntry{});
+  for (int p = 0; p < n; ++p) {
+    const Leaf& a = leaves[api_of[p]];
+    meta[p] = PatchMeta{a.l, a.x, a.y, a.b, a.f, 0};
+    for (int dir = 0; dir < 8; ++dir) {
+      NbrEntry e{NB_EXTERIOR, -1, -1, 0, 0, 0};
+      Moved m;
+      if (move_quadrant(d, a.b, a.l, a.x + kDirX[dir], a.y + kDirY[dir], mx, &m)) {
+        e.a = m.a;
+        e.fx = m.fx;
+        e.fy = m.fy;
+        int s = find(a.f, m.b, a.l, m.x, m.y);
+        if (s >= 0) {
+          e.kind = NB_SAME;
+          e.n0 = dev_of[s];
+        } else {
+          int c = (a.l > d.lmin) ? find(a.f, m.b, a.l - 1, m.x >> 1, m.y >> 1) : -1;
+          if (c >= 0) {
+            e.kind = NB_COARSE;
+            e.n0 = dev_of[c];
+            meta[p].flags |= 1;
+          } else {
+            // finer: the children of the same-size quadrant that touch this patch
+            const int ox = kDirX[dir], oy = kDirY[dir];
+            int cx[2], cy[2], nc;
+            if (ox != 0 && oy != 0) {
+              nc = 1;
+              cx[0] = 2 * m.x + (ox < 0 ? 1 : 0);
+              cy[0] = 2 * m.y + (oy < 0 ? 1 : 0);
+            } else if (ox != 0) {
+              nc = 2;
+              cx[0] = cx[1] = 2 * m.x + (ox < 0 ? 1 : 0);
+              cy[0] = 2 * m.y;
+              cy[1] = 2 * m.y + 1;
+            } else {
+              nc = 2;
+              cy[0] = cy[1] = 2 * m.y + (oy < 0 ? 1 : 0);
+              cx[0] = 2 * m.x;
+              cx[1] = 2 * m.x + 1;
+            }
+            int ids[2] = {-1, -1};
+            for (int k = 0; k < nc; ++k) {
+              ids[k] = (a.l < d.lmax) ? find(a.f, m.b, a.l + 1, cx[k], cy[k]) : -1;
+              if (ids[k] < 0) {
+                char buf[160];
+                std::snprintf(buf, sizeof buf,
+                              "leaf (f=%d b=%d l=%d x=%d y=%d): region %d has no neighbour within "
+                              "one level (layout not 2:1 balanced)",
+                              a.f, a.b, a.l, a.x, a.y, dir);
+                return buf;
+              }
+            }
+            e.kind = NB_FINE;
+            e.n0 = dev_of[ids[0]];
+            e.n1 = nc == 2 ? dev_of[ids[1]] : -1;
+          }
+        }
+      }
+      nbr[(size_t)p * 8 + dir] = e;
+    }
+  }
+  // work lists
+  list_all.resize(n);
+  list_coarse_all.clear();
+  for (int p = 0; p < n; ++p) {
+    list_all[p] = p;
+    if (meta[p].flags & 1) list_coarse_all.push_back(p);
+  }
+  for (int l = 0; l <= kMaxLevel; ++l) {
+    list_a[l].clear();
+    list_b[l].clear();
+  }
+  for (int l = 0; l <= kMaxLevel; ++l) {
+    std::vector<char> inT;
+    if (l > 0) inT.assign(n, 0);
+    for (int p = lev_start[l]; p < lev_start[l + 1]; ++p) {
+      if (meta[p].flags & 1) {
+        list_b[l].push_back(p);
+        for (int dir = 0; dir < 8; ++dir) {
+          const NbrEntry& e = nbr[(size_t)p * 8 + dir];
+          if (e.kind == NB_COARSE) inT[e.n0] = 1;
+        }
+      }
+    }
+    if (l > 0)
+      for (int p = lev_start[l - 1]; p < lev_start[l]; ++p)
+        if (inT[p]) list_a[l].push_back(p);
+    for (int p = lev_start[l]; p < lev_start[l + 1]; ++p) list_a[l].push_back(p);
+  }
+  return "";
+}
+
+// ------------------------------------------------------------------ regrid
+
+namespace {
+
+struct LeafSet {
+  const fc_forest_desc* d;
+  std::unordered_map<uint64_t, Leaf> m;
+  bool has(int f, int b, int l, int x, int y) const {
+    return m.count(leaf_key(f, b, l, x, y)) != 0;
+  }
+  void add(const Leaf& a) { m.emplace(leaf_key(a.f, a.b, a.l, a.x, a.y), a); }
+  void erase(const Leaf& a) { m.erase(leaf_key(a.f, a.b, a.l, a.x, a.y)); }
+  // level of the leaf containing quadrant (b, l, x, y) if that leaf is at
+  // level <= l, else -1 (the quadrant is subdivided)
+  int holder_level(int f, int b, int l, int x, int y, Leaf* out) const {
+    for (int k = l; k >= d->lmin; --k) {
+      auto it = m.find(leaf_key(f, b, k, x >> (l - k), y >> (l - k)));
+      if (it != m.end()) {
+        if (out) *out = it->second;
+        return k;
+      }
+    }
+    return -1;
+  }
+};
+
+void refine_into(LeafSet* s, const Leaf& a) {
+  s->erase(a);
+  for (int c = 0; c < 4; ++c) s->add(Leaf{a.f, a.b, a.l + 1, 2 * a.x + (c & 1), 2 * a.y + (c >> 1)});
+}
+
+// 2:1 balance by refinement: any leaf that holds a quadrant adjacent to a
+// leaf two or more levels finer is refined, until no such leaf remains.
+void balance(LeafSet* s, int mx) {
+  for (;;) {
+    std::unordered_map<uint64_t, Leaf> marks;
+    for (const auto& kv : s->m) {
+      const Leaf& c = kv.second;
+      if (c.l < s->d->lmin + 2) continue;
+      for (int dir = 0; dir < 8; ++dir) {
+        Moved m;
+        if (!move_quadrant(*s->d, c.b, c.l, c.x + kDirX[dir], c.y + kDirY[dir], mx, &m)) continue;
+        Leaf h;
+        int hl = s->holder_level(c.f, m.b, c.l, m.x, m.y, &h);
+        if (hl >= 0 && hl <= c.l - 2) marks.emplace(leaf_key(h.f, h.b, h.l, h.x, h.y), h);
+      }
+    }
+    if (marks.empty()) return;
+    for (const auto& kv : marks) refine_into(s, kv.second);
+  }
+}
+
+// Would the parent P of a family stay balanced?  Every quadrant two levels
+// finer than P that touches P must lie inside a leaf at most one level finer.
+bool parent_balanced(const LeafSet& s, const Leaf& P, int mx) {
+  const int l2 = P.l + 2;
+  const int x0 = 4 * P.x, y0 = 4 * P.y;
+  for (int k = -1; k <= 4; ++k)
+    for (int side = 0; side < 4; ++side) {
+      int zx, zy;
+      if (side == 0) { zx = x0 - 1; zy = y0 + k; }
+      else if (side == 1) { zx = x0 + 4; zy = y0 + k; }
+      else if (side == 2) { zx = x0 + k; zy = y0 - 1; }
+      else { zx = x0 + k; zy = y0 + 4; }
+      Moved m;
+      if (!move_quadrant(*s.d, P.b, l2, zx, zy, mx, &m)) continue;
+      if (s.holder_level(P.f, m.b, l2 - 1, m.x >> 1, m.y >> 1, nullptr) < 0) return false;
+    }
+  return true;
+}
+
+}  // namespace
+
+std::string regrid_layout(const HostForest& F, const std::vector<double>& delta, double tau_r,
+                          double tau_c, const std::vector<int>& lmax_f,
+                          std::vector<Leaf>* out) {
+  const fc_forest_desc& d = F.desc;
+  const int n = F.npatch();
+  std::vector<char> refine(n, 0);
+  for (int k = 0; k < n; ++k) {
+    const Leaf& a = F.leaves[k];
+    int lm = lmax_f.empty() ? d.lmax : std::min(lmax_f[a.f], d.lmax);
+    refine[k] = (delta[k] > tau_r) && (a.l < lm);
+  }
+  std::vector<Leaf> parents;
+  for (int k = 0; k < n; ++k) {
+    const Leaf& a = F.leaves[k];
+    if (a.l <= d.lmin || (a.x & 1) || (a.y & 1)) continue;
+    bool ok = true;
+    for (int c = 0; c < 4 && ok; ++c) {
+      int s = F.find(a.f, a.b, a.l, a.x + (c & 1), a.y + (c >> 1));
+      if (s < 0 || refine[s] || !(delta[s] < tau_c)) ok = false;
+    }
+    if (ok) parents.push_back(Leaf{a.f, a.b, a.l - 1, a.x / 2, a.y / 2});
+  }
+  LeafSet s;
+  s.d = &d;
+  s.m.reserve((size_t)n * 2);
+  for (int k = 0; k < n; ++k)
+    if (!refine[k]) s.add(F.leaves[k]);
+  for (int k = 0; k < n; ++k)
+    if (refine[k]) {
+      const Leaf& a = F.leaves[k];
+      for (int c = 0; c < 4; ++c)
+        s.add(Leaf{a.f, a.b, a.l + 1, 2 * a.x + (c & 1), 2 * a.y + (c >> 1)});
+    }
+  balance(&s, d.mx);
+  std::vector<Leaf> accepted;
+  for (const Leaf& P : parents) {
+    bool all = true;
+    for (int c = 0; c < 4 && all; ++c)
+      all = s.has(P.f, P.b, P.l + 1, 2 * P.x + (c & 1), 2 * P.y + (c >> 1));
+    if (all && parent_balanced(s, P, d.mx)) accepted.push_back(P);
+  }
+  for (const Leaf& P : accepted) {
+    for (int c = 0; c < 4; ++c)
+      s.erase(Leaf{P.f, P.b, P.l + 1, 2 * P.x + (c & 1), 2 * P.y + (c >> 1)});
+    s.add(P);
+  }
+  out->clear();
+  out->reserve(s.m.size());
+  for (const auto& kv : s.m) out->push_back(kv.second);
+  sort_leaves(out);
+  return "";
+}
+
+}  // namespace fc

@@ -1,0 +1,194 @@
+"""Parity of the CUDA path with the FP64 oracle, through the C ABI.
+
+FP64: max |gpu - oracle| / max |oracle| <= 1e-12 (the only differences are
+rounding order and fused multiply-adds).  FP32: the same measure against the
+FP64 oracle started from the same FP32-rounded data; the bound for each case
+is written in the test and the measured value is printed.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from gpu_helpers import F64_TOL, pair, relerr
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+fc = pytest.importorskip("paper_1703_03116_gb300")
+
+
+@pytest.mark.parametrize("mx", [8, 16, 32])
+@pytest.mark.parametrize("domain", ["walls", "periodic"])
+def test_fill_ghosts_bitwise_fp64(mx, domain):
+    """Alg. 1 on an adaptive layout: copy, average and interpolate take the
+    same operations in the same order on both sides -> identical bits."""
+    w = synth.swirl(3, lmin=2, lmax=5 if mx < 32 else 4, mx=mx)
+    w.domain = domain
+    ref, gpu = pair(fc, w, fc.F64)
+    n = len(ref)
+    q = synth.random_field((n, mx, mx), seed=mx)
+    ref.set_q(q)
+    gpu.set_q(q)
+    ref.fill_ghosts()
+    gpu.fill_ghosts()
+    a, b = gpu.get_q(full=True), ref.get_q_full()
+    assert np.all(np.isfinite(a))
+    np.testing.assert_array_equal(a, b)
+
+
+def test_fill_ghosts_fp32():
+    w = synth.swirl(5, lmin=2, lmax=5, mx=16)
+    ref, gpu = pair(fc, w, fc.F32)
+    q = synth.random_field((len(ref), 16, 16), seed=2).astype(np.float32)
+    ref.set_q(q.astype(np.float64))
+    gpu.set_q(q)
+    ref.fill_ghosts()
+    gpu.fill_ghosts()
+    err = relerr(gpu.get_q(full=True), ref.get_q_full())
+    print(f"fp32 ghost fill rel err {err:.2e}")
+    assert err <= 2e-7
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_uniform_periodic_100_steps(seed):
+    """Uniform periodic level-3 forest of 16^2 patches, (u,v) = (1, 0.5),
+    MC + transverse corrections, CFL 0.9, 100 global steps."""
+    w = synth.uniform_periodic(seed)
+    for dtype, tol in ((fc.F64, F64_TOL), (fc.F32, 2e-5)):
+        ref, gpu = pair(fc, w, dtype)
+        dt = w.cfl / 128
+        for n in range(w.steps):
+            ref.step_global(n * dt, dt)
+            gpu.step_global(n * dt, dt)
+        err = relerr(gpu.get_q(), ref.get_q())
+        print(f"uniform periodic seed {seed} dtype {dtype}: rel err {err:.2e}")
+        assert err <= tol
+
+
+@pytest.mark.parametrize("mx,lmax", [(8, 5), (16, 4), (32, 4)])
+def test_swirl_multirate(mx, lmax):
+    w = synth.swirl(2, lmin=2, lmax=lmax, mx=mx)
+    _, dtc = synth.time_step(w)
+    for dtype, tol in ((fc.F64, F64_TOL), (fc.F32, 1e-4)):
+        ref, gpu = pair(fc, w, dtype)
+        for n in range(3):
+            ref.step_multirate(n * dtc, dtc)
+            gpu.step_multirate(n * dtc, dtc)
+        err = relerr(gpu.get_q(), ref.get_q())
+        print(f"swirl multirate mx={mx} lmax={lmax} dtype {dtype}: rel err {err:.2e}")
+        assert np.all(np.isfinite(gpu.get_q()))
+        assert err <= tol
+
+
+def test_swirl_global_steps():
+    w = synth.swirl(7, lmin=2, lmax=4, mx=16)
+    ref, gpu = pair(fc, w, fc.F64)
+    dt = 0.9 / (16 * 16)
+    for n in range(8):
+        ref.step_global(n * dt, dt)
+        gpu.step_global(n * dt, dt)
+    assert relerr(gpu.get_q(), ref.get_q()) <= F64_TOL
+
+
+@pytest.mark.parametrize("scheme", [dict(limiter="none"), dict(limiter="first"),
+                                    dict(transverse=0), dict(transverse=1)])
+def test_scheme_options(scheme):
+    w = synth.swirl(4, lmin=2, lmax=4, mx=8)
+    for k, v in scheme.items():
+        setattr(w, k, v)
+    ref, gpu = pair(fc, w, fc.F64)
+    dt = 0.45 / (8 * 16)   # transverse=0 needs CFL <= 1/2
+    for n in range(4):
+        ref.step_global(n * dt, dt)
+        gpu.step_global(n * dt, dt)
+    assert relerr(gpu.get_q(), ref.get_q()) <= F64_TOL
+
+
+def test_tag_and_regrid_match_oracle():
+    w = synth.swirl(1, lmin=2, lmax=5, mx=16)
+    ref, gpu = pair(fc, w, fc.F64)
+    _, dtc = synth.time_step(w)
+    for n in range(2):
+        ref.step_multirate(n * dtc, dtc)
+        gpu.step_multirate(n * dtc, dtc)
+    np.testing.assert_allclose(gpu.tag(), ref.tag(), rtol=1e-12, atol=1e-14)
+    c_ref = ref.regrid(w.tau_refine, w.tau_coarsen)
+    c_gpu = gpu.tag_regrid(w.tau_refine, w.tau_coarsen)
+    assert c_gpu == c_ref and c_gpu > 0
+    np.testing.assert_array_equal(gpu.leaves(), ref.leaves())
+    assert relerr(gpu.get_q(), ref.get_q()) <= F64_TOL
+
+
+def test_mass_matches_oracle():
+    w = synth.swirl(0, lmin=2, lmax=5, mx=16)
+    ref, gpu = pair(fc, w, fc.F64)
+    m_ref, m_gpu = ref.mass(), gpu.mass()
+    assert abs(m_gpu[0] - m_ref[0]) <= 1e-14 * abs(m_ref[0])
+
+
+def test_batched_forests():
+    ws = synth.ensemble(6, seed=11, lmin=2, mx=16, levels=(3, 4, 5))
+    _, dtc = synth.time_step(ws[0], 5)
+    ref, gpu = pair(fc, ws, fc.F64)
+    lmax_f = [w.lmax for w in ws]
+    for n in range(4):
+        ref.step_multirate(n * dtc, dtc)
+        gpu.step_multirate(n * dtc, dtc)
+    assert relerr(gpu.get_q(), ref.get_q()) <= F64_TOL
+    ref.regrid(0.05, 0.0125, lmax_f)
+    gpu.tag_regrid(0.05, 0.0125, lmax_f)
+    np.testing.assert_array_equal(gpu.leaves(), ref.leaves())
+    np.testing.assert_allclose(gpu.mass(), ref.mass(), rtol=1e-13)
+
+
+def test_single_patch_and_empty_levels():
+    """One periodic patch (its own neighbour in every direction), and a run
+    whose level range includes levels with no patches."""
+    w = synth.uniform_periodic(0, level=0, mx=8, steps=10)
+    ref, gpu = pair(fc, w, fc.F64)
+    assert len(ref) == 1
+    for n in range(10):
+        ref.step_global(n * 0.9 / 8, 0.9 / 8)
+        gpu.step_global(n * 0.9 / 8, 0.9 / 8)
+    assert relerr(gpu.get_q(), ref.get_q()) <= F64_TOL
+    w = synth.swirl(0, lmin=1, lmax=5, mx=8)
+    w.parts = []  # zero field: the layout stays uniform at lmin
+    ref, gpu = pair(fc, w, fc.F64)
+    assert set(ref.leaves()[:, 2]) == {1}
+    q = synth.random_field((len(ref), 8, 8), seed=3)
+    ref.set_q(q)
+    gpu.set_q(q)
+    _, dtc = synth.time_step(w)
+    ref.step_multirate(0.0, dtc)
+    gpu.step_multirate(0.0, dtc)
+    assert relerr(gpu.get_q(), ref.get_q()) <= F64_TOL
+
+
+def test_full_size_swirl_one_coarse_step():
+    """The benchmark workload (levels 2-6, 32^2 patches) for one coarse
+    multirate step plus a regrid, compared everywhere with the oracle."""
+    w = synth.swirl(0)
+    _, dtc = synth.time_step(w)
+    for dtype, tol in ((fc.F64, F64_TOL), (fc.F32, 1e-4)):
+        ref, gpu = pair(fc, w, dtype)
+        assert len(ref) > 300
+        ref.step_multirate(0.0, dtc)
+        gpu.step_multirate(0.0, dtc)
+        err = relerr(gpu.get_q(), ref.get_q())
+        print(f"full-size swirl dtype {dtype}: {len(ref)} patches, rel err {err:.2e}")
+        assert err <= tol
+        if dtype == fc.F64:
+            ref.regrid(w.tau_refine, w.tau_coarsen)
+            gpu.tag_regrid(w.tau_refine, w.tau_coarsen)
+            np.testing.assert_array_equal(gpu.leaves(), ref.leaves())
+
+
+def test_launch_counter_counts_kernels():
+    w = synth.swirl(0, lmin=2, lmax=3, mx=8)
+    ref, gpu = pair(fc, w, fc.F64)
+    fc.launch_count(reset=True)
+    gpu.step_multirate(0.0, 0.01)
+    assert fc.launch_count() >= 3 * 3  # fill (2) + advance per substep

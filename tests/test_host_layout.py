@@ -1,0 +1,160 @@
+"""CPU tests of the library's host side: exported symbols, layout checks,
+neighbour tables and the regrid layout (compared with the oracle)."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+fc = pytest.importorskip("paper_1703_03116_gb300")
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = []
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", fn)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            names += re.findall(r"^\s*(?:const\s+)?\w+\s*\*?\s*(fc_\w+)\s*\(", src, flags=re.M)
+    return sorted(set(names))
+
+
+def test_library_exports_every_declared_symbol():
+    L = fc.load()
+    names = declared_functions()
+    assert len(names) >= 18
+    for n in names:
+        assert hasattr(L, n), n
+    assert set(names) == set(fc._lib.SIGNATURES), set(names) ^ set(fc._lib.SIGNATURES)
+
+
+def desc_for(w, nforests=1, lmax=None, dtype=None):
+    order, lim = {"none": (2, 0), "lw": (2, 0), "mc": (2, 1), "first": (1, 0)}[w.limiter]
+    return fc.make_desc(domain={"walls": fc.WALLS, "periodic": fc.PERIODIC}[w.domain], mx=w.mx,
+                        lmin=w.lmin, lmax=w.lmax if lmax is None else lmax,
+                        dtype=fc.F64 if dtype is None else dtype, velocity=w.velocity,
+                        order=order, limiter=lim, transverse=w.transverse, nforests=nforests)
+
+
+def test_layout_check_accepts_and_rejects():
+    w = synth.swirl(1, lmin=2, lmax=5, mx=8)
+    F = oracle.initial_forest(w)
+    lv = F.leaves()
+    d = desc_for(w)
+    fc.layout_check(d, lv)
+    # drop one leaf: no longer tiles the block
+    with pytest.raises(fc.FcError, match="PRECONDITION"):
+        fc.layout_check(d, lv[1:])
+    # refine one finest leaf twice: 2:1 balance broken
+    k = int(np.argmax(lv[:, 2]))
+    f, b, l, x, y = lv[k]
+    kids = [(f, b, l + 1, 2 * x + (c & 1), 2 * y + (c >> 1)) for c in range(4)]
+    g = kids[0]
+    grand = [(f, b, l + 2, 2 * g[3] + (c & 1), 2 * g[4] + (c >> 1)) for c in range(4)]
+    bad = np.concatenate([np.delete(lv, k, axis=0), np.array(kids[1:] + grand)])
+    d2 = desc_for(w, lmax=l + 2)
+    with pytest.raises(fc.FcError, match="balanced"):
+        fc.layout_check(d2, bad)
+
+
+def brute_holder(lv, f, b, L, X, Y, periodic):
+    """Leaf holding the level-L quadrant (X, Y), by scanning every leaf."""
+    n = 1 << L
+    if periodic:
+        X %= n
+        Y %= n
+    elif not (0 <= X < n and 0 <= Y < n):
+        return None
+    for k, (ff, bb, l, x, y) in enumerate(lv):
+        if ff != f or bb != b:
+            continue
+        if l <= L:
+            if (X >> (L - l)) == x and (Y >> (L - l)) == y:
+                return k
+    return "finer"
+
+
+@pytest.mark.parametrize("domain", ["walls", "periodic"])
+def test_neighbour_table_matches_brute_force(domain):
+    w = synth.swirl(4, lmin=2, lmax=5, mx=8)
+    if domain == "periodic":
+        w.domain = "periodic"
+    F = oracle.initial_forest(w)
+    lv = F.leaves()
+    nb = fc.layout_neighbours(desc_for(w), lv)
+    dirs = [(-1, 0), (1, 0), (0, -1), (0, 1), (-1, -1), (1, -1), (-1, 1), (1, 1)]
+    per = domain == "periodic"
+    kinds = np.zeros(4, int)
+    for k, (f, b, l, x, y) in enumerate(lv):
+        for d, (ox, oy) in enumerate(dirs):
+            kind, n0, n1, a, fx, fy = nb[k, d]
+            kinds[kind] += 1
+            h = brute_holder(lv, f, b, l, x + ox, y + oy, per)
+            if h is None:
+                assert kind == 0
+            elif h == "finer":
+                assert kind == 2
+                for n in (n0, n1):
+                    if n >= 0:
+                        assert lv[n, 2] == l + 1
+                assert (n1 >= 0) == (ox == 0 or oy == 0)
+            else:
+                assert kind == (1 if lv[h, 2] == l else 3)
+                assert n0 == h
+            assert a == 0  # one block: identity orientation
+    assert np.all(kinds[1:] > 0)
+
+
+def test_twenty_same_block_cases():
+    """Sec. 2.4: seen from the coarser grid there are 4 x (3 + 2) = 20 cases:
+    per face one same-size and two fine-neighbour positions, per corner one
+    same-size and one fine neighbour."""
+    seen = set()
+    for seed in range(6):
+        w = synth.swirl(seed, lmin=2, lmax=5, mx=8)
+        F = oracle.initial_forest(w)
+        lv = F.leaves()
+        nb = fc.layout_neighbours(desc_for(w), lv)
+        for k in range(len(lv)):
+            for d in range(8):
+                kind, n0, n1 = nb[k, d, :3]
+                if kind == 1:
+                    seen.add((d, "same"))
+                elif kind == 2:
+                    if d < 4:
+                        seen.add((d, "fine", 0))
+                        seen.add((d, "fine", 1))
+                    else:
+                        seen.add((d, "fine"))
+    assert len(seen) == 20
+
+
+@pytest.mark.parametrize("seed", range(4))
+@pytest.mark.parametrize("taus", [(0.05, 0.0125), (0.2, 0.15), (-1.0, -1.0), (np.inf, np.inf)])
+def test_regrid_layout_matches_oracle(seed, taus):
+    w = synth.swirl(seed, lmin=2, lmax=5, mx=8)
+    F = oracle.initial_forest(w)
+    lv = F.leaves()
+    F.set_q(synth.random_field((len(lv), 8, 8), seed=seed) ** 6)
+    delta = F.tag()
+    got = fc.layout_regrid(desc_for(w), lv, delta, *taus)
+    F.regrid(*taus)
+    assert np.array_equal(got, F.leaves())
+
+
+def test_regrid_layout_batched_forests_matches_oracle():
+    ws = synth.ensemble(5, seed=3, lmin=2, mx=8, levels=(3, 4, 5))
+    F = oracle.initial_forest(ws)
+    lv = F.leaves()
+    lmax_f = [w.lmax for w in ws]
+    assert len(set(lv[:, 0])) == 5
+    F.set_q(synth.random_field((len(lv), 8, 8), seed=1) ** 4)
+    delta = F.tag()
+    got = fc.layout_regrid(desc_for(ws[0], nforests=5, lmax=5), lv, delta, 0.05, 0.0125, lmax_f)
+    F.regrid(0.05, 0.0125, lmax_f)
+    assert np.array_equal(got, F.leaves())
