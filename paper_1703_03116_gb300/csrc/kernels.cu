@@ -269,6 +269,8 @@ __global__ void __launch_bounds__(256) advance_kernel(DevForest<real> D, int p0,
   real* YM = YP + NE;
   real* Sx = YM + NE;
   real* Sy = Sx + NT;
+  real* Tx = Sy + NT;
+  real* Ty = Tx + NT;
   const int order = D.order, limiter = D.limiter, transverse = D.transverse;
   const bool swirl = D.vel_kind == FC_VEL_SWIRL;
   const real cu = real(D.vel[0]), cv = real(D.vel[1]);
@@ -278,26 +280,31 @@ __global__ void __launch_bounds__(256) advance_kernel(DevForest<real> D, int p0,
     const real* src = D.buf[D.cur[pm.level]] + (size_t)p * S * S;
     real* dst = D.buf[D.cur[pm.level] ^ 1] + (size_t)p * S * S;
     const double hd = ldexp(1.0, -pm.level) / MX;
-    const real h = real(hd);
     const real nu = real(dt / hd);
     for (int k = threadIdx.x; k < S * S; k += blockDim.x) Q[k] = src[k];
+    // Swirl: psi = s(x) s(y) cos(pi t/T)/pi with s = sin^2(pi .), so the
+    // corner difference along an edge is s(corner) (s(y1) - s(y0)) and
+    // s(y1) - s(y0) = sin(pi (y0 + y1)) sin(pi h): corner tables S, edge
+    // tables T, no cancellation.
     real ucoef = real(0);
     if (swirl) {
-      ucoef = real(cospi(t_half / D.vel[0]) / M_PI / hd);
+      ucoef = real(cospi(t_half / D.vel[0]) / M_PI * sinpi(hd) / hd);
       for (int k = threadIdx.x; k < NT; k += blockDim.x) {
         const real xs = sinpi_r(real((pm.x * MX + k - 1) * hd));
         const real ys = sinpi_r(real((pm.y * MX + k - 1) * hd));
         Sx[k] = xs * xs;
         Sy[k] = ys * ys;
+        Tx[k] = sinpi_r(real((2 * (pm.x * MX + k - 1) + 1) * hd));
+        Ty[k] = sinpi_r(real((2 * (pm.y * MX + k - 1) + 1) * hd));
       }
     }
     __syncthreads();
     auto q = [&](int i, int j) -> real { return Q[(j + 2) * S + (i + 2)]; };
-    auto uvel = [&](int i, int j) -> real {  // x-edge (i,j)
-      return swirl ? ucoef * Sx[i + 1] * (Sy[j + 2] - Sy[j + 1]) : cu;
+    auto uvel = [&](int i, int j) -> real {  // x-edge (i,j): corners (i,j), (i,j+1)
+      return swirl ? ucoef * Sx[i + 1] * Ty[j + 1] : cu;
     };
-    auto vvel = [&](int i, int j) -> real {  // y-edge (i,j)
-      return swirl ? -ucoef * Sy[j + 1] * (Sx[i + 2] - Sx[i + 1]) : cv;
+    auto vvel = [&](int i, int j) -> real {  // y-edge (i,j): corners (i,j), (i+1,j)
+      return swirl ? -ucoef * Sy[j + 1] * Tx[i + 1] : cv;
     };
     // x-sweep
     for (int e = threadIdx.x; e < NE; e += blockDim.x) {
@@ -371,7 +378,7 @@ template <typename real, int MX>
 size_t advance_smem() {
   constexpr int S = MX + 4;
   constexpr int NE = (MX + 1) * (MX + 2);
-  return sizeof(real) * (size_t)(S * S + 6 * NE + 2 * (MX + 3));
+  return sizeof(real) * (size_t)(S * S + 6 * NE + 4 * (MX + 3));
 }
 
 template <typename real, int MX>
