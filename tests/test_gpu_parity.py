@@ -191,4 +191,6 @@ def test_launch_counter_counts_kernels():
     ref, gpu = pair(fc, w, fc.F64)
     fc.launch_count(reset=True)
     gpu.step_multirate(0.0, 0.01)
-    assert fc.launch_count() >= 3 * 3  # fill (2) + advance per substep
+    # 3 substeps (level 2 once, level 3 twice), each a copy/average fill and an
+    # advance; level 3 also interpolates from level 2
+    assert fc.launch_count() == 3 * 2 + 2
