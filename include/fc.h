@@ -175,6 +175,16 @@ fc_status fc_layout_regrid(const fc_forest_desc* desc, int nleaves, const int* l
  * filled ghost cell written once and its source read once).  reset != 0
  * clears the phase afterwards. */
 fc_status fc_timers_enable(fc_forest* forest, int enable);
+
+/* CUDA-graph replay of fc_step_multirate (on by default).  The first coarse
+ * step for a given layout, dt_coarse and buffer parity is captured into a
+ * graph (on an internal stream) and launched; later steps with the same key
+ * replay it after writing their start time to device memory, so a step costs
+ * two launches on `stream`.  A regrid discards the captured steps.  With
+ * timers on, a replayed graph re-records its own events: read the timers
+ * after each step to accumulate every step.  enable = 0 reverts to direct
+ * launches (same kernels, same results). */
+fc_status fc_set_graphs(fc_forest* forest, int enable);
 fc_status fc_timers_read(fc_forest* forest, int phase, double* ms, int64_t* launches,
                          double* bytes, int reset);
 

@@ -18,7 +18,7 @@ INCLUDE = os.path.join(ROOT, "include")
 OBJDIR = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libfc.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["kernels.cu", "forest.cpp", "capi.cpp"]
+SOURCES = ["advance.cu", "fill.cu", "aux_kernels.cu", "forest.cpp", "capi.cpp"]
 
 
 def _nvcc() -> str:
@@ -31,7 +31,8 @@ def _nvcc() -> str:
 def _compile(src: str) -> str:
     obj = os.path.join(OBJDIR, os.path.splitext(src)[0] + ".o")
     path = os.path.join(CSRC, src)
-    deps = [path] + [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".hpp")]
+    deps = [path] + [os.path.join(CSRC, f) for f in os.listdir(CSRC)
+                     if f.endswith((".hpp", ".cuh"))]
     deps.append(os.path.join(INCLUDE, "fc.h"))
     if os.path.exists(obj) and all(os.path.getmtime(d) <= os.path.getmtime(obj) for d in deps):
         return obj

@@ -1,0 +1,265 @@
+// The wave-propagation patch update (sm_103a), one CTA per patch.
+//
+// Scheme: the 2D unsplit wave-propagation method for q_t + (uq)_x + (vq)_y = 0
+// in flux form (the Clawpack algorithms the paper runs, Sec. 5): per edge the
+// upwind flux, an MC-limited second-order correction, and the two
+// fluctuations, each carried across the transverse edges of the cell it
+// enters; then the conservative update of the interior.
+//
+// Data path per patch: the whole (MX+4)^2 array (interior + 2 ghost layers,
+// contiguous in HBM) arrives in shared memory by one 1D TMA bulk copy
+// (cp.async.bulk, completion on an mbarrier); edge quantities of both sweeps
+// are computed once into shared arrays; final edge fluxes are formed in a
+// second pass; each interior cell then reads its four fluxes and is written
+// back once.  Per-launch scalars (dt/h, the streamfunction coefficient) are
+// computed on the host, so the FP32 kernel does no FP64 arithmetic.
+#include <cstdint>
+
+#include "device_util.cuh"
+
+namespace fc {
+namespace {
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
+               : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t done;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(done)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return done != 0;
+}
+
+// bounded wait: gives up after `limit` polls (each poll may suspend briefly)
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint32_t limit) {
+  for (uint32_t it = 0; it < limit; ++it)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+
+__device__ __forceinline__ void bulk_load(void* dst_smem, const void* src, uint32_t bytes,
+                                          uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+          "r"(smem_u32(dst_smem)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+
+template <typename real>
+__device__ __forceinline__ real sinpi_r(real x);
+template <>
+__device__ __forceinline__ float sinpi_r<float>(float x) { return sinpif(x); }
+template <>
+__device__ __forceinline__ double sinpi_r<double>(double x) { return sinpi(x); }
+
+// phi(W_up / W) W for the MC limiter without a division:
+// 0 unless W and W_up share a sign, else sign(W) min(|W + W_up|/2, 2|W|, 2|W_up|)
+template <typename real>
+__device__ __forceinline__ real mc_limited(real W, real Wup) {
+  const real m = fmin(real(0.5) * fabs(W + Wup), real(2) * fmin(fabs(W), fabs(Wup)));
+  return (W * Wup > real(0)) ? copysign(m, W) : real(0);
+}
+
+template <typename real>
+__device__ __forceinline__ real correction(int order, int limiter, real s, real W, real Wup,
+                                           real nu) {
+  if (order < 2) return real(0);
+  const real as = fabs(s);
+  const real lim = limiter ? mc_limited(W, Wup) : W;
+  return real(0.5) * as * (real(1) - nu * as) * lim;
+}
+
+constexpr uint32_t kWaitLimit = 1u << 22;
+
+// x-edge (i,j) lies between cells (i-1,j) and (i,j): i in [0,MX], j in [-1,MX]
+// y-edge (i,j) lies between cells (i,j-1) and (i,j): j in [0,MX], i in [-1,MX]
+template <typename real, int MX, int NT>
+__global__ void __launch_bounds__(NT) advance_kernel(DevForest<real> D, int p0, int p1,
+                                                     AdvArgs a, int* err) {
+  constexpr int S = MX + 4;
+  constexpr int NE = (MX + 1) * (MX + 2);
+  constexpr int NV = MX + 3;  // corner nodes -1..MX+1
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  __shared__ __align__(8) uint64_t bar;
+  real* Q = reinterpret_cast<real*>(smem_raw);
+  real* Fn = Q + S * S;
+  real* XP = Fn + NE;
+  real* XM = XP + NE;
+  real* Gn = XM + NE;
+  real* YP = Gn + NE;
+  real* YM = YP + NE;
+  real* Sx = YM + NE;
+  real* Sy = Sx + NV;
+  real* Tx = Sy + NV;
+  real* Ty = Tx + NV;
+  const int order = D.order, limiter = D.limiter, transverse = D.transverse;
+  const bool swirl = D.vel_kind == FC_VEL_SWIRL;
+  const real cu = real(D.vel[0]), cv = real(D.vel[1]);
+  const real nu = real(a.nu), half_nu = real(0.5 * a.nu), h = real(a.h);
+  __shared__ real ucoef_s;
+  constexpr uint32_t bytes = sizeof(real) * S * S;
+
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    if (swirl) {
+      const double t = a.t0_dev ? *a.t0_dev + a.t_off : a.t_half;
+      ucoef_s = real(cospi(t / a.period) * a.sfac);
+    }
+  }
+  __syncthreads();
+  const real ucoef = swirl ? ucoef_s : real(0);
+  uint32_t parity = 0;
+  for (int p = p0 + blockIdx.x; p < p1; p += gridDim.x, parity ^= 1) {
+    const PatchMeta pm = D.meta[p];
+    const real* src = D.buf[D.cur[pm.level]] + (size_t)p * S * S;
+    real* dst = D.buf[D.cur[pm.level] ^ 1] + (size_t)p * S * S;
+    if (threadIdx.x == 0) {
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      mbar_expect_tx(&bar, bytes);
+      bulk_load(Q, src, bytes, &bar);
+    }
+    // streamfunction tables while the tile is in flight:
+    // psi = s(x) s(y) cos(pi t/T)/pi, s = sin^2(pi .); along an edge the
+    // corner difference is s(corner) * sin(pi (z0 + z1)) * sin(pi h)
+    if (swirl) {
+      for (int k = threadIdx.x; k < NV; k += NT) {
+        const real xs = sinpi_r(real(pm.x * MX + k - 1) * h);
+        const real ys = sinpi_r(real(pm.y * MX + k - 1) * h);
+        Sx[k] = xs * xs;
+        Sy[k] = ys * ys;
+        Tx[k] = sinpi_r(real(2 * (pm.x * MX + k - 1) + 1) * h);
+        Ty[k] = sinpi_r(real(2 * (pm.y * MX + k - 1) + 1) * h);
+      }
+    }
+    // every thread observes the copy's completion (bounded); the CTA leaves
+    // together if any thread gave up
+    const bool landed = mbar_wait(&bar, parity, kWaitLimit);
+    if (!__syncthreads_and(landed)) {
+      if (threadIdx.x == 0) atomicOr(err, 1);
+      mbar_wait(&bar, parity, kWaitLimit);  // let the copy land before leaving
+      return;
+    }
+    auto q = [&](int i, int j) -> real { return Q[(j + 2) * S + (i + 2)]; };
+    auto uvel = [&](int i, int j) -> real { return swirl ? ucoef * Sx[i + 1] * Ty[j + 1] : cu; };
+    auto vvel = [&](int i, int j) -> real { return swirl ? -ucoef * Sy[j + 1] * Tx[i + 1] : cv; };
+    // both sweeps: normal flux and fluctuations of every edge
+    for (int e = threadIdx.x; e < 2 * NE; e += NT) {
+      if (e < NE) {
+        const int i = e % (MX + 1), j = e / (MX + 1) - 1;
+        const real s = uvel(i, j);
+        const real sp = s > real(0) ? s : real(0), sm = s < real(0) ? s : real(0);
+        const real qm = q(i - 1, j), q0 = q(i, j);
+        const real W = q0 - qm;
+        const real Wup = s >= real(0) ? qm - q(i - 2, j) : q(i + 1, j) - q0;
+        const real Ft = correction(order, limiter, s, W, Wup, nu);
+        Fn[e] = sp * qm + sm * q0 + Ft;
+        XP[e] = transverse > 1 ? sp * W - Ft : sp * W;
+        XM[e] = transverse > 1 ? sm * W + Ft : sm * W;
+      } else {
+        const int f = e - NE;
+        const int i = f % (MX + 2) - 1, j = f / (MX + 2);
+        const real s = vvel(i, j);
+        const real sp = s > real(0) ? s : real(0), sm = s < real(0) ? s : real(0);
+        const real qm = q(i, j - 1), q0 = q(i, j);
+        const real W = q0 - qm;
+        const real Wup = s >= real(0) ? qm - q(i, j - 2) : q(i, j + 1) - q0;
+        const real Gt = correction(order, limiter, s, W, Wup, nu);
+        Gn[f] = sp * qm + sm * q0 + Gt;
+        YP[f] = transverse > 1 ? sp * W - Gt : sp * W;
+        YM[f] = transverse > 1 ? sm * W + Gt : sm * W;
+      }
+    }
+    __syncthreads();
+    auto xe = [](int i, int j) { return (j + 1) * (MX + 1) + i; };
+    auto ye = [](int i, int j) { return j * (MX + 2) + (i + 1); };
+    // final fluxes: each fluctuation's transverse increment, gathered per edge
+    if (transverse > 0) {
+      for (int e = threadIdx.x; e < 2 * MX * (MX + 1); e += NT) {
+        if (e < MX * (MX + 1)) {  // x-edges i in [0,MX], interior rows
+          const int i = e % (MX + 1), j = e / (MX + 1);
+          const real s = uvel(i, j);
+          const real sp = s > real(0) ? s : real(0), sm = s < real(0) ? s : real(0);
+          const real yl = YP[ye(i - 1, j)] + YM[ye(i - 1, j + 1)];  // into cell (i-1,j)
+          const real yr = YP[ye(i, j)] + YM[ye(i, j + 1)];          // into cell (i,j)
+          Fn[xe(i, j)] -= half_nu * (sp * yl + sm * yr);
+        } else {  // y-edges j in [0,MX], interior columns
+          const int f = e - MX * (MX + 1);
+          const int i = f % MX, j = f / MX;
+          const real s = vvel(i, j);
+          const real sp = s > real(0) ? s : real(0), sm = s < real(0) ? s : real(0);
+          const real xb = XP[xe(i, j - 1)] + XM[xe(i + 1, j - 1)];  // into cell (i,j-1)
+          const real xt = XP[xe(i, j)] + XM[xe(i + 1, j)];          // into cell (i,j)
+          Gn[ye(i, j)] -= half_nu * (sp * xb + sm * xt);
+        }
+      }
+      __syncthreads();
+    }
+    for (int k = threadIdx.x; k < MX * MX; k += NT) {
+      const int i = k % MX, j = k / MX;
+      const real v = q(i, j) - nu * (Fn[xe(i + 1, j)] - Fn[xe(i, j)]) -
+                     nu * (Gn[ye(i, j + 1)] - Gn[ye(i, j)]);
+      dst[(j + 2) * S + (i + 2)] = v;
+    }
+    __syncthreads();
+  }
+}
+
+template <typename real, int MX>
+constexpr size_t advance_smem() {
+  return sizeof(real) * (size_t)((MX + 4) * (MX + 4) + 6 * (MX + 1) * (MX + 2) + 4 * (MX + 3));
+}
+
+template <typename real, int MX, int NT>
+cudaError_t advance_launch(const DevForest<real>& D, int p0, int p1, const AdvArgs& a, int* err,
+                           cudaStream_t s) {
+  static bool attr_set = false;
+  constexpr size_t smem = advance_smem<real, MX>();
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(advance_kernel<real, MX, NT>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  advance_kernel<real, MX, NT><<<p1 - p0, NT, smem, s>>>(D, p0, p1, a, err);
+  ++launch_counter();
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+template <typename real>
+cudaError_t launch_advance(const DevForest<real>& D, int p0, int p1, const AdvArgs& a, int* err,
+                           cudaStream_t s) {
+  if (p1 <= p0) return cudaSuccess;
+  switch (D.mx) {
+    case 8: return advance_launch<real, 8, 64>(D, p0, p1, a, err, s);
+    case 16: return advance_launch<real, 16, 128>(D, p0, p1, a, err, s);
+    case 32: return advance_launch<real, 32, 256>(D, p0, p1, a, err, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+template cudaError_t launch_advance<float>(const DevForest<float>&, int, int, const AdvArgs&,
+                                           int*, cudaStream_t);
+template cudaError_t launch_advance<double>(const DevForest<double>&, int, int, const AdvArgs&,
+                                            int*, cudaStream_t);
+
+}  // namespace fc

@@ -1,0 +1,233 @@
+// Auxiliary kernels: tagging (Sec. 3.1 indicator), FP64 mass sums, field
+// packing between the store and the caller's layout, and the regrid remap
+// (copy, Eq. ghost_fine interpolation into new children, Eq. ghost_coarse
+// averaging into new parents).
+#include <cmath>
+
+#include "device_util.cuh"
+
+namespace fc {
+
+uint64_t& launch_counter() {
+  static thread_local uint64_t c = 0;
+  return c;
+}
+
+namespace {
+// ------------------------------------------------------------------ tag
+
+template <typename real>
+__global__ void tag_kernel(DevForest<real> D, double* delta) {
+  __shared__ double red[256];
+  const int mx = D.mx, S = D.S;
+  for (int p = blockIdx.x; p < D.npatch; p += gridDim.x) {
+    const real* Q = D.buf[D.cur[D.meta[p].level]] + (size_t)p * S * S;
+    double m = 0.0;
+    for (int k = threadIdx.x; k < mx * mx; k += blockDim.x) {
+      const int i = k % mx + 2, j = k / mx + 2;
+      const double gx = (double)Q[j * S + i + 1] - (double)Q[j * S + i - 1];
+      const double gy = (double)Q[(j + 1) * S + i] - (double)Q[(j - 1) * S + i];
+      const double d = 0.5 * sqrt(gx * gx + gy * gy);
+      m = d > m ? d : m;
+    }
+    red[threadIdx.x] = m;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+      if (threadIdx.x < w) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + w]);
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) delta[p] = red[0];
+    __syncthreads();
+  }
+}
+
+// ------------------------------------------------------------------ mass
+
+template <typename real>
+__global__ void patch_sum_kernel(DevForest<real> D, double* sums) {
+  __shared__ double red[256];
+  const int mx = D.mx, S = D.S;
+  for (int p = blockIdx.x; p < D.npatch; p += gridDim.x) {
+    const PatchMeta pm = D.meta[p];
+    const real* Q = D.buf[D.cur[pm.level]] + (size_t)p * S * S;
+    double s = 0.0;
+    for (int k = threadIdx.x; k < mx * mx; k += blockDim.x)
+      s += (double)Q[(k / mx + 2) * S + k % mx + 2];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+      if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+      const double h = ldexp(1.0, -pm.level) / mx;
+      sums[p] = h * h * red[0];
+    }
+    __syncthreads();
+  }
+}
+
+__global__ void forest_sum_kernel(const double* sums, const int* api_to_dev, const int* fstart,
+                                  int nforests, double* out) {
+  __shared__ double red[256];
+  for (int f = blockIdx.x; f < nforests; f += gridDim.x) {
+    double s = 0.0;
+    for (int k = fstart[f] + threadIdx.x; k < fstart[f + 1]; k += blockDim.x)
+      s += sums[api_to_dev[k]];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+      if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) out[f] = red[0];
+    __syncthreads();
+  }
+}
+
+// ------------------------------------------------------------------ pack / unpack
+
+template <typename real>
+__global__ void pack_kernel(DevForest<real> D, const int* api_to_dev, real* out, int full) {
+  const int mx = D.mx, S = D.S;
+  const int per = full ? S * S : mx * mx;
+  const size_t total = (size_t)D.npatch * per;
+  for (size_t g = (size_t)blockIdx.x * blockDim.x + threadIdx.x; g < total;
+       g += (size_t)gridDim.x * blockDim.x) {
+    const int k = (int)(g / per), r = (int)(g % per);
+    const int p = api_to_dev[k];
+    const real* Q = D.buf[D.cur[D.meta[p].level]] + (size_t)p * S * S;
+    out[g] = full ? Q[r] : Q[(r / mx + 2) * S + r % mx + 2];
+  }
+}
+
+template <typename real>
+__global__ void unpack_kernel(DevForest<real> D, const int* api_to_dev, const real* in) {
+  const int mx = D.mx, S = D.S;
+  const size_t total = (size_t)D.npatch * mx * mx;
+  for (size_t g = (size_t)blockIdx.x * blockDim.x + threadIdx.x; g < total;
+       g += (size_t)gridDim.x * blockDim.x) {
+    const int k = (int)(g / (mx * mx)), r = (int)(g % (mx * mx));
+    const int p = api_to_dev[k];
+    real* Q = D.buf[D.cur[D.meta[p].level]] + (size_t)p * S * S;
+    Q[(r / mx + 2) * S + r % mx + 2] = in[g];
+  }
+}
+
+// ------------------------------------------------------------------ remap
+
+template <typename real>
+__global__ void remap_kernel(DevForest<real> Old, DevForest<real> New, const RemapEntry* rm) {
+  const int mx = New.mx, S = New.S;
+  for (int p = blockIdx.x; p < New.npatch; p += gridDim.x) {
+    const RemapEntry e = rm[p];
+    real* Dq = New.buf[New.cur[New.meta[p].level]] + (size_t)p * S * S;
+    for (int k = threadIdx.x; k < mx * mx; k += blockDim.x) {
+      const int i = k % mx, j = k / mx;
+      real v;
+      if (e.kind == RM_COPY) {
+        const int s = e.src[0];
+        v = Old.buf[Old.cur[Old.meta[s].level]][(size_t)s * S * S + (j + 2) * S + i + 2];
+      } else if (e.kind == RM_INTERP) {
+        const int s = e.src[0];
+        const real* C = Old.buf[Old.cur[Old.meta[s].level]] + (size_t)s * S * S;
+        const int ic = e.cx * (mx / 2) + (i >> 1) + 2, jc = e.cy * (mx / 2) + (j >> 1) + 2;
+        const real dx = (i & 1) ? real(1) : real(-1), dy = (j & 1) ? real(1) : real(-1);
+        const real q0 = C[jc * S + ic];
+        const real sx = minmod(C[jc * S + ic + 1] - q0, q0 - C[jc * S + ic - 1]);
+        const real sy = minmod(C[(jc + 1) * S + ic] - q0, q0 - C[(jc - 1) * S + ic]);
+        v = q0 + real(0.25) * (sx * dx + sy * dy);
+      } else {
+        const int cx = (2 * i >= mx), cy = (2 * j >= mx);
+        const int s = e.src[cx + 2 * cy];
+        const real* C = Old.buf[Old.cur[Old.meta[s].level]] + (size_t)s * S * S;
+        const int fi = 2 * i - cx * mx + 2, fj = 2 * j - cy * mx + 2;
+        v = real(0.25) * (((C[fj * S + fi] + C[fj * S + fi + 1]) + C[(fj + 1) * S + fi]) +
+                          C[(fj + 1) * S + fi + 1]);
+      }
+      Dq[(j + 2) * S + i + 2] = v;
+    }
+  }
+}
+
+inline int grid_for(int n) { return n < 1 ? 1 : (n < 65535 * 8 ? n : 65535 * 8); }
+
+}  // namespace
+
+template <typename real>
+cudaError_t launch_tag(const DevForest<real>& D, double* delta, cudaStream_t s) {
+  if (D.npatch <= 0) return cudaSuccess;
+  tag_kernel<real><<<grid_for(D.npatch), 256, 0, s>>>(D, delta);
+  ++launch_counter();
+  return cudaGetLastError();
+}
+
+template <typename real>
+cudaError_t launch_mass(const DevForest<real>& D, const int* api_to_dev, const int* fstart,
+                        int nforests, double* patch_sums, double* out, cudaStream_t s) {
+  if (D.npatch > 0) {
+    patch_sum_kernel<real><<<grid_for(D.npatch), 256, 0, s>>>(D, patch_sums);
+    ++launch_counter();
+  }
+  forest_sum_kernel<<<grid_for(nforests), 256, 0, s>>>(patch_sums, api_to_dev, fstart, nforests,
+                                                        out);
+  ++launch_counter();
+  return cudaGetLastError();
+}
+
+template <typename real>
+cudaError_t launch_pack(const DevForest<real>& D, const int* api_to_dev, real* out, int full,
+                        cudaStream_t s) {
+  if (D.npatch <= 0) return cudaSuccess;
+  pack_kernel<real><<<1216, 256, 0, s>>>(D, api_to_dev, out, full);
+  ++launch_counter();
+  return cudaGetLastError();
+}
+
+template <typename real>
+cudaError_t launch_unpack(const DevForest<real>& D, const int* api_to_dev, const real* in,
+                          cudaStream_t s) {
+  if (D.npatch <= 0) return cudaSuccess;
+  unpack_kernel<real><<<1216, 256, 0, s>>>(D, api_to_dev, in);
+  ++launch_counter();
+  return cudaGetLastError();
+}
+
+template <typename real>
+cudaError_t launch_remap(const DevForest<real>& Old, const DevForest<real>& New,
+                         const RemapEntry* rm, cudaStream_t s) {
+  if (New.npatch <= 0) return cudaSuccess;
+  remap_kernel<real><<<grid_for(New.npatch), 256, 0, s>>>(Old, New, rm);
+  ++launch_counter();
+  return cudaGetLastError();
+}
+
+#define FC_INSTANTIATE(real)                                                                   \
+  template cudaError_t launch_tag<real>(const DevForest<real>&, double*, cudaStream_t);        \
+  template cudaError_t launch_mass<real>(const DevForest<real>&, const int*, const int*, int, \
+                                         double*, double*, cudaStream_t);                      \
+  template cudaError_t launch_pack<real>(const DevForest<real>&, const int*, real*, int,      \
+                                         cudaStream_t);                                        \
+  template cudaError_t launch_unpack<real>(const DevForest<real>&, const int*, const real*,   \
+                                           cudaStream_t);                                      \
+  template cudaError_t launch_remap<real>(const DevForest<real>&, const DevForest<real>&,     \
+                                          const RemapEntry*, cudaStream_t);
+
+FC_INSTANTIATE(float)
+FC_INSTANTIATE(double)
+
+}  // namespace fc
+
+namespace fc {
+namespace {
+__global__ void set_time_kernel(double* t0_dev, double t0) { *t0_dev = t0; }
+}  // namespace
+
+// Stores the start time of a replayed coarse step in device memory (one
+// thread); kernels captured in a graph read it there.
+cudaError_t launch_set_time(double* t0_dev, double t0, cudaStream_t s) {
+  set_time_kernel<<<1, 1, 0, s>>>(t0_dev, t0);
+  ++launch_counter();
+  return cudaGetLastError();
+}
+}  // namespace fc

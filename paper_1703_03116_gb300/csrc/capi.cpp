@@ -61,60 +61,100 @@ struct fc_forest {
   double* d_mass = nullptr;
   double* d_delta = nullptr;
   RemapEntry* d_remap = nullptr;
+  int* d_err = nullptr;  // device error word (bit kErrTimeout)
   int cur[kMaxLevel + 1] = {0};
   bool has_old[kMaxLevel + 1] = {false};
   double t_start[kMaxLevel + 1] = {0};
   double dt_last[kMaxLevel + 1] = {0};
-  // per-phase CUDA-event timers
-  struct Phase {
-    std::vector<cudaEvent_t> ev;  // start/stop pairs
-    std::vector<double> bytes;    // algorithmic bytes of each pending pair
-    size_t used = 0;
-    double ms = 0.0, total_bytes = 0.0;
+  // per-phase CUDA-event timers: every timed launch is bracketed by a pair
+  struct TimerPair {
+    cudaEvent_t a = nullptr, b = nullptr;
+    double bytes = 0.0;
+    int phase = 0;
+  };
+  struct PhaseTotal {
+    double ms = 0.0, bytes = 0.0;
     int64_t launches = 0;
   };
   bool timing = false;
-  Phase ph[4];
+  std::vector<TimerPair> pending;  // recorded by direct launches, not yet read
+  std::vector<TimerPair> spare;    // event pairs free for reuse
+  PhaseTotal ph[4];
+  std::vector<TimerPair>* capture_pairs = nullptr;  // non-null while capturing a graph
+
+  // captured coarse multirate steps (CUDA graphs), valid for one layout
+  struct Graph {
+    cudaGraphExec_t exec = nullptr;
+    double dt = 0.0;
+    int cur_before[kMaxLevel + 1] = {0};
+    int cur_after[kMaxLevel + 1] = {0};
+    bool timing = false;
+    bool replayed = false;  // replayed since its timers were last read
+    std::vector<TimerPair> pairs;
+  };
+  bool use_graphs = true;
+  cudaStream_t cap_stream = nullptr;
+  double* d_t0 = nullptr;  // start time of the replayed coarse step
+  std::vector<Graph> graphs;
 };
 
 namespace {
 
+fc_forest::TimerPair take_pair(fc_forest* F) {
+  if (!F->spare.empty()) {
+    fc_forest::TimerPair p = F->spare.back();
+    F->spare.pop_back();
+    return p;
+  }
+  fc_forest::TimerPair p;
+  if (cudaEventCreate(&p.a) != cudaSuccess || cudaEventCreate(&p.b) != cudaSuccess) {
+    p.a = p.b = nullptr;
+  }
+  return p;
+}
+
 // Brackets one launch with a pair of events when the forest's timers are on.
+// While a graph is being captured the pair belongs to that graph.
 class Timed {
  public:
-  Timed(fc_forest* F, int phase, cudaStream_t s, double bytes) : F_(F), s_(s) {
+  Timed(fc_forest* F, int phase, cudaStream_t s, double bytes) : s_(s) {
     if (!F->timing) return;
-    fc_forest::Phase& P = F->ph[phase];
-    if (P.used * 2 + 2 > P.ev.size()) {
-      for (int k = 0; k < 2; ++k) {
-        cudaEvent_t e;
-        if (cudaEventCreate(&e) != cudaSuccess) return;
-        P.ev.push_back(e);
-      }
-    }
-    P_ = &P;
-    idx_ = P.used++;
-    if (P.bytes.size() < P.used) P.bytes.resize(P.used);
-    P.bytes[idx_] = bytes;
-    cudaEventRecord(P.ev[2 * idx_], s_);
+    fc_forest::TimerPair p = take_pair(F);
+    if (!p.a) return;
+    p.bytes = bytes;
+    p.phase = phase;
+    list_ = F->capture_pairs ? F->capture_pairs : &F->pending;
+    list_->push_back(p);
+    idx_ = list_->size() - 1;
+    cudaEventRecord(p.a, s_);
   }
   ~Timed() {
-    if (P_) cudaEventRecord(P_->ev[2 * idx_ + 1], s_);
+    if (list_) cudaEventRecord((*list_)[idx_].b, s_);
   }
 
  private:
-  fc_forest* F_;
   cudaStream_t s_;
-  fc_forest::Phase* P_ = nullptr;
+  std::vector<fc_forest::TimerPair>* list_ = nullptr;
   size_t idx_ = 0;
 };
 
-void destroy_timers(fc_forest* F) {
-  for (auto& P : F->ph) {
-    for (cudaEvent_t e : P.ev) cudaEventDestroy(e);
-    P.ev.clear();
-    P.used = 0;
+void destroy_graphs(fc_forest* F) {
+  for (auto& g : F->graphs) {
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+    for (auto& p : g.pairs) F->spare.push_back(p);
   }
+  F->graphs.clear();
+}
+
+void destroy_timers(fc_forest* F) {
+  destroy_graphs(F);
+  for (auto* v : {&F->pending, &F->spare})
+    for (auto& p : *v) {
+      if (p.a) cudaEventDestroy(p.a);
+      if (p.b) cudaEventDestroy(p.b);
+    }
+  F->pending.clear();
+  F->spare.clear();
 }
 
 void free_device(fc_forest* F) {
@@ -131,6 +171,8 @@ void free_device(fc_forest* F) {
   dfree(F->d_mass);
   dfree(F->d_delta);
   dfree(F->d_remap);
+  dfree(F->d_err);
+  dfree(F->d_t0);
 }
 
 // upload tables (and allocate a store) for the current host layout
@@ -187,6 +229,14 @@ fc_status upload(fc_forest* F, bool alloc_store) {
   FC_CUDA(dmalloc(&F->d_patch_sums, n));
   FC_CUDA(dmalloc(&F->d_mass, H.desc.nforests));
   FC_CUDA(dmalloc(&F->d_delta, n));
+  if (!F->d_err) {
+    FC_CUDA(dmalloc(&F->d_err, 1));
+    FC_CUDA(cudaMemset(F->d_err, 0, sizeof(int)));
+  }
+  if (!F->d_t0) {
+    FC_CUDA(dmalloc(&F->d_t0, 1));
+    FC_CUDA(cudaMemset(F->d_t0, 0, sizeof(double)));
+  }
   return FC_OK;
 }
 
@@ -210,6 +260,32 @@ DevForest<real> dev(const fc_forest* F) {
   D.limiter = H.desc.limiter;
   D.transverse = H.desc.transverse;
   return D;
+}
+
+// per-launch scalars of the patch update for level L, step t -> t + dt; while
+// a graph is captured, t is relative to the replayed step's start time
+AdvArgs adv_args(const fc_forest* F, int L, double t, double dt) {
+  const fc_forest_desc& d = F->host.desc;
+  AdvArgs a{};
+  a.h = std::ldexp(1.0, -L) / d.mx;
+  a.nu = dt / a.h;
+  a.period = d.vel[0];
+  a.sfac = d.vel_kind == FC_VEL_SWIRL ? std::sin(M_PI * a.h) / (M_PI * a.h) : 0.0;
+  a.t_half = t + 0.5 * dt;
+  a.t_off = t + 0.5 * dt;
+  a.t0_dev = F->capture_pairs ? F->d_t0 : nullptr;
+  return a;
+}
+
+// device error word -> status (and clear it)
+fc_status check_device_error(fc_forest* F, cudaStream_t s) {
+  int v = 0;
+  FC_CUDA(cudaMemcpyAsync(&v, F->d_err, sizeof(int), cudaMemcpyDeviceToHost, s));
+  FC_CUDA(cudaStreamSynchronize(s));
+  if (v == 0) return FC_OK;
+  FC_CUDA(cudaMemsetAsync(F->d_err, 0, sizeof(int), s));
+  if (v & kErrTimeout) return fail(FC_ERR_TIMEOUT, "a bounded device wait gave up");
+  return fail(FC_ERR_CUDA, "device error word set");
 }
 
 // algorithmic bytes of filling one patch's ghost ring (source read + write)
@@ -272,7 +348,7 @@ fc_status advance_level_t(fc_forest* F, int L, double t, double dt, cudaStream_t
     }
     {
       Timed tm(F, 0, s, advance_bytes(F, p1 - p0));
-      FC_CUDA(launch_advance(D, L, p0, p1, t, dt, s));
+      FC_CUDA(launch_advance(D, p0, p1, adv_args(F, L, t, dt), F->d_err, s));
     }
     F->cur[L] ^= 1;
   }
@@ -375,6 +451,7 @@ fc_status fc_forest_destroy(fc_forest* F) {
   if (!F) return FC_OK;
   cudaDeviceSynchronize();
   destroy_timers(F);
+  if (F->cap_stream) cudaStreamDestroy(F->cap_stream);
   free_device(F);
   delete F;
   return FC_OK;
@@ -389,24 +466,43 @@ fc_status fc_timers_enable(fc_forest* F, int enable) {
 fc_status fc_timers_read(fc_forest* F, int phase, double* ms, int64_t* launches, double* bytes,
                          int reset) {
   if (!F || phase < 0 || phase > 3) return fail(FC_ERR_INVALID_ARG, "bad phase");
-  fc_forest::Phase& P = F->ph[phase];
-  for (size_t k = 0; k < P.used; ++k) {
-    FC_CUDA(cudaEventSynchronize(P.ev[2 * k + 1]));
+  auto account = [&](const fc_forest::TimerPair& p) -> fc_status {
+    FC_CUDA(cudaEventSynchronize(p.b));
     float t = 0.f;
-    FC_CUDA(cudaEventElapsedTime(&t, P.ev[2 * k], P.ev[2 * k + 1]));
-    P.ms += t;
-    P.total_bytes += P.bytes[k];
-    P.launches += 1;
+    FC_CUDA(cudaEventElapsedTime(&t, p.a, p.b));
+    fc_forest::PhaseTotal& T = F->ph[p.phase];
+    T.ms += t;
+    T.bytes += p.bytes;
+    T.launches += 1;
+    return FC_OK;
+  };
+  for (const auto& p : F->pending) {
+    fc_status st = account(p);
+    if (st != FC_OK) return st;
+    F->spare.push_back(p);
   }
-  P.used = 0;
-  if (ms) *ms = P.ms;
-  if (launches) *launches = P.launches;
-  if (bytes) *bytes = P.total_bytes;
-  if (reset) {
-    P.ms = 0.0;
-    P.total_bytes = 0.0;
-    P.launches = 0;
+  F->pending.clear();
+  // a replayed graph re-records its own pairs: they hold its latest replay
+  for (auto& g : F->graphs) {
+    if (!g.replayed) continue;
+    for (const auto& p : g.pairs) {
+      fc_status st = account(p);
+      if (st != FC_OK) return st;
+    }
+    g.replayed = false;
   }
+  fc_forest::PhaseTotal& T = F->ph[phase];
+  if (ms) *ms = T.ms;
+  if (launches) *launches = T.launches;
+  if (bytes) *bytes = T.bytes;
+  if (reset) T = fc_forest::PhaseTotal{};
+  return FC_OK;
+}
+
+fc_status fc_set_graphs(fc_forest* F, int enable) {
+  if (!F) return fail(FC_ERR_INVALID_ARG, "null forest");
+  F->use_graphs = enable != 0;
+  if (!F->use_graphs) destroy_graphs(F);
   return FC_OK;
 }
 
@@ -461,6 +557,7 @@ static fc_status get_q_impl(const fc_forest* F, void* q, int on_device, void* st
   if (!on_device) {
     FC_CUDA(cudaMemcpyAsync(q, F->stage, bytes, cudaMemcpyDeviceToHost, s));
     FC_CUDA(cudaStreamSynchronize(s));
+    return check_device_error(const_cast<fc_forest*>(F), s);
   }
   return FC_OK;
 }
@@ -493,13 +590,18 @@ fc_status fc_step_global(fc_forest* F, double t, double dt, void* stream) {
   fc_status st = fill_all(F, s);
   if (st != FC_OK) return st;
   const HostForest& H = F->host;
-  cudaError_t e;
-  {
-    Timed tm(F, 0, s, advance_bytes(F, H.npatch()));
-    e = F->esize == 4 ? launch_advance(dev<float>(F), -1, 0, H.npatch(), t, dt, s)
-                      : launch_advance(dev<double>(F), -1, 0, H.npatch(), t, dt, s);
+  // one launch per level (per-level h and dt/h); all read the pre-step state
+  DevForest<float> Df = dev<float>(F);
+  DevForest<double> Dd = dev<double>(F);
+  for (int L = H.desc.lmin; L <= H.desc.lmax; ++L) {
+    const int p0 = H.lev_start[L], p1 = H.lev_start[L + 1];
+    if (p1 <= p0) continue;
+    const AdvArgs a = adv_args(F, L, t, dt);
+    Timed tm(F, 0, s, advance_bytes(F, p1 - p0));
+    cudaError_t e = F->esize == 4 ? launch_advance(Df, p0, p1, a, F->d_err, s)
+                                  : launch_advance(Dd, p0, p1, a, F->d_err, s);
+    if (e != cudaSuccess) return cuda_fail(e, "advance");
   }
-  if (e != cudaSuccess) return cuda_fail(e, "advance");
   for (int l = 0; l <= kMaxLevel; ++l) F->cur[l] ^= 1;
   reset_times(F);
   return FC_OK;
@@ -508,7 +610,58 @@ fc_status fc_step_global(fc_forest* F, double t, double dt, void* stream) {
 fc_status fc_step_multirate(fc_forest* F, double t, double dt_coarse, void* stream) {
   if (!F) return fail(FC_ERR_INVALID_ARG, "null forest");
   if (!(dt_coarse > 0.0)) return fail(FC_ERR_INVALID_ARG, "dt must be positive");
-  return multirate(F, F->host.desc.lmin, t, dt_coarse, as_stream(stream));
+  cudaStream_t s = as_stream(stream);
+  const int lmin = F->host.desc.lmin, lmax = F->host.desc.lmax;
+  if (!F->use_graphs) return multirate(F, lmin, t, dt_coarse, s);
+  // A coarse step is replayed from a CUDA graph captured for this layout, dt
+  // and starting buffer parity; the step's start time is written to device
+  // memory first (one single-thread kernel), the captured kernels read it.
+  fc_forest::Graph* g = nullptr;
+  for (auto& c : F->graphs)
+    if (c.dt == dt_coarse && c.timing == F->timing &&
+        std::equal(c.cur_before, c.cur_before + kMaxLevel + 1, F->cur))
+      g = &c;
+  if (!g) {
+    if (!F->cap_stream)
+      FC_CUDA(cudaStreamCreateWithFlags(&F->cap_stream, cudaStreamNonBlocking));
+    fc_forest::Graph ng;
+    ng.dt = dt_coarse;
+    ng.timing = F->timing;
+    std::copy(F->cur, F->cur + kMaxLevel + 1, ng.cur_before);
+    // capture with relative times; the host bookkeeping done while capturing
+    // is what one replay does to the state
+    F->capture_pairs = &ng.pairs;
+    FC_CUDA(cudaStreamBeginCapture(F->cap_stream, cudaStreamCaptureModeThreadLocal));
+    fc_status st = multirate(F, lmin, 0.0, dt_coarse, F->cap_stream);
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamEndCapture(F->cap_stream, &graph);
+    F->capture_pairs = nullptr;
+    std::copy(F->cur, F->cur + kMaxLevel + 1, ng.cur_after);
+    std::copy(ng.cur_before, ng.cur_before + kMaxLevel + 1, F->cur);
+    if (st != FC_OK) {
+      if (graph) cudaGraphDestroy(graph);
+      for (auto& p : ng.pairs) F->spare.push_back(p);
+      return st;
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+    e = cudaGraphInstantiate(&ng.exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
+    F->graphs.push_back(std::move(ng));
+    g = &F->graphs.back();
+  }
+  FC_CUDA(launch_set_time(F->d_t0, t, s));
+  FC_CUDA(cudaGraphLaunch(g->exec, s));
+  g->replayed = F->timing;
+  std::copy(g->cur_after, g->cur_after + kMaxLevel + 1, F->cur);
+  // per-level step bookkeeping after the replay (as the recursion leaves it)
+  for (int L = lmin; L <= lmax; ++L) {
+    const double dtl = std::ldexp(dt_coarse, -(L - lmin));
+    F->has_old[L] = true;
+    F->dt_last[L] = dtl;
+    F->t_start[L] = t + dt_coarse - dtl;
+  }
+  return FC_OK;
 }
 
 fc_status fc_tag(fc_forest* F, double* delta_host, void* stream) {
@@ -622,7 +775,8 @@ fc_status fc_tag_regrid(fc_forest* F, double tau_refine, double tau_coarsen,
   }
   if (e != cudaSuccess) return cuda_fail(e, "remap");
   FC_CUDA(cudaStreamSynchronize(s));
-  // swap contents: F takes G's layout and store
+  // swap contents: F takes G's layout and store; captured steps are stale
+  destroy_graphs(F);
   free_device(F);
   F->host = std::move(G->host);
   std::memcpy(F->buf, G->buf, sizeof F->buf);
@@ -641,6 +795,8 @@ fc_status fc_tag_regrid(fc_forest* F, double tau_refine, double tau_coarsen,
   F->d_mass = G->d_mass;
   F->d_delta = G->d_delta;
   F->d_remap = G->d_remap;
+  F->d_err = G->d_err;
+  F->d_t0 = G->d_t0;
   for (int l = 0; l <= kMaxLevel; ++l) F->cur[l] = 0;
   reset_times(F);
   delete G;  // its device pointers now belong to F
@@ -734,7 +890,7 @@ fc_status fc_forest_mass(const fc_forest* F, double* out, void* stream) {
   if (e != cudaSuccess) return cuda_fail(e, "mass");
   FC_CUDA(cudaMemcpyAsync(out, F->d_mass, sizeof(double) * nf, cudaMemcpyDeviceToHost, s));
   FC_CUDA(cudaStreamSynchronize(s));
-  return FC_OK;
+  return check_device_error(const_cast<fc_forest*>(F), s);
 }
 
 }  // extern "C"

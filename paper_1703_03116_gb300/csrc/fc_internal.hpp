@@ -109,13 +109,28 @@ struct FillArgs {
   double alpha;  // time-interpolation weight of the newer state
 };
 
+// Per-launch scalars of the patch update for one level: cell width h,
+// Courant ratio dt/h, and the swirl coefficient cos(pi t / T) * sfac with
+// sfac = sin(pi h) / (pi h) (0 for a constant velocity).  The velocity time t
+// is t_half, or *t0_dev + t_off when t0_dev is set (graph replay: the coarse
+// step's start time lives in device memory, the offset is baked in).
+struct AdvArgs {
+  double h, nu, sfac, period, t_half, t_off;
+  const double* t0_dev;
+};
+
+cudaError_t launch_set_time(double* t0_dev, double t0, cudaStream_t s);
+
+// device error word bits
+constexpr int kErrTimeout = 1;
+
 template <typename real>
 cudaError_t launch_fill_coarse(const DevForest<real>& D, const FillArgs& A, cudaStream_t s);
 template <typename real>
 cudaError_t launch_fill_fine(const DevForest<real>& D, const FillArgs& A, cudaStream_t s);
 template <typename real>
-cudaError_t launch_advance(const DevForest<real>& D, int level, int p0, int p1, double t,
-                           double dt, cudaStream_t s);
+cudaError_t launch_advance(const DevForest<real>& D, int p0, int p1, const AdvArgs& a, int* err,
+                           cudaStream_t s);
 template <typename real>
 cudaError_t launch_tag(const DevForest<real>& D, double* delta, cudaStream_t s);
 template <typename real>

@@ -160,6 +160,10 @@ class Forest:
         check(load().fc_tag_regrid(self._h, tau_r, tau_c, lm, ctypes.byref(ch), _stream(stream)))
         return ch.value
 
+    def graphs(self, enable: bool = True):
+        """Replay coarse multirate steps from captured CUDA graphs (default on)."""
+        check(load().fc_set_graphs(self._h, 1 if enable else 0))
+
     def timers(self, enable: bool = True):
         check(load().fc_timers_enable(self._h, 1 if enable else 0))
 

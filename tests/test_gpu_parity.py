@@ -194,3 +194,33 @@ def test_launch_counter_counts_kernels():
     # 3 substeps (level 2 once, level 3 twice), each a copy/average fill and an
     # advance; level 3 also interpolates from level 2
     assert fc.launch_count() == 3 * 2 + 2
+
+
+def test_graph_replay_matches_direct_launches():
+    """Coarse steps replayed from captured CUDA graphs give the same bits as
+    direct launches, across a regrid (which discards the captured steps)."""
+    w = synth.swirl(6, lmin=2, lmax=5, mx=16)
+    _, dtc = synth.time_step(w)
+    ref, a = pair(fc, w, fc.F32)
+    b = fc.Forest(a.desc, ref.leaves())
+    b.set_q(a.get_q())
+    b.graphs(False)
+    for n in range(6):
+        a.step_multirate(n * dtc, dtc)
+        b.step_multirate(n * dtc, dtc)
+        if n == 2:
+            assert a.tag_regrid(0.05, 0.0125) == b.tag_regrid(0.05, 0.0125)
+    np.testing.assert_array_equal(a.get_q(), b.get_q())
+
+
+def test_timers_count_replayed_launches():
+    w = synth.swirl(6, lmin=2, lmax=4, mx=16)
+    _, dtc = synth.time_step(w)
+    ref, gpu = pair(fc, w, fc.F32)
+    gpu.timers(True)
+    nlev = len(set(gpu.leaves()[:, 2]))
+    substeps = sum(1 << (l - 2) for l in set(gpu.leaves()[:, 2]))
+    for n in range(3):
+        gpu.step_multirate(n * dtc, dtc)
+        ms, launches, nbytes = gpu.read_timer(0, reset=True)
+        assert launches == substeps and ms > 0 and nbytes > 0, (n, launches, substeps, nlev)
