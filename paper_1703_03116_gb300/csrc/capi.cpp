@@ -90,6 +90,7 @@ struct fc_forest {
     int cur_after[kMaxLevel + 1] = {0};
     bool timing = false;
     bool replayed = false;  // replayed since its timers were last read
+    uint64_t kernels = 0;   // kernel nodes (counted per replay)
     std::vector<TimerPair> pairs;
   };
   bool use_graphs = true;
@@ -631,11 +632,14 @@ fc_status fc_step_multirate(fc_forest* F, double t, double dt_coarse, void* stre
     // capture with relative times; the host bookkeeping done while capturing
     // is what one replay does to the state
     F->capture_pairs = &ng.pairs;
+    const uint64_t launches_before = launch_counter();
     FC_CUDA(cudaStreamBeginCapture(F->cap_stream, cudaStreamCaptureModeThreadLocal));
     fc_status st = multirate(F, lmin, 0.0, dt_coarse, F->cap_stream);
     cudaGraph_t graph = nullptr;
     cudaError_t e = cudaStreamEndCapture(F->cap_stream, &graph);
     F->capture_pairs = nullptr;
+    ng.kernels = launch_counter() - launches_before;  // counted when replayed
+    launch_counter() = launches_before;
     std::copy(F->cur, F->cur + kMaxLevel + 1, ng.cur_after);
     std::copy(ng.cur_before, ng.cur_before + kMaxLevel + 1, F->cur);
     if (st != FC_OK) {
@@ -652,6 +656,7 @@ fc_status fc_step_multirate(fc_forest* F, double t, double dt_coarse, void* stre
   }
   FC_CUDA(launch_set_time(F->d_t0, t, s));
   FC_CUDA(cudaGraphLaunch(g->exec, s));
+  launch_counter() += g->kernels;
   g->replayed = F->timing;
   std::copy(g->cur_after, g->cur_after + kMaxLevel + 1, F->cur);
   // per-level step bookkeeping after the replay (as the recursion leaves it)

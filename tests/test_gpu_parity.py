@@ -189,11 +189,18 @@ def test_full_size_swirl_one_coarse_step():
 def test_launch_counter_counts_kernels():
     w = synth.swirl(0, lmin=2, lmax=3, mx=8)
     ref, gpu = pair(fc, w, fc.F64)
-    fc.launch_count(reset=True)
-    gpu.step_multirate(0.0, 0.01)
     # 3 substeps (level 2 once, level 3 twice), each a copy/average fill and an
     # advance; level 3 also interpolates from level 2
+    gpu.graphs(False)
+    fc.launch_count(reset=True)
+    gpu.step_multirate(0.0, 0.01)
     assert fc.launch_count() == 3 * 2 + 2
+    # graph replay: the same kernels plus the one that stores the step time
+    gpu.graphs(True)
+    for n in range(3):
+        fc.launch_count(reset=True)
+        gpu.step_multirate(0.01 * (n + 1), 0.01)
+        assert fc.launch_count() == 3 * 2 + 2 + 1
 
 
 def test_graph_replay_matches_direct_launches():
