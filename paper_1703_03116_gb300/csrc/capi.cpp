@@ -127,14 +127,17 @@ class Timed {
     list_ = F->capture_pairs ? F->capture_pairs : &F->pending;
     list_->push_back(p);
     idx_ = list_->size() - 1;
-    cudaEventRecord(p.a, s_);
+    // inside a capture only an external record becomes an event-record node
+    flags_ = F->capture_pairs ? cudaEventRecordExternal : cudaEventRecordDefault;
+    cudaEventRecordWithFlags(p.a, s_, flags_);
   }
   ~Timed() {
-    if (list_) cudaEventRecord((*list_)[idx_].b, s_);
+    if (list_) cudaEventRecordWithFlags((*list_)[idx_].b, s_, flags_);
   }
 
  private:
   cudaStream_t s_;
+  unsigned flags_ = cudaEventRecordDefault;
   std::vector<fc_forest::TimerPair>* list_ = nullptr;
   size_t idx_ = 0;
 };
