@@ -185,6 +185,25 @@ fc_status fc_timers_enable(fc_forest* forest, int enable);
  * after each step to accumulate every step.  enable = 0 reverts to direct
  * launches (same kernels, same results). */
 fc_status fc_set_graphs(fc_forest* forest, int enable);
+
+/* Patch-update kernel variants: 0 "staged" (one CTA per patch, the whole
+ * tile in shared memory, every thread on every phase -- low latency for
+ * launches of few patches) and 1 "walk" (lanes own patch columns and walk
+ * the rows with warp shuffles, tiles double-buffered per warp by TMA, a
+ * persistent grid of `warps`-warp CTAs -- fewest instructions per cell).
+ *
+ * fc_autotune times every candidate (staged; walk with 2, 4, 8 warps per
+ * CTA) on each level's launch of the current layout and keeps the fastest
+ * per launch size (sizes bucketed by powers of two; a bucket is tuned once
+ * per forest).  It overwrites the previous-state buffers, so call it when
+ * all levels hold the same time (after set_q or a regrid).  report: host,
+ * nullable, 32 x 3 ints per bucket b (patches in [2^b, 2^(b+1))):
+ * (variant or -1 if untuned, warps, ns per launch).  Synchronous.
+ *
+ * fc_set_advance_variant forces a variant for every launch (variant -1
+ * restores the tuned/heuristic choice); warps is 2, 4 or 8. */
+fc_status fc_autotune(fc_forest* forest, int* report, void* stream);
+fc_status fc_set_advance_variant(fc_forest* forest, int variant, int warps);
 fc_status fc_timers_read(fc_forest* forest, int phase, double* ms, int64_t* launches,
                          double* bytes, int reset);
 

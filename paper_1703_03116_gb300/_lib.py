@@ -53,6 +53,8 @@ SIGNATURES = {
                                         ctypes.c_double, _ip, ctypes.c_int, _ip, _ip]),
     "fc_timers_enable": (ctypes.c_int, [_vp, ctypes.c_int]),
     "fc_set_graphs": (ctypes.c_int, [_vp, ctypes.c_int]),
+    "fc_autotune": (ctypes.c_int, [_vp, _ip, _vp]),
+    "fc_set_advance_variant": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int]),
     "fc_timers_read": (ctypes.c_int, [_vp, ctypes.c_int, _dp, ctypes.POINTER(ctypes.c_int64),
                                       _dp, ctypes.c_int]),
     "fc_last_error": (ctypes.c_char_p, []),

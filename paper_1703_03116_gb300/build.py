@@ -18,7 +18,7 @@ INCLUDE = os.path.join(ROOT, "include")
 OBJDIR = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libfc.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["advance.cu", "fill.cu", "aux_kernels.cu", "forest.cpp", "capi.cpp"]
+SOURCES = ["advance.cu", "advance_walk.cu", "fill.cu", "aux_kernels.cu", "forest.cpp", "capi.cpp"]
 
 
 def _nvcc() -> str:
@@ -36,7 +36,8 @@ def _compile(src: str) -> str:
     deps.append(os.path.join(INCLUDE, "fc.h"))
     if os.path.exists(obj) and all(os.path.getmtime(d) <= os.path.getmtime(obj) for d in deps):
         return obj
-    cmd = [_nvcc(), *ARCH, "-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC",
+    cmd = [_nvcc(), *ARCH, "-O3", "-std=c++17", "-lineinfo", "--expt-relaxed-constexpr",
+           "-Xcompiler", "-fPIC",
            "-I", INCLUDE, "-I", CSRC, "-c", path, "-o", obj]
     if src.endswith(".cpp"):
         cmd[1:1] = ["-x", "cu"]

@@ -1,4 +1,5 @@
-// The wave-propagation patch update (sm_103a), one CTA per patch.
+// The wave-propagation patch update (sm_103a): "staged" variant and the
+// variant dispatcher.
 //
 // Scheme: the 2D unsplit wave-propagation method for q_t + (uq)_x + (vq)_y = 0
 // in flux form (the Clawpack algorithms the paper runs, Sec. 5): per edge the
@@ -6,77 +7,18 @@
 // fluctuations, each carried across the transverse edges of the cell it
 // enters; then the conservative update of the interior.
 //
-// Data path per patch: the whole (MX+4)^2 array (interior + 2 ghost layers,
-// contiguous in HBM) arrives in shared memory by one 1D TMA bulk copy
-// (cp.async.bulk, completion on an mbarrier); edge quantities of both sweeps
-// are computed once into shared arrays; final edge fluxes are formed in a
-// second pass; each interior cell then reads its four fluxes and is written
-// back once.  Per-launch scalars (dt/h, the streamfunction coefficient) are
-// computed on the host, so the FP32 kernel does no FP64 arithmetic.
+// Staged variant: one CTA per patch.  The whole (MX+4)^2 array (interior + 2
+// ghost layers, contiguous in HBM) arrives in shared memory by one 1D TMA
+// bulk copy; edge quantities of both sweeps are computed once into shared
+// arrays; final edge fluxes are formed in a second pass; each interior cell
+// then reads its four fluxes.  Every thread works on every phase, so a patch
+// finishes quickly -- the better choice when a launch has few patches.
 #include <cstdint>
 
 #include "device_util.cuh"
 
 namespace fc {
 namespace {
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
-               : "memory");
-  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
-               "r"(bytes)
-               : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
-  uint32_t done;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-      " selp.u32 %0, 1, 0, p;\n}\n"
-      : "=r"(done)
-      : "r"(smem_u32(bar)), "r"(parity)
-      : "memory");
-  return done != 0;
-}
-
-// bounded wait: gives up after `limit` polls (each poll may suspend briefly)
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint32_t limit) {
-  for (uint32_t it = 0; it < limit; ++it)
-    if (mbar_try_wait(bar, parity)) return true;
-  return false;
-}
-
-__device__ __forceinline__ void bulk_load(void* dst_smem, const void* src, uint32_t bytes,
-                                          uint64_t* bar) {
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
-          "r"(smem_u32(dst_smem)),
-      "l"(src), "r"(bytes), "r"(smem_u32(bar))
-      : "memory");
-}
-
-template <typename real>
-__device__ __forceinline__ real sinpi_r(real x);
-template <>
-__device__ __forceinline__ float sinpi_r<float>(float x) { return sinpif(x); }
-template <>
-__device__ __forceinline__ double sinpi_r<double>(double x) { return sinpi(x); }
-
-// phi(W_up / W) W for the MC limiter without a division:
-// 0 unless W and W_up share a sign, else sign(W) min(|W + W_up|/2, 2|W|, 2|W_up|)
-template <typename real>
-__device__ __forceinline__ real mc_limited(real W, real Wup) {
-  const real m = fmin(real(0.5) * fabs(W + Wup), real(2) * fmin(fabs(W), fabs(Wup)));
-  return (W * Wup > real(0)) ? copysign(m, W) : real(0);
-}
 
 template <typename real>
 __device__ __forceinline__ real correction(int order, int limiter, real s, real W, real Wup,
@@ -87,18 +29,17 @@ __device__ __forceinline__ real correction(int order, int limiter, real s, real 
   return real(0.5) * as * (real(1) - nu * as) * lim;
 }
 
-constexpr uint32_t kWaitLimit = 1u << 22;
-
 // x-edge (i,j) lies between cells (i-1,j) and (i,j): i in [0,MX], j in [-1,MX]
 // y-edge (i,j) lies between cells (i,j-1) and (i,j): j in [0,MX], i in [-1,MX]
 template <typename real, int MX, int NT>
-__global__ void __launch_bounds__(NT) advance_kernel(DevForest<real> D, int p0, int p1,
-                                                     AdvArgs a, int* err) {
+__global__ void __launch_bounds__(NT) advance_staged_kernel(DevForest<real> D, int p0, int p1,
+                                                            AdvArgs a, int* err) {
   constexpr int S = MX + 4;
   constexpr int NE = (MX + 1) * (MX + 2);
   constexpr int NV = MX + 3;  // corner nodes -1..MX+1
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t bar;
+  __shared__ real ucoef_s;
   real* Q = reinterpret_cast<real*>(smem_raw);
   real* Fn = Q + S * S;
   real* XP = Fn + NE;
@@ -114,7 +55,6 @@ __global__ void __launch_bounds__(NT) advance_kernel(DevForest<real> D, int p0, 
   const bool swirl = D.vel_kind == FC_VEL_SWIRL;
   const real cu = real(D.vel[0]), cv = real(D.vel[1]);
   const real nu = real(a.nu), half_nu = real(0.5 * a.nu), h = real(a.h);
-  __shared__ real ucoef_s;
   constexpr uint32_t bytes = sizeof(real) * S * S;
 
   if (threadIdx.x == 0) {
@@ -132,7 +72,7 @@ __global__ void __launch_bounds__(NT) advance_kernel(DevForest<real> D, int p0, 
     const real* src = D.buf[D.cur[pm.level]] + (size_t)p * S * S;
     real* dst = D.buf[D.cur[pm.level] ^ 1] + (size_t)p * S * S;
     if (threadIdx.x == 0) {
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      fence_proxy_async();
       mbar_expect_tx(&bar, bytes);
       bulk_load(Q, src, bytes, &bar);
     }
@@ -153,7 +93,7 @@ __global__ void __launch_bounds__(NT) advance_kernel(DevForest<real> D, int p0, 
     // together if any thread gave up
     const bool landed = mbar_wait(&bar, parity, kWaitLimit);
     if (!__syncthreads_and(landed)) {
-      if (threadIdx.x == 0) atomicOr(err, 1);
+      if (threadIdx.x == 0) atomicOr(err, kErrTimeout);
       mbar_wait(&bar, parity, kWaitLimit);  // let the copy land before leaving
       return;
     }
@@ -223,24 +163,35 @@ __global__ void __launch_bounds__(NT) advance_kernel(DevForest<real> D, int p0, 
 }
 
 template <typename real, int MX>
-constexpr size_t advance_smem() {
+constexpr size_t staged_smem() {
   return sizeof(real) * (size_t)((MX + 4) * (MX + 4) + 6 * (MX + 1) * (MX + 2) + 4 * (MX + 3));
 }
 
 template <typename real, int MX, int NT>
-cudaError_t advance_launch(const DevForest<real>& D, int p0, int p1, const AdvArgs& a, int* err,
-                           cudaStream_t s) {
+cudaError_t staged_launch(const DevForest<real>& D, int p0, int p1, const AdvArgs& a, int* err,
+                          cudaStream_t s) {
   static bool attr_set = false;
-  constexpr size_t smem = advance_smem<real, MX>();
+  constexpr size_t smem = staged_smem<real, MX>();
   if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(advance_kernel<real, MX, NT>,
+    cudaError_t e = cudaFuncSetAttribute(advance_staged_kernel<real, MX, NT>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
-  advance_kernel<real, MX, NT><<<p1 - p0, NT, smem, s>>>(D, p0, p1, a, err);
+  advance_staged_kernel<real, MX, NT><<<p1 - p0, NT, smem, s>>>(D, p0, p1, a, err);
   ++launch_counter();
   return cudaGetLastError();
+}
+
+template <typename real>
+cudaError_t launch_advance_staged(const DevForest<real>& D, int p0, int p1, const AdvArgs& a,
+                                  int* err, cudaStream_t s) {
+  switch (D.mx) {
+    case 8: return staged_launch<real, 8, 64>(D, p0, p1, a, err, s);
+    case 16: return staged_launch<real, 16, 128>(D, p0, p1, a, err, s);
+    case 32: return staged_launch<real, 32, 256>(D, p0, p1, a, err, s);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 }  // namespace
@@ -249,12 +200,8 @@ template <typename real>
 cudaError_t launch_advance(const DevForest<real>& D, int p0, int p1, const AdvArgs& a, int* err,
                            cudaStream_t s) {
   if (p1 <= p0) return cudaSuccess;
-  switch (D.mx) {
-    case 8: return advance_launch<real, 8, 64>(D, p0, p1, a, err, s);
-    case 16: return advance_launch<real, 16, 128>(D, p0, p1, a, err, s);
-    case 32: return advance_launch<real, 32, 256>(D, p0, p1, a, err, s);
-    default: return cudaErrorInvalidValue;
-  }
+  if (a.variant == ADV_WALK) return launch_advance_walk(D, p0, p1, a, err, s);
+  return launch_advance_staged(D, p0, p1, a, err, s);
 }
 
 template cudaError_t launch_advance<float>(const DevForest<float>&, int, int, const AdvArgs&,

@@ -94,6 +94,15 @@ struct fc_forest {
     std::vector<TimerPair> pairs;
   };
   bool use_graphs = true;
+  // autotuned patch-update configuration per launch size (bucket = log2 of
+  // the patches in one launch): variant and warps per CTA
+  struct Tune {
+    bool tuned = false;
+    int variant = ADV_STAGED, warps = 4;
+    float us = 0.f;
+  };
+  Tune tune[32];
+  int forced_variant = -1, forced_warps = 4;
   cudaStream_t cap_stream = nullptr;
   double* d_t0 = nullptr;  // start time of the replayed coarse step
   std::vector<Graph> graphs;
@@ -268,7 +277,9 @@ DevForest<real> dev(const fc_forest* F) {
 
 // per-launch scalars of the patch update for level L, step t -> t + dt; while
 // a graph is captured, t is relative to the replayed step's start time
-AdvArgs adv_args(const fc_forest* F, int L, double t, double dt) {
+void choose_variant(const fc_forest* F, int n, AdvArgs* a);
+
+AdvArgs adv_args(const fc_forest* F, int L, double t, double dt, int n) {
   const fc_forest_desc& d = F->host.desc;
   AdvArgs a{};
   a.h = std::ldexp(1.0, -L) / d.mx;
@@ -278,7 +289,35 @@ AdvArgs adv_args(const fc_forest* F, int L, double t, double dt) {
   a.t_half = t + 0.5 * dt;
   a.t_off = t + 0.5 * dt;
   a.t0_dev = F->capture_pairs ? F->d_t0 : nullptr;
+  a.variant = ADV_STAGED;
+  a.warps = 4;
+  a.ctas = 0;
+  choose_variant(F, n, &a);
   return a;
+}
+
+int size_bucket(int n) {
+  int b = 0;
+  while ((2 << b) <= n && b < 31) ++b;
+  return b;
+}
+
+// the patch-update configuration for a launch of n patches: the autotuned
+// choice when this size was tuned, else walk for launches that fill the GPU
+void choose_variant(const fc_forest* F, int n, AdvArgs* a) {
+  if (F->forced_variant >= 0) {
+    a->variant = F->forced_variant;
+    a->warps = F->forced_warps;
+    return;
+  }
+  const fc_forest::Tune& t = F->tune[size_bucket(n)];
+  if (t.tuned) {
+    a->variant = t.variant;
+    a->warps = t.warps;
+    return;
+  }
+  a->variant = n >= 1024 ? ADV_WALK : ADV_STAGED;
+  a->warps = F->esize == 4 ? 4 : 2;
 }
 
 // device error word -> status (and clear it)
@@ -352,7 +391,7 @@ fc_status advance_level_t(fc_forest* F, int L, double t, double dt, cudaStream_t
     }
     {
       Timed tm(F, 0, s, advance_bytes(F, p1 - p0));
-      FC_CUDA(launch_advance(D, p0, p1, adv_args(F, L, t, dt), F->d_err, s));
+      FC_CUDA(launch_advance(D, p0, p1, adv_args(F, L, t, dt, p1 - p0), F->d_err, s));
     }
     F->cur[L] ^= 1;
   }
@@ -503,6 +542,80 @@ fc_status fc_timers_read(fc_forest* F, int phase, double* ms, int64_t* launches,
   return FC_OK;
 }
 
+fc_status fc_set_advance_variant(fc_forest* F, int variant, int warps) {
+  if (!F || variant < -1 || variant > ADV_WALK || (warps != 2 && warps != 4 && warps != 8))
+    return fail(FC_ERR_INVALID_ARG, "variant must be -1, 0 or 1 and warps 2, 4 or 8");
+  F->forced_variant = variant;
+  F->forced_warps = warps;
+  destroy_graphs(F);
+  return FC_OK;
+}
+
+fc_status fc_autotune(fc_forest* F, int* report, void* stream) {
+  if (!F) return fail(FC_ERR_INVALID_ARG, "null forest");
+  cudaStream_t s = as_stream(stream);
+  const HostForest& H = F->host;
+  const struct {
+    int variant, warps;
+  } cand[] = {{ADV_STAGED, 4}, {ADV_WALK, 2}, {ADV_WALK, 4}, {ADV_WALK, 8}};
+  cudaEvent_t e0, e1;
+  FC_CUDA(cudaEventCreate(&e0));
+  FC_CUDA(cudaEventCreate(&e1));
+  DevForest<float> Df = dev<float>(F);
+  DevForest<double> Dd = dev<double>(F);
+  fc_status st = FC_OK;
+  for (int L = H.desc.lmin; L <= H.desc.lmax && st == FC_OK; ++L) {
+    const int p0 = H.lev_start[L], p1 = H.lev_start[L + 1];
+    if (p1 <= p0) continue;
+    fc_forest::Tune& t = F->tune[size_bucket(p1 - p0)];
+    if (t.tuned) continue;
+    AdvArgs a = adv_args(F, L, 0.0, 0.5 * std::ldexp(1.0, -L) / H.desc.mx, p1 - p0);
+    float best = 1e30f;
+    for (const auto& c : cand) {
+      a.variant = c.variant;
+      a.warps = c.warps;
+      auto run = [&]() {
+        return F->esize == 4 ? launch_advance(Df, p0, p1, a, F->d_err, s)
+                             : launch_advance(Dd, p0, p1, a, F->d_err, s);
+      };
+      cudaError_t e = run();  // warm-up (module load, attributes)
+      for (int k = 0; k < 3 && e == cudaSuccess; ++k) {
+        if (k == 0) e = cudaEventRecord(e0, s);
+        if (e == cudaSuccess) e = run();
+      }
+      if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+      if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+      float ms = 0.f;
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+      if (e != cudaSuccess) {
+        st = cuda_fail(e, "autotune");
+        break;
+      }
+      const float us = 1e3f * ms / 3.f;
+      if (us < best) {
+        best = us;
+        t.variant = c.variant;
+        t.warps = c.warps;
+        t.us = us;
+      }
+    }
+    t.tuned = st == FC_OK;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st != FC_OK) return st;
+  // the candidates overwrote the previous-state buffers
+  reset_times(F);
+  destroy_graphs(F);
+  if (report)
+    for (int b = 0; b < 32; ++b) {
+      report[3 * b] = F->tune[b].tuned ? F->tune[b].variant : -1;
+      report[3 * b + 1] = F->tune[b].warps;
+      report[3 * b + 2] = (int)(1e3f * F->tune[b].us);
+    }
+  return check_device_error(F, s);
+}
+
 fc_status fc_set_graphs(fc_forest* F, int enable) {
   if (!F) return fail(FC_ERR_INVALID_ARG, "null forest");
   F->use_graphs = enable != 0;
@@ -600,7 +713,7 @@ fc_status fc_step_global(fc_forest* F, double t, double dt, void* stream) {
   for (int L = H.desc.lmin; L <= H.desc.lmax; ++L) {
     const int p0 = H.lev_start[L], p1 = H.lev_start[L + 1];
     if (p1 <= p0) continue;
-    const AdvArgs a = adv_args(F, L, t, dt);
+    const AdvArgs a = adv_args(F, L, t, dt, p1 - p0);
     Timed tm(F, 0, s, advance_bytes(F, p1 - p0));
     cudaError_t e = F->esize == 4 ? launch_advance(Df, p0, p1, a, F->d_err, s)
                                   : launch_advance(Dd, p0, p1, a, F->d_err, s);

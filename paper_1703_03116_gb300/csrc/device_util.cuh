@@ -63,4 +63,72 @@ __device__ __forceinline__ real* patch_ptr(real* base, int p, int S) {
   return base + (size_t)p * S * S;
 }
 
+// ---------------------------------------------------------------- TMA / mbarrier
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
+               : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t done;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(done)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return done != 0;
+}
+
+// bounded wait: gives up after `limit` polls (each poll may suspend briefly)
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint32_t limit) {
+  for (uint32_t it = 0; it < limit; ++it)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+
+constexpr uint32_t kWaitLimit = 1u << 22;
+
+// 1D bulk copy global -> shared (TMA), completion counted on `bar`.
+// dst, src 16-byte aligned; bytes a multiple of 16.
+__device__ __forceinline__ void bulk_load(void* dst_smem, const void* src, uint32_t bytes,
+                                          uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+          "r"(smem_u32(dst_smem)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+template <typename real>
+__device__ __forceinline__ real sinpi_r(real x);
+template <>
+__device__ __forceinline__ float sinpi_r<float>(float x) { return sinpif(x); }
+template <>
+__device__ __forceinline__ double sinpi_r<double>(double x) { return sinpi(x); }
+
+// phi(W_up / W) W for the MC limiter without a division:
+// 0 unless W and W_up share a sign, else sign(W) min(|W + W_up|/2, 2|W|, 2|W_up|)
+template <typename real>
+__device__ __forceinline__ real mc_limited(real W, real Wup) {
+  const real m = fmin(real(0.5) * fabs(W + Wup), real(2) * fmin(fabs(W), fabs(Wup)));
+  return (W * Wup > real(0)) ? copysign(m, W) : real(0);
+}
+
 }  // namespace fc

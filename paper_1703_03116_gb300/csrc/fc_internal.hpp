@@ -117,7 +117,20 @@ struct FillArgs {
 struct AdvArgs {
   double h, nu, sfac, period, t_half, t_off;
   const double* t0_dev;
+  int variant;  // ADV_STAGED or ADV_WALK
+  int warps;    // walk variant: warps per CTA
+  int ctas;     // walk variant: CTAs in the grid (0: one per group of patches)
 };
+
+// Patch-update kernel variants (chosen per level launch by the autotuner):
+// staged -- one CTA per patch, every thread on every phase (low latency);
+// walk   -- lanes own patch columns and walk the rows, one warp per patch
+//           (fewest instructions per cell; the throughput choice).
+enum AdvVariant : int { ADV_STAGED = 0, ADV_WALK = 1 };
+
+template <typename real>
+cudaError_t launch_advance_walk(const DevForest<real>& D, int p0, int p1, const AdvArgs& a,
+                                int* err, cudaStream_t s);
 
 cudaError_t launch_set_time(double* t0_dev, double t0, cudaStream_t s);
 

@@ -160,6 +160,16 @@ class Forest:
         check(load().fc_tag_regrid(self._h, tau_r, tau_c, lm, ctypes.byref(ch), _stream(stream)))
         return ch.value
 
+    def autotune(self, stream=None) -> dict:
+        """Tune the patch-update kernel per launch size; returns {bucket: (variant, warps, ns)}."""
+        rep = np.zeros((32, 3), dtype=np.int32)
+        check(load().fc_autotune(self._h, _ip(rep), _stream(stream)))
+        return {b: tuple(int(v) for v in rep[b]) for b in range(32) if rep[b, 0] >= 0}
+
+    def set_advance_variant(self, variant: int, warps: int = 4):
+        """Force 0 staged / 1 walk for every launch; -1 restores the tuned choice."""
+        check(load().fc_set_advance_variant(self._h, variant, warps))
+
     def graphs(self, enable: bool = True):
         """Replay coarse multirate steps from captured CUDA graphs (default on)."""
         check(load().fc_set_graphs(self._h, 1 if enable else 0))

@@ -231,3 +231,49 @@ def test_timers_count_replayed_launches():
         gpu.step_multirate(n * dtc, dtc)
         ms, launches, nbytes = gpu.read_timer(0, reset=True)
         assert launches == substeps and ms > 0 and nbytes > 0, (n, launches, substeps, nlev)
+
+
+@pytest.mark.parametrize("variant,warps", [(0, 4), (1, 2), (1, 4), (1, 8)])
+@pytest.mark.parametrize("mx", [8, 16, 32])
+def test_advance_variants_match_oracle(variant, warps, mx):
+    """Both patch-update kernels (staged; walk with 2/4/8 warps per CTA) on
+    an adaptive swirl forest, FP64 and FP32, against the oracle."""
+    w = synth.swirl(8, lmin=2, lmax=4 if mx == 32 else 5, mx=mx)
+    _, dtc = synth.time_step(w)
+    for dtype, tol in ((fc.F64, F64_TOL), (fc.F32, 1e-4)):
+        ref, gpu = pair(fc, w, dtype)
+        gpu.set_advance_variant(variant, warps)
+        for n in range(2):
+            ref.step_multirate(n * dtc, dtc)
+            gpu.step_multirate(n * dtc, dtc)
+        err = relerr(gpu.get_q(), ref.get_q())
+        print(f"variant {variant} warps {warps} mx {mx} dtype {dtype}: rel err {err:.2e}")
+        assert err <= tol
+
+
+@pytest.mark.parametrize("scheme", [dict(limiter="none"), dict(limiter="first"),
+                                    dict(transverse=1), dict(domain="periodic"),
+                                    dict(velocity=("const", -0.7, 0.45))])
+def test_walk_variant_scheme_options(scheme):
+    w = synth.swirl(4, lmin=2, lmax=4, mx=16)
+    for k, v in scheme.items():
+        setattr(w, k, v)
+    ref, gpu = pair(fc, w, fc.F64)
+    gpu.set_advance_variant(1, 4)
+    dt = 0.45 / (16 * 16)
+    for n in range(4):
+        ref.step_global(n * dt, dt)
+        gpu.step_global(n * dt, dt)
+    assert relerr(gpu.get_q(), ref.get_q()) <= F64_TOL
+
+
+def test_autotune_then_parity():
+    ws = synth.ensemble(12, seed=5, lmin=2, mx=32, levels=(4, 5))
+    _, dtc = synth.time_step(ws[0], 5)
+    ref, gpu = pair(fc, ws, fc.F64)
+    rep = gpu.autotune()
+    assert len(rep) >= 2 and all(v[0] in (0, 1) and v[2] > 0 for v in rep.values())
+    for n in range(2):
+        ref.step_multirate(n * dtc, dtc)
+        gpu.step_multirate(n * dtc, dtc)
+    assert relerr(gpu.get_q(), ref.get_q()) <= F64_TOL
