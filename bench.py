@@ -151,6 +151,9 @@ class Runner:
                             velocity=w.velocity, nforests=len(workloads))
         self.F = fc.initial_forest(desc, q0_fn(workloads), lmax_f=self.lmax_f,
                                    tau_r=w.tau_refine, tau_c=w.tau_coarsen)
+        # pick the patch-update kernel per launch size on this layout (untimed setup)
+        self.tuning = {int(b): {"variant": ["staged", "walk"][v], "warps": k, "ns": ns}
+                       for b, (v, k, ns) in self.F.autotune().items()}
         self.n = 0
 
     def updates(self) -> int:
@@ -189,7 +192,7 @@ def measure(runner, steps, warmup, flush_buf, clock_index):
     phases = {k: F.read_timer(ph) for ph, k in enumerate(["advance", "fill", "regrid"])}
     F.timers(False)
     return dict(ms=ms, updates=updates, phases=phases, launches=launches,
-                clocks=clk.summary(), patches=len(F))
+                clocks=clk.summary(), patches=len(F), tuning=runner.tuning)
 
 
 def roofline_of(phase, peak_gbs, peak_src):
@@ -244,7 +247,7 @@ def run_ours(args):
                                        "4/5/6, 32x32 patches", "patches": b["patches"]},
                 "gpu_launches": b["launches"], "clocks": b["clocks"],
                 "roofline": roofline_of(b["phases"]["advance"], hbm, peak_src),
-                "phases_ms": {k: x[0] for k, x in b["phases"].items()}}
+                "phases_ms": {k: x[0] for k, x in b["phases"].items()}, "autotune": b["tuning"]}
         if rank == 0:
             print(json.dumps(line), flush=True)
         if dist is not None:
@@ -304,6 +307,7 @@ def run_ours(args):
         "clocks": r["clocks"], "e2e": e2e, "gpu_launches": r["launches"],
         "roofline": roofline_of(r["phases"]["advance"], hbm, peak_src),
         "phases_ms": {k: v[0] for k, v in r["phases"].items()} | {"step_total": r["ms"]},
+        "autotune": r["tuning"],
     }
     if rank == 0 and not args.no_variants:
         variants = {}
@@ -327,7 +331,7 @@ def run_ours(args):
                 "ms_per_step": b["ms"] / nsteps, "steps": nsteps,
                 "roofline": roofline_of(b["phases"]["advance"], hbm, peak_src),
                 "phases_ms": {k: x[0] for k, x in b["phases"].items()},
-                "gpu_launches": b["launches"], "clocks": b["clocks"]}
+                "gpu_launches": b["launches"], "clocks": b["clocks"], "autotune": b["tuning"]}
             del br
         out["variants"] = variants
         out["cpu_baseline"] = cpu_baseline(synth.swirl(seed=0))
