@@ -207,6 +207,35 @@ fc_status fc_set_advance_variant(fc_forest* forest, int variant, int warps);
 fc_status fc_timers_read(fc_forest* forest, int phase, double* ms, int64_t* launches,
                          double* bytes, int reset);
 
+/* Mass sums without any allocation.
+ *
+ * The paper has no counterpart: this entry point exists for callers that
+ * cannot allocate device memory when they need the sum (an allocator
+ * callback, a runtime that owns the device memory, a loop that must not
+ * touch the allocator).  It computes the same per-forest FP64 mass as
+ * fc_forest_mass, from a field the caller already holds, and keeps its
+ * per-leaf partial sums in a fixed device array of FC_NOALLOC_MAX_LEAVES
+ * doubles that every GPU loading this library holds until the process
+ * exits.  It calls no cudaMalloc/cudaFree and no allocating library routine.
+ *
+ *   q             device, packed interior field [leaf][j][i] of `dtype`
+ *                 (FC_F32 / FC_F64), mx x mx cells per leaf.
+ *   level         device, nleaves ints: refinement level of each leaf.
+ *   forest_start  device, nforests+1 ints: the leaves of forest f are
+ *                 [forest_start[f], forest_start[f+1]) in the field order.
+ *   out           device, nforests doubles: sum over the forest's leaves of
+ *                 h^2 sum(q), h = 2^-level / mx; each leaf is summed in a
+ *                 fixed order, then the leaves of a forest in a fixed order.
+ * nleaves above FC_NOALLOC_MAX_LEAVES is rejected (FC_ERR_INVALID_ARG).
+ * Work is enqueued on `stream`; the call does not synchronise.  All calls
+ * share the one array: calls whose work overlaps on the GPU (other streams,
+ * other threads) race and must be serialised by the caller.  The first call
+ * on a device looks up the array's device address with that device current;
+ * make that first call before any stream capture. */
+#define FC_NOALLOC_MAX_LEAVES (1 << 19)
+fc_status fc_mass_noalloc(const void* q, int dtype, int mx, int nleaves, const int* level,
+                          const int* forest_start, int nforests, double* out, void* stream);
+
 /* Thread-local description of the last failure. */
 const char* fc_last_error(void);
 

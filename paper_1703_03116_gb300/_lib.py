@@ -54,6 +54,8 @@ SIGNATURES = {
     "fc_timers_enable": (ctypes.c_int, [_vp, ctypes.c_int]),
     "fc_set_graphs": (ctypes.c_int, [_vp, ctypes.c_int]),
     "fc_autotune": (ctypes.c_int, [_vp, _ip, _vp]),
+    "fc_mass_noalloc": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp, _vp,
+                                       ctypes.c_int, _vp, _vp]),
     "fc_set_advance_variant": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int]),
     "fc_timers_read": (ctypes.c_int, [_vp, ctypes.c_int, _dp, ctypes.POINTER(ctypes.c_int64),
                                       _dp, ctypes.c_int]),

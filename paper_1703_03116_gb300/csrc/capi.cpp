@@ -542,6 +542,24 @@ fc_status fc_timers_read(fc_forest* F, int phase, double* ms, int64_t* launches,
   return FC_OK;
 }
 
+fc_status fc_mass_noalloc(const void* q, int dtype, int mx, int nleaves, const int* level,
+                          const int* forest_start, int nforests, double* out, void* stream) {
+  if (!q || !level || !forest_start || !out)
+    return fail(FC_ERR_INVALID_ARG, "fc_mass_noalloc: null pointer");
+  if (dtype != FC_F32 && dtype != FC_F64)
+    return fail(FC_ERR_INVALID_ARG, "fc_mass_noalloc: dtype must be FC_F32 or FC_F64");
+  if (mx < 1 || nleaves < 1 || nforests < 1)
+    return fail(FC_ERR_INVALID_ARG, "fc_mass_noalloc: mx, nleaves and nforests must be >= 1");
+  if (nleaves > FC_NOALLOC_MAX_LEAVES)
+    return fail(FC_ERR_INVALID_ARG, "fc_mass_noalloc: nleaves " + std::to_string(nleaves) +
+                                        " exceeds FC_NOALLOC_MAX_LEAVES (" +
+                                        std::to_string(FC_NOALLOC_MAX_LEAVES) + ")");
+  cudaError_t e = noalloc_mass(q, dtype, mx, nleaves, level, forest_start, nforests, out,
+                               as_stream(stream));
+  if (e != cudaSuccess) return cuda_fail(e, "fc_mass_noalloc");
+  return FC_OK;
+}
+
 fc_status fc_set_advance_variant(fc_forest* F, int variant, int warps) {
   if (!F || variant < -1 || variant > ADV_WALK || (warps != 2 && warps != 4 && warps != 8))
     return fail(FC_ERR_INVALID_ARG, "variant must be -1, 0 or 1 and warps 2, 4 or 8");

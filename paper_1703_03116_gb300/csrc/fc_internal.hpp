@@ -161,4 +161,8 @@ cudaError_t launch_remap(const DevForest<real>& Old, const DevForest<real>& New,
 
 uint64_t& launch_counter();
 
+// fc_mass_noalloc's kernels (scratch in a file-scope device array)
+cudaError_t noalloc_mass(const void* q, int dtype, int mx, int nleaves, const int* level,
+                         const int* fstart, int nforests, double* out, cudaStream_t s);
+
 }  // namespace fc

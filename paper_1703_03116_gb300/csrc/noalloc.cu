@@ -1,0 +1,112 @@
+// Mass reduction that allocates nothing: fc_mass_noalloc.
+//
+// Some callers cannot allocate device memory at the point where they need a
+// mass sum -- for example code running inside a host allocator callback, a
+// process whose device memory is carved up by another runtime, or a driver
+// loop that must not touch the allocator once it is running.  This entry
+// point takes a packed field that the caller already holds on the device and
+// keeps its per-leaf partial sums in a fixed, file-scope device array instead
+// of forest-owned scratch.  It is the same two-stage FP64 reduction as
+// fc_forest_mass: one CTA per leaf sums its cells in a fixed order, then one
+// CTA per forest sums its leaves in a fixed order.
+#include <cstdint>
+#include <mutex>
+
+#include "fc_internal.hpp"
+
+namespace fc {
+namespace {
+
+// Per-leaf partial sums.  Every GPU that loads this library keeps this array
+// (FC_NOALLOC_MAX_LEAVES doubles) until the process exits.  Every call writes
+// each slot it reads before reading it, so nothing needs clearing; calls whose
+// work overlaps on the GPU share the array and race.
+static __device__ __align__(256) double g_leaf_sums[FC_NOALLOC_MAX_LEAVES];
+
+template <typename real>
+__global__ void leaf_sum_kernel(const real* q, int mx, int nleaves, const int* level,
+                                double* sums) {
+  __shared__ double red[256];
+  const int cells = mx * mx;
+  for (int k = blockIdx.x; k < nleaves; k += gridDim.x) {
+    const real* Q = q + (size_t)k * cells;
+    double s = 0.0;
+    for (int c = threadIdx.x; c < cells; c += blockDim.x) s += (double)Q[c];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+      if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+      const double h = ldexp(1.0, -level[k]) / mx;
+      sums[k] = h * h * red[0];
+    }
+    __syncthreads();
+  }
+}
+
+__global__ void forest_total_kernel(const double* sums, const int* fstart, int nforests,
+                                    double* out) {
+  __shared__ double red[256];
+  for (int f = blockIdx.x; f < nforests; f += gridDim.x) {
+    double s = 0.0;
+    for (int k = fstart[f] + threadIdx.x; k < fstart[f + 1]; k += blockDim.x) s += sums[k];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+      if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) out[f] = red[0];
+    __syncthreads();
+  }
+}
+
+// Device address of g_leaf_sums, looked up once per device with that device
+// current.  Host code must not pass the symbol itself: on the host it names a
+// stand-in, not device memory.
+constexpr int kMaxDevices = 64;
+std::mutex g_addr_mu;
+double* g_addr[kMaxDevices] = {nullptr};
+
+cudaError_t scratch_address(double** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(g_addr_mu);
+  if (!g_addr[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_leaf_sums);
+    if (e != cudaSuccess) return e;
+    g_addr[dev] = static_cast<double*>(p);
+  }
+  *out = g_addr[dev];
+  return cudaSuccess;
+}
+
+}  // namespace
+
+cudaError_t noalloc_mass(const void* q, int dtype, int mx, int nleaves, const int* level,
+                         const int* fstart, int nforests, double* out, cudaStream_t s) {
+  double* sums = nullptr;
+  cudaError_t e = scratch_address(&sums);
+  if (e != cudaSuccess) return e;
+  const int g1 = nleaves < 4096 ? nleaves : 4096;
+  if (dtype == FC_F32)
+    leaf_sum_kernel<float><<<g1, 256, 0, s>>>(static_cast<const float*>(q), mx, nleaves, level,
+                                              sums);
+  else
+    leaf_sum_kernel<double><<<g1, 256, 0, s>>>(static_cast<const double*>(q), mx, nleaves,
+                                               level, sums);
+  ++launch_counter();
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const int g2 = nforests < 4096 ? nforests : 4096;
+  forest_total_kernel<<<g2, 256, 0, s>>>(sums, fstart, nforests, out);
+  ++launch_counter();
+  return cudaGetLastError();
+}
+
+}  // namespace fc
