@@ -203,6 +203,14 @@ fc_status fc_set_graphs(fc_forest* forest, int enable);
  * fc_set_advance_variant forces a variant for every launch (variant -1
  * restores the tuned/heuristic choice); warps is 2, 4 or 8. */
 fc_status fc_autotune(fc_forest* forest, int* report, void* stream);
+
+/* Fused ghost fill in multirate substeps (on by default): the patch-update
+ * kernel applies Alg. 1 to the ghost ring of the tile it holds in shared
+ * memory, so a level substep is one fill launch (the coarse neighbours'
+ * time-interpolated data) plus the update, and the level's ghost cells are
+ * never written to HBM.  enable = 0: separate fill kernels write every ghost
+ * ring first (same results, bit for bit). */
+fc_status fc_set_fused_fill(fc_forest* forest, int enable);
 fc_status fc_set_advance_variant(fc_forest* forest, int variant, int warps);
 fc_status fc_timers_read(fc_forest* forest, int phase, double* ms, int64_t* launches,
                          double* bytes, int reset);

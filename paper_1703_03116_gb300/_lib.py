@@ -54,6 +54,7 @@ SIGNATURES = {
     "fc_timers_enable": (ctypes.c_int, [_vp, ctypes.c_int]),
     "fc_set_graphs": (ctypes.c_int, [_vp, ctypes.c_int]),
     "fc_autotune": (ctypes.c_int, [_vp, _ip, _vp]),
+    "fc_set_fused_fill": (ctypes.c_int, [_vp, ctypes.c_int]),
     "fc_mass_noalloc": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp, _vp,
                                        ctypes.c_int, _vp, _vp]),
     "fc_set_advance_variant": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int]),

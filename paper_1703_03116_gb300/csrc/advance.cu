@@ -15,7 +15,7 @@
 // finishes quickly -- the better choice when a launch has few patches.
 #include <cstdint>
 
-#include "device_util.cuh"
+#include "ghost_gather.cuh"
 
 namespace fc {
 namespace {
@@ -40,6 +40,7 @@ __global__ void __launch_bounds__(NT) advance_staged_kernel(DevForest<real> D, i
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t bar;
   __shared__ real ucoef_s;
+  __shared__ NbrStage st;
   real* Q = reinterpret_cast<real*>(smem_raw);
   real* Fn = Q + S * S;
   real* XP = Fn + NE;
@@ -76,6 +77,7 @@ __global__ void __launch_bounds__(NT) advance_staged_kernel(DevForest<real> D, i
       mbar_expect_tx(&bar, bytes);
       bulk_load(Q, src, bytes, &bar);
     }
+    if (a.gather) stage_neighbours(D.meta, D.nbr, p, st, threadIdx.x);
     // streamfunction tables while the tile is in flight:
     // psi = s(x) s(y) cos(pi t/T)/pi, s = sin^2(pi .); along an edge the
     // corner difference is s(corner) * sin(pi (z0 + z1)) * sin(pi h)
@@ -97,6 +99,9 @@ __global__ void __launch_bounds__(NT) advance_staged_kernel(DevForest<real> D, i
       mbar_wait(&bar, parity, kWaitLimit);  // let the copy land before leaving
       return;
     }
+    if (a.gather)  // Alg. 1 for this patch, into the tile's ghost ring
+      fill_patch_ghosts<real, MX>(D, st, pm, a.tlevel, real(a.alpha), Q, threadIdx.x, NT,
+                                  []() { __syncthreads(); });
     auto q = [&](int i, int j) -> real { return Q[(j + 2) * S + (i + 2)]; };
     auto uvel = [&](int i, int j) -> real { return swirl ? ucoef * Sx[i + 1] * Ty[j + 1] : cu; };
     auto vvel = [&](int i, int j) -> real { return swirl ? -ucoef * Sy[j + 1] * Tx[i + 1] : cv; };

@@ -19,7 +19,7 @@
 //    current one is computed.  Grids are persistent (CTAs loop over groups).
 #include <cstdint>
 
-#include "device_util.cuh"
+#include "ghost_gather.cuh"
 
 namespace fc {
 namespace {
@@ -77,6 +77,7 @@ __global__ void __launch_bounds__(NW * 32) advance_walk_kernel(DevForest<real> D
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t bars[NW][2];
   __shared__ real ucoef_s;
+  __shared__ NbrStage nst[NW][PPW];
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int seg = lane / MX, li = lane % MX;
@@ -160,7 +161,13 @@ __global__ void __launch_bounds__(NW * 32) advance_walk_kernel(DevForest<real> D
       return;
     }
     par ^= 1;
-    const real* T = tile(b, seg);
+    real* T = tile(b, seg);
+    if (a.gather) {  // Alg. 1 for this segment's patch, into the tile's ghost ring
+      stage_neighbours(D.meta, D.nbr, pc, nst[warp][seg], li);
+      __syncwarp();
+      fill_patch_ghosts<real, MX>(D, nst[warp][seg], pm, a.tlevel, real(a.alpha), T, li, MX,
+                                  []() { __syncwarp(); });
+    }
     auto Q = [&](int i, int j) -> real { return T[(j + 2) * S + (i + 2)]; };
 
     // side pass: lanes own rows r = -1..MX+1

@@ -54,7 +54,9 @@ struct fc_forest {
   PatchMeta* d_meta = nullptr;
   NbrEntry* d_nbr = nullptr;
   int* d_lists = nullptr;  // all work lists, concatenated
-  size_t off_all = 0, off_coarse_all = 0, off_a[kMaxLevel + 1] = {0}, off_b[kMaxLevel + 1] = {0};
+  size_t off_all = 0, off_coarse_all = 0, off_a[kMaxLevel + 1] = {0}, off_b[kMaxLevel + 1] = {0},
+         off_t[kMaxLevel + 1] = {0};
+  bool fuse = true;  // multirate substeps: update kernel gathers its own ghosts
   int* d_api_to_dev = nullptr;
   int* d_fstart = nullptr;
   double* d_patch_sums = nullptr;
@@ -230,6 +232,8 @@ fc_status upload(fc_forest* F, bool alloc_store) {
     lists.insert(lists.end(), H.list_a[l].begin(), H.list_a[l].end());
     F->off_b[l] = lists.size();
     lists.insert(lists.end(), H.list_b[l].begin(), H.list_b[l].end());
+    F->off_t[l] = lists.size();
+    lists.insert(lists.end(), H.list_t[l].begin(), H.list_t[l].end());
   }
   FC_CUDA(dmalloc(&F->d_lists, lists.size()));
   if (!lists.empty())
@@ -292,6 +296,9 @@ AdvArgs adv_args(const fc_forest* F, int L, double t, double dt, int n) {
   a.variant = ADV_STAGED;
   a.warps = 4;
   a.ctas = 0;
+  a.gather = 0;
+  a.tlevel = -1;
+  a.alpha = 0.0;
   choose_variant(F, n, &a);
   return a;
 }
@@ -379,19 +386,34 @@ fc_status advance_level_t(fc_forest* F, int L, double t, double dt, cudaStream_t
   DevForest<real> D = dev<real>(F);
   if (p1 > p0) {
     const double gb = ghost_bytes(F);
-    FillArgs A{F->d_lists + F->off_a[L], (int)H.list_a[L].size(), tlevel, alpha};
-    {
-      Timed tm(F, 1, s, gb * A.ntargets);
-      FC_CUDA(launch_fill_coarse(D, A, s));
-    }
-    FillArgs B{F->d_lists + F->off_b[L], (int)H.list_b[L].size(), tlevel, alpha};
-    {
-      Timed tm(F, 1, s, gb * B.ntargets);
-      FC_CUDA(launch_fill_fine(D, B, s));
+    AdvArgs a = adv_args(F, L, t, dt, p1 - p0);
+    if (F->fuse) {
+      // coarse neighbours first (their interiors time-interpolated into qT,
+      // their coarse ghost regions filled); the update kernel then fills
+      // each level-L patch's ghost ring in shared memory itself
+      FillArgs A{F->d_lists + F->off_t[L], (int)H.list_t[L].size(), tlevel, alpha};
+      {
+        Timed tm(F, 1, s, gb * A.ntargets);
+        FC_CUDA(launch_fill_coarse(D, A, s));
+      }
+      a.gather = 1;
+      a.tlevel = tlevel;
+      a.alpha = alpha;
+    } else {
+      FillArgs A{F->d_lists + F->off_a[L], (int)H.list_a[L].size(), tlevel, alpha};
+      {
+        Timed tm(F, 1, s, gb * A.ntargets);
+        FC_CUDA(launch_fill_coarse(D, A, s));
+      }
+      FillArgs B{F->d_lists + F->off_b[L], (int)H.list_b[L].size(), tlevel, alpha};
+      {
+        Timed tm(F, 1, s, gb * B.ntargets);
+        FC_CUDA(launch_fill_fine(D, B, s));
+      }
     }
     {
       Timed tm(F, 0, s, advance_bytes(F, p1 - p0));
-      FC_CUDA(launch_advance(D, p0, p1, adv_args(F, L, t, dt, p1 - p0), F->d_err, s));
+      FC_CUDA(launch_advance(D, p0, p1, a, F->d_err, s));
     }
     F->cur[L] ^= 1;
   }
@@ -632,6 +654,13 @@ fc_status fc_autotune(fc_forest* F, int* report, void* stream) {
       report[3 * b + 2] = (int)(1e3f * F->tune[b].us);
     }
   return check_device_error(F, s);
+}
+
+fc_status fc_set_fused_fill(fc_forest* F, int enable) {
+  if (!F) return fail(FC_ERR_INVALID_ARG, "null forest");
+  F->fuse = enable != 0;
+  destroy_graphs(F);
+  return FC_OK;
 }
 
 fc_status fc_set_graphs(fc_forest* F, int enable) {
@@ -928,6 +957,7 @@ fc_status fc_tag_regrid(fc_forest* F, double tau_refine, double tau_coarsen,
   F->off_coarse_all = G->off_coarse_all;
   std::memcpy(F->off_a, G->off_a, sizeof F->off_a);
   std::memcpy(F->off_b, G->off_b, sizeof F->off_b);
+  std::memcpy(F->off_t, G->off_t, sizeof F->off_t);
   F->d_api_to_dev = G->d_api_to_dev;
   F->d_fstart = G->d_fstart;
   F->d_patch_sums = G->d_patch_sums;

@@ -69,7 +69,11 @@ struct HostForest {
   std::vector<NbrEntry> nbr;             // device order, 8 per patch
   int lev_start[kMaxLevel + 2] = {0};    // device patches of level l: [lev_start[l], lev_start[l+1])
   std::vector<int> list_all, list_coarse_all;
-  std::vector<int> list_a[kMaxLevel + 1], list_b[kMaxLevel + 1];
+  // multirate substep of level l: list_t = coarse neighbours (level l-1) of
+  // level-l patches, filled through the time-interpolation buffer; list_a =
+  // list_t plus the level-l patches; list_b = level-l patches with a coarser
+  // neighbour
+  std::vector<int> list_a[kMaxLevel + 1], list_b[kMaxLevel + 1], list_t[kMaxLevel + 1];
   std::vector<int> forest_start;         // leaves of forest f: [forest_start[f], forest_start[f+1])
 
   // Build everything from `leaves`; returns an empty string or an error.
@@ -120,6 +124,11 @@ struct AdvArgs {
   int variant;  // ADV_STAGED or ADV_WALK
   int warps;    // walk variant: warps per CTA
   int ctas;     // walk variant: CTAs in the grid (0: one per group of patches)
+  // gather != 0: the kernel fills each patch's ghost ring itself (Alg. 1 in
+  // shared memory) before the update; coarser neighbours on `tlevel` are
+  // read through the time-interpolation buffer
+  int gather, tlevel;
+  double alpha;
 };
 
 // Patch-update kernel variants (chosen per level launch by the autotuner):

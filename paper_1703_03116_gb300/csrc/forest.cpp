@@ -191,6 +191,7 @@ std::string HostForest::build() {
   for (int l = 0; l <= kMaxLevel; ++l) {
     list_a[l].clear();
     list_b[l].clear();
+    list_t[l].clear();
   }
   for (int l = 0; l <= kMaxLevel; ++l) {
     std::vector<char> inT;
@@ -206,7 +207,10 @@ std::string HostForest::build() {
     }
     if (l > 0)
       for (int p = lev_start[l - 1]; p < lev_start[l]; ++p)
-        if (inT[p]) list_a[l].push_back(p);
+        if (inT[p]) {
+          list_a[l].push_back(p);
+          list_t[l].push_back(p);
+        }
     for (int p = lev_start[l]; p < lev_start[l + 1]; ++p) list_a[l].push_back(p);
   }
   return "";

@@ -1,0 +1,159 @@
+// Ghost-cell rules of Alg. 1 (Sec. 2.3), shared by the standalone fill
+// kernels (which write the ghost ring of a patch array in HBM) and by the
+// patch-update kernels (which fill the ghost ring of the tile they hold in
+// shared memory before computing).
+//
+//  copy     (same-size neighbour):  q_c(I_c) = q_n(A I_c + F)      Eq. transform
+//  average  (finer neighbour):      q_c(I_c) = 1/4 sum_k q_f(I_f^k) Eq. ghost_coarse
+//  interp.  (coarser neighbour):    q_f = q_c + 1/4 (s_x d_x + s_y d_y),
+//           s = minmod of the one-sided differences in the coarse index
+//           space                                                   Eq. ghost_fine
+//  walls    zeroth-order extrapolation: an exterior ghost copies the owner's
+//           cell with each out-of-domain index clamped into the interior.
+#pragma once
+
+#include "device_util.cuh"
+
+namespace fc {
+
+// the eight face/corner entries of one patch and the layout of their patches
+struct NbrStage {
+  NbrEntry e[8];
+  PatchMeta m0[8], m1[8];
+};
+
+// threads tid = 0..7 of a cooperating group stage the entries of patch p
+__device__ __forceinline__ void stage_neighbours(const PatchMeta* meta, const NbrEntry* nbr,
+                                                 int p, NbrStage& st, int tid) {
+  if (tid < 8) {
+    const NbrEntry e = nbr[(size_t)p * 8 + tid];
+    st.e[tid] = e;
+    if (e.n0 >= 0) st.m0[tid] = meta[e.n0];
+    if (e.n1 >= 0) st.m1[tid] = meta[e.n1];
+  }
+}
+
+// interior cell (i, j) of source patch n (level nlev), time-interpolated when
+// n lies on the level read through the interpolation buffer
+template <typename real>
+__device__ __forceinline__ real src_interior(const DevForest<real>& D, int tlevel, real alpha,
+                                             int n, int nlev, int i, int j) {
+  const size_t o = (size_t)n * D.S * D.S + (size_t)(j + kMbc) * D.S + (i + kMbc);
+  const int c = D.cur[nlev];
+  if (nlev == tlevel) return (real(1) - alpha) * D.buf[c ^ 1][o] + alpha * D.buf[c][o];
+  return D.buf[c][o];
+}
+
+// Ghost (i, j) of the owner (layout pm) from a same-size or finer neighbour.
+// Returns false when the region is not of that kind (or the entry is malformed).
+template <typename real, int MX>
+__device__ __forceinline__ bool copy_or_average(const DevForest<real>& D, const NbrStage& st,
+                                                const PatchMeta& pm, int tlevel, real alpha,
+                                                int i, int j, real& v) {
+  const int r = region_of<MX>(i, j);
+  const NbrEntry& e = st.e[r];
+  if (e.kind != NB_SAME && e.kind != NB_FINE) return false;
+  const int2 Ip = apply_a(e.a, pm.x * MX + i, pm.y * MX + j);
+  const int gx = Ip.x + e.fx, gy = Ip.y + e.fy;
+  if (e.kind == NB_SAME) {
+    const PatchMeta& nm = st.m0[r];
+    const int lx = gx - nm.x * MX, ly = gy - nm.y * MX;
+    if (lx < 0 || lx >= MX || ly < 0 || ly >= MX) return false;
+    v = src_interior(D, tlevel, alpha, e.n0, nm.level, lx, ly);
+    return true;
+  }
+  int n = e.n0;
+  const PatchMeta* nm = &st.m0[r];
+  int lx = 2 * gx - nm->x * MX, ly = 2 * gy - nm->y * MX;
+  if (lx < 0 || lx >= MX || ly < 0 || ly >= MX) {
+    if (e.n1 < 0) return false;
+    n = e.n1;
+    nm = &st.m1[r];
+    lx = 2 * gx - nm->x * MX;
+    ly = 2 * gy - nm->y * MX;
+    if (lx < 0 || lx >= MX || ly < 0 || ly >= MX) return false;
+  }
+  real s[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int2 d = apply_a(e.a, (q & 1) ? 1 : -1, (q & 2) ? 1 : -1);
+    s[q] = src_interior(D, tlevel, alpha, n, nm->level, lx + (d.x > 0), ly + (d.y > 0));
+  }
+  v = real(0.25) * (((s[0] + s[1]) + s[2]) + s[3]);
+  return true;
+}
+
+// Ghost (i, j) of the owner from its coarser neighbour; the coarse patch is
+// read through the interpolation buffer when it lies on `tlevel`.
+template <typename real, int MX>
+__device__ __forceinline__ bool interpolate(const DevForest<real>& D, const NbrStage& st,
+                                            const PatchMeta& pm, int tlevel, int i, int j,
+                                            real& v) {
+  constexpr int S = MX + 4;
+  const int r = region_of<MX>(i, j);
+  const NbrEntry& e = st.e[r];
+  if (e.kind != NB_COARSE) return false;
+  const int2 Ip = apply_a(e.a, pm.x * MX + i, pm.y * MX + j);
+  const int gx = Ip.x + e.fx, gy = Ip.y + e.fy;
+  const PatchMeta& nm = st.m0[r];
+  const int ic = (gx >> 1) - nm.x * MX, jc = (gy >> 1) - nm.y * MX;
+  if (ic < 0 || ic >= MX || jc < 0 || jc >= MX) return false;
+  const real dx = (gx & 1) ? real(1) : real(-1);
+  const real dy = (gy & 1) ? real(1) : real(-1);
+  const real* C = patch_ptr(nm.level == tlevel ? D.qT : D.buf[D.cur[nm.level]], e.n0, S) +
+                  (jc + kMbc) * S + ic + kMbc;
+  const real q0 = C[0];
+  const real sx = minmod(C[1] - q0, q0 - C[-1]);
+  const real sy = minmod(C[S] - q0, q0 - C[-S]);
+  v = q0 + real(0.25) * (sx * dx + sy * dy);
+  return true;
+}
+
+// walls: exterior ghosts of the owner's array Q (threads tid, stride nt)
+template <typename real, int MX>
+__device__ __forceinline__ void wall_bc(const PatchMeta& pm, real* Q, int tid, int nt) {
+  constexpr int S = MX + 4;
+  const int N = MX << pm.level;
+  for (int k = tid; k < num_ghosts<MX>(); k += nt) {
+    int i, j;
+    ghost_ij<MX>(k, i, j);
+    const int gx = pm.x * MX + i, gy = pm.y * MX + j;
+    const bool ox = gx < 0 || gx >= N, oy = gy < 0 || gy >= N;
+    if (!ox && !oy) continue;
+    const int ic = ox ? (gx < 0 ? 0 : MX - 1) : i;
+    const int jc = oy ? (gy < 0 ? 0 : MX - 1) : j;
+    Q[(j + kMbc) * S + i + kMbc] = Q[(jc + kMbc) * S + ic + kMbc];
+  }
+}
+
+// The whole of Alg. 1 for one patch into array Q (shared or global):
+// copy/average, boundary condition, interpolation, boundary condition.
+// `sync` orders the phases across the cooperating threads.
+template <typename real, int MX, class Sync>
+__device__ __forceinline__ void fill_patch_ghosts(const DevForest<real>& D, const NbrStage& st,
+                                                  const PatchMeta& pm, int tlevel, real alpha,
+                                                  real* Q, int tid, int nt, Sync sync) {
+  constexpr int S = MX + 4;
+  for (int k = tid; k < num_ghosts<MX>(); k += nt) {
+    int i, j;
+    ghost_ij<MX>(k, i, j);
+    real v;
+    if (copy_or_average<real, MX>(D, st, pm, tlevel, alpha, i, j, v))
+      Q[(j + kMbc) * S + i + kMbc] = v;
+  }
+  sync();
+  const bool walls = D.domain == FC_DOMAIN_WALLS;
+  if (walls) wall_bc<real, MX>(pm, Q, tid, nt);
+  sync();
+  for (int k = tid; k < num_ghosts<MX>(); k += nt) {
+    int i, j;
+    ghost_ij<MX>(k, i, j);
+    real v;
+    if (interpolate<real, MX>(D, st, pm, tlevel, i, j, v)) Q[(j + kMbc) * S + i + kMbc] = v;
+  }
+  sync();
+  if (walls) wall_bc<real, MX>(pm, Q, tid, nt);
+  sync();
+}
+
+}  // namespace fc

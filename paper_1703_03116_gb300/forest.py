@@ -170,6 +170,10 @@ class Forest:
         """Force 0 staged / 1 walk for every launch; -1 restores the tuned choice."""
         check(load().fc_set_advance_variant(self._h, variant, warps))
 
+    def fused_fill(self, enable: bool = True):
+        """Multirate substeps fill each patch's ghosts inside the update kernel (default on)."""
+        check(load().fc_set_fused_fill(self._h, 1 if enable else 0))
+
     def graphs(self, enable: bool = True):
         """Replay coarse multirate steps from captured CUDA graphs (default on)."""
         check(load().fc_set_graphs(self._h, 1 if enable else 0))

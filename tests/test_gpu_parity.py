@@ -189,18 +189,41 @@ def test_full_size_swirl_one_coarse_step():
 def test_launch_counter_counts_kernels():
     w = synth.swirl(0, lmin=2, lmax=3, mx=8)
     ref, gpu = pair(fc, w, fc.F64)
-    # 3 substeps (level 2 once, level 3 twice), each a copy/average fill and an
-    # advance; level 3 also interpolates from level 2
+    # 3 substeps (level 2 once, level 3 twice).  Separate fills: each substep a
+    # copy/average fill and an update, level 3 also an interpolation fill.
     gpu.graphs(False)
+    gpu.fused_fill(False)
     fc.launch_count(reset=True)
     gpu.step_multirate(0.0, 0.01)
     assert fc.launch_count() == 3 * 2 + 2
+    # fused fill: level 2 one update; level 3 the fill of its level-2
+    # neighbours plus the update
+    gpu.fused_fill(True)
+    fc.launch_count(reset=True)
+    gpu.step_multirate(0.01, 0.01)
+    assert fc.launch_count() == 1 + 2 * 2
     # graph replay: the same kernels plus the one that stores the step time
     gpu.graphs(True)
     for n in range(3):
         fc.launch_count(reset=True)
-        gpu.step_multirate(0.01 * (n + 1), 0.01)
-        assert fc.launch_count() == 3 * 2 + 2 + 1
+        gpu.step_multirate(0.01 * (n + 2), 0.01)
+        assert fc.launch_count() == 1 + 2 * 2 + 1
+
+
+@pytest.mark.parametrize("variant", [0, 1])
+def test_fused_fill_matches_separate_fills_bitwise(variant):
+    w = synth.swirl(9, lmin=2, lmax=5, mx=16)
+    _, dtc = synth.time_step(w)
+    ref, a = pair(fc, w, fc.F64)
+    b = fc.Forest(a.desc, ref.leaves())
+    b.set_q(a.get_q())
+    a.set_advance_variant(variant, 4)
+    b.set_advance_variant(variant, 4)
+    b.fused_fill(False)
+    for n in range(3):
+        a.step_multirate(n * dtc, dtc)
+        b.step_multirate(n * dtc, dtc)
+    np.testing.assert_array_equal(a.get_q(), b.get_q())
 
 
 def test_graph_replay_matches_direct_launches():
