@@ -135,6 +135,25 @@ fc_status fc_tag_regrid(fc_forest* forest, double tau_refine, double tau_coarsen
 /* The per-leaf indicator alone, into a host array of nleaves doubles. */
 fc_status fc_tag(fc_forest* forest, double* delta_host, void* stream);
 
+/* Velocity scale sigma: every edge speed is multiplied by sigma (default 1).
+ * It is the scalar parameter of the adjoint's velocity derivative. */
+fc_status fc_set_velocity_scale(fc_forest* forest, double scale);
+
+/* Adjoint of one global time step (the transposes of Alg. 1 and of the
+ * wave-propagation update; BASELINE's differentiation pattern, no counterpart
+ * in the paper).  The forest must hold q^n, the state at the start of the
+ * step (it is not advanced).  With the step's map q^{n+1} = S(Fill(q^n)),
+ *   lam     device, in/out, field layout: on entry dL/dq^{n+1}, on return
+ *           dL/dq^n = (dq^{n+1}/dq^n)^T lam, using the piece of the MC
+ *           limiter and of the minmod interpolation slopes that q^n selects
+ *           (the a.e. derivative);
+ *   dscale  device, one double, accumulated: += lam^T dq^{n+1}/dsigma.
+ * Kernels: per-level update transposes (shared-memory tiles), then atomic
+ * scatters for the interpolation and copy/average transposes, so the
+ * rounding order of those sums is not fixed.  Asynchronous on `stream`. */
+fc_status fc_adjoint_step_global(fc_forest* forest, double t, double dt, void* lam,
+                                 double* dscale, void* stream);
+
 /* Total mass per forest, sum over leaves of h^2 sum(q), accumulated in FP64
  * on the device in a fixed order.  out: host, nforests doubles.  Synchronous. */
 fc_status fc_forest_mass(const fc_forest* forest, double* out, void* stream);

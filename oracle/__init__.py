@@ -18,7 +18,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SO = os.path.join(_HERE, "liboracle.so")
-_SRC = ["forest.c", "ghost.c", "claw.c", "drive.c"]
+_SRC = ["forest.c", "ghost.c", "claw.c", "drive.c", "adjoint.c"]
 _HDR = ["oracle.h", "internal.h"]
 
 WALLS, PERIODIC, SPHERE = 0, 1, 2
@@ -48,7 +48,7 @@ class _Params(ctypes.Structure):
         ("lmin", ctypes.c_int), ("lmax", ctypes.c_int),
         ("vel_kind", ctypes.c_int), ("vel", ctypes.c_double * 4),
         ("order", ctypes.c_int), ("limiter", ctypes.c_int),
-        ("transverse", ctypes.c_int),
+        ("transverse", ctypes.c_int), ("vel_scale", ctypes.c_double),
     ]
 
 
@@ -75,6 +75,10 @@ def lib():
     L.or_tag.argtypes = [vp, dp]
     L.or_regrid.argtypes = [vp, ctypes.c_double, ctypes.c_double, ip, ip]
     L.or_mass.argtypes = [vp, dp]
+    L.or_adjoint_global.argtypes = [vp, ctypes.c_int, ctypes.c_double, ctypes.c_double, dp, dp,
+                                    dp, dp]
+    L.or_adjoint_step_global.argtypes = [vp, ctypes.c_double, ctypes.c_double, dp, dp]
+    L.or_set_params.argtypes = [vp, ctypes.POINTER(_Params)]
     L.or_single_grid_periodic.argtypes = [ctypes.POINTER(_Params), ctypes.c_int, dp,
                                           ctypes.c_double, ctypes.c_double, ctypes.c_int]
     L.or_mc_phi.restype = ctypes.c_double
@@ -117,6 +121,7 @@ def params(domain: int, mx: int, mbc: int, lmin: int, lmax: int, velocity,
     else:
         raise ValueError(velocity)
     p.order, p.limiter, p.transverse = order, limiter, transverse
+    p.vel_scale = 1.0
     return p
 
 
@@ -205,6 +210,29 @@ class Forest:
         out = np.zeros(self.prm.nforests)
         lib().or_mass(self.h, _dptr(out))
         return out
+
+    def adjoint_global(self, nsteps: int, t0: float, dt: float, q_target: np.ndarray):
+        """(loss, dL/dq0, dL/dscale) of L = 1/2 |q_N - q_target|^2 after nsteps
+        global steps from the current state (which is left unchanged)."""
+        qt = np.ascontiguousarray(q_target, dtype=np.float64).reshape(len(self), self.mx, self.mx)
+        g = np.zeros_like(qt)
+        gs = np.zeros(1)
+        loss = np.zeros(1)
+        _check(lib().or_adjoint_global(self.h, nsteps, t0, dt, _dptr(qt), _dptr(g), _dptr(gs),
+                                       _dptr(loss)))
+        return float(loss[0]), g, float(gs[0])
+
+    def adjoint_step_global(self, t: float, dt: float, lam: np.ndarray):
+        """Adjoint of one global step at the current state: returns (lam_n, dscale)."""
+        lam = np.ascontiguousarray(lam, dtype=np.float64).reshape(len(self), self.mx, self.mx).copy()
+        ds = np.zeros(1)
+        _check(lib().or_adjoint_step_global(self.h, t, dt, _dptr(lam), _dptr(ds)))
+        return lam, float(ds[0])
+
+    def set_velocity_scale(self, s: float):
+        """Scale every edge speed (the parameter of the velocity-scale gradient)."""
+        self.prm.vel_scale = float(s)
+        lib().or_set_params(self.h, ctypes.byref(self.prm))
 
 
 def single_grid_periodic(prm: _Params, q: np.ndarray, t0: float, dt: float,

@@ -60,20 +60,32 @@ static double dsq(long J0, double h) { /* s(y_{J0+1}) - s(y_{J0}) */
   return sin(M_PI * ((double)(2 * J0 + 1) * h)) * sin(M_PI * h);
 }
 
+static double scale_of(const or_params* P) { return P->vel_scale != 0.0 ? P->vel_scale : 1.0; }
+
 /* speed at x-edge (i-1/2, j) */
 static double u_edge(const velctx* c, int i, int j) {
-  if (c->P->vel_kind == OR_VEL_CONST) return c->P->vel[0];
+  if (c->P->vel_kind == OR_VEL_CONST) return scale_of(c->P) * c->P->vel[0];
   long I = c->gx0 + i, J = c->gy0 + j;
   double ct = cos(M_PI * c->thalf / c->P->vel[0]) / M_PI;
-  return ct * s2(I, c->h) * dsq(J, c->h) / c->h;
+  return scale_of(c->P) * (ct * s2(I, c->h) * dsq(J, c->h) / c->h);
 }
 
 /* speed at y-edge (i, j-1/2) */
 static double v_edge(const velctx* c, int i, int j) {
-  if (c->P->vel_kind == OR_VEL_CONST) return c->P->vel[1];
+  if (c->P->vel_kind == OR_VEL_CONST) return scale_of(c->P) * c->P->vel[1];
   long I = c->gx0 + i, J = c->gy0 + j;
   double ct = cos(M_PI * c->thalf / c->P->vel[0]) / M_PI;
-  return -ct * s2(J, c->h) * dsq(I, c->h) / c->h;
+  return scale_of(c->P) * (-ct * s2(J, c->h) * dsq(I, c->h) / c->h);
+}
+
+double or_u_edge(const or_params* P, double h, double t, long gx0, long gy0, int i, int j) {
+  velctx c = {P, h, t, gx0, gy0};
+  return u_edge(&c, i, j);
+}
+
+double or_v_edge(const or_params* P, double h, double t, long gx0, long gy0, int i, int j) {
+  velctx c = {P, h, t, gx0, gy0};
+  return v_edge(&c, i, j);
 }
 
 static double pos(double a) { return a > 0.0 ? a : 0.0; }

@@ -175,6 +175,8 @@ void or_destroy(or_forest* F) {
 
 int or_num_leaves(const or_forest* F) { return F->n; }
 
+void or_set_params(or_forest* F, const or_params* P) { F->P.vel_scale = P->vel_scale; }
+
 void or_get_leaves(const or_forest* F, int* out) {
   for (int k = 0; k < F->n; ++k) {
     out[5 * k] = F->lv[k].f;

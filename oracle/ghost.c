@@ -187,7 +187,19 @@ static void fill_regions(const or_forest* F, const gmap* G, int p, double* dst,
     }
 }
 
-int or_fill_all(or_forest* F) {
+int or_fill_all(or_forest* F) { return or_fill_all_snapshot(F, NULL); }
+
+int or_ghost_holder(or_forest* F, int p, int k, int* rel, int* src, double* x, double* y) {
+  const gmap* G = classify_all(F);
+  const gmap* g = &G[(size_t)p * nghost(F) + k];
+  *rel = g->rel;
+  *src = g->src;
+  *x = g->x;
+  *y = g->y;
+  return 0;
+}
+
+int or_fill_all_snapshot(or_forest* F, double* snapshot) {
   size_t S2 = (size_t)F->S * F->S;
   const gmap* G = classify_all(F);
   for (int p = 0; p < F->n; ++p)
@@ -212,6 +224,7 @@ int or_fill_all(or_forest* F) {
   for (int p = 0; p < F->n; ++p) fill_regions(F, G, p, cur[p], sp, REL_COARSE);
   /* phase 4 */
   for (int p = 0; p < F->n; ++p) apply_bc(F, p, cur[p]);
+  if (snapshot) memcpy(snapshot, snap, sizeof(double) * S2 * F->n);
   free(sp);
   free(snap);
   free(cur);

@@ -44,6 +44,14 @@ int or_touch(const or_forest* F, const or_leaf* a, const or_leaf* c);
 /* claw.c */
 void or_claw_step(const or_params* P, double* q, int mx, int mbc, double h,
                   double dt, double t, long gx0, long gy0);
+/* edge speeds at velocity time t (the half step of the step using them) */
+double or_u_edge(const or_params* P, double h, double t, long gx0, long gy0, int i, int j);
+double or_v_edge(const or_params* P, double h, double t, long gx0, long gy0, int i, int j);
+
+/* ghost.c: Alg. 1 that also returns the state after phase 2 (the data that
+ * the interpolation reads), and the ghost-holder map of the current mesh */
+int or_fill_all_snapshot(or_forest* F, double* snapshot);
+int or_ghost_holder(or_forest* F, int p, int k, int* rel, int* src, double* x, double* y);
 
 /* ghost.c */
 int or_fill_all(or_forest* F);

@@ -37,6 +37,7 @@ typedef struct {
   int order;       /* 1: first order, 2: second-order corrections */
   int limiter;     /* 0: unlimited (Lax-Wendroff), 1: MC */
   int transverse;  /* 0: none, 1: fluctuations, 2: fluctuations + corrections */
+  double vel_scale; /* every edge speed is multiplied by this (0 is read as 1) */
 } or_params;
 
 typedef struct or_forest or_forest;
@@ -44,6 +45,8 @@ typedef struct or_forest or_forest;
 /* leaves: n rows of (forest, block, level, ix, iy) */
 or_forest* or_create(const or_params* P, int n, const int* leaves);
 void or_destroy(or_forest* F);
+/* take the velocity scale of P (the layout parameters cannot change) */
+void or_set_params(or_forest* F, const or_params* P);
 int or_num_leaves(const or_forest* F);
 void or_get_leaves(const or_forest* F, int* out);
 /* interior data, [leaf][j][i], leaves in the order of or_get_leaves */
@@ -59,6 +62,21 @@ int or_step_multirate(or_forest* F, double t, double dt_coarse);
 int or_tag(or_forest* F, double* delta);                /* ghost fill + per-leaf indicator */
 int or_regrid(or_forest* F, double tau_r, double tau_c, const int* lmax_f, int* changed);
 void or_mass(const or_forest* F, double* per_forest);
+
+/* Adjoint of global time stepping (reverse mode, a.e. derivatives of the
+ * limiter and of the minmod interpolation slopes, branches taken from the
+ * forward state).  Starting from the forest's current interior state q0, run
+ * nsteps global steps (t0, dt), form L = 1/2 sum over interior cells of
+ * (q_N - q_target)^2, and return dL/dq0 (interior layout, leaf order) and
+ * dL/d(velocity scale) at the current scale.  The forest's state is left at
+ * q0.  Every intermediate state is stored (test sizes only). */
+int or_adjoint_global(or_forest* F, int nsteps, double t0, double dt, const double* q_target,
+                      double* grad_q0, double* grad_scale, double* loss);
+
+/* one adjoint step: given lam (interior, adjoint of q^{n+1}) and the current
+ * state q^n, overwrite lam with the adjoint of q^n and add the step's
+ * velocity-scale derivative to *dscale */
+int or_adjoint_step_global(or_forest* F, double t, double dt, double* lam, double* dscale);
 
 /* one uniform periodic N x N grid, used to check the forest against it */
 int or_single_grid_periodic(const or_params* P, int N, double* q, double t0,

@@ -55,6 +55,9 @@ SIGNATURES = {
     "fc_set_graphs": (ctypes.c_int, [_vp, ctypes.c_int]),
     "fc_autotune": (ctypes.c_int, [_vp, _ip, _vp]),
     "fc_set_fused_fill": (ctypes.c_int, [_vp, ctypes.c_int]),
+    "fc_set_velocity_scale": (ctypes.c_int, [_vp, ctypes.c_double]),
+    "fc_adjoint_step_global": (ctypes.c_int, [_vp, ctypes.c_double, ctypes.c_double, _vp, _vp,
+                                              _vp]),
     "fc_mass_noalloc": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp, _vp,
                                        ctypes.c_int, _vp, _vp]),
     "fc_set_advance_variant": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int]),

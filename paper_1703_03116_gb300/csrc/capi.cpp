@@ -105,6 +105,8 @@ struct fc_forest {
   };
   Tune tune[32];
   int forced_variant = -1, forced_warps = 4;
+  double vel_scale = 1.0;                 // multiplies every edge speed
+  void* lam[2] = {nullptr, nullptr};      // adjoint tiles (patch-store layout), lazily allocated
   cudaStream_t cap_stream = nullptr;
   double* d_t0 = nullptr;  // start time of the replayed coarse step
   std::vector<Graph> graphs;
@@ -188,6 +190,8 @@ void free_device(fc_forest* F) {
   dfree(F->d_remap);
   dfree(F->d_err);
   dfree(F->d_t0);
+  dfree(F->lam[0]);
+  dfree(F->lam[1]);
 }
 
 // upload tables (and allocate a store) for the current host layout
@@ -273,6 +277,10 @@ DevForest<real> dev(const fc_forest* F) {
   for (int l = 0; l <= kMaxLevel; ++l) D.cur[l] = F->cur[l];
   D.vel_kind = H.desc.vel_kind;
   for (int k = 0; k < 4; ++k) D.vel[k] = H.desc.vel[k];
+  if (D.vel_kind == FC_VEL_CONST) {  // the velocity scale multiplies every edge speed
+    D.vel[0] *= F->vel_scale;
+    D.vel[1] *= F->vel_scale;
+  }
   D.order = H.desc.order;
   D.limiter = H.desc.limiter;
   D.transverse = H.desc.transverse;
@@ -289,7 +297,7 @@ AdvArgs adv_args(const fc_forest* F, int L, double t, double dt, int n) {
   a.h = std::ldexp(1.0, -L) / d.mx;
   a.nu = dt / a.h;
   a.period = d.vel[0];
-  a.sfac = d.vel_kind == FC_VEL_SWIRL ? std::sin(M_PI * a.h) / (M_PI * a.h) : 0.0;
+  a.sfac = d.vel_kind == FC_VEL_SWIRL ? F->vel_scale * std::sin(M_PI * a.h) / (M_PI * a.h) : 0.0;
   a.t_half = t + 0.5 * dt;
   a.t_off = t + 0.5 * dt;
   a.t0_dev = F->capture_pairs ? F->d_t0 : nullptr;
@@ -654,6 +662,62 @@ fc_status fc_autotune(fc_forest* F, int* report, void* stream) {
       report[3 * b + 2] = (int)(1e3f * F->tune[b].us);
     }
   return check_device_error(F, s);
+}
+
+fc_status fc_set_velocity_scale(fc_forest* F, double scale) {
+  if (!F || !(scale == scale)) return fail(FC_ERR_INVALID_ARG, "bad velocity scale");
+  F->vel_scale = scale;
+  destroy_graphs(F);
+  return FC_OK;
+}
+
+}  // extern "C"
+
+template <typename real>
+static fc_status adjoint_step_t(fc_forest* F, double t, double dt, void* lam, double* dscale,
+                                cudaStream_t s) {
+  const HostForest& H = F->host;
+  const size_t S = (size_t)H.desc.mx + 2 * kMbc;
+  const size_t cells = std::max<size_t>((size_t)H.npatch() * S * S, 1);
+  for (int b = 0; b < 2; ++b)
+    if (!F->lam[b] && cudaMalloc(&F->lam[b], cells * sizeof(real)) != cudaSuccess)
+      return fail(FC_ERR_OOM, "adjoint buffer allocation failed");
+  // the caller's adjoint (field layout) into the interior of lam[0]
+  DevForest<real> L = dev<real>(F);
+  L.buf[0] = L.buf[1] = static_cast<real*>(F->lam[0]);
+  for (int l = 0; l <= kMaxLevel; ++l) L.cur[l] = 0;
+  FC_CUDA(launch_unpack(L, F->d_api_to_dev, static_cast<const real*>(lam), s));
+  // the forward ghost fill of the current state: the forward tiles
+  fc_status st = fill_all(F, s);
+  if (st != FC_OK) return st;
+  AdjArgs g{};
+  g.t = t;
+  g.dt = dt;
+  g.period = H.desc.vel[0];
+  g.scale = F->vel_scale;
+  g.dscale_factor = F->vel_scale != 0.0 ? 1.0 / F->vel_scale : 0.0;
+  g.lev_start = H.lev_start;
+  g.coarse_list = F->d_lists + F->off_coarse_all;
+  g.ncoarse = (int)H.list_coarse_all.size();
+  {
+    Timed tm(F, 3, s, 0.0);
+    FC_CUDA(launch_adjoint_step(dev<real>(F), g, static_cast<const real*>(F->lam[0]),
+                                static_cast<real*>(F->lam[1]), dscale, s));
+  }
+  L.buf[0] = L.buf[1] = static_cast<real*>(F->lam[1]);
+  FC_CUDA(launch_pack(L, F->d_api_to_dev, static_cast<real*>(lam), 0, s));
+  return FC_OK;
+}
+
+extern "C" {
+
+fc_status fc_adjoint_step_global(fc_forest* F, double t, double dt, void* lam, double* dscale,
+                                 void* stream) {
+  if (!F || !lam || !dscale) return fail(FC_ERR_INVALID_ARG, "null argument");
+  if (!(dt > 0.0)) return fail(FC_ERR_INVALID_ARG, "dt must be positive");
+  cudaStream_t s = as_stream(stream);
+  return F->esize == 4 ? adjoint_step_t<float>(F, t, dt, lam, dscale, s)
+                       : adjoint_step_t<double>(F, t, dt, lam, dscale, s);
 }
 
 fc_status fc_set_fused_fill(fc_forest* F, int enable) {

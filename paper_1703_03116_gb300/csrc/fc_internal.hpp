@@ -143,6 +143,18 @@ cudaError_t launch_advance_walk(const DevForest<real>& D, int p0, int p1, const 
 
 cudaError_t launch_set_time(double* t0_dev, double t0, cudaStream_t s);
 
+// Adjoint of one global step (t -> t + dt): per-level update transposes, then
+// the transpose of Alg. 1 (interpolation, boundary condition, copy/average).
+struct AdjArgs {
+  double t, dt, period, scale, dscale_factor;  // dscale += factor * sum_e dL/ds_e s_e
+  const int* lev_start;                        // host, device-order level ranges
+  const int* coarse_list;                      // device: patches with a coarser neighbour
+  int ncoarse;
+};
+template <typename real>
+cudaError_t launch_adjoint_step(const DevForest<real>& D, const AdjArgs& g, const real* lam_in,
+                                real* lam_out, double* dscale, cudaStream_t s);
+
 // device error word bits
 constexpr int kErrTimeout = 1;
 

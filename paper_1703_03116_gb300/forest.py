@@ -170,6 +170,16 @@ class Forest:
         """Force 0 staged / 1 walk for every launch; -1 restores the tuned choice."""
         check(load().fc_set_advance_variant(self._h, variant, warps))
 
+    def set_velocity_scale(self, scale: float):
+        check(load().fc_set_velocity_scale(self._h, float(scale)))
+
+    def adjoint_step_global(self, t: float, dt: float, lam, dscale, stream=None):
+        """In place: lam (CUDA tensor, field layout) <- adjoint of the step's input;
+        dscale (CUDA float64 tensor, 1 element) += velocity-scale derivative."""
+        assert lam.is_cuda and lam.is_contiguous() and dscale.is_cuda
+        check(load().fc_adjoint_step_global(self._h, t, dt, ctypes.c_void_p(lam.data_ptr()),
+                                            ctypes.c_void_p(dscale.data_ptr()), _stream(stream)))
+
     def fused_fill(self, enable: bool = True):
         """Multirate substeps fill each patch's ghosts inside the update kernel (default on)."""
         check(load().fc_set_fused_fill(self._h, 1 if enable else 0))

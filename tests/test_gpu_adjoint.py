@@ -1,0 +1,132 @@
+"""The GPU adjoint (fc_adjoint_step_global, autograd with sqrt(N) checkpoints)
+against the oracle's adjoint, the transpose identity and finite differences.
+
+FP64: relative error of the gradient <= 1e-10 against the oracle (the adjoint
+sums ghost contributions with atomics, so only the rounding order differs).
+FP32: <= 1e-3 against the FP64 oracle adjoint, as the config-5 tolerance.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from gpu_helpers import desc_for, relerr
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+fc = pytest.importorskip("paper_1703_03116_gb300")
+from paper_1703_03116_gb300.autograd import advect  # noqa: E402
+
+DEV = torch.device("cuda", 0)
+
+
+def _tensor(a, dtype):
+    return torch.tensor(np.ascontiguousarray(a), dtype=dtype, device=DEV)
+
+
+def test_gpu_adjoint_transpose_identity_linear():
+    """Unlimited scheme on a uniform periodic forest: the step is linear, so
+    <S v, w> = <v, S^T w> to rounding."""
+    w0 = synth.smooth_periodic(0, level=2, mx=16, velocity=("swirl", 4.0), limiter="none")
+    F = fc.Forest(desc_for(fc, w0, fc.F64), oracle.uniform_leaves(2))
+    n = len(F)
+    v = _tensor(synth.random_field((n, 16, 16), seed=1) - 0.5, torch.float64)
+    w = _tensor(synth.random_field((n, 16, 16), seed=2) - 0.5, torch.float64)
+    dt = 0.9 / 64
+    F.set_q(v)
+    F.step_global(0.2, dt)
+    Jv = torch.empty_like(v)
+    F.get_q(out=Jv)
+    F.set_q(torch.zeros_like(v))
+    lam = w.clone()
+    ds = torch.zeros(1, dtype=torch.float64, device=DEV)
+    F.adjoint_step_global(0.2, dt, lam, ds)
+    a, b = float((Jv * w).sum()), float((v * lam).sum())
+    assert abs(a - b) <= 1e-13 * abs(a)
+
+
+def _case(mx=8, lmax=4, seed=3):
+    w = synth.swirl(seed, lmin=2, lmax=lmax, mx=mx)
+    ref = oracle.initial_forest(w)
+    x, y = synth.cell_centres(ref.leaves(), mx)
+    q0 = synth.evaluate(synth.smooth_periodic(1), x, y) + 0.3 * np.sin(3 * x + 1) * np.cos(2 * y)
+    qt = synth.evaluate(synth.smooth_periodic(2), x, y)
+    ref.set_q(q0)
+    return w, ref, q0, qt
+
+
+@pytest.mark.parametrize("mx,lmax", [(8, 4), (16, 4), (32, 3)])
+def test_gpu_adjoint_step_matches_oracle_fp64(mx, lmax):
+    w, ref, q0, qt = _case(mx, lmax)
+    F = fc.Forest(desc_for(fc, w, fc.F64), ref.leaves())
+    F.set_q(q0)
+    lam0 = synth.random_field(q0.shape, seed=9) - 0.5
+    dt = 0.9 / (mx * 2 ** lmax)
+    lam_ref, ds_ref = ref.adjoint_step_global(0.3, dt, lam0)
+    lam = _tensor(lam0, torch.float64)
+    ds = torch.zeros(1, dtype=torch.float64, device=DEV)
+    F.adjoint_step_global(0.3, dt, lam, ds)
+    assert relerr(lam.cpu().numpy(), lam_ref) <= 1e-12
+    assert abs(float(ds) - ds_ref) <= 1e-12 * abs(ds_ref)
+
+
+@pytest.mark.parametrize("dtype,tol", [("f64", 1e-10), ("f32", 1e-3)])
+def test_autograd_gradient_matches_oracle(dtype, tol):
+    w, ref, q0, qt = _case(8, 4)
+    nsteps, dt = 9, 0.9 / 128
+    loss_ref, g_ref, gs_ref = ref.adjoint_global(nsteps, 0.0, dt, qt)
+    fdt = fc.F64 if dtype == "f64" else fc.F32
+    tdt = torch.float64 if dtype == "f64" else torch.float32
+    F = fc.Forest(desc_for(fc, w, fdt), ref.leaves())
+    q = _tensor(q0, tdt).requires_grad_(True)
+    s = torch.ones((), dtype=tdt, device=DEV, requires_grad=True)
+    qN = advect(q, s, F, 0.0, dt, nsteps)
+    loss = 0.5 * ((qN - _tensor(qt, tdt)) ** 2).sum()
+    loss.backward()
+    err_q = relerr(q.grad.double().cpu().numpy(), g_ref)
+    err_s = abs(float(s.grad) - gs_ref) / abs(gs_ref)
+    print(f"{dtype}: loss {float(loss):.6e} vs {loss_ref:.6e}, grad q0 rel err {err_q:.2e}, "
+          f"grad scale rel err {err_s:.2e}")
+    assert err_q <= tol and err_s <= tol
+
+
+def test_checkpoint_segments_give_the_same_gradient():
+    w, ref, q0, qt = _case(8, 4)
+    F = fc.Forest(desc_for(fc, w, fc.F64), ref.leaves())
+    grads = []
+    for seg in (1, 3, 0, 9):
+        q = _tensor(q0, torch.float64).requires_grad_(True)
+        s = torch.ones((), dtype=torch.float64, device=DEV, requires_grad=True)
+        qN = advect(q, s, F, 0.0, 0.9 / 128, 9, segment=seg)
+        (0.5 * ((qN - _tensor(qt, torch.float64)) ** 2).sum()).backward()
+        grads.append((q.grad.cpu().numpy(), float(s.grad)))
+    for g, gs in grads[1:]:
+        assert relerr(g, grads[0][0]) <= 1e-12 and abs(gs - grads[0][1]) <= 1e-12 * abs(gs)
+
+
+def test_autograd_central_differences_fp64():
+    w, ref, q0, qt = _case(16, 4)
+    F = fc.Forest(desc_for(fc, w, fc.F64), ref.leaves())
+    nsteps, dt = 6, 0.9 / 256
+    qt_t = _tensor(qt, torch.float64)
+
+    def L(q, s):
+        with torch.no_grad():
+            qN = advect(q, s, F, 0.0, dt, nsteps)
+            return float(0.5 * ((qN - qt_t) ** 2).sum())
+
+    q = _tensor(q0, torch.float64).requires_grad_(True)
+    s = torch.ones((), dtype=torch.float64, device=DEV, requires_grad=True)
+    qN = advect(q, s, F, 0.0, dt, nsteps)
+    (0.5 * ((qN - qt_t) ** 2).sum()).backward()
+    d = _tensor(synth.random_field(q0.shape, seed=4) - 0.5, torch.float64)
+    eps = 1e-7
+    q0t = _tensor(q0, torch.float64)
+    one = torch.ones((), dtype=torch.float64, device=DEV)
+    fd = (L(q0t + eps * d, one) - L(q0t - eps * d, one)) / (2 * eps)
+    assert abs(fd - float((q.grad * d).sum())) <= 1e-6 * abs(fd)
+    fds = (L(q0t, one + 1e-6) - L(q0t, one - 1e-6)) / 2e-6
+    assert abs(fds - float(s.grad)) <= 1e-6 * abs(fds)
