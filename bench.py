@@ -128,6 +128,25 @@ class Clocks:
                 "samples": len(sm)}
 
 
+def rank_workload(rank: int):
+    """The independent forest a rank advances (weak scaling: one forest per GPU)."""
+    return synth.swirl(seed=rank)
+
+
+def aggregate(values, ops, dist=None, device="cpu"):
+    """Combine per-rank scalars across ranks: ops[k] is "max" (times) or "sum"
+    (work).  The only collective of the run; it sits outside the data path."""
+    if dist is None:
+        return [float(v) for v in values]
+    import torch
+    out = []
+    for v, op in zip(values, ops):
+        t = torch.tensor([float(v)], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX if op == "max" else dist.ReduceOp.SUM)
+        out.append(float(t.item()))
+    return out
+
+
 def peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -204,6 +223,44 @@ def roofline_of(phase, peak_gbs, peak_src):
             "avg_launch_us": 1e3 * ms / max(n, 1), "bytes_per_launch": nbytes / max(n, 1)}
 
 
+def adjoint_cost(fc, torch, flush_buf, nsteps: int = 64):
+    """Forward vs gradient cost on the frozen swirl forest (FP32, global steps,
+    sqrt(N) checkpoints): L = 1/2 |q_N - q_target|^2, gradients with respect
+    to q0 and the velocity scale."""
+    from paper_1703_03116_gb300.autograd import advect
+    w = synth.swirl(seed=0)
+    tw = synth.adjoint_target(w)
+    desc = fc.make_desc(domain=fc.WALLS, mx=w.mx, lmin=w.lmin, lmax=w.lmax, dtype=fc.F32,
+                        velocity=w.velocity)
+    F = fc.initial_forest(desc, q0_fn([w]), tau_r=w.tau_refine, tau_c=w.tau_coarsen)
+    leaves = F.leaves()
+    dev = flush_buf.device
+    q0 = torch.tensor(q0_fn([w])(leaves), dtype=torch.float32, device=dev)
+    qt = torch.tensor(q0_fn([tw])(leaves), dtype=torch.float32, device=dev)
+    dt = w.cfl / (w.mx * 2 ** w.lmax)
+    updates = nsteps * len(leaves) * w.mx * w.mx  # global steps: every patch every step
+    times = {}
+    for name in ("forward", "forward+backward"):
+        q = q0.clone().requires_grad_(name != "forward")
+        s = torch.ones((), dtype=torch.float32, device=dev, requires_grad=name != "forward")
+        flush_buf.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        qN = advect(q, s, F, 0.0, dt, nsteps)
+        loss = 0.5 * ((qN - qt) ** 2).sum()
+        if name != "forward":
+            loss.backward()
+        e1.record()
+        torch.cuda.synchronize()
+        times[name] = e0.elapsed_time(e1)
+    fwd, both = times["forward"], times["forward+backward"]
+    return {"workload": f"frozen swirl forest ({len(leaves)} patches), {nsteps} global steps, "
+                        "FP32, sqrt(N) checkpoints",
+            "forward_ms": fwd, "gradient_ms": both - fwd,
+            "gradient_over_forward": (both - fwd) / fwd,
+            "forward_cell_updates_per_s": updates / (fwd * 1e-3)}
+
+
 def run_ours(args):
     import torch
 
@@ -221,14 +278,9 @@ def run_ours(args):
     flush_buf = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
 
     def reduce(v, op):
-        if dist is None:
-            return v
-        t = torch.tensor([v], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=op)
-        return float(t.item())
+        return aggregate([v], [op], dist, dev)[0]
 
-    MAX = dist.ReduceOp.MAX if dist else None
-    SUM = dist.ReduceOp.SUM if dist else None
+    MAX, SUM = "max", "sum"
     pk = peaks()
     hbm = pk.get("hbm_gbs")
     peak_src = "measured" if hbm else "fallback"
@@ -253,7 +305,7 @@ def run_ours(args):
         if dist is not None:
             dist.destroy_process_group()
         return
-    run = Runner(fc, torch, [synth.swirl(seed=rank)], dtype)
+    run = Runner(fc, torch, [rank_workload(rank)], dtype)
     torch.cuda.synchronize()
     if dist is not None:
         dist.barrier()
@@ -333,6 +385,7 @@ def run_ours(args):
                 "phases_ms": {k: x[0] for k, x in b["phases"].items()},
                 "gpu_launches": b["launches"], "clocks": b["clocks"], "autotune": b["tuning"]}
             del br
+        variants["adjoint"] = adjoint_cost(fc, torch, flush_buf)
         out["variants"] = variants
         out["cpu_baseline"] = cpu_baseline(synth.swirl(seed=0))
     if rank == 0:

@@ -88,7 +88,7 @@ def test_autograd_gradient_matches_oracle(dtype, tol):
     loss.backward()
     err_q = relerr(q.grad.double().cpu().numpy(), g_ref)
     err_s = abs(float(s.grad) - gs_ref) / abs(gs_ref)
-    print(f"{dtype}: loss {float(loss):.6e} vs {loss_ref:.6e}, grad q0 rel err {err_q:.2e}, "
+    print(f"{dtype}: loss {float(loss.detach()):.6e} vs {loss_ref:.6e}, grad q0 rel err {err_q:.2e}, "
           f"grad scale rel err {err_s:.2e}")
     assert err_q <= tol and err_s <= tol
 
@@ -108,9 +108,11 @@ def test_checkpoint_segments_give_the_same_gradient():
 
 
 def test_autograd_central_differences_fp64():
-    w, ref, q0, qt = _case(16, 4)
+    """The map is piecewise linear (limiter and interpolation slopes), so the
+    step must stay on one piece: smooth data and a small step."""
+    w, ref, q0, qt = _case(8, 4)
     F = fc.Forest(desc_for(fc, w, fc.F64), ref.leaves())
-    nsteps, dt = 6, 0.9 / 256
+    nsteps, dt = 4, 0.9 / 128
     qt_t = _tensor(qt, torch.float64)
 
     def L(q, s):
