@@ -240,7 +240,7 @@ def adjoint_cost(fc, torch, flush_buf, nsteps: int = 64):
     dt = w.cfl / (w.mx * 2 ** w.lmax)
     updates = nsteps * len(leaves) * w.mx * w.mx  # global steps: every patch every step
     times = {}
-    for name in ("forward", "forward+backward"):
+    for name in ("warm-up", "forward", "forward+backward"):
         q = q0.clone().requires_grad_(name != "forward")
         s = torch.ones((), dtype=torch.float32, device=dev, requires_grad=name != "forward")
         flush_buf.zero_()
