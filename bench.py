@@ -171,8 +171,9 @@ class Runner:
         self.F = fc.initial_forest(desc, q0_fn(workloads), lmax_f=self.lmax_f,
                                    tau_r=w.tau_refine, tau_c=w.tau_coarsen)
         # pick the patch-update kernel per launch size on this layout (untimed setup)
-        self.tuning = {int(b): {"variant": ["staged", "walk"][v], "warps": k, "ns": ns}
-                       for b, (v, k, ns) in self.F.autotune().items()}
+        self.tuning = {int(b): {"variant": ["staged", "walk"][v], "warps": k,
+                                "fill": "fused" if fu else "separate", "ns": ns}
+                       for b, (v, k, fu, ns) in self.F.autotune().items()}
         self.n = 0
 
     def updates(self) -> int:

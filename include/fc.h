@@ -212,12 +212,14 @@ fc_status fc_set_graphs(fc_forest* forest, int enable);
  * persistent grid of `warps`-warp CTAs -- fewest instructions per cell).
  *
  * fc_autotune times every candidate (staged; walk with 2, 4, 8 warps per
- * CTA) on each level's launch of the current layout and keeps the fastest
- * per launch size (sizes bucketed by powers of two; a bucket is tuned once
- * per forest).  It overwrites the previous-state buffers, so call it when
- * all levels hold the same time (after set_q or a regrid).  report: host,
- * nullable, 32 x 3 ints per bucket b (patches in [2^b, 2^(b+1))):
- * (variant or -1 if untuned, warps, ns per launch).  Synchronous.
+ * CTA; each with the level's ghosts filled inside the update kernel or by
+ * separate fill kernels) as a whole level substep of the current layout and
+ * keeps the fastest per launch size (sizes bucketed by powers of two; a
+ * bucket is tuned once per forest).  It overwrites the previous-state
+ * buffers, so call it when all levels hold the same time (after set_q or a
+ * regrid).  report: host, nullable, 32 x 4 ints per bucket b (patches in
+ * [2^b, 2^(b+1))): (variant or -1 if untuned, warps, fused, ns per substep).
+ * Synchronous.
  *
  * fc_set_advance_variant forces a variant for every launch (variant -1
  * restores the tuned/heuristic choice); warps is 2, 4 or 8. */

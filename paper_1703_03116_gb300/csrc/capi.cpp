@@ -101,6 +101,7 @@ struct fc_forest {
   struct Tune {
     bool tuned = false;
     int variant = ADV_STAGED, warps = 4;
+    int fused = 1;  // substep fills the level's ghosts inside the update kernel
     float us = 0.f;
   };
   Tune tune[32];
@@ -395,7 +396,9 @@ fc_status advance_level_t(fc_forest* F, int L, double t, double dt, cudaStream_t
   if (p1 > p0) {
     const double gb = ghost_bytes(F);
     AdvArgs a = adv_args(F, L, t, dt, p1 - p0);
-    if (F->fuse) {
+    const fc_forest::Tune& tn = F->tune[size_bucket(p1 - p0)];
+    const bool fused = F->fuse && (F->forced_variant >= 0 || !tn.tuned || tn.fused);
+    if (fused) {
       // coarse neighbours first (their interiors time-interpolated into qT,
       // their coarse ghost regions filled); the update kernel then fills
       // each level-L patch's ghost ring in shared memory itself
@@ -619,10 +622,28 @@ fc_status fc_autotune(fc_forest* F, int* report, void* stream) {
     if (t.tuned) continue;
     AdvArgs a = adv_args(F, L, 0.0, 0.5 * std::ldexp(1.0, -L) / H.desc.mx, p1 - p0);
     float best = 1e30f;
-    for (const auto& c : cand) {
+    // every candidate is timed as a whole substep: its fills plus the update
+    for (int c2 = 0; c2 < 2 * 4; ++c2) {
+      const auto& c = cand[c2 % 4];
+      const int fused = c2 / 4;
+      if (fused && !F->fuse) continue;
       a.variant = c.variant;
       a.warps = c.warps;
+      a.gather = fused;
+      a.tlevel = -1;
       auto run = [&]() {
+        cudaError_t e;
+        if (fused) {
+          FillArgs A{F->d_lists + F->off_t[L], (int)H.list_t[L].size(), -1, 0.0};
+          e = F->esize == 4 ? launch_fill_coarse(Df, A, s) : launch_fill_coarse(Dd, A, s);
+        } else {
+          FillArgs A{F->d_lists + F->off_a[L], (int)H.list_a[L].size(), -1, 0.0};
+          FillArgs B{F->d_lists + F->off_b[L], (int)H.list_b[L].size(), -1, 0.0};
+          e = F->esize == 4 ? launch_fill_coarse(Df, A, s) : launch_fill_coarse(Dd, A, s);
+          if (e == cudaSuccess)
+            e = F->esize == 4 ? launch_fill_fine(Df, B, s) : launch_fill_fine(Dd, B, s);
+        }
+        if (e != cudaSuccess) return e;
         return F->esize == 4 ? launch_advance(Df, p0, p1, a, F->d_err, s)
                              : launch_advance(Dd, p0, p1, a, F->d_err, s);
       };
@@ -644,6 +665,7 @@ fc_status fc_autotune(fc_forest* F, int* report, void* stream) {
         best = us;
         t.variant = c.variant;
         t.warps = c.warps;
+        t.fused = fused;
         t.us = us;
       }
     }
@@ -657,9 +679,10 @@ fc_status fc_autotune(fc_forest* F, int* report, void* stream) {
   destroy_graphs(F);
   if (report)
     for (int b = 0; b < 32; ++b) {
-      report[3 * b] = F->tune[b].tuned ? F->tune[b].variant : -1;
-      report[3 * b + 1] = F->tune[b].warps;
-      report[3 * b + 2] = (int)(1e3f * F->tune[b].us);
+      report[4 * b] = F->tune[b].tuned ? F->tune[b].variant : -1;
+      report[4 * b + 1] = F->tune[b].warps;
+      report[4 * b + 2] = F->tune[b].fused;
+      report[4 * b + 3] = (int)(1e3f * F->tune[b].us);
     }
   return check_device_error(F, s);
 }

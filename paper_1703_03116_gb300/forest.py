@@ -161,8 +161,8 @@ class Forest:
         return ch.value
 
     def autotune(self, stream=None) -> dict:
-        """Tune the patch-update kernel per launch size; returns {bucket: (variant, warps, ns)}."""
-        rep = np.zeros((32, 3), dtype=np.int32)
+        """Tune level substeps per launch size; returns {bucket: (variant, warps, fused, ns)}."""
+        rep = np.zeros((32, 4), dtype=np.int32)
         check(load().fc_autotune(self._h, _ip(rep), _stream(stream)))
         return {b: tuple(int(v) for v in rep[b]) for b in range(32) if rep[b, 0] >= 0}
 
