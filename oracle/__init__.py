@@ -18,11 +18,11 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SO = os.path.join(_HERE, "liboracle.so")
-_SRC = ["forest.c", "ghost.c", "claw.c", "drive.c", "adjoint.c"]
+_SRC = ["forest.c", "ghost.c", "claw.c", "drive.c", "adjoint.c", "sphere.c"]
 _HDR = ["oracle.h", "internal.h"]
 
 WALLS, PERIODIC, SPHERE = 0, 1, 2
-VEL_CONST, VEL_SWIRL = 0, 1
+VEL_CONST, VEL_SWIRL, VEL_ROTATION = 0, 1, 2
 
 
 def build(force: bool = False) -> str:
@@ -79,6 +79,8 @@ def lib():
                                     dp, dp]
     L.or_adjoint_step_global.argtypes = [vp, ctypes.c_double, ctypes.c_double, dp, dp]
     L.or_set_params.argtypes = [vp, ctypes.POINTER(_Params)]
+    L.or_sphere_centres.argtypes = [vp, dp]
+    L.or_get_kappa.argtypes = [vp, dp]
     L.or_single_grid_periodic.argtypes = [ctypes.POINTER(_Params), ctypes.c_int, dp,
                                           ctypes.c_double, ctypes.c_double, ctypes.c_int]
     L.or_mc_phi.restype = ctypes.c_double
@@ -118,6 +120,10 @@ def params(domain: int, mx: int, mbc: int, lmin: int, lmax: int, velocity,
     elif velocity[0] == "swirl":
         p.vel_kind = VEL_SWIRL
         p.vel[0] = float(velocity[1])
+    elif velocity[0] == "rotation":
+        p.vel_kind = VEL_ROTATION
+        for k in range(3):
+            p.vel[k] = float(velocity[1 + k])
     else:
         raise ValueError(velocity)
     p.order, p.limiter, p.transverse = order, limiter, transverse
@@ -125,9 +131,10 @@ def params(domain: int, mx: int, mbc: int, lmin: int, lmax: int, velocity,
     return p
 
 
-def uniform_leaves(level: int, nforests: int = 1) -> np.ndarray:
+def uniform_leaves(level: int, nforests: int = 1, nblocks: int = 1) -> np.ndarray:
     n = 1 << level
-    out = [(f, 0, level, x, y) for f in range(nforests) for y in range(n) for x in range(n)]
+    out = [(f, b, level, x, y) for f in range(nforests) for b in range(nblocks)
+           for y in range(n) for x in range(n)]
     return np.asarray(out, dtype=np.int32).reshape(-1, 5)
 
 
@@ -229,6 +236,18 @@ class Forest:
         _check(lib().or_adjoint_step_global(self.h, t, dt, _dptr(lam), _dptr(ds)))
         return lam, float(ds[0])
 
+    def sphere_centres(self) -> np.ndarray:
+        """Unit-sphere positions of the interior cell centres, (n, mx, mx, 3)."""
+        out = np.zeros((len(self), self.mx, self.mx, 3))
+        lib().or_sphere_centres(self.h, _dptr(out))
+        return out
+
+    def kappa(self) -> np.ndarray:
+        """Cell capacities (spherical areas) of the interior cells, (n, mx, mx)."""
+        out = np.zeros((len(self), self.mx, self.mx))
+        lib().or_get_kappa(self.h, _dptr(out))
+        return out
+
     def set_velocity_scale(self, s: float):
         """Scale every edge speed (the parameter of the velocity-scale gradient)."""
         self.prm.vel_scale = float(s)
@@ -278,13 +297,23 @@ def initial_forest(workloads, lmax: Optional[int] = None) -> Forest:
     nf = len(workloads)
     lmax_all = max(w.lmax for w in workloads) if lmax is None else lmax
     prm = params_for(w0, nforests=nf, lmax=lmax_all)
-    leaves = np.concatenate([uniform_leaves(w0.lmin) + np.array([f, 0, 0, 0, 0], np.int32)
+    sphere = w0.domain == "sphere"
+    nb = 6 if sphere else 1
+    leaves = np.concatenate([uniform_leaves(w0.lmin, 1, nb) + np.array([f, 0, 0, 0, 0], np.int32)
                              for f in range(nf)])
     F = Forest(prm, leaves)
     lmax_f = [w.lmax for w in workloads]
 
     def set_analytic():
         lv = F.leaves()
+        if sphere:
+            X = F.sphere_centres()
+            q = np.empty(X.shape[:3])
+            for f, w in enumerate(workloads):
+                sel = lv[:, 0] == f
+                q[sel] = synth.evaluate_sphere(w, X[sel])
+            F.set_q(q)
+            return
         x, y = synth.cell_centres(lv, w0.mx)
         q = np.empty(x.shape)
         for f, w in enumerate(workloads):

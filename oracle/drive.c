@@ -33,7 +33,12 @@ static double cell_h(const or_forest* F, int l) { return 1.0 / ldexp((double)F->
 
 static void advance_leaf(or_forest* F, int p, double t, double dt) {
   const or_leaf* a = &F->lv[p];
-  size_t S2 = (size_t)F->S * F->S;
+  size_t S2 = (size_t)F->S * F->S, S = (size_t)F->S;
+  if (F->P.domain == OR_SPHERE) {
+    or_claw_step_capacity(&F->P, F->q + p * S2, F->P.mx, F->P.mbc, dt, F->kappa + p * S2,
+                          F->phix + p * (S + 1) * S, F->phiy + p * S * (S + 1));
+    return;
+  }
   or_claw_step(&F->P, F->q + p * S2, F->P.mx, F->P.mbc, cell_h(F, a->l), dt, t,
                (long)a->x * F->P.mx, (long)a->y * F->P.mx);
 }
@@ -252,7 +257,15 @@ int or_regrid(or_forest* F, double tau_r, double tau_c, const int* lmax_f, int* 
         int fi = 2 * i - cx * mx, fj = 2 * j - cy * mx;
         double a0 = C[OR_IDX(F, fi, fj)], a1 = C[OR_IDX(F, fi + 1, fj)];
         double a2 = C[OR_IDX(F, fi, fj + 1)], a3 = C[OR_IDX(F, fi + 1, fj + 1)];
-        D[OR_IDX(F, i, j)] = 0.25 * (((a0 + a1) + a2) + a3);
+        if (F->P.domain == OR_SPHERE) { /* area-weighted, as the ghost average */
+          const double* K = F->kappa + ch[cx + 2 * cy] * S2;
+          double k0 = K[OR_IDX(F, fi, fj)], k1 = K[OR_IDX(F, fi + 1, fj)];
+          double k2 = K[OR_IDX(F, fi, fj + 1)], k3 = K[OR_IDX(F, fi + 1, fj + 1)];
+          D[OR_IDX(F, i, j)] =
+              (((k0 * a0 + k1 * a1) + k2 * a2) + k3 * a3) / (((k0 + k1) + k2) + k3);
+        } else {
+          D[OR_IDX(F, i, j)] = 0.25 * (((a0 + a1) + a2) + a3);
+        }
       }
   }
   if (status == 0) {
@@ -270,6 +283,7 @@ int or_regrid(or_forest* F, double tau_r, double tau_c, const int* lmax_f, int* 
     for (size_t c = 0; c < S2 * (size_t)nw.n; ++c) F->qold[c] = F->qT[c] = NAN;
     or_build_index(F);
     or_drop_cache(F);
+    or_update_metrics(F);
     if (changed) *changed = nchanged;
   } else {
     free(nw.a);
@@ -290,6 +304,13 @@ void or_mass(const or_forest* F, double* per_forest) {
   for (int f = 0; f < F->P.nforests; ++f) per_forest[f] = 0.0;
   for (int p = 0; p < F->n; ++p) {
     double h = cell_h(F, F->lv[p].l), s = 0.0;
+    if (F->P.domain == OR_SPHERE) { /* capacity-weighted: sum kappa q */
+      for (int j = 0; j < mx; ++j)
+        for (int i = 0; i < mx; ++i)
+          s += F->kappa[p * S2 + OR_IDX(F, i, j)] * F->q[p * S2 + OR_IDX(F, i, j)];
+      per_forest[F->lv[p].f] += s;
+      continue;
+    }
     for (int j = 0; j < mx; ++j)
       for (int i = 0; i < mx; ++i) s += F->q[p * S2 + OR_IDX(F, i, j)];
     per_forest[F->lv[p].f] += h * h * s;

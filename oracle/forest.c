@@ -96,8 +96,8 @@ int or_locate(const or_forest* F, int f, int* b, double* x, double* y) {
       *x -= floor(*x);
       *y -= floor(*y);
     } else {
-      or_set_error("sphere domain not supported by this oracle build");
-      return -4;
+      int r = or_sphere_fold(b, x, y);
+      if (r != 0) return r; /* -3: beyond a three-valent cube corner */
     }
   }
   for (int l = F->P.lmin; l <= F->P.lmax; ++l) {
@@ -114,7 +114,14 @@ int or_locate(const or_forest* F, int f, int* b, double* x, double* y) {
  * shifted by one block length in each direction. */
 int or_touch(const or_forest* F, const or_leaf* a, const or_leaf* c) {
   if (a->f != c->f) return 0;
-  if (F->P.domain == OR_SPHERE) return 0; /* not in this build */
+  if (F->P.domain == OR_SPHERE) { /* closed boxes on the cube surface */
+    long alo[3], ahi[3], clo[3], chi[3];
+    or_sphere_box(a, LFINE, alo, ahi);
+    or_sphere_box(c, LFINE, clo, chi);
+    for (int k = 0; k < 3; ++k)
+      if (alo[k] > chi[k] || clo[k] > ahi[k]) return 0;
+    return 1;
+  }
   long R = 1L << LFINE;
   long ax0 = (long)a->x << (LFINE - a->l), ax1 = (long)(a->x + 1) << (LFINE - a->l);
   long ay0 = (long)a->y << (LFINE - a->l), ay1 = (long)(a->y + 1) << (LFINE - a->l);
@@ -138,8 +145,8 @@ or_forest* or_create(const or_params* P, int n, const int* leaves) {
     or_set_error("bad level range");
     return NULL;
   }
-  if (P->domain == OR_SPHERE) {
-    or_set_error("sphere domain not supported by this oracle build");
+  if (P->domain == OR_SPHERE && P->vel_kind != OR_VEL_ROTATION) {
+    or_set_error("the sphere takes the solid-body rotation velocity");
     return NULL;
   }
   or_forest* F = (or_forest*)calloc(1, sizeof(or_forest));
@@ -159,12 +166,33 @@ or_forest* or_create(const or_params* P, int n, const int* leaves) {
   F->qold = (double*)malloc(sizeof(double) * (cells ? cells : 1));
   F->qT = (double*)malloc(sizeof(double) * (cells ? cells : 1));
   for (size_t c = 0; c < cells; ++c) F->q[c] = F->qold[c] = F->qT[c] = NAN;
+  or_update_metrics(F);
   return F;
+}
+
+void or_update_metrics(or_forest* F) {
+  free(F->kappa);
+  free(F->phix);
+  free(F->phiy);
+  F->kappa = F->phix = F->phiy = NULL;
+  if (F->P.domain != OR_SPHERE) return;
+  size_t S = (size_t)F->S, n = (size_t)(F->n > 0 ? F->n : 1);
+  F->kappa = (double*)malloc(sizeof(double) * n * S * S);
+  F->phix = (double*)malloc(sizeof(double) * n * (S + 1) * S);
+  F->phiy = (double*)malloc(sizeof(double) * n * S * (S + 1));
+  double scale = F->P.vel_scale != 0.0 ? F->P.vel_scale : 1.0;
+  double om[3] = {scale * F->P.vel[0], scale * F->P.vel[1], scale * F->P.vel[2]};
+  for (int p = 0; p < F->n; ++p)
+    or_sphere_metrics(&F->lv[p], F->P.mx, F->P.mbc, om, F->kappa + p * S * S,
+                      F->phix + p * (S + 1) * S, F->phiy + p * S * (S + 1));
 }
 
 void or_destroy(or_forest* F) {
   if (!F) return;
   or_drop_cache(F);
+  free(F->kappa);
+  free(F->phix);
+  free(F->phiy);
   free(F->lv);
   free(F->byKey);
   free(F->q);
@@ -175,7 +203,10 @@ void or_destroy(or_forest* F) {
 
 int or_num_leaves(const or_forest* F) { return F->n; }
 
-void or_set_params(or_forest* F, const or_params* P) { F->P.vel_scale = P->vel_scale; }
+void or_set_params(or_forest* F, const or_params* P) {
+  F->P.vel_scale = P->vel_scale;
+  or_update_metrics(F); /* sphere fluxes carry the scale */
+}
 
 void or_get_leaves(const or_forest* F, int* out) {
   for (int k = 0; k < F->n; ++k) {

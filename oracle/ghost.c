@@ -76,7 +76,9 @@ static double copy_value(const or_forest* F, const gmap* g, double* const* srcp)
   return cell_at(F, g->src, srcp[g->src], g->x, g->y);
 }
 
-/* Eq. ghost_coarse: mean of the four fine cells inside the coarse ghost cell */
+/* Eq. ghost_coarse: mean of the four fine cells inside the coarse ghost cell;
+ * on the sphere the mean is weighted by the cell areas (Sec. 2.5: cell areas
+ * are needed to average onto a coarse ghost region of a mapped grid) */
 static double average_value(const or_forest* F, const gmap* g, double* const* srcp) {
   const or_leaf* c = &F->lv[g->src];
   double hf = 1.0 / ldexp((double)F->P.mx, c->l);
@@ -85,8 +87,21 @@ static double average_value(const or_forest* F, const gmap* g, double* const* sr
   double a1 = cell_at(F, g->src, src, g->x + 0.5 * hf, g->y - 0.5 * hf);
   double a2 = cell_at(F, g->src, src, g->x - 0.5 * hf, g->y + 0.5 * hf);
   double a3 = cell_at(F, g->src, src, g->x + 0.5 * hf, g->y + 0.5 * hf);
+  if (F->P.domain == OR_SPHERE) {
+    const double* K = F->kappa + (size_t)g->src * F->S * F->S;
+    double k0 = cell_at(F, g->src, K, g->x - 0.5 * hf, g->y - 0.5 * hf);
+    double k1 = cell_at(F, g->src, K, g->x + 0.5 * hf, g->y - 0.5 * hf);
+    double k2 = cell_at(F, g->src, K, g->x - 0.5 * hf, g->y + 0.5 * hf);
+    double k3 = cell_at(F, g->src, K, g->x + 0.5 * hf, g->y + 0.5 * hf);
+    return (((k0 * a0 + k1 * a1) + k2 * a2) + k3 * a3) / (((k0 + k1) + k2) + k3);
+  }
   return 0.25 * (((a0 + a1) + a2) + a3);
 }
+
+/* Three-valent cube corner (no corner neighbour; a stated reading): the
+ * corner ghost cell takes the mean of the two edge ghosts that share its
+ * row and column next to the patch, once the edge ghosts are final. */
+static void corner3_fill(or_forest* F, const gmap* G, int p, double* Q);
 
 double or_minmod(double a, double b) {
   if (a * b <= 0.0) return 0.0;
@@ -224,6 +239,7 @@ int or_fill_all_snapshot(or_forest* F, double* snapshot) {
   for (int p = 0; p < F->n; ++p) fill_regions(F, G, p, cur[p], sp, REL_COARSE);
   /* phase 4 */
   for (int p = 0; p < F->n; ++p) apply_bc(F, p, cur[p]);
+  for (int p = 0; p < F->n; ++p) corner3_fill(F, G, p, cur[p]);
   if (snapshot) memcpy(snapshot, snap, sizeof(double) * S2 * F->n);
   free(sp);
   free(snap);
@@ -272,6 +288,21 @@ int or_fill_level(or_forest* F, int L, double alpha) {
     if (F->lv[p].l == L) fill_regions(F, G, p, srcp[p], srcp, REL_COARSE);
   for (int p = 0; p < F->n; ++p)
     if (F->lv[p].l == L) apply_bc(F, p, srcp[p]);
+  for (int p = 0; p < F->n; ++p)
+    if (F->lv[p].l == L - 1 || F->lv[p].l == L) corner3_fill(F, G, p, srcp[p]);
   free(srcp);
   return 0;
+}
+
+static void corner3_fill(or_forest* F, const gmap* G, int p, double* Q) {
+  if (F->P.domain != OR_SPHERE) return;
+  int ng = nghost(F), mx = F->P.mx, mbc = F->P.mbc, k = 0;
+  for (int j = -mbc; j < mx + mbc; ++j)
+    for (int i = -mbc; i < mx + mbc; ++i) {
+      if (!is_ghost(F, i, j)) continue;
+      const gmap* g = &G[(size_t)p * ng + k++];
+      if (g->rel != REL_CORNER3) continue;
+      int ic = i < 0 ? 0 : mx - 1, jc = j < 0 ? 0 : mx - 1;
+      Q[OR_IDX(F, i, j)] = 0.5 * (Q[OR_IDX(F, i, jc)] + Q[OR_IDX(F, ic, j)]);
+    }
 }

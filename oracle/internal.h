@@ -19,7 +19,22 @@ struct or_forest {
   double* qold;      /* state saved before a leaf's last advance (multirate) */
   double* qT;        /* time-interpolated coarse data (multirate) */
   void* gcache;      /* memoised ghost-cell holders of the current mesh */
+  /* cubed sphere: per-leaf metric terms over the extended index range */
+  double* kappa;     /* n * S * S cell capacities (spherical areas) */
+  double* phix;      /* n * (S+1) * S x-edge volume fluxes */
+  double* phiy;      /* n * S * (S+1) y-edge volume fluxes */
 };
+
+/* sphere.c */
+int or_sphere_fold(int* b, double* x, double* y);
+void or_sphere_box(const or_leaf* a, int LF, long lo[3], long hi[3]);
+void or_sphere_point(int b, double x, double y, double X[3]);
+void or_sphere_metrics(const or_leaf* a, int mx, int mbc, const double* omega, double* kappa,
+                       double* phix, double* phiy);
+void or_claw_step_capacity(const or_params* P, double* q, int mx, int mbc, double dt,
+                           const double* kappa, const double* phix, const double* phiy);
+/* (re)compute the metric terms of every leaf (sphere only) */
+void or_update_metrics(or_forest* F);
 
 /* relation of the leaf that holds a ghost cell to the ghost's owner */
 enum { REL_SAME = 0, REL_FINE = 1, REL_COARSE = -1, REL_EXTERIOR = -100,

@@ -23,7 +23,7 @@ extern "C" {
 #endif
 
 enum { OR_WALLS = 0, OR_PERIODIC = 1, OR_SPHERE = 2 };
-enum { OR_VEL_CONST = 0, OR_VEL_SWIRL = 1 };
+enum { OR_VEL_CONST = 0, OR_VEL_SWIRL = 1, OR_VEL_ROTATION = 2 /* sphere: vel[0..2] = omega */ };
 
 #define OR_MAXLEV 18
 
@@ -77,6 +77,11 @@ int or_adjoint_global(or_forest* F, int nsteps, double t0, double dt, const doub
  * state q^n, overwrite lam with the adjoint of q^n and add the step's
  * velocity-scale derivative to *dscale */
 int or_adjoint_step_global(or_forest* F, double t, double dt, double* lam, double* dscale);
+
+/* cubed sphere: unit-sphere positions of every interior cell centre
+ * (n x mx x mx x 3) and the cell capacities (n x mx x mx) */
+void or_sphere_centres(const or_forest* F, double* xyz);
+void or_get_kappa(const or_forest* F, double* kappa);
 
 /* one uniform periodic N x N grid, used to check the forest against it */
 int or_single_grid_periodic(const or_params* P, int N, double* q, double t0,

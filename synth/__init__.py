@@ -151,6 +151,62 @@ def adjoint_target(w: Workload, seed: int = 0, max_shift: float = 0.05) -> Workl
     return dataclasses.replace(w, parts=parts, name=w.name + " (target)")
 
 
+@dataclasses.dataclass
+class CosineBell:
+    centre: np.ndarray   # (3,) unit vector
+    radius: float = 0.5  # great-circle radius
+    height: float = 1.0
+
+
+@dataclasses.dataclass
+class SlottedCylinder:
+    centre: np.ndarray   # (3,) unit vector
+    along: np.ndarray    # (3,) unit tangent at the centre: direction the slot opens to
+    radius: float = 0.5
+    slot: float = 0.1    # slot width
+
+
+def _unit(v):
+    v = np.asarray(v, dtype=np.float64)
+    return v / np.linalg.norm(v)
+
+
+def sphere(seed: int = 0, lmin: int = 1, lmax: int = 7, mx: int = 32) -> Workload:
+    """Cubed-sphere workload: solid-body rotation about a seeded axis with
+    |omega| = 2 pi (one revolution in t = 1), two cosine bells (great-circle
+    radius 0.5, height 1) and a slotted cylinder (radius 0.5, slot width 0.1,
+    seeded orientation), centres seeded on the sphere."""
+    g = _rng(seed)
+    axis = _unit(g.normal(size=3))
+    omega = 2.0 * np.pi * axis
+    cs = [_unit(g.normal(size=3)) for _ in range(3)]
+    t = g.normal(size=3)
+    along = _unit(t - np.dot(t, cs[2]) * cs[2])
+    return Workload(
+        name=f"cubed sphere levels {lmin}-{lmax} mx={mx}", domain="sphere", mx=mx, mbc=2,
+        lmin=lmin, lmax=lmax, velocity=("rotation", *omega), limiter="mc", transverse=2,
+        cfl=0.9, parts=[CosineBell(cs[0]), CosineBell(cs[1]), SlottedCylinder(cs[2], along)],
+        t_final=1.0, regrid_every=4, seed=seed)
+
+
+def evaluate_sphere(w: Workload, X: np.ndarray) -> np.ndarray:
+    """Initial field of a sphere workload at unit vectors X (..., 3)."""
+    X = np.asarray(X, dtype=np.float64)
+    q = np.zeros(X.shape[:-1])
+    for p in w.parts:
+        r = np.arccos(np.clip(X @ p.centre, -1.0, 1.0))  # great-circle distance
+        if isinstance(p, CosineBell):
+            q = q + np.where(r < p.radius,
+                             0.5 * p.height * (1.0 + np.cos(np.pi * r / p.radius)), 0.0)
+        elif isinstance(p, SlottedCylinder):
+            side = np.cross(p.centre, p.along)
+            slot = (np.abs(X @ side) < 0.5 * p.slot) & (X @ p.along > -0.5 * p.radius)
+            q = q + ((r < p.radius) & ~slot).astype(np.float64)
+        else:
+            raise TypeError(type(p))
+    return q
+
+
 def evaluate(w: Workload, x: np.ndarray, y: np.ndarray) -> np.ndarray:
     """Initial field of workload ``w`` at points (x, y) (unit-square coords)."""
     x = np.asarray(x, dtype=np.float64)
@@ -211,7 +267,12 @@ def time_step(w: Workload, lmax: Optional[int] = None):
     """
     L = w.lmax if lmax is None else lmax
     h_f = 1.0 / (w.mx * 2 ** L)
-    if w.velocity[0] == "const":
+    if w.velocity[0] == "rotation":
+        # unit sphere: a block spans pi/2 radians; the smallest equiangular
+        # cell side is about 0.7 of the nominal one; speed <= |omega|
+        h_f = 0.7 * (np.pi / 2) / (w.mx * 2 ** L)
+        smax = float(np.linalg.norm(w.velocity[1:4]))
+    elif w.velocity[0] == "const":
         smax = max(abs(w.velocity[1]), abs(w.velocity[2]))
     else:
         smax = 1.0
