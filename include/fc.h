@@ -46,19 +46,35 @@ typedef enum {
 
 typedef enum { FC_F32 = 0, FC_F64 = 1 } fc_dtype;
 typedef enum { FC_DOMAIN_WALLS = 0, FC_DOMAIN_PERIODIC = 1, FC_DOMAIN_SPHERE = 2 } fc_domain;
-typedef enum { FC_VEL_CONST = 0, FC_VEL_SWIRL = 1 } fc_velocity;
+typedef enum { FC_VEL_CONST = 0, FC_VEL_SWIRL = 1, FC_VEL_ROTATION = 2 } fc_velocity;
 
 /* Problem description (Sec. 2; Sec. 5.1 "Problem setup").
  *   domain      unit square with walls, periodic unit square, or cubed sphere.
  *   nforests    independent forests in one store (a batched ensemble); each
- *               forest of a square domain is one block.
+ *               forest of a square domain is one block, each forest of the
+ *               cubed sphere six blocks (Sec. 2.4): block b is the face of
+ *               the cube [-1,1]^3 with outward normal n and block point
+ *               (x, y) in [0,1]^2 at n + (2x-1) ex + (2y-1) ey, with
+ *               (n; ex, ey) = 0: (+Z; +X, +Y), 1: (-Z; +X, -Y),
+ *               2: (+X; +Y, +Z), 3: (-X; -Y, +Z), 4: (+Y; -X, +Z),
+ *               5: (-Y; +X, +Z); the grid is equiangular gnomonic (cube
+ *               point n + tan((x-1/2) pi/2) ex + tan((y-1/2) pi/2) ey,
+ *               projected onto the unit sphere).
  *   mx, mbc     interior cells per side (power of two, 8..64) and ghost layers
  *               (Proposition 1 requires mbc <= mx/4; only mbc = 2 is built).
  *   lmin, lmax  level range; a level-l leaf has edge 2^-l of its block.
  *   dtype       FC_F32 or FC_F64 for the stored field and the update.
  *   vel_kind    FC_VEL_CONST: (u, v) = (vel[0], vel[1]);
  *               FC_VEL_SWIRL: streamfunction sin^2(pi x) sin^2(pi y)
- *               cos(pi t / T) / pi with T = vel[0].
+ *               cos(pi t / T) / pi with T = vel[0];
+ *               FC_VEL_ROTATION (sphere only): solid-body rotation
+ *               u = omega x X, omega = (vel[0], vel[1], vel[2]).  The sphere
+ *               runs the capacity form: FP64 metrics per patch (cell
+ *               areas kappa, edge volume fluxes omega . (X_b - X_a) between
+ *               the edge's end points), ghost-cell metrics from the patch's
+ *               own mapping, area-weighted fine-to-coarse averages, and
+ *               corner ghosts beyond a cube vertex set to the mean of the
+ *               two edge ghosts next to them.
  *   order       1 (first order) or 2 (second-order wave corrections).
  *   limiter     0 unlimited, 1 MC.
  *   transverse  0 none, 1 fluctuations, 2 fluctuations and corrections. */
@@ -140,8 +156,8 @@ fc_status fc_tag(fc_forest* forest, double* delta_host, void* stream);
 fc_status fc_set_velocity_scale(fc_forest* forest, double scale);
 
 /* Adjoint of one global time step (the transposes of Alg. 1 and of the
- * wave-propagation update; BASELINE's differentiation pattern, no counterpart
- * in the paper).  The forest must hold q^n, the state at the start of the
+ * wave-propagation update; an extension for differentiation, with no
+ * counterpart in the paper; square domains only).  The forest must hold q^n, the state at the start of the
  * step (it is not advanced).  With the step's map q^{n+1} = S(Fill(q^n)),
  *   lam     device, in/out, field layout: on entry dL/dq^{n+1}, on return
  *           dL/dq^n = (dq^{n+1}/dq^n)^T lam, using the piece of the MC
@@ -154,7 +170,8 @@ fc_status fc_set_velocity_scale(fc_forest* forest, double scale);
 fc_status fc_adjoint_step_global(fc_forest* forest, double t, double dt, void* lam,
                                  double* dscale, void* stream);
 
-/* Total mass per forest, sum over leaves of h^2 sum(q), accumulated in FP64
+/* Total mass per forest, sum over leaves of h^2 sum(q) (on the sphere
+ * sum(kappa q)), accumulated in FP64
  * on the device in a fixed order.  out: host, nforests doubles.  Synchronous. */
 fc_status fc_forest_mass(const fc_forest* forest, double* out, void* stream);
 
@@ -167,7 +184,8 @@ fc_status fc_forest_mass(const fc_forest* forest, double* out, void* stream);
  * a valid leaf list.  out: host, nleaves * 8 rows of 6 ints
  *   (kind, n0, n1, a, fx, fy)
  * in the leaves' field order, regions (-x, +x, -y, +y, (-,-), (+,-), (-,+),
- * (+,+)); kind 0 exterior, 1 same size, 2 finer, 3 coarser; n0/n1 are field
+ * (+,+)); kind 0 exterior, 1 same size, 2 finer, 3 coarser, 4 corner
+ * region beyond a vertex of the cubed sphere (no neighbour); n0/n1 are field
  * indices of the neighbour leaves; (a, fx, fy) encode Eq. (transform)
  * I' = A I + F on level-l global cell indices (a: bit 0 swaps axes, bits 1
  * and 2 negate the first and second output).

@@ -115,10 +115,15 @@ void or_sphere_point(int b, double x, double y, double X[3]) {
   for (int k = 0; k < 3; ++k) X[k] = P[k] / l;
 }
 
-/* area of the spherical triangle (a, b, c) (Van Oosterom & Strackee) */
+/* area of the spherical triangle (a, b, c) (Van Oosterom & Strackee).  The
+ * triple product a . (b x c) equals a . ((b - a) x (c - a)); the second form
+ * keeps its relative accuracy for small triangles (the first cancels from
+ * O(1) terms down to O(h^2)). */
 static double tri_area(const double* a, const double* b, const double* c) {
-  double bc[3] = {b[1] * c[2] - b[2] * c[1], b[2] * c[0] - b[0] * c[2], b[0] * c[1] - b[1] * c[0]};
-  double num = fabs(dot3(a, bc));
+  double u[3] = {b[0] - a[0], b[1] - a[1], b[2] - a[2]};
+  double v[3] = {c[0] - a[0], c[1] - a[1], c[2] - a[2]};
+  double uv[3] = {u[1] * v[2] - u[2] * v[1], u[2] * v[0] - u[0] * v[2], u[0] * v[1] - u[1] * v[0]};
+  double num = fabs(dot3(a, uv));
   double den = 1.0 + dot3(a, b) + dot3(b, c) + dot3(c, a);
   return 2.0 * atan2(num, den);
 }

@@ -13,6 +13,14 @@
 // arrays; final edge fluxes are formed in a second pass; each interior cell
 // then reads its four fluxes.  Every thread works on every phase, so a patch
 // finishes quickly -- the better choice when a launch has few patches.
+//
+// Capacity form (CAP, the cubed sphere, Sec. 5.3): the patch's FP64 metric
+// block arrives by a second bulk copy.  Edge speeds become edge volume fluxes
+// phi, and every 1/h becomes 1/kappa of the cell concerned: the correction
+// 1/2 |phi| (1 - dt |phi| (1/kappa_L + 1/kappa_R)/2) phi(theta) W, the
+// transverse increments 1/2 dt/kappa_cell phi^-+ (fluctuation entering that
+// cell), and the update Q -= dt/kappa (F(i+1/2) - F(i-1/2) + G(j+1/2) -
+// G(j-1/2)).
 #include <cstdint>
 
 #include "ghost_gather.cuh"
@@ -31,17 +39,20 @@ __device__ __forceinline__ real correction(int order, int limiter, real s, real 
 
 // x-edge (i,j) lies between cells (i-1,j) and (i,j): i in [0,MX], j in [-1,MX]
 // y-edge (i,j) lies between cells (i,j-1) and (i,j): j in [0,MX], i in [-1,MX]
-template <typename real, int MX, int NT>
+template <typename real, int MX, int NT, bool CAP>
 __global__ void __launch_bounds__(NT) advance_staged_kernel(DevForest<real> D, int p0, int p1,
                                                             AdvArgs a, int* err) {
   constexpr int S = MX + 4;
   constexpr int NE = (MX + 1) * (MX + 2);
   constexpr int NV = MX + 3;  // corner nodes -1..MX+1
+  constexpr int MS = CAP ? metric_stride(S) : 0;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t bar;
   __shared__ real ucoef_s;
   __shared__ NbrStage st;
-  real* Q = reinterpret_cast<real*>(smem_raw);
+  // capacity form: kappa, phi_x, phi_y of the patch (MS doubles) come first
+  const double* Ms = reinterpret_cast<const double*>(smem_raw);
+  real* Q = reinterpret_cast<real*>(smem_raw + sizeof(double) * MS);
   real* Fn = Q + S * S;
   real* XP = Fn + NE;
   real* XM = XP + NE;
@@ -53,10 +64,12 @@ __global__ void __launch_bounds__(NT) advance_staged_kernel(DevForest<real> D, i
   real* Tx = Sy + NV;
   real* Ty = Tx + NV;
   const int order = D.order, limiter = D.limiter, transverse = D.transverse;
-  const bool swirl = D.vel_kind == FC_VEL_SWIRL;
+  const bool swirl = !CAP && D.vel_kind == FC_VEL_SWIRL;
   const real cu = real(D.vel[0]), cv = real(D.vel[1]);
   const real nu = real(a.nu), half_nu = real(0.5 * a.nu), h = real(a.h);
   constexpr uint32_t bytes = sizeof(real) * S * S;
+  constexpr uint32_t mbytes = sizeof(double) * MS;
+  const real dt = real(a.dt), half_dt = real(0.5 * a.dt);
 
   if (threadIdx.x == 0) {
     mbar_init(&bar, 1);
@@ -74,8 +87,9 @@ __global__ void __launch_bounds__(NT) advance_staged_kernel(DevForest<real> D, i
     real* dst = D.buf[D.cur[pm.level] ^ 1] + (size_t)p * S * S;
     if (threadIdx.x == 0) {
       fence_proxy_async();
-      mbar_expect_tx(&bar, bytes);
+      mbar_expect_tx(&bar, bytes + mbytes);
       bulk_load(Q, src, bytes, &bar);
+      if (CAP) bulk_load(smem_raw, D.metric + (size_t)p * MS, mbytes, &bar);
     }
     if (a.gather) stage_neighbours(D.meta, D.nbr, p, st, threadIdx.x);
     // streamfunction tables while the tile is in flight:
@@ -103,8 +117,23 @@ __global__ void __launch_bounds__(NT) advance_staged_kernel(DevForest<real> D, i
       fill_patch_ghosts<real, MX>(D, st, pm, a.tlevel, real(a.alpha), Q, threadIdx.x, NT,
                                   []() { __syncthreads(); });
     auto q = [&](int i, int j) -> real { return Q[(j + 2) * S + (i + 2)]; };
-    auto uvel = [&](int i, int j) -> real { return swirl ? ucoef * Sx[i + 1] * Ty[j + 1] : cu; };
-    auto vvel = [&](int i, int j) -> real { return swirl ? -ucoef * Sy[j + 1] * Tx[i + 1] : cv; };
+    // capacity form: kappa of cell (i,j), flux through x-edge / y-edge (i,j)
+    auto kap = [&](int i, int j) -> real { return real(Ms[(j + 2) * S + (i + 2)]); };
+    auto uvel = [&](int i, int j) -> real {
+      if (CAP) return real(Ms[S * S + (j + 2) * (S + 1) + (i + 2)]);
+      return swirl ? ucoef * Sx[i + 1] * Ty[j + 1] : cu;
+    };
+    auto vvel = [&](int i, int j) -> real {
+      if (CAP) return real(Ms[S * S + S * (S + 1) + (j + 2) * S + (i + 2)]);
+      return swirl ? -ucoef * Sy[j + 1] * Tx[i + 1] : cv;
+    };
+    // dt |phi| (1/kappa_L + 1/kappa_R)/2 = nu_e |phi| in the correction
+    auto nu_x = [&](int i, int j) -> real {
+      return CAP ? dt * (real(0.5) * (real(1) / kap(i - 1, j) + real(1) / kap(i, j))) : nu;
+    };
+    auto nu_y = [&](int i, int j) -> real {
+      return CAP ? dt * (real(0.5) * (real(1) / kap(i, j - 1) + real(1) / kap(i, j))) : nu;
+    };
     // both sweeps: normal flux and fluctuations of every edge
     for (int e = threadIdx.x; e < 2 * NE; e += NT) {
       if (e < NE) {
@@ -114,7 +143,7 @@ __global__ void __launch_bounds__(NT) advance_staged_kernel(DevForest<real> D, i
         const real qm = q(i - 1, j), q0 = q(i, j);
         const real W = q0 - qm;
         const real Wup = s >= real(0) ? qm - q(i - 2, j) : q(i + 1, j) - q0;
-        const real Ft = correction(order, limiter, s, W, Wup, nu);
+        const real Ft = correction(order, limiter, s, W, Wup, nu_x(i, j));
         Fn[e] = sp * qm + sm * q0 + Ft;
         XP[e] = transverse > 1 ? sp * W - Ft : sp * W;
         XM[e] = transverse > 1 ? sm * W + Ft : sm * W;
@@ -126,7 +155,7 @@ __global__ void __launch_bounds__(NT) advance_staged_kernel(DevForest<real> D, i
         const real qm = q(i, j - 1), q0 = q(i, j);
         const real W = q0 - qm;
         const real Wup = s >= real(0) ? qm - q(i, j - 2) : q(i, j + 1) - q0;
-        const real Gt = correction(order, limiter, s, W, Wup, nu);
+        const real Gt = correction(order, limiter, s, W, Wup, nu_y(i, j));
         Gn[f] = sp * qm + sm * q0 + Gt;
         YP[f] = transverse > 1 ? sp * W - Gt : sp * W;
         YM[f] = transverse > 1 ? sm * W + Gt : sm * W;
@@ -144,7 +173,10 @@ __global__ void __launch_bounds__(NT) advance_staged_kernel(DevForest<real> D, i
           const real sp = s > real(0) ? s : real(0), sm = s < real(0) ? s : real(0);
           const real yl = YP[ye(i - 1, j)] + YM[ye(i - 1, j + 1)];  // into cell (i-1,j)
           const real yr = YP[ye(i, j)] + YM[ye(i, j + 1)];          // into cell (i,j)
-          Fn[xe(i, j)] -= half_nu * (sp * yl + sm * yr);
+          if (CAP)
+            Fn[xe(i, j)] -= half_dt * (sp * yl / kap(i - 1, j) + sm * yr / kap(i, j));
+          else
+            Fn[xe(i, j)] -= half_nu * (sp * yl + sm * yr);
         } else {  // y-edges j in [0,MX], interior columns
           const int f = e - MX * (MX + 1);
           const int i = f % MX, j = f / MX;
@@ -152,40 +184,56 @@ __global__ void __launch_bounds__(NT) advance_staged_kernel(DevForest<real> D, i
           const real sp = s > real(0) ? s : real(0), sm = s < real(0) ? s : real(0);
           const real xb = XP[xe(i, j - 1)] + XM[xe(i + 1, j - 1)];  // into cell (i,j-1)
           const real xt = XP[xe(i, j)] + XM[xe(i + 1, j)];          // into cell (i,j)
-          Gn[ye(i, j)] -= half_nu * (sp * xb + sm * xt);
+          if (CAP)
+            Gn[ye(i, j)] -= half_dt * (sp * xb / kap(i, j - 1) + sm * xt / kap(i, j));
+          else
+            Gn[ye(i, j)] -= half_nu * (sp * xb + sm * xt);
         }
       }
       __syncthreads();
     }
     for (int k = threadIdx.x; k < MX * MX; k += NT) {
       const int i = k % MX, j = k / MX;
-      const real v = q(i, j) - nu * (Fn[xe(i + 1, j)] - Fn[xe(i, j)]) -
-                     nu * (Gn[ye(i, j + 1)] - Gn[ye(i, j)]);
+      real v;
+      if (CAP)
+        v = q(i, j) - dt / kap(i, j) *
+                          ((Fn[xe(i + 1, j)] - Fn[xe(i, j)]) + (Gn[ye(i, j + 1)] - Gn[ye(i, j)]));
+      else
+        v = q(i, j) - nu * (Fn[xe(i + 1, j)] - Fn[xe(i, j)]) -
+            nu * (Gn[ye(i, j + 1)] - Gn[ye(i, j)]);
       dst[(j + 2) * S + (i + 2)] = v;
     }
     __syncthreads();
   }
 }
 
-template <typename real, int MX>
+template <typename real, int MX, bool CAP>
 constexpr size_t staged_smem() {
-  return sizeof(real) * (size_t)((MX + 4) * (MX + 4) + 6 * (MX + 1) * (MX + 2) + 4 * (MX + 3));
+  return sizeof(double) * (size_t)(CAP ? metric_stride(MX + 4) : 0) +
+         sizeof(real) * (size_t)((MX + 4) * (MX + 4) + 6 * (MX + 1) * (MX + 2) + 4 * (MX + 3));
+}
+
+template <typename real, int MX, int NT, bool CAP>
+cudaError_t staged_launch_t(const DevForest<real>& D, int p0, int p1, const AdvArgs& a, int* err,
+                            cudaStream_t s) {
+  static bool attr_set = false;
+  constexpr size_t smem = staged_smem<real, MX, CAP>();
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(advance_staged_kernel<real, MX, NT, CAP>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  advance_staged_kernel<real, MX, NT, CAP><<<p1 - p0, NT, smem, s>>>(D, p0, p1, a, err);
+  ++launch_counter();
+  return cudaGetLastError();
 }
 
 template <typename real, int MX, int NT>
 cudaError_t staged_launch(const DevForest<real>& D, int p0, int p1, const AdvArgs& a, int* err,
                           cudaStream_t s) {
-  static bool attr_set = false;
-  constexpr size_t smem = staged_smem<real, MX>();
-  if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(advance_staged_kernel<real, MX, NT>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    attr_set = true;
-  }
-  advance_staged_kernel<real, MX, NT><<<p1 - p0, NT, smem, s>>>(D, p0, p1, a, err);
-  ++launch_counter();
-  return cudaGetLastError();
+  if (D.metric) return staged_launch_t<real, MX, NT, true>(D, p0, p1, a, err, s);
+  return staged_launch_t<real, MX, NT, false>(D, p0, p1, a, err, s);
 }
 
 template <typename real>
@@ -205,7 +253,8 @@ template <typename real>
 cudaError_t launch_advance(const DevForest<real>& D, int p0, int p1, const AdvArgs& a, int* err,
                            cudaStream_t s) {
   if (p1 <= p0) return cudaSuccess;
-  if (a.variant == ADV_WALK) return launch_advance_walk(D, p0, p1, a, err, s);
+  // the walk variant has no capacity form: mapped grids always run staged
+  if (a.variant == ADV_WALK && !D.metric) return launch_advance_walk(D, p0, p1, a, err, s);
   return launch_advance_staged(D, p0, p1, a, err, s);
 }
 

@@ -1,7 +1,8 @@
 // Auxiliary kernels: tagging (Sec. 3.1 indicator), FP64 mass sums, field
 // packing between the store and the caller's layout, and the regrid remap
 // (copy, Eq. ghost_fine interpolation into new children, Eq. ghost_coarse
-// averaging into new parents).
+// averaging into new parents).  On the cubed sphere mass is sum(kappa q) and
+// new parents take the area-weighted mean of their children.
 #include <cmath>
 
 #include "device_util.cuh"
@@ -51,8 +52,16 @@ __global__ void patch_sum_kernel(DevForest<real> D, double* sums) {
     const PatchMeta pm = D.meta[p];
     const real* Q = D.buf[D.cur[pm.level]] + (size_t)p * S * S;
     double s = 0.0;
-    for (int k = threadIdx.x; k < mx * mx; k += blockDim.x)
-      s += (double)Q[(k / mx + 2) * S + k % mx + 2];
+    if (D.metric) {  // mapped grid: sum of kappa q
+      const double* K = D.metric + (size_t)p * metric_stride(S);
+      for (int k = threadIdx.x; k < mx * mx; k += blockDim.x) {
+        const int o = (k / mx + 2) * S + k % mx + 2;
+        s += K[o] * (double)Q[o];
+      }
+    } else {
+      for (int k = threadIdx.x; k < mx * mx; k += blockDim.x)
+        s += (double)Q[(k / mx + 2) * S + k % mx + 2];
+    }
     red[threadIdx.x] = s;
     __syncthreads();
     for (int w = blockDim.x / 2; w > 0; w >>= 1) {
@@ -61,7 +70,7 @@ __global__ void patch_sum_kernel(DevForest<real> D, double* sums) {
     }
     if (threadIdx.x == 0) {
       const double h = ldexp(1.0, -pm.level) / mx;
-      sums[p] = h * h * red[0];
+      sums[p] = D.metric ? red[0] : h * h * red[0];
     }
     __syncthreads();
   }
@@ -142,8 +151,18 @@ __global__ void remap_kernel(DevForest<real> Old, DevForest<real> New, const Rem
         const int s = e.src[cx + 2 * cy];
         const real* C = Old.buf[Old.cur[Old.meta[s].level]] + (size_t)s * S * S;
         const int fi = 2 * i - cx * mx + 2, fj = 2 * j - cy * mx + 2;
-        v = real(0.25) * (((C[fj * S + fi] + C[fj * S + fi + 1]) + C[(fj + 1) * S + fi]) +
-                          C[(fj + 1) * S + fi + 1]);
+        if (Old.metric) {  // mapped grid: area-weighted, as the ghost average
+          const double* K = Old.metric + (size_t)s * metric_stride(S);
+          const double k0 = K[fj * S + fi], k1 = K[fj * S + fi + 1];
+          const double k2 = K[(fj + 1) * S + fi], k3 = K[(fj + 1) * S + fi + 1];
+          v = real((((k0 * double(C[fj * S + fi]) + k1 * double(C[fj * S + fi + 1])) +
+                     k2 * double(C[(fj + 1) * S + fi])) +
+                    k3 * double(C[(fj + 1) * S + fi + 1])) /
+                   (((k0 + k1) + k2) + k3));
+        } else {
+          v = real(0.25) * (((C[fj * S + fi] + C[fj * S + fi + 1]) + C[(fj + 1) * S + fi]) +
+                            C[(fj + 1) * S + fi + 1]);
+        }
       }
       Dq[(j + 2) * S + i + 2] = v;
     }

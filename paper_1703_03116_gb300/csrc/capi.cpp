@@ -107,6 +107,7 @@ struct fc_forest {
   Tune tune[32];
   int forced_variant = -1, forced_warps = 4;
   double vel_scale = 1.0;                 // multiplies every edge speed
+  double* d_metric = nullptr;             // cubed sphere: FP64 metric blocks per patch
   void* lam[2] = {nullptr, nullptr};      // adjoint tiles (patch-store layout), lazily allocated
   cudaStream_t cap_stream = nullptr;
   double* d_t0 = nullptr;  // start time of the replayed coarse step
@@ -193,6 +194,24 @@ void free_device(fc_forest* F) {
   dfree(F->d_t0);
   dfree(F->lam[0]);
   dfree(F->lam[1]);
+  dfree(F->d_metric);
+}
+
+// cubed sphere: (re)compute the metric blocks of the current layout for the
+// rotation vector times the velocity scale (synchronous)
+fc_status update_metrics(fc_forest* F) {
+  const HostForest& H = F->host;
+  if (H.desc.domain != FC_DOMAIN_SPHERE) return FC_OK;
+  const int n = H.npatch();
+  const int S = H.desc.mx + 2 * kMbc;
+  dfree(F->d_metric);
+  if (dmalloc(&F->d_metric, (size_t)n * metric_stride(S)) != cudaSuccess)
+    return fail(FC_ERR_OOM, "metric allocation failed");
+  const double w[3] = {F->vel_scale * H.desc.vel[0], F->vel_scale * H.desc.vel[1],
+                       F->vel_scale * H.desc.vel[2]};
+  FC_CUDA(launch_sphere_metrics(F->d_meta, n, H.desc.mx, w, F->d_metric, 0));
+  FC_CUDA(cudaStreamSynchronize(0));
+  return FC_OK;
 }
 
 // upload tables (and allocate a store) for the current host layout
@@ -259,7 +278,7 @@ fc_status upload(fc_forest* F, bool alloc_store) {
     FC_CUDA(dmalloc(&F->d_t0, 1));
     FC_CUDA(cudaMemset(F->d_t0, 0, sizeof(double)));
   }
-  return FC_OK;
+  return update_metrics(F);
 }
 
 template <typename real>
@@ -272,6 +291,7 @@ DevForest<real> dev(const fc_forest* F) {
   D.domain = H.desc.domain;
   D.meta = F->d_meta;
   D.nbr = F->d_nbr;
+  D.metric = F->d_metric;
   D.buf[0] = static_cast<real*>(F->buf[0]);
   D.buf[1] = static_cast<real*>(F->buf[1]);
   D.qT = static_cast<real*>(F->qT);
@@ -297,6 +317,7 @@ AdvArgs adv_args(const fc_forest* F, int L, double t, double dt, int n) {
   AdvArgs a{};
   a.h = std::ldexp(1.0, -L) / d.mx;
   a.nu = dt / a.h;
+  a.dt = dt;
   a.period = d.vel[0];
   a.sfac = d.vel_kind == FC_VEL_SWIRL ? F->vel_scale * std::sin(M_PI * a.h) / (M_PI * a.h) : 0.0;
   a.t_half = t + 0.5 * dt;
@@ -356,7 +377,10 @@ double ghost_bytes(const fc_forest* F) {
 // algorithmic bytes of advancing n patches: read (mx+4)^2, write mx^2 each
 double advance_bytes(const fc_forest* F, int n) {
   const double mx = F->host.desc.mx;
-  return (double)n * ((mx + 4) * (mx + 4) + mx * mx) * (double)F->esize;
+  // read the patch with its ghosts, write the interior; a mapped grid also
+  // reads its FP64 metric block
+  const double metric = F->d_metric ? 8.0 * metric_stride(F->host.desc.mx + 2 * kMbc) : 0.0;
+  return (double)n * (((mx + 4) * (mx + 4) + mx * mx) * (double)F->esize + metric);
 }
 
 template <typename real>
@@ -467,10 +491,14 @@ fc_status check_desc(const fc_forest_desc* d) {
     return fail(FC_ERR_INVALID_ARG, "level range must satisfy 0 <= lmin <= lmax <= 16");
   if (d->nforests < 1 || d->nforests > 65535) return fail(FC_ERR_INVALID_ARG, "bad nforests");
   if (d->dtype != FC_F32 && d->dtype != FC_F64) return fail(FC_ERR_INVALID_ARG, "bad dtype");
-  if (d->domain != FC_DOMAIN_WALLS && d->domain != FC_DOMAIN_PERIODIC)
-    return fail(FC_ERR_INVALID_ARG, "domain not supported by this build");
-  if (d->vel_kind != FC_VEL_CONST && d->vel_kind != FC_VEL_SWIRL)
+  if (d->domain != FC_DOMAIN_WALLS && d->domain != FC_DOMAIN_PERIODIC &&
+      d->domain != FC_DOMAIN_SPHERE)
+    return fail(FC_ERR_INVALID_ARG, "bad domain");
+  if (d->vel_kind != FC_VEL_CONST && d->vel_kind != FC_VEL_SWIRL &&
+      d->vel_kind != FC_VEL_ROTATION)
     return fail(FC_ERR_INVALID_ARG, "bad velocity kind");
+  if ((d->domain == FC_DOMAIN_SPHERE) != (d->vel_kind == FC_VEL_ROTATION))
+    return fail(FC_ERR_INVALID_ARG, "the cubed sphere takes the solid-body rotation, and only it");
   if (d->vel_kind == FC_VEL_SWIRL && !(d->vel[0] != 0.0))
     return fail(FC_ERR_INVALID_ARG, "swirl period must be nonzero");
   if (d->order < 1 || d->order > 2 || d->limiter < 0 || d->limiter > 1 || d->transverse < 0 ||
@@ -627,6 +655,7 @@ fc_status fc_autotune(fc_forest* F, int* report, void* stream) {
       const auto& c = cand[c2 % 4];
       const int fused = c2 / 4;
       if (fused && !F->fuse) continue;
+      if (c.variant == ADV_WALK && F->d_metric) continue;  // no capacity form in walk
       a.variant = c.variant;
       a.warps = c.warps;
       a.gather = fused;
@@ -691,7 +720,8 @@ fc_status fc_set_velocity_scale(fc_forest* F, double scale) {
   if (!F || !(scale == scale)) return fail(FC_ERR_INVALID_ARG, "bad velocity scale");
   F->vel_scale = scale;
   destroy_graphs(F);
-  return FC_OK;
+  FC_CUDA(cudaDeviceSynchronize());  // no launch may still read the old metrics
+  return update_metrics(F);           // sphere: the edge fluxes carry the scale
 }
 
 }  // extern "C"
@@ -738,6 +768,8 @@ fc_status fc_adjoint_step_global(fc_forest* F, double t, double dt, void* lam, d
                                  void* stream) {
   if (!F || !lam || !dscale) return fail(FC_ERR_INVALID_ARG, "null argument");
   if (!(dt > 0.0)) return fail(FC_ERR_INVALID_ARG, "dt must be positive");
+  if (F->host.desc.domain == FC_DOMAIN_SPHERE)
+    return fail(FC_ERR_INVALID_ARG, "the adjoint is built for the square domains");
   cudaStream_t s = as_stream(stream);
   return F->esize == 4 ? adjoint_step_t<float>(F, t, dt, lam, dscale, s)
                        : adjoint_step_t<double>(F, t, dt, lam, dscale, s);
@@ -967,6 +999,7 @@ fc_status fc_tag_regrid(fc_forest* F, double tau_refine, double tau_coarsen,
   if (!G) return fail(FC_ERR_OOM, "host allocation failed");
   G->host.desc = F->host.desc;
   G->esize = F->esize;
+  G->vel_scale = F->vel_scale;  // the sphere's metrics carry it
   G->host.leaves = nl;
   err = G->host.build();
   if (!err.empty()) {
@@ -1053,6 +1086,7 @@ fc_status fc_tag_regrid(fc_forest* F, double tau_refine, double tau_coarsen,
   F->d_remap = G->d_remap;
   F->d_err = G->d_err;
   F->d_t0 = G->d_t0;
+  F->d_metric = G->d_metric;
   for (int l = 0; l <= kMaxLevel; ++l) F->cur[l] = 0;
   reset_times(F);
   delete G;  // its device pointers now belong to F

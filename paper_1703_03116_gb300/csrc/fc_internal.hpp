@@ -19,8 +19,10 @@ constexpr int kMbc = 2;  // ghost layers built into the kernels
 
 // Neighbour relation of one face or corner region of a patch (Sec. 2.2):
 // same-size neighbour (copy), finer neighbour(s) (average), coarser neighbour
-// (interpolate), or outside the physical domain (boundary condition).
-enum NbrKind : int { NB_EXTERIOR = 0, NB_SAME = 1, NB_FINE = 2, NB_COARSE = 3 };
+// (interpolate), outside the physical domain (boundary condition), or the
+// corner region beyond a cube vertex of the cubed sphere, where only three
+// blocks meet and no block holds the diagonal cells (Sec. 2.4).
+enum NbrKind : int { NB_EXTERIOR = 0, NB_SAME = 1, NB_FINE = 2, NB_COARSE = 3, NB_CORNER3 = 4 };
 
 // Region order: faces -x, +x, -y, +y, then corners (-,-), (+,-), (-,+), (+,+).
 constexpr int kDirX[8] = {-1, 1, 0, 0, -1, 1, -1, 1};
@@ -30,6 +32,13 @@ constexpr int kDirY[8] = {0, 0, -1, 1, -1, -1, 1, 1};
 // global cell index I into the neighbour block's level-l global index I'.
 // A is a signed permutation: bit 0 swaps the axes, bits 1 and 2 negate the
 // first and second output component.
+inline void apply_code_host(int a, int x, int y, int* u, int* v) {
+  *u = (a & 1) ? y : x;
+  *v = (a & 1) ? x : y;
+  if (a & 2) *u = -*u;
+  if (a & 4) *v = -*v;
+}
+
 struct NbrEntry {
   int kind;
   int n0, n1;  // device patch indices; n1 only for a face with two fine patches
@@ -93,9 +102,32 @@ void sort_leaves(std::vector<Leaf>* v);
 
 // ---------------------------------------------------------------- device side
 
+// Cubed-sphere metric block of one patch, FP64 over the extended index range
+// (cells -2..mx+1): capacity kappa[S*S] (spherical cell area), then the
+// volume flux of the velocity field through every x-edge, phix[S*(S+1)]
+// (edge i-1/2 of row j at j*(S+1) + i, shifted by 2), then through every
+// y-edge, phiy[(S+1)*S] (edge j-1/2 of column i at j*S + i, shifted by 2).
+__host__ __device__ constexpr int metric_stride(int S) { return S * S + 2 * S * (S + 1); }
+
+// Cubed sphere (FC_DOMAIN_SPHERE): block b is the face of the cube [-1,1]^3
+// with outward normal n; its block coordinates (x, y) in [0,1]^2 sit at
+// n + (2x - 1) ex + (2y - 1) ey.  Axes are signed codes: +-1, +-2, +-3 for
+// +-X, +-Y, +-Z.  (The block numbering is part of the C ABI.)
+__host__ __device__ inline void cube_face(int b, int* n, int* ex, int* ey) {
+  switch (b) {
+    case 0: *n = 3; *ex = 1; *ey = 2; break;     // +Z
+    case 1: *n = -3; *ex = 1; *ey = -2; break;   // -Z
+    case 2: *n = 1; *ex = 2; *ey = 3; break;     // +X
+    case 3: *n = -1; *ex = -2; *ey = 3; break;   // -X
+    case 4: *n = 2; *ex = -1; *ey = 3; break;    // +Y
+    default: *n = -2; *ex = 1; *ey = 3; break;   // -Y
+  }
+}
+
 template <typename real>
 struct DevForest {
   int mx, S, npatch, domain;
+  const double* metric;  // cubed sphere: metric_stride(S) doubles per patch; else null
   const PatchMeta* meta;
   const NbrEntry* nbr;
   real* buf[2];
@@ -120,6 +152,7 @@ struct FillArgs {
 // step's start time lives in device memory, the offset is baked in).
 struct AdvArgs {
   double h, nu, sfac, period, t_half, t_off;
+  double dt;  // time step (capacity form: dt / kappa per cell)
   const double* t0_dev;
   int variant;  // ADV_STAGED or ADV_WALK
   int warps;    // walk variant: warps per CTA
@@ -181,6 +214,13 @@ cudaError_t launch_remap(const DevForest<real>& Old, const DevForest<real>& New,
                          const RemapEntry* rm, cudaStream_t s);
 
 uint64_t& launch_counter();
+
+// Cubed-sphere metric blocks of patches [0, npatch) for the solid-body
+// rotation omega (already scaled): equiangular gnomonic mapping of each
+// face, capacities from two spherical triangles per cell, edge fluxes from
+// the stream function -omega . X (Sec. 5.3 mapped grids).
+cudaError_t launch_sphere_metrics(const PatchMeta* meta, int npatch, int mx, const double* omega,
+                                  double* metric, cudaStream_t s);
 
 // fc_mass_noalloc's kernels (scratch in a file-scope device array)
 cudaError_t noalloc_mass(const void* q, int dtype, int mx, int nleaves, const int* level,

@@ -7,6 +7,8 @@
 //   alpha q_new (multirate: the coarse data a finer level interpolates from).
 // fill_fine: phases 3-4 -- interpolation from the coarser neighbour, then
 //   the boundary condition again.
+// On the cubed sphere the corner ghosts beyond a cube vertex are set last,
+// by whichever kernel finishes the patch's edge ghosts.
 //
 // The rules themselves live in ghost_gather.cuh, shared with the patch-update
 // kernels, which apply them to the tile they hold in shared memory.
@@ -43,6 +45,10 @@ __global__ void __launch_bounds__(256) fill_coarse_kernel(DevForest<real> D, Fil
       __syncthreads();
       wall_bc<real, MX>(pm, Q, threadIdx.x, blockDim.x);
     }
+    if (D.domain == FC_DOMAIN_SPHERE && !(pm.flags & 1)) {  // edge ghosts are final
+      __syncthreads();
+      corner3_fill<real, MX>(st, Q, threadIdx.x, blockDim.x);
+    }
     __syncthreads();
   }
 }
@@ -66,6 +72,10 @@ __global__ void __launch_bounds__(256) fill_fine_kernel(DevForest<real> D, FillA
     if (D.domain == FC_DOMAIN_WALLS) {
       __syncthreads();
       wall_bc<real, MX>(pm, Q, threadIdx.x, blockDim.x);
+    }
+    if (D.domain == FC_DOMAIN_SPHERE) {
+      __syncthreads();
+      corner3_fill<real, MX>(st, Q, threadIdx.x, blockDim.x);
     }
     __syncthreads();
   }

@@ -47,12 +47,93 @@ static int nblocks(const fc_forest_desc& d) { return d.domain == FC_DOMAIN_SPHER
 
 namespace {
 
+// ------------------------------------------------------------ cubed sphere
+//
+// Folding across a cube edge in index space (Sec. 2.4).  At resolution M
+// cells per block side, cell I has the doubled cube coordinate
+// U = 2I + 1 - M in (-M, M); M times the cell centre on the face plane is
+// M n + U ex + V ey.  A cell beyond the +ex side (U > M) overshoots by
+// O = U - M; it is carried over the edge onto the face whose normal is ex,
+// at depth O below the edge: M ex + V ey + (M - O) n.  Its doubled
+// coordinates there are the components along that face's axes.
+
+int axis_comp(int code, int k) {  // component k of the signed axis `code`
+  return (code == k + 1) ? 1 : (code == -(k + 1)) ? -1 : 0;
+}
+
+int face_with_normal(int code) {
+  for (int c = 0; c < 6; ++c) {
+    int n, ex, ey;
+    cube_face(c, &n, &ex, &ey);
+    if (n == code) return c;
+  }
+  return -1;
+}
+
+// Map cell (I, J) of face b across its side `side` (0: -x, 1: +x, 2: -y,
+// 3: +y) at resolution M, without checking that (I, J) lies beyond it; the
+// map is affine in (I, J).
+void fold_side(int b, int side, long M, long I, long J, int* c, long* Ic, long* Jc) {
+  int n, ex, ey;
+  cube_face(b, &n, &ex, &ey);
+  const long U = 2 * I + 1 - M, V = 2 * J + 1 - M;
+  long P[3];
+  for (int k = 0; k < 3; ++k) {
+    const long en = axis_comp(n, k), e1 = axis_comp(ex, k), e2 = axis_comp(ey, k);
+    if (side < 2) {
+      const long s = side == 0 ? -1 : 1;  // crossing direction s ex
+      const long O = s * U - M;
+      P[k] = M * s * e1 + V * e2 + (M - O) * en;
+    } else {
+      const long s = side == 2 ? -1 : 1;
+      const long O = s * V - M;
+      P[k] = M * s * e2 + U * e1 + (M - O) * en;
+    }
+  }
+  const int dir = side < 2 ? (side == 0 ? -ex : ex) : (side == 2 ? -ey : ey);
+  *c = face_with_normal(dir);
+  int cn, cex, cey;
+  cube_face(*c, &cn, &cex, &cey);
+  long Uc = 0, Vc = 0;
+  for (int k = 0; k < 3; ++k) {
+    Uc += P[k] * axis_comp(cex, k);
+    Vc += P[k] * axis_comp(cey, k);
+  }
+  *Ic = (Uc + M - 1) / 2;
+  *Jc = (Vc + M - 1) / 2;
+}
+
+// the transform I' = A I + F of side `side` of face b at resolution M
+void side_transform(int b, int side, long M, int* a, int* fx, int* fy) {
+  const long I0 = side == 0 ? -1 : (side == 1 ? M : 0);
+  const long J0 = side == 2 ? -1 : (side == 3 ? M : 0);
+  int c;
+  long x0, y0, x1, y1, x2, y2;
+  fold_side(b, side, M, I0, J0, &c, &x0, &y0);
+  fold_side(b, side, M, I0 + 1, J0, &c, &x1, &y1);
+  fold_side(b, side, M, I0, J0 + 1, &c, &x2, &y2);
+  const long a11 = x1 - x0, a21 = y1 - y0, a12 = x2 - x0, a22 = y2 - y0;
+  int code;
+  if (a11 == 0)  // axes swapped: u = +-J, v = +-I
+    code = 1 | (a12 < 0 ? 2 : 0) | (a21 < 0 ? 4 : 0);
+  else
+    code = (a11 < 0 ? 2 : 0) | (a22 < 0 ? 4 : 0);
+  int u, v;
+  apply_code_host(code, (int)I0, (int)J0, &u, &v);
+  *a = code;
+  *fx = (int)(x0 - u);
+  *fy = (int)(y0 - v);
+}
+
 // Where does quadrant (b, l, x, y) of a forest lie once moved across the
 // block boundary?  For the square domains the neighbour lies in the same
-// block (periodic) or outside the domain (walls).  Returns false for the
-// exterior.  *fx, *fy: shift of level-l cell indices into the new frame.
+// block (periodic) or outside the domain (walls); on the cubed sphere it is
+// folded across the cube edge.  Returns false for the exterior and beyond a
+// cube vertex (then corner3 is set).  (a, fx, fy): the transform of level-l
+// cell indices into the new block's frame.
 struct Moved {
   int b, x, y, a, fx, fy;
+  bool corner3;
 };
 
 bool move_quadrant(const fc_forest_desc& d, int b, int l, int x, int y, int mx, Moved* m) {
@@ -63,6 +144,7 @@ bool move_quadrant(const fc_forest_desc& d, int b, int l, int x, int y, int mx, 
   m->a = 0;
   m->fx = 0;
   m->fy = 0;
+  m->corner3 = false;
   if (x >= 0 && x < N && y >= 0 && y < N) return true;
   if (d.domain == FC_DOMAIN_WALLS) return false;
   if (d.domain == FC_DOMAIN_PERIODIC) {
@@ -72,7 +154,20 @@ bool move_quadrant(const fc_forest_desc& d, int b, int l, int x, int y, int mx, 
     if (y >= N) { m->y = y - N; m->fy = -N * mx; }
     return true;
   }
-  return false;  // cubed sphere: not in this build
+  // cubed sphere: one coordinate out -> fold across that cube edge; both out
+  // -> beyond a cube vertex
+  const bool ox = x < 0 || x >= N, oy = y < 0 || y >= N;
+  if (ox && oy) {
+    m->corner3 = true;
+    return false;
+  }
+  const int side = ox ? (x < 0 ? 0 : 1) : (y < 0 ? 2 : 3);
+  long X, Y;
+  fold_side(b, side, N, x, y, &m->b, &X, &Y);
+  m->x = (int)X;
+  m->y = (int)Y;
+  side_transform(b, side, (long)N * mx, &m->a, &m->fx, &m->fy);
+  return true;
 }
 
 }  // namespace
@@ -142,8 +237,11 @@ std::string HostForest::build() {
             e.n0 = dev_of[c];
             meta[p].flags |= 1;
           } else {
-            // finer: the children of the same-size quadrant that touch this patch
-            const int ox = kDirX[dir], oy = kDirY[dir];
+            // finer: the children of the same-size quadrant that touch this
+            // patch, on its side facing back along the direction of travel
+            // (expressed in the neighbour block's frame)
+            int ox, oy;
+            apply_code_host(m.a, kDirX[dir], kDirY[dir], &ox, &oy);
             int cx[2], cy[2], nc;
             if (ox != 0 && oy != 0) {
               nc = 1;
@@ -177,6 +275,8 @@ std::string HostForest::build() {
             e.n1 = nc == 2 ? dev_of[ids[1]] : -1;
           }
         }
+      } else if (m.corner3) {
+        e.kind = NB_CORNER3;
       }
       nbr[(size_t)p * 8 + dir] = e;
     }

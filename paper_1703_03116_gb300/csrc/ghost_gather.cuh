@@ -73,11 +73,17 @@ __device__ __forceinline__ bool copy_or_average(const DevForest<real>& D, const 
     ly = 2 * gy - nm->y * MX;
     if (lx < 0 || lx >= MX || ly < 0 || ly >= MX) return false;
   }
+  // the four fine cells, in the neighbour's frame: (0,0), (1,0), (0,1), (1,1)
   real s[4];
 #pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    const int2 d = apply_a(e.a, (q & 1) ? 1 : -1, (q & 2) ? 1 : -1);
-    s[q] = src_interior(D, tlevel, alpha, n, nm->level, lx + (d.x > 0), ly + (d.y > 0));
+  for (int q = 0; q < 4; ++q)
+    s[q] = src_interior(D, tlevel, alpha, n, nm->level, lx + (q & 1), ly + (q >> 1));
+  if (D.metric) {  // mapped grid: weighted by the fine cells' areas
+    const double* K = D.metric + (size_t)n * metric_stride(D.S) + (ly + kMbc) * D.S + lx + kMbc;
+    const double k0 = K[0], k1 = K[1], k2 = K[D.S], k3 = K[D.S + 1];
+    v = real((((k0 * double(s[0]) + k1 * double(s[1])) + k2 * double(s[2])) + k3 * double(s[3])) /
+             (((k0 + k1) + k2) + k3));
+    return true;
   }
   v = real(0.25) * (((s[0] + s[1]) + s[2]) + s[3]);
   return true;
@@ -126,6 +132,25 @@ __device__ __forceinline__ void wall_bc(const PatchMeta& pm, real* Q, int tid, i
   }
 }
 
+// Cubed sphere, corner regions beyond a cube vertex (no block holds them; a
+// stated reading of Sec. 2.4): each of the 2 x 2 corner ghosts takes the mean
+// of the two edge ghosts in its row and column next to the patch, once the
+// edge ghosts are final.  Threads tid, stride nt.
+template <typename real, int MX>
+__device__ __forceinline__ void corner3_fill(const NbrStage& st, real* Q, int tid, int nt) {
+  constexpr int S = MX + 4;
+  for (int k = tid; k < 16; k += nt) {
+    const int r = 4 + (k >> 2);
+    if (st.e[r].kind != NB_CORNER3) continue;
+    // corners (-,-), (+,-), (-,+), (+,+)
+    const int i = (r & 1) ? MX + (k & 1) : -2 + (k & 1);
+    const int j = (r & 2) ? MX + ((k >> 1) & 1) : -2 + ((k >> 1) & 1);
+    const int ic = i < 0 ? 0 : MX - 1, jc = j < 0 ? 0 : MX - 1;
+    Q[(j + kMbc) * S + i + kMbc] =
+        real(0.5) * (Q[(jc + kMbc) * S + i + kMbc] + Q[(j + kMbc) * S + ic + kMbc]);
+  }
+}
+
 // The whole of Alg. 1 for one patch into array Q (shared or global):
 // copy/average, boundary condition, interpolation, boundary condition.
 // `sync` orders the phases across the cooperating threads.
@@ -154,6 +179,10 @@ __device__ __forceinline__ void fill_patch_ghosts(const DevForest<real>& D, cons
   sync();
   if (walls) wall_bc<real, MX>(pm, Q, tid, nt);
   sync();
+  if (D.domain == FC_DOMAIN_SPHERE) {
+    corner3_fill<real, MX>(st, Q, tid, nt);
+    sync();
+  }
 }
 
 }  // namespace fc

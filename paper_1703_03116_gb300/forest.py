@@ -24,6 +24,10 @@ def make_desc(domain: int = _lib.WALLS, mx: int = 32, lmin: int = 2, lmax: int =
     elif velocity[0] == "swirl":
         d.vel_kind = _lib.VEL_SWIRL
         d.vel[0] = float(velocity[1])
+    elif velocity[0] == "rotation":
+        d.vel_kind = _lib.VEL_ROTATION
+        for k in range(3):
+            d.vel[k] = float(velocity[1 + k])
     else:
         raise ValueError(f"unknown velocity {velocity!r}")
     d.order, d.limiter, d.transverse = order, limiter, transverse
@@ -228,7 +232,7 @@ def layout_check(desc: Desc, leaves) -> None:
 
 def layout_neighbours(desc: Desc, leaves) -> np.ndarray:
     leaves = _iarr(leaves).reshape(-1, 5)
-    out = np.zeros((len(leaves), 8, 6), dtype=np.int32)
+    out = np.zeros((len(leaves), 8, 6), dtype=np.int32)  # kind 4: beyond a cube vertex
     check(load().fc_layout_neighbours(ctypes.byref(desc), len(leaves), _ip(leaves), _ip(out)))
     return out
 

@@ -9,7 +9,8 @@ F64_TOL = 1e-12   # FP64 path: max |gpu - oracle| / max |oracle|
 
 def desc_for(fc, w, dtype, nforests=1, lmax=None):
     order, lim = {"none": (2, 0), "lw": (2, 0), "mc": (2, 1), "first": (1, 0)}[w.limiter]
-    return fc.make_desc(domain={"walls": fc.WALLS, "periodic": fc.PERIODIC}[w.domain], mx=w.mx,
+    domain = {"walls": fc.WALLS, "periodic": fc.PERIODIC, "sphere": fc.SPHERE}[w.domain]
+    return fc.make_desc(domain=domain, mx=w.mx,
                         lmin=w.lmin, lmax=w.lmax if lmax is None else lmax, dtype=dtype,
                         velocity=w.velocity, order=order, limiter=lim,
                         transverse=w.transverse, nforests=nforests)
