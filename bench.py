@@ -41,6 +41,9 @@ METRIC = "cell-updates/s"
 L2_FLUSH_BYTES = 512 << 20
 WORKLOAD = ("adaptive swirl forest, levels 2-6, 32x32 patches, mbc 2, walls, MC + transverse, "
             "CFL 0.9, multirate, regrid every 4 coarse steps")
+SPHERE_WORKLOAD = ("cubed sphere (6 trees), levels 1-7, 32x32 patches, mbc 2, solid-body rotation "
+                   "|omega| = 2 pi, two cosine bells + slotted cylinder, capacity form, CFL 0.9, "
+                   "multirate, regrid every 4 coarse steps")
 
 
 def parse():
@@ -52,7 +55,7 @@ def parse():
     ap.add_argument("--dtype", choices=["f32", "f64"], default="f32")
     ap.add_argument("--no-variants", action="store_true", help="skip FP64, batched and CPU legs")
     ap.add_argument("--ensemble", type=int, default=256, help="forests in the batched variant")
-    ap.add_argument("--mode", choices=["full", "batched"], default="full",
+    ap.add_argument("--mode", choices=["full", "batched", "sphere"], default="full",
                     help="batched: time only the ensemble (a case sized for profiling)")
     return ap.parse_args()
 
@@ -70,8 +73,12 @@ def q0_fn(workloads):
         out = np.empty((len(leaves), mx, mx))
         for f in np.unique(leaves[:, 0]):
             sel = leaves[:, 0] == f
-            x, y = synth.cell_centres(leaves[sel], mx)
-            out[sel] = synth.evaluate(workloads[int(f)], x, y)
+            w = workloads[int(f)]
+            if w.domain == "sphere":
+                out[sel] = synth.evaluate_sphere(w, synth.sphere_cell_centres(leaves[sel], mx))
+            else:
+                x, y = synth.cell_centres(leaves[sel], mx)
+                out[sel] = synth.evaluate(w, x, y)
         return out
     return q0
 
@@ -166,7 +173,8 @@ class Runner:
         self.lmax = max(x.lmax for x in workloads)
         self.lmax_f = [x.lmax for x in workloads]
         _, self.dtc = synth.time_step(w, self.lmax)
-        desc = fc.make_desc(domain=fc.WALLS, mx=w.mx, lmin=w.lmin, lmax=self.lmax, dtype=dtype,
+        domain = {"walls": fc.WALLS, "periodic": fc.PERIODIC, "sphere": fc.SPHERE}[w.domain]
+        desc = fc.make_desc(domain=domain, mx=w.mx, lmin=w.lmin, lmax=self.lmax, dtype=dtype,
                             velocity=w.velocity, nforests=len(workloads))
         self.F = fc.initial_forest(desc, q0_fn(workloads), lmax_f=self.lmax_f,
                                    tau_r=w.tau_refine, tau_c=w.tau_coarsen)
@@ -197,6 +205,7 @@ def measure(runner, steps, warmup, flush_buf, clock_index):
     fc.launch_count(reset=True)
     events, updates = [], 0
     with Clocks(clock_index) as clk:
+        torch.cuda.nvtx.range_push("timed_steps")  # lets a profiler select the timed region
         for _ in range(steps):
             flush_buf.zero_()  # a write larger than L2 between timed steps (untimed)
             updates += runner.updates()
@@ -206,6 +215,7 @@ def measure(runner, steps, warmup, flush_buf, clock_index):
             runner.step()
             e1.record()
             events.append((e0, e1))
+        torch.cuda.nvtx.range_pop()
         torch.cuda.synchronize()
     launches = fc.launch_count()
     ms = sum(a.elapsed_time(b) for a, b in events)
@@ -288,16 +298,21 @@ def run_ours(args):
     hbm = hbm or 6800.0
 
     dtype = fc.F32 if args.dtype == "f32" else fc.F64
-    if args.mode == "batched":
-        ws = synth.ensemble(args.ensemble, seed=rank, mx=32)
+    if args.mode in ("batched", "sphere"):
+        if args.mode == "batched":
+            ws = synth.ensemble(args.ensemble, seed=rank, mx=32)
+            label = (f"{args.ensemble} independent swirl forests, levels 2 to 4/5/6, "
+                     "32x32 patches")
+        else:
+            ws = [synth.sphere(seed=rank)]
+            label = SPHERE_WORKLOAD
         b = measure(Runner(fc, torch, ws, dtype), args.steps, args.warmup, flush_buf, local)
         line = {"metric": METRIC, "value": reduce(float(b["updates"]), SUM) /
                 (reduce(b["ms"], MAX) * 1e-3), "unit": METRIC, "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": b["ms"] / args.steps,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                 "dtype": args.dtype, "data": "synthetic",
-                "config": {"workload": f"{args.ensemble} independent swirl forests, levels 2 to "
-                                       "4/5/6, 32x32 patches", "patches": b["patches"]},
+                "config": {"workload": label, "patches": b["patches"]},
                 "gpu_launches": b["launches"], "clocks": b["clocks"],
                 "roofline": roofline_of(b["phases"]["advance"], hbm, peak_src),
                 "phases_ms": {k: x[0] for k, x in b["phases"].items()}, "autotune": b["tuning"]}
@@ -386,6 +401,17 @@ def run_ours(args):
                 "phases_ms": {k: x[0] for k, x in b["phases"].items()},
                 "gpu_launches": b["launches"], "clocks": b["clocks"], "autotune": b["tuning"]}
             del br
+        sr = Runner(fc, torch, [synth.sphere(seed=0)], fc.F32)
+        nsteps = 8
+        sv = measure(sr, nsteps, 2, flush_buf, local)
+        variants["sphere"] = {
+            "workload": SPHERE_WORKLOAD, "dtype": "f32 field and update, f64 metrics and mass",
+            "patches": sv["patches"], "value": sv["updates"] / (sv["ms"] * 1e-3),
+            "ms_per_step": sv["ms"] / nsteps, "steps": nsteps,
+            "roofline": roofline_of(sv["phases"]["advance"], hbm, peak_src),
+            "phases_ms": {k: x[0] for k, x in sv["phases"].items()},
+            "gpu_launches": sv["launches"], "clocks": sv["clocks"]}
+        del sr
         variants["adjoint"] = adjoint_cost(fc, torch, flush_buf)
         out["variants"] = variants
         out["cpu_baseline"] = cpu_baseline(synth.swirl(seed=0))

@@ -157,8 +157,34 @@ class Timed {
   size_t idx_ = 0;
 };
 
+// add one timed launch to its phase's totals (waits for its end event)
+cudaError_t account_pair(fc_forest* F, const fc_forest::TimerPair& p) {
+  cudaError_t e = cudaEventSynchronize(p.b);
+  float t = 0.f;
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&t, p.a, p.b);
+  if (e != cudaSuccess) return e;
+  fc_forest::PhaseTotal& T = F->ph[p.phase];
+  T.ms += t;
+  T.bytes += p.bytes;
+  T.launches += 1;
+  return cudaSuccess;
+}
+
+// a replayed graph's event pairs hold only its latest replay: they are read
+// before the graph is replayed again or destroyed
+cudaError_t account_graph(fc_forest* F, fc_forest::Graph& g) {
+  if (!g.replayed) return cudaSuccess;
+  g.replayed = false;
+  for (const auto& p : g.pairs) {
+    cudaError_t e = account_pair(F, p);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
 void destroy_graphs(fc_forest* F) {
   for (auto& g : F->graphs) {
+    account_graph(F, g);
     if (g.exec) cudaGraphExecDestroy(g.exec);
     for (auto& p : g.pairs) F->spare.push_back(p);
   }
@@ -570,31 +596,12 @@ fc_status fc_timers_enable(fc_forest* F, int enable) {
 fc_status fc_timers_read(fc_forest* F, int phase, double* ms, int64_t* launches, double* bytes,
                          int reset) {
   if (!F || phase < 0 || phase > 3) return fail(FC_ERR_INVALID_ARG, "bad phase");
-  auto account = [&](const fc_forest::TimerPair& p) -> fc_status {
-    FC_CUDA(cudaEventSynchronize(p.b));
-    float t = 0.f;
-    FC_CUDA(cudaEventElapsedTime(&t, p.a, p.b));
-    fc_forest::PhaseTotal& T = F->ph[p.phase];
-    T.ms += t;
-    T.bytes += p.bytes;
-    T.launches += 1;
-    return FC_OK;
-  };
   for (const auto& p : F->pending) {
-    fc_status st = account(p);
-    if (st != FC_OK) return st;
+    FC_CUDA(account_pair(F, p));
     F->spare.push_back(p);
   }
   F->pending.clear();
-  // a replayed graph re-records its own pairs: they hold its latest replay
-  for (auto& g : F->graphs) {
-    if (!g.replayed) continue;
-    for (const auto& p : g.pairs) {
-      fc_status st = account(p);
-      if (st != FC_OK) return st;
-    }
-    g.replayed = false;
-  }
+  for (auto& g : F->graphs) FC_CUDA(account_graph(F, g));
   fc_forest::PhaseTotal& T = F->ph[phase];
   if (ms) *ms = T.ms;
   if (launches) *launches = T.launches;
@@ -936,6 +943,7 @@ fc_status fc_step_multirate(fc_forest* F, double t, double dt_coarse, void* stre
     F->graphs.push_back(std::move(ng));
     g = &F->graphs.back();
   }
+  FC_CUDA(account_graph(F, *g));  // its pairs are about to be re-recorded
   FC_CUDA(launch_set_time(F->d_t0, t, s));
   FC_CUDA(cudaGraphLaunch(g->exec, s));
   launch_counter() += g->kernels;

@@ -238,6 +238,27 @@ def evaluate(w: Workload, x: np.ndarray, y: np.ndarray) -> np.ndarray:
     return q
 
 
+# cubed-sphere block convention of the C interface: block b is the cube face
+# with outward normal n, block point (x, y) at n + (2x-1) ex + (2y-1) ey
+_CUBE = {0: ((0, 0, 1), (1, 0, 0), (0, 1, 0)), 1: ((0, 0, -1), (1, 0, 0), (0, -1, 0)),
+         2: ((1, 0, 0), (0, 1, 0), (0, 0, 1)), 3: ((-1, 0, 0), (0, -1, 0), (0, 0, 1)),
+         4: ((0, 1, 0), (-1, 0, 0), (0, 0, 1)), 5: ((0, -1, 0), (1, 0, 0), (0, 0, 1))}
+
+
+def sphere_cell_centres(leaves: np.ndarray, mx: int) -> np.ndarray:
+    """Unit-sphere positions (n, mx, mx, 3) of the cell centres of cubed-sphere
+    leaves (equiangular gnomonic grid on each face), where the initial field
+    is evaluated."""
+    leaves = np.asarray(leaves)
+    x, y = cell_centres(leaves, mx)
+    ta = np.tan((x - 0.5) * np.pi / 2)[..., None]
+    tb = np.tan((y - 0.5) * np.pi / 2)[..., None]
+    frames = np.array([_CUBE[int(b)] for b in leaves[:, 1]], dtype=np.float64)  # (n, 3, 3)
+    P = (frames[:, None, None, 0, :] + ta * frames[:, None, None, 1, :]
+         + tb * frames[:, None, None, 2, :])
+    return P / np.linalg.norm(P, axis=-1, keepdims=True)
+
+
 def cell_centres(leaves: np.ndarray, mx: int):
     """Cell-centre coordinates of every interior cell of every leaf.
 

@@ -256,6 +256,25 @@ def test_timers_count_replayed_launches():
         assert launches == substeps and ms > 0 and nbytes > 0, (n, launches, substeps, nlev)
 
 
+def test_timers_count_every_replay_across_regrids():
+    """Several replays of the same graphs between reads, and a regrid (which
+    drops the graphs) in between: every advance launch is counted once."""
+    w = synth.swirl(6, lmin=2, lmax=4, mx=16)
+    _, dtc = synth.time_step(w)
+    _, gpu = pair(fc, w, fc.F32)
+    gpu.step_multirate(0.0, dtc)  # capture outside the timed region
+    gpu.timers(True)
+    gpu.read_timer(0, reset=True)
+    expect = 0
+    for n in range(1, 9):
+        expect += sum(1 << (l - 2) for l in set(gpu.leaves()[:, 2]))
+        gpu.step_multirate(n * dtc, dtc)
+        if n % 4 == 0:
+            gpu.tag_regrid(w.tau_refine, w.tau_coarsen)
+    ms, launches, nbytes = gpu.read_timer(0, reset=True)
+    assert launches == expect and ms > 0 and nbytes > 0
+
+
 @pytest.mark.parametrize("variant,warps", [(0, 4), (1, 2), (1, 4), (1, 8)])
 @pytest.mark.parametrize("mx", [8, 16, 32])
 def test_advance_variants_match_oracle(variant, warps, mx):

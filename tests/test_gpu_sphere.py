@@ -148,3 +148,26 @@ def test_adjoint_is_refused_on_the_sphere():
     ds = torch.zeros(1, dtype=torch.float64, device="cuda")
     with pytest.raises(fc.FcError):
         gpu.adjoint_step_global(0.0, 1e-3, lam, ds)
+
+
+def test_full_size_sphere_one_coarse_step():
+    """The benchmark's sphere workload (levels 1-7, 32^2 patches) for one
+    coarse multirate step (64 finest-level substeps) plus a regrid, compared
+    everywhere with the oracle."""
+    w = synth.sphere(0)
+    _, dtc = synth.time_step(w)
+    for dtype, tol in ((fc.F64, F64_TOL), (fc.F32, 2e-4)):
+        ref, gpu = pair(fc, w, dtype)
+        assert ref.leaves()[:, 2].max() == 7
+        ref.step_multirate(0.0, dtc)
+        gpu.step_multirate(0.0, dtc)
+        err = relerr(gpu.get_q(), ref.get_q())
+        m_gpu, m_ref = gpu.mass()[0], ref.mass()[0]
+        print(f"full-size sphere dtype {dtype}: {len(ref)} patches, rel err {err:.2e}, "
+              f"mass rel diff {abs(m_gpu - m_ref) / abs(m_ref):.2e}")
+        assert err <= tol
+        if dtype == fc.F64:
+            ref.regrid(w.tau_refine, w.tau_coarsen)
+            gpu.tag_regrid(w.tau_refine, w.tau_coarsen)
+            np.testing.assert_array_equal(gpu.leaves(), ref.leaves())
+            assert relerr(gpu.get_q(), ref.get_q()) <= F64_TOL

@@ -164,3 +164,11 @@ def test_balance_across_a_cube_vertex_matches_oracle():
     assert lv[:, 2].max() == 5
     near = lv[lv[:, 2] >= 3]
     assert set(near[:, 1]) >= {0, 2, 4}  # +Z, +X, +Y meet at (1, 1, 1)
+
+
+def test_input_generator_centres_match_the_oracle():
+    """The seeded input generator places sphere cell centres by the block
+    convention of the C interface; the oracle by its own face frames."""
+    w, F = adaptive_sphere(0)
+    X = synth.sphere_cell_centres(F.leaves(), w.mx)
+    np.testing.assert_allclose(X, F.sphere_centres(), rtol=0, atol=1e-15)
