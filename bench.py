@@ -388,19 +388,25 @@ def run_ours(args):
             "phases_ms": {k: x[0] for k, x in v["phases"].items()}}
         del vr
         if args.ensemble > 0:
-            ws = synth.ensemble(args.ensemble, seed=0, mx=32)
-            br = Runner(fc, torch, ws, dtype)
-            nsteps = 8
-            b = measure(br, nsteps, 2, flush_buf, local)
-            variants["batched"] = {
-                "workload": f"{args.ensemble} independent swirl forests, levels 2 to 4/5/6 "
-                            "(seeded), 32x32 patches, one launch per level substep for all",
-                "patches": b["patches"], "value": b["updates"] / (b["ms"] * 1e-3),
-                "ms_per_step": b["ms"] / nsteps, "steps": nsteps,
-                "roofline": roofline_of(b["phases"]["advance"], hbm, peak_src),
-                "phases_ms": {k: x[0] for k, x in b["phases"].items()},
-                "gpu_launches": b["launches"], "clocks": b["clocks"], "autotune": b["tuning"]}
-            del br
+            # the ensemble at 32^2 in the line's dtype, at 16^2, and in the other dtype
+            for key, mxb, dtb in (("batched", 32, dtype), ("batched_mx16", 16, dtype),
+                                  ("batched_f64" if other == fc.F64 else "batched_f32", 32,
+                                   other)):
+                ws = synth.ensemble(args.ensemble, seed=0, mx=mxb)
+                br = Runner(fc, torch, ws, dtb)
+                nsteps = 8
+                b = measure(br, nsteps, 2, flush_buf, local)
+                variants[key] = {
+                    "workload": f"{args.ensemble} independent swirl forests, levels 2 to 4/5/6 "
+                                f"(seeded), {mxb}x{mxb} patches, one launch per level substep "
+                                "for all",
+                    "dtype": "f32" if dtb == fc.F32 else "f64",
+                    "patches": b["patches"], "value": b["updates"] / (b["ms"] * 1e-3),
+                    "ms_per_step": b["ms"] / nsteps, "steps": nsteps,
+                    "roofline": roofline_of(b["phases"]["advance"], hbm, peak_src),
+                    "phases_ms": {k: x[0] for k, x in b["phases"].items()},
+                    "gpu_launches": b["launches"], "clocks": b["clocks"], "autotune": b["tuning"]}
+                del br
         sr = Runner(fc, torch, [synth.sphere(seed=0)], fc.F32)
         nsteps = 8
         sv = measure(sr, nsteps, 2, flush_buf, local)

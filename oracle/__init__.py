@@ -78,6 +78,9 @@ def lib():
     L.or_adjoint_global.argtypes = [vp, ctypes.c_int, ctypes.c_double, ctypes.c_double, dp, dp,
                                     dp, dp]
     L.or_adjoint_step_global.argtypes = [vp, ctypes.c_double, ctypes.c_double, dp, dp]
+    L.or_adjoint_multirate.argtypes = [vp, ctypes.c_int, ctypes.c_double, ctypes.c_double, dp,
+                                       dp, dp, dp]
+    L.or_adjoint_step_multirate.argtypes = [vp, ctypes.c_double, ctypes.c_double, dp, dp]
     L.or_set_params.argtypes = [vp, ctypes.POINTER(_Params)]
     L.or_sphere_centres.argtypes = [vp, dp]
     L.or_get_kappa.argtypes = [vp, dp]
@@ -234,6 +237,24 @@ class Forest:
         lam = np.ascontiguousarray(lam, dtype=np.float64).reshape(len(self), self.mx, self.mx).copy()
         ds = np.zeros(1)
         _check(lib().or_adjoint_step_global(self.h, t, dt, _dptr(lam), _dptr(ds)))
+        return lam, float(ds[0])
+
+    def adjoint_multirate(self, ncoarse: int, t0: float, dtc: float, q_target: np.ndarray):
+        """(loss, dL/dq0, dL/dscale) after ncoarse coarse multirate steps from the
+        current state (which is left unchanged)."""
+        qt = np.ascontiguousarray(q_target, dtype=np.float64).reshape(len(self), self.mx, self.mx)
+        g = np.zeros_like(qt)
+        gs = np.zeros(1)
+        loss = np.zeros(1)
+        _check(lib().or_adjoint_multirate(self.h, ncoarse, t0, dtc, _dptr(qt), _dptr(g),
+                                          _dptr(gs), _dptr(loss)))
+        return float(loss[0]), g, float(gs[0])
+
+    def adjoint_step_multirate(self, t: float, dtc: float, lam: np.ndarray):
+        """Adjoint of one coarse multirate step at the current state: (lam_n, dscale)."""
+        lam = np.ascontiguousarray(lam, dtype=np.float64).reshape(len(self), self.mx, self.mx).copy()
+        ds = np.zeros(1)
+        _check(lib().or_adjoint_step_multirate(self.h, t, dtc, _dptr(lam), _dptr(ds)))
         return lam, float(ds[0])
 
     def sphere_centres(self) -> np.ndarray:

@@ -372,3 +372,243 @@ int or_adjoint_global(or_forest* F, int nsteps, double t0, double dt, const doub
   free(states);
   return 0;
 }
+
+/* ------------------------------------------------------------------------
+ * Adjoint of multirate stepping (Sec. 4 local time stepping, coarse-first
+ * recursion; the reading of the forward is in drive.c).
+ *
+ * State of the forward: per leaf the current interior q and the interior
+ * qold of its level's previous state.  One substep of level L with weight
+ * alpha:
+ *   qT(c) = (1 - alpha) qold(c) + alpha q(c)     for leaves c of level L-1,
+ *   ghosts of L-1 (in qT) and of L (in q) by Alg. 1 restricted to L-1, L,
+ *   qold(p) = q(p), q(p) = step(q(p) with ghosts)  for leaves p of level L.
+ * Its transpose, with lam (adjoint of q) and mu (adjoint of qold):
+ *   lt(p) = step^T lam(p)  (a whole tile with ghosts),
+ *   lam(p) = mu(p) + interior of lt(p), mu(p) = 0  (qold(p) was overwritten),
+ *   the ghosts of lt and of the qT tiles' adjoint lT, through Alg. 1
+ *   backwards: boundary condition of L, interpolation (into lT), boundary
+ *   condition of L-1 and L, copy/average (into lT for sources of level L-1,
+ *   else into lam),
+ *   mu(c) += (1 - alpha) lT(c), lam(c) += alpha lT(c).
+ * The substeps are reversed in the opposite order of the recursion; each is
+ * replayed from the stored state before it (test sizes only).
+ * ------------------------------------------------------------------------ */
+
+typedef struct {
+  int L;
+  double t, dt, alpha;
+} mr_sub;
+
+static int mr_list(const or_forest* F, int L, double t, double dt, double alpha, mr_sub* out,
+                   int k) {
+  out[k].L = L;
+  out[k].t = t;
+  out[k].dt = dt;
+  out[k].alpha = alpha;
+  ++k;
+  if (L < F->P.lmax) {
+    k = mr_list(F, L + 1, t, 0.5 * dt, 0.0, out, k);
+    k = mr_list(F, L + 1, t + 0.5 * dt, 0.5 * dt, 0.5, out, k);
+  }
+  return k;
+}
+
+/* transpose of or_fill_level(F, L, alpha) for the ghosts of level L (in Lq)
+ * and of level L-1 (in LT); qT holds the forward's time-interpolated tiles */
+static void fill_level_reverse(or_forest* F, int L, double* Lq, double* LT) {
+  size_t S2 = (size_t)F->S * F->S;
+  int mx = F->P.mx, mbc = F->P.mbc;
+  /* phase 4: boundary condition of level L */
+  for (int p = 0; p < F->n; ++p)
+    if (F->lv[p].l == L) bc_reverse(F, p, Lq + p * S2);
+  /* phase 3: interpolation of level L's coarse ghosts from qT */
+  for (int p = 0; p < F->n; ++p) {
+    if (F->lv[p].l != L) continue;
+    int k = 0;
+    for (int j = -mbc; j < mx + mbc; ++j)
+      for (int i = -mbc; i < mx + mbc; ++i) {
+        if (!is_ghost_cell(F, i, j)) continue;
+        int rel, n;
+        double x, y;
+        or_ghost_holder(F, p, k++, &rel, &n, &x, &y);
+        if (rel != REL_COARSE) continue;
+        double lg = Lq[p * S2 + OR_IDX(F, i, j)];
+        Lq[p * S2 + OR_IDX(F, i, j)] = 0.0;
+        const or_leaf* c = &F->lv[n];
+        double s = ldexp((double)mx, c->l);
+        int ic = (int)floor(x * s) - c->x * mx, jc = (int)floor(y * s) - c->y * mx;
+        double xc = ((double)c->x * mx + ic + 0.5) / s, yc = ((double)c->y * mx + jc + 0.5) / s;
+        double dx = (x > xc) ? 1.0 : -1.0, dy = (y > yc) ? 1.0 : -1.0;
+        const double* Qn = F->qT + n * S2;
+        double* Ln = LT + n * S2;
+        double q0 = Qn[OR_IDX(F, ic, jc)];
+        double ax = Qn[OR_IDX(F, ic + 1, jc)] - q0, bx = q0 - Qn[OR_IDX(F, ic - 1, jc)];
+        double ay = Qn[OR_IDX(F, ic, jc + 1)] - q0, by = q0 - Qn[OR_IDX(F, ic, jc - 1)];
+        double dax, dbx, day, dby;
+        minmod_grad(ax, bx, &dax, &dbx);
+        minmod_grad(ay, by, &day, &dby);
+        double lsx = 0.25 * dx * lg, lsy = 0.25 * dy * lg;
+        Ln[OR_IDX(F, ic, jc)] += lg + lsx * (dbx - dax) + lsy * (dby - day);
+        Ln[OR_IDX(F, ic + 1, jc)] += lsx * dax;
+        Ln[OR_IDX(F, ic - 1, jc)] -= lsx * dbx;
+        Ln[OR_IDX(F, ic, jc + 1)] += lsy * day;
+        Ln[OR_IDX(F, ic, jc - 1)] -= lsy * dby;
+      }
+  }
+  /* phase 2: boundary condition of levels L-1 (qT) and L */
+  for (int p = 0; p < F->n; ++p) {
+    if (F->lv[p].l == L) bc_reverse(F, p, Lq + p * S2);
+    if (F->lv[p].l == L - 1) bc_reverse(F, p, LT + p * S2);
+  }
+  /* phase 1: copy and average into the ghosts of levels L-1 and L */
+  for (int p = 0; p < F->n; ++p) {
+    int lp = F->lv[p].l;
+    if (lp != L && lp != L - 1) continue;
+    double* Lp = (lp == L ? Lq : LT) + p * S2;
+    int k = 0;
+    for (int j = -mbc; j < mx + mbc; ++j)
+      for (int i = -mbc; i < mx + mbc; ++i) {
+        if (!is_ghost_cell(F, i, j)) continue;
+        int rel, n;
+        double x, y;
+        or_ghost_holder(F, p, k++, &rel, &n, &x, &y);
+        if (rel != REL_SAME && rel != REL_FINE) continue;
+        double lg = Lp[OR_IDX(F, i, j)];
+        Lp[OR_IDX(F, i, j)] = 0.0;
+        double* Ln = (F->lv[n].l == L - 1 ? LT : Lq) + n * S2;
+        if (rel == REL_SAME) {
+          Ln[cell_index(F, n, x, y)] += lg;
+        } else {
+          double hf = 1.0 / ldexp((double)mx, F->lv[n].l);
+          for (int q = 0; q < 4; ++q) {
+            double ox = (q & 1) ? 0.5 * hf : -0.5 * hf, oy = (q & 2) ? 0.5 * hf : -0.5 * hf;
+            Ln[cell_index(F, n, x + ox, y + oy)] += 0.25 * lg;
+          }
+        }
+      }
+  }
+}
+
+int or_adjoint_step_multirate(or_forest* F, double t, double dt_coarse, double* lam,
+                              double* dscale) {
+  if (F->P.domain == OR_SPHERE) {
+    or_set_error("the adjoint is stated for the square domains");
+    return -1;
+  }
+  size_t S2 = (size_t)F->S * F->S, nS = S2 * (size_t)(F->n > 0 ? F->n : 1);
+  int mx = F->P.mx, nsub = (1 << (F->P.lmax - F->P.lmin + 1)) - 1;
+  mr_sub* sub = (mr_sub*)malloc(sizeof(mr_sub) * (size_t)nsub);
+  mr_list(F, F->P.lmin, t, dt_coarse, 0.0, sub, 0);
+  /* forward, keeping the state (q, qold) before every substep */
+  double* keep = (double*)malloc(sizeof(double) * nS * 2 * (size_t)nsub);
+  int status = 0;
+  for (int k = 0; k < nsub && status == 0; ++k) {
+    memcpy(keep + 2 * k * nS, F->q, sizeof(double) * nS);
+    memcpy(keep + (2 * k + 1) * nS, F->qold, sizeof(double) * nS);
+    const mr_sub* s = &sub[k];
+    if (or_fill_level(F, s->L, s->alpha)) status = -1;
+    for (int p = 0; p < F->n && status == 0; ++p)
+      if (F->lv[p].l == s->L) {
+        memcpy(F->qold + p * S2, F->q + p * S2, sizeof(double) * S2);
+        or_advance_leaf(F, p, s->t, s->dt);
+      }
+  }
+  double* Lq = (double*)calloc(nS, sizeof(double));  /* adjoint of q (tiles) */
+  double* Lo = (double*)calloc(nS, sizeof(double));  /* adjoint of qold */
+  double* LT = (double*)calloc(nS, sizeof(double));  /* adjoint of qT */
+  double* lnew = (double*)malloc(sizeof(double) * (size_t)mx * mx);
+  for (int p = 0; p < F->n; ++p)
+    for (int j = 0; j < mx; ++j)
+      for (int i = 0; i < mx; ++i)
+        Lq[p * S2 + OR_IDX(F, i, j)] = lam[((size_t)p * mx + j) * mx + i];
+  double sum = 0.0;
+  for (int k = nsub - 1; k >= 0 && status == 0; --k) {
+    const mr_sub* s = &sub[k];
+    memcpy(F->q, keep + 2 * k * nS, sizeof(double) * nS);
+    memcpy(F->qold, keep + (2 * k + 1) * nS, sizeof(double) * nS);
+    if (or_fill_level(F, s->L, s->alpha)) {
+      status = -1;
+      break;
+    }
+    memset(LT, 0, sizeof(double) * nS);
+    for (int p = 0; p < F->n; ++p) {
+      const or_leaf* a = &F->lv[p];
+      if (a->l != s->L) continue;
+      double* Lp = Lq + p * S2;
+      for (int j = 0; j < mx; ++j)
+        for (int i = 0; i < mx; ++i) {
+          lnew[j * mx + i] = Lp[OR_IDX(F, i, j)];
+          Lp[OR_IDX(F, i, j)] = 0.0;
+        }
+      double h = 1.0 / ldexp((double)mx, a->l);
+      sum += claw_step_adjoint(&F->P, F->q + p * S2, mx, F->P.mbc, h, s->dt, s->t,
+                               (long)a->x * mx, (long)a->y * mx, lnew, Lp);
+      for (int j = 0; j < mx; ++j)
+        for (int i = 0; i < mx; ++i) {
+          Lp[OR_IDX(F, i, j)] += Lo[p * S2 + OR_IDX(F, i, j)];
+          Lo[p * S2 + OR_IDX(F, i, j)] = 0.0;
+        }
+    }
+    fill_level_reverse(F, s->L, Lq, LT);
+    for (int p = 0; p < F->n; ++p)
+      if (F->lv[p].l == s->L - 1)
+        for (int j = 0; j < mx; ++j)
+          for (int i = 0; i < mx; ++i) {
+            double g = LT[p * S2 + OR_IDX(F, i, j)];
+            Lo[p * S2 + OR_IDX(F, i, j)] += (1.0 - s->alpha) * g;
+            Lq[p * S2 + OR_IDX(F, i, j)] += s->alpha * g;
+          }
+  }
+  /* the state is left at the start of the coarse step */
+  if (status == 0) {
+    memcpy(F->q, keep, sizeof(double) * nS);
+    memcpy(F->qold, keep + nS, sizeof(double) * nS);
+    for (int p = 0; p < F->n; ++p)
+      for (int j = 0; j < mx; ++j)
+        for (int i = 0; i < mx; ++i)
+          lam[((size_t)p * mx + j) * mx + i] = Lq[p * S2 + OR_IDX(F, i, j)];
+    *dscale += sum / scale_of(&F->P);
+  }
+  free(lnew);
+  free(LT);
+  free(Lo);
+  free(Lq);
+  free(keep);
+  free(sub);
+  return status;
+}
+
+int or_adjoint_multirate(or_forest* F, int ncoarse, double t0, double dt_coarse,
+                         const double* q_target, double* grad_q0, double* grad_scale,
+                         double* loss) {
+  int mx = F->P.mx;
+  size_t ni = (size_t)F->n * mx * mx;
+  double* states = (double*)malloc(sizeof(double) * ni * (size_t)(ncoarse + 1));
+  or_get_q(F, states);
+  for (int n = 0; n < ncoarse; ++n) {
+    if (or_step_multirate(F, t0 + n * dt_coarse, dt_coarse)) {
+      free(states);
+      return -1;
+    }
+    or_get_q(F, states + (size_t)(n + 1) * ni);
+  }
+  double l = 0.0;
+  for (size_t k = 0; k < ni; ++k) {
+    double d = states[(size_t)ncoarse * ni + k] - q_target[k];
+    grad_q0[k] = d;
+    l += 0.5 * d * d;
+  }
+  *loss = l;
+  *grad_scale = 0.0;
+  for (int n = ncoarse - 1; n >= 0; --n) {
+    or_set_q(F, states + (size_t)n * ni);
+    if (or_adjoint_step_multirate(F, t0 + n * dt_coarse, dt_coarse, grad_q0, grad_scale)) {
+      free(states);
+      return -1;
+    }
+  }
+  or_set_q(F, states);
+  free(states);
+  return 0;
+}

@@ -31,7 +31,7 @@
 
 static double cell_h(const or_forest* F, int l) { return 1.0 / ldexp((double)F->P.mx, l); }
 
-static void advance_leaf(or_forest* F, int p, double t, double dt) {
+void or_advance_leaf(or_forest* F, int p, double t, double dt) {
   const or_leaf* a = &F->lv[p];
   size_t S2 = (size_t)F->S * F->S, S = (size_t)F->S;
   if (F->P.domain == OR_SPHERE) {
@@ -47,7 +47,7 @@ int or_fill_ghosts(or_forest* F) { return or_fill_all(F); }
 
 int or_step_global(or_forest* F, double t, double dt) {
   if (or_fill_all(F)) return -1;
-  for (int p = 0; p < F->n; ++p) advance_leaf(F, p, t, dt);
+  for (int p = 0; p < F->n; ++p) or_advance_leaf(F, p, t, dt);
   return 0;
 }
 
@@ -57,7 +57,7 @@ static int mr_level(or_forest* F, int L, double t, double dt, double alpha) {
   for (int p = 0; p < F->n; ++p)
     if (F->lv[p].l == L) {
       memcpy(F->qold + p * S2, F->q + p * S2, sizeof(double) * S2);
-      advance_leaf(F, p, t, dt);
+      or_advance_leaf(F, p, t, dt);
     }
   if (L < F->P.lmax) {
     if (mr_level(F, L + 1, t, 0.5 * dt, 0.0)) return -1;

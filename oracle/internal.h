@@ -71,6 +71,8 @@ int or_ghost_holder(or_forest* F, int p, int k, int* rel, int* src, double* x, d
 /* ghost.c */
 int or_fill_all(or_forest* F);
 int or_fill_level(or_forest* F, int level, double alpha);
+/* the wave-propagation step of leaf p (flat or capacity form) */
+void or_advance_leaf(or_forest* F, int p, double t, double dt);
 void or_drop_cache(or_forest* F);
 
 #endif

@@ -78,6 +78,18 @@ int or_adjoint_global(or_forest* F, int nsteps, double t0, double dt, const doub
  * velocity-scale derivative to *dscale */
 int or_adjoint_step_global(or_forest* F, double t, double dt, double* lam, double* dscale);
 
+/* Adjoint of one coarse multirate step (Sec. 4 recursion, coarse level
+ * first, time-interpolated coarse ghosts): given lam (interior, adjoint of
+ * the state after the step) and the forest at the step's start, overwrite lam
+ * with the adjoint of the start state and add the velocity-scale derivative
+ * to *dscale.  The forest is left at the start state.  Square domains. */
+int or_adjoint_step_multirate(or_forest* F, double t, double dt_coarse, double* lam,
+                              double* dscale);
+/* as or_adjoint_global, over ncoarse coarse multirate steps */
+int or_adjoint_multirate(or_forest* F, int ncoarse, double t0, double dt_coarse,
+                         const double* q_target, double* grad_q0, double* grad_scale,
+                         double* loss);
+
 /* cubed sphere: unit-sphere positions of every interior cell centre
  * (n x mx x mx x 3) and the cell capacities (n x mx x mx) */
 void or_sphere_centres(const or_forest* F, double* xyz);

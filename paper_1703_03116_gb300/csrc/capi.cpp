@@ -224,8 +224,10 @@ void free_device(fc_forest* F) {
 }
 
 // cubed sphere: (re)compute the metric blocks of the current layout for the
-// rotation vector times the velocity scale (synchronous)
-fc_status update_metrics(fc_forest* F) {
+// rotation vector times the velocity scale (synchronous); after a regrid the
+// kept patches copy theirs from the old layout (rm, old: device)
+fc_status update_metrics(fc_forest* F, const RemapEntry* rm = nullptr,
+                         const double* old = nullptr) {
   const HostForest& H = F->host;
   if (H.desc.domain != FC_DOMAIN_SPHERE) return FC_OK;
   const int n = H.npatch();
@@ -235,13 +237,14 @@ fc_status update_metrics(fc_forest* F) {
     return fail(FC_ERR_OOM, "metric allocation failed");
   const double w[3] = {F->vel_scale * H.desc.vel[0], F->vel_scale * H.desc.vel[1],
                        F->vel_scale * H.desc.vel[2]};
-  FC_CUDA(launch_sphere_metrics(F->d_meta, n, H.desc.mx, w, F->d_metric, 0));
+  FC_CUDA(launch_sphere_metrics(F->d_meta, n, H.desc.mx, w, F->d_metric, rm, old, 0));
   FC_CUDA(cudaStreamSynchronize(0));
   return FC_OK;
 }
 
-// upload tables (and allocate a store) for the current host layout
-fc_status upload(fc_forest* F, bool alloc_store) {
+// upload tables (and allocate a store) for the current host layout; the
+// sphere's metrics too unless the caller builds them (regrid)
+fc_status upload(fc_forest* F, bool alloc_store, bool metrics = true) {
   const HostForest& H = F->host;
   const int n = H.npatch();
   const size_t S = (size_t)H.desc.mx + 2 * kMbc;
@@ -304,7 +307,7 @@ fc_status upload(fc_forest* F, bool alloc_store) {
     FC_CUDA(dmalloc(&F->d_t0, 1));
     FC_CUDA(cudaMemset(F->d_t0, 0, sizeof(double)));
   }
-  return update_metrics(F);
+  return metrics ? update_metrics(F) : FC_OK;
 }
 
 template <typename real>
@@ -1014,7 +1017,7 @@ fc_status fc_tag_regrid(fc_forest* F, double tau_refine, double tau_coarsen,
     delete G;
     return fail(FC_ERR_STATE, "regrid produced an invalid layout: " + err);
   }
-  st = upload(G, true);
+  st = upload(G, true, false);
   if (st != FC_OK) {
     free_device(G);
     delete G;
@@ -1063,6 +1066,15 @@ fc_status fc_tag_regrid(fc_forest* F, double tau_refine, double tau_coarsen,
   }
   FC_CUDA(cudaMemcpyAsync(G->d_remap, rm.data(), sizeof(RemapEntry) * rm.size(),
                           cudaMemcpyHostToDevice, s));
+  if (F->d_metric) {  // the new layout's metrics: kept patches copy theirs
+    FC_CUDA(cudaStreamSynchronize(s));
+    st = update_metrics(G, G->d_remap, F->d_metric);
+    if (st != FC_OK) {
+      free_device(G);
+      delete G;
+      return st;
+    }
+  }
   cudaError_t e;
   {
     Timed tm(F, 2, s, 2.0 * (double)N.npatch() * N.desc.mx * N.desc.mx * F->esize);

@@ -218,9 +218,12 @@ uint64_t& launch_counter();
 // Cubed-sphere metric blocks of patches [0, npatch) for the solid-body
 // rotation omega (already scaled): equiangular gnomonic mapping of each
 // face, capacities from two spherical triangles per cell, edge fluxes from
-// the stream function -omega . X (Sec. 5.3 mapped grids).
+// the stream function -omega . X (Sec. 5.3 mapped grids).  With a remap list
+// (rm, device, one entry per patch), RM_COPY patches copy their block from
+// old_metric (same omega) instead.
 cudaError_t launch_sphere_metrics(const PatchMeta* meta, int npatch, int mx, const double* omega,
-                                  double* metric, cudaStream_t s);
+                                  double* metric, const RemapEntry* rm, const double* old_metric,
+                                  cudaStream_t s);
 
 // fc_mass_noalloc's kernels (scratch in a file-scope device array)
 cudaError_t noalloc_mass(const void* q, int dtype, int mx, int nleaves, const int* level,

@@ -44,16 +44,25 @@ __device__ __forceinline__ double tri_area(const double* a, const double* b, con
 }
 
 // one CTA per patch; X: the (S+1)^2 grid corners on the sphere, in shared
-// memory as three planes
+// memory as three planes.  After a regrid (rm != null) a patch that kept its
+// quadrant copies its block from the old layout's store instead.
 __global__ void __launch_bounds__(256) metrics_kernel(const PatchMeta* meta, int npatch, int mx,
                                                       double w0, double w1, double w2,
-                                                      double* metric) {
+                                                      double* metric, const RemapEntry* rm,
+                                                      const double* old_metric) {
   extern __shared__ double Xs[];
   const int S = mx + 2 * kMbc, SN = S + 1;
   double* X0 = Xs;
   double* X1 = X0 + SN * SN;
   double* X2 = X1 + SN * SN;
   for (int p = blockIdx.x; p < npatch; p += gridDim.x) {
+    if (rm && rm[p].kind == RM_COPY) {
+      const double2* src =
+          reinterpret_cast<const double2*>(old_metric + (size_t)rm[p].src[0] * metric_stride(S));
+      double2* dst = reinterpret_cast<double2*>(metric + (size_t)p * metric_stride(S));
+      for (int k = threadIdx.x; k < metric_stride(S) / 2; k += blockDim.x) dst[k] = src[k];
+      continue;
+    }
     const PatchMeta pm = meta[p];
     int n, ex, ey;
     cube_face(pm.block, &n, &ex, &ey);
@@ -113,7 +122,8 @@ __global__ void __launch_bounds__(256) metrics_kernel(const PatchMeta* meta, int
 }  // namespace
 
 cudaError_t launch_sphere_metrics(const PatchMeta* meta, int npatch, int mx, const double* omega,
-                                  double* metric, cudaStream_t s) {
+                                  double* metric, const RemapEntry* rm, const double* old_metric,
+                                  cudaStream_t s) {
   if (npatch <= 0) return cudaSuccess;
   const int SN = mx + 2 * kMbc + 1;
   const size_t smem = sizeof(double) * 3 * (size_t)SN * SN;
@@ -126,7 +136,8 @@ cudaError_t launch_sphere_metrics(const PatchMeta* meta, int npatch, int mx, con
   }
   if (smem > 64 * 1024) return cudaErrorInvalidValue;
   const int grid = npatch < 65535 * 8 ? npatch : 65535 * 8;
-  metrics_kernel<<<grid, 256, smem, s>>>(meta, npatch, mx, omega[0], omega[1], omega[2], metric);
+  metrics_kernel<<<grid, 256, smem, s>>>(meta, npatch, mx, omega[0], omega[1], omega[2], metric,
+                                         rm, old_metric);
   ++launch_counter();
   return cudaGetLastError();
 }

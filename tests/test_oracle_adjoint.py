@@ -62,3 +62,47 @@ def test_adjoint_matches_central_differences_adaptive_mc():
     eps = 1e-6
     fds = (_loss(F, q0, qt, dt, n, 1 + eps) - _loss(F, q0, qt, dt, n, 1 - eps)) / (2 * eps)
     assert abs(fds - gs) <= 1e-6 * abs(fds)
+
+
+def _loss_mr(F, q, qt, dtc, ncoarse, scale=1.0):
+    F.set_q(q)
+    F.set_velocity_scale(scale)
+    for k in range(ncoarse):
+        F.step_multirate(k * dtc, dtc)
+    r = 0.5 * np.sum((F.get_q() - qt) ** 2)
+    F.set_velocity_scale(1.0)
+    return r
+
+
+def test_multirate_adjoint_matches_central_differences():
+    """Multirate (coarse-first recursion with time-interpolated coarse
+    ghosts) on an adaptive MC forest of three levels: the adjoint's
+    directional derivatives match central differences."""
+    F, q0, qt, _, _ = _smooth_adaptive()
+    assert len(set(F.leaves()[:, 2])) == 3
+    dtc = 4 * 0.9 / 128  # ratio 4 between levels 2 and 4
+    n = 2
+    loss, g, gs = F.adjoint_multirate(n, 0.0, dtc, qt)
+    assert abs(loss - _loss_mr(F, q0, qt, dtc, n)) <= 1e-14 * loss
+    for seed in (7, 8):
+        d = synth.random_field(q0.shape, seed=seed) - 0.5
+        eps = 1e-7
+        fd = (_loss_mr(F, q0 + eps * d, qt, dtc, n) - _loss_mr(F, q0 - eps * d, qt, dtc, n)) / (
+            2 * eps)
+        assert abs(fd - np.sum(g * d)) <= 1e-6 * abs(fd), (fd, np.sum(g * d))
+    eps = 1e-6
+    fds = (_loss_mr(F, q0, qt, dtc, n, 1 + eps) - _loss_mr(F, q0, qt, dtc, n, 1 - eps)) / (2 * eps)
+    assert abs(fds - gs) <= 1e-6 * abs(fds), (fds, gs)
+
+
+def test_multirate_adjoint_single_level_is_the_global_adjoint():
+    """With one level a coarse multirate step is one global step."""
+    prm = oracle.params(oracle.WALLS, 8, 2, 3, 3, ("swirl", 4.0))
+    F = oracle.Forest(prm, oracle.uniform_leaves(3))
+    q = synth.random_field((len(F), 8, 8), seed=3)
+    lam = synth.random_field((len(F), 8, 8), seed=4) - 0.5
+    F.set_q(q)
+    a, da = F.adjoint_step_multirate(0.2, 0.01, lam)
+    b, db = F.adjoint_step_global(0.2, 0.01, lam)
+    np.testing.assert_array_equal(a, b)
+    assert da == db
