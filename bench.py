@@ -195,13 +195,16 @@ class Runner:
 
 
 def measure(runner, steps, warmup, flush_buf, clock_index):
+    """W untimed warm-up steps, then the K timed steps (CUDA events around
+    each step on the launching stream, L2 flushed before each, outside the
+    events), then K more steps with the library's per-launch phase timers on
+    (an event pair around every kernel, graph nodes included) for the
+    per-kernel rooflines -- kept out of the timed steps, whose value they
+    would otherwise slow down."""
     torch, fc, F = runner.torch, runner.fc, runner.F
     for _ in range(warmup):
         runner.step()
     torch.cuda.synchronize()
-    F.timers(True)
-    for ph in range(4):
-        F.read_timer(ph, reset=True)
     fc.launch_count(reset=True)
     events, updates = [], 0
     with Clocks(clock_index) as clk:
@@ -219,6 +222,14 @@ def measure(runner, steps, warmup, flush_buf, clock_index):
         torch.cuda.synchronize()
     launches = fc.launch_count()
     ms = sum(a.elapsed_time(b) for a, b in events)
+    # per-kernel timing pass
+    F.timers(True)
+    for ph in range(4):
+        F.read_timer(ph, reset=True)
+    for _ in range(steps):
+        flush_buf.zero_()
+        runner.step()
+    torch.cuda.synchronize()
     phases = {k: F.read_timer(ph) for ph, k in enumerate(["advance", "fill", "regrid"])}
     F.timers(False)
     return dict(ms=ms, updates=updates, phases=phases, launches=launches,
@@ -234,41 +245,64 @@ def roofline_of(phase, peak_gbs, peak_src):
             "avg_launch_us": 1e3 * ms / max(n, 1), "bytes_per_launch": nbytes / max(n, 1)}
 
 
-def adjoint_cost(fc, torch, flush_buf, nsteps: int = 64):
-    """Forward vs gradient cost on the frozen swirl forest (FP32, global steps,
-    sqrt(N) checkpoints): L = 1/2 |q_N - q_target|^2, gradients with respect
-    to q0 and the velocity scale."""
+def adjoint_cost(fc, torch, flush_buf, ncoarse: int = 25):
+    """Forward vs gradient cost of the adjoint workload: the swirl forest
+    frozen after its initial regrid, 25 coarse multirate steps (400
+    finest-level substeps), FP32, sqrt(N) checkpoints; L = 1/2 |q_N -
+    q_target|^2 (target: the run from the shifted disc), gradients with
+    respect to q0 and the velocity scale.  Also the adjoint of one coarse step
+    alone against the forward coarse step."""
     from paper_1703_03116_gb300.autograd import advect
     w = synth.swirl(seed=0)
     tw = synth.adjoint_target(w)
     desc = fc.make_desc(domain=fc.WALLS, mx=w.mx, lmin=w.lmin, lmax=w.lmax, dtype=fc.F32,
                         velocity=w.velocity)
     F = fc.initial_forest(desc, q0_fn([w]), tau_r=w.tau_refine, tau_c=w.tau_coarsen)
+    F.autotune()
     leaves = F.leaves()
     dev = flush_buf.device
     q0 = torch.tensor(q0_fn([w])(leaves), dtype=torch.float32, device=dev)
     qt = torch.tensor(q0_fn([tw])(leaves), dtype=torch.float32, device=dev)
-    dt = w.cfl / (w.mx * 2 ** w.lmax)
-    updates = nsteps * len(leaves) * w.mx * w.mx  # global steps: every patch every step
+    _, dtc = synth.time_step(w)
+    updates = ncoarse * cell_updates(leaves, w.lmin, w.mx)
+
+    def timed(fn):
+        flush_buf.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1)
+
     times = {}
     for name in ("warm-up", "forward", "forward+backward"):
         q = q0.clone().requires_grad_(name != "forward")
         s = torch.ones((), dtype=torch.float32, device=dev, requires_grad=name != "forward")
-        flush_buf.zero_()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
-        qN = advect(q, s, F, 0.0, dt, nsteps)
-        loss = 0.5 * ((qN - qt) ** 2).sum()
-        if name != "forward":
-            loss.backward()
-        e1.record()
-        torch.cuda.synchronize()
-        times[name] = e0.elapsed_time(e1)
+
+        def run():
+            qN = advect(q, s, F, 0.0, dtc, ncoarse, multirate=True)
+            loss = 0.5 * ((qN - qt) ** 2).sum()
+            if name != "forward":
+                loss.backward()
+        times[name] = timed(run)
     fwd, both = times["forward"], times["forward+backward"]
-    return {"workload": f"frozen swirl forest ({len(leaves)} patches), {nsteps} global steps, "
-                        "FP32, sqrt(N) checkpoints",
+    # one coarse step: forward vs its adjoint (which replays the forward once)
+    F.set_q(q0)
+    lam = (q0 - qt).contiguous()
+    ds = torch.zeros(1, dtype=torch.float64, device=dev)
+    F.adjoint_step_multirate(0.0, dtc, lam, ds)  # warm-up (state buffers)
+    K = 5
+    t_fwd = timed(lambda: [F.step_multirate(k * dtc, dtc) for k in range(K)]) / K
+    F.set_q(q0)
+    t_adj = timed(lambda: [F.adjoint_step_multirate(0.0, dtc, lam, ds) for _ in range(K)]) / K
+    return {"workload": f"swirl forest frozen after the initial regrid ({len(leaves)} patches), "
+                        f"{ncoarse} coarse multirate steps = {ncoarse * 16} finest substeps, FP32, "
+                        "sqrt(N) checkpoints",
             "forward_ms": fwd, "gradient_ms": both - fwd,
             "gradient_over_forward": (both - fwd) / fwd,
+            "coarse_step_forward_ms": t_fwd, "coarse_step_adjoint_ms": t_adj,
+            "adjoint_step_over_forward_step": t_adj / t_fwd,
             "forward_cell_updates_per_s": updates / (fwd * 1e-3)}
 
 

@@ -170,6 +170,25 @@ fc_status fc_set_velocity_scale(fc_forest* forest, double scale);
 fc_status fc_adjoint_step_global(fc_forest* forest, double t, double dt, void* lam,
                                  double* dscale, void* stream);
 
+/* Adjoint of one coarse multirate step (the coarse-first recursion of
+ * fc_step_multirate, Sec. 4): the transpose of every level substep -- the
+ * update, the level-restricted Alg. 1 fill, the time interpolation
+ * q_T = (1 - alpha) q_old + alpha q of the coarser level and the copy q_old = q
+ * -- in reverse order, on the pieces the forward state selects.  The forest
+ * must hold the state at the step's start time t; the call replays the
+ * forward step once on the device (keeping, before each substep, the states
+ * of the levels it touches) and leaves the forest at the start state.
+ *   lam     device, in/out, field layout: dL/dq(t + dt_coarse) on entry,
+ *           dL/dq(t) on return;
+ *   dscale  device, one double, accumulated: += lam^T dq/dsigma.
+ * Device memory: three adjoint stores plus the kept states (about two
+ * stores per substep for the levels it touches), held until the forest is
+ * destroyed.  Square domains only (FC_ERR_INVALID_ARG on the sphere).
+ * Work runs on `stream`; the call ends by reading the device error word
+ * (synchronous). */
+fc_status fc_adjoint_step_multirate(fc_forest* forest, double t, double dt_coarse, void* lam,
+                                    double* dscale, void* stream);
+
 /* Total mass per forest, sum over leaves of h^2 sum(q) (on the sphere
  * sum(kappa q)), accumulated in FP64
  * on the device in a fixed order.  out: host, nforests doubles.  Synchronous. */

@@ -58,6 +58,8 @@ SIGNATURES = {
     "fc_set_velocity_scale": (ctypes.c_int, [_vp, ctypes.c_double]),
     "fc_adjoint_step_global": (ctypes.c_int, [_vp, ctypes.c_double, ctypes.c_double, _vp, _vp,
                                               _vp]),
+    "fc_adjoint_step_multirate": (ctypes.c_int, [_vp, ctypes.c_double, ctypes.c_double, _vp,
+                                                 _vp, _vp]),
     "fc_mass_noalloc": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp, _vp,
                                        ctypes.c_int, _vp, _vp]),
     "fc_set_advance_variant": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int]),

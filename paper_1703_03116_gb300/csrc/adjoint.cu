@@ -19,6 +19,14 @@
 //  adj_copy        transpose of copy / average (Eq. transform,
 //                  Eq. ghost_coarse): ghost adjoints go to the neighbours'
 //                  interior cells (atomic adds).
+//
+// Multirate substep of level L (launch_adjoint_substep): the same transposes
+// restricted to what the substep's fill touched -- level L's update, level
+// L's ghosts, and the ghosts of the level L-1 patches read through the
+// time-interpolation buffer qT -- plus the transposes of the copy
+// q_old = q taken before the update (adj_combine) and of
+// qT = (1 - alpha) q_old + alpha q (adj_time, and inside adj_copy for
+// sources read on the fly).
 // The adjoint tiles use the patch-store layout ((mx+4)^2 per patch).
 #include "ghost_gather.cuh"
 
@@ -104,7 +112,10 @@ __global__ void __launch_bounds__(NT) adj_advance_kernel(DevForest<real> D, AdvA
   const bool swirl = D.vel_kind == FC_VEL_SWIRL;
   const real cu = real(D.vel[0]), cv = real(D.vel[1]);
   const real nu = real(a.nu), hn = real(0.5 * a.nu), h = real(a.h);
-  if (threadIdx.x == 0 && swirl) ucoef_s = real(cospi(a.t_half / a.period) * a.sfac);
+  if (threadIdx.x == 0 && swirl) {
+    const double t = a.t0_dev ? *a.t0_dev + a.t_off : a.t_half;  // graph replay: time on device
+    ucoef_s = real(cospi(t / a.period) * a.sfac);
+  }
   __syncthreads();
   const real ucoef = swirl ? ucoef_s : real(0);
   double dsum = 0.0;
@@ -317,10 +328,12 @@ __global__ void __launch_bounds__(NT) adj_advance_kernel(DevForest<real> D, AdvA
   if (threadIdx.x == 0) atomicAdd(dscale, red[0] * dfac);
 }
 
-// transpose of the interpolation: fine ghost adjoint -> coarse cells read
+// transpose of the interpolation: fine ghost adjoint -> coarse cells read.
+// A coarse patch on `tlevel` was read through the time-interpolation buffer
+// qT; its adjoint goes to lamT (its qT tile) instead of lam.
 template <typename real, int MX>
 __global__ void adj_interp_kernel(DevForest<real> D, const int* targets, int ntargets,
-                                  real* lam) {
+                                  real* lam, int tlevel, real* lamT) {
   constexpr int S = MX + 4;
   __shared__ NbrStage st;
   for (int t = blockIdx.x; t < ntargets; t += gridDim.x) {
@@ -343,8 +356,9 @@ __global__ void adj_interp_kernel(DevForest<real> D, const int* targets, int nta
       const real dx = (gx & 1) ? real(1) : real(-1);
       const real dy = (gy & 1) ? real(1) : real(-1);
       const size_t o = (size_t)(jc + kMbc) * S + ic + kMbc;
-      const real* C = patch_ptr(D.buf[D.cur[nm.level]], e.n0, S) + o;
-      real* LC = lam + (size_t)e.n0 * S * S + o;
+      const bool viaT = nm.level == tlevel;
+      const real* C = patch_ptr(viaT ? D.qT : D.buf[D.cur[nm.level]], e.n0, S) + o;
+      real* LC = (viaT ? lamT : lam) + (size_t)e.n0 * S * S + o;
       const real lg = L[(j + kMbc) * S + i + kMbc];
       L[(j + kMbc) * S + i + kMbc] = real(0);
       const real q0 = C[0];
@@ -364,11 +378,13 @@ __global__ void adj_interp_kernel(DevForest<real> D, const int* targets, int nta
   }
 }
 
-// transpose of the first wall-BC pass (every patch, local)
+// transpose of a wall-BC pass (local to each patch): patches targets[t]
+// (or p0 + t without a list), t < n
 template <typename real, int MX>
-__global__ void adj_bc_kernel(DevForest<real> D, real* lam) {
+__global__ void adj_bc_kernel(DevForest<real> D, real* lam, const int* targets, int p0, int n) {
   constexpr int S = MX + 4;
-  for (int p = blockIdx.x; p < D.npatch; p += gridDim.x) {
+  for (int t = blockIdx.x; t < n; t += gridDim.x) {
+    const int p = targets ? targets[t] : p0 + t;
     const PatchMeta pm = D.meta[p];
     real* L = lam + (size_t)p * S * S;
     const int N = MX << pm.level;
@@ -387,16 +403,32 @@ __global__ void adj_bc_kernel(DevForest<real> D, real* lam) {
   }
 }
 
-// transpose of copy / average: ghost adjoint -> neighbour interiors
+// transpose of copy / average: ghost adjoint -> neighbour interiors, for
+// patches targets[t] (or p0 + t), t < n.  Multirate (tlevel >= 0): a patch on
+// tlevel keeps its ghost adjoints in lamT (its qT tile); a source on tlevel
+// was read as (1 - alpha) q_old + alpha q, so its share goes to lamO and lam.
+template <typename real>
+__device__ __forceinline__ void adj_src_add(real* lam, real* lamO, bool viaT, real alpha,
+                                            size_t o, real v) {
+  if (viaT) {
+    atomicAdd(lamO + o, (real(1) - alpha) * v);
+    atomicAdd(lam + o, alpha * v);
+  } else {
+    atomicAdd(lam + o, v);
+  }
+}
+
 template <typename real, int MX>
-__global__ void adj_copy_kernel(DevForest<real> D, real* lam) {
+__global__ void adj_copy_kernel(DevForest<real> D, real* lam, const int* targets, int p0, int n,
+                                int tlevel, real alpha, real* lamT, real* lamO) {
   constexpr int S = MX + 4;
   __shared__ NbrStage st;
-  for (int p = blockIdx.x; p < D.npatch; p += gridDim.x) {
+  for (int t = blockIdx.x; t < n; t += gridDim.x) {
+    const int p = targets ? targets[t] : p0 + t;
     stage_neighbours(D.meta, D.nbr, p, st, threadIdx.x);
     const PatchMeta pm = D.meta[p];
     __syncthreads();
-    real* L = lam + (size_t)p * S * S;
+    real* L = (pm.level == tlevel ? lamT : lam) + (size_t)p * S * S;
     for (int k = threadIdx.x; k < num_ghosts<MX>(); k += blockDim.x) {
       int i, j;
       ghost_ij<MX>(k, i, j);
@@ -411,7 +443,8 @@ __global__ void adj_copy_kernel(DevForest<real> D, real* lam) {
         const PatchMeta& nm = st.m0[r];
         const int lx = gx - nm.x * MX, ly = gy - nm.y * MX;
         if (lx < 0 || lx >= MX || ly < 0 || ly >= MX) continue;
-        atomicAdd(lam + (size_t)e.n0 * S * S + (ly + kMbc) * S + lx + kMbc, lg);
+        adj_src_add(lam, lamO, nm.level == tlevel, alpha,
+                    (size_t)e.n0 * S * S + (ly + kMbc) * S + lx + kMbc, lg);
       } else {
         int n = e.n0;
         const PatchMeta* nm = &st.m0[r];
@@ -425,11 +458,45 @@ __global__ void adj_copy_kernel(DevForest<real> D, real* lam) {
           if (lx < 0 || lx >= MX || ly < 0 || ly >= MX) continue;
         }
         for (int q = 0; q < 4; ++q)
-          atomicAdd(lam + (size_t)n * S * S + (ly + (q >> 1) + kMbc) * S + lx + (q & 1) + kMbc,
-                    real(0.25) * lg);
+          adj_src_add(lam, lamO, nm->level == tlevel, alpha,
+                      (size_t)n * S * S + (ly + (q >> 1) + kMbc) * S + lx + (q & 1) + kMbc,
+                      real(0.25) * lg);
       }
     }
     __syncthreads();
+  }
+}
+
+// multirate: adjoint of the level's new interior plus that of its previous
+// state (the copy q_old = q taken before the update), whose old value is dead
+template <typename real, int MX>
+__global__ void adj_combine_kernel(real* lam, real* lamO, int p0, int p1) {
+  constexpr int S = MX + 4;
+  for (int p = p0 + blockIdx.x; p < p1; p += gridDim.x)
+    for (int k = threadIdx.x; k < MX * MX; k += blockDim.x) {
+      const size_t o = (size_t)p * S * S + (k / MX + 2) * S + k % MX + 2;
+      lam[o] += lamO[o];
+      lamO[o] = real(0);
+    }
+}
+
+// multirate: transpose of qT = (1 - alpha) q_old + alpha q on the coarse
+// patches read through qT (each listed once); clears their qT adjoint tiles
+template <typename real, int MX>
+__global__ void adj_time_kernel(const int* targets, int n, real alpha, real* lam, real* lamO,
+                                real* lamT) {
+  constexpr int S = MX + 4;
+  for (int t = blockIdx.x; t < n; t += gridDim.x) {
+    const size_t base = (size_t)targets[t] * S * S;
+    for (int k = threadIdx.x; k < S * S; k += blockDim.x) {
+      const int i = k % S - 2, j = k / S - 2;
+      const real v = lamT[base + k];
+      lamT[base + k] = real(0);
+      if (i >= 0 && i < MX && j >= 0 && j < MX) {
+        lamO[base + k] += (real(1) - alpha) * v;
+        lam[base + k] += alpha * v;
+      }
+    }
   }
 }
 
@@ -441,9 +508,12 @@ constexpr size_t adj_smem() {
 
 inline int grid_for(int n) { return n < 1 ? 1 : (n < 65535 * 8 ? n : 65535 * 8); }
 
+// transpose of the update of level L's patches [p0, p1) over (t, t + dt)
 template <typename real, int MX>
-cudaError_t adjoint_mx(const DevForest<real>& D, const AdjArgs& g, const real* lam_in,
-                       real* lam_out, double* dscale, cudaStream_t s) {
+cudaError_t adj_advance_level(const DevForest<real>& D, int L, int p0, int p1, double t, double dt,
+                              double period, double scale, double dfac, const real* lam_in,
+                              real* lam_out, double* dscale, cudaStream_t s,
+                              const double* t0_dev = nullptr) {
   constexpr int NT = 256;
   static bool attr = false;
   constexpr size_t smem = adj_smem<real, MX>();
@@ -453,37 +523,105 @@ cudaError_t adjoint_mx(const DevForest<real>& D, const AdjArgs& g, const real* l
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  // one launch per level (per-level h and dt/h); all read the pre-step state
-  for (int L = 0; L <= kMaxLevel; ++L) {
-    const int p0 = g.lev_start[L], p1 = g.lev_start[L + 1];
-    if (p1 <= p0) continue;
-    AdvArgs al{};
-    al.h = ldexp(1.0, -L) / MX;
-    al.nu = g.dt / al.h;
-    al.period = g.period;
-    al.t_half = g.t + 0.5 * g.dt;
-    al.sfac = D.vel_kind == FC_VEL_SWIRL ? g.scale * sin(M_PI * al.h) / (M_PI * al.h) : 0.0;
-    adj_advance_kernel<real, MX, NT><<<p1 - p0, NT, smem, s>>>(D, al, lam_in, lam_out, dscale,
-                                                                 g.dscale_factor, p0, p1);
-    ++launch_counter();
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-  }
-  if (g.ncoarse > 0) {
-    adj_interp_kernel<real, MX><<<grid_for(g.ncoarse), 128, 0, s>>>(D, g.coarse_list, g.ncoarse,
-                                                                     lam_out);
-    ++launch_counter();
-  }
-  if (D.domain == FC_DOMAIN_WALLS) {
-    adj_bc_kernel<real, MX><<<grid_for(D.npatch), 128, 0, s>>>(D, lam_out);
-    ++launch_counter();
-  }
-  adj_copy_kernel<real, MX><<<grid_for(D.npatch), 128, 0, s>>>(D, lam_out);
+  if (p1 <= p0) return cudaSuccess;
+  AdvArgs al{};
+  al.h = ldexp(1.0, -L) / MX;
+  al.nu = dt / al.h;
+  al.period = period;
+  al.t_half = t + 0.5 * dt;
+  al.t_off = t + 0.5 * dt;  // with t0_dev: t is relative to the replayed step's start
+  al.t0_dev = t0_dev;
+  al.sfac = D.vel_kind == FC_VEL_SWIRL ? scale * sin(M_PI * al.h) / (M_PI * al.h) : 0.0;
+  adj_advance_kernel<real, MX, NT><<<p1 - p0, NT, smem, s>>>(D, al, lam_in, lam_out, dscale, dfac,
+                                                               p0, p1);
   ++launch_counter();
   return cudaGetLastError();
 }
 
+template <typename real, int MX>
+cudaError_t adjoint_mx(const DevForest<real>& D, const AdjArgs& g, const real* lam_in,
+                       real* lam_out, double* dscale, cudaStream_t s) {
+  // one launch per level (per-level h and dt/h); all read the pre-step state
+  for (int L = 0; L <= kMaxLevel; ++L) {
+    cudaError_t e = adj_advance_level<real, MX>(D, L, g.lev_start[L], g.lev_start[L + 1], g.t,
+                                                g.dt, g.period, g.scale, g.dscale_factor, lam_in,
+                                                lam_out, dscale, s);
+    if (e != cudaSuccess) return e;
+  }
+  if (g.ncoarse > 0) {
+    adj_interp_kernel<real, MX><<<grid_for(g.ncoarse), 128, 0, s>>>(D, g.coarse_list, g.ncoarse,
+                                                                     lam_out, -1, nullptr);
+    ++launch_counter();
+  }
+  if (D.domain == FC_DOMAIN_WALLS) {
+    adj_bc_kernel<real, MX><<<grid_for(D.npatch), 128, 0, s>>>(D, lam_out, nullptr, 0, D.npatch);
+    ++launch_counter();
+  }
+  adj_copy_kernel<real, MX><<<grid_for(D.npatch), 128, 0, s>>>(D, lam_out, nullptr, 0, D.npatch,
+                                                                 -1, real(0), nullptr, nullptr);
+  ++launch_counter();
+  return cudaGetLastError();
+}
+
+// adjoint of one multirate substep of level L (see launch_adjoint_substep)
+template <typename real, int MX>
+cudaError_t adjoint_sub_mx(const DevForest<real>& D, const AdjSubArgs& g, real* lam, real* lamO,
+                           real* lamT, double* dscale, cudaStream_t s) {
+  const int n = g.p1 - g.p0;
+  const bool walls = D.domain == FC_DOMAIN_WALLS;
+  const real alpha = real(g.alpha);
+  cudaError_t e = adj_advance_level<real, MX>(D, g.L, g.p0, g.p1, g.t, g.dt, g.period, g.scale,
+                                              g.dscale_factor, lam, lam, dscale, s, g.t0_dev);
+  if (e != cudaSuccess || n <= 0) return e;
+  adj_combine_kernel<real, MX><<<grid_for(n), 128, 0, s>>>(lam, lamO, g.p0, g.p1);
+  ++launch_counter();
+  if (walls) {  // phase 4
+    adj_bc_kernel<real, MX><<<grid_for(n), 128, 0, s>>>(D, lam, nullptr, g.p0, n);
+    ++launch_counter();
+  }
+  if (g.nb > 0) {  // phase 3
+    adj_interp_kernel<real, MX><<<grid_for(g.nb), 128, 0, s>>>(D, g.list_b, g.nb, lam, g.tlevel,
+                                                               lamT);
+    ++launch_counter();
+  }
+  if (walls) {  // phase 2
+    adj_bc_kernel<real, MX><<<grid_for(n), 128, 0, s>>>(D, lam, nullptr, g.p0, n);
+    ++launch_counter();
+    if (g.nt > 0) {
+      adj_bc_kernel<real, MX><<<grid_for(g.nt), 128, 0, s>>>(D, lamT, g.list_t, 0, g.nt);
+      ++launch_counter();
+    }
+  }
+  // phase 1 on the coarse patches read through qT and on level L
+  adj_copy_kernel<real, MX><<<grid_for(g.na), 128, 0, s>>>(D, lam, g.list_a, 0, g.na, g.tlevel,
+                                                           alpha, lamT, lamO);
+  ++launch_counter();
+  if (g.nt > 0) {
+    adj_time_kernel<real, MX><<<grid_for(g.nt), 128, 0, s>>>(g.list_t, g.nt, alpha, lam, lamO,
+                                                             lamT);
+    ++launch_counter();
+  }
+  return cudaGetLastError();
+}
+
 }  // namespace
+
+template <typename real>
+cudaError_t launch_adjoint_substep(const DevForest<real>& D, const AdjSubArgs& g, real* lam,
+                                   real* lamO, real* lamT, double* dscale, cudaStream_t s) {
+  switch (D.mx) {
+    case 8: return adjoint_sub_mx<real, 8>(D, g, lam, lamO, lamT, dscale, s);
+    case 16: return adjoint_sub_mx<real, 16>(D, g, lam, lamO, lamT, dscale, s);
+    case 32: return adjoint_sub_mx<real, 32>(D, g, lam, lamO, lamT, dscale, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+template cudaError_t launch_adjoint_substep<float>(const DevForest<float>&, const AdjSubArgs&,
+                                                   float*, float*, float*, double*, cudaStream_t);
+template cudaError_t launch_adjoint_substep<double>(const DevForest<double>&, const AdjSubArgs&,
+                                                    double*, double*, double*, double*,
+                                                    cudaStream_t);
 
 template <typename real>
 cudaError_t launch_adjoint_step(const DevForest<real>& D, const AdjArgs& g, const real* lam_in,

@@ -1,6 +1,8 @@
 // C ABI (include/fc.h): forest lifetime, device store, and the time-stepping
 // scheduler (Alg. 1 fills, global and multirate level substeps, regrid).
 #include <algorithm>
+#include <functional>
+#include <tuple>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -109,6 +111,18 @@ struct fc_forest {
   double vel_scale = 1.0;                 // multiplies every edge speed
   double* d_metric = nullptr;             // cubed sphere: FP64 metric blocks per patch
   void* lam[2] = {nullptr, nullptr};      // adjoint tiles (patch-store layout), lazily allocated
+  void* madj[3] = {nullptr, nullptr, nullptr};  // multirate adjoint: current, previous, qT tiles
+  void* mio = nullptr;                    // multirate adjoint: lam in field layout (graph input)
+  double* d_ds = nullptr;                 // multirate adjoint: the step's dscale (graph output)
+  void* msnap = nullptr;                  // multirate adjoint: the start state, then the filled
+  size_t msnap_bytes = 0;                 // tiles of every substep
+  struct AdjGraph {
+    cudaGraphExec_t exec = nullptr;
+    double dt = 0.0;
+    int cur[kMaxLevel + 1] = {0};
+    uint64_t kernels = 0;
+  };
+  std::vector<AdjGraph> adj_graphs;       // captured adjoint coarse steps, valid for one layout
   cudaStream_t cap_stream = nullptr;
   double* d_t0 = nullptr;  // start time of the replayed coarse step
   std::vector<Graph> graphs;
@@ -189,6 +203,9 @@ void destroy_graphs(fc_forest* F) {
     for (auto& p : g.pairs) F->spare.push_back(p);
   }
   F->graphs.clear();
+  for (auto& g : F->adj_graphs)
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+  F->adj_graphs.clear();
 }
 
 void destroy_timers(fc_forest* F) {
@@ -220,6 +237,11 @@ void free_device(fc_forest* F) {
   dfree(F->d_t0);
   dfree(F->lam[0]);
   dfree(F->lam[1]);
+  for (auto& b : F->madj) dfree(b);
+  dfree(F->mio);
+  dfree(F->d_ds);
+  dfree(F->msnap);
+  F->msnap_bytes = 0;
   dfree(F->d_metric);
 }
 
@@ -772,7 +794,200 @@ static fc_status adjoint_step_t(fc_forest* F, double t, double dt, void* lam, do
   return FC_OK;
 }
 
+// Adjoint of one coarse multirate step (the coarse-first recursion of
+// fc_step_multirate).  The forward step is replayed once, keeping after each
+// substep's fill the level's ghost-filled tiles and the time-interpolated
+// coarse tiles (qT) it read; the substeps are then reversed, each on its kept
+// tiles.  The whole sequence is captured once per (layout, dt, buffer
+// parity) as a CUDA graph and replayed; the step's start time, lam and
+// dscale pass through device buffers of the forest.  The forest is left at
+// the step's start state.
+template <typename real>
+static fc_status capture_adjoint_multirate(fc_forest* F, double dtc, cudaStream_t cs,
+                                           fc_forest::AdjGraph* out) {
+  const HostForest& H = F->host;
+  const int lmin = H.desc.lmin, lmax = H.desc.lmax;
+  const size_t S2 = (size_t)(H.desc.mx + 2 * kMbc) * (H.desc.mx + 2 * kMbc);
+  const size_t tile = S2 * sizeof(real);
+  const size_t cells = std::max<size_t>((size_t)H.npatch() * S2, 1);
+  struct Sub {
+    int L;
+    double t, dt, alpha;  // t relative to the step's start
+    size_t offq, offt;    // byte offsets of the kept level-L tiles and qT tiles
+    int cur[kMaxLevel + 1];
+  };
+  std::vector<Sub> subs;
+  std::function<void(int, double, double, double)> rec = [&](int L, double t, double dt,
+                                                               double alpha) {
+    subs.push_back(Sub{L, t, dt, alpha, 0, 0, {0}});
+    if (L < lmax) {
+      rec(L + 1, t, 0.5 * dt, 0.0);
+      rec(L + 1, t + 0.5 * dt, 0.5 * dt, 0.5);
+    }
+  };
+  rec(lmin, 0.0, dtc, 0.0);
+  const size_t store = cells * sizeof(real);
+  size_t need = 2 * store;  // the start state: both stores
+  for (auto& u : subs) {
+    u.offq = need;
+    need += (size_t)(H.lev_start[u.L + 1] - H.lev_start[u.L]) * tile;
+    u.offt = need;
+    if (u.L > lmin) need += (size_t)(H.lev_start[u.L] - H.lev_start[u.L - 1]) * tile;
+  }
+  for (auto& b : F->madj)
+    if (!b && cudaMalloc(&b, cells * sizeof(real)) != cudaSuccess)
+      return fail(FC_ERR_OOM, "adjoint buffer allocation failed");
+  if (!F->mio && cudaMalloc(&F->mio, std::max<size_t>((size_t)H.npatch() * H.desc.mx *
+                                                          H.desc.mx, 1) * sizeof(real)) !=
+                     cudaSuccess)
+    return fail(FC_ERR_OOM, "adjoint buffer allocation failed");
+  if (!F->d_ds) FC_CUDA(dmalloc(&F->d_ds, 1));
+  if (need > F->msnap_bytes) {
+    dfree(F->msnap);
+    F->msnap_bytes = 0;
+    if (cudaMalloc(&F->msnap, need) != cudaSuccess)
+      return fail(FC_ERR_OOM, "adjoint state allocation failed");
+    F->msnap_bytes = need;
+  }
+  char* pool = static_cast<char*>(F->msnap);
+  real* LQ = static_cast<real*>(F->madj[0]);
+  real* LO = static_cast<real*>(F->madj[1]);
+  real* LT = static_cast<real*>(F->madj[2]);
+  int cur0[kMaxLevel + 1];
+  std::copy(F->cur, F->cur + kMaxLevel + 1, cur0);
+  const uint64_t launches_before = launch_counter();
+  FC_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+  auto body = [&]() -> cudaError_t {
+    cudaError_t e = cudaSuccess;
+    auto cp = [&](void* dst, const void* src, size_t n) {
+      if (e == cudaSuccess && n > 0) e = cudaMemcpyAsync(dst, src, n, cudaMemcpyDeviceToDevice, cs);
+    };
+    auto tiles = [&](void* base, int p) { return static_cast<char*>(base) + (size_t)p * tile; };
+    cp(pool, F->buf[0], store);
+    cp(pool + store, F->buf[1], store);
+    // forward replay; after each fill keep level L's tiles and the qT tiles of L-1
+    for (auto& u : subs) {
+      std::copy(F->cur, F->cur + kMaxLevel + 1, u.cur);
+      const int p0 = H.lev_start[u.L], p1 = H.lev_start[u.L + 1];
+      if (p1 <= p0) continue;
+      DevForest<real> D = dev<real>(F);
+      const int tl = u.L > lmin ? u.L - 1 : -1;
+      FillArgs A{F->d_lists + F->off_a[u.L], (int)H.list_a[u.L].size(), tl, u.alpha};
+      FillArgs B{F->d_lists + F->off_b[u.L], (int)H.list_b[u.L].size(), tl, u.alpha};
+      if (e == cudaSuccess) e = launch_fill_coarse(D, A, cs);
+      if (e == cudaSuccess) e = launch_fill_fine(D, B, cs);
+      cp(pool + u.offq, tiles(F->buf[F->cur[u.L]], p0), (size_t)(p1 - p0) * tile);
+      if (tl >= 0)
+        cp(pool + u.offt, tiles(F->qT, H.lev_start[tl]),
+           (size_t)(H.lev_start[u.L] - H.lev_start[tl]) * tile);
+      AdvArgs a = adv_args(F, u.L, u.t, u.dt, p1 - p0);  // the forward's kernel choice
+      a.t0_dev = F->d_t0;
+      a.t_off = u.t + 0.5 * u.dt;
+      if (e == cudaSuccess) e = launch_advance(D, p0, p1, a, F->d_err, cs);
+      F->cur[u.L] ^= 1;
+    }
+    if (e == cudaSuccess) e = cudaMemsetAsync(LQ, 0, cells * sizeof(real), cs);
+    if (e == cudaSuccess) e = cudaMemsetAsync(LO, 0, cells * sizeof(real), cs);
+    if (e == cudaSuccess) e = cudaMemsetAsync(LT, 0, cells * sizeof(real), cs);
+    if (e == cudaSuccess) e = cudaMemsetAsync(F->d_ds, 0, sizeof(double), cs);
+    DevForest<real> Lv = dev<real>(F);
+    Lv.buf[0] = Lv.buf[1] = LQ;
+    for (int l = 0; l <= kMaxLevel; ++l) Lv.cur[l] = 0;
+    if (e == cudaSuccess)
+      e = launch_unpack(Lv, F->d_api_to_dev, static_cast<const real*>(F->mio), cs);
+    for (size_t k = subs.size(); k-- > 0 && e == cudaSuccess;) {
+      const Sub& u = subs[k];
+      const int p0 = H.lev_start[u.L], p1 = H.lev_start[u.L + 1];
+      if (p1 <= p0) continue;
+      std::copy(u.cur, u.cur + kMaxLevel + 1, F->cur);
+      cp(tiles(F->buf[F->cur[u.L]], p0), pool + u.offq, (size_t)(p1 - p0) * tile);
+      const int tl = u.L > lmin ? u.L - 1 : -1;
+      if (tl >= 0)
+        cp(tiles(F->qT, H.lev_start[tl]), pool + u.offt,
+           (size_t)(H.lev_start[u.L] - H.lev_start[tl]) * tile);
+      AdjSubArgs g{};
+      g.L = u.L;
+      g.p0 = p0;
+      g.p1 = p1;
+      g.t = u.t;
+      g.dt = u.dt;
+      g.t0_dev = F->d_t0;
+      g.period = H.desc.vel[0];
+      g.scale = F->vel_scale;
+      g.dscale_factor = F->vel_scale != 0.0 ? 1.0 / F->vel_scale : 0.0;
+      g.tlevel = tl;
+      g.alpha = u.alpha;
+      g.list_a = F->d_lists + F->off_a[u.L];
+      g.na = (int)H.list_a[u.L].size();
+      g.list_b = F->d_lists + F->off_b[u.L];
+      g.nb = (int)H.list_b[u.L].size();
+      g.list_t = F->d_lists + F->off_t[u.L];
+      g.nt = (int)H.list_t[u.L].size();
+      if (e == cudaSuccess) e = launch_adjoint_substep(dev<real>(F), g, LQ, LO, LT, F->d_ds, cs);
+    }
+    if (e == cudaSuccess) e = launch_pack(Lv, F->d_api_to_dev, static_cast<real*>(F->mio), 0, cs);
+    cp(F->buf[0], pool, store);
+    cp(F->buf[1], pool + store, store);
+    return e;
+  };
+  const cudaError_t eb = body();
+  cudaGraph_t graph = nullptr;
+  const cudaError_t ee = cudaStreamEndCapture(cs, &graph);
+  out->kernels = launch_counter() - launches_before;  // counted when replayed
+  launch_counter() = launches_before;
+  std::copy(cur0, cur0 + kMaxLevel + 1, F->cur);
+  if (eb != cudaSuccess || ee != cudaSuccess) {
+    if (graph) cudaGraphDestroy(graph);
+    return cuda_fail(eb != cudaSuccess ? eb : ee, "adjoint capture");
+  }
+  const cudaError_t ei = cudaGraphInstantiate(&out->exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (ei != cudaSuccess) return cuda_fail(ei, "cudaGraphInstantiate");
+  out->dt = dtc;
+  std::copy(cur0, cur0 + kMaxLevel + 1, out->cur);
+  return FC_OK;
+}
+
+template <typename real>
+static fc_status adjoint_multirate_t(fc_forest* F, double t0, double dtc, void* lam,
+                                     double* dscale, cudaStream_t s) {
+  fc_forest::AdjGraph* g = nullptr;
+  for (auto& c : F->adj_graphs)
+    if (c.dt == dtc && std::equal(c.cur, c.cur + kMaxLevel + 1, F->cur)) g = &c;
+  if (!g) {
+    if (!F->cap_stream)
+      FC_CUDA(cudaStreamCreateWithFlags(&F->cap_stream, cudaStreamNonBlocking));
+    fc_forest::AdjGraph ng;
+    fc_status st = capture_adjoint_multirate<real>(F, dtc, F->cap_stream, &ng);
+    if (st != FC_OK) return st;
+    F->adj_graphs.push_back(ng);
+    g = &F->adj_graphs.back();
+  }
+  const size_t nbytes = (size_t)F->host.npatch() * F->host.desc.mx * F->host.desc.mx * sizeof(real);
+  FC_CUDA(cudaMemcpyAsync(F->mio, lam, nbytes, cudaMemcpyDeviceToDevice, s));
+  FC_CUDA(launch_set_time(F->d_t0, t0, s));
+  FC_CUDA(cudaGraphLaunch(g->exec, s));
+  launch_counter() += g->kernels;
+  FC_CUDA(cudaMemcpyAsync(lam, F->mio, nbytes, cudaMemcpyDeviceToDevice, s));
+  FC_CUDA(launch_add_double(dscale, F->d_ds, s));
+  reset_times(F);  // the state is the step's start state again
+  return FC_OK;
+}
+
 extern "C" {
+
+fc_status fc_adjoint_step_multirate(fc_forest* F, double t, double dt_coarse, void* lam,
+                                    double* dscale, void* stream) {
+  if (!F || !lam || !dscale) return fail(FC_ERR_INVALID_ARG, "null argument");
+  if (!(dt_coarse > 0.0)) return fail(FC_ERR_INVALID_ARG, "dt must be positive");
+  if (F->host.desc.domain == FC_DOMAIN_SPHERE)
+    return fail(FC_ERR_INVALID_ARG, "the adjoint is built for the square domains");
+  cudaStream_t s = as_stream(stream);
+  fc_status st = F->esize == 4 ? adjoint_multirate_t<float>(F, t, dt_coarse, lam, dscale, s)
+                               : adjoint_multirate_t<double>(F, t, dt_coarse, lam, dscale, s);
+  if (st != FC_OK) return st;
+  return check_device_error(F, s);
+}
 
 fc_status fc_adjoint_step_global(fc_forest* F, double t, double dt, void* lam, double* dscale,
                                  void* stream) {

@@ -175,6 +175,8 @@ cudaError_t launch_advance_walk(const DevForest<real>& D, int p0, int p1, const 
                                 int* err, cudaStream_t s);
 
 cudaError_t launch_set_time(double* t0_dev, double t0, cudaStream_t s);
+// *dst += *src (one thread; device doubles)
+cudaError_t launch_add_double(double* dst, const double* src, cudaStream_t s);
 
 // Adjoint of one global step (t -> t + dt): per-level update transposes, then
 // the transpose of Alg. 1 (interpolation, boundary condition, copy/average).
@@ -187,6 +189,28 @@ struct AdjArgs {
 template <typename real>
 cudaError_t launch_adjoint_step(const DevForest<real>& D, const AdjArgs& g, const real* lam_in,
                                 real* lam_out, double* dscale, cudaStream_t s);
+
+// Adjoint of one multirate substep of level L over (t, t + dt), on the
+// forward state before it (ghosts of the substep's fill in place, qT filled):
+// lam (adjoint of the current states, patch-store tiles), lamO (adjoint of
+// the previous states), lamT (adjoint of the qT tiles, zero on entry and on
+// return).  tlevel = L - 1 with weight alpha, or -1 on the coarsest level.
+struct AdjSubArgs {
+  int L, p0, p1;  // level and its device range
+  double t, dt, period, scale, dscale_factor;
+  const double* t0_dev;  // set: t is relative to the time stored there (graph replay)
+  int tlevel;
+  double alpha;
+  const int* list_a;  // device: list_t then level L's patches (the substep's fill targets)
+  int na;
+  const int* list_b;  // device: level-L patches with a coarser neighbour
+  int nb;
+  const int* list_t;  // device: level L-1 patches read through qT
+  int nt;
+};
+template <typename real>
+cudaError_t launch_adjoint_substep(const DevForest<real>& D, const AdjSubArgs& g, real* lam,
+                                   real* lamO, real* lamT, double* dscale, cudaStream_t s);
 
 // device error word bits
 constexpr int kErrTimeout = 1;

@@ -184,6 +184,16 @@ class Forest:
         check(load().fc_adjoint_step_global(self._h, t, dt, ctypes.c_void_p(lam.data_ptr()),
                                             ctypes.c_void_p(dscale.data_ptr()), _stream(stream)))
 
+    def adjoint_step_multirate(self, t: float, dt_coarse: float, lam, dscale, stream=None):
+        """Adjoint of one coarse multirate step from the current state (left
+        unchanged): lam (CUDA tensor, field layout) in place, dscale += the
+        velocity-scale derivative (CUDA float64 tensor, 1 element)."""
+        assert lam.is_cuda and lam.is_contiguous() and dscale.is_cuda
+        check(load().fc_adjoint_step_multirate(self._h, t, dt_coarse,
+                                               ctypes.c_void_p(lam.data_ptr()),
+                                               ctypes.c_void_p(dscale.data_ptr()),
+                                               _stream(stream)))
+
     def fused_fill(self, enable: bool = True):
         """Multirate substeps fill each patch's ghosts inside the update kernel (default on)."""
         check(load().fc_set_fused_fill(self._h, 1 if enable else 0))
