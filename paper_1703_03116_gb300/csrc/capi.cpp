@@ -32,16 +32,49 @@ fc_status cuda_fail(cudaError_t e, const char* where) {
     if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
   } while (0)
 
+// Device memory of a forest comes from the stream-ordered allocator: a
+// regrid allocates the new layout's store and frees the old one without
+// synchronising the device, and the pool keeps freed blocks for the next
+// regrid.  Allocations and frees are ordered on the calling thread's current
+// allocation stream (the API call's stream while a regrid runs).
+thread_local cudaStream_t g_alloc_stream = 0;
+
+struct AllocStream {
+  explicit AllocStream(cudaStream_t s) : prev_(g_alloc_stream) { g_alloc_stream = s; }
+  ~AllocStream() { g_alloc_stream = prev_; }
+
+ private:
+  cudaStream_t prev_;
+};
+
+// keep freed blocks in the device's default pool (per process)
+void keep_pool_memory() {
+  static thread_local int done_for = -1;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev == done_for) return;
+  cudaMemPool_t pool;
+  if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+    uint64_t keep = UINT64_MAX;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+  }
+  done_for = dev;
+}
+
 template <typename T>
 cudaError_t dmalloc(T** p, size_t n) {
   *p = nullptr;
   if (n == 0) n = 1;
-  return cudaMalloc((void**)p, n * sizeof(T));
+  return cudaMallocAsync((void**)p, n * sizeof(T), g_alloc_stream);
+}
+
+cudaError_t dmalloc_bytes(void** p, size_t bytes) {
+  *p = nullptr;
+  return cudaMallocAsync(p, bytes ? bytes : 1, g_alloc_stream);
 }
 
 template <typename T>
 void dfree(T*& p) {
-  if (p) cudaFree((void*)p);
+  if (p) cudaFreeAsync((void*)p, g_alloc_stream);
   p = nullptr;
 }
 
@@ -98,6 +131,13 @@ struct fc_forest {
     std::vector<TimerPair> pairs;
   };
   bool use_graphs = true;
+  // while a coarse step is captured: the coarse-neighbour fill of each
+  // substep runs on a side stream, forked where its inputs are ready (the
+  // graph becomes a DAG whose critical path is the chain of updates)
+  bool dag = false;
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_pre[kMaxLevel + 1] = {}, ev_post[kMaxLevel + 1] = {}, ev_fill[kMaxLevel + 1] = {};
+  bool pre_ok[kMaxLevel + 1] = {}, post_ok[kMaxLevel + 1] = {};
   // autotuned patch-update configuration per launch size (bucket = log2 of
   // the patches in one launch): variant and warps per CTA
   struct Tune {
@@ -259,8 +299,8 @@ fc_status update_metrics(fc_forest* F, const RemapEntry* rm = nullptr,
     return fail(FC_ERR_OOM, "metric allocation failed");
   const double w[3] = {F->vel_scale * H.desc.vel[0], F->vel_scale * H.desc.vel[1],
                        F->vel_scale * H.desc.vel[2]};
-  FC_CUDA(launch_sphere_metrics(F->d_meta, n, H.desc.mx, w, F->d_metric, rm, old, 0));
-  FC_CUDA(cudaStreamSynchronize(0));
+  FC_CUDA(launch_sphere_metrics(F->d_meta, n, H.desc.mx, w, F->d_metric, rm, old,
+                                g_alloc_stream));
   return FC_OK;
 }
 
@@ -274,16 +314,17 @@ fc_status upload(fc_forest* F, bool alloc_store, bool metrics = true) {
   if (alloc_store) {
     for (int b = 0; b < 2; ++b) {
       dfree(F->buf[b]);
-      if (cudaMalloc(&F->buf[b], std::max<size_t>(cells, 1) * F->esize) != cudaSuccess)
+      if (dmalloc_bytes(&F->buf[b], std::max<size_t>(cells, 1) * F->esize) != cudaSuccess)
         return fail(FC_ERR_OOM, "device store allocation failed");
-      FC_CUDA(cudaMemset(F->buf[b], 0, std::max<size_t>(cells, 1) * F->esize));
+      FC_CUDA(cudaMemsetAsync(F->buf[b], 0, std::max<size_t>(cells, 1) * F->esize,
+                              g_alloc_stream));
     }
     dfree(F->qT);
     dfree(F->stage);
-    if (cudaMalloc(&F->qT, std::max<size_t>(cells, 1) * F->esize) != cudaSuccess ||
-        cudaMalloc(&F->stage, std::max<size_t>(cells, 1) * F->esize) != cudaSuccess)
+    if (dmalloc_bytes(&F->qT, std::max<size_t>(cells, 1) * F->esize) != cudaSuccess ||
+        dmalloc_bytes(&F->stage, std::max<size_t>(cells, 1) * F->esize) != cudaSuccess)
       return fail(FC_ERR_OOM, "device store allocation failed");
-    FC_CUDA(cudaMemset(F->qT, 0, std::max<size_t>(cells, 1) * F->esize));
+    FC_CUDA(cudaMemsetAsync(F->qT, 0, std::max<size_t>(cells, 1) * F->esize, g_alloc_stream));
   }
   dfree(F->d_meta);
   dfree(F->d_nbr);
@@ -295,8 +336,11 @@ fc_status upload(fc_forest* F, bool alloc_store, bool metrics = true) {
   dfree(F->d_delta);
   FC_CUDA(dmalloc(&F->d_meta, n));
   FC_CUDA(dmalloc(&F->d_nbr, (size_t)n * 8));
-  FC_CUDA(cudaMemcpy(F->d_meta, H.meta.data(), sizeof(PatchMeta) * n, cudaMemcpyHostToDevice));
-  FC_CUDA(cudaMemcpy(F->d_nbr, H.nbr.data(), sizeof(NbrEntry) * n * 8, cudaMemcpyHostToDevice));
+  // (host sources are pageable: each copy has taken its data when it returns)
+  FC_CUDA(cudaMemcpyAsync(F->d_meta, H.meta.data(), sizeof(PatchMeta) * n, cudaMemcpyHostToDevice,
+                          g_alloc_stream));
+  FC_CUDA(cudaMemcpyAsync(F->d_nbr, H.nbr.data(), sizeof(NbrEntry) * n * 8,
+                          cudaMemcpyHostToDevice, g_alloc_stream));
   std::vector<int> lists;
   F->off_all = lists.size();
   lists.insert(lists.end(), H.list_all.begin(), H.list_all.end());
@@ -312,22 +356,25 @@ fc_status upload(fc_forest* F, bool alloc_store, bool metrics = true) {
   }
   FC_CUDA(dmalloc(&F->d_lists, lists.size()));
   if (!lists.empty())
-    FC_CUDA(cudaMemcpy(F->d_lists, lists.data(), sizeof(int) * lists.size(), cudaMemcpyHostToDevice));
+    FC_CUDA(cudaMemcpyAsync(F->d_lists, lists.data(), sizeof(int) * lists.size(),
+                            cudaMemcpyHostToDevice, g_alloc_stream));
   FC_CUDA(dmalloc(&F->d_api_to_dev, n));
-  FC_CUDA(cudaMemcpy(F->d_api_to_dev, H.dev_of.data(), sizeof(int) * n, cudaMemcpyHostToDevice));
+  FC_CUDA(cudaMemcpyAsync(F->d_api_to_dev, H.dev_of.data(), sizeof(int) * n,
+                          cudaMemcpyHostToDevice, g_alloc_stream));
   FC_CUDA(dmalloc(&F->d_fstart, H.forest_start.size()));
-  FC_CUDA(cudaMemcpy(F->d_fstart, H.forest_start.data(), sizeof(int) * H.forest_start.size(),
-                     cudaMemcpyHostToDevice));
+  FC_CUDA(cudaMemcpyAsync(F->d_fstart, H.forest_start.data(),
+                          sizeof(int) * H.forest_start.size(), cudaMemcpyHostToDevice,
+                          g_alloc_stream));
   FC_CUDA(dmalloc(&F->d_patch_sums, n));
   FC_CUDA(dmalloc(&F->d_mass, H.desc.nforests));
   FC_CUDA(dmalloc(&F->d_delta, n));
   if (!F->d_err) {
     FC_CUDA(dmalloc(&F->d_err, 1));
-    FC_CUDA(cudaMemset(F->d_err, 0, sizeof(int)));
+    FC_CUDA(cudaMemsetAsync(F->d_err, 0, sizeof(int), g_alloc_stream));
   }
   if (!F->d_t0) {
     FC_CUDA(dmalloc(&F->d_t0, 1));
-    FC_CUDA(cudaMemset(F->d_t0, 0, sizeof(double)));
+    FC_CUDA(cudaMemsetAsync(F->d_t0, 0, sizeof(double), g_alloc_stream));
   }
   return metrics ? update_metrics(F) : FC_OK;
 }
@@ -478,7 +525,22 @@ fc_status advance_level_t(fc_forest* F, int L, double t, double dt, cudaStream_t
       // their coarse ghost regions filled); the update kernel then fills
       // each level-L patch's ghost ring in shared memory itself
       FillArgs A{F->d_lists + F->off_t[L], (int)H.list_t[L].size(), tlevel, alpha};
-      {
+      // inside a captured step the fill forks off where its inputs are final:
+      // alpha = 0 reads level L-1's state from before its update and level
+      // L's current one (fork before level L-1's update); alpha = 1/2 waits
+      // for level L's previous substep only
+      const bool fork = F->dag && A.ntargets > 0 && tlevel >= 0 &&
+                        ((alpha == 0.0 && F->pre_ok[L - 1]) ||
+                         (std::fabs(alpha - 0.5) < 1e-9 && F->post_ok[L]));
+      if (fork) {
+        FC_CUDA(cudaStreamWaitEvent(F->side, alpha == 0.0 ? F->ev_pre[L - 1] : F->ev_post[L], 0));
+        {
+          Timed tm(F, 1, F->side, gb * A.ntargets);
+          FC_CUDA(launch_fill_coarse(D, A, F->side));
+        }
+        FC_CUDA(cudaEventRecord(F->ev_fill[L], F->side));
+        FC_CUDA(cudaStreamWaitEvent(s, F->ev_fill[L], 0));
+      } else {
         Timed tm(F, 1, s, gb * A.ntargets);
         FC_CUDA(launch_fill_coarse(D, A, s));
       }
@@ -497,9 +559,17 @@ fc_status advance_level_t(fc_forest* F, int L, double t, double dt, cudaStream_t
         FC_CUDA(launch_fill_fine(D, B, s));
       }
     }
+    if (F->dag) {
+      FC_CUDA(cudaEventRecord(F->ev_pre[L], s));
+      F->pre_ok[L] = true;
+    }
     {
       Timed tm(F, 0, s, advance_bytes(F, p1 - p0));
       FC_CUDA(launch_advance(D, p0, p1, a, F->d_err, s));
+    }
+    if (F->dag) {
+      FC_CUDA(cudaEventRecord(F->ev_post[L], s));
+      F->post_ok[L] = true;
     }
     F->cur[L] ^= 1;
   }
@@ -592,9 +662,12 @@ fc_status fc_forest_create(const fc_forest_desc* desc, int nleaves, const int* l
     delete F;
     return fail(FC_ERR_PRECONDITION, err);
   }
-  st = upload(F, true);
+  keep_pool_memory();
+  st = upload(F, true);  // on the legacy default stream
+  if (st == FC_OK && cudaStreamSynchronize(0) != cudaSuccess) st = cuda_fail(cudaGetLastError(), "create");
   if (st != FC_OK) {
     free_device(F);
+    cudaStreamSynchronize(0);
     delete F;
     return st;
   }
@@ -607,7 +680,14 @@ fc_status fc_forest_destroy(fc_forest* F) {
   cudaDeviceSynchronize();
   destroy_timers(F);
   if (F->cap_stream) cudaStreamDestroy(F->cap_stream);
+  if (F->side) {
+    cudaStreamDestroy(F->side);
+    for (int l = 0; l <= kMaxLevel; ++l)
+      for (cudaEvent_t ev : {F->ev_pre[l], F->ev_post[l], F->ev_fill[l]})
+        if (ev) cudaEventDestroy(ev);
+  }
   free_device(F);
+  cudaStreamSynchronize(0);
   delete F;
   return FC_OK;
 }
@@ -753,7 +833,9 @@ fc_status fc_set_velocity_scale(fc_forest* F, double scale) {
   F->vel_scale = scale;
   destroy_graphs(F);
   FC_CUDA(cudaDeviceSynchronize());  // no launch may still read the old metrics
-  return update_metrics(F);           // sphere: the edge fluxes carry the scale
+  fc_status st = update_metrics(F);   // sphere: the edge fluxes carry the scale
+  if (st == FC_OK) FC_CUDA(cudaStreamSynchronize(0));
+  return st;
 }
 
 }  // extern "C"
@@ -761,11 +843,12 @@ fc_status fc_set_velocity_scale(fc_forest* F, double scale) {
 template <typename real>
 static fc_status adjoint_step_t(fc_forest* F, double t, double dt, void* lam, double* dscale,
                                 cudaStream_t s) {
+  AllocStream alloc_on(s);
   const HostForest& H = F->host;
   const size_t S = (size_t)H.desc.mx + 2 * kMbc;
   const size_t cells = std::max<size_t>((size_t)H.npatch() * S * S, 1);
   for (int b = 0; b < 2; ++b)
-    if (!F->lam[b] && cudaMalloc(&F->lam[b], cells * sizeof(real)) != cudaSuccess)
+    if (!F->lam[b] && dmalloc_bytes(&F->lam[b], cells * sizeof(real)) != cudaSuccess)
       return fail(FC_ERR_OOM, "adjoint buffer allocation failed");
   // the caller's adjoint (field layout) into the interior of lam[0]
   DevForest<real> L = dev<real>(F);
@@ -835,17 +918,17 @@ static fc_status capture_adjoint_multirate(fc_forest* F, double dtc, cudaStream_
     if (u.L > lmin) need += (size_t)(H.lev_start[u.L] - H.lev_start[u.L - 1]) * tile;
   }
   for (auto& b : F->madj)
-    if (!b && cudaMalloc(&b, cells * sizeof(real)) != cudaSuccess)
+    if (!b && dmalloc_bytes(&b, cells * sizeof(real)) != cudaSuccess)
       return fail(FC_ERR_OOM, "adjoint buffer allocation failed");
-  if (!F->mio && cudaMalloc(&F->mio, std::max<size_t>((size_t)H.npatch() * H.desc.mx *
-                                                          H.desc.mx, 1) * sizeof(real)) !=
+  if (!F->mio && dmalloc_bytes(&F->mio, std::max<size_t>((size_t)H.npatch() * H.desc.mx *
+                                                              H.desc.mx, 1) * sizeof(real)) !=
                      cudaSuccess)
     return fail(FC_ERR_OOM, "adjoint buffer allocation failed");
   if (!F->d_ds) FC_CUDA(dmalloc(&F->d_ds, 1));
   if (need > F->msnap_bytes) {
     dfree(F->msnap);
     F->msnap_bytes = 0;
-    if (cudaMalloc(&F->msnap, need) != cudaSuccess)
+    if (dmalloc_bytes(&F->msnap, need) != cudaSuccess)
       return fail(FC_ERR_OOM, "adjoint state allocation failed");
     F->msnap_bytes = need;
   }
@@ -951,6 +1034,7 @@ static fc_status capture_adjoint_multirate(fc_forest* F, double dtc, cudaStream_
 template <typename real>
 static fc_status adjoint_multirate_t(fc_forest* F, double t0, double dtc, void* lam,
                                      double* dscale, cudaStream_t s) {
+  AllocStream alloc_on(s);  // buffers first allocated here are ordered before the replay on s
   fc_forest::AdjGraph* g = nullptr;
   for (auto& c : F->adj_graphs)
     if (c.dt == dtc && std::equal(c.cur, c.cur + kMaxLevel + 1, F->cur)) g = &c;
@@ -1138,13 +1222,22 @@ fc_status fc_step_multirate(fc_forest* F, double t, double dt_coarse, void* stre
     std::copy(F->cur, F->cur + kMaxLevel + 1, ng.cur_before);
     // capture with relative times; the host bookkeeping done while capturing
     // is what one replay does to the state
+    if (!F->side) {
+      FC_CUDA(cudaStreamCreateWithFlags(&F->side, cudaStreamNonBlocking));
+      for (int l = 0; l <= kMaxLevel; ++l)
+        for (cudaEvent_t* ev : {&F->ev_pre[l], &F->ev_post[l], &F->ev_fill[l]})
+          FC_CUDA(cudaEventCreateWithFlags(ev, cudaEventDisableTiming));
+    }
     F->capture_pairs = &ng.pairs;
+    F->dag = true;
+    for (int l = 0; l <= kMaxLevel; ++l) F->pre_ok[l] = F->post_ok[l] = false;
     const uint64_t launches_before = launch_counter();
     FC_CUDA(cudaStreamBeginCapture(F->cap_stream, cudaStreamCaptureModeThreadLocal));
     fc_status st = multirate(F, lmin, 0.0, dt_coarse, F->cap_stream);
     cudaGraph_t graph = nullptr;
     cudaError_t e = cudaStreamEndCapture(F->cap_stream, &graph);
     F->capture_pairs = nullptr;
+    F->dag = false;
     ng.kernels = launch_counter() - launches_before;  // counted when replayed
     launch_counter() = launches_before;
     std::copy(F->cur, F->cur + kMaxLevel + 1, ng.cur_after);
@@ -1221,6 +1314,7 @@ fc_status fc_tag_regrid(fc_forest* F, double tau_refine, double tau_coarsen,
     if (changed) *changed = 0;
     return FC_OK;
   }
+  AllocStream alloc_on(s);  // the new layout's memory and the old one's release, ordered on s
   fc_forest* G = new (std::nothrow) fc_forest();
   if (!G) return fail(FC_ERR_OOM, "host allocation failed");
   G->host.desc = F->host.desc;
@@ -1282,7 +1376,6 @@ fc_status fc_tag_regrid(fc_forest* F, double tau_refine, double tau_coarsen,
   FC_CUDA(cudaMemcpyAsync(G->d_remap, rm.data(), sizeof(RemapEntry) * rm.size(),
                           cudaMemcpyHostToDevice, s));
   if (F->d_metric) {  // the new layout's metrics: kept patches copy theirs
-    FC_CUDA(cudaStreamSynchronize(s));
     st = update_metrics(G, G->d_remap, F->d_metric);
     if (st != FC_OK) {
       free_device(G);
@@ -1297,7 +1390,6 @@ fc_status fc_tag_regrid(fc_forest* F, double tau_refine, double tau_coarsen,
                       : launch_remap(dev<double>(F), dev<double>(G), G->d_remap, s);
   }
   if (e != cudaSuccess) return cuda_fail(e, "remap");
-  FC_CUDA(cudaStreamSynchronize(s));
   // swap contents: F takes G's layout and store; captured steps are stale
   destroy_graphs(F);
   free_device(F);
@@ -1326,6 +1418,7 @@ fc_status fc_tag_regrid(fc_forest* F, double tau_refine, double tau_coarsen,
   reset_times(F);
   delete G;  // its device pointers now belong to F
   if (changed) *changed = created + (n - kept);
+  FC_CUDA(cudaStreamSynchronize(s));  // the new layout is ready for any stream
   return FC_OK;
 }
 

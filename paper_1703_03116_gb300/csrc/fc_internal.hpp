@@ -44,6 +44,9 @@ struct NbrEntry {
   int n0, n1;  // device patch indices; n1 only for a face with two fine patches
   int a;       // orientation code of A
   int fx, fy;  // F
+  // the neighbours' level and quadrant coordinates, copied here so a
+  // kernel gathering ghosts reads one table instead of two dependent ones
+  int lev, x0, y0, x1, y1, pad;
 };
 
 struct PatchMeta {

@@ -220,7 +220,7 @@ std::string HostForest::build() {
     const Leaf& a = leaves[api_of[p]];
     meta[p] = PatchMeta{a.l, a.x, a.y, a.b, a.f, 0};
     for (int dir = 0; dir < 8; ++dir) {
-      NbrEntry e{NB_EXTERIOR, -1, -1, 0, 0, 0};
+      NbrEntry e{NB_EXTERIOR, -1, -1, 0, 0, 0, 0, 0, 0, 0, 0, 0};
       Moved m;
       if (move_quadrant(d, a.b, a.l, a.x + kDirX[dir], a.y + kDirY[dir], mx, &m)) {
         e.a = m.a;
@@ -277,6 +277,17 @@ std::string HostForest::build() {
         }
       } else if (m.corner3) {
         e.kind = NB_CORNER3;
+      }
+      if (e.n0 >= 0) {
+        const Leaf& n0 = leaves[api_of[e.n0]];
+        e.lev = n0.l;
+        e.x0 = n0.x;
+        e.y0 = n0.y;
+      }
+      if (e.n1 >= 0) {
+        const Leaf& n1 = leaves[api_of[e.n1]];
+        e.x1 = n1.x;
+        e.y1 = n1.y;
       }
       nbr[(size_t)p * 8 + dir] = e;
     }

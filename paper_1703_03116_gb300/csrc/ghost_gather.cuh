@@ -23,13 +23,15 @@ struct NbrStage {
 };
 
 // threads tid = 0..7 of a cooperating group stage the entries of patch p
+// (the neighbours' level and coordinates travel in the entries: one read)
 __device__ __forceinline__ void stage_neighbours(const PatchMeta* meta, const NbrEntry* nbr,
                                                  int p, NbrStage& st, int tid) {
+  (void)meta;
   if (tid < 8) {
     const NbrEntry e = nbr[(size_t)p * 8 + tid];
     st.e[tid] = e;
-    if (e.n0 >= 0) st.m0[tid] = meta[e.n0];
-    if (e.n1 >= 0) st.m1[tid] = meta[e.n1];
+    st.m0[tid] = PatchMeta{e.lev, e.x0, e.y0, 0, 0, 0};
+    st.m1[tid] = PatchMeta{e.lev, e.x1, e.y1, 0, 0, 0};
   }
 }
 
@@ -40,7 +42,12 @@ __device__ __forceinline__ real src_interior(const DevForest<real>& D, int tleve
                                              int n, int nlev, int i, int j) {
   const size_t o = (size_t)n * D.S * D.S + (size_t)(j + kMbc) * D.S + (i + kMbc);
   const int c = D.cur[nlev];
-  if (nlev == tlevel) return (real(1) - alpha) * D.buf[c ^ 1][o] + alpha * D.buf[c][o];
+  if (nlev == tlevel) {
+    // alpha = 0 reads the older state alone: the newer one may still be
+    // being written (the fill can run beside the update that makes it)
+    if (alpha == real(0)) return D.buf[c ^ 1][o];
+    return (real(1) - alpha) * D.buf[c ^ 1][o] + alpha * D.buf[c][o];
+  }
   return D.buf[c][o];
 }
 
