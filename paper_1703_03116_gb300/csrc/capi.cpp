@@ -131,6 +131,9 @@ struct fc_forest {
     std::vector<TimerPair> pairs;
   };
   bool use_graphs = true;
+  // untimed executable graphs of a previous layout: a new capture of the same
+  // shape updates one in place instead of instantiating a new one
+  std::vector<cudaGraphExec_t> stale;
   // while a coarse step is captured: the coarse-neighbour fill of each
   // substep runs on a side stream, forked where its inputs are ready (the
   // graph becomes a DAG whose critical path is the chain of updates)
@@ -246,6 +249,21 @@ void destroy_graphs(fc_forest* F) {
   for (auto& g : F->adj_graphs)
     if (g.exec) cudaGraphExecDestroy(g.exec);
   F->adj_graphs.clear();
+  for (auto& x : F->stale) cudaGraphExecDestroy(x);
+  F->stale.clear();
+}
+
+// after a regrid: the captured steps are stale; untimed ones are kept for
+// an in-place update by the next capture
+void retire_graphs(fc_forest* F) {
+  std::vector<cudaGraphExec_t> keep;
+  for (auto& g : F->graphs)
+    if (!g.timing && g.pairs.empty() && g.exec) {
+      keep.push_back(g.exec);
+      g.exec = nullptr;
+    }
+  destroy_graphs(F);
+  F->stale = std::move(keep);
 }
 
 void destroy_timers(fc_forest* F) {
@@ -1248,7 +1266,19 @@ fc_status fc_step_multirate(fc_forest* F, double t, double dt_coarse, void* stre
       return st;
     }
     if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
-    e = cudaGraphInstantiate(&ng.exec, graph, 0);
+    if (!ng.timing)  // same shape as a stale step: update its parameters in place
+      while (!ng.exec && !F->stale.empty()) {
+        cudaGraphExec_t x = F->stale.back();
+        F->stale.pop_back();
+        cudaGraphExecUpdateResultInfo info;
+        if (cudaGraphExecUpdate(x, graph, &info) == cudaSuccess) {
+          ng.exec = x;
+        } else {
+          cudaGetLastError();  // clear the failed update's status
+          cudaGraphExecDestroy(x);
+        }
+      }
+    if (!ng.exec) e = cudaGraphInstantiate(&ng.exec, graph, 0);
     cudaGraphDestroy(graph);
     if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
     F->graphs.push_back(std::move(ng));
@@ -1391,7 +1421,7 @@ fc_status fc_tag_regrid(fc_forest* F, double tau_refine, double tau_coarsen,
   }
   if (e != cudaSuccess) return cuda_fail(e, "remap");
   // swap contents: F takes G's layout and store; captured steps are stale
-  destroy_graphs(F);
+  retire_graphs(F);
   free_device(F);
   F->host = std::move(G->host);
   std::memcpy(F->buf, G->buf, sizeof F->buf);

@@ -359,23 +359,29 @@ void refine_into(LeafSet* s, const Leaf& a) {
 }
 
 // 2:1 balance by refinement: any leaf that holds a quadrant adjacent to a
-// leaf two or more levels finer is refined, until no such leaf remains.
-void balance(LeafSet* s, int mx) {
-  for (;;) {
-    std::unordered_map<uint64_t, Leaf> marks;
-    for (const auto& kv : s->m) {
-      const Leaf& c = kv.second;
-      if (c.l < s->d->lmin + 2) continue;
-      for (int dir = 0; dir < 8; ++dir) {
-        Moved m;
-        if (!move_quadrant(*s->d, c.b, c.l, c.x + kDirX[dir], c.y + kDirY[dir], mx, &m)) continue;
-        Leaf h;
-        int hl = s->holder_level(c.f, m.b, c.l, m.x, m.y, &h);
-        if (hl >= 0 && hl <= c.l - 2) marks.emplace(leaf_key(h.f, h.b, h.l, h.x, h.y), h);
+// leaf two or more levels finer is refined, until no such leaf remains.  The
+// layout before the new refinements was balanced, so only leaves next to new
+// leaves can violate it: a worklist seeded with the new leaves ripples the
+// refinement outwards.  Every leaf refined here is refined in any balanced
+// refinement, so the result is the (unique) coarsest balanced one.
+void balance(LeafSet* s, int mx, std::vector<Leaf> work) {
+  while (!work.empty()) {
+    const Leaf c = work.back();
+    work.pop_back();
+    if (c.l < s->d->lmin + 2 || !s->has(c.f, c.b, c.l, c.x, c.y)) continue;
+    for (int dir = 0; dir < 8; ++dir) {
+      Moved m;
+      if (!move_quadrant(*s->d, c.b, c.l, c.x + kDirX[dir], c.y + kDirY[dir], mx, &m)) continue;
+      Leaf h;
+      int hl = s->holder_level(c.f, m.b, c.l, m.x, m.y, &h);
+      if (hl >= 0 && hl <= c.l - 2) {
+        refine_into(s, h);
+        for (int k = 0; k < 4; ++k)
+          work.push_back(Leaf{h.f, h.b, h.l + 1, 2 * h.x + (k & 1), 2 * h.y + (k >> 1)});
+        work.push_back(c);  // look again: the new holder may still be too coarse
+        break;
       }
     }
-    if (marks.empty()) return;
-    for (const auto& kv : marks) refine_into(s, kv.second);
   }
 }
 
@@ -427,13 +433,17 @@ std::string regrid_layout(const HostForest& F, const std::vector<double>& delta,
   s.m.reserve((size_t)n * 2);
   for (int k = 0; k < n; ++k)
     if (!refine[k]) s.add(F.leaves[k]);
+  std::vector<Leaf> fresh;
   for (int k = 0; k < n; ++k)
     if (refine[k]) {
       const Leaf& a = F.leaves[k];
-      for (int c = 0; c < 4; ++c)
-        s.add(Leaf{a.f, a.b, a.l + 1, 2 * a.x + (c & 1), 2 * a.y + (c >> 1)});
+      for (int c = 0; c < 4; ++c) {
+        const Leaf ch{a.f, a.b, a.l + 1, 2 * a.x + (c & 1), 2 * a.y + (c >> 1)};
+        s.add(ch);
+        fresh.push_back(ch);
+      }
     }
-  balance(&s, d.mx);
+  balance(&s, d.mx, std::move(fresh));
   std::vector<Leaf> accepted;
   for (const Leaf& P : parents) {
     bool all = true;
