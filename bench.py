@@ -55,7 +55,7 @@ def parse():
     ap.add_argument("--dtype", choices=["f32", "f64"], default="f32")
     ap.add_argument("--no-variants", action="store_true", help="skip FP64, batched and CPU legs")
     ap.add_argument("--ensemble", type=int, default=256, help="forests in the batched variant")
-    ap.add_argument("--mode", choices=["full", "batched", "sphere"], default="full",
+    ap.add_argument("--mode", choices=["full", "batched", "sphere", "adjoint"], default="full",
                     help="batched: time only the ensemble (a case sized for profiling)")
     return ap.parse_args()
 
@@ -295,7 +295,9 @@ def adjoint_cost(fc, torch, flush_buf, ncoarse: int = 25):
     K = 5
     t_fwd = timed(lambda: [F.step_multirate(k * dtc, dtc) for k in range(K)]) / K
     F.set_q(q0)
+    torch.cuda.nvtx.range_push("adjoint_steps")  # lets a profiler select these steps
     t_adj = timed(lambda: [F.adjoint_step_multirate(0.0, dtc, lam, ds) for _ in range(K)]) / K
+    torch.cuda.nvtx.range_pop()
     return {"workload": f"swirl forest frozen after the initial regrid ({len(leaves)} patches), "
                         f"{ncoarse} coarse multirate steps = {ncoarse * 16} finest substeps, FP32, "
                         "sqrt(N) checkpoints",
@@ -332,6 +334,13 @@ def run_ours(args):
     hbm = hbm or 6800.0
 
     dtype = fc.F32 if args.dtype == "f32" else fc.F64
+    if args.mode == "adjoint":  # the adjoint cost alone (a case sized for profiling)
+        if rank == 0:
+            print(json.dumps({"variants": {"adjoint": adjoint_cost(fc, torch, flush_buf)}}),
+                  flush=True)
+        if dist is not None:
+            dist.destroy_process_group()
+        return
     if args.mode in ("batched", "sphere"):
         if args.mode == "batched":
             ws = synth.ensemble(args.ensemble, seed=rank, mx=32)

@@ -20,13 +20,13 @@
 //                  Eq. ghost_coarse): ghost adjoints go to the neighbours'
 //                  interior cells (atomic adds).
 //
-// Multirate substep of level L (launch_adjoint_substep): the same transposes
-// restricted to what the substep's fill touched -- level L's update, level
-// L's ghosts, and the ghosts of the level L-1 patches read through the
-// time-interpolation buffer qT -- plus the transposes of the copy
-// q_old = q taken before the update (adj_combine) and of
-// qT = (1 - alpha) q_old + alpha q (adj_time, and inside adj_copy for
-// sources read on the fly).
+// Multirate substep of level L (launch_adjoint_substep), three kernels: the
+// update's transpose plus that of the copy q_old = q taken before it
+// (adj_advance with lamO); the transposes of level L's ghosts, each patch's
+// four phases in one CTA (adj_level_ghosts); the transposes of the ghosts of
+// the level L-1 patches read through the time-interpolated tiles and of
+// qT = (1 - alpha) q_old + alpha q (adj_coarse_tiles; sources read on the fly
+// split their share inside the copy transpose).
 // The adjoint tiles use the patch-store layout ((mx+4)^2 per patch).
 #include "ghost_gather.cuh"
 
@@ -84,11 +84,16 @@ __device__ __forceinline__ EdgeFw<real> edge_fw(int order, int limiter, int tran
   return e;
 }
 
+// The forward tile of patch p is read from the store, or from
+// tiles + (p - tiles_p0) tiles when `tiles` is given (kept copies).  With
+// lamO (multirate) the adjoint of the patch's previous state is added to the
+// new interior adjoint and cleared (the copy q_old = q before the update).
 template <typename real, int MX, int NT>
 __global__ void __launch_bounds__(NT) adj_advance_kernel(DevForest<real> D, AdvArgs a,
                                                          const real* lam_in, real* lam_out,
                                                          double* dscale, double dfac, int p0,
-                                                         int p1) {
+                                                         int p1, const real* tiles, int tiles_p0,
+                                                         real* lamO) {
   constexpr int S = MX + 4;
   constexpr int NE = (MX + 1) * (MX + 2);
   constexpr int NV = MX + 3;
@@ -118,11 +123,15 @@ __global__ void __launch_bounds__(NT) adj_advance_kernel(DevForest<real> D, AdvA
   }
   __syncthreads();
   const real ucoef = swirl ? ucoef_s : real(0);
-  double dsum = 0.0;
+  // velocity-scale derivative: per-thread partial sums in the field's
+  // precision (FP64 arithmetic is scarce on this GPU), FP64 from the block
+  // reduction on
+  real dsum = 0;
 
   for (int p = p0 + blockIdx.x; p < p1; p += gridDim.x) {
     const PatchMeta pm = D.meta[p];
-    const real* src = D.buf[D.cur[pm.level]] + (size_t)p * S * S;
+    const real* src = tiles ? tiles + (size_t)(p - tiles_p0) * S * S
+                            : D.buf[D.cur[pm.level]] + (size_t)p * S * S;
     const real* lin = lam_in + (size_t)p * S * S;
     for (int k = threadIdx.x; k < S * S; k += NT) {
       Q[k] = src[k];
@@ -223,15 +232,15 @@ __global__ void __launch_bounds__(NT) adj_advance_kernel(DevForest<real> D, AdvA
           const int i = k % (MX + 1), j = k / (MX + 1);
           const real s = uvel(i, j);
           const real yl = YS[j * (MX + 2) + i], yr = YS[j * (MX + 2) + i + 1];  // Y(i-1,j), Y(i,j)
-          dsum += -(double)hn * ((s > real(0) ? s : real(0)) * yl + (s < real(0) ? s : real(0)) * yr) *
-                  (double)LF[xe(i, j)];
+          dsum -= hn * ((s > real(0) ? s : real(0)) * yl + (s < real(0) ? s : real(0)) * yr) *
+                  LF[xe(i, j)];
         } else {
           const int f = k - MX * (MX + 1);
           const int i = f % MX, j = f / MX;
           const real s = vvel(i, j);
           const real xb = XS[j * MX + i], xt = XS[(j + 1) * MX + i];  // X(i,j-1), X(i,j)
-          dsum += -(double)hn * ((s > real(0) ? s : real(0)) * xb + (s < real(0) ? s : real(0)) * xt) *
-                  (double)LG[ye(i, j)];
+          dsum -= hn * ((s > real(0) ? s : real(0)) * xb + (s < real(0) ? s : real(0)) * xt) *
+                  LG[ye(i, j)];
         }
       }
     }
@@ -275,18 +284,18 @@ __global__ void __launch_bounds__(NT) adj_advance_kernel(DevForest<real> D, AdvA
       const real sp = s > real(0) ? s : real(0), sm = s < real(0) ? s : real(0);
       const real ip = s > real(0) ? real(1) : real(0), im = s < real(0) ? real(1) : real(0);
       real lFt = lF, lW = 0, lWup = 0;
-      double ds = 0.0;
+      real ds = 0;
       if (transverse > 0) {
         lW += sp * lP + sm * lM;
-        ds += (double)(lP * ip * e.W + lM * im * e.W);
+        ds += lP * ip * e.W + lM * im * e.W;
         if (transverse > 1) lFt += -lP + lM;
       }
       atomicAdd(lb, sp * lF);
       atomicAdd(lc, sm * lF);
-      ds += (double)(lF * (ip * qb + im * qc));
+      ds += lF * (ip * qb + im * qc);
       lW += e.c * e.dW * lFt;
       lWup += e.c * e.dWup * lFt;
-      ds += (double)(lFt * e.dc * e.lim);
+      ds += lFt * e.dc * e.lim;
       atomicAdd(lc, lW);
       atomicAdd(lb, -lW);
       if (e.up) {
@@ -296,7 +305,7 @@ __global__ void __launch_bounds__(NT) adj_advance_kernel(DevForest<real> D, AdvA
         atomicAdd(ld, lWup);
         atomicAdd(lc, -lWup);
       }
-      dsum += ds * (double)s;
+      dsum += ds * s;
     }
     __syncthreads();
     // transpose of the second wall-BC pass
@@ -316,10 +325,23 @@ __global__ void __launch_bounds__(NT) adj_advance_kernel(DevForest<real> D, AdvA
       __syncthreads();
     }
     real* lout = lam_out + (size_t)p * S * S;
-    for (int k = threadIdx.x; k < S * S; k += NT) lout[k] = LQ[k];
+    if (lamO) {
+      real* lo = lamO + (size_t)p * S * S;
+      for (int k = threadIdx.x; k < S * S; k += NT) {
+        const int i = k % S - 2, j = k / S - 2;
+        if (i >= 0 && i < MX && j >= 0 && j < MX) {
+          lout[k] = LQ[k] + lo[k];
+          lo[k] = real(0);
+        } else {
+          lout[k] = LQ[k];
+        }
+      }
+    } else {
+      for (int k = threadIdx.x; k < S * S; k += NT) lout[k] = LQ[k];
+    }
     __syncthreads();
   }
-  red[threadIdx.x] = dsum;
+  red[threadIdx.x] = (double)dsum;
   __syncthreads();
   for (int w = NT / 2; w > 0; w >>= 1) {
     if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
@@ -328,12 +350,140 @@ __global__ void __launch_bounds__(NT) adj_advance_kernel(DevForest<real> D, AdvA
   if (threadIdx.x == 0) atomicAdd(dscale, red[0] * dfac);
 }
 
-// transpose of the interpolation: fine ghost adjoint -> coarse cells read.
-// A coarse patch on `tlevel` was read through the time-interpolation buffer
-// qT; its adjoint goes to lamT (its qT tile) instead of lam.
+// ---------------------------------------------------------------------
+// Transposes of Alg. 1, per patch (threads tid, stride nt of a group that
+// holds the patch's staged neighbour entries).  Each consumes (zeroes) the
+// adjoint of the patch's own ghost cells it handles and scatters it, with
+// atomics, to the cells those ghosts were computed from.
+
+// transpose of a wall-BC pass: exterior ghost adjoint -> the clamped cell (an
+// exterior ghost copies a non-exterior cell, so one pass in any order)
+template <typename real, int MX>
+__device__ void adj_bc_patch(const PatchMeta& pm, real* L, int tid, int nt) {
+  constexpr int S = MX + 4;
+  const int N = MX << pm.level;
+  for (int k = tid; k < num_ghosts<MX>(); k += nt) {
+    int i, j;
+    ghost_ij<MX>(k, i, j);
+    const int gx = pm.x * MX + i, gy = pm.y * MX + j;
+    const bool ox = gx < 0 || gx >= N, oy = gy < 0 || gy >= N;
+    if (!ox && !oy) continue;
+    const int ic = ox ? (gx < 0 ? 0 : MX - 1) : i;
+    const int jc = oy ? (gy < 0 ? 0 : MX - 1) : j;
+    atomicAdd(&L[(jc + kMbc) * S + ic + kMbc], L[(j + kMbc) * S + i + kMbc]);
+    L[(j + kMbc) * S + i + kMbc] = real(0);
+  }
+}
+
+// transpose of the interpolation (Eq. ghost_fine): each coarse ghost's
+// adjoint goes to the coarse cells it read, on the minmod pieces the forward
+// data select.  A coarse patch on `tlevel` was read through the time-
+// interpolated tiles (coarse_src: patch c at coarse_src + (c - coarse_p0)
+// tiles, else D.qT) and takes the adjoint in lamT; else from the store, lam.
+template <typename real, int MX>
+__device__ void adj_interp_patch(const DevForest<real>& D, const NbrStage& st, const PatchMeta& pm,
+                                 real* L, real* lam, int tlevel, real* lamT, const real* coarse_src,
+                                 int coarse_p0, int tid, int nt) {
+  constexpr int S = MX + 4;
+  for (int k = tid; k < num_ghosts<MX>(); k += nt) {
+    int i, j;
+    ghost_ij<MX>(k, i, j);
+    const int r = region_of<MX>(i, j);
+    const NbrEntry& e = st.e[r];
+    if (e.kind != NB_COARSE) continue;
+    const int2 Ip = apply_a(e.a, pm.x * MX + i, pm.y * MX + j);
+    const int gx = Ip.x + e.fx, gy = Ip.y + e.fy;
+    const PatchMeta& nm = st.m0[r];
+    const int ic = (gx >> 1) - nm.x * MX, jc = (gy >> 1) - nm.y * MX;
+    if (ic < 0 || ic >= MX || jc < 0 || jc >= MX) continue;
+    const real dx = (gx & 1) ? real(1) : real(-1);
+    const real dy = (gy & 1) ? real(1) : real(-1);
+    const size_t o = (size_t)(jc + kMbc) * S + ic + kMbc;
+    const bool viaT = nm.level == tlevel;
+    const real* C = (viaT ? (coarse_src ? coarse_src + (size_t)(e.n0 - coarse_p0) * S * S
+                                        : patch_ptr(D.qT, e.n0, S))
+                          : patch_ptr(D.buf[D.cur[nm.level]], e.n0, S)) +
+                    o;
+    real* LC = (viaT ? lamT : lam) + (size_t)e.n0 * S * S + o;
+    const real lg = L[(j + kMbc) * S + i + kMbc];
+    L[(j + kMbc) * S + i + kMbc] = real(0);
+    const real q0 = C[0];
+    const real ax = C[1] - q0, bx = q0 - C[-1], ay = C[S] - q0, by = q0 - C[-S];
+    const real dax = (ax * bx > real(0) && fabs(ax) < fabs(bx)) ? real(1) : real(0);
+    const real dbx = (ax * bx > real(0) && !(fabs(ax) < fabs(bx))) ? real(1) : real(0);
+    const real day = (ay * by > real(0) && fabs(ay) < fabs(by)) ? real(1) : real(0);
+    const real dby = (ay * by > real(0) && !(fabs(ay) < fabs(by))) ? real(1) : real(0);
+    const real lsx = real(0.25) * dx * lg, lsy = real(0.25) * dy * lg;
+    atomicAdd(LC, lg + lsx * (dbx - dax) + lsy * (dby - day));
+    atomicAdd(LC + 1, lsx * dax);
+    atomicAdd(LC - 1, -lsx * dbx);
+    atomicAdd(LC + S, lsy * day);
+    atomicAdd(LC - S, -lsy * dby);
+  }
+}
+
+// a source on tlevel was read as (1 - alpha) q_old + alpha q: its share goes
+// to lamO and lam (alpha = 0: the previous state alone)
+template <typename real>
+__device__ __forceinline__ void adj_src_add(real* lam, real* lamO, bool viaT, real alpha,
+                                            size_t o, real v) {
+  if (viaT) {
+    atomicAdd(lamO + o, (real(1) - alpha) * v);
+    if (alpha != real(0)) atomicAdd(lam + o, alpha * v);
+  } else {
+    atomicAdd(lam + o, v);
+  }
+}
+
+// transpose of copy / average (Eq. transform, Eq. ghost_coarse): ghost
+// adjoint (in L, the patch's own tile) -> neighbour interiors
+template <typename real, int MX>
+__device__ void adj_copy_patch(const NbrStage& st, const PatchMeta& pm, real* L, real* lam,
+                               int tlevel, real alpha, real* lamO, int tid, int nt) {
+  constexpr int S = MX + 4;
+  for (int k = tid; k < num_ghosts<MX>(); k += nt) {
+    int i, j;
+    ghost_ij<MX>(k, i, j);
+    const int r = region_of<MX>(i, j);
+    const NbrEntry& e = st.e[r];
+    if (e.kind != NB_SAME && e.kind != NB_FINE) continue;
+    const real lg = L[(j + kMbc) * S + i + kMbc];
+    L[(j + kMbc) * S + i + kMbc] = real(0);
+    const int2 Ip = apply_a(e.a, pm.x * MX + i, pm.y * MX + j);
+    const int gx = Ip.x + e.fx, gy = Ip.y + e.fy;
+    if (e.kind == NB_SAME) {
+      const PatchMeta& nm = st.m0[r];
+      const int lx = gx - nm.x * MX, ly = gy - nm.y * MX;
+      if (lx < 0 || lx >= MX || ly < 0 || ly >= MX) continue;
+      adj_src_add(lam, lamO, nm.level == tlevel, alpha,
+                  (size_t)e.n0 * S * S + (ly + kMbc) * S + lx + kMbc, lg);
+    } else {
+      int n = e.n0;
+      const PatchMeta* nm = &st.m0[r];
+      int lx = 2 * gx - nm->x * MX, ly = 2 * gy - nm->y * MX;
+      if (lx < 0 || lx >= MX || ly < 0 || ly >= MX) {
+        if (e.n1 < 0) continue;
+        n = e.n1;
+        nm = &st.m1[r];
+        lx = 2 * gx - nm->x * MX;
+        ly = 2 * gy - nm->y * MX;
+        if (lx < 0 || lx >= MX || ly < 0 || ly >= MX) continue;
+      }
+      for (int q = 0; q < 4; ++q)
+        adj_src_add(lam, lamO, nm->level == tlevel, alpha,
+                    (size_t)n * S * S + (ly + (q >> 1) + kMbc) * S + lx + (q & 1) + kMbc,
+                    real(0.25) * lg);
+    }
+  }
+}
+
+// --------------------------------------------------------------- kernels
+
+// global step: the whole transpose of Alg. 1 is split by phase over all
+// patches (the phases scatter into other patches' ghost cells)
 template <typename real, int MX>
 __global__ void adj_interp_kernel(DevForest<real> D, const int* targets, int ntargets,
-                                  real* lam, int tlevel, real* lamT) {
+                                  real* lam) {
   constexpr int S = MX + 4;
   __shared__ NbrStage st;
   for (int t = blockIdx.x; t < ntargets; t += gridDim.x) {
@@ -341,162 +491,99 @@ __global__ void adj_interp_kernel(DevForest<real> D, const int* targets, int nta
     stage_neighbours(D.meta, D.nbr, p, st, threadIdx.x);
     const PatchMeta pm = D.meta[p];
     __syncthreads();
-    real* L = lam + (size_t)p * S * S;
-    for (int k = threadIdx.x; k < num_ghosts<MX>(); k += blockDim.x) {
-      int i, j;
-      ghost_ij<MX>(k, i, j);
-      const int r = region_of<MX>(i, j);
-      const NbrEntry& e = st.e[r];
-      if (e.kind != NB_COARSE) continue;
-      const int2 Ip = apply_a(e.a, pm.x * MX + i, pm.y * MX + j);
-      const int gx = Ip.x + e.fx, gy = Ip.y + e.fy;
-      const PatchMeta& nm = st.m0[r];
-      const int ic = (gx >> 1) - nm.x * MX, jc = (gy >> 1) - nm.y * MX;
-      if (ic < 0 || ic >= MX || jc < 0 || jc >= MX) continue;
-      const real dx = (gx & 1) ? real(1) : real(-1);
-      const real dy = (gy & 1) ? real(1) : real(-1);
-      const size_t o = (size_t)(jc + kMbc) * S + ic + kMbc;
-      const bool viaT = nm.level == tlevel;
-      const real* C = patch_ptr(viaT ? D.qT : D.buf[D.cur[nm.level]], e.n0, S) + o;
-      real* LC = (viaT ? lamT : lam) + (size_t)e.n0 * S * S + o;
-      const real lg = L[(j + kMbc) * S + i + kMbc];
-      L[(j + kMbc) * S + i + kMbc] = real(0);
-      const real q0 = C[0];
-      const real ax = C[1] - q0, bx = q0 - C[-1], ay = C[S] - q0, by = q0 - C[-S];
-      const real dax = (ax * bx > real(0) && fabs(ax) < fabs(bx)) ? real(1) : real(0);
-      const real dbx = (ax * bx > real(0) && !(fabs(ax) < fabs(bx))) ? real(1) : real(0);
-      const real day = (ay * by > real(0) && fabs(ay) < fabs(by)) ? real(1) : real(0);
-      const real dby = (ay * by > real(0) && !(fabs(ay) < fabs(by))) ? real(1) : real(0);
-      const real lsx = real(0.25) * dx * lg, lsy = real(0.25) * dy * lg;
-      atomicAdd(LC, lg + lsx * (dbx - dax) + lsy * (dby - day));
-      atomicAdd(LC + 1, lsx * dax);
-      atomicAdd(LC - 1, -lsx * dbx);
-      atomicAdd(LC + S, lsy * day);
-      atomicAdd(LC - S, -lsy * dby);
-    }
+    adj_interp_patch<real, MX>(D, st, pm, lam + (size_t)p * S * S, lam, -1, nullptr, nullptr, 0,
+                               threadIdx.x, blockDim.x);
     __syncthreads();
   }
 }
 
-// transpose of a wall-BC pass (local to each patch): patches targets[t]
-// (or p0 + t without a list), t < n
 template <typename real, int MX>
-__global__ void adj_bc_kernel(DevForest<real> D, real* lam, const int* targets, int p0, int n) {
+__global__ void adj_bc_kernel(DevForest<real> D, real* lam) {
   constexpr int S = MX + 4;
-  for (int t = blockIdx.x; t < n; t += gridDim.x) {
-    const int p = targets ? targets[t] : p0 + t;
-    const PatchMeta pm = D.meta[p];
-    real* L = lam + (size_t)p * S * S;
-    const int N = MX << pm.level;
-    // an exterior ghost copies a non-exterior cell, so one pass in any order
-    for (int k = threadIdx.x; k < num_ghosts<MX>(); k += blockDim.x) {
-      int i, j;
-      ghost_ij<MX>(k, i, j);
-      const int gx = pm.x * MX + i, gy = pm.y * MX + j;
-      const bool ox = gx < 0 || gx >= N, oy = gy < 0 || gy >= N;
-      if (!ox && !oy) continue;
-      const int ic = ox ? (gx < 0 ? 0 : MX - 1) : i;
-      const int jc = oy ? (gy < 0 ? 0 : MX - 1) : j;
-      atomicAdd(&L[(jc + kMbc) * S + ic + kMbc], L[(j + kMbc) * S + i + kMbc]);
-      L[(j + kMbc) * S + i + kMbc] = real(0);
-    }
-  }
-}
-
-// transpose of copy / average: ghost adjoint -> neighbour interiors, for
-// patches targets[t] (or p0 + t), t < n.  Multirate (tlevel >= 0): a patch on
-// tlevel keeps its ghost adjoints in lamT (its qT tile); a source on tlevel
-// was read as (1 - alpha) q_old + alpha q, so its share goes to lamO and lam.
-template <typename real>
-__device__ __forceinline__ void adj_src_add(real* lam, real* lamO, bool viaT, real alpha,
-                                            size_t o, real v) {
-  if (viaT) {
-    atomicAdd(lamO + o, (real(1) - alpha) * v);
-    atomicAdd(lam + o, alpha * v);
-  } else {
-    atomicAdd(lam + o, v);
-  }
+  for (int p = blockIdx.x; p < D.npatch; p += gridDim.x)
+    adj_bc_patch<real, MX>(D.meta[p], lam + (size_t)p * S * S, threadIdx.x, blockDim.x);
 }
 
 template <typename real, int MX>
-__global__ void adj_copy_kernel(DevForest<real> D, real* lam, const int* targets, int p0, int n,
-                                int tlevel, real alpha, real* lamT, real* lamO) {
+__global__ void adj_copy_kernel(DevForest<real> D, real* lam) {
   constexpr int S = MX + 4;
   __shared__ NbrStage st;
-  for (int t = blockIdx.x; t < n; t += gridDim.x) {
-    const int p = targets ? targets[t] : p0 + t;
+  for (int p = blockIdx.x; p < D.npatch; p += gridDim.x) {
     stage_neighbours(D.meta, D.nbr, p, st, threadIdx.x);
     const PatchMeta pm = D.meta[p];
     __syncthreads();
-    real* L = (pm.level == tlevel ? lamT : lam) + (size_t)p * S * S;
-    for (int k = threadIdx.x; k < num_ghosts<MX>(); k += blockDim.x) {
-      int i, j;
-      ghost_ij<MX>(k, i, j);
-      const int r = region_of<MX>(i, j);
-      const NbrEntry& e = st.e[r];
-      if (e.kind != NB_SAME && e.kind != NB_FINE) continue;
-      const real lg = L[(j + kMbc) * S + i + kMbc];
-      L[(j + kMbc) * S + i + kMbc] = real(0);
-      const int2 Ip = apply_a(e.a, pm.x * MX + i, pm.y * MX + j);
-      const int gx = Ip.x + e.fx, gy = Ip.y + e.fy;
-      if (e.kind == NB_SAME) {
-        const PatchMeta& nm = st.m0[r];
-        const int lx = gx - nm.x * MX, ly = gy - nm.y * MX;
-        if (lx < 0 || lx >= MX || ly < 0 || ly >= MX) continue;
-        adj_src_add(lam, lamO, nm.level == tlevel, alpha,
-                    (size_t)e.n0 * S * S + (ly + kMbc) * S + lx + kMbc, lg);
-      } else {
-        int n = e.n0;
-        const PatchMeta* nm = &st.m0[r];
-        int lx = 2 * gx - nm->x * MX, ly = 2 * gy - nm->y * MX;
-        if (lx < 0 || lx >= MX || ly < 0 || ly >= MX) {
-          if (e.n1 < 0) continue;
-          n = e.n1;
-          nm = &st.m1[r];
-          lx = 2 * gx - nm->x * MX;
-          ly = 2 * gy - nm->y * MX;
-          if (lx < 0 || lx >= MX || ly < 0 || ly >= MX) continue;
-        }
-        for (int q = 0; q < 4; ++q)
-          adj_src_add(lam, lamO, nm->level == tlevel, alpha,
-                      (size_t)n * S * S + (ly + (q >> 1) + kMbc) * S + lx + (q & 1) + kMbc,
-                      real(0.25) * lg);
-      }
-    }
+    adj_copy_patch<real, MX>(st, pm, lam + (size_t)p * S * S, lam, -1, real(0), nullptr,
+                             threadIdx.x, blockDim.x);
     __syncthreads();
   }
 }
 
-// multirate: adjoint of the level's new interior plus that of its previous
-// state (the copy q_old = q taken before the update), whose old value is dead
+// multirate substep, level L's patches [p0, p1): the transposes of the
+// level-L ghosts in reverse phase order -- boundary condition, interpolation
+// from the time-interpolated coarse tiles (into lamT), boundary condition,
+// copy / average.  Only the patch's own ghost cells are read, so one CTA per
+// patch runs all four.
 template <typename real, int MX>
-__global__ void adj_combine_kernel(real* lam, real* lamO, int p0, int p1) {
+__global__ void adj_level_ghosts_kernel(DevForest<real> D, int p0, int p1, real* lam, int tlevel,
+                                        real alpha, real* lamT, real* lamO, const real* coarse_src,
+                                        int coarse_p0) {
   constexpr int S = MX + 4;
-  for (int p = p0 + blockIdx.x; p < p1; p += gridDim.x)
-    for (int k = threadIdx.x; k < MX * MX; k += blockDim.x) {
-      const size_t o = (size_t)p * S * S + (k / MX + 2) * S + k % MX + 2;
-      lam[o] += lamO[o];
-      lamO[o] = real(0);
+  __shared__ NbrStage st;
+  const bool walls = D.domain == FC_DOMAIN_WALLS;
+  for (int p = p0 + blockIdx.x; p < p1; p += gridDim.x) {
+    stage_neighbours(D.meta, D.nbr, p, st, threadIdx.x);
+    const PatchMeta pm = D.meta[p];
+    real* L = lam + (size_t)p * S * S;
+    __syncthreads();
+    if (walls) {
+      adj_bc_patch<real, MX>(pm, L, threadIdx.x, blockDim.x);
+      __syncthreads();
     }
+    adj_interp_patch<real, MX>(D, st, pm, L, lam, tlevel, lamT, coarse_src, coarse_p0, threadIdx.x,
+                               blockDim.x);
+    __syncthreads();
+    if (walls) {
+      adj_bc_patch<real, MX>(pm, L, threadIdx.x, blockDim.x);
+      __syncthreads();
+    }
+    adj_copy_patch<real, MX>(st, pm, L, lam, tlevel, alpha, lamO, threadIdx.x, blockDim.x);
+    __syncthreads();
+  }
 }
 
-// multirate: transpose of qT = (1 - alpha) q_old + alpha q on the coarse
-// patches read through qT (each listed once); clears their qT adjoint tiles
+// multirate substep, the level L-1 patches read through the time-
+// interpolated tiles (each listed once): the transposes of their ghosts
+// (boundary condition, copy / average) and of the time interpolation of
+// their interiors; their lamT tiles are cleared
 template <typename real, int MX>
-__global__ void adj_time_kernel(const int* targets, int n, real alpha, real* lam, real* lamO,
-                                real* lamT) {
+__global__ void adj_coarse_tiles_kernel(DevForest<real> D, const int* targets, int n, real* lam,
+                                        int tlevel, real alpha, real* lamT, real* lamO) {
   constexpr int S = MX + 4;
+  __shared__ NbrStage st;
+  const bool walls = D.domain == FC_DOMAIN_WALLS;
   for (int t = blockIdx.x; t < n; t += gridDim.x) {
-    const size_t base = (size_t)targets[t] * S * S;
+    const int p = targets[t];
+    stage_neighbours(D.meta, D.nbr, p, st, threadIdx.x);
+    const PatchMeta pm = D.meta[p];
+    real* T = lamT + (size_t)p * S * S;
+    __syncthreads();
+    if (walls) {
+      adj_bc_patch<real, MX>(pm, T, threadIdx.x, blockDim.x);
+      __syncthreads();
+    }
+    adj_copy_patch<real, MX>(st, pm, T, lam, tlevel, alpha, lamO, threadIdx.x, blockDim.x);
+    __syncthreads();
+    const size_t base = (size_t)p * S * S;
     for (int k = threadIdx.x; k < S * S; k += blockDim.x) {
       const int i = k % S - 2, j = k / S - 2;
-      const real v = lamT[base + k];
-      lamT[base + k] = real(0);
-      if (i >= 0 && i < MX && j >= 0 && j < MX) {
-        lamO[base + k] += (real(1) - alpha) * v;
-        lam[base + k] += alpha * v;
+      const real v = T[k];
+      T[k] = real(0);
+      if (i >= 0 && i < MX && j >= 0 && j < MX) {  // other CTAs may add here too
+        atomicAdd(lamO + base + k, (real(1) - alpha) * v);
+        if (alpha != real(0)) atomicAdd(lam + base + k, alpha * v);
       }
     }
+    __syncthreads();
   }
 }
 
@@ -513,7 +600,8 @@ template <typename real, int MX>
 cudaError_t adj_advance_level(const DevForest<real>& D, int L, int p0, int p1, double t, double dt,
                               double period, double scale, double dfac, const real* lam_in,
                               real* lam_out, double* dscale, cudaStream_t s,
-                              const double* t0_dev = nullptr) {
+                              const double* t0_dev = nullptr, const real* tiles = nullptr,
+                              int tiles_p0 = 0, real* lamO = nullptr) {
   constexpr int NT = 256;
   static bool attr = false;
   constexpr size_t smem = adj_smem<real, MX>();
@@ -533,7 +621,7 @@ cudaError_t adj_advance_level(const DevForest<real>& D, int L, int p0, int p1, d
   al.t0_dev = t0_dev;
   al.sfac = D.vel_kind == FC_VEL_SWIRL ? scale * sin(M_PI * al.h) / (M_PI * al.h) : 0.0;
   adj_advance_kernel<real, MX, NT><<<p1 - p0, NT, smem, s>>>(D, al, lam_in, lam_out, dscale, dfac,
-                                                               p0, p1);
+                                                               p0, p1, tiles, tiles_p0, lamO);
   ++launch_counter();
   return cudaGetLastError();
 }
@@ -550,15 +638,14 @@ cudaError_t adjoint_mx(const DevForest<real>& D, const AdjArgs& g, const real* l
   }
   if (g.ncoarse > 0) {
     adj_interp_kernel<real, MX><<<grid_for(g.ncoarse), 128, 0, s>>>(D, g.coarse_list, g.ncoarse,
-                                                                     lam_out, -1, nullptr);
+                                                                     lam_out);
     ++launch_counter();
   }
   if (D.domain == FC_DOMAIN_WALLS) {
-    adj_bc_kernel<real, MX><<<grid_for(D.npatch), 128, 0, s>>>(D, lam_out, nullptr, 0, D.npatch);
+    adj_bc_kernel<real, MX><<<grid_for(D.npatch), 128, 0, s>>>(D, lam_out);
     ++launch_counter();
   }
-  adj_copy_kernel<real, MX><<<grid_for(D.npatch), 128, 0, s>>>(D, lam_out, nullptr, 0, D.npatch,
-                                                                 -1, real(0), nullptr, nullptr);
+  adj_copy_kernel<real, MX><<<grid_for(D.npatch), 128, 0, s>>>(D, lam_out);
   ++launch_counter();
   return cudaGetLastError();
 }
@@ -568,37 +655,19 @@ template <typename real, int MX>
 cudaError_t adjoint_sub_mx(const DevForest<real>& D, const AdjSubArgs& g, real* lam, real* lamO,
                            real* lamT, double* dscale, cudaStream_t s) {
   const int n = g.p1 - g.p0;
-  const bool walls = D.domain == FC_DOMAIN_WALLS;
+  if (n <= 0) return cudaSuccess;
   const real alpha = real(g.alpha);
-  cudaError_t e = adj_advance_level<real, MX>(D, g.L, g.p0, g.p1, g.t, g.dt, g.period, g.scale,
-                                              g.dscale_factor, lam, lam, dscale, s, g.t0_dev);
-  if (e != cudaSuccess || n <= 0) return e;
-  adj_combine_kernel<real, MX><<<grid_for(n), 128, 0, s>>>(lam, lamO, g.p0, g.p1);
-  ++launch_counter();
-  if (walls) {  // phase 4
-    adj_bc_kernel<real, MX><<<grid_for(n), 128, 0, s>>>(D, lam, nullptr, g.p0, n);
-    ++launch_counter();
-  }
-  if (g.nb > 0) {  // phase 3
-    adj_interp_kernel<real, MX><<<grid_for(g.nb), 128, 0, s>>>(D, g.list_b, g.nb, lam, g.tlevel,
-                                                               lamT);
-    ++launch_counter();
-  }
-  if (walls) {  // phase 2
-    adj_bc_kernel<real, MX><<<grid_for(n), 128, 0, s>>>(D, lam, nullptr, g.p0, n);
-    ++launch_counter();
-    if (g.nt > 0) {
-      adj_bc_kernel<real, MX><<<grid_for(g.nt), 128, 0, s>>>(D, lamT, g.list_t, 0, g.nt);
-      ++launch_counter();
-    }
-  }
-  // phase 1 on the coarse patches read through qT and on level L
-  adj_copy_kernel<real, MX><<<grid_for(g.na), 128, 0, s>>>(D, lam, g.list_a, 0, g.na, g.tlevel,
-                                                           alpha, lamT, lamO);
+  cudaError_t e = adj_advance_level<real, MX>(
+      D, g.L, g.p0, g.p1, g.t, g.dt, g.period, g.scale, g.dscale_factor, lam, lam, dscale, s,
+      g.t0_dev, static_cast<const real*>(g.tiles), g.tiles_p0, lamO);
+  if (e != cudaSuccess) return e;
+  adj_level_ghosts_kernel<real, MX><<<grid_for(n), 128, 0, s>>>(
+      D, g.p0, g.p1, lam, g.tlevel, alpha, lamT, lamO, static_cast<const real*>(g.coarse),
+      g.coarse_p0);
   ++launch_counter();
   if (g.nt > 0) {
-    adj_time_kernel<real, MX><<<grid_for(g.nt), 128, 0, s>>>(g.list_t, g.nt, alpha, lam, lamO,
-                                                             lamT);
+    adj_coarse_tiles_kernel<real, MX><<<grid_for(g.nt), 128, 0, s>>>(D, g.list_t, g.nt, lam,
+                                                                     g.tlevel, alpha, lamT, lamO);
     ++launch_counter();
   }
   return cudaGetLastError();

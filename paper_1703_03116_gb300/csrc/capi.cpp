@@ -1001,12 +1001,12 @@ static fc_status capture_adjoint_multirate(fc_forest* F, double dtc, cudaStream_
       const int p0 = H.lev_start[u.L], p1 = H.lev_start[u.L + 1];
       if (p1 <= p0) continue;
       std::copy(u.cur, u.cur + kMaxLevel + 1, F->cur);
-      cp(tiles(F->buf[F->cur[u.L]], p0), pool + u.offq, (size_t)(p1 - p0) * tile);
       const int tl = u.L > lmin ? u.L - 1 : -1;
-      if (tl >= 0)
-        cp(tiles(F->qT, H.lev_start[tl]), pool + u.offt,
-           (size_t)(H.lev_start[u.L] - H.lev_start[tl]) * tile);
       AdjSubArgs g{};
+      g.tiles = pool + u.offq;  // read where they were kept: no copies back
+      g.tiles_p0 = p0;
+      g.coarse = tl >= 0 ? pool + u.offt : nullptr;
+      g.coarse_p0 = tl >= 0 ? H.lev_start[tl] : 0;
       g.L = u.L;
       g.p0 = p0;
       g.p1 = p1;

@@ -210,6 +210,13 @@ struct AdjSubArgs {
   int nb;
   const int* list_t;  // device: level L-1 patches read through qT
   int nt;
+  // the forward's kept tiles: level L's ghost-filled tiles (patch p at
+  // tiles + (p - tiles_p0) tiles) and the time-interpolated coarse tiles
+  // (coarse + (c - coarse_p0) tiles); null: read the store and qT
+  const void* tiles;
+  int tiles_p0;
+  const void* coarse;
+  int coarse_p0;
 };
 template <typename real>
 cudaError_t launch_adjoint_substep(const DevForest<real>& D, const AdjSubArgs& g, real* lam,
