@@ -602,7 +602,9 @@ cudaError_t adj_advance_level(const DevForest<real>& D, int L, int p0, int p1, d
                               real* lam_out, double* dscale, cudaStream_t s,
                               const double* t0_dev = nullptr, const real* tiles = nullptr,
                               int tiles_p0 = 0, real* lamO = nullptr) {
-  constexpr int NT = 256;
+  // a whole CTA per patch: the more threads, the shorter each thread's chain
+  // through the phases (the kernel is latency-bound at these launch sizes)
+  constexpr int NT = MX >= 32 ? (sizeof(real) == 4 ? 1024 : 512) : (MX >= 16 ? 512 : 256);
   static bool attr = false;
   constexpr size_t smem = adj_smem<real, MX>();
   if (!attr) {
@@ -661,12 +663,12 @@ cudaError_t adjoint_sub_mx(const DevForest<real>& D, const AdjSubArgs& g, real* 
       D, g.L, g.p0, g.p1, g.t, g.dt, g.period, g.scale, g.dscale_factor, lam, lam, dscale, s,
       g.t0_dev, static_cast<const real*>(g.tiles), g.tiles_p0, lamO);
   if (e != cudaSuccess) return e;
-  adj_level_ghosts_kernel<real, MX><<<grid_for(n), 128, 0, s>>>(
+  adj_level_ghosts_kernel<real, MX><<<grid_for(n), 256, 0, s>>>(
       D, g.p0, g.p1, lam, g.tlevel, alpha, lamT, lamO, static_cast<const real*>(g.coarse),
       g.coarse_p0);
   ++launch_counter();
   if (g.nt > 0) {
-    adj_coarse_tiles_kernel<real, MX><<<grid_for(g.nt), 128, 0, s>>>(D, g.list_t, g.nt, lam,
+    adj_coarse_tiles_kernel<real, MX><<<grid_for(g.nt), 256, 0, s>>>(D, g.list_t, g.nt, lam,
                                                                      g.tlevel, alpha, lamT, lamO);
     ++launch_counter();
   }

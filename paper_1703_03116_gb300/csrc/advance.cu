@@ -116,6 +116,10 @@ __global__ void __launch_bounds__(NT) advance_staged_kernel(DevForest<real> D, i
     if (a.gather)  // Alg. 1 for this patch, into the tile's ghost ring
       fill_patch_ghosts<real, MX>(D, st, pm, a.tlevel, real(a.alpha), Q, threadIdx.x, NT,
                                   []() { __syncthreads(); });
+    if (a.keep) {  // the adjoint's replay keeps the ghost-filled input tile
+      real* kp = static_cast<real*>(a.keep) + (size_t)(p - a.keep_p0) * S * S;
+      for (int k = threadIdx.x; k < S * S; k += NT) kp[k] = Q[k];
+    }
     auto q = [&](int i, int j) -> real { return Q[(j + 2) * S + (i + 2)]; };
     // capacity form: kappa of cell (i,j), flux through x-edge / y-edge (i,j)
     auto kap = [&](int i, int j) -> real { return real(Ms[(j + 2) * S + (i + 2)]); };

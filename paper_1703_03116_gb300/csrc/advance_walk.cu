@@ -168,6 +168,10 @@ __global__ void __launch_bounds__(NW * 32) advance_walk_kernel(DevForest<real> D
       fill_patch_ghosts<real, MX>(D, nst[warp][seg], pm, a.tlevel, real(a.alpha), T, li, MX,
                                   []() { __syncwarp(); });
     }
+    if (a.keep && valid) {  // the adjoint's replay keeps the ghost-filled input tile
+      real* kp = static_cast<real*>(a.keep) + (size_t)(p - a.keep_p0) * TILE;
+      for (int k = li; k < TILE; k += MX) kp[k] = T[k];
+    }
     auto Q = [&](int i, int j) -> real { return T[(j + 2) * S + (i + 2)]; };
 
     // side pass: lanes own rows r = -1..MX+1

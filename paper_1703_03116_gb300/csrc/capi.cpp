@@ -141,6 +141,12 @@ struct fc_forest {
   cudaStream_t side = nullptr;
   cudaEvent_t ev_pre[kMaxLevel + 1] = {}, ev_post[kMaxLevel + 1] = {}, ev_fill[kMaxLevel + 1] = {};
   bool pre_ok[kMaxLevel + 1] = {}, post_ok[kMaxLevel + 1] = {};
+  // the adjoint's replay of a coarse step: times relative to the step start
+  // (on the device), and where each substep keeps the update's ghost-filled
+  // input tiles and the time-interpolated coarse tiles it read
+  bool rel_time = false;
+  void* keep_tiles = nullptr;
+  void* keep_qT = nullptr;
   // autotuned patch-update configuration per launch size (bucket = log2 of
   // the patches in one launch): variant and warps per CTA
   struct Tune {
@@ -438,7 +444,7 @@ AdvArgs adv_args(const fc_forest* F, int L, double t, double dt, int n) {
   a.sfac = d.vel_kind == FC_VEL_SWIRL ? F->vel_scale * std::sin(M_PI * a.h) / (M_PI * a.h) : 0.0;
   a.t_half = t + 0.5 * dt;
   a.t_off = t + 0.5 * dt;
-  a.t0_dev = F->capture_pairs ? F->d_t0 : nullptr;
+  a.t0_dev = (F->capture_pairs || F->rel_time) ? F->d_t0 : nullptr;
   a.variant = ADV_STAGED;
   a.warps = 4;
   a.ctas = 0;
@@ -521,6 +527,28 @@ fc_status fill_all(fc_forest* F, cudaStream_t s) {
   return F->esize == 4 ? fill_all_t<float>(F, s) : fill_all_t<double>(F, s);
 }
 
+// the adjoint's replay: copy the time-interpolated tiles of level L-1 (what
+// level L's interpolation reads) to where the adjoint will read them
+cudaError_t keep_coarse_tiles(fc_forest* F, int L, cudaStream_t s) {
+  const HostForest& H = F->host;
+  if (!F->keep_qT || L <= H.desc.lmin) return cudaSuccess;
+  const size_t tile = (size_t)(H.desc.mx + 2 * kMbc) * (H.desc.mx + 2 * kMbc) * F->esize;
+  const int a = H.lev_start[L - 1], b = H.lev_start[L];
+  if (b <= a) return cudaSuccess;
+  return cudaMemcpyAsync(F->keep_qT, static_cast<char*>(F->qT) + (size_t)a * tile,
+                         (size_t)(b - a) * tile, cudaMemcpyDeviceToDevice, s);
+}
+
+// the side stream and events of captured steps (created outside a capture)
+fc_status ensure_side(fc_forest* F) {
+  if (F->side) return FC_OK;
+  FC_CUDA(cudaStreamCreateWithFlags(&F->side, cudaStreamNonBlocking));
+  for (int l = 0; l <= kMaxLevel; ++l)
+    for (cudaEvent_t* ev : {&F->ev_pre[l], &F->ev_post[l], &F->ev_fill[l]})
+      FC_CUDA(cudaEventCreateWithFlags(ev, cudaEventDisableTiming));
+  return FC_OK;
+}
+
 template <typename real>
 fc_status advance_level_t(fc_forest* F, int L, double t, double dt, cudaStream_t s) {
   const HostForest& H = F->host;
@@ -556,11 +584,15 @@ fc_status advance_level_t(fc_forest* F, int L, double t, double dt, cudaStream_t
           Timed tm(F, 1, F->side, gb * A.ntargets);
           FC_CUDA(launch_fill_coarse(D, A, F->side));
         }
+        FC_CUDA(keep_coarse_tiles(F, L, F->side));
         FC_CUDA(cudaEventRecord(F->ev_fill[L], F->side));
         FC_CUDA(cudaStreamWaitEvent(s, F->ev_fill[L], 0));
       } else {
-        Timed tm(F, 1, s, gb * A.ntargets);
-        FC_CUDA(launch_fill_coarse(D, A, s));
+        {
+          Timed tm(F, 1, s, gb * A.ntargets);
+          FC_CUDA(launch_fill_coarse(D, A, s));
+        }
+        FC_CUDA(keep_coarse_tiles(F, L, s));
       }
       a.gather = 1;
       a.tlevel = tlevel;
@@ -576,7 +608,10 @@ fc_status advance_level_t(fc_forest* F, int L, double t, double dt, cudaStream_t
         Timed tm(F, 1, s, gb * B.ntargets);
         FC_CUDA(launch_fill_fine(D, B, s));
       }
+      FC_CUDA(keep_coarse_tiles(F, L, s));
     }
+    a.keep = F->keep_tiles;
+    a.keep_p0 = p0;
     if (F->dag) {
       FC_CUDA(cudaEventRecord(F->ev_pre[L], s));
       F->pre_ok[L] = true;
@@ -956,6 +991,13 @@ static fc_status capture_adjoint_multirate(fc_forest* F, double dtc, cudaStream_
   real* LT = static_cast<real*>(F->madj[2]);
   int cur0[kMaxLevel + 1];
   std::copy(F->cur, F->cur + kMaxLevel + 1, cur0);
+  {
+    const fc_status sst = ensure_side(F);
+    if (sst != FC_OK) return sst;
+  }
+  const bool timing = F->timing;
+  F->timing = false;  // no timer events inside the adjoint's graph
+  fc_status replay_st = FC_OK;
   const uint64_t launches_before = launch_counter();
   FC_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
   auto body = [&]() -> cudaError_t {
@@ -966,27 +1008,22 @@ static fc_status capture_adjoint_multirate(fc_forest* F, double dtc, cudaStream_
     auto tiles = [&](void* base, int p) { return static_cast<char*>(base) + (size_t)p * tile; };
     cp(pool, F->buf[0], store);
     cp(pool + store, F->buf[1], store);
-    // forward replay; after each fill keep level L's tiles and the qT tiles of L-1
+    // forward replay through the forward's own level substeps (fused gather,
+    // fills forked where their inputs are final), keeping what the reverse
+    // reads: each update's ghost-filled input tiles and the coarse tiles
+    reset_times(F);
+    F->dag = true;
+    F->rel_time = true;
+    for (int l = 0; l <= kMaxLevel; ++l) F->pre_ok[l] = F->post_ok[l] = false;
     for (auto& u : subs) {
       std::copy(F->cur, F->cur + kMaxLevel + 1, u.cur);
-      const int p0 = H.lev_start[u.L], p1 = H.lev_start[u.L + 1];
-      if (p1 <= p0) continue;
-      DevForest<real> D = dev<real>(F);
-      const int tl = u.L > lmin ? u.L - 1 : -1;
-      FillArgs A{F->d_lists + F->off_a[u.L], (int)H.list_a[u.L].size(), tl, u.alpha};
-      FillArgs B{F->d_lists + F->off_b[u.L], (int)H.list_b[u.L].size(), tl, u.alpha};
-      if (e == cudaSuccess) e = launch_fill_coarse(D, A, cs);
-      if (e == cudaSuccess) e = launch_fill_fine(D, B, cs);
-      cp(pool + u.offq, tiles(F->buf[F->cur[u.L]], p0), (size_t)(p1 - p0) * tile);
-      if (tl >= 0)
-        cp(pool + u.offt, tiles(F->qT, H.lev_start[tl]),
-           (size_t)(H.lev_start[u.L] - H.lev_start[tl]) * tile);
-      AdvArgs a = adv_args(F, u.L, u.t, u.dt, p1 - p0);  // the forward's kernel choice
-      a.t0_dev = F->d_t0;
-      a.t_off = u.t + 0.5 * u.dt;
-      if (e == cudaSuccess) e = launch_advance(D, p0, p1, a, F->d_err, cs);
-      F->cur[u.L] ^= 1;
+      F->keep_tiles = pool + u.offq;
+      F->keep_qT = u.L > lmin ? pool + u.offt : nullptr;
+      if (e == cudaSuccess && replay_st == FC_OK) replay_st = advance_level(F, u.L, u.t, u.dt, cs);
     }
+    F->dag = false;
+    F->rel_time = false;
+    F->keep_tiles = F->keep_qT = nullptr;
     if (e == cudaSuccess) e = cudaMemsetAsync(LQ, 0, cells * sizeof(real), cs);
     if (e == cudaSuccess) e = cudaMemsetAsync(LO, 0, cells * sizeof(real), cs);
     if (e == cudaSuccess) e = cudaMemsetAsync(LT, 0, cells * sizeof(real), cs);
@@ -1037,6 +1074,12 @@ static fc_status capture_adjoint_multirate(fc_forest* F, double dtc, cudaStream_
   out->kernels = launch_counter() - launches_before;  // counted when replayed
   launch_counter() = launches_before;
   std::copy(cur0, cur0 + kMaxLevel + 1, F->cur);
+  F->timing = timing;
+  reset_times(F);
+  if (replay_st != FC_OK) {
+    if (graph) cudaGraphDestroy(graph);
+    return replay_st;
+  }
   if (eb != cudaSuccess || ee != cudaSuccess) {
     if (graph) cudaGraphDestroy(graph);
     return cuda_fail(eb != cudaSuccess ? eb : ee, "adjoint capture");
@@ -1240,11 +1283,9 @@ fc_status fc_step_multirate(fc_forest* F, double t, double dt_coarse, void* stre
     std::copy(F->cur, F->cur + kMaxLevel + 1, ng.cur_before);
     // capture with relative times; the host bookkeeping done while capturing
     // is what one replay does to the state
-    if (!F->side) {
-      FC_CUDA(cudaStreamCreateWithFlags(&F->side, cudaStreamNonBlocking));
-      for (int l = 0; l <= kMaxLevel; ++l)
-        for (cudaEvent_t* ev : {&F->ev_pre[l], &F->ev_post[l], &F->ev_fill[l]})
-          FC_CUDA(cudaEventCreateWithFlags(ev, cudaEventDisableTiming));
+    {
+      const fc_status sst = ensure_side(F);
+      if (sst != FC_OK) return sst;
     }
     F->capture_pairs = &ng.pairs;
     F->dag = true;

@@ -165,6 +165,10 @@ struct AdvArgs {
   // read through the time-interpolation buffer
   int gather, tlevel;
   double alpha;
+  // set: each patch's ghost-filled input tile is also written to
+  // keep + (p - keep_p0) tiles (the adjoint's replay of the forward)
+  void* keep;
+  int keep_p0;
 };
 
 // Patch-update kernel variants (chosen per level launch by the autotuner):
