@@ -179,7 +179,7 @@ class Runner:
         self.F = fc.initial_forest(desc, q0_fn(workloads), lmax_f=self.lmax_f,
                                    tau_r=w.tau_refine, tau_c=w.tau_coarsen)
         # pick the patch-update kernel per launch size on this layout (untimed setup)
-        self.tuning = {int(b): {"variant": ["staged", "walk"][v], "warps": k,
+        self.tuning = {int(b): {"variant": ["staged", "walk", "walk1"][v], "warps": k,
                                 "fill": "fused" if fu else "separate", "ns": ns}
                        for b, (v, k, fu, ns) in self.F.autotune().items()}
         self.n = 0

@@ -246,10 +246,11 @@ fc_status fc_set_graphs(fc_forest* forest, int enable);
  * tile in shared memory, every thread on every phase -- low latency for
  * launches of few patches) and 1 "walk" (lanes own patch columns and walk
  * the rows with warp shuffles, tiles double-buffered per warp by TMA, a
- * persistent grid of `warps`-warp CTAs -- fewest instructions per cell).
+ * persistent grid of `warps`-warp CTAs -- fewest instructions per cell) and
+ * 2 (walk1: the walk with one tile buffer per warp, twice the warps per SM).
  *
  * fc_autotune times every candidate (staged; walk with 2, 4, 8 warps per
- * CTA; each with the level's ghosts filled inside the update kernel or by
+ * CTA; walk1 with 4 or 8; each with the level's ghosts filled inside the update kernel or by
  * separate fill kernels) as a whole level substep of the current layout and
  * keeps the fastest per launch size (sizes bucketed by powers of two; a
  * bucket is tuned once per forest).  It overwrites the previous-state

@@ -258,7 +258,8 @@ cudaError_t launch_advance(const DevForest<real>& D, int p0, int p1, const AdvAr
                            cudaStream_t s) {
   if (p1 <= p0) return cudaSuccess;
   // the walk variant has no capacity form: mapped grids always run staged
-  if (a.variant == ADV_WALK && !D.metric) return launch_advance_walk(D, p0, p1, a, err, s);
+  if ((a.variant == ADV_WALK || a.variant == ADV_WALK1) && !D.metric)
+    return launch_advance_walk(D, p0, p1, a, err, s);
   return launch_advance_staged(D, p0, p1, a, err, s);
 }
 

@@ -60,12 +60,15 @@ constexpr int side_reals() {
   return ((2 * (MX + 3) + 3 * (MX + 2) + 4 * (MX + 1)) + 3) & ~3;
 }
 
-template <typename real, int MX>
+// NB tile buffers per warp: 2 overlap the next group's copy with this
+// group's compute; 1 halves the shared memory, so twice the warps fit on an
+// SM and other warps hide the copy instead
+template <typename real, int MX, int NB>
 constexpr int warp_reals() {
-  return 2 * (32 / MX) * tile_stride<MX>() + (32 / MX) * side_reals<MX>();
+  return NB * (32 / MX) * tile_stride<MX>() + (32 / MX) * side_reals<MX>();
 }
 
-template <typename real, int MX, int NW, bool SWIRL>
+template <typename real, int MX, int NW, bool SWIRL, int NB>
 __global__ void __launch_bounds__(NW * 32) advance_walk_kernel(DevForest<real> D, int p0, int p1,
                                                                AdvArgs a, int* err) {
   constexpr int S = MX + 4;
@@ -81,8 +84,8 @@ __global__ void __launch_bounds__(NW * 32) advance_walk_kernel(DevForest<real> D
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int seg = lane / MX, li = lane % MX;
-  real* wbase = reinterpret_cast<real*>(smem_raw) + (size_t)warp * warp_reals<real, MX>();
-  real* side = wbase + 2 * PPW * TS + seg * side_reals<MX>();
+  real* wbase = reinterpret_cast<real*>(smem_raw) + (size_t)warp * warp_reals<real, MX, NB>();
+  real* side = wbase + NB * PPW * TS + seg * side_reals<MX>();
   real* TyS = side;           // sin(pi (y_r + y_{r+1})), r = -1..MX+1 at [r+1]
   real* SyS = TyS + NS;       // sin^2(pi y_r), r = -1..MX+1 at [r+1]
   real* FeN = SyS + NS;       // x-edge MX: normal flux, rows -1..MX at [r+1]
@@ -129,10 +132,13 @@ __global__ void __launch_bounds__(NW * 32) advance_walk_kernel(DevForest<real> D
 
   uint32_t par0 = 0, par1 = 0;
   int b = 0;
-  int g = blockIdx.x * NW + warp;
+  const int g_first = blockIdx.x * NW + warp;
+  int g = g_first;
   if (g < ngroups && lane == 0) issue(g, 0);
-  for (; g < ngroups; g += TW, b ^= 1) {
-    const bool prefetch = g + TW < ngroups;
+  for (; g < ngroups; g += TW, b ^= (NB - 1)) {
+    const bool prefetch = NB == 2 && g + TW < ngroups;
+    // one buffer: the group's copy starts once the warp left the previous one
+    if (NB == 1 && g != g_first && lane == 0) issue(g, 0);
     if (prefetch && lane == 0) issue(g + TW, b ^ 1);
     const int p = p0 + g * PPW + seg;
     const bool valid = p < p1;
@@ -258,12 +264,12 @@ __global__ void __launch_bounds__(NW * 32) advance_walk_kernel(DevForest<real> D
   }
 }
 
-template <typename real, int MX, int NW, bool SWIRL>
+template <typename real, int MX, int NW, bool SWIRL, int NB>
 cudaError_t walk_launch(const DevForest<real>& D, int p0, int p1, const AdvArgs& a, int* err,
                         cudaStream_t s) {
   static int max_ctas = 0;
-  constexpr size_t smem = sizeof(real) * (size_t)NW * warp_reals<real, MX>();
-  auto kern = advance_walk_kernel<real, MX, NW, SWIRL>;
+  constexpr size_t smem = sizeof(real) * (size_t)NW * warp_reals<real, MX, NB>();
+  auto kern = advance_walk_kernel<real, MX, NW, SWIRL, NB>;
   if (max_ctas == 0) {
     cudaError_t e =
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -288,8 +294,12 @@ cudaError_t walk_launch(const DevForest<real>& D, int p0, int p1, const AdvArgs&
 template <typename real, int MX, int NW>
 cudaError_t walk_vel(const DevForest<real>& D, int p0, int p1, const AdvArgs& a, int* err,
                      cudaStream_t s) {
-  if (D.vel_kind == FC_VEL_SWIRL) return walk_launch<real, MX, NW, true>(D, p0, p1, a, err, s);
-  return walk_launch<real, MX, NW, false>(D, p0, p1, a, err, s);
+  const bool one = a.variant == ADV_WALK1;
+  if (D.vel_kind == FC_VEL_SWIRL)
+    return one ? walk_launch<real, MX, NW, true, 1>(D, p0, p1, a, err, s)
+               : walk_launch<real, MX, NW, true, 2>(D, p0, p1, a, err, s);
+  return one ? walk_launch<real, MX, NW, false, 1>(D, p0, p1, a, err, s)
+             : walk_launch<real, MX, NW, false, 2>(D, p0, p1, a, err, s);
 }
 
 template <typename real, int MX>

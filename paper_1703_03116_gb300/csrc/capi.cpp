@@ -787,8 +787,8 @@ fc_status fc_mass_noalloc(const void* q, int dtype, int mx, int nleaves, const i
 }
 
 fc_status fc_set_advance_variant(fc_forest* F, int variant, int warps) {
-  if (!F || variant < -1 || variant > ADV_WALK || (warps != 2 && warps != 4 && warps != 8))
-    return fail(FC_ERR_INVALID_ARG, "variant must be -1, 0 or 1 and warps 2, 4 or 8");
+  if (!F || variant < -1 || variant > ADV_WALK1 || (warps != 2 && warps != 4 && warps != 8))
+    return fail(FC_ERR_INVALID_ARG, "variant must be -1, 0, 1 or 2 and warps 2, 4 or 8");
   F->forced_variant = variant;
   F->forced_warps = warps;
   destroy_graphs(F);
@@ -801,7 +801,9 @@ fc_status fc_autotune(fc_forest* F, int* report, void* stream) {
   const HostForest& H = F->host;
   const struct {
     int variant, warps;
-  } cand[] = {{ADV_STAGED, 4}, {ADV_WALK, 2}, {ADV_WALK, 4}, {ADV_WALK, 8}};
+  } cand[] = {{ADV_STAGED, 4}, {ADV_WALK, 2}, {ADV_WALK, 4}, {ADV_WALK, 8}, {ADV_WALK1, 4},
+              {ADV_WALK1, 8}};
+  constexpr int ncand = sizeof(cand) / sizeof(cand[0]);
   cudaEvent_t e0, e1;
   FC_CUDA(cudaEventCreate(&e0));
   FC_CUDA(cudaEventCreate(&e1));
@@ -816,11 +818,11 @@ fc_status fc_autotune(fc_forest* F, int* report, void* stream) {
     AdvArgs a = adv_args(F, L, 0.0, 0.5 * std::ldexp(1.0, -L) / H.desc.mx, p1 - p0);
     float best = 1e30f;
     // every candidate is timed as a whole substep: its fills plus the update
-    for (int c2 = 0; c2 < 2 * 4; ++c2) {
-      const auto& c = cand[c2 % 4];
-      const int fused = c2 / 4;
+    for (int c2 = 0; c2 < 2 * ncand; ++c2) {
+      const auto& c = cand[c2 % ncand];
+      const int fused = c2 / ncand;
       if (fused && !F->fuse) continue;
-      if (c.variant == ADV_WALK && F->d_metric) continue;  // no capacity form in walk
+      if (c.variant != ADV_STAGED && F->d_metric) continue;  // no capacity form in walk
       a.variant = c.variant;
       a.warps = c.warps;
       a.gather = fused;

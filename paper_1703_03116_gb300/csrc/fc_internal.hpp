@@ -174,8 +174,10 @@ struct AdvArgs {
 // Patch-update kernel variants (chosen per level launch by the autotuner):
 // staged -- one CTA per patch, every thread on every phase (low latency);
 // walk   -- lanes own patch columns and walk the rows, one warp per patch
-//           (fewest instructions per cell; the throughput choice).
-enum AdvVariant : int { ADV_STAGED = 0, ADV_WALK = 1 };
+//           (fewest instructions per cell; the throughput choice), tiles
+//           double-buffered per warp;
+// walk1  -- the walk with one tile buffer per warp (twice the warps per SM).
+enum AdvVariant : int { ADV_STAGED = 0, ADV_WALK = 1, ADV_WALK1 = 2 };
 
 template <typename real>
 cudaError_t launch_advance_walk(const DevForest<real>& D, int p0, int p1, const AdvArgs& a,

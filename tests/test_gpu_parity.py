@@ -275,7 +275,7 @@ def test_timers_count_every_replay_across_regrids():
     assert launches == expect and ms > 0 and nbytes > 0
 
 
-@pytest.mark.parametrize("variant,warps", [(0, 4), (1, 2), (1, 4), (1, 8)])
+@pytest.mark.parametrize("variant,warps", [(0, 4), (1, 2), (1, 4), (1, 8), (2, 4), (2, 8)])
 @pytest.mark.parametrize("mx", [8, 16, 32])
 def test_advance_variants_match_oracle(variant, warps, mx):
     """Both patch-update kernels (staged; walk with 2/4/8 warps per CTA) on
