@@ -2,6 +2,7 @@
 // CUDA kernels.  Nothing here crosses the C ABI (include/fc.h).
 #pragma once
 
+#include <climits>
 #include <cstddef>
 #include <cstdint>
 #include <string>
@@ -61,6 +62,90 @@ inline uint64_t leaf_key(int f, int b, int l, int x, int y) {
   return ((uint64_t)(uint32_t)f << 48) | ((uint64_t)(uint32_t)b << 45) |
          ((uint64_t)(uint32_t)l << 40) | ((uint64_t)(uint32_t)x << 20) | (uint64_t)(uint32_t)y;
 }
+inline Leaf leaf_of_key(uint64_t k) {
+  return Leaf{(int)(k >> 48), (int)((k >> 45) & 7), (int)((k >> 40) & 31), (int)((k >> 20) & 0xFFFFF),
+              (int)(k & 0xFFFFF)};
+}
+
+// Leaf key -> int map with open addressing and linear probing (host tables
+// of up to millions of leaves; no allocation per entry).  Keys with the top
+// 16 bits all set never occur (forest < 65535) and mark empty / erased slots.
+class KeyMap {
+ public:
+  void clear(size_t n_expected = 0) {
+    size_t cap = 16;
+    while (cap < 2 * n_expected + 2) cap <<= 1;
+    keys_.assign(cap, kEmpty);
+    vals_.assign(cap, 0);
+    used_ = live_ = 0;
+  }
+  // false if the key is present already
+  bool insert(uint64_t k, int v) {
+    if (keys_.empty() || 2 * (used_ + 1) > keys_.size()) grow();
+    size_t i = mix(k) & (keys_.size() - 1), tomb = SIZE_MAX;
+    for (;; i = (i + 1) & (keys_.size() - 1)) {
+      if (keys_[i] == k) return false;
+      if (keys_[i] == kErased && tomb == SIZE_MAX) tomb = i;
+      if (keys_[i] == kEmpty) break;
+    }
+    if (tomb != SIZE_MAX) {
+      i = tomb;
+    } else {
+      ++used_;
+    }
+    keys_[i] = k;
+    vals_[i] = v;
+    ++live_;
+    return true;
+  }
+  int find(uint64_t k) const {  // -1 if absent
+    if (keys_.empty()) return -1;
+    for (size_t i = mix(k) & (keys_.size() - 1);; i = (i + 1) & (keys_.size() - 1)) {
+      if (keys_[i] == k) return vals_[i];
+      if (keys_[i] == kEmpty) return -1;
+    }
+  }
+  bool erase(uint64_t k) {
+    if (keys_.empty()) return false;
+    for (size_t i = mix(k) & (keys_.size() - 1);; i = (i + 1) & (keys_.size() - 1)) {
+      if (keys_[i] == k) {
+        keys_[i] = kErased;
+        --live_;
+        return true;
+      }
+      if (keys_[i] == kEmpty) return false;
+    }
+  }
+  size_t size() const { return live_; }
+  template <class Fn>
+  void for_each(Fn fn) const {
+    for (size_t i = 0; i < keys_.size(); ++i)
+      if (keys_[i] != kEmpty && keys_[i] != kErased) fn(keys_[i], vals_[i]);
+  }
+
+ private:
+  static constexpr uint64_t kEmpty = ~0ull, kErased = ~0ull - 1;
+  static uint64_t mix(uint64_t k) {  // a 64-bit finaliser (xor-shift-multiply)
+    k ^= k >> 33;
+    k *= 0xff51afd7ed558ccdull;
+    k ^= k >> 33;
+    k *= 0xc4ceb9fe1a85ec53ull;
+    k ^= k >> 33;
+    return k;
+  }
+  void grow() {
+    std::vector<uint64_t> ok;
+    std::vector<int> ov;
+    ok.swap(keys_);
+    ov.swap(vals_);
+    clear(live_ + 16);
+    for (size_t i = 0; i < ok.size(); ++i)
+      if (ok[i] != kEmpty && ok[i] != kErased) insert(ok[i], ov[i]);
+  }
+  std::vector<uint64_t> keys_;
+  std::vector<int> vals_;
+  size_t used_ = 0, live_ = 0;
+};
 
 // Remap entry for regridding (Sec. 3.1).
 enum RemapKind : int { RM_COPY = 0, RM_INTERP = 1, RM_AVERAGE = 2 };
@@ -74,7 +159,7 @@ struct RemapEntry {
 struct HostForest {
   fc_forest_desc desc{};
   std::vector<Leaf> leaves;              // field order (forest, block, Morton)
-  std::unordered_map<uint64_t, int> idx; // key -> index in `leaves`
+  KeyMap idx;                            // key -> index in `leaves`
   std::vector<int> dev_of;               // leaves index -> device patch index
   std::vector<int> api_of;               // device patch index -> leaves index
   std::vector<PatchMeta> meta;           // device order
@@ -90,9 +175,10 @@ struct HostForest {
 
   // Build everything from `leaves`; returns an empty string or an error.
   std::string build();
+  std::string neighbour_rows(int pb, int pe);  // rows [pb, pe) of `nbr` and `meta` flags
+  std::string work_lists();
   int find(int f, int b, int l, int x, int y) const {
-    auto it = idx.find(leaf_key(f, b, l, x, y));
-    return it == idx.end() ? -1 : it->second;
+    return idx.find(leaf_key(f, b, l, x, y));
   }
   int npatch() const { return (int)leaves.size(); }
 };

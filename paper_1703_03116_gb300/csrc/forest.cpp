@@ -13,6 +13,7 @@
 // coarsened, and 2:1 balancing may add refinement.
 #include <algorithm>
 #include <cstdio>
+#include <thread>
 
 #include "fc_internal.hpp"
 
@@ -34,16 +35,45 @@ static uint64_t morton_key(const Leaf& a) {
 }
 
 void sort_leaves(std::vector<Leaf>* v) {
-  std::sort(v->begin(), v->end(), [](const Leaf& a, const Leaf& b) {
-    if (a.f != b.f) return a.f < b.f;
-    if (a.b != b.b) return a.b < b.b;
-    uint64_t ka = morton_key(a), kb = morton_key(b);
-    if (ka != kb) return ka < kb;
+  // order (forest, block, Morton key, level), keys computed once
+  struct K {
+    uint64_t fb, m;
+    int l;
+    Leaf a;
+  };
+  std::vector<K> ks(v->size());
+  for (size_t i = 0; i < v->size(); ++i) {
+    const Leaf& a = (*v)[i];
+    ks[i] = K{((uint64_t)(uint32_t)a.f << 8) | (uint32_t)a.b, morton_key(a), a.l, a};
+  }
+  std::sort(ks.begin(), ks.end(), [](const K& a, const K& b) {
+    if (a.fb != b.fb) return a.fb < b.fb;
+    if (a.m != b.m) return a.m < b.m;
     return a.l < b.l;
   });
+  for (size_t i = 0; i < v->size(); ++i) (*v)[i] = ks[i].a;
 }
 
 static int nblocks(const fc_forest_desc& d) { return d.domain == FC_DOMAIN_SPHERE ? 6 : 1; }
+
+// Run fn(begin, end) over [0, n) split into contiguous chunks on host
+// threads (one chunk when n is small); boundaries from `cut`, if given,
+// else even.
+template <class Fn>
+static void parallel_chunks(int n, int min_per_thread, Fn fn) {
+  const int hw = (int)std::max(1u, std::thread::hardware_concurrency());
+  const int nt = std::max(1, std::min(std::min(hw, 16), n / std::max(1, min_per_thread)));
+  if (nt <= 1) {
+    fn(0, n, 0);
+    return;
+  }
+  std::vector<std::thread> th;
+  for (int t = 0; t < nt; ++t) {
+    const int b = (int)((long)n * t / nt), e = (int)((long)n * (t + 1) / nt);
+    th.emplace_back([=]() { fn(b, e, t); });
+  }
+  for (auto& x : th) x.join();
+}
 
 namespace {
 
@@ -174,17 +204,15 @@ bool move_quadrant(const fc_forest_desc& d, int b, int l, int x, int y, int mx, 
 
 std::string HostForest::build() {
   const fc_forest_desc& d = desc;
-  const int mx = d.mx;
   const int nb = nblocks(d);
   sort_leaves(&leaves);
-  idx.clear();
-  idx.reserve(leaves.size() * 2);
+  idx.clear(leaves.size());
   for (size_t k = 0; k < leaves.size(); ++k) {
     const Leaf& a = leaves[k];
     if (a.f < 0 || a.f >= d.nforests || a.b < 0 || a.b >= nb || a.l < d.lmin || a.l > d.lmax ||
         a.x < 0 || a.y < 0 || a.x >= (1 << a.l) || a.y >= (1 << a.l))
       return "leaf out of range";
-    if (!idx.emplace(leaf_key(a.f, a.b, a.l, a.x, a.y), (int)k).second) return "duplicate leaf";
+    if (!idx.insert(leaf_key(a.f, a.b, a.l, a.x, a.y), (int)k)) return "duplicate leaf";
   }
   // exact tiling: areas of each block sum to one and no leaf has a leaf ancestor
   std::vector<double> area((size_t)d.nforests * nb, 0.0);
@@ -216,7 +244,23 @@ std::string HostForest::build() {
 
   meta.assign(n, PatchMeta{});
   nbr.assign((size_t)n * 8, NbrEntry{});
-  for (int p = 0; p < n; ++p) {
+  // the rows are independent (each reads the leaf tables only): host threads
+  // take contiguous ranges of patches on large layouts
+  std::vector<std::string> row_err(16);
+  parallel_chunks(n, 8192, [&](int pb, int pe, int tid) {
+    const std::string e = neighbour_rows(pb, pe);
+    if (!e.empty()) row_err[tid] = e;
+  });
+  for (const auto& e : row_err)
+    if (!e.empty()) return e;
+  // work lists
+  return work_lists();
+}
+
+std::string HostForest::neighbour_rows(int pb, int pe) {
+  const fc_forest_desc& d = desc;
+  const int mx = d.mx;
+  for (int p = pb; p < pe; ++p) {
     const Leaf& a = leaves[api_of[p]];
     meta[p] = PatchMeta{a.l, a.x, a.y, a.b, a.f, 0};
     for (int dir = 0; dir < 8; ++dir) {
@@ -292,7 +336,11 @@ std::string HostForest::build() {
       nbr[(size_t)p * 8 + dir] = e;
     }
   }
-  // work lists
+  return "";
+}
+
+std::string HostForest::work_lists() {
+  const int n = npatch();
   list_all.resize(n);
   list_coarse_all.clear();
   for (int p = 0; p < n; ++p) {
@@ -333,19 +381,19 @@ namespace {
 
 struct LeafSet {
   const fc_forest_desc* d;
-  std::unordered_map<uint64_t, Leaf> m;
+  KeyMap m;  // leaf key -> 1
   bool has(int f, int b, int l, int x, int y) const {
-    return m.count(leaf_key(f, b, l, x, y)) != 0;
+    return m.find(leaf_key(f, b, l, x, y)) >= 0;
   }
-  void add(const Leaf& a) { m.emplace(leaf_key(a.f, a.b, a.l, a.x, a.y), a); }
+  void add(const Leaf& a) { m.insert(leaf_key(a.f, a.b, a.l, a.x, a.y), 1); }
   void erase(const Leaf& a) { m.erase(leaf_key(a.f, a.b, a.l, a.x, a.y)); }
   // level of the leaf containing quadrant (b, l, x, y) if that leaf is at
   // level <= l, else -1 (the quadrant is subdivided)
   int holder_level(int f, int b, int l, int x, int y, Leaf* out) const {
     for (int k = l; k >= d->lmin; --k) {
-      auto it = m.find(leaf_key(f, b, k, x >> (l - k), y >> (l - k)));
-      if (it != m.end()) {
-        if (out) *out = it->second;
+      const int xs = x >> (l - k), ys = y >> (l - k);
+      if (m.find(leaf_key(f, b, k, xs, ys)) >= 0) {
+        if (out) *out = Leaf{f, b, k, xs, ys};
         return k;
       }
     }
@@ -406,19 +454,23 @@ bool parent_balanced(const LeafSet& s, const Leaf& P, int mx) {
 
 }  // namespace
 
-std::string regrid_layout(const HostForest& F, const std::vector<double>& delta, double tau_r,
-                          double tau_c, const std::vector<int>& lmax_f,
-                          std::vector<Leaf>* out) {
+namespace {
+
+// the new layout of the leaves [k0, k1) of F (whole forests: balance and
+// coarsening never cross a forest)
+void regrid_range(const HostForest& F, const std::vector<double>& delta, double tau_r,
+                  double tau_c, const std::vector<int>& lmax_f, int k0, int k1,
+                  std::vector<Leaf>* out) {
   const fc_forest_desc& d = F.desc;
   const int n = F.npatch();
   std::vector<char> refine(n, 0);
-  for (int k = 0; k < n; ++k) {
+  for (int k = k0; k < k1; ++k) {
     const Leaf& a = F.leaves[k];
     int lm = lmax_f.empty() ? d.lmax : std::min(lmax_f[a.f], d.lmax);
     refine[k] = (delta[k] > tau_r) && (a.l < lm);
   }
   std::vector<Leaf> parents;
-  for (int k = 0; k < n; ++k) {
+  for (int k = k0; k < k1; ++k) {
     const Leaf& a = F.leaves[k];
     if (a.l <= d.lmin || (a.x & 1) || (a.y & 1)) continue;
     bool ok = true;
@@ -430,11 +482,11 @@ std::string regrid_layout(const HostForest& F, const std::vector<double>& delta,
   }
   LeafSet s;
   s.d = &d;
-  s.m.reserve((size_t)n * 2);
-  for (int k = 0; k < n; ++k)
+  s.m.clear((size_t)(k1 - k0) * 2);
+  for (int k = k0; k < k1; ++k)
     if (!refine[k]) s.add(F.leaves[k]);
   std::vector<Leaf> fresh;
-  for (int k = 0; k < n; ++k)
+  for (int k = k0; k < k1; ++k)
     if (refine[k]) {
       const Leaf& a = F.leaves[k];
       for (int c = 0; c < 4; ++c) {
@@ -458,8 +510,30 @@ std::string regrid_layout(const HostForest& F, const std::vector<double>& delta,
   }
   out->clear();
   out->reserve(s.m.size());
-  for (const auto& kv : s.m) out->push_back(kv.second);
+  s.m.for_each([&](uint64_t k, int) { out->push_back(leaf_of_key(k)); });
   sort_leaves(out);
+}
+
+}  // namespace
+
+std::string regrid_layout(const HostForest& F, const std::vector<double>& delta, double tau_r,
+                          double tau_c, const std::vector<int>& lmax_f,
+                          std::vector<Leaf>* out) {
+  // forests are independent: host threads take contiguous ranges of forests
+  const int nf = F.desc.nforests;
+  const int n = F.npatch();
+  const int hw = (int)std::max(1u, std::thread::hardware_concurrency());
+  const int nt = std::max(1, std::min({hw, 16, nf, n / 8192}));
+  std::vector<std::vector<Leaf>> parts(nt);
+  parallel_chunks(nt, 1, [&](int tb, int te, int) {
+    for (int t = tb; t < te; ++t) {
+      const int f0 = (int)((long)nf * t / nt), f1 = (int)((long)nf * (t + 1) / nt);
+      regrid_range(F, delta, tau_r, tau_c, lmax_f, F.forest_start[f0], F.forest_start[f1],
+                   &parts[t]);
+    }
+  });
+  out->clear();
+  for (auto& pt : parts) out->insert(out->end(), pt.begin(), pt.end());
   return "";
 }
 
