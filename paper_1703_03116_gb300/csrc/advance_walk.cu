@@ -212,7 +212,7 @@ __global__ void __launch_bounds__(NW * 32) advance_walk_kernel(DevForest<real> D
     // and y-edge (li, r+1), finishes the fluxes of row r and updates row r-1
     real qa = Q(li, -2), qb = Q(li, -1), qc = Q(li, 0), qd = 0;
     real X_prev = 0, Gn_cur = 0, v_cur = 0, YP_cur = 0, Gf_prev = 0, dF_prev = 0;
-#pragma unroll
+#pragma unroll 2  // fully unrolled, the row walk overflowed the instruction cache
     for (int r = -1; r <= MX; ++r) {
       if (r + 2 <= MX + 1) qd = Q(li, r + 2);
       // x-edge (li, r): cells (li-1, r) | (li, r)
