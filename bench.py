@@ -245,6 +245,31 @@ def roofline_of(phase, peak_gbs, peak_src):
             "avg_launch_us": 1e3 * ms / max(n, 1), "bytes_per_launch": nbytes / max(n, 1)}
 
 
+# FP64 pipe operations (DADD, DMUL, DFMA, DMNMX, DSETP; one each) per cell
+# update of the wave-propagation update as the kernels compute it: per edge
+# 23 (speed split 2, jump and upwind jump 3, correction coefficient 3, MC
+# limiter 8, limited correction 1, flux 2, fluctuations 4), two edges per
+# cell; edge speeds 4; transverse increments of the two final fluxes 10;
+# fluctuation sums 2; flux difference and update 4.
+FP64_OPS_PER_CELL = 66
+# GB300 FP64 pipe: 2 operations per clock per SM
+FP64_OPS_PER_CLK_SM = 2
+GB300_SMS = 152
+
+
+def roofline_fp64_alu(phase, mx, sm_mhz):
+    """The FP64 update against the FP64 pipe (the bound in FP64 on this GPU):
+    achieved = FP64_OPS_PER_CELL x cells updated / advance-kernel time."""
+    ms, n, nbytes = phase
+    cells = nbytes * mx * mx / (((mx + 4) ** 2 + mx * mx) * 8.0)  # advance bytes -> cells
+    peak = FP64_OPS_PER_CLK_SM * GB300_SMS * sm_mhz * 1e6 / 1e9
+    achieved = FP64_OPS_PER_CELL * cells / (ms * 1e-3) / 1e9 if ms > 0 else None
+    return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Gop/s (FP64 pipe)",
+            "frac": achieved / peak if achieved else None, "ops_per_cell": FP64_OPS_PER_CELL,
+            "peak_source": f"{FP64_OPS_PER_CLK_SM} FP64 ops/clk/SM x {GB300_SMS} SMs x "
+                           f"{sm_mhz:.0f} MHz"}
+
+
 def adjoint_cost(fc, torch, flush_buf, ncoarse: int = 25):
     """Forward vs gradient cost of the adjoint workload: the swirl forest
     frozen after its initial regrid, 25 coarse multirate steps (400
@@ -429,6 +454,9 @@ def run_ours(args):
             "value": v["updates"] / (v["ms"] * 1e-3), "ms_per_step": v["ms"] / max(8, args.steps // 4),
             "roofline": roofline_of(v["phases"]["advance"], hbm, peak_src),
             "phases_ms": {k: x[0] for k, x in v["phases"].items()}}
+        if other == fc.F64:
+            variants["f64"]["roofline_fp64_alu"] = roofline_fp64_alu(
+                v["phases"]["advance"], 32, v["clocks"].get("sm_mhz") or 2070.0)
         del vr
         if args.ensemble > 0:
             # the ensemble at 32^2 in the line's dtype, at 16^2, and in the other dtype
@@ -449,6 +477,9 @@ def run_ours(args):
                     "roofline": roofline_of(b["phases"]["advance"], hbm, peak_src),
                     "phases_ms": {k: x[0] for k, x in b["phases"].items()},
                     "gpu_launches": b["launches"], "clocks": b["clocks"], "autotune": b["tuning"]}
+                if dtb == fc.F64:
+                    variants[key]["roofline_fp64_alu"] = roofline_fp64_alu(
+                        b["phases"]["advance"], mxb, b["clocks"].get("sm_mhz") or 2070.0)
                 del br
         sr = Runner(fc, torch, [synth.sphere(seed=0)], fc.F32)
         nsteps = 8

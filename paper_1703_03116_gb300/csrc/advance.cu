@@ -246,7 +246,7 @@ cudaError_t launch_advance_staged(const DevForest<real>& D, int p0, int p1, cons
   switch (D.mx) {
     case 8: return staged_launch<real, 8, 64>(D, p0, p1, a, err, s);
     case 16: return staged_launch<real, 16, 128>(D, p0, p1, a, err, s);
-    case 32: return staged_launch<real, 32, 256>(D, p0, p1, a, err, s);
+    case 32: return staged_launch<real, 32, 512>(D, p0, p1, a, err, s);
     default: return cudaErrorInvalidValue;
   }
 }
