@@ -111,7 +111,7 @@ __global__ void __launch_bounds__(NT) adj_advance_kernel(DevForest<real> D, AdvA
   real* Sy = Sx + NV;
   real* Tx = Sy + NV;
   real* Ty = Tx + NV;
-  __shared__ double red[NT];
+  __shared__ double red[NT / 32];
   __shared__ real ucoef_s;
   const int order = D.order, limiter = D.limiter, transverse = D.transverse;
   const bool swirl = D.vel_kind == FC_VEL_SWIRL;
@@ -119,7 +119,7 @@ __global__ void __launch_bounds__(NT) adj_advance_kernel(DevForest<real> D, AdvA
   const real nu = real(a.nu), hn = real(0.5 * a.nu), h = real(a.h);
   if (threadIdx.x == 0 && swirl) {
     const double t = a.t0_dev ? *a.t0_dev + a.t_off : a.t_half;  // graph replay: time on device
-    ucoef_s = real(cospi(t / a.period) * a.sfac);
+    ucoef_s = cospi_ratio<real>(t, a.period) * real(a.sfac);
   }
   __syncthreads();
   const real ucoef = swirl ? ucoef_s : real(0);
@@ -341,13 +341,15 @@ __global__ void __launch_bounds__(NT) adj_advance_kernel(DevForest<real> D, AdvA
     }
     __syncthreads();
   }
-  red[threadIdx.x] = (double)dsum;
+  // within warps by shuffles, then the warps' partial sums in FP64
+  for (int o = 16; o > 0; o >>= 1) dsum += __shfl_down_sync(0xffffffffu, dsum, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = (double)dsum;
   __syncthreads();
-  for (int w = NT / 2; w > 0; w >>= 1) {
-    if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
-    __syncthreads();
+  if (threadIdx.x < 32) {
+    double v = threadIdx.x < NT / 32 ? red[threadIdx.x] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if (threadIdx.x == 0) atomicAdd(dscale, v * dfac);
   }
-  if (threadIdx.x == 0) atomicAdd(dscale, red[0] * dfac);
 }
 
 // ---------------------------------------------------------------------

@@ -75,7 +75,7 @@ __global__ void __launch_bounds__(NT) advance_staged_kernel(DevForest<real> D, i
     mbar_init(&bar, 1);
     if (swirl) {
       const double t = a.t0_dev ? *a.t0_dev + a.t_off : a.t_half;
-      ucoef_s = real(cospi(t / a.period) * a.sfac);
+      ucoef_s = cospi_ratio<real>(t, a.period) * real(a.sfac);
     }
   }
   __syncthreads();

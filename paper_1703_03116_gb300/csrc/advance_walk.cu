@@ -98,7 +98,7 @@ __global__ void __launch_bounds__(NW * 32) advance_walk_kernel(DevForest<real> D
 
   if (threadIdx.x == 0 && SWIRL) {
     const double t = a.t0_dev ? *a.t0_dev + a.t_off : a.t_half;
-    ucoef_s = real(cospi(t / a.period) * a.sfac);
+    ucoef_s = cospi_ratio<real>(t, a.period) * real(a.sfac);
   }
   if (lane == 0) {
     mbar_init(&bars[warp][0], 1);

@@ -123,6 +123,17 @@ __device__ __forceinline__ float sinpi_r<float>(float x) { return sinpif(x); }
 template <>
 __device__ __forceinline__ double sinpi_r<double>(double x) { return sinpi(x); }
 
+// cos(pi t / T) in the field's precision (a CTA evaluates it once, on one
+// thread, while the others wait: FP64 is slow on this GPU)
+template <typename real>
+__device__ __forceinline__ real cospi_ratio(double t, double T);
+template <>
+__device__ __forceinline__ float cospi_ratio<float>(double t, double T) {
+  return cospif(float(t) / float(T));
+}
+template <>
+__device__ __forceinline__ double cospi_ratio<double>(double t, double T) { return cospi(t / T); }
+
 // phi(W_up / W) W for the MC limiter without a division:
 // 0 unless W and W_up share a sign, else sign(W) min(|W + W_up|/2, 2|W|, 2|W_up|)
 template <typename real>
