@@ -661,15 +661,17 @@ cudaError_t adjoint_sub_mx(const DevForest<real>& D, const AdjSubArgs& g, real* 
   const int n = g.p1 - g.p0;
   if (n <= 0) return cudaSuccess;
   const real alpha = real(g.alpha);
-  cudaError_t e = adj_advance_level<real, MX>(
-      D, g.L, g.p0, g.p1, g.t, g.dt, g.period, g.scale, g.dscale_factor, lam, lam, dscale, s,
-      g.t0_dev, static_cast<const real*>(g.tiles), g.tiles_p0, lamO);
-  if (e != cudaSuccess) return e;
-  adj_level_ghosts_kernel<real, MX><<<grid_for(n), 256, 0, s>>>(
-      D, g.p0, g.p1, lam, g.tlevel, alpha, lamT, lamO, static_cast<const real*>(g.coarse),
-      g.coarse_p0);
-  ++launch_counter();
-  if (g.nt > 0) {
+  if (g.part != 2) {
+    cudaError_t e = adj_advance_level<real, MX>(
+        D, g.L, g.p0, g.p1, g.t, g.dt, g.period, g.scale, g.dscale_factor, lam, lam, dscale, s,
+        g.t0_dev, static_cast<const real*>(g.tiles), g.tiles_p0, lamO);
+    if (e != cudaSuccess) return e;
+    adj_level_ghosts_kernel<real, MX><<<grid_for(n), 256, 0, s>>>(
+        D, g.p0, g.p1, lam, g.tlevel, alpha, lamT, lamO, static_cast<const real*>(g.coarse),
+        g.coarse_p0);
+    ++launch_counter();
+  }
+  if (g.nt > 0 && g.part != 1) {
     adj_coarse_tiles_kernel<real, MX><<<grid_for(g.nt), 256, 0, s>>>(D, g.list_t, g.nt, lam,
                                                                      g.tlevel, alpha, lamT, lamO);
     ++launch_counter();

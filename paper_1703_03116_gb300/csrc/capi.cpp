@@ -140,6 +140,7 @@ struct fc_forest {
   bool dag = false;
   cudaStream_t side = nullptr;
   cudaEvent_t ev_pre[kMaxLevel + 1] = {}, ev_post[kMaxLevel + 1] = {}, ev_fill[kMaxLevel + 1] = {};
+  cudaEvent_t ev_adj[2] = {};  // the adjoint graph's fork and join
   bool pre_ok[kMaxLevel + 1] = {}, post_ok[kMaxLevel + 1] = {};
   // the adjoint's replay of a coarse step: times relative to the step start
   // (on the device), and where each substep keeps the update's ghost-filled
@@ -546,6 +547,7 @@ fc_status ensure_side(fc_forest* F) {
   for (int l = 0; l <= kMaxLevel; ++l)
     for (cudaEvent_t* ev : {&F->ev_pre[l], &F->ev_post[l], &F->ev_fill[l]})
       FC_CUDA(cudaEventCreateWithFlags(ev, cudaEventDisableTiming));
+  for (cudaEvent_t& ev : F->ev_adj) FC_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
   return FC_OK;
 }
 
@@ -738,6 +740,8 @@ fc_status fc_forest_destroy(fc_forest* F) {
     for (int l = 0; l <= kMaxLevel; ++l)
       for (cudaEvent_t ev : {F->ev_pre[l], F->ev_post[l], F->ev_fill[l]})
         if (ev) cudaEventDestroy(ev);
+    for (cudaEvent_t ev : F->ev_adj)
+      if (ev) cudaEventDestroy(ev);
   }
   free_device(F);
   cudaStreamSynchronize(0);
@@ -1035,6 +1039,7 @@ static fc_status capture_adjoint_multirate(fc_forest* F, double dtc, cudaStream_
     for (int l = 0; l <= kMaxLevel; ++l) Lv.cur[l] = 0;
     if (e == cudaSuccess)
       e = launch_unpack(Lv, F->d_api_to_dev, static_cast<const real*>(F->mio), cs);
+    unsigned pending = 0;  // levels written by coarse-tile transposes still running beside
     for (size_t k = subs.size(); k-- > 0 && e == cudaSuccess;) {
       const Sub& u = subs[k];
       const int p0 = H.lev_start[u.L], p1 = H.lev_start[u.L + 1];
@@ -1063,7 +1068,30 @@ static fc_status capture_adjoint_multirate(fc_forest* F, double dtc, cudaStream_
       g.nb = (int)H.list_b[u.L].size();
       g.list_t = F->d_lists + F->off_t[u.L];
       g.nt = (int)H.list_t[u.L].size();
+      // the coarse tiles' transposes of an alpha = 1/2 substep (they write
+      // levels L-1 and L) run beside the reversed substeps of level L+1 that
+      // come next, which touch those levels only by commutative atomic adds;
+      // they are joined before the next update transpose of level L or L-1
+      if (e == cudaSuccess && (pending & ((1u << u.L) | (1u << (u.L + 1))))) {
+        e = cudaEventRecord(F->ev_adj[1], F->side);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, F->ev_adj[1], 0);
+        pending = 0;
+      }
+      const bool beside = std::fabs(u.alpha - 0.5) < 1e-9 && g.nt > 0;
+      g.part = beside ? 1 : 0;
       if (e == cudaSuccess) e = launch_adjoint_substep(dev<real>(F), g, LQ, LO, LT, F->d_ds, cs);
+      if (beside && e == cudaSuccess) {
+        e = cudaEventRecord(F->ev_adj[0], cs);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(F->side, F->ev_adj[0], 0);
+        g.part = 2;
+        if (e == cudaSuccess)
+          e = launch_adjoint_substep(dev<real>(F), g, LQ, LO, LT, F->d_ds, F->side);
+        pending |= (1u << u.L) | (1u << (u.L - 1));
+      }
+    }
+    if (pending && e == cudaSuccess) {  // join the side stream before the result is read
+      e = cudaEventRecord(F->ev_adj[1], F->side);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, F->ev_adj[1], 0);
     }
     if (e == cudaSuccess) e = launch_pack(Lv, F->d_api_to_dev, static_cast<real*>(F->mio), 0, cs);
     cp(F->buf[0], pool, store);

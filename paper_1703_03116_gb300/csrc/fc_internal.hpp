@@ -309,6 +309,9 @@ struct AdjSubArgs {
   int tiles_p0;
   const void* coarse;
   int coarse_p0;
+  // kernels to launch: 0 all three, 1 the update's and the level ghosts'
+  // transposes, 2 the coarse tiles' transposes alone
+  int part;
 };
 template <typename real>
 cudaError_t launch_adjoint_substep(const DevForest<real>& D, const AdjSubArgs& g, real* lam,
