@@ -9,11 +9,14 @@ each level substep the ghost fill (Alg. 1 phases) and the patch update, plus
 the regrid when it falls due.  Metric: cell updates per second, the paper's
 rate (mx^2 x patch advances / wall time).
 
-Variants on the same line: the same forest in FP64, and a batched ensemble
-of 256 independent swirl forests (maximum level drawn from {4,5,6}) advanced
-together -- one launch per level substep covers every forest.
+Variants on the same line: the same forest in FP64; a batched ensemble of
+256 independent swirl forests (maximum level drawn from {4,5,6}) advanced
+together -- one launch per level substep covers every forest -- at 32^2 and
+16^2 patches and in FP64; the cubed sphere (levels 1-7, capacity form); and
+the adjoint (gradient of a final-time misfit over 25 coarse multirate steps).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--mode full|batched|sphere|adjoint]
 
 Multi-GPU (torchrun): each rank advances its own independent forest (seeded
 by rank): weak scaling, no collective on the data path.  Prints one JSON line
