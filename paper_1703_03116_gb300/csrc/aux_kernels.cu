@@ -23,13 +23,16 @@ __global__ void tag_kernel(DevForest<real> D, double* delta) {
   const int mx = D.mx, S = D.S;
   for (int p = blockIdx.x; p < D.npatch; p += gridDim.x) {
     const real* Q = D.buf[D.cur[D.meta[p].level]] + (size_t)p * S * S;
+    // the indicator is max over cells of |grad q| / 2; the square root is
+    // monotone, so it is taken once, of the largest squared difference
+    // (same value, bit for bit, as the maximum of the per-cell roots)
     double m = 0.0;
     for (int k = threadIdx.x; k < mx * mx; k += blockDim.x) {
       const int i = k % mx + 2, j = k / mx + 2;
       const double gx = (double)Q[j * S + i + 1] - (double)Q[j * S + i - 1];
       const double gy = (double)Q[(j + 1) * S + i] - (double)Q[(j - 1) * S + i];
-      const double d = 0.5 * sqrt(gx * gx + gy * gy);
-      m = d > m ? d : m;
+      const double d2 = gx * gx + gy * gy;
+      m = d2 > m ? d2 : m;
     }
     red[threadIdx.x] = m;
     __syncthreads();
@@ -37,7 +40,7 @@ __global__ void tag_kernel(DevForest<real> D, double* delta) {
       if (threadIdx.x < w) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + w]);
       __syncthreads();
     }
-    if (threadIdx.x == 0) delta[p] = red[0];
+    if (threadIdx.x == 0) delta[p] = 0.5 * sqrt(red[0]);
     __syncthreads();
   }
 }

@@ -1437,37 +1437,46 @@ fc_status fc_tag_regrid(fc_forest* F, double tau_refine, double tau_coarsen,
   const HostForest& O = F->host;
   const HostForest& N = G->host;
   std::vector<RemapEntry> rm(N.npatch());
-  int created = 0, kept = 0;
-  for (int p = 0; p < N.npatch(); ++p) {
-    const Leaf& a = N.leaves[N.api_of[p]];
-    RemapEntry e{RM_COPY, {-1, -1, -1, -1}, 0, 0};
-    int o = O.find(a.f, a.b, a.l, a.x, a.y);
-    if (o >= 0) {
-      e.src[0] = O.dev_of[o];
-      ++kept;
-    } else {
-      ++created;
-      int par = a.l > 0 ? O.find(a.f, a.b, a.l - 1, a.x >> 1, a.y >> 1) : -1;
-      if (par >= 0) {
-        e.kind = RM_INTERP;
-        e.src[0] = O.dev_of[par];
-        e.cx = a.x & 1;
-        e.cy = a.y & 1;
+  // each entry reads the two layouts' tables only: host threads take ranges
+  std::vector<char> orphan(16, 0);
+  parallel_chunks(N.npatch(), 8192, [&](int pb, int pe, int tid) {
+    for (int p = pb; p < pe; ++p) {
+      const Leaf& a = N.leaves[N.api_of[p]];
+      RemapEntry e{RM_COPY, {-1, -1, -1, -1}, 0, 0};
+      int o = O.find(a.f, a.b, a.l, a.x, a.y);
+      if (o >= 0) {
+        e.src[0] = O.dev_of[o];
       } else {
-        e.kind = RM_AVERAGE;
-        for (int c = 0; c < 4; ++c) {
-          int ch = O.find(a.f, a.b, a.l + 1, 2 * a.x + (c & 1), 2 * a.y + (c >> 1));
-          if (ch < 0) {
-            free_device(G);
-            delete G;
-            return fail(FC_ERR_STATE, "regrid: new leaf has neither an old parent nor children");
+        int par = a.l > 0 ? O.find(a.f, a.b, a.l - 1, a.x >> 1, a.y >> 1) : -1;
+        if (par >= 0) {
+          e.kind = RM_INTERP;
+          e.src[0] = O.dev_of[par];
+          e.cx = a.x & 1;
+          e.cy = a.y & 1;
+        } else {
+          e.kind = RM_AVERAGE;
+          for (int c = 0; c < 4; ++c) {
+            int ch = O.find(a.f, a.b, a.l + 1, 2 * a.x + (c & 1), 2 * a.y + (c >> 1));
+            if (ch < 0) {
+              orphan[tid] = 1;
+              break;
+            }
+            e.src[c] = O.dev_of[ch];
           }
-          e.src[c] = O.dev_of[ch];
         }
       }
+      rm[p] = e;
     }
-    rm[p] = e;
-  }
+  });
+  for (char o : orphan)
+    if (o) {
+      free_device(G);
+      delete G;
+      return fail(FC_ERR_STATE, "regrid: new leaf has neither an old parent nor children");
+    }
+  int kept = 0;
+  for (const RemapEntry& e : rm) kept += e.kind == RM_COPY;
+  const int created = N.npatch() - kept;
   dfree(G->d_remap);
   if (dmalloc(&G->d_remap, rm.size()) != cudaSuccess) {
     free_device(G);

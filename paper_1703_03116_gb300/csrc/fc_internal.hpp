@@ -2,11 +2,17 @@
 // CUDA kernels.  Nothing here crosses the C ABI (include/fc.h).
 #pragma once
 
+#include <algorithm>
 #include <climits>
 #include <cstddef>
 #include <cstdint>
+#include <memory>
+#include <new>
 #include <string>
+#include <thread>
+#include <type_traits>
 #include <unordered_map>
+#include <utility>
 #include <vector>
 
 #include <cuda_runtime.h>
@@ -50,6 +56,47 @@ struct NbrEntry {
   int lev, x0, y0, x1, y1, pad;
 };
 
+// Allocator whose construct without arguments leaves trivially constructible
+// elements uninitialised: host tables that are written in full (by host
+// threads, which then also take the first-touch page faults in parallel)
+// skip a serial zero fill.
+template <class T>
+struct UninitAlloc : std::allocator<T> {
+  template <class U>
+  struct rebind {
+    using other = UninitAlloc<U>;
+  };
+  UninitAlloc() = default;
+  template <class U>
+  UninitAlloc(const UninitAlloc<U>&) noexcept {}
+  template <class U>
+  void construct(U* p) noexcept(std::is_nothrow_default_constructible<U>::value) {
+    ::new (static_cast<void*>(p)) U;
+  }
+  template <class U, class... A>
+  void construct(U* p, A&&... a) {
+    ::new (static_cast<void*>(p)) U(std::forward<A>(a)...);
+  }
+};
+
+// Run fn(begin, end, thread) over [0, n) split into even contiguous chunks on
+// host threads (one chunk, on the calling thread, when n is small).
+template <class Fn>
+inline void parallel_chunks(int n, int min_per_thread, Fn fn) {
+  const int hw = (int)std::max(1u, std::thread::hardware_concurrency());
+  const int nt = std::max(1, std::min(std::min(hw, 16), n / std::max(1, min_per_thread)));
+  if (nt <= 1) {
+    fn(0, n, 0);
+    return;
+  }
+  std::vector<std::thread> th;
+  for (int t = 0; t < nt; ++t) {
+    const int b = (int)((long)n * t / nt), e = (int)((long)n * (t + 1) / nt);
+    th.emplace_back([=]() { fn(b, e, t); });
+  }
+  for (auto& x : th) x.join();
+}
+
 struct PatchMeta {
   int level, x, y, block, forest, flags;  // flags bit 0: has a coarser neighbour
 };
@@ -70,60 +117,90 @@ inline Leaf leaf_of_key(uint64_t k) {
 // Leaf key -> int map with open addressing and linear probing (host tables
 // of up to millions of leaves; no allocation per entry).  Keys with the top
 // 16 bits all set never occur (forest < 65535) and mark empty / erased slots.
+// The probe of a key starts inside a window of slots that belongs to its
+// forest (the forest index picks the window, a hash of the key the slot in
+// it), so the lookups around one forest's leaves stay within a few
+// cache-resident kilobytes; probing itself runs on over the whole table.
 class KeyMap {
  public:
-  void clear(size_t n_expected = 0) {
+  // n_expected keys from nforests consecutive forests
+  void clear(size_t n_expected = 0, size_t nforests = 1) {
     size_t cap = 16;
     while (cap < 2 * n_expected + 2) cap <<= 1;
-    keys_.assign(cap, kEmpty);
-    vals_.assign(cap, 0);
+    slots_.assign(cap, Slot{kEmpty, 0});
+    forests_ = nforests < 1 ? 1 : nforests;
+    win_ = cap;
+    while (win_ > 16 && win_ * forests_ > cap) win_ >>= 1;
     used_ = live_ = 0;
   }
   // false if the key is present already
   bool insert(uint64_t k, int v) {
-    if (keys_.empty() || 2 * (used_ + 1) > keys_.size()) grow();
-    size_t i = mix(k) & (keys_.size() - 1), tomb = SIZE_MAX;
-    for (;; i = (i + 1) & (keys_.size() - 1)) {
-      if (keys_[i] == k) return false;
-      if (keys_[i] == kErased && tomb == SIZE_MAX) tomb = i;
-      if (keys_[i] == kEmpty) break;
+    if (slots_.empty() || 2 * (used_ + 1) > slots_.size()) grow();
+    const size_t mask = slots_.size() - 1;
+    size_t i = start(k), tomb = SIZE_MAX;
+    for (;; i = (i + 1) & mask) {
+      if (slots_[i].k == k) return false;
+      if (slots_[i].k == kErased && tomb == SIZE_MAX) tomb = i;
+      if (slots_[i].k == kEmpty) break;
     }
     if (tomb != SIZE_MAX) {
       i = tomb;
     } else {
       ++used_;
     }
-    keys_[i] = k;
-    vals_[i] = v;
+    slots_[i] = Slot{k, v};
     ++live_;
     return true;
   }
+  // Insert from several threads at once into a map just cleared for at
+  // least as many keys (no growth, no erased slots); false if the key is
+  // present.  The map is read only after the threads have joined, and the
+  // count is then set by set_size.
+  bool insert_concurrent(uint64_t k, int v) {
+    const size_t mask = slots_.size() - 1;
+    for (size_t i = start(k);; i = (i + 1) & mask) {
+      uint64_t seen = kEmpty;
+      if (__atomic_compare_exchange_n(&slots_[i].k, &seen, k, false, __ATOMIC_RELAXED,
+                                      __ATOMIC_RELAXED)) {
+        slots_[i].v = v;
+        return true;
+      }
+      if (seen == k) return false;
+    }
+  }
+  void set_size(size_t n) { used_ = live_ = n; }
   int find(uint64_t k) const {  // -1 if absent
-    if (keys_.empty()) return -1;
-    for (size_t i = mix(k) & (keys_.size() - 1);; i = (i + 1) & (keys_.size() - 1)) {
-      if (keys_[i] == k) return vals_[i];
-      if (keys_[i] == kEmpty) return -1;
+    if (slots_.empty()) return -1;
+    const size_t mask = slots_.size() - 1;
+    for (size_t i = start(k);; i = (i + 1) & mask) {
+      if (slots_[i].k == k) return slots_[i].v;
+      if (slots_[i].k == kEmpty) return -1;
     }
   }
   bool erase(uint64_t k) {
-    if (keys_.empty()) return false;
-    for (size_t i = mix(k) & (keys_.size() - 1);; i = (i + 1) & (keys_.size() - 1)) {
-      if (keys_[i] == k) {
-        keys_[i] = kErased;
+    if (slots_.empty()) return false;
+    const size_t mask = slots_.size() - 1;
+    for (size_t i = start(k);; i = (i + 1) & mask) {
+      if (slots_[i].k == k) {
+        slots_[i].k = kErased;
         --live_;
         return true;
       }
-      if (keys_[i] == kEmpty) return false;
+      if (slots_[i].k == kEmpty) return false;
     }
   }
   size_t size() const { return live_; }
   template <class Fn>
   void for_each(Fn fn) const {
-    for (size_t i = 0; i < keys_.size(); ++i)
-      if (keys_[i] != kEmpty && keys_[i] != kErased) fn(keys_[i], vals_[i]);
+    for (const Slot& e : slots_)
+      if (e.k != kEmpty && e.k != kErased) fn(e.k, e.v);
   }
 
  private:
+  struct Slot {
+    uint64_t k;
+    int v;
+  };
   static constexpr uint64_t kEmpty = ~0ull, kErased = ~0ull - 1;
   static uint64_t mix(uint64_t k) {  // a 64-bit finaliser (xor-shift-multiply)
     k ^= k >> 33;
@@ -133,17 +210,18 @@ class KeyMap {
     k ^= k >> 33;
     return k;
   }
-  void grow() {
-    std::vector<uint64_t> ok;
-    std::vector<int> ov;
-    ok.swap(keys_);
-    ov.swap(vals_);
-    clear(live_ + 16);
-    for (size_t i = 0; i < ok.size(); ++i)
-      if (ok[i] != kEmpty && ok[i] != kErased) insert(ok[i], ov[i]);
+  size_t start(uint64_t k) const {
+    return ((k >> 48) * win_ + (mix(k) & (win_ - 1))) & (slots_.size() - 1);
   }
-  std::vector<uint64_t> keys_;
-  std::vector<int> vals_;
+  void grow() {
+    std::vector<Slot> old;
+    old.swap(slots_);
+    clear(live_ + 16, forests_);
+    for (const Slot& e : old)
+      if (e.k != kEmpty && e.k != kErased) insert(e.k, e.v);
+  }
+  std::vector<Slot> slots_;
+  size_t forests_ = 1, win_ = 16;
   size_t used_ = 0, live_ = 0;
 };
 
@@ -162,8 +240,8 @@ struct HostForest {
   KeyMap idx;                            // key -> index in `leaves`
   std::vector<int> dev_of;               // leaves index -> device patch index
   std::vector<int> api_of;               // device patch index -> leaves index
-  std::vector<PatchMeta> meta;           // device order
-  std::vector<NbrEntry> nbr;             // device order, 8 per patch
+  std::vector<PatchMeta, UninitAlloc<PatchMeta>> meta;  // device order
+  std::vector<NbrEntry, UninitAlloc<NbrEntry>> nbr;     // device order, 8 per patch
   int lev_start[kMaxLevel + 2] = {0};    // device patches of level l: [lev_start[l], lev_start[l+1])
   std::vector<int> list_all, list_coarse_all;
   // multirate substep of level l: list_t = coarse neighbours (level l-1) of
@@ -172,10 +250,13 @@ struct HostForest {
   // neighbour
   std::vector<int> list_a[kMaxLevel + 1], list_b[kMaxLevel + 1], list_t[kMaxLevel + 1];
   std::vector<int> forest_start;         // leaves of forest f: [forest_start[f], forest_start[f+1])
+  std::vector<char> feeds_finer;         // device order: coarser neighbour of a patch one level finer
 
   // Build everything from `leaves`; returns an empty string or an error.
   std::string build();
-  std::string neighbour_rows(int pb, int pe);  // rows [pb, pe) of `nbr` and `meta` flags
+  // rows of `nbr` and `meta` for the leaves [kb, ke) (field order); marks
+  // feeds_finer
+  std::string neighbour_rows(int kb, int ke);
   std::string work_lists();
   int find(int f, int b, int l, int x, int y) const {
     return idx.find(leaf_key(f, b, l, x, y));

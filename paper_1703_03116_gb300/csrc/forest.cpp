@@ -12,6 +12,7 @@
 // Sec. 3.1: tagged grids are refined, quiet families of four siblings are
 // coarsened, and 2:1 balancing may add refinement.
 #include <algorithm>
+#include <cmath>
 #include <cstdio>
 #include <thread>
 
@@ -35,45 +36,31 @@ static uint64_t morton_key(const Leaf& a) {
 }
 
 void sort_leaves(std::vector<Leaf>* v) {
-  // order (forest, block, Morton key, level), keys computed once
+  // order (forest, block, Morton key, level)
   struct K {
     uint64_t fb, m;
     int l;
     Leaf a;
   };
-  std::vector<K> ks(v->size());
-  for (size_t i = 0; i < v->size(); ++i) {
-    const Leaf& a = (*v)[i];
-    ks[i] = K{((uint64_t)(uint32_t)a.f << 8) | (uint32_t)a.b, morton_key(a), a.l, a};
-  }
-  std::sort(ks.begin(), ks.end(), [](const K& a, const K& b) {
+  const auto key = [](const Leaf& a) {
+    return K{((uint64_t)(uint32_t)a.f << 8) | (uint32_t)a.b, morton_key(a), a.l, a};
+  };
+  const auto less = [](const K& a, const K& b) {
     if (a.fb != b.fb) return a.fb < b.fb;
     if (a.m != b.m) return a.m < b.m;
     return a.l < b.l;
-  });
+  };
+  // a regrid's output is in order already: check that without a copy
+  bool sorted = true;
+  for (size_t i = 1; sorted && i < v->size(); ++i) sorted = !less(key((*v)[i]), key((*v)[i - 1]));
+  if (sorted) return;
+  std::vector<K> ks(v->size());  // keys computed once
+  for (size_t i = 0; i < v->size(); ++i) ks[i] = key((*v)[i]);
+  std::sort(ks.begin(), ks.end(), less);
   for (size_t i = 0; i < v->size(); ++i) (*v)[i] = ks[i].a;
 }
 
 static int nblocks(const fc_forest_desc& d) { return d.domain == FC_DOMAIN_SPHERE ? 6 : 1; }
-
-// Run fn(begin, end) over [0, n) split into contiguous chunks on host
-// threads (one chunk when n is small); boundaries from `cut`, if given,
-// else even.
-template <class Fn>
-static void parallel_chunks(int n, int min_per_thread, Fn fn) {
-  const int hw = (int)std::max(1u, std::thread::hardware_concurrency());
-  const int nt = std::max(1, std::min(std::min(hw, 16), n / std::max(1, min_per_thread)));
-  if (nt <= 1) {
-    fn(0, n, 0);
-    return;
-  }
-  std::vector<std::thread> th;
-  for (int t = 0; t < nt; ++t) {
-    const int b = (int)((long)n * t / nt), e = (int)((long)n * (t + 1) / nt);
-    th.emplace_back([=]() { fn(b, e, t); });
-  }
-  for (auto& x : th) x.join();
-}
 
 namespace {
 
@@ -206,49 +193,74 @@ std::string HostForest::build() {
   const fc_forest_desc& d = desc;
   const int nb = nblocks(d);
   sort_leaves(&leaves);
-  idx.clear(leaves.size());
-  for (size_t k = 0; k < leaves.size(); ++k) {
-    const Leaf& a = leaves[k];
+  const int n = (int)leaves.size();
+  for (const Leaf& a : leaves)
     if (a.f < 0 || a.f >= d.nforests || a.b < 0 || a.b >= nb || a.l < d.lmin || a.l > d.lmax ||
         a.x < 0 || a.y < 0 || a.x >= (1 << a.l) || a.y >= (1 << a.l))
       return "leaf out of range";
-    if (!idx.insert(leaf_key(a.f, a.b, a.l, a.x, a.y), (int)k)) return "duplicate leaf";
-  }
-  // exact tiling: areas of each block sum to one and no leaf has a leaf ancestor
+  // the key map, filled by host threads (leaves of a thread: a few forests,
+  // whose probe windows are their own)
+  idx.clear(leaves.size(), d.nforests);
+  std::vector<char> dup(16, 0);
+  parallel_chunks(n, 16384, [&](int kb, int ke, int tid) {
+    for (int k = kb; k < ke; ++k) {
+      const Leaf& a = leaves[k];
+      if (!idx.insert_concurrent(leaf_key(a.f, a.b, a.l, a.x, a.y), k)) dup[tid] = 1;
+    }
+  });
+  idx.set_size(leaves.size());
+  for (char c : dup)
+    if (c) return "duplicate leaf";
+  // exact tiling: areas of each block sum to one and no leaf has a leaf
+  // ancestor (the ancestor lookups read the finished key map: host threads)
+  std::vector<char> overlap(16, 0);
+  parallel_chunks(n, 16384, [&](int kb, int ke, int tid) {
+    for (int k = kb; k < ke && !overlap[tid]; ++k) {
+      const Leaf& a = leaves[k];
+      for (int l = a.l - 1; l >= d.lmin; --l)
+        if (find(a.f, a.b, l, a.x >> (a.l - l), a.y >> (a.l - l)) >= 0) {
+          overlap[tid] = 1;
+          break;
+        }
+    }
+  });
+  for (char o : overlap)
+    if (o) return "overlapping leaves";
   std::vector<double> area((size_t)d.nforests * nb, 0.0);
-  for (const Leaf& a : leaves) {
-    area[(size_t)a.f * nb + a.b] += std::ldexp(1.0, -2 * a.l);
-    for (int l = a.l - 1; l >= d.lmin; --l)
-      if (find(a.f, a.b, l, a.x >> (a.l - l), a.y >> (a.l - l)) >= 0)
-        return "overlapping leaves";
-  }
+  for (const Leaf& a : leaves) area[(size_t)a.f * nb + a.b] += std::ldexp(1.0, -2 * a.l);
   for (double s : area)
     if (s != 1.0) return "leaves do not tile every block";
 
-  // device order: (level, field order)
-  const int n = (int)leaves.size();
-  std::vector<int> order(n);
-  for (int k = 0; k < n; ++k) order[k] = k;
-  std::stable_sort(order.begin(), order.end(),
-                   [&](int a, int b) { return leaves[a].l < leaves[b].l; });
-  api_of = order;
-  dev_of.assign(n, 0);
-  for (int p = 0; p < n; ++p) dev_of[api_of[p]] = p;
+  // device order: (level, field order), a counting sort by level
   for (int l = 0; l <= kMaxLevel + 1; ++l) lev_start[l] = 0;
-  for (int p = 0; p < n; ++p) lev_start[leaves[api_of[p]].l + 1]++;
+  for (const Leaf& a : leaves) lev_start[a.l + 1]++;
   for (int l = 1; l <= kMaxLevel + 1; ++l) lev_start[l] += lev_start[l - 1];
+  api_of.resize(n);
+  dev_of.resize(n);
+  {
+    int next[kMaxLevel + 1];
+    for (int l = 0; l <= kMaxLevel; ++l) next[l] = lev_start[l];
+    for (int k = 0; k < n; ++k) {
+      const int p = next[leaves[k].l]++;
+      api_of[p] = k;
+      dev_of[k] = p;
+    }
+  }
 
   forest_start.assign(d.nforests + 1, 0);
   for (const Leaf& a : leaves) forest_start[a.f + 1]++;
   for (int f = 0; f < d.nforests; ++f) forest_start[f + 1] += forest_start[f];
 
-  meta.assign(n, PatchMeta{});
-  nbr.assign((size_t)n * 8, NbrEntry{});
+  // every row is written below (no zero fill)
+  meta.resize(n);
+  nbr.resize((size_t)n * 8);
+  feeds_finer.assign(n, 0);
   // the rows are independent (each reads the leaf tables only): host threads
-  // take contiguous ranges of patches on large layouts
+  // take contiguous ranges of leaves in field order, so one thread's lookups
+  // stay within a few forests
   std::vector<std::string> row_err(16);
-  parallel_chunks(n, 8192, [&](int pb, int pe, int tid) {
-    const std::string e = neighbour_rows(pb, pe);
+  parallel_chunks(n, 8192, [&](int kb, int ke, int tid) {
+    const std::string e = neighbour_rows(kb, ke);
     if (!e.empty()) row_err[tid] = e;
   });
   for (const auto& e : row_err)
@@ -257,14 +269,16 @@ std::string HostForest::build() {
   return work_lists();
 }
 
-std::string HostForest::neighbour_rows(int pb, int pe) {
+std::string HostForest::neighbour_rows(int kb, int ke) {
   const fc_forest_desc& d = desc;
   const int mx = d.mx;
-  for (int p = pb; p < pe; ++p) {
-    const Leaf& a = leaves[api_of[p]];
+  for (int k = kb; k < ke; ++k) {
+    const int p = dev_of[k];
+    const Leaf& a = leaves[k];
     meta[p] = PatchMeta{a.l, a.x, a.y, a.b, a.f, 0};
     for (int dir = 0; dir < 8; ++dir) {
       NbrEntry e{NB_EXTERIOR, -1, -1, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+      int k0 = -1, k1 = -1;  // the neighbours' leaf indices
       Moved m;
       if (move_quadrant(d, a.b, a.l, a.x + kDirX[dir], a.y + kDirY[dir], mx, &m)) {
         e.a = m.a;
@@ -273,13 +287,15 @@ std::string HostForest::neighbour_rows(int pb, int pe) {
         int s = find(a.f, m.b, a.l, m.x, m.y);
         if (s >= 0) {
           e.kind = NB_SAME;
-          e.n0 = dev_of[s];
+          k0 = s;
         } else {
           int c = (a.l > d.lmin) ? find(a.f, m.b, a.l - 1, m.x >> 1, m.y >> 1) : -1;
           if (c >= 0) {
             e.kind = NB_COARSE;
-            e.n0 = dev_of[c];
+            k0 = c;
             meta[p].flags |= 1;
+            // several threads may mark the same patch: all store the same byte
+            __atomic_store_n(&feeds_finer[dev_of[c]], (char)1, __ATOMIC_RELAXED);
           } else {
             // finer: the children of the same-size quadrant that touch this
             // patch, on its side facing back along the direction of travel
@@ -303,9 +319,9 @@ std::string HostForest::neighbour_rows(int pb, int pe) {
               cx[1] = 2 * m.x + 1;
             }
             int ids[2] = {-1, -1};
-            for (int k = 0; k < nc; ++k) {
-              ids[k] = (a.l < d.lmax) ? find(a.f, m.b, a.l + 1, cx[k], cy[k]) : -1;
-              if (ids[k] < 0) {
+            for (int q = 0; q < nc; ++q) {
+              ids[q] = (a.l < d.lmax) ? find(a.f, m.b, a.l + 1, cx[q], cy[q]) : -1;
+              if (ids[q] < 0) {
                 char buf[160];
                 std::snprintf(buf, sizeof buf,
                               "leaf (f=%d b=%d l=%d x=%d y=%d): region %d has no neighbour within "
@@ -315,21 +331,23 @@ std::string HostForest::neighbour_rows(int pb, int pe) {
               }
             }
             e.kind = NB_FINE;
-            e.n0 = dev_of[ids[0]];
-            e.n1 = nc == 2 ? dev_of[ids[1]] : -1;
+            k0 = ids[0];
+            k1 = nc == 2 ? ids[1] : -1;
           }
         }
       } else if (m.corner3) {
         e.kind = NB_CORNER3;
       }
-      if (e.n0 >= 0) {
-        const Leaf& n0 = leaves[api_of[e.n0]];
+      if (k0 >= 0) {
+        const Leaf& n0 = leaves[k0];
+        e.n0 = dev_of[k0];
         e.lev = n0.l;
         e.x0 = n0.x;
         e.y0 = n0.y;
       }
-      if (e.n1 >= 0) {
-        const Leaf& n1 = leaves[api_of[e.n1]];
+      if (k1 >= 0) {
+        const Leaf& n1 = leaves[k1];
+        e.n1 = dev_of[k1];
         e.x1 = n1.x;
         e.y1 = n1.y;
       }
@@ -343,6 +361,9 @@ std::string HostForest::work_lists() {
   const int n = npatch();
   list_all.resize(n);
   list_coarse_all.clear();
+  // feeds_finer[p]: p is the coarser neighbour of a patch one level finer
+  // (2:1 balance: a coarse neighbour is always exactly one level coarser)
+  const std::vector<char>& inT = feeds_finer;
   for (int p = 0; p < n; ++p) {
     list_all[p] = p;
     if (meta[p].flags & 1) list_coarse_all.push_back(p);
@@ -351,26 +372,16 @@ std::string HostForest::work_lists() {
     list_a[l].clear();
     list_b[l].clear();
     list_t[l].clear();
-  }
-  for (int l = 0; l <= kMaxLevel; ++l) {
-    std::vector<char> inT;
-    if (l > 0) inT.assign(n, 0);
-    for (int p = lev_start[l]; p < lev_start[l + 1]; ++p) {
-      if (meta[p].flags & 1) {
-        list_b[l].push_back(p);
-        for (int dir = 0; dir < 8; ++dir) {
-          const NbrEntry& e = nbr[(size_t)p * 8 + dir];
-          if (e.kind == NB_COARSE) inT[e.n0] = 1;
-        }
-      }
-    }
     if (l > 0)
       for (int p = lev_start[l - 1]; p < lev_start[l]; ++p)
         if (inT[p]) {
           list_a[l].push_back(p);
           list_t[l].push_back(p);
         }
-    for (int p = lev_start[l]; p < lev_start[l + 1]; ++p) list_a[l].push_back(p);
+    for (int p = lev_start[l]; p < lev_start[l + 1]; ++p) {
+      list_a[l].push_back(p);
+      if (meta[p].flags & 1) list_b[l].push_back(p);
+    }
   }
   return "";
 }
@@ -482,7 +493,7 @@ void regrid_range(const HostForest& F, const std::vector<double>& delta, double 
   }
   LeafSet s;
   s.d = &d;
-  s.m.clear((size_t)(k1 - k0) * 2);
+  s.m.clear((size_t)(k1 - k0) * 2, k1 > k0 ? F.leaves[k1 - 1].f - F.leaves[k0].f + 1 : 1);
   for (int k = k0; k < k1; ++k)
     if (!refine[k]) s.add(F.leaves[k]);
   std::vector<Leaf> fresh;
