@@ -258,8 +258,38 @@ struct HostForest {
   // feeds_finer
   std::string neighbour_rows(int kb, int ke);
   std::string work_lists();
+  // dense leaf lookup (when `dense`): owner[own_off[f] + (b << 2 lo) +
+  // (Y << lo) + X] is the leaf covering cell (X, Y) of block b at level
+  // lo = own_lo[f], forest f's finest occupied level
+  bool dense = false;
+  std::vector<int, UninitAlloc<int>> owner;
+  std::vector<size_t> own_off;
+  std::vector<int> own_lo;
+  // the leaf (b, l, x, y) of forest f, or -1 (in-range f, b expected)
   int find(int f, int b, int l, int x, int y) const {
+    if (dense) {
+      const int lo = own_lo[f];
+      if (l > lo || l < 0 || x < 0 || y < 0 || x >= (1 << l) || y >= (1 << l)) return -1;
+      const int s = lo - l;
+      const int k = owner[own_off[f] + ((size_t)b << (2 * lo)) + ((size_t)(y << s) << lo) +
+                          (x << s)];
+      return leaves[k].l == l ? k : -1;
+    }
     return idx.find(leaf_key(f, b, l, x, y));
+  }
+  // the leaf covering quadrant (b, l, x, y) of forest f if it is at level l
+  // or l - 1, else -1 (the quadrant is subdivided, or lies in a leaf two or
+  // more levels coarser); quadrant in range and l <= own_lo[f] expected
+  int holder(int f, int b, int l, int x, int y) const {
+    if (dense) {
+      const int lo = own_lo[f], s = lo - l;
+      const int k = owner[own_off[f] + ((size_t)b << (2 * lo)) + ((size_t)(y << s) << lo) +
+                          (x << s)];
+      const int lk = leaves[k].l;
+      return lk == l || lk == l - 1 ? k : -1;
+    }
+    const int k = idx.find(leaf_key(f, b, l, x, y));
+    return k >= 0 || l == 0 ? k : idx.find(leaf_key(f, b, l - 1, x >> 1, y >> 1));
   }
   int npatch() const { return (int)leaves.size(); }
 };

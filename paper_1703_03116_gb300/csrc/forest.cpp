@@ -198,38 +198,82 @@ std::string HostForest::build() {
     if (a.f < 0 || a.f >= d.nforests || a.b < 0 || a.b >= nb || a.l < d.lmin || a.l > d.lmax ||
         a.x < 0 || a.y < 0 || a.x >= (1 << a.l) || a.y >= (1 << a.l))
       return "leaf out of range";
-  // the key map, filled by host threads (leaves of a thread: a few forests,
-  // whose probe windows are their own)
-  idx.clear(leaves.size(), d.nforests);
-  std::vector<char> dup(16, 0);
-  parallel_chunks(n, 16384, [&](int kb, int ke, int tid) {
-    for (int k = kb; k < ke; ++k) {
-      const Leaf& a = leaves[k];
-      if (!idx.insert_concurrent(leaf_key(a.f, a.b, a.l, a.x, a.y), k)) dup[tid] = 1;
-    }
-  });
-  idx.set_size(leaves.size());
-  for (char c : dup)
-    if (c) return "duplicate leaf";
-  // exact tiling: areas of each block sum to one and no leaf has a leaf
-  // ancestor (the ancestor lookups read the finished key map: host threads)
-  std::vector<char> overlap(16, 0);
-  parallel_chunks(n, 16384, [&](int kb, int ke, int tid) {
-    for (int k = kb; k < ke && !overlap[tid]; ++k) {
-      const Leaf& a = leaves[k];
-      for (int l = a.l - 1; l >= d.lmin; --l)
-        if (find(a.f, a.b, l, a.x >> (a.l - l), a.y >> (a.l - l)) >= 0) {
-          overlap[tid] = 1;
-          break;
+  forest_start.assign(d.nforests + 1, 0);
+  for (const Leaf& a : leaves) forest_start[a.f + 1]++;
+  for (int f = 0; f < d.nforests; ++f) forest_start[f + 1] += forest_start[f];
+
+  // Leaf lookup.  Where it is small, a dense map from every cell of each
+  // block's finest occupied level to the leaf covering it (filling it also
+  // checks that the leaves tile every block exactly); else the key map.
+  own_lo.assign(d.nforests, 0);
+  for (const Leaf& a : leaves) own_lo[a.f] = std::max(own_lo[a.f], a.l);
+  own_off.assign(d.nforests + 1, 0);
+  for (int f = 0; f < d.nforests; ++f)
+    own_off[f + 1] = own_off[f] + ((size_t)nb << (2 * own_lo[f]));
+  dense = own_off[d.nforests] <= std::max<size_t>((size_t)1 << 22, 64 * (size_t)n);
+  if (dense) {
+    owner.resize(own_off[d.nforests]);
+    // forests are independent: host threads take ranges of forests
+    std::vector<int> bad(16, 0);  // 1 overlap, 2 a cell without a leaf
+    const int per = std::max(1, 16384 / std::max(1, n / std::max(1, d.nforests)));
+    parallel_chunks(d.nforests, per, [&](int fb, int fe, int tid) {
+      for (int f = fb; f < fe && !bad[tid]; ++f) {
+        const int lo = own_lo[f];
+        int* own = owner.data() + own_off[f];
+        std::fill(own, owner.data() + own_off[f + 1], -1);
+        for (int k = forest_start[f]; k < forest_start[f + 1] && !bad[tid]; ++k) {
+          const Leaf& a = leaves[k];
+          const int s = lo - a.l, w = 1 << s;
+          int* o = own + ((size_t)a.b << (2 * lo)) + ((size_t)(a.y << s) << lo) + (a.x << s);
+          for (int j = 0; j < w; ++j, o += (size_t)1 << lo)
+            for (int i = 0; i < w; ++i) {
+              if (o[i] >= 0) bad[tid] = 1;
+              o[i] = k;
+            }
         }
+        for (const int* o = own; !bad[tid] && o < owner.data() + own_off[f + 1]; ++o)
+          if (*o < 0) bad[tid] = 2;
+      }
+    });
+    for (int e : bad) {
+      if (e == 1) return "overlapping leaves";
+      if (e == 2) return "leaves do not tile every block";
     }
-  });
-  for (char o : overlap)
-    if (o) return "overlapping leaves";
-  std::vector<double> area((size_t)d.nforests * nb, 0.0);
-  for (const Leaf& a : leaves) area[(size_t)a.f * nb + a.b] += std::ldexp(1.0, -2 * a.l);
-  for (double s : area)
-    if (s != 1.0) return "leaves do not tile every block";
+  } else {
+    owner.clear();
+    // the key map, filled by host threads (leaves of a thread: a few
+    // forests, whose probe windows are their own)
+    idx.clear(leaves.size(), d.nforests);
+    std::vector<char> dup(16, 0);
+    parallel_chunks(n, 16384, [&](int kb, int ke, int tid) {
+      for (int k = kb; k < ke; ++k) {
+        const Leaf& a = leaves[k];
+        if (!idx.insert_concurrent(leaf_key(a.f, a.b, a.l, a.x, a.y), k)) dup[tid] = 1;
+      }
+    });
+    idx.set_size(leaves.size());
+    for (char c : dup)
+      if (c) return "duplicate leaf";
+    // exact tiling: areas of each block sum to one and no leaf has a leaf
+    // ancestor (the ancestor lookups read the finished key map: host threads)
+    std::vector<char> overlap(16, 0);
+    parallel_chunks(n, 16384, [&](int kb, int ke, int tid) {
+      for (int k = kb; k < ke && !overlap[tid]; ++k) {
+        const Leaf& a = leaves[k];
+        for (int l = a.l - 1; l >= d.lmin; --l)
+          if (find(a.f, a.b, l, a.x >> (a.l - l), a.y >> (a.l - l)) >= 0) {
+            overlap[tid] = 1;
+            break;
+          }
+      }
+    });
+    for (char o : overlap)
+      if (o) return "overlapping leaves";
+    std::vector<double> area((size_t)d.nforests * nb, 0.0);
+    for (const Leaf& a : leaves) area[(size_t)a.f * nb + a.b] += std::ldexp(1.0, -2 * a.l);
+    for (double s : area)
+      if (s != 1.0) return "leaves do not tile every block";
+  }
 
   // device order: (level, field order), a counting sort by level
   for (int l = 0; l <= kMaxLevel + 1; ++l) lev_start[l] = 0;
@@ -246,10 +290,6 @@ std::string HostForest::build() {
       dev_of[k] = p;
     }
   }
-
-  forest_start.assign(d.nforests + 1, 0);
-  for (const Leaf& a : leaves) forest_start[a.f + 1]++;
-  for (int f = 0; f < d.nforests; ++f) forest_start[f + 1] += forest_start[f];
 
   // every row is written below (no zero fill)
   meta.resize(n);
@@ -284,12 +324,12 @@ std::string HostForest::neighbour_rows(int kb, int ke) {
         e.a = m.a;
         e.fx = m.fx;
         e.fy = m.fy;
-        int s = find(a.f, m.b, a.l, m.x, m.y);
-        if (s >= 0) {
+        const int h = holder(a.f, m.b, a.l, m.x, m.y);
+        if (h >= 0 && leaves[h].l == a.l) {
           e.kind = NB_SAME;
-          k0 = s;
+          k0 = h;
         } else {
-          int c = (a.l > d.lmin) ? find(a.f, m.b, a.l - 1, m.x >> 1, m.y >> 1) : -1;
+          const int c = h;  // a coarser leaf, one level up
           if (c >= 0) {
             e.kind = NB_COARSE;
             k0 = c;

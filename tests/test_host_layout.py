@@ -86,9 +86,34 @@ def test_neighbour_table_matches_brute_force(domain):
         w.domain = "periodic"
     F = oracle.initial_forest(w)
     lv = F.leaves()
-    nb = fc.layout_neighbours(desc_for(w), lv)
+    check_neighbours_by_brute_force(fc.layout_neighbours(desc_for(w), lv), lv,
+                                    domain == "periodic")
+
+
+def test_deep_layout_matches_brute_force():
+    """A layout refined towards one point down to level 12.  A map of its
+    finest-level cells would hold 4^12 entries, so leaves are looked up
+    through the key map: the same neighbour table, the same regrid."""
+    w = synth.swirl(0, lmin=2, lmax=12, mx=8)
+    d = desc_for(w)
+    lv = np.array([(0, 0, 2, x, y) for y in range(4) for x in range(4)], dtype=np.int32)
+    px, py = 0.3141, 0.2718
+    for _ in range(10):
+        h = 2.0 ** -lv[:, 2].astype(float)
+        inside = ((lv[:, 3] * h <= px) & (px < (lv[:, 3] + 1) * h) &
+                  (lv[:, 4] * h <= py) & (py < (lv[:, 4] + 1) * h))
+        lv = fc.layout_regrid(d, lv, inside.astype(float), 0.5, -1.0)
+    assert lv[:, 2].max() == 12 and len(lv) < 400
+    fc.layout_check(d, lv)
+    check_neighbours_by_brute_force(fc.layout_neighbours(d, lv), lv, False)
+    # coarsening everything back: families merge level by level, balanced
+    for _ in range(10):
+        lv = fc.layout_regrid(d, lv, np.zeros(len(lv)), 0.5, 0.25)
+    assert len(lv) == 16 and set(lv[:, 2]) == {2}
+
+
+def check_neighbours_by_brute_force(nb, lv, per):
     dirs = [(-1, 0), (1, 0), (0, -1), (0, 1), (-1, -1), (1, -1), (-1, 1), (1, 1)]
-    per = domain == "periodic"
     kinds = np.zeros(4, int)
     for k, (f, b, l, x, y) in enumerate(lv):
         for d, (ox, oy) in enumerate(dirs):
