@@ -137,7 +137,8 @@ fc_status fc_step_global(fc_forest* forest, double t, double dt, void* stream);
 fc_status fc_step_multirate(fc_forest* forest, double t, double dt_coarse, void* stream);
 
 /* Tag and regrid (Sec. 3.1).  Fills ghosts, computes on the device the
- * per-leaf indicator max 1/2 |(q(i+1,j)-q(i-1,j), q(i,j+1)-q(i,j-1))| (FP64),
+ * per-leaf indicator max 1/2 |(q(i+1,j)-q(i-1,j), q(i,j+1)-q(i,j-1))| (in
+ * the field's precision; the square root in FP64),
  * refines leaves above tau_refine (below their forest's maximum level
  * lmax_per_forest[f], or desc.lmax when NULL), 2:1 balances by refinement,
  * coarsens families of four leaves all below tau_coarsen whose parent stays

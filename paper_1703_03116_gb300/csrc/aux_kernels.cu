@@ -17,30 +17,36 @@ uint64_t& launch_counter() {
 namespace {
 // ------------------------------------------------------------------ tag
 
+// The indicator is max over cells of |grad q| / 2 (central differences),
+// computed in the field's precision (FP64 on a GPU whose FP64 rate is a
+// small fraction of FP32 would bound this memory-bound pass by arithmetic).
+// The square root is monotone, so it is taken once per patch, of the largest
+// squared difference: the same value, bit for bit, as the maximum of the
+// per-cell roots.
 template <typename real>
 __global__ void tag_kernel(DevForest<real> D, double* delta) {
-  __shared__ double red[256];
+  __shared__ real red[256];
   const int mx = D.mx, S = D.S;
   for (int p = blockIdx.x; p < D.npatch; p += gridDim.x) {
     const real* Q = D.buf[D.cur[D.meta[p].level]] + (size_t)p * S * S;
-    // the indicator is max over cells of |grad q| / 2; the square root is
-    // monotone, so it is taken once, of the largest squared difference
-    // (same value, bit for bit, as the maximum of the per-cell roots)
-    double m = 0.0;
+    real m = real(0);
     for (int k = threadIdx.x; k < mx * mx; k += blockDim.x) {
       const int i = k % mx + 2, j = k / mx + 2;
-      const double gx = (double)Q[j * S + i + 1] - (double)Q[j * S + i - 1];
-      const double gy = (double)Q[(j + 1) * S + i] - (double)Q[(j - 1) * S + i];
-      const double d2 = gx * gx + gy * gy;
+      const real gx = Q[j * S + i + 1] - Q[j * S + i - 1];
+      const real gy = Q[(j + 1) * S + i] - Q[(j - 1) * S + i];
+      const real d2 = gx * gx + gy * gy;
       m = d2 > m ? d2 : m;
     }
     red[threadIdx.x] = m;
     __syncthreads();
     for (int w = blockDim.x / 2; w > 0; w >>= 1) {
-      if (threadIdx.x < w) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + w]);
+      if (threadIdx.x < w) {
+        const real o = red[threadIdx.x + w];
+        if (o > red[threadIdx.x]) red[threadIdx.x] = o;
+      }
       __syncthreads();
     }
-    if (threadIdx.x == 0) delta[p] = 0.5 * sqrt(red[0]);
+    if (threadIdx.x == 0) delta[p] = 0.5 * sqrt((double)red[0]);
     __syncthreads();
   }
 }

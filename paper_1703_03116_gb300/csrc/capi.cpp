@@ -86,6 +86,10 @@ struct fc_forest {
   void* buf[2] = {nullptr, nullptr};
   void* qT = nullptr;
   void* stage = nullptr;  // device staging for host copies
+  // the layout's small tables and per-patch scratch share one allocation
+  // (d_tables, filled by one copy): d_meta, d_lists, d_api_to_dev, d_fstart,
+  // d_patch_sums, d_mass and d_delta point into it
+  void* d_tables = nullptr;
   PatchMeta* d_meta = nullptr;
   NbrEntry* d_nbr = nullptr;
   int* d_lists = nullptr;  // all work lists, concatenated
@@ -284,19 +288,24 @@ void destroy_timers(fc_forest* F) {
   F->spare.clear();
 }
 
+void free_tables(fc_forest* F) {
+  dfree(F->d_tables);
+  dfree(F->d_nbr);
+  F->d_meta = nullptr;
+  F->d_lists = nullptr;
+  F->d_api_to_dev = nullptr;
+  F->d_fstart = nullptr;
+  F->d_patch_sums = nullptr;
+  F->d_mass = nullptr;
+  F->d_delta = nullptr;
+}
+
 void free_device(fc_forest* F) {
   dfree(F->buf[0]);
   dfree(F->buf[1]);
   dfree(F->qT);
   dfree(F->stage);
-  dfree(F->d_meta);
-  dfree(F->d_nbr);
-  dfree(F->d_lists);
-  dfree(F->d_api_to_dev);
-  dfree(F->d_fstart);
-  dfree(F->d_patch_sums);
-  dfree(F->d_mass);
-  dfree(F->d_delta);
+  free_tables(F);
   dfree(F->d_remap);
   dfree(F->d_err);
   dfree(F->d_t0);
@@ -351,21 +360,8 @@ fc_status upload(fc_forest* F, bool alloc_store, bool metrics = true) {
       return fail(FC_ERR_OOM, "device store allocation failed");
     FC_CUDA(cudaMemsetAsync(F->qT, 0, std::max<size_t>(cells, 1) * F->esize, g_alloc_stream));
   }
-  dfree(F->d_meta);
-  dfree(F->d_nbr);
-  dfree(F->d_lists);
-  dfree(F->d_api_to_dev);
-  dfree(F->d_fstart);
-  dfree(F->d_patch_sums);
-  dfree(F->d_mass);
-  dfree(F->d_delta);
-  FC_CUDA(dmalloc(&F->d_meta, n));
-  FC_CUDA(dmalloc(&F->d_nbr, (size_t)n * 8));
-  // (host sources are pageable: each copy has taken its data when it returns)
-  FC_CUDA(cudaMemcpyAsync(F->d_meta, H.meta.data(), sizeof(PatchMeta) * n, cudaMemcpyHostToDevice,
-                          g_alloc_stream));
-  FC_CUDA(cudaMemcpyAsync(F->d_nbr, H.nbr.data(), sizeof(NbrEntry) * n * 8,
-                          cudaMemcpyHostToDevice, g_alloc_stream));
+  free_tables(F);
+  // every work list, concatenated
   std::vector<int> lists;
   F->off_all = lists.size();
   lists.insert(lists.end(), H.list_all.begin(), H.list_all.end());
@@ -379,20 +375,40 @@ fc_status upload(fc_forest* F, bool alloc_store, bool metrics = true) {
     F->off_t[l] = lists.size();
     lists.insert(lists.end(), H.list_t[l].begin(), H.list_t[l].end());
   }
-  FC_CUDA(dmalloc(&F->d_lists, lists.size()));
-  if (!lists.empty())
-    FC_CUDA(cudaMemcpyAsync(F->d_lists, lists.data(), sizeof(int) * lists.size(),
-                            cudaMemcpyHostToDevice, g_alloc_stream));
-  FC_CUDA(dmalloc(&F->d_api_to_dev, n));
-  FC_CUDA(cudaMemcpyAsync(F->d_api_to_dev, H.dev_of.data(), sizeof(int) * n,
-                          cudaMemcpyHostToDevice, g_alloc_stream));
-  FC_CUDA(dmalloc(&F->d_fstart, H.forest_start.size()));
-  FC_CUDA(cudaMemcpyAsync(F->d_fstart, H.forest_start.data(),
-                          sizeof(int) * H.forest_start.size(), cudaMemcpyHostToDevice,
+  // one block: the uploaded tables, then the device-written scratch (each
+  // part 16-byte aligned)
+  const int nf = H.desc.nforests;
+  size_t off = 0;
+  const auto part = [&](size_t bytes) {
+    const size_t at = off;
+    off += (bytes + 15) & ~(size_t)15;
+    return at;
+  };
+  const size_t o_meta = part(sizeof(PatchMeta) * n), o_lists = part(sizeof(int) * lists.size()),
+               o_api = part(sizeof(int) * n), o_fstart = part(sizeof(int) * (nf + 1));
+  const size_t uploaded = off;
+  const size_t o_sums = part(sizeof(double) * n), o_mass = part(sizeof(double) * nf),
+               o_delta = part(sizeof(double) * n);
+  std::vector<char> host(uploaded, 0);
+  std::memcpy(host.data() + o_meta, H.meta.data(), sizeof(PatchMeta) * n);
+  if (!lists.empty()) std::memcpy(host.data() + o_lists, lists.data(), sizeof(int) * lists.size());
+  std::memcpy(host.data() + o_api, H.dev_of.data(), sizeof(int) * n);
+  std::memcpy(host.data() + o_fstart, H.forest_start.data(), sizeof(int) * (nf + 1));
+  FC_CUDA(dmalloc_bytes(&F->d_tables, off));
+  char* base = static_cast<char*>(F->d_tables);
+  F->d_meta = reinterpret_cast<PatchMeta*>(base + o_meta);
+  F->d_lists = reinterpret_cast<int*>(base + o_lists);
+  F->d_api_to_dev = reinterpret_cast<int*>(base + o_api);
+  F->d_fstart = reinterpret_cast<int*>(base + o_fstart);
+  F->d_patch_sums = reinterpret_cast<double*>(base + o_sums);
+  F->d_mass = reinterpret_cast<double*>(base + o_mass);
+  F->d_delta = reinterpret_cast<double*>(base + o_delta);
+  FC_CUDA(dmalloc(&F->d_nbr, (size_t)n * 8));
+  // (host sources are pageable: each copy has taken its data when it returns)
+  FC_CUDA(cudaMemcpyAsync(F->d_tables, host.data(), uploaded, cudaMemcpyHostToDevice,
                           g_alloc_stream));
-  FC_CUDA(dmalloc(&F->d_patch_sums, n));
-  FC_CUDA(dmalloc(&F->d_mass, H.desc.nforests));
-  FC_CUDA(dmalloc(&F->d_delta, n));
+  FC_CUDA(cudaMemcpyAsync(F->d_nbr, H.nbr.data(), sizeof(NbrEntry) * n * 8,
+                          cudaMemcpyHostToDevice, g_alloc_stream));
   if (!F->d_err) {
     FC_CUDA(dmalloc(&F->d_err, 1));
     FC_CUDA(cudaMemsetAsync(F->d_err, 0, sizeof(int), g_alloc_stream));
@@ -1507,6 +1523,7 @@ fc_status fc_tag_regrid(fc_forest* F, double tau_refine, double tau_coarsen,
   std::memcpy(F->buf, G->buf, sizeof F->buf);
   F->qT = G->qT;
   F->stage = G->stage;
+  F->d_tables = G->d_tables;
   F->d_meta = G->d_meta;
   F->d_nbr = G->d_nbr;
   F->d_lists = G->d_lists;

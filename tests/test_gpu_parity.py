@@ -122,6 +122,21 @@ def test_tag_and_regrid_match_oracle():
     assert relerr(gpu.get_q(), ref.get_q()) <= F64_TOL
 
 
+def test_tag_in_single_precision_matches_oracle():
+    """FP32 fields: the indicator is computed in FP32 (the square root of the
+    patch maximum in FP64); it follows the FP64 oracle to the field's error."""
+    w = synth.swirl(1, lmin=2, lmax=5, mx=16)
+    ref, gpu = pair(fc, w, fc.F32)
+    _, dtc = synth.time_step(w)
+    for n in range(2):
+        ref.step_multirate(n * dtc, dtc)
+        gpu.step_multirate(n * dtc, dtc)
+    t_ref, t_gpu = ref.tag(), gpu.tag()
+    assert np.abs(t_gpu - t_ref).max() <= 1e-4 * np.abs(t_ref).max()
+    assert np.array_equal(t_gpu > w.tau_refine, t_ref > w.tau_refine) or \
+        np.min(np.abs(t_ref - w.tau_refine)) < 1e-4 * np.abs(t_ref).max()
+
+
 def test_mass_matches_oracle():
     w = synth.swirl(0, lmin=2, lmax=5, mx=16)
     ref, gpu = pair(fc, w, fc.F64)
