@@ -1438,6 +1438,10 @@ fc_status fc_tag_regrid(fc_forest* F, double tau_refine, double tau_coarsen,
   G->esize = F->esize;
   G->vel_scale = F->vel_scale;  // the sphere's metrics carry it
   G->host.leaves = nl;
+  // the old layout's host neighbour table and patch records were read once,
+  // by its upload: the new layout's build reuses their memory
+  G->host.nbr.swap(F->host.nbr);
+  G->host.meta.swap(F->host.meta);
   err = G->host.build();
   if (!err.empty()) {
     delete G;

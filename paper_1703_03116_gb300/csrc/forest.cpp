@@ -52,7 +52,14 @@ void sort_leaves(std::vector<Leaf>* v) {
   };
   // a regrid's output is in order already: check that without a copy
   bool sorted = true;
-  for (size_t i = 1; sorted && i < v->size(); ++i) sorted = !less(key((*v)[i]), key((*v)[i - 1]));
+  if (!v->empty()) {
+    K prev = key((*v)[0]);
+    for (size_t i = 1; sorted && i < v->size(); ++i) {
+      const K cur = key((*v)[i]);
+      sorted = !less(cur, prev);
+      prev = cur;
+    }
+  }
   if (sorted) return;
   std::vector<K> ks(v->size());  // keys computed once
   for (size_t i = 0; i < v->size(); ++i) ks[i] = key((*v)[i]);
@@ -503,6 +510,21 @@ bool parent_balanced(const LeafSet& s, const Leaf& P, int mx) {
   return true;
 }
 
+// append the leaves of s that cover quadrant a, in field order (a is a
+// leaf of the previous layout)
+void emit_region(const LeafSet& s, const Leaf& a, int lmin, std::vector<Leaf>* out) {
+  if (s.has(a.f, a.b, a.l, a.x, a.y)) {
+    out->push_back(a);
+    return;
+  }
+  if (a.l > lmin && s.has(a.f, a.b, a.l - 1, a.x >> 1, a.y >> 1)) {
+    if (!(a.x & 1) && !(a.y & 1)) out->push_back(Leaf{a.f, a.b, a.l - 1, a.x >> 1, a.y >> 1});
+    return;
+  }
+  for (int c = 0; c < 4; ++c)
+    emit_region(s, Leaf{a.f, a.b, a.l + 1, 2 * a.x + (c & 1), 2 * a.y + (c >> 1)}, lmin, out);
+}
+
 }  // namespace
 
 namespace {
@@ -559,10 +581,13 @@ void regrid_range(const HostForest& F, const std::vector<double>& delta, double 
       s.erase(Leaf{P.f, P.b, P.l + 1, 2 * P.x + (c & 1), 2 * P.y + (c >> 1)});
     s.add(P);
   }
+  // the new leaves in field order, without a sort: each old leaf's region
+  // now holds the old leaf itself, or new leaves below it (refinement and
+  // balance), or lies in a new parent (a coarsened family, emitted in place
+  // of the family's first child, where its key sorts)
   out->clear();
   out->reserve(s.m.size());
-  s.m.for_each([&](uint64_t k, int) { out->push_back(leaf_of_key(k)); });
-  sort_leaves(out);
+  for (int k = k0; k < k1; ++k) emit_region(s, F.leaves[k], d.lmin, out);
 }
 
 }  // namespace
