@@ -253,8 +253,9 @@ fc_status fc_set_graphs(fc_forest* forest, int enable);
  * fc_autotune times every candidate (staged; walk with 2, 4, 8 warps per
  * CTA; walk1 with 4 or 8; each with the level's ghosts filled inside the update kernel or by
  * separate fill kernels) as a whole level substep of the current layout,
- * eight substeps replayed from one CUDA graph as in a captured step, and
- * keeps the fastest per launch size (sizes bucketed by powers of two; a
+ * eight substeps replayed from one CUDA graph as in a captured step (walk
+ * only for launches of at least two patches per SM: below that staged has
+ * measured about twice as fast), and keeps the fastest per launch size (sizes bucketed by powers of two; a
  * bucket is tuned once per forest).  It overwrites the previous-state
  * buffers, so call it when all levels hold the same time (after set_q or a
  * regrid).  report: host, nullable, 32 x 4 ints per bucket b (patches in

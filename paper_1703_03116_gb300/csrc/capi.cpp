@@ -829,6 +829,9 @@ fc_status fc_autotune(fc_forest* F, int* report, void* stream) {
   FC_CUDA(cudaEventCreate(&e1));
   if (!F->cap_stream) FC_CUDA(cudaStreamCreateWithFlags(&F->cap_stream, cudaStreamNonBlocking));
   cudaStream_t cs = F->cap_stream;
+  int dev_id = 0, nsm = 0;
+  FC_CUDA(cudaGetDevice(&dev_id));
+  FC_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev_id));
   DevForest<float> Df = dev<float>(F);
   DevForest<double> Dd = dev<double>(F);
   fc_status st = FC_OK;
@@ -845,6 +848,9 @@ fc_status fc_autotune(fc_forest* F, int* report, void* stream) {
       const int fused = c2 / ncand;
       if (fused && !F->fuse) continue;
       if (c.variant != ADV_STAGED && F->d_metric) continue;  // no capacity form in walk
+      // below two patches per SM the walk's warps mostly idle: staged has
+      // measured about twice as fast there (graph-replayed substeps)
+      if (c.variant != ADV_STAGED && p1 - p0 < 2 * nsm) continue;
       a.variant = c.variant;
       a.warps = c.warps;
       a.gather = fused;
