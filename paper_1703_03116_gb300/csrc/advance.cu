@@ -40,8 +40,9 @@ __device__ __forceinline__ real correction(int order, int limiter, real s, real 
 // x-edge (i,j) lies between cells (i-1,j) and (i,j): i in [0,MX], j in [-1,MX]
 // y-edge (i,j) lies between cells (i,j-1) and (i,j): j in [0,MX], i in [-1,MX]
 template <typename real, int MX, int NT, bool CAP>
-__global__ void __launch_bounds__(NT) advance_staged_kernel(DevForest<real> D, int p0, int p1,
-                                                            AdvArgs a, int* err) {
+// (FP32: three CTAs of 512 threads per SM, at most 42 registers a thread)
+__global__ void __launch_bounds__(NT, NT >= 512 && sizeof(real) == 4 ? 3 : 1)
+    advance_staged_kernel(DevForest<real> D, int p0, int p1, AdvArgs a, int* err) {
   constexpr int S = MX + 4;
   constexpr int NE = (MX + 1) * (MX + 2);
   constexpr int NV = MX + 3;  // corner nodes -1..MX+1
@@ -50,6 +51,7 @@ __global__ void __launch_bounds__(NT) advance_staged_kernel(DevForest<real> D, i
   __shared__ __align__(8) uint64_t bar;
   __shared__ real ucoef_s;
   __shared__ NbrStage st;
+  __shared__ NbrStage sco[8];  // a.direct: each coarse region's neighbour's entries
   // capacity form: kappa, phi_x, phi_y of the patch (MS doubles) come first
   const double* Ms = reinterpret_cast<const double*>(smem_raw);
   real* Q = reinterpret_cast<real*>(smem_raw + sizeof(double) * MS);
@@ -113,9 +115,15 @@ __global__ void __launch_bounds__(NT) advance_staged_kernel(DevForest<real> D, i
       mbar_wait(&bar, parity, kWaitLimit);  // let the copy land before leaving
       return;
     }
+    if (a.gather && a.direct) {  // the coarse neighbours' entries (8 threads per region)
+      const int r = threadIdx.x >> 3;
+      if (r < 8 && st.e[r].kind == NB_COARSE && st.e[r].lev == a.tlevel)
+        stage_neighbours(D.meta, D.nbr, st.e[r].n0, sco[r], threadIdx.x & 7);
+      __syncthreads();
+    }
     if (a.gather)  // Alg. 1 for this patch, into the tile's ghost ring
       fill_patch_ghosts<real, MX>(D, st, pm, a.tlevel, real(a.alpha), Q, threadIdx.x, NT,
-                                  []() { __syncthreads(); });
+                                  []() { __syncthreads(); }, a.direct ? sco : nullptr);
     if (a.keep) {  // the adjoint's replay keeps the ghost-filled input tile
       real* kp = static_cast<real*>(a.keep) + (size_t)(p - a.keep_p0) * S * S;
       for (int k = threadIdx.x; k < S * S; k += NT) kp[k] = Q[k];

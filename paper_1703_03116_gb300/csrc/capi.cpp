@@ -589,6 +589,14 @@ fc_status advance_level_t(fc_forest* F, int L, double t, double dt, cudaStream_t
       // their coarse ghost regions filled); the update kernel then fills
       // each level-L patch's ghost ring in shared memory itself
       FillArgs A{F->d_lists + F->off_t[L], (int)H.list_t[L].size(), tlevel, alpha};
+      // the second substep of a pair (alpha > 0) waits on the level's first
+      // one; the staged update then computes the coarse cells it reads
+      // itself, so no fill launch sits between the two updates (the
+      // adjoint's replay keeps the filled tiles: it runs the fill)
+      const bool direct = tlevel >= 0 && alpha != 0.0 && a.variant == ADV_STAGED &&
+                          H.desc.domain != FC_DOMAIN_SPHERE && !F->keep_qT && !F->keep_tiles;
+      if (direct) A.ntargets = 0;
+      a.direct = direct ? 1 : 0;
       // inside a captured step the fill forks off where its inputs are final:
       // alpha = 0 reads level L-1's state from before its update and level
       // L's current one (fork before level L-1's update); alpha = 1/2 waits

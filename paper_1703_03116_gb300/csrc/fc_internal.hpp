@@ -366,6 +366,11 @@ struct AdvArgs {
   // keep + (p - keep_p0) tiles (the adjoint's replay of the forward)
   void* keep;
   int keep_p0;
+  // direct != 0 (staged update, gather on): coarse neighbours on tlevel are
+  // not read from a filled time-interpolated tile; the update computes the
+  // cells its interpolation reads as that fill would (no fill launch before
+  // it on the critical path)
+  int direct;
 };
 
 // Patch-update kernel variants (chosen per level launch by the autotuner):

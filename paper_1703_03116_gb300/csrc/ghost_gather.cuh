@@ -122,6 +122,63 @@ __device__ __forceinline__ bool interpolate(const DevForest<real>& D, const NbrS
   return true;
 }
 
+// The value the coarse-neighbour fill of a multirate substep (phases 1-2 at
+// tlevel and alpha, then the wall condition) leaves in cell (i, j) of the
+// time-interpolated tile of patch c (on tlevel; sc: its staged entries, cm:
+// its level and position): the interior (1 - alpha) q_old + alpha q_new,
+// ghosts copied from same-size or averaged from finer neighbours, exterior
+// ghosts from the cell the wall condition clamps them to; any other ghost
+// keeps what the tile holds (that fill leaves it alone).  An update that
+// computes the few coarse cells its interpolation reads this way needs no
+// fill launch before it.  Not for the cubed sphere (its corner rule).
+template <typename real, int MX>
+__device__ __forceinline__ real coarse_cell(const DevForest<real>& D, const NbrStage& sc,
+                                            const PatchMeta& cm, int c, int tlevel, real alpha,
+                                            int i, int j) {
+  constexpr int S = MX + 4;
+  if (D.domain == FC_DOMAIN_WALLS) {
+    const int N = MX << cm.level;
+    const int gx = cm.x * MX + i, gy = cm.y * MX + j;
+    const bool ox = gx < 0 || gx >= N, oy = gy < 0 || gy >= N;
+    if (ox) i = gx < 0 ? 0 : MX - 1;
+    if (oy) j = gy < 0 ? 0 : MX - 1;
+  }
+  if (i >= 0 && i < MX && j >= 0 && j < MX)
+    return src_interior(D, tlevel, alpha, c, cm.level, i, j);
+  real v;
+  if (copy_or_average<real, MX>(D, sc, cm, tlevel, alpha, i, j, v)) return v;
+  return D.qT[(size_t)c * S * S + (j + kMbc) * S + i + kMbc];
+}
+
+// interpolate(), reading a coarse neighbour on tlevel through coarse_cell
+// (sco[r]: the staged entries of region r's coarse neighbour)
+template <typename real, int MX>
+__device__ __forceinline__ bool interpolate_direct(const DevForest<real>& D, const NbrStage& st,
+                                                   const NbrStage* sco, const PatchMeta& pm,
+                                                   int tlevel, real alpha, int i, int j,
+                                                   real& v) {
+  const int r = region_of<MX>(i, j);
+  const NbrEntry& e = st.e[r];
+  if (e.kind != NB_COARSE) return false;
+  const PatchMeta& nm = st.m0[r];
+  if (nm.level != tlevel) return interpolate<real, MX>(D, st, pm, tlevel, i, j, v);
+  const int2 Ip = apply_a(e.a, pm.x * MX + i, pm.y * MX + j);
+  const int gx = Ip.x + e.fx, gy = Ip.y + e.fy;
+  const int ic = (gx >> 1) - nm.x * MX, jc = (gy >> 1) - nm.y * MX;
+  if (ic < 0 || ic >= MX || jc < 0 || jc >= MX) return false;
+  const real dx = (gx & 1) ? real(1) : real(-1);
+  const real dy = (gy & 1) ? real(1) : real(-1);
+  const NbrStage& sc = sco[r];
+  auto C = [&](int di, int dj) {
+    return coarse_cell<real, MX>(D, sc, nm, e.n0, tlevel, alpha, ic + di, jc + dj);
+  };
+  const real q0 = C(0, 0);
+  const real sx = minmod(C(1, 0) - q0, q0 - C(-1, 0));
+  const real sy = minmod(C(0, 1) - q0, q0 - C(0, -1));
+  v = q0 + real(0.25) * (sx * dx + sy * dy);
+  return true;
+}
+
 // walls: exterior ghosts of the owner's array Q (threads tid, stride nt)
 template <typename real, int MX>
 __device__ __forceinline__ void wall_bc(const PatchMeta& pm, real* Q, int tid, int nt) {
@@ -160,11 +217,14 @@ __device__ __forceinline__ void corner3_fill(const NbrStage& st, real* Q, int ti
 
 // The whole of Alg. 1 for one patch into array Q (shared or global):
 // copy/average, boundary condition, interpolation, boundary condition.
-// `sync` orders the phases across the cooperating threads.
+// `sync` orders the phases across the cooperating threads.  sco non-null:
+// coarse neighbours on tlevel are read through coarse_cell (no fill of
+// their tiles ran for this substep).
 template <typename real, int MX, class Sync>
 __device__ __forceinline__ void fill_patch_ghosts(const DevForest<real>& D, const NbrStage& st,
                                                   const PatchMeta& pm, int tlevel, real alpha,
-                                                  real* Q, int tid, int nt, Sync sync) {
+                                                  real* Q, int tid, int nt, Sync sync,
+                                                  const NbrStage* sco = nullptr) {
   constexpr int S = MX + 4;
   for (int k = tid; k < num_ghosts<MX>(); k += nt) {
     int i, j;
@@ -181,7 +241,9 @@ __device__ __forceinline__ void fill_patch_ghosts(const DevForest<real>& D, cons
     int i, j;
     ghost_ij<MX>(k, i, j);
     real v;
-    if (interpolate<real, MX>(D, st, pm, tlevel, i, j, v)) Q[(j + kMbc) * S + i + kMbc] = v;
+    if (sco ? interpolate_direct<real, MX>(D, st, sco, pm, tlevel, alpha, i, j, v)
+            : interpolate<real, MX>(D, st, pm, tlevel, i, j, v))
+      Q[(j + kMbc) * S + i + kMbc] = v;
   }
   sync();
   if (walls) wall_bc<real, MX>(pm, Q, tid, nt);
