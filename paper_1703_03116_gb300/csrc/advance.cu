@@ -40,8 +40,10 @@ __device__ __forceinline__ real correction(int order, int limiter, real s, real 
 // x-edge (i,j) lies between cells (i-1,j) and (i,j): i in [0,MX], j in [-1,MX]
 // y-edge (i,j) lies between cells (i,j-1) and (i,j): j in [0,MX], i in [-1,MX]
 template <typename real, int MX, int NT, bool CAP>
-// (FP32: three CTAs of 512 threads per SM, at most 42 registers a thread)
-__global__ void __launch_bounds__(NT, NT >= 512 && sizeof(real) == 4 ? 3 : 1)
+// (resident CTAs per SM: 3 of 512 FP32 threads, at most 42 registers a
+// thread; 2 FP64; 8 of 128 and 16 of 64 threads, at most 64 registers)
+__global__ void __launch_bounds__(NT, NT >= 512 ? (sizeof(real) == 4 ? 3 : 2)
+                                                : (NT >= 128 ? 8 : 16))
     advance_staged_kernel(DevForest<real> D, int p0, int p1, AdvArgs a, int* err) {
   constexpr int S = MX + 4;
   constexpr int NE = (MX + 1) * (MX + 2);
@@ -52,6 +54,8 @@ __global__ void __launch_bounds__(NT, NT >= 512 && sizeof(real) == 4 ? 3 : 1)
   __shared__ real ucoef_s;
   __shared__ NbrStage st;
   __shared__ NbrStage sco[8];  // a.direct: each coarse region's neighbour's entries
+  __shared__ real ring[num_ghosts<MX>()];  // ghost values gathered while the tile loads
+  __shared__ bool ring_w[num_ghosts<MX>()];
   // capacity form: kappa, phi_x, phi_y of the patch (MS doubles) come first
   const double* Ms = reinterpret_cast<const double*>(smem_raw);
   real* Q = reinterpret_cast<real*>(smem_raw + sizeof(double) * MS);
@@ -107,6 +111,36 @@ __global__ void __launch_bounds__(NT, NT >= 512 && sizeof(real) == 4 ? 3 : 1)
         Ty[k] = sinpi_r(real(2 * (pm.y * MX + k - 1) + 1) * h);
       }
     }
+    // Alg. 1 for this patch, its neighbour reads while the tile is in
+    // flight: each thread computes the values of its ghost cells (copied from
+    // same-size or averaged from finer neighbours, interpolated from coarser
+    // ones; every ghost is one of these or exterior) into registers, stored
+    // into the tile once it has landed; then the wall condition (the
+    // exterior ghosts copy cells that are final by then) and, on the sphere,
+    // the corners beyond a cube vertex
+    constexpr int NG = num_ghosts<MX>();
+    if (a.gather) {
+      __syncthreads();  // the patch's entries
+      if (a.direct) {   // the coarse neighbours' entries (8 threads per region)
+        const int r = threadIdx.x >> 3;
+        if (r < 8 && st.e[r].kind == NB_COARSE && st.e[r].lev == a.tlevel)
+          stage_neighbours(D.meta, D.nbr, st.e[r].n0, sco[r], threadIdx.x & 7);
+        __syncthreads();
+      }
+      const real alpha = real(a.alpha);
+#pragma unroll 1
+      for (int k = threadIdx.x; k < NG; k += NT) {
+        int i, j;
+        ghost_ij<MX>(k, i, j);
+        real v;
+        const bool w =
+            copy_or_average<real, MX>(D, st, pm, a.tlevel, alpha, i, j, v) ||
+            (a.direct ? interpolate_direct<real, MX>(D, st, sco, pm, a.tlevel, alpha, i, j, v)
+                      : interpolate<real, MX>(D, st, pm, a.tlevel, i, j, v));
+        ring[k] = w ? v : real(0);
+        ring_w[k] = w;
+      }
+    }
     // every thread observes the copy's completion (bounded); the CTA leaves
     // together if any thread gave up
     const bool landed = mbar_wait(&bar, parity, kWaitLimit);
@@ -115,15 +149,23 @@ __global__ void __launch_bounds__(NT, NT >= 512 && sizeof(real) == 4 ? 3 : 1)
       mbar_wait(&bar, parity, kWaitLimit);  // let the copy land before leaving
       return;
     }
-    if (a.gather && a.direct) {  // the coarse neighbours' entries (8 threads per region)
-      const int r = threadIdx.x >> 3;
-      if (r < 8 && st.e[r].kind == NB_COARSE && st.e[r].lev == a.tlevel)
-        stage_neighbours(D.meta, D.nbr, st.e[r].n0, sco[r], threadIdx.x & 7);
+    if (a.gather) {
+      for (int k = threadIdx.x; k < NG; k += NT)  // each thread its own cells
+        if (ring_w[k]) {
+          int i, j;
+          ghost_ij<MX>(k, i, j);
+          Q[(j + kMbc) * S + i + kMbc] = ring[k];
+        }
       __syncthreads();
+      if (D.domain == FC_DOMAIN_WALLS) {
+        wall_bc<real, MX>(pm, Q, threadIdx.x, NT);
+        __syncthreads();
+      }
+      if (D.domain == FC_DOMAIN_SPHERE) {
+        corner3_fill<real, MX>(st, Q, threadIdx.x, NT);
+        __syncthreads();
+      }
     }
-    if (a.gather)  // Alg. 1 for this patch, into the tile's ghost ring
-      fill_patch_ghosts<real, MX>(D, st, pm, a.tlevel, real(a.alpha), Q, threadIdx.x, NT,
-                                  []() { __syncthreads(); }, a.direct ? sco : nullptr);
     if (a.keep) {  // the adjoint's replay keeps the ghost-filled input tile
       real* kp = static_cast<real*>(a.keep) + (size_t)(p - a.keep_p0) * S * S;
       for (int k = threadIdx.x; k < S * S; k += NT) kp[k] = Q[k];
