@@ -146,6 +146,16 @@ struct fc_forest {
   cudaEvent_t ev_pre[kMaxLevel + 1] = {}, ev_post[kMaxLevel + 1] = {}, ev_fill[kMaxLevel + 1] = {};
   cudaEvent_t ev_adj[2] = {};  // the adjoint graph's fork and join
   bool pre_ok[kMaxLevel + 1] = {}, post_ok[kMaxLevel + 1] = {};
+  // a captured coarse step with fused fills runs each level on its own
+  // stream (lev_stream[L], forked from ev_start), each update waiting only
+  // for what it reads: the coarser level's state (before its latest update
+  // at alpha = 0, after it otherwise) and the finer level's state at the
+  // same time (after its latest update); the critical path is then the
+  // finest level's chain of substeps, not all of them
+  bool dag_levels = false;
+  cudaStream_t lev_stream[kMaxLevel + 1] = {};
+  bool lev_forked[kMaxLevel + 1] = {};
+  cudaEvent_t ev_start = nullptr;
   // the adjoint's replay of a coarse step: times relative to the step start
   // (on the device), and where each substep keeps the update's ghost-filled
   // input tiles and the time-interpolated coarse tiles it read
@@ -564,6 +574,9 @@ fc_status ensure_side(fc_forest* F) {
     for (cudaEvent_t* ev : {&F->ev_pre[l], &F->ev_post[l], &F->ev_fill[l]})
       FC_CUDA(cudaEventCreateWithFlags(ev, cudaEventDisableTiming));
   for (cudaEvent_t& ev : F->ev_adj) FC_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+  FC_CUDA(cudaEventCreateWithFlags(&F->ev_start, cudaEventDisableTiming));
+  for (int l = 0; l <= kMaxLevel; ++l)
+    FC_CUDA(cudaStreamCreateWithFlags(&F->lev_stream[l], cudaStreamNonBlocking));
   return FC_OK;
 }
 
@@ -584,6 +597,27 @@ fc_status advance_level_t(fc_forest* F, int L, double t, double dt, cudaStream_t
     AdvArgs a = adv_args(F, L, t, dt, p1 - p0);
     const fc_forest::Tune& tn = F->tune[size_bucket(p1 - p0)];
     const bool fused = F->fuse && (F->forced_variant >= 0 || !tn.tuned || tn.fused);
+    // per-level streams of a captured step (see fc_forest::dag_levels)
+    const bool lev = F->dag_levels;
+    if (lev) {
+      s = F->lev_stream[L];
+      if (!F->lev_forked[L]) {
+        FC_CUDA(cudaStreamWaitEvent(s, F->ev_start, 0));
+        F->lev_forked[L] = true;
+      }
+      // the coarser level's state this substep reads: from before its
+      // latest update (alpha = 0) or after it
+      if (tlevel >= 0) {
+        if (alpha == 0.0) {
+          if (F->pre_ok[L - 1]) FC_CUDA(cudaStreamWaitEvent(s, F->ev_pre[L - 1], 0));
+        } else if (F->post_ok[L - 1]) {
+          FC_CUDA(cudaStreamWaitEvent(s, F->ev_post[L - 1], 0));
+        }
+      }
+      // separate fills also read the finer level now
+      if (!fused && L < H.desc.lmax && F->post_ok[L + 1])
+        FC_CUDA(cudaStreamWaitEvent(s, F->ev_post[L + 1], 0));
+    }
     if (fused) {
       // coarse neighbours first (their interiors time-interpolated into qT,
       // their coarse ghost regions filled); the update kernel then fills
@@ -601,7 +635,7 @@ fc_status advance_level_t(fc_forest* F, int L, double t, double dt, cudaStream_t
       // alpha = 0 reads level L-1's state from before its update and level
       // L's current one (fork before level L-1's update); alpha = 1/2 waits
       // for level L's previous substep only
-      const bool fork = F->dag && A.ntargets > 0 && tlevel >= 0 &&
+      const bool fork = F->dag && !lev && A.ntargets > 0 && tlevel >= 0 &&
                         ((alpha == 0.0 && F->pre_ok[L - 1]) ||
                          (std::fabs(alpha - 0.5) < 1e-9 && F->post_ok[L]));
       if (fork) {
@@ -638,6 +672,9 @@ fc_status advance_level_t(fc_forest* F, int L, double t, double dt, cudaStream_t
     }
     a.keep = F->keep_tiles;
     a.keep_p0 = p0;
+    // the update reads the finer level at this time: after its latest update
+    if (lev && fused && L < H.desc.lmax && F->post_ok[L + 1])
+      FC_CUDA(cudaStreamWaitEvent(s, F->ev_post[L + 1], 0));
     if (F->dag) {
       FC_CUDA(cudaEventRecord(F->ev_pre[L], s));
       F->pre_ok[L] = true;
@@ -766,6 +803,9 @@ fc_status fc_forest_destroy(fc_forest* F) {
         if (ev) cudaEventDestroy(ev);
     for (cudaEvent_t ev : F->ev_adj)
       if (ev) cudaEventDestroy(ev);
+    if (F->ev_start) cudaEventDestroy(F->ev_start);
+    for (cudaStream_t ls : F->lev_stream)
+      if (ls) cudaStreamDestroy(ls);
   }
   free_device(F);
   cudaStreamSynchronize(0);
@@ -1368,14 +1408,29 @@ fc_status fc_step_multirate(fc_forest* F, double t, double dt_coarse, void* stre
     }
     F->capture_pairs = &ng.pairs;
     F->dag = true;
-    for (int l = 0; l <= kMaxLevel; ++l) F->pre_ok[l] = F->post_ok[l] = false;
+    F->dag_levels = F->fuse;
+    for (int l = 0; l <= kMaxLevel; ++l) {
+      F->pre_ok[l] = F->post_ok[l] = false;
+      F->lev_forked[l] = false;
+    }
     const uint64_t launches_before = launch_counter();
     FC_CUDA(cudaStreamBeginCapture(F->cap_stream, cudaStreamCaptureModeThreadLocal));
-    fc_status st = multirate(F, lmin, 0.0, dt_coarse, F->cap_stream);
+    cudaError_t ej = cudaEventRecord(F->ev_start, F->cap_stream);
+    fc_status st = ej == cudaSuccess ? multirate(F, lmin, 0.0, dt_coarse, F->cap_stream)
+                                     : cuda_fail(ej, "cudaEventRecord");
+    // join every level stream back into the step's stream
+    for (int l = 0; l <= kMaxLevel && st == FC_OK; ++l)
+      if (F->lev_forked[l]) {
+        ej = cudaEventRecord(F->ev_fill[l], F->lev_stream[l]);
+        if (ej == cudaSuccess) ej = cudaStreamWaitEvent(F->cap_stream, F->ev_fill[l], 0);
+        if (ej != cudaSuccess) st = cuda_fail(ej, "level join");
+      }
     cudaGraph_t graph = nullptr;
     cudaError_t e = cudaStreamEndCapture(F->cap_stream, &graph);
     F->capture_pairs = nullptr;
     F->dag = false;
+    F->dag_levels = false;
+    for (int l = 0; l <= kMaxLevel; ++l) F->lev_forked[l] = false;
     ng.kernels = launch_counter() - launches_before;  // counted when replayed
     launch_counter() = launches_before;
     std::copy(F->cur, F->cur + kMaxLevel + 1, ng.cur_after);
