@@ -1108,15 +1108,27 @@ static fc_status capture_adjoint_multirate(fc_forest* F, double dtc, cudaStream_
     // reads: each update's ghost-filled input tiles and the coarse tiles
     reset_times(F);
     F->dag = true;
+    F->dag_levels = F->fuse;  // each level on its own stream, as in a captured step
     F->rel_time = true;
-    for (int l = 0; l <= kMaxLevel; ++l) F->pre_ok[l] = F->post_ok[l] = false;
+    for (int l = 0; l <= kMaxLevel; ++l) {
+      F->pre_ok[l] = F->post_ok[l] = false;
+      F->lev_forked[l] = false;
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(F->ev_start, cs);
     for (auto& u : subs) {
       std::copy(F->cur, F->cur + kMaxLevel + 1, u.cur);
       F->keep_tiles = pool + u.offq;
       F->keep_qT = u.L > lmin ? pool + u.offt : nullptr;
       if (e == cudaSuccess && replay_st == FC_OK) replay_st = advance_level(F, u.L, u.t, u.dt, cs);
     }
+    for (int l = 0; l <= kMaxLevel; ++l)  // the level streams rejoin before the reverse sweep
+      if (F->lev_forked[l]) {
+        if (e == cudaSuccess) e = cudaEventRecord(F->ev_fill[l], F->lev_stream[l]);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, F->ev_fill[l], 0);
+        F->lev_forked[l] = false;
+      }
     F->dag = false;
+    F->dag_levels = false;
     F->rel_time = false;
     F->keep_tiles = F->keep_qT = nullptr;
     if (e == cudaSuccess) e = cudaMemsetAsync(LQ, 0, cells * sizeof(real), cs);
