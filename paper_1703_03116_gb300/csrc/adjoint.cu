@@ -21,12 +21,15 @@
 //                  interior cells (atomic adds).
 //
 // Multirate substep of level L (launch_adjoint_substep), three kernels: the
-// update's transpose plus that of the copy q_old = q taken before it
-// (adj_advance with lamO); the transposes of level L's ghosts, each patch's
-// four phases in one CTA (adj_level_ghosts); the transposes of the ghosts of
-// the level L-1 patches read through the time-interpolated tiles and of
-// qT = (1 - alpha) q_old + alpha q (adj_coarse_tiles; sources read on the fly
-// split their share inside the copy transpose).
+// update's transpose (adj_advance); the transposes of level L's ghosts, each
+// patch's four phases in one CTA (adj_level_ghosts); the transposes of the
+// ghosts of the level L-1 patches read through the time-interpolated tiles
+// and of qT = (1 - alpha) q_old + alpha q (adj_coarse_tiles; sources read on
+// the fly split their share inside the copy transpose).  Each level's
+// adjoint of one state accumulates in one of two buffers (AdjAcc), every
+// contribution an atomic add into a zeroed accumulator, so the substeps of
+// different levels can run side by side wherever their forward substeps
+// could.
 // The adjoint tiles use the patch-store layout ((mx+4)^2 per patch).
 #include "ghost_gather.cuh"
 
@@ -85,15 +88,17 @@ __device__ __forceinline__ EdgeFw<real> edge_fw(int order, int limiter, int tran
 }
 
 // The forward tile of patch p is read from the store, or from
-// tiles + (p - tiles_p0) tiles when `tiles` is given (kept copies).  With
-// lamO (multirate) the adjoint of the patch's previous state is added to the
-// new interior adjoint and cleared (the copy q_old = q before the update).
+// tiles + (p - tiles_p0) tiles when `tiles` is given (kept copies).  acc
+// (multirate accumulators): lam_in's tile is cleared once read, and the
+// input tile's adjoint is added to lam_out's interior (other levels' and
+// neighbours' transposes add there too) while its ghost ring, which only
+// this patch's ghost transposes read, is stored.
 template <typename real, int MX, int NT>
 __global__ void __launch_bounds__(NT) adj_advance_kernel(DevForest<real> D, AdvArgs a,
-                                                         const real* lam_in, real* lam_out,
+                                                         real* lam_in, real* lam_out,
                                                          double* dscale, double dfac, int p0,
                                                          int p1, const real* tiles, int tiles_p0,
-                                                         real* lamO) {
+                                                         int acc) {
   constexpr int S = MX + 4;
   constexpr int NE = (MX + 1) * (MX + 2);
   constexpr int NV = MX + 3;
@@ -132,13 +137,16 @@ __global__ void __launch_bounds__(NT) adj_advance_kernel(DevForest<real> D, AdvA
     const PatchMeta pm = D.meta[p];
     const real* src = tiles ? tiles + (size_t)(p - tiles_p0) * S * S
                             : D.buf[D.cur[pm.level]] + (size_t)p * S * S;
-    const real* lin = lam_in + (size_t)p * S * S;
+    real* lin = lam_in + (size_t)p * S * S;
     for (int k = threadIdx.x; k < S * S; k += NT) {
       Q[k] = src[k];
       LQ[k] = real(0);
     }
-    for (int k = threadIdx.x; k < MX * MX; k += NT)
-      LN[k] = lin[(k / MX + 2) * S + (k % MX) + 2];
+    for (int k = threadIdx.x; k < MX * MX; k += NT) {
+      const int o = (k / MX + 2) * S + (k % MX) + 2;
+      LN[k] = lin[o];
+      if (acc) lin[o] = real(0);  // consumed: the buffer's next state starts from zero
+    }
     if (swirl)
       for (int k = threadIdx.x; k < NV; k += NT) {
         const real xs = sinpi_r(real(pm.x * MX + k - 1) * h);
@@ -325,16 +333,13 @@ __global__ void __launch_bounds__(NT) adj_advance_kernel(DevForest<real> D, AdvA
       __syncthreads();
     }
     real* lout = lam_out + (size_t)p * S * S;
-    if (lamO) {
-      real* lo = lamO + (size_t)p * S * S;
+    if (acc) {
       for (int k = threadIdx.x; k < S * S; k += NT) {
         const int i = k % S - 2, j = k / S - 2;
-        if (i >= 0 && i < MX && j >= 0 && j < MX) {
-          lout[k] = LQ[k] + lo[k];
-          lo[k] = real(0);
-        } else {
+        if (i >= 0 && i < MX && j >= 0 && j < MX)
+          atomicAdd(lout + k, LQ[k]);
+        else
           lout[k] = LQ[k];
-        }
       }
     } else {
       for (int k = threadIdx.x; k < S * S; k += NT) lout[k] = LQ[k];
@@ -424,24 +429,35 @@ __device__ void adj_interp_patch(const DevForest<real>& D, const NbrStage& st, c
   }
 }
 
-// a source on tlevel was read as (1 - alpha) q_old + alpha q: its share goes
-// to lamO and lam (alpha = 0: the previous state alone)
+// Where the transposes of copies and averages add: a neighbour on the
+// coarser level tlevel was read as (1 - alpha) q_old + alpha q (its shares
+// go to the accumulators of its older and newer states); a same-size one at
+// `same`, a finer one at `fine` (accumulators of those levels' states at the
+// substep's time).
 template <typename real>
-__device__ __forceinline__ void adj_src_add(real* lam, real* lamO, bool viaT, real alpha,
-                                            size_t o, real v) {
+struct AdjTargets {
+  real* same;
+  real* fine;
+  real* t_old;
+  real* t_new;
+};
+
+template <typename real>
+__device__ __forceinline__ void adj_src_add(const AdjTargets<real>& g, bool viaT, bool fine,
+                                            real alpha, size_t o, real v) {
   if (viaT) {
-    atomicAdd(lamO + o, (real(1) - alpha) * v);
-    if (alpha != real(0)) atomicAdd(lam + o, alpha * v);
+    atomicAdd(g.t_old + o, (real(1) - alpha) * v);
+    if (alpha != real(0)) atomicAdd(g.t_new + o, alpha * v);
   } else {
-    atomicAdd(lam + o, v);
+    atomicAdd((fine ? g.fine : g.same) + o, v);
   }
 }
 
 // transpose of copy / average (Eq. transform, Eq. ghost_coarse): ghost
 // adjoint (in L, the patch's own tile) -> neighbour interiors
 template <typename real, int MX>
-__device__ void adj_copy_patch(const NbrStage& st, const PatchMeta& pm, real* L, real* lam,
-                               int tlevel, real alpha, real* lamO, int tid, int nt) {
+__device__ void adj_copy_patch(const NbrStage& st, const PatchMeta& pm, real* L,
+                               const AdjTargets<real>& g, int tlevel, real alpha, int tid, int nt) {
   constexpr int S = MX + 4;
   for (int k = tid; k < num_ghosts<MX>(); k += nt) {
     int i, j;
@@ -457,7 +473,7 @@ __device__ void adj_copy_patch(const NbrStage& st, const PatchMeta& pm, real* L,
       const PatchMeta& nm = st.m0[r];
       const int lx = gx - nm.x * MX, ly = gy - nm.y * MX;
       if (lx < 0 || lx >= MX || ly < 0 || ly >= MX) continue;
-      adj_src_add(lam, lamO, nm.level == tlevel, alpha,
+      adj_src_add(g, nm.level == tlevel, false, alpha,
                   (size_t)e.n0 * S * S + (ly + kMbc) * S + lx + kMbc, lg);
     } else {
       int n = e.n0;
@@ -472,7 +488,7 @@ __device__ void adj_copy_patch(const NbrStage& st, const PatchMeta& pm, real* L,
         if (lx < 0 || lx >= MX || ly < 0 || ly >= MX) continue;
       }
       for (int q = 0; q < 4; ++q)
-        adj_src_add(lam, lamO, nm->level == tlevel, alpha,
+        adj_src_add(g, nm->level == tlevel, true, alpha,
                     (size_t)n * S * S + (ly + (q >> 1) + kMbc) * S + lx + (q & 1) + kMbc,
                     real(0.25) * lg);
     }
@@ -514,7 +530,8 @@ __global__ void adj_copy_kernel(DevForest<real> D, real* lam) {
     stage_neighbours(D.meta, D.nbr, p, st, threadIdx.x);
     const PatchMeta pm = D.meta[p];
     __syncthreads();
-    adj_copy_patch<real, MX>(st, pm, lam + (size_t)p * S * S, lam, -1, real(0), nullptr,
+    adj_copy_patch<real, MX>(st, pm, lam + (size_t)p * S * S,
+                             AdjTargets<real>{lam, lam, nullptr, nullptr}, -1, real(0),
                              threadIdx.x, blockDim.x);
     __syncthreads();
   }
@@ -523,12 +540,14 @@ __global__ void adj_copy_kernel(DevForest<real> D, real* lam) {
 // multirate substep, level L's patches [p0, p1): the transposes of the
 // level-L ghosts in reverse phase order -- boundary condition, interpolation
 // from the time-interpolated coarse tiles (into lamT), boundary condition,
-// copy / average.  Only the patch's own ghost cells are read, so one CTA per
-// patch runs all four.
+// copy / average (into the accumulators of level L, lam, and of level L+1,
+// lam_fine, for their states at the substep's start).  Only the patch's own
+// ghost cells (in lam, zeroed as consumed) are read, so one CTA per patch
+// runs all four.
 template <typename real, int MX>
-__global__ void adj_level_ghosts_kernel(DevForest<real> D, int p0, int p1, real* lam, int tlevel,
-                                        real alpha, real* lamT, real* lamO, const real* coarse_src,
-                                        int coarse_p0) {
+__global__ void adj_level_ghosts_kernel(DevForest<real> D, int p0, int p1, real* lam,
+                                        real* lam_fine, int tlevel, real* lamT,
+                                        const real* coarse_src, int coarse_p0) {
   constexpr int S = MX + 4;
   __shared__ NbrStage st;
   const bool walls = D.domain == FC_DOMAIN_WALLS;
@@ -548,18 +567,22 @@ __global__ void adj_level_ghosts_kernel(DevForest<real> D, int p0, int p1, real*
       adj_bc_patch<real, MX>(pm, L, threadIdx.x, blockDim.x);
       __syncthreads();
     }
-    adj_copy_patch<real, MX>(st, pm, L, lam, tlevel, alpha, lamO, threadIdx.x, blockDim.x);
+    adj_copy_patch<real, MX>(st, pm, L, AdjTargets<real>{lam, lam_fine, nullptr, nullptr}, tlevel,
+                             real(0), threadIdx.x, blockDim.x);
     __syncthreads();
   }
 }
 
 // multirate substep, the level L-1 patches read through the time-
 // interpolated tiles (each listed once): the transposes of their ghosts
-// (boundary condition, copy / average) and of the time interpolation of
-// their interiors; their lamT tiles are cleared
+// (boundary condition, copy / average: same-size neighbours on level L-1
+// split between the accumulators of its older and newer states, lam_old and
+// lam_new; finer ones, on level L, into lam) and of the time interpolation
+// of their interiors; their lamT tiles are cleared
 template <typename real, int MX>
 __global__ void adj_coarse_tiles_kernel(DevForest<real> D, const int* targets, int n, real* lam,
-                                        int tlevel, real alpha, real* lamT, real* lamO) {
+                                        real* lam_old, real* lam_new, int tlevel, real alpha,
+                                        real* lamT) {
   constexpr int S = MX + 4;
   __shared__ NbrStage st;
   const bool walls = D.domain == FC_DOMAIN_WALLS;
@@ -573,7 +596,8 @@ __global__ void adj_coarse_tiles_kernel(DevForest<real> D, const int* targets, i
       adj_bc_patch<real, MX>(pm, T, threadIdx.x, blockDim.x);
       __syncthreads();
     }
-    adj_copy_patch<real, MX>(st, pm, T, lam, tlevel, alpha, lamO, threadIdx.x, blockDim.x);
+    adj_copy_patch<real, MX>(st, pm, T, AdjTargets<real>{lam, lam, lam_old, lam_new}, tlevel,
+                             alpha, threadIdx.x, blockDim.x);
     __syncthreads();
     const size_t base = (size_t)p * S * S;
     for (int k = threadIdx.x; k < S * S; k += blockDim.x) {
@@ -581,8 +605,8 @@ __global__ void adj_coarse_tiles_kernel(DevForest<real> D, const int* targets, i
       const real v = T[k];
       T[k] = real(0);
       if (i >= 0 && i < MX && j >= 0 && j < MX) {  // other CTAs may add here too
-        atomicAdd(lamO + base + k, (real(1) - alpha) * v);
-        if (alpha != real(0)) atomicAdd(lam + base + k, alpha * v);
+        atomicAdd(lam_old + base + k, (real(1) - alpha) * v);
+        if (alpha != real(0)) atomicAdd(lam_new + base + k, alpha * v);
       }
     }
     __syncthreads();
@@ -600,10 +624,10 @@ inline int grid_for(int n) { return n < 1 ? 1 : (n < 65535 * 8 ? n : 65535 * 8);
 // transpose of the update of level L's patches [p0, p1) over (t, t + dt)
 template <typename real, int MX>
 cudaError_t adj_advance_level(const DevForest<real>& D, int L, int p0, int p1, double t, double dt,
-                              double period, double scale, double dfac, const real* lam_in,
+                              double period, double scale, double dfac, real* lam_in,
                               real* lam_out, double* dscale, cudaStream_t s,
                               const double* t0_dev = nullptr, const real* tiles = nullptr,
-                              int tiles_p0 = 0, real* lamO = nullptr) {
+                              int tiles_p0 = 0, int acc = 0) {
   // a whole CTA per patch: the more threads, the shorter each thread's chain
   // through the phases (the kernel is latency-bound at these launch sizes)
   constexpr int NT = MX >= 32 ? (sizeof(real) == 4 ? 1024 : 512) : (MX >= 16 ? 512 : 256);
@@ -625,7 +649,7 @@ cudaError_t adj_advance_level(const DevForest<real>& D, int L, int p0, int p1, d
   al.t0_dev = t0_dev;
   al.sfac = D.vel_kind == FC_VEL_SWIRL ? scale * sin(M_PI * al.h) / (M_PI * al.h) : 0.0;
   adj_advance_kernel<real, MX, NT><<<p1 - p0, NT, smem, s>>>(D, al, lam_in, lam_out, dscale, dfac,
-                                                               p0, p1, tiles, tiles_p0, lamO);
+                                                               p0, p1, tiles, tiles_p0, acc);
   ++launch_counter();
   return cudaGetLastError();
 }
@@ -636,8 +660,8 @@ cudaError_t adjoint_mx(const DevForest<real>& D, const AdjArgs& g, const real* l
   // one launch per level (per-level h and dt/h); all read the pre-step state
   for (int L = 0; L <= kMaxLevel; ++L) {
     cudaError_t e = adj_advance_level<real, MX>(D, L, g.lev_start[L], g.lev_start[L + 1], g.t,
-                                                g.dt, g.period, g.scale, g.dscale_factor, lam_in,
-                                                lam_out, dscale, s);
+                                                g.dt, g.period, g.scale, g.dscale_factor,
+                                                const_cast<real*>(lam_in), lam_out, dscale, s);
     if (e != cudaSuccess) return e;
   }
   if (g.ncoarse > 0) {
@@ -656,24 +680,22 @@ cudaError_t adjoint_mx(const DevForest<real>& D, const AdjArgs& g, const real* l
 
 // adjoint of one multirate substep of level L (see launch_adjoint_substep)
 template <typename real, int MX>
-cudaError_t adjoint_sub_mx(const DevForest<real>& D, const AdjSubArgs& g, real* lam, real* lamO,
-                           real* lamT, double* dscale, cudaStream_t s) {
+cudaError_t adjoint_sub_mx(const DevForest<real>& D, const AdjSubArgs& g, const AdjAcc<real>& c,
+                           double* dscale, cudaStream_t s) {
   const int n = g.p1 - g.p0;
   if (n <= 0) return cudaSuccess;
   const real alpha = real(g.alpha);
-  if (g.part != 2) {
-    cudaError_t e = adj_advance_level<real, MX>(
-        D, g.L, g.p0, g.p1, g.t, g.dt, g.period, g.scale, g.dscale_factor, lam, lam, dscale, s,
-        g.t0_dev, static_cast<const real*>(g.tiles), g.tiles_p0, lamO);
-    if (e != cudaSuccess) return e;
-    adj_level_ghosts_kernel<real, MX><<<grid_for(n), 256, 0, s>>>(
-        D, g.p0, g.p1, lam, g.tlevel, alpha, lamT, lamO, static_cast<const real*>(g.coarse),
-        g.coarse_p0);
-    ++launch_counter();
-  }
-  if (g.nt > 0 && g.part != 1) {
-    adj_coarse_tiles_kernel<real, MX><<<grid_for(g.nt), 256, 0, s>>>(D, g.list_t, g.nt, lam,
-                                                                     g.tlevel, alpha, lamT, lamO);
+  cudaError_t e = adj_advance_level<real, MX>(
+      D, g.L, g.p0, g.p1, g.t, g.dt, g.period, g.scale, g.dscale_factor, c.lam_in, c.lam_out,
+      dscale, s, g.t0_dev, static_cast<const real*>(g.tiles), g.tiles_p0, 1);
+  if (e != cudaSuccess) return e;
+  adj_level_ghosts_kernel<real, MX><<<grid_for(n), 256, 0, s>>>(
+      D, g.p0, g.p1, c.lam_out, c.lam_fine, g.tlevel, c.lamT, static_cast<const real*>(g.coarse),
+      g.coarse_p0);
+  ++launch_counter();
+  if (g.nt > 0) {
+    adj_coarse_tiles_kernel<real, MX><<<grid_for(g.nt), 256, 0, s>>>(
+        D, g.list_t, g.nt, c.lam_out, c.lam_old, c.lam_new, g.tlevel, alpha, c.lamT);
     ++launch_counter();
   }
   return cudaGetLastError();
@@ -682,21 +704,20 @@ cudaError_t adjoint_sub_mx(const DevForest<real>& D, const AdjSubArgs& g, real* 
 }  // namespace
 
 template <typename real>
-cudaError_t launch_adjoint_substep(const DevForest<real>& D, const AdjSubArgs& g, real* lam,
-                                   real* lamO, real* lamT, double* dscale, cudaStream_t s) {
+cudaError_t launch_adjoint_substep(const DevForest<real>& D, const AdjSubArgs& g,
+                                   const AdjAcc<real>& c, double* dscale, cudaStream_t s) {
   switch (D.mx) {
-    case 8: return adjoint_sub_mx<real, 8>(D, g, lam, lamO, lamT, dscale, s);
-    case 16: return adjoint_sub_mx<real, 16>(D, g, lam, lamO, lamT, dscale, s);
-    case 32: return adjoint_sub_mx<real, 32>(D, g, lam, lamO, lamT, dscale, s);
+    case 8: return adjoint_sub_mx<real, 8>(D, g, c, dscale, s);
+    case 16: return adjoint_sub_mx<real, 16>(D, g, c, dscale, s);
+    case 32: return adjoint_sub_mx<real, 32>(D, g, c, dscale, s);
     default: return cudaErrorInvalidValue;
   }
 }
 
 template cudaError_t launch_adjoint_substep<float>(const DevForest<float>&, const AdjSubArgs&,
-                                                   float*, float*, float*, double*, cudaStream_t);
+                                                   const AdjAcc<float>&, double*, cudaStream_t);
 template cudaError_t launch_adjoint_substep<double>(const DevForest<double>&, const AdjSubArgs&,
-                                                    double*, double*, double*, double*,
-                                                    cudaStream_t);
+                                                    const AdjAcc<double>&, double*, cudaStream_t);
 
 template <typename real>
 cudaError_t launch_adjoint_step(const DevForest<real>& D, const AdjArgs& g, const real* lam_in,

@@ -156,6 +156,7 @@ struct fc_forest {
   cudaStream_t lev_stream[kMaxLevel + 1] = {};
   bool lev_forked[kMaxLevel + 1] = {};
   cudaEvent_t ev_start = nullptr;
+  std::vector<cudaEvent_t> ev_rev;  // the adjoint's reversed substeps (one per substep)
   // the adjoint's replay of a coarse step: times relative to the step start
   // (on the device), and where each substep keeps the update's ghost-filled
   // input tiles and the time-interpolated coarse tiles it read
@@ -804,6 +805,8 @@ fc_status fc_forest_destroy(fc_forest* F) {
     for (cudaEvent_t ev : F->ev_adj)
       if (ev) cudaEventDestroy(ev);
     if (F->ev_start) cudaEventDestroy(F->ev_start);
+    for (cudaEvent_t ev : F->ev_rev)
+      if (ev) cudaEventDestroy(ev);
     for (cudaStream_t ls : F->lev_stream)
       if (ls) cudaStreamDestroy(ls);
   }
@@ -1042,21 +1045,35 @@ static fc_status capture_adjoint_multirate(fc_forest* F, double dtc, cudaStream_
   const size_t tile = S2 * sizeof(real);
   const size_t cells = std::max<size_t>((size_t)H.npatch() * S2, 1);
   struct Sub {
-    int L;
+    int L, j;             // level and its substep index in the step
     double t, dt, alpha;  // t relative to the step's start
     size_t offq, offt;    // byte offsets of the kept level-L tiles and qT tiles
     int cur[kMaxLevel + 1];
   };
   std::vector<Sub> subs;
+  int nsub[kMaxLevel + 2] = {0};
   std::function<void(int, double, double, double)> rec = [&](int L, double t, double dt,
                                                                double alpha) {
-    subs.push_back(Sub{L, t, dt, alpha, 0, 0, {0}});
+    subs.push_back(Sub{L, nsub[L]++, t, dt, alpha, 0, 0, {0}});
     if (L < lmax) {
       rec(L + 1, t, 0.5 * dt, 0.0);
       rec(L + 1, t + 0.5 * dt, 0.5 * dt, 0.5);
     }
   };
   rec(lmin, 0.0, dtc, 0.0);
+  // sub index of level L's substep j
+  auto sub_of = [&](int L, int j) -> int {
+    if (L < lmin || L > lmax || j < 0 || j >= nsub[L]) return -1;
+    for (size_t k = 0; k < subs.size(); ++k)
+      if (subs[k].L == L && subs[k].j == j) return (int)k;
+    return -1;
+  };
+  if (F->ev_rev.size() < subs.size()) {
+    const size_t have = F->ev_rev.size();
+    F->ev_rev.resize(subs.size(), nullptr);
+    for (size_t k = have; k < subs.size(); ++k)
+      FC_CUDA(cudaEventCreateWithFlags(&F->ev_rev[k], cudaEventDisableTiming));
+  }
   const size_t store = cells * sizeof(real);
   size_t need = 2 * store;  // the start state: both stores
   for (auto& u : subs) {
@@ -1136,15 +1153,37 @@ static fc_status capture_adjoint_multirate(fc_forest* F, double dtc, cudaStream_
     if (e == cudaSuccess) e = cudaMemsetAsync(LT, 0, cells * sizeof(real), cs);
     if (e == cudaSuccess) e = cudaMemsetAsync(F->d_ds, 0, sizeof(double), cs);
     DevForest<real> Lv = dev<real>(F);
-    Lv.buf[0] = Lv.buf[1] = LQ;
+    Lv.buf[0] = LQ;
+    Lv.buf[1] = LO;
     for (int l = 0; l <= kMaxLevel; ++l) Lv.cur[l] = 0;
     if (e == cudaSuccess)
       e = launch_unpack(Lv, F->d_api_to_dev, static_cast<const real*>(F->mio), cs);
-    unsigned pending = 0;  // levels written by coarse-tile transposes still running beside
+    // Reverse sweep.  Each level's adjoint of its latest state accumulates in
+    // buf[par[L]] (LQ or LO), the next older one in the other buffer.  Each
+    // level runs on its own stream; the reverse of level L's substep j waits
+    // for the reverses of the substeps that read what it wrote: the finer
+    // level's substeps 2j + 1 and 2j + 2 (they read level L's new state), and
+    // for odd j the coarser level's substep (j + 1) / 2 (its ghosts averaged
+    // level L's new state).  These are the forward's waits reversed, so the
+    // critical path is again the finest level's chain.
+    real* bufs[2] = {LQ, LO};
+    int par[kMaxLevel + 2] = {0};
+    std::vector<char> done(subs.size(), 0);
+    bool forked[kMaxLevel + 1] = {};
+    if (e == cudaSuccess) e = cudaEventRecord(F->ev_start, cs);
     for (size_t k = subs.size(); k-- > 0 && e == cudaSuccess;) {
       const Sub& u = subs[k];
       const int p0 = H.lev_start[u.L], p1 = H.lev_start[u.L + 1];
       if (p1 <= p0) continue;
+      cudaStream_t ls = F->lev_stream[u.L];
+      if (!forked[u.L]) {
+        e = cudaStreamWaitEvent(ls, F->ev_start, 0);
+        forked[u.L] = true;
+      }
+      const int deps[3] = {sub_of(u.L + 1, 2 * u.j + 1), sub_of(u.L + 1, 2 * u.j + 2),
+                           (u.j & 1) ? sub_of(u.L - 1, (u.j + 1) / 2) : -1};
+      for (int d : deps)
+        if (d >= 0 && done[d] && e == cudaSuccess) e = cudaStreamWaitEvent(ls, F->ev_rev[d], 0);
       std::copy(u.cur, u.cur + kMaxLevel + 1, F->cur);
       const int tl = u.L > lmin ? u.L - 1 : -1;
       AdjSubArgs g{};
@@ -1169,31 +1208,25 @@ static fc_status capture_adjoint_multirate(fc_forest* F, double dtc, cudaStream_
       g.nb = (int)H.list_b[u.L].size();
       g.list_t = F->d_lists + F->off_t[u.L];
       g.nt = (int)H.list_t[u.L].size();
-      // the coarse tiles' transposes of an alpha = 1/2 substep (they write
-      // levels L-1 and L) run beside the reversed substeps of level L+1 that
-      // come next, which touch those levels only by commutative atomic adds;
-      // they are joined before the next update transpose of level L or L-1
-      if (e == cudaSuccess && (pending & ((1u << u.L) | (1u << (u.L + 1))))) {
-        e = cudaEventRecord(F->ev_adj[1], F->side);
-        if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, F->ev_adj[1], 0);
-        pending = 0;
-      }
-      const bool beside = std::fabs(u.alpha - 0.5) < 1e-9 && g.nt > 0;
-      g.part = beside ? 1 : 0;
-      if (e == cudaSuccess) e = launch_adjoint_substep(dev<real>(F), g, LQ, LO, LT, F->d_ds, cs);
-      if (beside && e == cudaSuccess) {
-        e = cudaEventRecord(F->ev_adj[0], cs);
-        if (e == cudaSuccess) e = cudaStreamWaitEvent(F->side, F->ev_adj[0], 0);
-        g.part = 2;
-        if (e == cudaSuccess)
-          e = launch_adjoint_substep(dev<real>(F), g, LQ, LO, LT, F->d_ds, F->side);
-        pending |= (1u << u.L) | (1u << (u.L - 1));
-      }
+      AdjAcc<real> c{};
+      c.lam_in = bufs[par[u.L]];
+      c.lam_out = bufs[par[u.L] ^ 1];
+      c.lam_fine = bufs[par[u.L + 1]];
+      c.lam_new = tl >= 0 ? bufs[par[tl]] : nullptr;
+      c.lam_old = tl >= 0 ? bufs[par[tl] ^ 1] : nullptr;
+      c.lamT = LT;
+      if (e == cudaSuccess) e = launch_adjoint_substep(dev<real>(F), g, c, F->d_ds, ls);
+      if (e == cudaSuccess) e = cudaEventRecord(F->ev_rev[k], ls);
+      done[k] = 1;
+      par[u.L] ^= 1;
     }
-    if (pending && e == cudaSuccess) {  // join the side stream before the result is read
-      e = cudaEventRecord(F->ev_adj[1], F->side);
-      if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, F->ev_adj[1], 0);
-    }
+    for (int l = 0; l <= kMaxLevel && e == cudaSuccess; ++l)  // rejoin before the result is read
+      if (forked[l]) {
+        e = cudaEventRecord(F->ev_fill[l], F->lev_stream[l]);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, F->ev_fill[l], 0);
+      }
+    // each level's adjoint of the step's start state is in buf[par[l]]
+    for (int l = 0; l <= kMaxLevel; ++l) Lv.cur[l] = par[l];
     if (e == cudaSuccess) e = launch_pack(Lv, F->d_api_to_dev, static_cast<real*>(F->mio), 0, cs);
     cp(F->buf[0], pool, store);
     cp(F->buf[1], pool + store, store);

@@ -402,10 +402,9 @@ cudaError_t launch_adjoint_step(const DevForest<real>& D, const AdjArgs& g, cons
                                 real* lam_out, double* dscale, cudaStream_t s);
 
 // Adjoint of one multirate substep of level L over (t, t + dt), on the
-// forward state before it (ghosts of the substep's fill in place, qT filled):
-// lam (adjoint of the current states, patch-store tiles), lamO (adjoint of
-// the previous states), lamT (adjoint of the qT tiles, zero on entry and on
-// return).  tlevel = L - 1 with weight alpha, or -1 on the coarsest level.
+// forward state before it (ghosts of the substep's fill in place, qT
+// filled), adding into the accumulators of AdjAcc.  tlevel = L - 1 with
+// weight alpha, or -1 on the coarsest level.
 struct AdjSubArgs {
   int L, p0, p1;  // level and its device range
   double t, dt, period, scale, dscale_factor;
@@ -425,13 +424,22 @@ struct AdjSubArgs {
   int tiles_p0;
   const void* coarse;
   int coarse_p0;
-  // kernels to launch: 0 all three, 1 the update's and the level ghosts'
-  // transposes, 2 the coarse tiles' transposes alone
-  int part;
+};
+// The adjoint's accumulators for one substep of level L (patch-store tile
+// layout): each level's adjoint of one state lives in one of two buffers and
+// receives every contribution by atomic adds, starting from zero.
+template <typename real>
+struct AdjAcc {
+  real* lam_in;    // level L, the state after the substep: read, then cleared
+  real* lam_out;   // level L, the state before it
+  real* lam_fine;  // level L+1, its state at the substep's start
+  real* lam_old;   // level L-1, the older and newer states of the time
+  real* lam_new;   //   interpolation
+  real* lamT;      // the qT tiles' adjoint (zero on entry and on return)
 };
 template <typename real>
-cudaError_t launch_adjoint_substep(const DevForest<real>& D, const AdjSubArgs& g, real* lam,
-                                   real* lamO, real* lamT, double* dscale, cudaStream_t s);
+cudaError_t launch_adjoint_substep(const DevForest<real>& D, const AdjSubArgs& g,
+                                   const AdjAcc<real>& c, double* dscale, cudaStream_t s);
 
 // device error word bits
 constexpr int kErrTimeout = 1;
