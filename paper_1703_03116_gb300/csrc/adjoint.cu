@@ -628,9 +628,11 @@ cudaError_t adj_advance_level(const DevForest<real>& D, int L, int p0, int p1, d
                               real* lam_out, double* dscale, cudaStream_t s,
                               const double* t0_dev = nullptr, const real* tiles = nullptr,
                               int tiles_p0 = 0, int acc = 0) {
-  // a whole CTA per patch: the more threads, the shorter each thread's chain
-  // through the phases (the kernel is latency-bound at these launch sizes)
-  constexpr int NT = MX >= 32 ? (sizeof(real) == 4 ? 1024 : 512) : (MX >= 16 ? 512 : 256);
+  // a whole CTA per patch, 512 threads at mx = 32: two CTAs per SM hold a
+  // finest level's patches in one wave while the coarser levels' reversed
+  // substeps run beside it (1024 threads, one CTA per SM, measured slower
+  // once the levels overlapped; 256 too)
+  constexpr int NT = MX >= 16 ? 512 : 256;
   static bool attr = false;
   constexpr size_t smem = adj_smem<real, MX>();
   if (!attr) {
