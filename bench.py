@@ -107,6 +107,12 @@ class Clocks:
                  "-lms", "100", "-i", str(self.index)], stdout=self.f, stderr=subprocess.DEVNULL)
         except (OSError, FileNotFoundError):
             self.proc = None
+        # the sampler's start-up (driver queries) must not land in the timed
+        # steps: wait, bounded, for its first sample before they begin
+        t_end = time.time() + 3.0
+        while (self.proc is not None and self.proc.poll() is None and time.time() < t_end
+               and os.path.getsize(self.f.name) == 0):
+            time.sleep(0.01)
         return self
 
     def __exit__(self, *exc):
