@@ -20,12 +20,12 @@
 //                  Eq. ghost_coarse): ghost adjoints go to the neighbours'
 //                  interior cells (atomic adds).
 //
-// Multirate substep of level L (launch_adjoint_substep), three kernels: the
-// update's transpose (adj_advance); the transposes of level L's ghosts, each
-// patch's four phases in one CTA (adj_level_ghosts); the transposes of the
-// ghosts of the level L-1 patches read through the time-interpolated tiles
-// and of qT = (1 - alpha) q_old + alpha q (adj_coarse_tiles; sources read on
-// the fly split their share inside the copy transpose).  Each level's
+// Multirate substep of level L (launch_adjoint_substep), two kernels: the
+// update's transpose followed, in the same CTA, by that of the patch's ghost
+// fill (adj_advance); the transposes of the ghosts of the level L-1 patches
+// read through the time-interpolated tiles and of qT = (1 - alpha) q_old +
+// alpha q (adj_coarse_tiles; sources read on the fly split their share
+// inside the copy transpose).  Each level's
 // adjoint of one state accumulates in one of two buffers (AdjAcc), every
 // contribution an atomic add into a zeroed accumulator, so the substeps of
 // different levels can run side by side wherever their forward substeps
@@ -87,18 +87,169 @@ __device__ __forceinline__ EdgeFw<real> edge_fw(int order, int limiter, int tran
   return e;
 }
 
+// ---------------------------------------------------------------------
+// Transposes of Alg. 1, per patch (threads tid, stride nt of a group that
+// holds the patch's staged neighbour entries).  Each consumes (zeroes) the
+// adjoint of the patch's own ghost cells it handles and scatters it, with
+// atomics, to the cells those ghosts were computed from.
+
+// transpose of a wall-BC pass: exterior ghost adjoint -> the clamped cell (an
+// exterior ghost copies a non-exterior cell, so one pass in any order)
+template <typename real, int MX>
+__device__ void adj_bc_patch(const PatchMeta& pm, real* L, int tid, int nt) {
+  constexpr int S = MX + 4;
+  const int N = MX << pm.level;
+  for (int k = tid; k < num_ghosts<MX>(); k += nt) {
+    int i, j;
+    ghost_ij<MX>(k, i, j);
+    const int gx = pm.x * MX + i, gy = pm.y * MX + j;
+    const bool ox = gx < 0 || gx >= N, oy = gy < 0 || gy >= N;
+    if (!ox && !oy) continue;
+    const int ic = ox ? (gx < 0 ? 0 : MX - 1) : i;
+    const int jc = oy ? (gy < 0 ? 0 : MX - 1) : j;
+    atomicAdd(&L[(jc + kMbc) * S + ic + kMbc], L[(j + kMbc) * S + i + kMbc]);
+    L[(j + kMbc) * S + i + kMbc] = real(0);
+  }
+}
+
+// transpose of the interpolation (Eq. ghost_fine): each coarse ghost's
+// adjoint goes to the coarse cells it read, on the minmod pieces the forward
+// data select.  A coarse patch on `tlevel` was read through the time-
+// interpolated tiles (coarse_src: patch c at coarse_src + (c - coarse_p0)
+// tiles, else D.qT) and takes the adjoint in lamT; else from the store, lam.
+template <typename real, int MX>
+__device__ void adj_interp_patch(const DevForest<real>& D, const NbrStage& st, const PatchMeta& pm,
+                                 real* L, real* lam, int tlevel, real* lamT, const real* coarse_src,
+                                 int coarse_p0, int tid, int nt) {
+  constexpr int S = MX + 4;
+  for (int k = tid; k < num_ghosts<MX>(); k += nt) {
+    int i, j;
+    ghost_ij<MX>(k, i, j);
+    const int r = region_of<MX>(i, j);
+    const NbrEntry& e = st.e[r];
+    if (e.kind != NB_COARSE) continue;
+    const int2 Ip = apply_a(e.a, pm.x * MX + i, pm.y * MX + j);
+    const int gx = Ip.x + e.fx, gy = Ip.y + e.fy;
+    const PatchMeta& nm = st.m0[r];
+    const int ic = (gx >> 1) - nm.x * MX, jc = (gy >> 1) - nm.y * MX;
+    if (ic < 0 || ic >= MX || jc < 0 || jc >= MX) continue;
+    const real dx = (gx & 1) ? real(1) : real(-1);
+    const real dy = (gy & 1) ? real(1) : real(-1);
+    const size_t o = (size_t)(jc + kMbc) * S + ic + kMbc;
+    const bool viaT = nm.level == tlevel;
+    const real* C = (viaT ? (coarse_src ? coarse_src + (size_t)(e.n0 - coarse_p0) * S * S
+                                        : patch_ptr(D.qT, e.n0, S))
+                          : patch_ptr(D.buf[D.cur[nm.level]], e.n0, S)) +
+                    o;
+    real* LC = (viaT ? lamT : lam) + (size_t)e.n0 * S * S + o;
+    const real lg = L[(j + kMbc) * S + i + kMbc];
+    L[(j + kMbc) * S + i + kMbc] = real(0);
+    const real q0 = C[0];
+    const real ax = C[1] - q0, bx = q0 - C[-1], ay = C[S] - q0, by = q0 - C[-S];
+    const real dax = (ax * bx > real(0) && fabs(ax) < fabs(bx)) ? real(1) : real(0);
+    const real dbx = (ax * bx > real(0) && !(fabs(ax) < fabs(bx))) ? real(1) : real(0);
+    const real day = (ay * by > real(0) && fabs(ay) < fabs(by)) ? real(1) : real(0);
+    const real dby = (ay * by > real(0) && !(fabs(ay) < fabs(by))) ? real(1) : real(0);
+    const real lsx = real(0.25) * dx * lg, lsy = real(0.25) * dy * lg;
+    atomicAdd(LC, lg + lsx * (dbx - dax) + lsy * (dby - day));
+    atomicAdd(LC + 1, lsx * dax);
+    atomicAdd(LC - 1, -lsx * dbx);
+    atomicAdd(LC + S, lsy * day);
+    atomicAdd(LC - S, -lsy * dby);
+  }
+}
+
+// Where the transposes of copies and averages add: a neighbour on the
+// coarser level tlevel was read as (1 - alpha) q_old + alpha q (its shares
+// go to the accumulators of its older and newer states); a same-size one at
+// `same`, a finer one at `fine` (accumulators of those levels' states at the
+// substep's time).
+template <typename real>
+struct AdjTargets {
+  real* same;
+  real* fine;
+  real* t_old;
+  real* t_new;
+};
+
+template <typename real>
+__device__ __forceinline__ void adj_src_add(const AdjTargets<real>& g, bool viaT, bool fine,
+                                            real alpha, size_t o, real v) {
+  if (viaT) {
+    atomicAdd(g.t_old + o, (real(1) - alpha) * v);
+    if (alpha != real(0)) atomicAdd(g.t_new + o, alpha * v);
+  } else {
+    atomicAdd((fine ? g.fine : g.same) + o, v);
+  }
+}
+
+// transpose of copy / average (Eq. transform, Eq. ghost_coarse): ghost
+// adjoint (in L, the patch's own tile) -> neighbour interiors
+template <typename real, int MX>
+__device__ void adj_copy_patch(const NbrStage& st, const PatchMeta& pm, real* L,
+                               const AdjTargets<real>& g, int tlevel, real alpha, int tid, int nt) {
+  constexpr int S = MX + 4;
+  for (int k = tid; k < num_ghosts<MX>(); k += nt) {
+    int i, j;
+    ghost_ij<MX>(k, i, j);
+    const int r = region_of<MX>(i, j);
+    const NbrEntry& e = st.e[r];
+    if (e.kind != NB_SAME && e.kind != NB_FINE) continue;
+    const real lg = L[(j + kMbc) * S + i + kMbc];
+    L[(j + kMbc) * S + i + kMbc] = real(0);
+    const int2 Ip = apply_a(e.a, pm.x * MX + i, pm.y * MX + j);
+    const int gx = Ip.x + e.fx, gy = Ip.y + e.fy;
+    if (e.kind == NB_SAME) {
+      const PatchMeta& nm = st.m0[r];
+      const int lx = gx - nm.x * MX, ly = gy - nm.y * MX;
+      if (lx < 0 || lx >= MX || ly < 0 || ly >= MX) continue;
+      adj_src_add(g, nm.level == tlevel, false, alpha,
+                  (size_t)e.n0 * S * S + (ly + kMbc) * S + lx + kMbc, lg);
+    } else {
+      int n = e.n0;
+      const PatchMeta* nm = &st.m0[r];
+      int lx = 2 * gx - nm->x * MX, ly = 2 * gy - nm->y * MX;
+      if (lx < 0 || lx >= MX || ly < 0 || ly >= MX) {
+        if (e.n1 < 0) continue;
+        n = e.n1;
+        nm = &st.m1[r];
+        lx = 2 * gx - nm->x * MX;
+        ly = 2 * gy - nm->y * MX;
+        if (lx < 0 || lx >= MX || ly < 0 || ly >= MX) continue;
+      }
+      for (int q = 0; q < 4; ++q)
+        adj_src_add(g, nm->level == tlevel, true, alpha,
+                    (size_t)n * S * S + (ly + (q >> 1) + kMbc) * S + lx + (q & 1) + kMbc,
+                    real(0.25) * lg);
+    }
+  }
+}
+
+// Where the update transpose of a multirate substep also transposes its
+// patches' ghost fill (the level's Alg. 1, reversed: interpolation from the
+// coarse tiles into lamT, then copies and averages into the accumulators of
+// level L, lam_out, and of level L+1, lam_fine) straight from the tile's
+// adjoint in shared memory.
+template <typename real>
+struct AdjGhosts {
+  real* lam_fine;
+  real* lamT;
+  const real* coarse_src;
+  int coarse_p0, tlevel;
+};
+
 // The forward tile of patch p is read from the store, or from
 // tiles + (p - tiles_p0) tiles when `tiles` is given (kept copies).  acc
-// (multirate accumulators): lam_in's tile is cleared once read, and the
-// input tile's adjoint is added to lam_out's interior (other levels' and
-// neighbours' transposes add there too) while its ghost ring, which only
-// this patch's ghost transposes read, is stored.
+// (multirate accumulators, with g): lam_in's tile is cleared once read, the
+// ghost ring of the input tile's adjoint is transposed through the level's
+// ghost fill at once (g), and its interior is added to lam_out's (other
+// levels' and neighbours' transposes add there too).
 template <typename real, int MX, int NT>
 __global__ void __launch_bounds__(NT) adj_advance_kernel(DevForest<real> D, AdvArgs a,
                                                          real* lam_in, real* lam_out,
                                                          double* dscale, double dfac, int p0,
                                                          int p1, const real* tiles, int tiles_p0,
-                                                         int acc) {
+                                                         int acc, AdjGhosts<real> g) {
   constexpr int S = MX + 4;
   constexpr int NE = (MX + 1) * (MX + 2);
   constexpr int NV = MX + 3;
@@ -118,6 +269,7 @@ __global__ void __launch_bounds__(NT) adj_advance_kernel(DevForest<real> D, AdvA
   real* Ty = Tx + NV;
   __shared__ double red[NT / 32];
   __shared__ real ucoef_s;
+  __shared__ NbrStage st;  // acc: the patch's neighbour entries
   const int order = D.order, limiter = D.limiter, transverse = D.transverse;
   const bool swirl = D.vel_kind == FC_VEL_SWIRL;
   const real cu = real(D.vel[0]), cv = real(D.vel[1]);
@@ -138,6 +290,7 @@ __global__ void __launch_bounds__(NT) adj_advance_kernel(DevForest<real> D, AdvA
     const real* src = tiles ? tiles + (size_t)(p - tiles_p0) * S * S
                             : D.buf[D.cur[pm.level]] + (size_t)p * S * S;
     real* lin = lam_in + (size_t)p * S * S;
+    if (acc) stage_neighbours(D.meta, D.nbr, p, st, threadIdx.x);
     for (int k = threadIdx.x; k < S * S; k += NT) {
       Q[k] = src[k];
       LQ[k] = real(0);
@@ -334,12 +487,18 @@ __global__ void __launch_bounds__(NT) adj_advance_kernel(DevForest<real> D, AdvA
     }
     real* lout = lam_out + (size_t)p * S * S;
     if (acc) {
-      for (int k = threadIdx.x; k < S * S; k += NT) {
-        const int i = k % S - 2, j = k / S - 2;
-        if (i >= 0 && i < MX && j >= 0 && j < MX)
-          atomicAdd(lout + k, LQ[k]);
-        else
-          lout[k] = LQ[k];
+      // the level's ghost fill reversed (its wall passes' transposes add
+      // nothing once the exterior adjoint has moved to the clamped cells
+      // above): interpolation from the coarse tiles, then copies / averages
+      adj_interp_patch<real, MX>(D, st, pm, LQ, lam_out, g.tlevel, g.lamT, g.coarse_src,
+                                 g.coarse_p0, threadIdx.x, NT);
+      __syncthreads();
+      adj_copy_patch<real, MX>(st, pm, LQ, AdjTargets<real>{lam_out, g.lam_fine, nullptr, nullptr},
+                               g.tlevel, real(0), threadIdx.x, NT);
+      __syncthreads();
+      for (int k = threadIdx.x; k < MX * MX; k += NT) {
+        const int o = (k / MX + 2) * S + (k % MX) + 2;
+        atomicAdd(lout + o, LQ[o]);
       }
     } else {
       for (int k = threadIdx.x; k < S * S; k += NT) lout[k] = LQ[k];
@@ -354,144 +513,6 @@ __global__ void __launch_bounds__(NT) adj_advance_kernel(DevForest<real> D, AdvA
     double v = threadIdx.x < NT / 32 ? red[threadIdx.x] : 0.0;
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
     if (threadIdx.x == 0) atomicAdd(dscale, v * dfac);
-  }
-}
-
-// ---------------------------------------------------------------------
-// Transposes of Alg. 1, per patch (threads tid, stride nt of a group that
-// holds the patch's staged neighbour entries).  Each consumes (zeroes) the
-// adjoint of the patch's own ghost cells it handles and scatters it, with
-// atomics, to the cells those ghosts were computed from.
-
-// transpose of a wall-BC pass: exterior ghost adjoint -> the clamped cell (an
-// exterior ghost copies a non-exterior cell, so one pass in any order)
-template <typename real, int MX>
-__device__ void adj_bc_patch(const PatchMeta& pm, real* L, int tid, int nt) {
-  constexpr int S = MX + 4;
-  const int N = MX << pm.level;
-  for (int k = tid; k < num_ghosts<MX>(); k += nt) {
-    int i, j;
-    ghost_ij<MX>(k, i, j);
-    const int gx = pm.x * MX + i, gy = pm.y * MX + j;
-    const bool ox = gx < 0 || gx >= N, oy = gy < 0 || gy >= N;
-    if (!ox && !oy) continue;
-    const int ic = ox ? (gx < 0 ? 0 : MX - 1) : i;
-    const int jc = oy ? (gy < 0 ? 0 : MX - 1) : j;
-    atomicAdd(&L[(jc + kMbc) * S + ic + kMbc], L[(j + kMbc) * S + i + kMbc]);
-    L[(j + kMbc) * S + i + kMbc] = real(0);
-  }
-}
-
-// transpose of the interpolation (Eq. ghost_fine): each coarse ghost's
-// adjoint goes to the coarse cells it read, on the minmod pieces the forward
-// data select.  A coarse patch on `tlevel` was read through the time-
-// interpolated tiles (coarse_src: patch c at coarse_src + (c - coarse_p0)
-// tiles, else D.qT) and takes the adjoint in lamT; else from the store, lam.
-template <typename real, int MX>
-__device__ void adj_interp_patch(const DevForest<real>& D, const NbrStage& st, const PatchMeta& pm,
-                                 real* L, real* lam, int tlevel, real* lamT, const real* coarse_src,
-                                 int coarse_p0, int tid, int nt) {
-  constexpr int S = MX + 4;
-  for (int k = tid; k < num_ghosts<MX>(); k += nt) {
-    int i, j;
-    ghost_ij<MX>(k, i, j);
-    const int r = region_of<MX>(i, j);
-    const NbrEntry& e = st.e[r];
-    if (e.kind != NB_COARSE) continue;
-    const int2 Ip = apply_a(e.a, pm.x * MX + i, pm.y * MX + j);
-    const int gx = Ip.x + e.fx, gy = Ip.y + e.fy;
-    const PatchMeta& nm = st.m0[r];
-    const int ic = (gx >> 1) - nm.x * MX, jc = (gy >> 1) - nm.y * MX;
-    if (ic < 0 || ic >= MX || jc < 0 || jc >= MX) continue;
-    const real dx = (gx & 1) ? real(1) : real(-1);
-    const real dy = (gy & 1) ? real(1) : real(-1);
-    const size_t o = (size_t)(jc + kMbc) * S + ic + kMbc;
-    const bool viaT = nm.level == tlevel;
-    const real* C = (viaT ? (coarse_src ? coarse_src + (size_t)(e.n0 - coarse_p0) * S * S
-                                        : patch_ptr(D.qT, e.n0, S))
-                          : patch_ptr(D.buf[D.cur[nm.level]], e.n0, S)) +
-                    o;
-    real* LC = (viaT ? lamT : lam) + (size_t)e.n0 * S * S + o;
-    const real lg = L[(j + kMbc) * S + i + kMbc];
-    L[(j + kMbc) * S + i + kMbc] = real(0);
-    const real q0 = C[0];
-    const real ax = C[1] - q0, bx = q0 - C[-1], ay = C[S] - q0, by = q0 - C[-S];
-    const real dax = (ax * bx > real(0) && fabs(ax) < fabs(bx)) ? real(1) : real(0);
-    const real dbx = (ax * bx > real(0) && !(fabs(ax) < fabs(bx))) ? real(1) : real(0);
-    const real day = (ay * by > real(0) && fabs(ay) < fabs(by)) ? real(1) : real(0);
-    const real dby = (ay * by > real(0) && !(fabs(ay) < fabs(by))) ? real(1) : real(0);
-    const real lsx = real(0.25) * dx * lg, lsy = real(0.25) * dy * lg;
-    atomicAdd(LC, lg + lsx * (dbx - dax) + lsy * (dby - day));
-    atomicAdd(LC + 1, lsx * dax);
-    atomicAdd(LC - 1, -lsx * dbx);
-    atomicAdd(LC + S, lsy * day);
-    atomicAdd(LC - S, -lsy * dby);
-  }
-}
-
-// Where the transposes of copies and averages add: a neighbour on the
-// coarser level tlevel was read as (1 - alpha) q_old + alpha q (its shares
-// go to the accumulators of its older and newer states); a same-size one at
-// `same`, a finer one at `fine` (accumulators of those levels' states at the
-// substep's time).
-template <typename real>
-struct AdjTargets {
-  real* same;
-  real* fine;
-  real* t_old;
-  real* t_new;
-};
-
-template <typename real>
-__device__ __forceinline__ void adj_src_add(const AdjTargets<real>& g, bool viaT, bool fine,
-                                            real alpha, size_t o, real v) {
-  if (viaT) {
-    atomicAdd(g.t_old + o, (real(1) - alpha) * v);
-    if (alpha != real(0)) atomicAdd(g.t_new + o, alpha * v);
-  } else {
-    atomicAdd((fine ? g.fine : g.same) + o, v);
-  }
-}
-
-// transpose of copy / average (Eq. transform, Eq. ghost_coarse): ghost
-// adjoint (in L, the patch's own tile) -> neighbour interiors
-template <typename real, int MX>
-__device__ void adj_copy_patch(const NbrStage& st, const PatchMeta& pm, real* L,
-                               const AdjTargets<real>& g, int tlevel, real alpha, int tid, int nt) {
-  constexpr int S = MX + 4;
-  for (int k = tid; k < num_ghosts<MX>(); k += nt) {
-    int i, j;
-    ghost_ij<MX>(k, i, j);
-    const int r = region_of<MX>(i, j);
-    const NbrEntry& e = st.e[r];
-    if (e.kind != NB_SAME && e.kind != NB_FINE) continue;
-    const real lg = L[(j + kMbc) * S + i + kMbc];
-    L[(j + kMbc) * S + i + kMbc] = real(0);
-    const int2 Ip = apply_a(e.a, pm.x * MX + i, pm.y * MX + j);
-    const int gx = Ip.x + e.fx, gy = Ip.y + e.fy;
-    if (e.kind == NB_SAME) {
-      const PatchMeta& nm = st.m0[r];
-      const int lx = gx - nm.x * MX, ly = gy - nm.y * MX;
-      if (lx < 0 || lx >= MX || ly < 0 || ly >= MX) continue;
-      adj_src_add(g, nm.level == tlevel, false, alpha,
-                  (size_t)e.n0 * S * S + (ly + kMbc) * S + lx + kMbc, lg);
-    } else {
-      int n = e.n0;
-      const PatchMeta* nm = &st.m0[r];
-      int lx = 2 * gx - nm->x * MX, ly = 2 * gy - nm->y * MX;
-      if (lx < 0 || lx >= MX || ly < 0 || ly >= MX) {
-        if (e.n1 < 0) continue;
-        n = e.n1;
-        nm = &st.m1[r];
-        lx = 2 * gx - nm->x * MX;
-        ly = 2 * gy - nm->y * MX;
-        if (lx < 0 || lx >= MX || ly < 0 || ly >= MX) continue;
-      }
-      for (int q = 0; q < 4; ++q)
-        adj_src_add(g, nm->level == tlevel, true, alpha,
-                    (size_t)n * S * S + (ly + (q >> 1) + kMbc) * S + lx + (q & 1) + kMbc,
-                    real(0.25) * lg);
-    }
   }
 }
 
@@ -533,42 +554,6 @@ __global__ void adj_copy_kernel(DevForest<real> D, real* lam) {
     adj_copy_patch<real, MX>(st, pm, lam + (size_t)p * S * S,
                              AdjTargets<real>{lam, lam, nullptr, nullptr}, -1, real(0),
                              threadIdx.x, blockDim.x);
-    __syncthreads();
-  }
-}
-
-// multirate substep, level L's patches [p0, p1): the transposes of the
-// level-L ghosts in reverse phase order -- boundary condition, interpolation
-// from the time-interpolated coarse tiles (into lamT), boundary condition,
-// copy / average (into the accumulators of level L, lam, and of level L+1,
-// lam_fine, for their states at the substep's start).  Only the patch's own
-// ghost cells (in lam, zeroed as consumed) are read, so one CTA per patch
-// runs all four.
-template <typename real, int MX>
-__global__ void adj_level_ghosts_kernel(DevForest<real> D, int p0, int p1, real* lam,
-                                        real* lam_fine, int tlevel, real* lamT,
-                                        const real* coarse_src, int coarse_p0) {
-  constexpr int S = MX + 4;
-  __shared__ NbrStage st;
-  const bool walls = D.domain == FC_DOMAIN_WALLS;
-  for (int p = p0 + blockIdx.x; p < p1; p += gridDim.x) {
-    stage_neighbours(D.meta, D.nbr, p, st, threadIdx.x);
-    const PatchMeta pm = D.meta[p];
-    real* L = lam + (size_t)p * S * S;
-    __syncthreads();
-    if (walls) {
-      adj_bc_patch<real, MX>(pm, L, threadIdx.x, blockDim.x);
-      __syncthreads();
-    }
-    adj_interp_patch<real, MX>(D, st, pm, L, lam, tlevel, lamT, coarse_src, coarse_p0, threadIdx.x,
-                               blockDim.x);
-    __syncthreads();
-    if (walls) {
-      adj_bc_patch<real, MX>(pm, L, threadIdx.x, blockDim.x);
-      __syncthreads();
-    }
-    adj_copy_patch<real, MX>(st, pm, L, AdjTargets<real>{lam, lam_fine, nullptr, nullptr}, tlevel,
-                             real(0), threadIdx.x, blockDim.x);
     __syncthreads();
   }
 }
@@ -627,7 +612,8 @@ cudaError_t adj_advance_level(const DevForest<real>& D, int L, int p0, int p1, d
                               double period, double scale, double dfac, real* lam_in,
                               real* lam_out, double* dscale, cudaStream_t s,
                               const double* t0_dev = nullptr, const real* tiles = nullptr,
-                              int tiles_p0 = 0, int acc = 0) {
+                              int tiles_p0 = 0, int acc = 0,
+                              AdjGhosts<real> g = AdjGhosts<real>{}) {
   // a whole CTA per patch, 512 threads at mx = 32: two CTAs per SM hold a
   // finest level's patches in one wave while the coarser levels' reversed
   // substeps run beside it (1024 threads, one CTA per SM, measured slower
@@ -651,7 +637,7 @@ cudaError_t adj_advance_level(const DevForest<real>& D, int L, int p0, int p1, d
   al.t0_dev = t0_dev;
   al.sfac = D.vel_kind == FC_VEL_SWIRL ? scale * sin(M_PI * al.h) / (M_PI * al.h) : 0.0;
   adj_advance_kernel<real, MX, NT><<<p1 - p0, NT, smem, s>>>(D, al, lam_in, lam_out, dscale, dfac,
-                                                               p0, p1, tiles, tiles_p0, acc);
+                                                               p0, p1, tiles, tiles_p0, acc, g);
   ++launch_counter();
   return cudaGetLastError();
 }
@@ -689,12 +675,10 @@ cudaError_t adjoint_sub_mx(const DevForest<real>& D, const AdjSubArgs& g, const 
   const real alpha = real(g.alpha);
   cudaError_t e = adj_advance_level<real, MX>(
       D, g.L, g.p0, g.p1, g.t, g.dt, g.period, g.scale, g.dscale_factor, c.lam_in, c.lam_out,
-      dscale, s, g.t0_dev, static_cast<const real*>(g.tiles), g.tiles_p0, 1);
+      dscale, s, g.t0_dev, static_cast<const real*>(g.tiles), g.tiles_p0, 1,
+      AdjGhosts<real>{c.lam_fine, c.lamT, static_cast<const real*>(g.coarse), g.coarse_p0,
+                      g.tlevel});
   if (e != cudaSuccess) return e;
-  adj_level_ghosts_kernel<real, MX><<<grid_for(n), 256, 0, s>>>(
-      D, g.p0, g.p1, c.lam_out, c.lam_fine, g.tlevel, c.lamT, static_cast<const real*>(g.coarse),
-      g.coarse_p0);
-  ++launch_counter();
   if (g.nt > 0) {
     adj_coarse_tiles_kernel<real, MX><<<grid_for(g.nt), 256, 0, s>>>(
         D, g.list_t, g.nt, c.lam_out, c.lam_old, c.lam_new, g.tlevel, alpha, c.lamT);
