@@ -138,13 +138,11 @@ struct fc_forest {
   // untimed executable graphs of a previous layout: a new capture of the same
   // shape updates one in place instead of instantiating a new one
   std::vector<cudaGraphExec_t> stale;
-  // while a coarse step is captured: the coarse-neighbour fill of each
-  // substep runs on a side stream, forked where its inputs are ready (the
-  // graph becomes a DAG whose critical path is the chain of updates)
+  // while a coarse step is captured: each level's point before and after
+  // its latest update (ev_pre, ev_post; pre_ok, post_ok once recorded in the
+  // step), and its stream's end (ev_fill)
   bool dag = false;
-  cudaStream_t side = nullptr;
   cudaEvent_t ev_pre[kMaxLevel + 1] = {}, ev_post[kMaxLevel + 1] = {}, ev_fill[kMaxLevel + 1] = {};
-  cudaEvent_t ev_adj[2] = {};  // the adjoint graph's fork and join
   bool pre_ok[kMaxLevel + 1] = {}, post_ok[kMaxLevel + 1] = {};
   // a captured coarse step with fused fills runs each level on its own
   // stream (lev_stream[L], forked from ev_start), each update waiting only
@@ -567,17 +565,15 @@ cudaError_t keep_coarse_tiles(fc_forest* F, int L, cudaStream_t s) {
                          (size_t)(b - a) * tile, cudaMemcpyDeviceToDevice, s);
 }
 
-// the side stream and events of captured steps (created outside a capture)
-fc_status ensure_side(fc_forest* F) {
-  if (F->side) return FC_OK;
-  FC_CUDA(cudaStreamCreateWithFlags(&F->side, cudaStreamNonBlocking));
+// the level streams and events of captured steps (created outside a capture)
+fc_status ensure_streams(fc_forest* F) {
+  if (F->ev_start) return FC_OK;
   for (int l = 0; l <= kMaxLevel; ++l)
     for (cudaEvent_t* ev : {&F->ev_pre[l], &F->ev_post[l], &F->ev_fill[l]})
       FC_CUDA(cudaEventCreateWithFlags(ev, cudaEventDisableTiming));
-  for (cudaEvent_t& ev : F->ev_adj) FC_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
-  FC_CUDA(cudaEventCreateWithFlags(&F->ev_start, cudaEventDisableTiming));
   for (int l = 0; l <= kMaxLevel; ++l)
     FC_CUDA(cudaStreamCreateWithFlags(&F->lev_stream[l], cudaStreamNonBlocking));
+  FC_CUDA(cudaEventCreateWithFlags(&F->ev_start, cudaEventDisableTiming));  // last: "created"
   return FC_OK;
 }
 
@@ -632,29 +628,13 @@ fc_status advance_level_t(fc_forest* F, int L, double t, double dt, cudaStream_t
                           H.desc.domain != FC_DOMAIN_SPHERE && !F->keep_qT && !F->keep_tiles;
       if (direct) A.ntargets = 0;
       a.direct = direct ? 1 : 0;
-      // inside a captured step the fill forks off where its inputs are final:
-      // alpha = 0 reads level L-1's state from before its update and level
-      // L's current one (fork before level L-1's update); alpha = 1/2 waits
-      // for level L's previous substep only
-      const bool fork = F->dag && !lev && A.ntargets > 0 && tlevel >= 0 &&
-                        ((alpha == 0.0 && F->pre_ok[L - 1]) ||
-                         (std::fabs(alpha - 0.5) < 1e-9 && F->post_ok[L]));
-      if (fork) {
-        FC_CUDA(cudaStreamWaitEvent(F->side, alpha == 0.0 ? F->ev_pre[L - 1] : F->ev_post[L], 0));
-        {
-          Timed tm(F, 1, F->side, gb * A.ntargets);
-          FC_CUDA(launch_fill_coarse(D, A, F->side));
-        }
-        FC_CUDA(keep_coarse_tiles(F, L, F->side));
-        FC_CUDA(cudaEventRecord(F->ev_fill[L], F->side));
-        FC_CUDA(cudaStreamWaitEvent(s, F->ev_fill[L], 0));
-      } else {
-        {
-          Timed tm(F, 1, s, gb * A.ntargets);
-          FC_CUDA(launch_fill_coarse(D, A, s));
-        }
-        FC_CUDA(keep_coarse_tiles(F, L, s));
+      // (inside a captured step this runs on the level's own stream, after
+      // the waits above: see fc_forest::dag_levels)
+      {
+        Timed tm(F, 1, s, gb * A.ntargets);
+        FC_CUDA(launch_fill_coarse(D, A, s));
       }
+      FC_CUDA(keep_coarse_tiles(F, L, s));
       a.gather = 1;
       a.tlevel = tlevel;
       a.alpha = alpha;
@@ -797,13 +777,10 @@ fc_status fc_forest_destroy(fc_forest* F) {
   cudaDeviceSynchronize();
   destroy_timers(F);
   if (F->cap_stream) cudaStreamDestroy(F->cap_stream);
-  if (F->side) {
-    cudaStreamDestroy(F->side);
+  if (F->ev_start) {
     for (int l = 0; l <= kMaxLevel; ++l)
       for (cudaEvent_t ev : {F->ev_pre[l], F->ev_post[l], F->ev_fill[l]})
         if (ev) cudaEventDestroy(ev);
-    for (cudaEvent_t ev : F->ev_adj)
-      if (ev) cudaEventDestroy(ev);
     if (F->ev_start) cudaEventDestroy(F->ev_start);
     for (cudaEvent_t ev : F->ev_rev)
       if (ev) cudaEventDestroy(ev);
@@ -1104,7 +1081,7 @@ static fc_status capture_adjoint_multirate(fc_forest* F, double dtc, cudaStream_
   int cur0[kMaxLevel + 1];
   std::copy(F->cur, F->cur + kMaxLevel + 1, cur0);
   {
-    const fc_status sst = ensure_side(F);
+    const fc_status sst = ensure_streams(F);
     if (sst != FC_OK) return sst;
   }
   const bool timing = F->timing;
@@ -1448,7 +1425,7 @@ fc_status fc_step_multirate(fc_forest* F, double t, double dt_coarse, void* stre
     // capture with relative times; the host bookkeeping done while capturing
     // is what one replay does to the state
     {
-      const fc_status sst = ensure_side(F);
+      const fc_status sst = ensure_streams(F);
       if (sst != FC_OK) return sst;
     }
     F->capture_pairs = &ng.pairs;
