@@ -182,6 +182,9 @@ fc_status fc_adjoint_step_global(fc_forest* forest, double t, double dt, void* l
  *   lam     device, in/out, field layout: dL/dq(t + dt_coarse) on entry,
  *           dL/dq(t) on return;
  *   dscale  device, one double, accumulated: += lam^T dq/dsigma.
+ * Every contribution to an adjoint is an atomic add (the levels' reversed
+ * substeps run side by side where their forward substeps could), so the
+ * rounding order of those sums is not fixed.
  * Device memory: three adjoint stores plus the kept states (about two
  * stores per substep for the levels it touches), held until the forest is
  * destroyed.  Square domains only (FC_ERR_INVALID_ARG on the sphere).
