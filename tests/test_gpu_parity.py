@@ -259,6 +259,33 @@ def test_graph_replay_matches_direct_launches():
     np.testing.assert_array_equal(a.get_q(), b.get_q())
 
 
+def test_level_branches_match_one_stream_over_many_steps():
+    """The captured steps run each level on its own stream, every substep
+    waiting only for the states it reads.  A missing wait would be a race:
+    over 12 coarse steps of the full-size swirl forest (levels 2-6, 32^2),
+    regridding every 4, the replayed steps must give the same bits as direct
+    launches on one stream, and two replayed runs the same bits as each
+    other."""
+    w = synth.swirl(0)
+    _, dtc = synth.time_step(w)
+    ref, a = pair(fc, w, fc.F32)
+    runs = [a]
+    for graphs in (True, False):
+        f = fc.Forest(a.desc, ref.leaves())
+        f.set_q(a.get_q())
+        f.graphs(graphs)
+        runs.append(f)
+    for n in range(12):
+        for f in runs:
+            f.step_multirate(n * dtc, dtc)
+        if (n + 1) % 4 == 0:
+            changed = [f.tag_regrid(w.tau_refine, w.tau_coarsen) for f in runs]
+            assert len(set(changed)) == 1
+    q = [f.get_q() for f in runs]
+    np.testing.assert_array_equal(q[0], q[1])
+    np.testing.assert_array_equal(q[0], q[2])
+
+
 def test_timers_count_replayed_launches():
     w = synth.swirl(6, lmin=2, lmax=4, mx=16)
     _, dtc = synth.time_step(w)
