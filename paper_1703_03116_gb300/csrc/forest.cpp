@@ -437,17 +437,50 @@ std::string HostForest::work_lists() {
 
 namespace {
 
+// The leaf set of a regrid in progress.  Where it is small, a dense map from
+// every cell of each forest's finest level in play to the level of the leaf
+// covering it (a byte a cell; the set is a tiling throughout, so a leaf is
+// present when its anchor cell carries its level, and every erase is
+// followed by adds over the same cells); else a key map.
 struct LeafSet {
   const fc_forest_desc* d;
+  bool dense = false;
+  int f0 = 0;
+  std::vector<int> lo;      // finest level in play, per forest from f0
+  std::vector<size_t> off;  // start of each forest's cells
+  std::vector<int8_t> lev;
   KeyMap m;  // leaf key -> 1
+  size_t anchor(int f, int b, int l, int x, int y) const {
+    const int L = lo[f - f0], s = L - l;
+    return off[f - f0] + ((size_t)b << (2 * L)) + ((size_t)(y << s) << L) + (x << s);
+  }
   bool has(int f, int b, int l, int x, int y) const {
+    if (dense) return l <= lo[f - f0] && lev[anchor(f, b, l, x, y)] == l;
     return m.find(leaf_key(f, b, l, x, y)) >= 0;
   }
-  void add(const Leaf& a) { m.insert(leaf_key(a.f, a.b, a.l, a.x, a.y), 1); }
-  void erase(const Leaf& a) { m.erase(leaf_key(a.f, a.b, a.l, a.x, a.y)); }
+  void add(const Leaf& a) {
+    if (!dense) {
+      m.insert(leaf_key(a.f, a.b, a.l, a.x, a.y), 1);
+      return;
+    }
+    const int L = lo[a.f - f0], w = 1 << (L - a.l);
+    int8_t* row = lev.data() + anchor(a.f, a.b, a.l, a.x, a.y);
+    for (int j = 0; j < w; ++j, row += (size_t)1 << L) std::fill(row, row + w, (int8_t)a.l);
+  }
+  void erase(const Leaf& a) {
+    if (!dense) m.erase(leaf_key(a.f, a.b, a.l, a.x, a.y));
+  }
   // level of the leaf containing quadrant (b, l, x, y) if that leaf is at
   // level <= l, else -1 (the quadrant is subdivided)
   int holder_level(int f, int b, int l, int x, int y, Leaf* out) const {
+    if (dense) {
+      const int L = lo[f - f0];
+      const int cl = l < L ? l : L;
+      const int k = lev[anchor(f, b, cl, x >> (l - cl), y >> (l - cl))];
+      if (k > l) return -1;
+      if (out) *out = Leaf{f, b, k, x >> (l - k), y >> (l - k)};
+      return k;
+    }
     for (int k = l; k >= d->lmin; --k) {
       const int xs = x >> (l - k), ys = y >> (l - k);
       if (m.find(leaf_key(f, b, k, xs, ys)) >= 0) {
@@ -555,7 +588,24 @@ void regrid_range(const HostForest& F, const std::vector<double>& delta, double 
   }
   LeafSet s;
   s.d = &d;
-  s.m.clear((size_t)(k1 - k0) * 2, k1 > k0 ? F.leaves[k1 - 1].f - F.leaves[k0].f + 1 : 1);
+  {
+    const int nb = d.domain == FC_DOMAIN_SPHERE ? 6 : 1;
+    const int fa = k1 > k0 ? F.leaves[k0].f : 0, fb = k1 > k0 ? F.leaves[k1 - 1].f + 1 : 0;
+    s.f0 = fa;
+    s.lo.assign(fb - fa, 0);
+    for (int f = fa; f < fb; ++f)
+      s.lo[f - fa] = lmax_f.empty() ? d.lmax : std::min(lmax_f[f], d.lmax);
+    for (int k = k0; k < k1; ++k)
+      s.lo[F.leaves[k].f - fa] = std::max(s.lo[F.leaves[k].f - fa], F.leaves[k].l);
+    s.off.assign(fb - fa + 1, 0);
+    for (int f = fa; f < fb; ++f)
+      s.off[f - fa + 1] = s.off[f - fa] + ((size_t)nb << (2 * s.lo[f - fa]));
+    s.dense = s.off[fb - fa] <= ((size_t)1 << 22);
+    if (s.dense)
+      s.lev.assign(s.off[fb - fa], (int8_t)-1);
+    else
+      s.m.clear((size_t)(k1 - k0) * 2, fb - fa > 0 ? fb - fa : 1);
+  }
   for (int k = k0; k < k1; ++k)
     if (!refine[k]) s.add(F.leaves[k]);
   std::vector<Leaf> fresh;
@@ -568,6 +618,7 @@ void regrid_range(const HostForest& F, const std::vector<double>& delta, double 
         fresh.push_back(ch);
       }
     }
+  const size_t fresh_count = fresh.size();
   balance(&s, d.mx, std::move(fresh));
   std::vector<Leaf> accepted;
   for (const Leaf& P : parents) {
@@ -586,7 +637,7 @@ void regrid_range(const HostForest& F, const std::vector<double>& delta, double 
   // balance), or lies in a new parent (a coarsened family, emitted in place
   // of the family's first child, where its key sorts)
   out->clear();
-  out->reserve(s.m.size());
+  out->reserve((size_t)(k1 - k0) + 3 * fresh_count);
   for (int k = k0; k < k1; ++k) emit_region(s, F.leaves[k], d.lmin, out);
 }
 
