@@ -59,7 +59,8 @@ def parse():
     ap.add_argument("--dtype", choices=["f32", "f64"], default="f32")
     ap.add_argument("--no-variants", action="store_true", help="skip FP64, batched and CPU legs")
     ap.add_argument("--ensemble", type=int, default=256, help="forests in the batched variant")
-    ap.add_argument("--mode", choices=["full", "batched", "sphere", "adjoint"], default="full",
+    ap.add_argument("--mode", choices=["full", "batched", "sphere", "adjoint", "sweep"],
+                    default="full",
                     help="batched: time only the ensemble (a case sized for profiling)")
     return ap.parse_args()
 
@@ -378,6 +379,38 @@ def adjoint_cost(fc, torch, flush_buf, ncoarse: int = 25):
             "forward_cell_updates_per_s": updates / (fwd * 1e-3)}
 
 
+def granularity_sweep(fc, torch, hbm):
+    """Efficiency of one level substep against patches per launch (the GPU
+    counterpart of the paper's grids-per-process study, Sec. 5): uniform
+    periodic forests of 4^l patches (l = 2..7) for mx = 8, 16, 32, FP32; each
+    substep timed by the autotuner (candidates replayed from a CUDA graph),
+    the fastest kept."""
+    rows = []
+    for mx in (8, 16, 32):
+        for level in range(2, 8):
+            w = synth.uniform_periodic(seed=0, level=level, mx=mx)
+            desc = fc.make_desc(domain=fc.PERIODIC, mx=mx, lmin=level, lmax=level, dtype=fc.F32,
+                                velocity=w.velocity)
+            leaves = fc.uniform_leaves(level)
+            F = fc.Forest(desc, leaves)
+            F.set_q(q0_fn([w])(leaves))
+            rep = F.autotune()
+            n = len(leaves)
+            b = max(k for k in rep if (1 << k) <= n)
+            v, warps, fused, ns = rep[b]
+            cells = n * mx * mx
+            nbytes = n * ((mx + 4) ** 2 + mx * mx) * 4
+            rows.append({"mx": mx, "patches": n, "variant": ["staged", "walk", "walk1"][v],
+                         "warps": warps, "us_per_substep": ns * 1e-3,
+                         "cell_updates_per_s": cells / (ns * 1e-9),
+                         "hbm_frac": nbytes / (ns * 1e-9) / 1e9 / hbm})
+            F.close()
+            torch.cuda.synchronize()
+    return {"workload": "uniform periodic forests, levels 2-7 (16-16384 patches), mx 8/16/32, "
+                        "FP32, constant velocity, one level substep (gather fused)",
+            "rows": rows}
+
+
 def run_ours(args):
     import torch
 
@@ -404,6 +437,13 @@ def run_ours(args):
     hbm = hbm or 6800.0
 
     dtype = fc.F32 if args.dtype == "f32" else fc.F64
+    if args.mode == "sweep":  # substep efficiency against launch size
+        if rank == 0:
+            print(json.dumps({"variants": {"granularity": granularity_sweep(fc, torch, hbm)}}),
+                  flush=True)
+        if dist is not None:
+            dist.destroy_process_group()
+        return
     if args.mode == "adjoint":  # the adjoint cost alone (a case sized for profiling)
         if rank == 0:
             print(json.dumps({"variants": {"adjoint": adjoint_cost(fc, torch, flush_buf)}}),
