@@ -89,6 +89,8 @@ typedef struct {
   int order;
   int limiter;
   int transverse;
+  int indicator;  /* regrid indicator: 0 max |grad q| / 2, 1 max q - min q (Sec. 5.1) */
+  int smooth;     /* 1: smooth grading of the target levels (Sec. 3.3; square domains) */
 } fc_forest_desc;
 
 /* Create a forest from an explicit leaf list (Sec. 2: quadrants identified
@@ -138,11 +140,16 @@ fc_status fc_step_multirate(fc_forest* forest, double t, double dt_coarse, void*
 
 /* Tag and regrid (Sec. 3.1).  Fills ghosts, computes on the device the
  * per-leaf indicator max 1/2 |(q(i+1,j)-q(i-1,j), q(i,j+1)-q(i,j-1))| (in
- * the field's precision; the square root in FP64),
+ * the field's precision; the square root in FP64), or with desc.indicator =
+ * 1 the spread max q - min q of the leaf's interior,
  * refines leaves above tau_refine (below their forest's maximum level
  * lmax_per_forest[f], or desc.lmax when NULL), 2:1 balances by refinement,
  * coarsens families of four leaves all below tau_coarsen whose parent stays
- * balanced, and remaps the field on the device (copy; Eq. ghost_fine
+ * balanced (desc.smooth = 1: each leaf's target level -- one finer if above
+ * tau_refine, one coarser if below tau_coarsen, else its own -- is first
+ * raised to the largest target among the leaves it touches; leaves refine
+ * when their graded target is finer, families coarsen when all four graded
+ * targets are coarser), and remaps the field on the device (copy; Eq. ghost_fine
  * interpolation for new children; Eq. ghost_coarse averaging for new
  * parents).  *changed (host) receives the number of leaves created plus
  * removed.  Synchronous. */

@@ -49,6 +49,7 @@ class _Params(ctypes.Structure):
         ("vel_kind", ctypes.c_int), ("vel", ctypes.c_double * 4),
         ("order", ctypes.c_int), ("limiter", ctypes.c_int),
         ("transverse", ctypes.c_int), ("vel_scale", ctypes.c_double),
+        ("indicator", ctypes.c_int), ("smooth", ctypes.c_int),
     ]
 
 
@@ -114,7 +115,7 @@ def _check(rc: int):
 
 def params(domain: int, mx: int, mbc: int, lmin: int, lmax: int, velocity,
            order: int = 2, limiter: int = 1, transverse: int = 2,
-           nforests: int = 1) -> _Params:
+           nforests: int = 1, indicator: int = 0, smooth: int = 0) -> _Params:
     p = _Params()
     p.domain, p.nforests, p.mx, p.mbc, p.lmin, p.lmax = domain, nforests, mx, mbc, lmin, lmax
     if velocity[0] == "const":
@@ -131,6 +132,7 @@ def params(domain: int, mx: int, mbc: int, lmin: int, lmax: int, velocity,
         raise ValueError(velocity)
     p.order, p.limiter, p.transverse = order, limiter, transverse
     p.vel_scale = 1.0
+    p.indicator, p.smooth = indicator, smooth
     return p
 
 
@@ -297,11 +299,15 @@ _DOMAIN = {"walls": WALLS, "periodic": PERIODIC, "sphere": SPHERE}
 _LIMITER = {"none": (2, 0), "lw": (2, 0), "mc": (2, 1), "first": (1, 0)}
 
 
+_INDICATOR = {"gradient": 0, "maxmin": 1}
+
+
 def params_for(w, nforests: int = 1, lmax: Optional[int] = None) -> _Params:
     order, lim = _LIMITER[w.limiter]
     return params(_DOMAIN[w.domain], w.mx, w.mbc, w.lmin,
                   w.lmax if lmax is None else lmax, w.velocity, order=order,
-                  limiter=lim, transverse=w.transverse, nforests=nforests)
+                  limiter=lim, transverse=w.transverse, nforests=nforests,
+                  indicator=_INDICATOR[w.indicator], smooth=int(w.smooth))
 
 
 def initial_forest(workloads, lmax: Optional[int] = None) -> Forest:

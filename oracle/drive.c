@@ -74,6 +74,21 @@ int or_tag(or_forest* F, double* delta) {
   if (or_fill_all(F)) return -1;
   size_t S2 = (size_t)F->S * F->S;
   int mx = F->P.mx;
+  if (F->P.indicator == 1) {
+    /* Sec. 5.1: the spread of the patch's values, largest minus smallest */
+    for (int p = 0; p < F->n; ++p) {
+      const double* Q = F->q + p * S2;
+      double lo = Q[OR_IDX(F, 0, 0)], hi = lo;
+      for (int j = 0; j < mx; ++j)
+        for (int i = 0; i < mx; ++i) {
+          double v = Q[OR_IDX(F, i, j)];
+          if (v < lo) lo = v;
+          if (v > hi) hi = v;
+        }
+      delta[p] = hi - lo;
+    }
+    return 0;
+  }
   for (int p = 0; p < F->n; ++p) {
     const double* Q = F->q + p * S2;
     double m = 0.0;
@@ -155,7 +170,33 @@ int or_regrid(or_forest* F, double tau_r, double tau_c, const int* lmax_f, int* 
     int lm = lmax_f ? lmax_f[F->lv[p].f] : F->P.lmax;
     refine[p] = (delta[p] > tau_r) && (F->lv[p].l < lm);
   }
-  /* candidate families: four sibling leaves, none tagged to refine, all below tau_c */
+  /* Sec. 3.3 smooth grading: each leaf's target level (one finer if tagged to
+     refine, one coarser if below tau_c, else its own) is raised to the
+     largest target among the leaves it touches; a leaf refines when its
+     graded target is finer than it, and a family coarsens only when every
+     sibling's graded target is coarser */
+  int* target = NULL;
+  if (F->P.smooth) {
+    int* t0 = (int*)malloc(sizeof(int) * (size_t)(n > 0 ? n : 1));
+    target = (int*)malloc(sizeof(int) * (size_t)(n > 0 ? n : 1));
+    for (int p = 0; p < n; ++p) {
+      int l = F->lv[p].l;
+      t0[p] = refine[p] ? l + 1 : (delta[p] < tau_c && l > F->P.lmin) ? l - 1 : l;
+    }
+    for (int p = 0; p < n; ++p) {
+      int t = t0[p];
+      for (int q = 0; q < n; ++q)
+        if (q != p && t0[q] > t && or_touch(F, &F->lv[p], &F->lv[q])) t = t0[q];
+      target[p] = t;
+    }
+    for (int p = 0; p < n; ++p) {
+      int lm = lmax_f ? lmax_f[F->lv[p].f] : F->P.lmax;
+      refine[p] = target[p] > F->lv[p].l && F->lv[p].l < lm;
+    }
+    free(t0);
+  }
+  /* candidate families: four sibling leaves, none tagged to refine, all below
+     tau_c (graded: all four with a coarser target) */
   int* fam = (int*)malloc(sizeof(int) * 4 * (size_t)(n > 0 ? n : 1));
   int nfam = 0;
   for (int p = 0; p < n; ++p) {
@@ -164,7 +205,8 @@ int or_regrid(or_forest* F, double tau_r, double tau_c, const int* lmax_f, int* 
     int s[4], ok = 1;
     for (int c = 0; c < 4 && ok; ++c) {
       s[c] = or_find(F, a->f, a->b, a->l, a->x + (c & 1), a->y + (c >> 1));
-      if (s[c] < 0 || refine[s[c]] || !(delta[s[c]] < tau_c)) ok = 0;
+      if (s[c] < 0 || refine[s[c]]) ok = 0;
+      else if (target ? !(target[s[c]] < a->l) : !(delta[s[c]] < tau_c)) ok = 0;
     }
     if (!ok) continue;
     for (int c = 0; c < 4; ++c) fam[4 * nfam + c] = s[c];
@@ -294,6 +336,7 @@ int or_regrid(or_forest* F, double tau_r, double tau_c, const int* lmax_f, int* 
   free(gone);
   free(fam);
   free(refine);
+  free(target);
   free(delta);
   return status;
 }

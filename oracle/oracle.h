@@ -38,6 +38,8 @@ typedef struct {
   int limiter;     /* 0: unlimited (Lax-Wendroff), 1: MC */
   int transverse;  /* 0: none, 1: fluctuations, 2: fluctuations + corrections */
   double vel_scale; /* every edge speed is multiplied by this (0 is read as 1) */
+  int indicator;   /* regrid indicator: 0 max |grad q| / 2, 1 max q - min q (Sec. 5.1) */
+  int smooth;      /* 1: smooth grading of target levels before refining (Sec. 3.3) */
 } or_params;
 
 typedef struct or_forest or_forest;

@@ -28,6 +28,7 @@ class Desc(ctypes.Structure):
         ("vel", ctypes.c_double * 4),
         ("order", ctypes.c_int), ("limiter", ctypes.c_int),
         ("transverse", ctypes.c_int),
+        ("indicator", ctypes.c_int), ("smooth", ctypes.c_int),
     ]
 
 

@@ -23,12 +23,35 @@ namespace {
 // The square root is monotone, so it is taken once per patch, of the largest
 // squared difference: the same value, bit for bit, as the maximum of the
 // per-cell roots.
+// kind 1 (Sec. 5.1): the spread max q - min q of the interior instead, in
+// the field's precision (exact: a difference of two stored values).
 template <typename real>
-__global__ void tag_kernel(DevForest<real> D, double* delta) {
-  __shared__ real red[256];
+__global__ void tag_kernel(DevForest<real> D, int kind, double* delta) {
+  __shared__ real red[256], red2[256];
   const int mx = D.mx, S = D.S;
   for (int p = blockIdx.x; p < D.npatch; p += gridDim.x) {
     const real* Q = D.buf[D.cur[D.meta[p].level]] + (size_t)p * S * S;
+    if (kind == 1) {
+      real hi = Q[2 * S + 2], lo = hi;
+      for (int k = threadIdx.x; k < mx * mx; k += blockDim.x) {
+        const real v = Q[(k / mx + 2) * S + k % mx + 2];
+        hi = v > hi ? v : hi;
+        lo = v < lo ? v : lo;
+      }
+      red[threadIdx.x] = hi;
+      red2[threadIdx.x] = lo;
+      __syncthreads();
+      for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) {
+          if (red[threadIdx.x + w] > red[threadIdx.x]) red[threadIdx.x] = red[threadIdx.x + w];
+          if (red2[threadIdx.x + w] < red2[threadIdx.x]) red2[threadIdx.x] = red2[threadIdx.x + w];
+        }
+        __syncthreads();
+      }
+      if (threadIdx.x == 0) delta[p] = (double)red[0] - (double)red2[0];
+      __syncthreads();
+      continue;
+    }
     real m = real(0);
     for (int k = threadIdx.x; k < mx * mx; k += blockDim.x) {
       const int i = k % mx + 2, j = k / mx + 2;
@@ -183,9 +206,9 @@ inline int grid_for(int n) { return n < 1 ? 1 : (n < 65535 * 8 ? n : 65535 * 8);
 }  // namespace
 
 template <typename real>
-cudaError_t launch_tag(const DevForest<real>& D, double* delta, cudaStream_t s) {
+cudaError_t launch_tag(const DevForest<real>& D, int kind, double* delta, cudaStream_t s) {
   if (D.npatch <= 0) return cudaSuccess;
-  tag_kernel<real><<<grid_for(D.npatch), 256, 0, s>>>(D, delta);
+  tag_kernel<real><<<grid_for(D.npatch), 256, 0, s>>>(D, kind, delta);
   ++launch_counter();
   return cudaGetLastError();
 }
@@ -231,7 +254,7 @@ cudaError_t launch_remap(const DevForest<real>& Old, const DevForest<real>& New,
 }
 
 #define FC_INSTANTIATE(real)                                                                   \
-  template cudaError_t launch_tag<real>(const DevForest<real>&, double*, cudaStream_t);        \
+  template cudaError_t launch_tag<real>(const DevForest<real>&, int, double*, cudaStream_t);        \
   template cudaError_t launch_mass<real>(const DevForest<real>&, const int*, const int*, int, \
                                          double*, double*, cudaStream_t);                      \
   template cudaError_t launch_pack<real>(const DevForest<real>&, const int*, real*, int,      \

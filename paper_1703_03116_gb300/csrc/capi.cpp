@@ -722,6 +722,10 @@ fc_status check_desc(const fc_forest_desc* d) {
   if (d->order < 1 || d->order > 2 || d->limiter < 0 || d->limiter > 1 || d->transverse < 0 ||
       d->transverse > 2)
     return fail(FC_ERR_INVALID_ARG, "bad scheme options");
+  if (d->indicator < 0 || d->indicator > 1 || d->smooth < 0 || d->smooth > 1)
+    return fail(FC_ERR_INVALID_ARG, "bad regrid policy");
+  if (d->smooth && d->domain == FC_DOMAIN_SPHERE)
+    return fail(FC_ERR_INVALID_ARG, "smooth grading is built for the square domains");
   return FC_OK;
 }
 
@@ -1500,14 +1504,17 @@ fc_status fc_step_multirate(fc_forest* F, double t, double dt_coarse, void* stre
 fc_status fc_tag(fc_forest* F, double* delta_host, void* stream) {
   if (!F || !delta_host) return fail(FC_ERR_INVALID_ARG, "null argument");
   cudaStream_t s = as_stream(stream);
-  fc_status st = fill_all(F, s);
-  if (st != FC_OK) return st;
+  const int kind = F->host.desc.indicator;
+  if (kind == 0) {  // central differences read the first ghost layer
+    const fc_status st = fill_all(F, s);
+    if (st != FC_OK) return st;
+  }
   const int n = F->host.npatch();
   cudaError_t e;
   {
     Timed tm(F, 2, s, (double)n * F->host.desc.mx * F->host.desc.mx * F->esize);
-    e = F->esize == 4 ? launch_tag(dev<float>(F), F->d_delta, s)
-                      : launch_tag(dev<double>(F), F->d_delta, s);
+    e = F->esize == 4 ? launch_tag(dev<float>(F), kind, F->d_delta, s)
+                      : launch_tag(dev<double>(F), kind, F->d_delta, s);
   }
   if (e != cudaSuccess) return cuda_fail(e, "tag");
   std::vector<double> dd(n);

@@ -452,7 +452,7 @@ template <typename real>
 cudaError_t launch_advance(const DevForest<real>& D, int p0, int p1, const AdvArgs& a, int* err,
                            cudaStream_t s);
 template <typename real>
-cudaError_t launch_tag(const DevForest<real>& D, double* delta, cudaStream_t s);
+cudaError_t launch_tag(const DevForest<real>& D, int kind, double* delta, cudaStream_t s);
 template <typename real>
 cudaError_t launch_mass(const DevForest<real>& D, const int* api_to_dev, const int* fstart,
                         int nforests, double* patch_sums, double* out, cudaStream_t s);

@@ -575,6 +575,34 @@ void regrid_range(const HostForest& F, const std::vector<double>& delta, double 
     int lm = lmax_f.empty() ? d.lmax : std::min(lmax_f[a.f], d.lmax);
     refine[k] = (delta[k] > tau_r) && (a.l < lm);
   }
+  // Sec. 3.3 smooth grading: each leaf's target level (one finer if tagged
+  // to refine, one coarser if below tau_c, else its own) is raised to the
+  // largest target among the leaves it touches (the neighbour table's
+  // entries); a leaf refines when its graded target is finer, and a family
+  // coarsens only when all four graded targets are coarser
+  std::vector<int> target;
+  if (d.smooth) {
+    std::vector<int> t0(n, 0);
+    for (int k = k0; k < k1; ++k) {
+      const int l = F.leaves[k].l;
+      t0[k] = refine[k] ? l + 1 : (delta[k] < tau_c && l > d.lmin) ? l - 1 : l;
+    }
+    target.assign(n, 0);
+    for (int k = k0; k < k1; ++k) {
+      int t = t0[k];
+      const int p = F.dev_of[k];
+      for (int dir = 0; dir < 8; ++dir) {
+        const NbrEntry& e = F.nbr[(size_t)p * 8 + dir];
+        if (e.kind != NB_SAME && e.kind != NB_COARSE && e.kind != NB_FINE) continue;
+        for (const int id : {e.n0, e.n1})
+          if (id >= 0) t = std::max(t, t0[F.api_of[id]]);
+      }
+      target[k] = t;
+      const Leaf& a = F.leaves[k];
+      const int lm = lmax_f.empty() ? d.lmax : std::min(lmax_f[a.f], d.lmax);
+      refine[k] = t > a.l && a.l < lm;
+    }
+  }
   std::vector<Leaf> parents;
   for (int k = k0; k < k1; ++k) {
     const Leaf& a = F.leaves[k];
@@ -582,7 +610,8 @@ void regrid_range(const HostForest& F, const std::vector<double>& delta, double 
     bool ok = true;
     for (int c = 0; c < 4 && ok; ++c) {
       int s = F.find(a.f, a.b, a.l, a.x + (c & 1), a.y + (c >> 1));
-      if (s < 0 || refine[s] || !(delta[s] < tau_c)) ok = false;
+      if (s < 0 || refine[s]) ok = false;
+      else if (d.smooth ? !(target[s] < a.l) : !(delta[s] < tau_c)) ok = false;
     }
     if (ok) parents.push_back(Leaf{a.f, a.b, a.l - 1, a.x / 2, a.y / 2});
   }

@@ -76,6 +76,8 @@ class Workload:
     tau_refine: float = 0.05
     tau_coarsen: float = 0.0125
     seed: int = 0
+    indicator: str = "gradient"  # regrid indicator: "gradient" | "maxmin" (Sec. 5.1)
+    smooth: bool = False         # smooth grading of the target levels (Sec. 3.3)
 
 
 def _rng(seed: int) -> np.random.Generator:

@@ -13,7 +13,9 @@ def desc_for(fc, w, dtype, nforests=1, lmax=None):
     return fc.make_desc(domain=domain, mx=w.mx,
                         lmin=w.lmin, lmax=w.lmax if lmax is None else lmax, dtype=dtype,
                         velocity=w.velocity, order=order, limiter=lim,
-                        transverse=w.transverse, nforests=nforests)
+                        transverse=w.transverse, nforests=nforests,
+                        indicator={"gradient": 0, "maxmin": 1}[w.indicator],
+                        smooth=int(w.smooth))
 
 
 def pair(fc, workloads, dtype):

@@ -137,6 +137,27 @@ def test_tag_in_single_precision_matches_oracle():
         np.min(np.abs(t_ref - w.tau_refine)) < 1e-4 * np.abs(t_ref).max()
 
 
+@pytest.mark.parametrize("domain", ["walls", "periodic"])
+def test_graded_spread_regrid_matches_oracle(domain):
+    """The paper's regrid policy on the device (spread indicator, Sec. 5.1;
+    smooth grading, Sec. 3.3): the same indicators as the oracle, the same
+    layouts, and stepping continues alike, over three regrids."""
+    w = synth.swirl(2, lmin=2, lmax=5, mx=16)
+    w.domain, w.indicator, w.smooth = domain, "maxmin", True
+    ref, gpu = pair(fc, w, fc.F64)
+    _, dtc = synth.time_step(w)
+    for n in range(6):
+        ref.step_multirate(n * dtc, dtc)
+        gpu.step_multirate(n * dtc, dtc)
+        if n % 2 == 1:
+            np.testing.assert_allclose(gpu.tag(), ref.tag(), rtol=1e-12, atol=1e-14)
+            c_ref = ref.regrid(0.3, 0.02)
+            c_gpu = gpu.tag_regrid(0.3, 0.02)
+            assert c_gpu == c_ref
+            np.testing.assert_array_equal(gpu.leaves(), ref.leaves())
+    assert relerr(gpu.get_q(), ref.get_q()) <= F64_TOL
+
+
 def test_mass_matches_oracle():
     w = synth.swirl(0, lmin=2, lmax=5, mx=16)
     ref, gpu = pair(fc, w, fc.F64)

@@ -172,6 +172,48 @@ def test_regrid_layout_matches_oracle(seed, taus):
     assert np.array_equal(got, F.leaves())
 
 
+@pytest.mark.parametrize("seed", range(3))
+@pytest.mark.parametrize("domain", ["walls", "periodic"])
+@pytest.mark.parametrize("taus", [(0.3, 0.05), (0.6, 0.2)])
+def test_graded_regrid_layout_matches_oracle(seed, domain, taus):
+    """The paper's policy (spread indicator, smooth grading) on the host
+    against the oracle's: the same leaves, in the same order."""
+    w = synth.swirl(seed, lmin=2, lmax=5, mx=8)
+    w.domain, w.indicator, w.smooth = domain, "maxmin", True
+    F = oracle.initial_forest(w)
+    lv = F.leaves()
+    F.set_q(synth.random_field((len(lv), 8, 8), seed=seed) ** 3)
+    delta = F.tag()
+    d = desc_for(w)
+    d.indicator, d.smooth = 1, 1
+    got = fc.layout_regrid(d, lv, delta, *taus)
+    F.regrid(*taus)
+    assert np.array_equal(got, F.leaves())
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_graded_regrid_of_a_moved_disc_matches_oracle(seed):
+    """Refinement and coarsening together: the disc moves off the layout
+    adapted to it, so grading both adds a ring of refinement and holds back
+    coarsening next to it."""
+    w = synth.swirl(seed, lmin=2, lmax=5, mx=8)
+    w.indicator, w.smooth = "maxmin", True
+    F = oracle.initial_forest(w)
+    lv = F.leaves()
+    x, y = synth.cell_centres(lv, 8)
+    F.set_q(synth.evaluate(synth.adjoint_target(w, seed=seed, max_shift=0.15), x, y))
+    delta = F.tag()
+    d = desc_for(w)
+    d.indicator, d.smooth = 1, 1
+    got = fc.layout_regrid(d, lv, delta, 0.5, 0.01)
+    n_before = len(lv)
+    F.regrid(0.5, 0.01)
+    ref = F.leaves()
+    assert np.array_equal(got, ref)
+    parents = {tuple(r) for r in ref} - {tuple(r) for r in lv}
+    assert any(r[2] < lv[:, 2].max() for r in ref) and len(parents) > 0 and n_before > 0
+
+
 def test_regrid_layout_batched_forests_matches_oracle():
     ws = synth.ensemble(5, seed=3, lmin=2, mx=8, levels=(3, 4, 5))
     F = oracle.initial_forest(ws)
