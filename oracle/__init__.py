@@ -50,6 +50,7 @@ class _Params(ctypes.Structure):
         ("order", ctypes.c_int), ("limiter", ctypes.c_int),
         ("transverse", ctypes.c_int), ("vel_scale", ctypes.c_double),
         ("indicator", ctypes.c_int), ("smooth", ctypes.c_int),
+        ("reflux", ctypes.c_int),
     ]
 
 
@@ -115,7 +116,8 @@ def _check(rc: int):
 
 def params(domain: int, mx: int, mbc: int, lmin: int, lmax: int, velocity,
            order: int = 2, limiter: int = 1, transverse: int = 2,
-           nforests: int = 1, indicator: int = 0, smooth: int = 0) -> _Params:
+           nforests: int = 1, indicator: int = 0, smooth: int = 0,
+           reflux: int = 0) -> _Params:
     p = _Params()
     p.domain, p.nforests, p.mx, p.mbc, p.lmin, p.lmax = domain, nforests, mx, mbc, lmin, lmax
     if velocity[0] == "const":
@@ -132,7 +134,7 @@ def params(domain: int, mx: int, mbc: int, lmin: int, lmax: int, velocity,
         raise ValueError(velocity)
     p.order, p.limiter, p.transverse = order, limiter, transverse
     p.vel_scale = 1.0
-    p.indicator, p.smooth = indicator, smooth
+    p.indicator, p.smooth, p.reflux = indicator, smooth, reflux
     return p
 
 
@@ -307,7 +309,8 @@ def params_for(w, nforests: int = 1, lmax: Optional[int] = None) -> _Params:
     return params(_DOMAIN[w.domain], w.mx, w.mbc, w.lmin,
                   w.lmax if lmax is None else lmax, w.velocity, order=order,
                   limiter=lim, transverse=w.transverse, nforests=nforests,
-                  indicator=_INDICATOR[w.indicator], smooth=int(w.smooth))
+                  indicator=_INDICATOR[w.indicator], smooth=int(w.smooth),
+                  reflux=int(w.reflux))
 
 
 def initial_forest(workloads, lmax: Optional[int] = None) -> Forest:

@@ -314,6 +314,10 @@ static void fill_reverse(or_forest* F, double* L, const double* snap) {
 static double scale_of(const or_params* P) { return P->vel_scale != 0.0 ? P->vel_scale : 1.0; }
 
 int or_adjoint_step_global(or_forest* F, double t, double dt, double* lam, double* dscale) {
+  if (F->P.reflux) {
+    or_set_error("the adjoint is stated without refluxing");
+    return -1;
+  }
   size_t S2 = (size_t)F->S * F->S;
   int mx = F->P.mx;
   double* snap = (double*)malloc(sizeof(double) * S2 * (size_t)(F->n > 0 ? F->n : 1));
@@ -494,6 +498,10 @@ int or_adjoint_step_multirate(or_forest* F, double t, double dt_coarse, double* 
                               double* dscale) {
   if (F->P.domain == OR_SPHERE) {
     or_set_error("the adjoint is stated for the square domains");
+    return -1;
+  }
+  if (F->P.reflux) {
+    or_set_error("the adjoint is stated without refluxing");
     return -1;
   }
   size_t S2 = (size_t)F->S * F->S, nS = S2 * (size_t)(F->n > 0 ? F->n : 1);

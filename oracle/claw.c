@@ -105,6 +105,11 @@ static double correction(const or_params* P, double s, double W, double Wup, dou
 
 void or_claw_step(const or_params* P, double* q, int mx, int mbc, double h, double dt,
                   double t, long gx0, long gy0) {
+  or_claw_step_flux(P, q, mx, mbc, h, dt, t, gx0, gy0, NULL);
+}
+
+void or_claw_step_flux(const or_params* P, double* q, int mx, int mbc, double h, double dt,
+                       double t, long gx0, long gy0, double* bflux) {
   int S = mx + 2 * mbc;
   int SE = S + 1;
   double nu = dt / h;
@@ -154,6 +159,14 @@ void or_claw_step(const or_params* P, double* q, int mx, int mbc, double h, doub
         FX(i + 1, j - 1) -= 0.5 * nu * pos(u_edge(&c, i + 1, j - 1)) * Mf;
         FX(i, j - 1) -= 0.5 * nu * neg(u_edge(&c, i, j - 1)) * Mf;
       }
+    }
+  /* the fluxes through the patch's faces, as the update below uses them */
+  if (bflux)
+    for (int k = 0; k < mx; ++k) {
+      bflux[k] = FX(0, k);
+      bflux[mx + k] = FX(mx, k);
+      bflux[2 * mx + k] = GY(k, 0);
+      bflux[3 * mx + k] = GY(k, mx);
     }
   /* conservative update of the interior */
   for (int j = 0; j < mx; ++j)

@@ -39,34 +39,123 @@ void or_advance_leaf(or_forest* F, int p, double t, double dt) {
                           F->phix + p * (S + 1) * S, F->phiy + p * S * (S + 1));
     return;
   }
-  or_claw_step(&F->P, F->q + p * S2, F->P.mx, F->P.mbc, cell_h(F, a->l), dt, t,
-               (long)a->x * F->P.mx, (long)a->y * F->P.mx);
+  double* bf = (F->P.reflux && F->bflux) ? F->bflux + ((size_t)p * 2 + F->fslot) * 4 * F->P.mx
+                                          : NULL;
+  or_claw_step_flux(&F->P, F->q + p * S2, F->P.mx, F->P.mbc, cell_h(F, a->l), dt, t,
+                    (long)a->x * F->P.mx, (long)a->y * F->P.mx, bf);
+}
+
+/* the face-flux store of the current leaves (refluxing) */
+static void flux_store(or_forest* F) {
+  if (!F->P.reflux || (F->bflux && F->nbflux == F->n)) return;
+  free(F->bflux);
+  size_t m = (size_t)(F->n > 0 ? F->n : 1) * 2 * 4 * F->P.mx;
+  F->bflux = (double*)malloc(sizeof(double) * m);
+  for (size_t c = 0; c < m; ++c) F->bflux[c] = NAN;
+  F->nbflux = F->n;
+}
+
+/*
+ * Refluxing of level L (Berger and Colella's correction; the paper's scheme
+ * has none).  Over one level-L update of length dt, a coarse cell next to a
+ * face whose other side is finer took the flux Fc that its own update
+ * computed; mass leaves the fine side through the same face by the fine
+ * fluxes, time dt_f over faces of length h/2 each.  The coarse cell exchanges
+ * Fc for the fine fluxes' average Fbar = w * sum over the face's two fine cells
+ * and the fine substeps (w = 1/4 with two substeps of dt/2, 1/2 with one
+ * substep of dt), by q += (dt/h) (Fc - Fbar) on a face in +x or +y and
+ * q += (dt/h) (Fbar - Fc) on a face in -x or -y.  The fine neighbours are
+ * found by locating the centres of the fine cells across the face.  Faces are
+ * corrected in the order -x, +x, -y, +y (a corner cell takes two).
+ */
+static void reflux_level(or_forest* F, int L, double dt, int cslot, int nfs, double w) {
+  const int mx = F->P.mx;
+  const size_t S2 = (size_t)F->S * F->S, fs = 4 * (size_t)mx;
+  const double h = cell_h(F, L), nu = dt / h;
+  for (int p = 0; p < F->n; ++p) {
+    const or_leaf* a = &F->lv[p];
+    if (a->l != L) continue;
+    double* Q = F->q + p * S2;
+    const double x0 = a->x * mx * h, y0 = a->y * mx * h, x1 = x0 + mx * h, y1 = y0 + mx * h;
+    for (int dir = 0; dir < 4; ++dir)
+      for (int k = 0; k < mx; ++k) {
+        /* the centres of the two fine cells across the face from coarse cell k */
+        double px[2], py[2];
+        for (int c = 0; c < 2; ++c) {
+          double along = (k + 0.25 + 0.5 * c) * h;
+          if (dir < 2) {
+            px[c] = dir == 0 ? x0 - 0.25 * h : x1 + 0.25 * h;
+            py[c] = y0 + along;
+          } else {
+            px[c] = x0 + along;
+            py[c] = dir == 2 ? y0 - 0.25 * h : y1 + 0.25 * h;
+          }
+        }
+        double fsum = 0.0;
+        int ok = 1;
+        double pair[2][2];
+        for (int c = 0; c < 2 && ok; ++c) {
+          int b = a->b;
+          double x = px[c], y = py[c];
+          int pf = or_locate(F, a->f, &b, &x, &y);
+          if (pf < 0 || F->lv[pf].l != L + 1) {
+            ok = 0;
+            break;
+          }
+          const or_leaf* fl = &F->lv[pf];
+          double hf = 0.5 * h;
+          int jf = dir < 2 ? (int)floor(y / hf) - fl->y * mx : (int)floor(x / hf) - fl->x * mx;
+          int ff = dir ^ 1; /* the fine leaf's face on the shared edge */
+          for (int s = 0; s < nfs; ++s)
+            pair[s][c] = F->bflux[((size_t)pf * 2 + s) * fs + (size_t)ff * mx + jf];
+        }
+        if (!ok) continue;
+        for (int s = 0; s < nfs; ++s) fsum += pair[s][0] + pair[s][1];
+        const double Fbar = w * fsum;
+        const double Fc = F->bflux[((size_t)p * 2 + cslot) * fs + (size_t)dir * mx + k];
+        int i = dir == 0 ? 0 : dir == 1 ? mx - 1 : k;
+        int j = dir == 2 ? 0 : dir == 3 ? mx - 1 : k;
+        if (dir == 0 || dir == 2)
+          Q[OR_IDX(F, i, j)] += nu * (Fbar - Fc);
+        else
+          Q[OR_IDX(F, i, j)] += nu * (Fc - Fbar);
+      }
+  }
 }
 
 int or_fill_ghosts(or_forest* F) { return or_fill_all(F); }
 
 int or_step_global(or_forest* F, double t, double dt) {
   if (or_fill_all(F)) return -1;
+  flux_store(F);
+  F->fslot = 0;
   for (int p = 0; p < F->n; ++p) or_advance_leaf(F, p, t, dt);
+  if (F->P.reflux) /* every level took one step of dt: one fine substep */
+    for (int L = F->P.lmin; L < F->P.lmax; ++L) reflux_level(F, L, dt, 0, 1, 0.5);
   return 0;
 }
 
 static int mr_level(or_forest* F, int L, double t, double dt, double alpha) {
   size_t S2 = (size_t)F->S * F->S;
   if (or_fill_level(F, L, alpha)) return -1;
+  const int slot = alpha != 0.0; /* the second substep of a pair */
   for (int p = 0; p < F->n; ++p)
     if (F->lv[p].l == L) {
       memcpy(F->qold + p * S2, F->q + p * S2, sizeof(double) * S2);
+      F->fslot = slot;
       or_advance_leaf(F, p, t, dt);
     }
   if (L < F->P.lmax) {
     if (mr_level(F, L + 1, t, 0.5 * dt, 0.0)) return -1;
     if (mr_level(F, L + 1, t + 0.5 * dt, 0.5 * dt, 0.5)) return -1;
+    /* both fine substeps of this step are done: two slots of dt/2 */
+    if (F->P.reflux) reflux_level(F, L, dt, slot, 2, 0.25);
   }
   return 0;
 }
 
 int or_step_multirate(or_forest* F, double t, double dt_coarse) {
+  flux_store(F);
   return mr_level(F, F->P.lmin, t, dt_coarse, 0.0);
 }
 

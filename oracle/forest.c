@@ -145,6 +145,10 @@ or_forest* or_create(const or_params* P, int n, const int* leaves) {
     or_set_error("bad level range");
     return NULL;
   }
+  if (P->domain == OR_SPHERE && P->reflux) {
+    or_set_error("refluxing is built for the square domains");
+    return NULL;
+  }
   if (P->domain == OR_SPHERE && P->vel_kind != OR_VEL_ROTATION) {
     or_set_error("the sphere takes the solid-body rotation velocity");
     return NULL;
@@ -193,6 +197,7 @@ void or_destroy(or_forest* F) {
   free(F->kappa);
   free(F->phix);
   free(F->phiy);
+  free(F->bflux);
   free(F->lv);
   free(F->byKey);
   free(F->q);

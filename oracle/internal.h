@@ -23,6 +23,11 @@ struct or_forest {
   double* kappa;     /* n * S * S cell capacities (spherical areas) */
   double* phix;      /* n * (S+1) * S x-edge volume fluxes */
   double* phiy;      /* n * S * (S+1) y-edge volume fluxes */
+  /* refluxing: per leaf, two substep slots of the final fluxes through its
+   * four faces ([slot][face][cell], faces -x, +x, -y, +y, mx cells each) */
+  double* bflux;
+  int nbflux;        /* leaves bflux is sized for */
+  int fslot;         /* the slot the next leaf update writes */
 };
 
 /* sphere.c */
@@ -59,6 +64,11 @@ int or_touch(const or_forest* F, const or_leaf* a, const or_leaf* c);
 /* claw.c */
 void or_claw_step(const or_params* P, double* q, int mx, int mbc, double h,
                   double dt, double t, long gx0, long gy0);
+/* as or_claw_step; bflux (4 mx, may be NULL) receives the final fluxes through
+ * the patch's faces: F at x-edges 0 and mx of each row, then G at y-edges 0
+ * and mx of each column */
+void or_claw_step_flux(const or_params* P, double* q, int mx, int mbc, double h, double dt,
+                       double t, long gx0, long gy0, double* bflux);
 /* edge speeds at velocity time t (the half step of the step using them) */
 double or_u_edge(const or_params* P, double h, double t, long gx0, long gy0, int i, int j);
 double or_v_edge(const or_params* P, double h, double t, long gx0, long gy0, int i, int j);

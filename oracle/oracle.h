@@ -11,6 +11,12 @@
  * the leaf set for the quadrant that contains its centre (Sec. 2.2 "Ghost
  * regions"), instead of using a precomputed neighbour list.
  *
+ * Refluxing (or_params.reflux) is not in the paper: it is the standard
+ * correction of Berger and Colella (J. Comput. Phys. 82, 1989), which replaces
+ * the flux a coarse cell used at a coarse/fine face by the fine fluxes through
+ * that face, summed over the face's fine cells and the fine substeps.  Pinned
+ * by first-order closed forms and by exact conservation of mass.
+ *
  * Parity unpinned (checked only against the same stated reading): the
  * multirate time interpolation of coarse data, the fill of the corner ghost
  * block at three-valent cube corners, and the capacity form on the sphere.
@@ -40,6 +46,8 @@ typedef struct {
   double vel_scale; /* every edge speed is multiplied by this (0 is read as 1) */
   int indicator;   /* regrid indicator: 0 max |grad q| / 2, 1 max q - min q (Sec. 5.1) */
   int smooth;      /* 1: smooth grading of target levels before refining (Sec. 3.3) */
+  int reflux;      /* 1: conservative correction of coarse cells at coarse/fine faces (square
+                      domains; an extension: the paper's scheme has none) */
 } or_params;
 
 typedef struct or_forest or_forest;

@@ -78,6 +78,7 @@ class Workload:
     seed: int = 0
     indicator: str = "gradient"  # regrid indicator: "gradient" | "maxmin" (Sec. 5.1)
     smooth: bool = False         # smooth grading of the target levels (Sec. 3.3)
+    reflux: bool = False         # conservative coarse/fine correction (off in the paper)
 
 
 def _rng(seed: int) -> np.random.Generator:
