@@ -77,7 +77,9 @@ typedef enum { FC_VEL_CONST = 0, FC_VEL_SWIRL = 1, FC_VEL_ROTATION = 2 } fc_velo
  *               two edge ghosts next to them.
  *   order       1 (first order) or 2 (second-order wave corrections).
  *   limiter     0 unlimited, 1 MC.
- *   transverse  0 none, 1 fluctuations, 2 fluctuations and corrections. */
+ *   transverse  0 none, 1 fluctuations, 2 fluctuations and corrections.
+ *   reflux      0 (the paper's scheme) or 1: conservative correction at
+ *               coarse/fine faces (square domains; see fc_step_multirate). */
 typedef struct {
   int domain;
   int nforests;
@@ -91,6 +93,7 @@ typedef struct {
   int transverse;
   int indicator;  /* regrid indicator: 0 max |grad q| / 2, 1 max q - min q (Sec. 5.1) */
   int smooth;     /* 1: smooth grading of the target levels (Sec. 3.3; square domains) */
+  int reflux;     /* 1: refluxing at coarse/fine faces (an extension; square domains) */
 } fc_forest_desc;
 
 /* Create a forest from an explicit leaf list (Sec. 2: quadrants identified
@@ -135,7 +138,18 @@ fc_status fc_advance_level(fc_forest* forest, int level, double t, double dt, vo
 fc_status fc_step_global(fc_forest* forest, double t, double dt, void* stream);
 
 /* One coarse multirate step: the coarse-first recursion of fc_advance_level
- * over all levels, 2^(lmax-lmin) substeps of the finest level. */
+ * over all levels, 2^(lmax-lmin) substeps of the finest level.
+ * With desc.reflux = 1 (not in the paper: Berger and Colella's refluxing),
+ * every level substep also records the final fluxes through its patches'
+ * faces, and after the two finer substeps that follow a level-l substep of
+ * length dt, each level-l cell next to a finer face exchanges the flux its
+ * update used, Fc, for the fine fluxes' mean Fbar = 1/4 (sum over the face's
+ * two fine cells and the two fine substeps): q += (dt/h)(Fc - Fbar) on a +x
+ * or +y face, q += (dt/h)(Fbar - Fc) on a -x or -y face, faces in the order
+ * -x, +x, -y, +y.  Total mass is then conserved to rounding.  (In
+ * fc_step_global the weight is 1/2: one fine step of the same dt.)  Every
+ * update runs the staged variant then; fc_advance_level records the fluxes
+ * but corrects nothing. */
 fc_status fc_step_multirate(fc_forest* forest, double t, double dt_coarse, void* stream);
 
 /* Tag and regrid (Sec. 3.1).  Fills ghosts, computes on the device the

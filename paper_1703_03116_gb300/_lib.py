@@ -29,6 +29,7 @@ class Desc(ctypes.Structure):
         ("order", ctypes.c_int), ("limiter", ctypes.c_int),
         ("transverse", ctypes.c_int),
         ("indicator", ctypes.c_int), ("smooth", ctypes.c_int),
+        ("reflux", ctypes.c_int),
     ]
 
 

@@ -246,6 +246,13 @@ __global__ void __launch_bounds__(NT, NT >= 512 ? (sizeof(real) == 4 ? 3 : 2)
       }
       __syncthreads();
     }
+    if (a.bflux) {  // refluxing: the final fluxes through the patch's faces
+      real* bf = static_cast<real*>(a.bflux) + ((size_t)p * 2 + a.bslot) * 4 * MX;
+      for (int k = threadIdx.x; k < 4 * MX; k += NT) {
+        const int f = k / MX, c = k % MX;
+        bf[k] = f == 0 ? Fn[xe(0, c)] : f == 1 ? Fn[xe(MX, c)] : f == 2 ? Gn[ye(c, 0)] : Gn[ye(c, MX)];
+      }
+    }
     for (int k = threadIdx.x; k < MX * MX; k += NT) {
       const int i = k % MX, j = k / MX;
       real v;
@@ -307,8 +314,9 @@ template <typename real>
 cudaError_t launch_advance(const DevForest<real>& D, int p0, int p1, const AdvArgs& a, int* err,
                            cudaStream_t s) {
   if (p1 <= p0) return cudaSuccess;
-  // the walk variant has no capacity form: mapped grids always run staged
-  if ((a.variant == ADV_WALK || a.variant == ADV_WALK1) && !D.metric)
+  // the walk variant has no capacity form and records no face fluxes:
+  // mapped grids and refluxing always run staged
+  if ((a.variant == ADV_WALK || a.variant == ADV_WALK1) && !D.metric && !a.bflux)
     return launch_advance_walk(D, p0, p1, a, err, s);
   return launch_advance_staged(D, p0, p1, a, err, s);
 }

@@ -203,7 +203,71 @@ __global__ void remap_kernel(DevForest<real> Old, DevForest<real> New, const Rem
 
 inline int grid_for(int n) { return n < 1 ? 1 : (n < 65535 * 8 ? n : 65535 * 8); }
 
+// Refluxing (Berger and Colella's correction; the paper's scheme has none):
+// one warp per level-L patch, lane k on face cell k.  A face whose other side
+// is finer (an NB_FINE face entry: n0 holds the half of the face at cells
+// 0..MX/2-1, n1 the other half, the square domains' identity orientation)
+// gives coarse cell k the fine fluxes of fine cells 2k - half*MX and the next
+// through the fine patch's opposite face, summed over nfs substep slots and
+// scaled by w, in place of its own flux Fc of slot cslot.  The faces go one
+// after the other (-x, +x, -y, +y): a corner cell takes two corrections, from
+// two lanes, ordered by the warp barrier between faces.
+template <typename real, int MX>
+__global__ void reflux_kernel(DevForest<real> D, int p0, int p1, const real* __restrict__ bflux,
+                              int cslot, int nfs, real w, real nu) {
+  const int lane = threadIdx.x & 31;
+  const int p = p0 + blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (p >= p1) return;  // whole warps leave together
+  real* Q = D.buf[D.cur[D.meta[p].level]] + (size_t)p * D.S * D.S;
+  for (int dir = 0; dir < 4; ++dir) {
+    const NbrEntry& e = D.nbr[(size_t)p * 8 + dir];
+    if (e.kind == NB_FINE && lane < MX) {
+      const int k = lane, half = k >= MX / 2 ? 1 : 0;
+      const int n = half ? e.n1 : e.n0;
+      const int jf = 2 * k - half * MX;
+      const int ff = dir ^ 1;  // the fine patch's face on the shared edge
+      real acc = real(0);
+      for (int s = 0; s < nfs; ++s) {
+        const real* b = bflux + (((size_t)n * 2 + s) * 4 + ff) * MX + jf;
+        acc += b[0] + b[1];
+      }
+      const real Fbar = w * acc;
+      const real Fc = bflux[(((size_t)p * 2 + cslot) * 4 + dir) * MX + k];
+      const int i = dir == 0 ? 0 : (dir == 1 ? MX - 1 : k);
+      const int j = dir == 2 ? 0 : (dir == 3 ? MX - 1 : k);
+      real* c = Q + (size_t)(j + kMbc) * D.S + (i + kMbc);
+      *c = (dir == 0 || dir == 2) ? *c + nu * (Fbar - Fc) : *c + nu * (Fc - Fbar);
+    }
+    __syncwarp();
+  }
+}
+
 }  // namespace
+
+template <typename real>
+cudaError_t launch_reflux(const DevForest<real>& D, int p0, int p1, const real* bflux, int cslot,
+                          int nfs, double w, double nu, cudaStream_t s) {
+  if (p1 <= p0) return cudaSuccess;
+  constexpr int kWarps = 4;
+  const int grid = (p1 - p0 + kWarps - 1) / kWarps;
+  switch (D.mx) {
+    case 8:
+      reflux_kernel<real, 8><<<grid, 32 * kWarps, 0, s>>>(D, p0, p1, bflux, cslot, nfs, real(w),
+                                                           real(nu));
+      break;
+    case 16:
+      reflux_kernel<real, 16><<<grid, 32 * kWarps, 0, s>>>(D, p0, p1, bflux, cslot, nfs, real(w),
+                                                            real(nu));
+      break;
+    case 32:
+      reflux_kernel<real, 32><<<grid, 32 * kWarps, 0, s>>>(D, p0, p1, bflux, cslot, nfs, real(w),
+                                                            real(nu));
+      break;
+    default: return cudaErrorInvalidValue;
+  }
+  ++launch_counter();
+  return cudaGetLastError();
+}
 
 template <typename real>
 cudaError_t launch_tag(const DevForest<real>& D, int kind, double* delta, cudaStream_t s) {
@@ -255,6 +319,8 @@ cudaError_t launch_remap(const DevForest<real>& Old, const DevForest<real>& New,
 
 #define FC_INSTANTIATE(real)                                                                   \
   template cudaError_t launch_tag<real>(const DevForest<real>&, int, double*, cudaStream_t);        \
+  template cudaError_t launch_reflux<real>(const DevForest<real>&, int, int, const real*, int, int, \
+                                           double, double, cudaStream_t);                          \
   template cudaError_t launch_mass<real>(const DevForest<real>&, const int*, const int*, int, \
                                          double*, double*, cudaStream_t);                      \
   template cudaError_t launch_pack<real>(const DevForest<real>&, const int*, real*, int,      \

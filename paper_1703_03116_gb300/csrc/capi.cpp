@@ -86,6 +86,11 @@ struct fc_forest {
   void* buf[2] = {nullptr, nullptr};
   void* qT = nullptr;
   void* stage = nullptr;  // device staging for host copies
+  // refluxing (desc.reflux): per patch, two substep slots of the final fluxes
+  // through its four faces (field precision), and the slot each level's
+  // latest update wrote
+  void* bflux = nullptr;
+  int bslot[kMaxLevel + 1] = {};
   // the layout's small tables and per-patch scratch share one allocation
   // (d_tables, filled by one copy): d_meta, d_lists, d_api_to_dev, d_fstart,
   // d_patch_sums, d_mass and d_delta point into it
@@ -314,6 +319,7 @@ void free_device(fc_forest* F) {
   dfree(F->buf[1]);
   dfree(F->qT);
   dfree(F->stage);
+  dfree(F->bflux);
   free_tables(F);
   dfree(F->d_remap);
   dfree(F->d_err);
@@ -368,6 +374,13 @@ fc_status upload(fc_forest* F, bool alloc_store, bool metrics = true) {
         dmalloc_bytes(&F->stage, std::max<size_t>(cells, 1) * F->esize) != cudaSuccess)
       return fail(FC_ERR_OOM, "device store allocation failed");
     FC_CUDA(cudaMemsetAsync(F->qT, 0, std::max<size_t>(cells, 1) * F->esize, g_alloc_stream));
+    dfree(F->bflux);
+    if (H.desc.reflux) {
+      const size_t nb = (size_t)std::max(n, 1) * 2 * 4 * H.desc.mx * F->esize;
+      if (dmalloc_bytes(&F->bflux, nb) != cudaSuccess)
+        return fail(FC_ERR_OOM, "device flux store allocation failed");
+      FC_CUDA(cudaMemsetAsync(F->bflux, 0, nb, g_alloc_stream));
+    }
   }
   free_tables(F);
   // every work list, concatenated
@@ -477,6 +490,8 @@ AdvArgs adv_args(const fc_forest* F, int L, double t, double dt, int n) {
   a.gather = 0;
   a.tlevel = -1;
   a.alpha = 0.0;
+  a.bflux = F->bflux;
+  a.bslot = 0;
   choose_variant(F, n, &a);
   return a;
 }
@@ -490,6 +505,11 @@ int size_bucket(int n) {
 // the patch-update configuration for a launch of n patches: the autotuned
 // choice when this size was tuned, else walk for launches that fill the GPU
 void choose_variant(const fc_forest* F, int n, AdvArgs* a) {
+  if (F->bflux) {  // only the staged update records the face fluxes
+    a->variant = ADV_STAGED;
+    a->warps = 4;
+    return;
+  }
   if (F->forced_variant >= 0) {
     a->variant = F->forced_variant;
     a->warps = F->forced_warps;
@@ -653,6 +673,8 @@ fc_status advance_level_t(fc_forest* F, int L, double t, double dt, cudaStream_t
     }
     a.keep = F->keep_tiles;
     a.keep_p0 = p0;
+    a.bslot = alpha != 0.0 ? 1 : 0;  // the second substep of a pair
+    F->bslot[L] = a.bslot;
     // the update reads the finer level at this time: after its latest update
     if (lev && fused && L < H.desc.lmax && F->post_ok[L + 1])
       FC_CUDA(cudaStreamWaitEvent(s, F->ev_post[L + 1], 0));
@@ -681,12 +703,44 @@ fc_status advance_level(fc_forest* F, int L, double t, double dt, cudaStream_t s
                        : advance_level_t<double>(F, L, t, dt, s);
 }
 
+// refluxing of level L after one of its updates of length dt: with nfs
+// finer substeps of weight w (see fc_step_multirate)
+fc_status reflux_level(fc_forest* F, int L, double dt, int nfs, double w, cudaStream_t s) {
+  const HostForest& H = F->host;
+  const int p0 = H.lev_start[L], p1 = H.lev_start[L + 1];
+  if (!F->bflux || p1 <= p0 || L >= H.desc.lmax || H.lev_start[L + 2] <= p1) return FC_OK;
+  const double nu = dt / (std::ldexp(1.0, -L) / H.desc.mx);
+  Timed tm(F, 3, s, 0.0);
+  const cudaError_t e =
+      F->esize == 4 ? launch_reflux(dev<float>(F), p0, p1, static_cast<const float*>(F->bflux),
+                                    F->bslot[L], nfs, w, nu, s)
+                    : launch_reflux(dev<double>(F), p0, p1, static_cast<const double*>(F->bflux),
+                                    F->bslot[L], nfs, w, nu, s);
+  return e == cudaSuccess ? FC_OK : cuda_fail(e, "reflux");
+}
+
 fc_status multirate(fc_forest* F, int L, double t, double dt, cudaStream_t s) {
   fc_status st = advance_level(F, L, t, dt, s);
   if (st != FC_OK) return st;
   if (L < F->host.desc.lmax) {
     if ((st = multirate(F, L + 1, t, 0.5 * dt, s)) != FC_OK) return st;
     if ((st = multirate(F, L + 1, t + 0.5 * dt, 0.5 * dt, s)) != FC_OK) return st;
+    const HostForest& H = F->host;
+    if (F->bflux && H.lev_start[L + 1] > H.lev_start[L]) {
+      // after both finer substeps (their fluxes written, their reads of this
+      // level's states done); on a captured step's level stream, and the
+      // level's post-update event moves past the correction (what the
+      // coarser level and this level's next substep read)
+      if (F->dag_levels) {
+        s = F->lev_stream[L];
+        if (F->post_ok[L + 1]) FC_CUDA(cudaStreamWaitEvent(s, F->ev_post[L + 1], 0));
+      }
+      if ((st = reflux_level(F, L, dt, 2, 0.25, s)) != FC_OK) return st;
+      if (F->dag) {
+        FC_CUDA(cudaEventRecord(F->ev_post[L], s));
+        F->post_ok[L] = true;
+      }
+    }
   }
   return FC_OK;
 }
@@ -726,6 +780,8 @@ fc_status check_desc(const fc_forest_desc* d) {
     return fail(FC_ERR_INVALID_ARG, "bad regrid policy");
   if (d->smooth && d->domain == FC_DOMAIN_SPHERE)
     return fail(FC_ERR_INVALID_ARG, "smooth grading is built for the square domains");
+  if (d->reflux < 0 || d->reflux > 1 || (d->reflux && d->domain == FC_DOMAIN_SPHERE))
+    return fail(FC_ERR_INVALID_ARG, "refluxing is built for the square domains (reflux 0 or 1)");
   return FC_OK;
 }
 
@@ -1272,6 +1328,8 @@ fc_status fc_adjoint_step_multirate(fc_forest* F, double t, double dt_coarse, vo
   if (!(dt_coarse > 0.0)) return fail(FC_ERR_INVALID_ARG, "dt must be positive");
   if (F->host.desc.domain == FC_DOMAIN_SPHERE)
     return fail(FC_ERR_INVALID_ARG, "the adjoint is built for the square domains");
+  if (F->host.desc.reflux)
+    return fail(FC_ERR_PRECONDITION, "the adjoint is built without refluxing");
   cudaStream_t s = as_stream(stream);
   fc_status st = F->esize == 4 ? adjoint_multirate_t<float>(F, t, dt_coarse, lam, dscale, s)
                                : adjoint_multirate_t<double>(F, t, dt_coarse, lam, dscale, s);
@@ -1285,6 +1343,8 @@ fc_status fc_adjoint_step_global(fc_forest* F, double t, double dt, void* lam, d
   if (!(dt > 0.0)) return fail(FC_ERR_INVALID_ARG, "dt must be positive");
   if (F->host.desc.domain == FC_DOMAIN_SPHERE)
     return fail(FC_ERR_INVALID_ARG, "the adjoint is built for the square domains");
+  if (F->host.desc.reflux)
+    return fail(FC_ERR_PRECONDITION, "the adjoint is built without refluxing");
   cudaStream_t s = as_stream(stream);
   return F->esize == 4 ? adjoint_step_t<float>(F, t, dt, lam, dscale, s)
                        : adjoint_step_t<double>(F, t, dt, lam, dscale, s);
@@ -1401,6 +1461,11 @@ fc_status fc_step_global(fc_forest* F, double t, double dt, void* stream) {
     if (e != cudaSuccess) return cuda_fail(e, "advance");
   }
   for (int l = 0; l <= kMaxLevel; ++l) F->cur[l] ^= 1;
+  // refluxing: every level took one step of dt, one fine step per face
+  for (int L = H.desc.lmin; L < H.desc.lmax && F->bflux; ++L) {
+    F->bslot[L] = 0;
+    if ((st = reflux_level(F, L, dt, 1, 0.5, s)) != FC_OK) return st;
+  }
   reset_times(F);
   return FC_OK;
 }
@@ -1644,6 +1709,7 @@ fc_status fc_tag_regrid(fc_forest* F, double tau_refine, double tau_coarsen,
   std::memcpy(F->buf, G->buf, sizeof F->buf);
   F->qT = G->qT;
   F->stage = G->stage;
+  F->bflux = G->bflux;
   F->d_tables = G->d_tables;
   F->d_meta = G->d_meta;
   F->d_nbr = G->d_nbr;

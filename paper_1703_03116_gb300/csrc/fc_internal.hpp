@@ -371,6 +371,10 @@ struct AdvArgs {
   // cells its interpolation reads as that fill would (no fill launch before
   // it on the critical path)
   int direct;
+  // refluxing: each patch's final fluxes through its faces go to
+  // bflux + ((p * 2 + bslot) * 4 + face) * mx (faces -x, +x, -y, +y; null: off)
+  void* bflux;
+  int bslot;
 };
 
 // Patch-update kernel variants (chosen per level launch by the autotuner):
@@ -453,6 +457,12 @@ cudaError_t launch_advance(const DevForest<real>& D, int p0, int p1, const AdvAr
                            cudaStream_t s);
 template <typename real>
 cudaError_t launch_tag(const DevForest<real>& D, int kind, double* delta, cudaStream_t s);
+// refluxing of the level-L patches p0..p1 (all on one level, cell width h,
+// their latest update of length dt wrote flux slot cslot; the finer
+// neighbours' fluxes of nfs slots are averaged with weight w)
+template <typename real>
+cudaError_t launch_reflux(const DevForest<real>& D, int p0, int p1, const real* bflux, int cslot,
+                          int nfs, double w, double nu, cudaStream_t s);
 template <typename real>
 cudaError_t launch_mass(const DevForest<real>& D, const int* api_to_dev, const int* fstart,
                         int nforests, double* patch_sums, double* out, cudaStream_t s);

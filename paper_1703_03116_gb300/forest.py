@@ -15,7 +15,7 @@ _NP = {_lib.F32: np.float32, _lib.F64: np.float64}
 def make_desc(domain: int = _lib.WALLS, mx: int = 32, lmin: int = 2, lmax: int = 6,
               dtype: int = _lib.F64, velocity=("swirl", 4.0), order: int = 2,
               limiter: int = 1, transverse: int = 2, nforests: int = 1, mbc: int = 2,
-              indicator: int = 0, smooth: int = 0) -> Desc:
+              indicator: int = 0, smooth: int = 0, reflux: int = 0) -> Desc:
     d = Desc()
     d.domain, d.nforests, d.mx, d.mbc, d.lmin, d.lmax, d.dtype = (
         domain, nforests, mx, mbc, lmin, lmax, dtype)
@@ -32,7 +32,7 @@ def make_desc(domain: int = _lib.WALLS, mx: int = 32, lmin: int = 2, lmax: int =
     else:
         raise ValueError(f"unknown velocity {velocity!r}")
     d.order, d.limiter, d.transverse = order, limiter, transverse
-    d.indicator, d.smooth = indicator, smooth
+    d.indicator, d.smooth, d.reflux = indicator, smooth, reflux
     return d
 
 

@@ -15,7 +15,7 @@ def desc_for(fc, w, dtype, nforests=1, lmax=None):
                         velocity=w.velocity, order=order, limiter=lim,
                         transverse=w.transverse, nforests=nforests,
                         indicator={"gradient": 0, "maxmin": 1}[w.indicator],
-                        smooth=int(w.smooth))
+                        smooth=int(w.smooth), reflux=int(w.reflux))
 
 
 def pair(fc, workloads, dtype):

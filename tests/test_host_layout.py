@@ -225,3 +225,19 @@ def test_regrid_layout_batched_forests_matches_oracle():
     got = fc.layout_regrid(desc_for(ws[0], nforests=5, lmax=5), lv, delta, 0.05, 0.0125, lmax_f)
     F.regrid(0.05, 0.0125, lmax_f)
     assert np.array_equal(got, F.leaves())
+
+
+def test_reflux_option_checked():
+    """Refluxing is built for the square domains, as 0 or 1."""
+    w = synth.swirl(1, lmin=2, lmax=3, mx=8)
+    lv = oracle.initial_forest(w).leaves()
+    d = desc_for(w)
+    d.reflux = 1
+    fc.layout_check(d, lv)
+    d.reflux = 2
+    with pytest.raises(fc.FcError, match="INVALID_ARG"):
+        fc.layout_check(d, lv)
+    s = fc.make_desc(domain=fc.SPHERE, mx=8, lmin=0, lmax=1,
+                     velocity=("rotation", 0.0, 0.0, 1.0), reflux=1)
+    with pytest.raises(fc.FcError, match="INVALID_ARG"):
+        fc.layout_check(s, fc.uniform_leaves(0, nblocks=6))
