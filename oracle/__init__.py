@@ -22,7 +22,7 @@ _SRC = ["forest.c", "ghost.c", "claw.c", "drive.c", "adjoint.c", "sphere.c"]
 _HDR = ["oracle.h", "internal.h"]
 
 WALLS, PERIODIC, SPHERE = 0, 1, 2
-VEL_CONST, VEL_SWIRL, VEL_ROTATION = 0, 1, 2
+VEL_CONST, VEL_SWIRL, VEL_ROTATION, VEL_DEFORM = 0, 1, 2, 3
 
 
 def build(force: bool = False) -> str:
@@ -86,6 +86,7 @@ def lib():
     L.or_set_params.argtypes = [vp, ctypes.POINTER(_Params)]
     L.or_sphere_centres.argtypes = [vp, dp]
     L.or_get_kappa.argtypes = [vp, dp]
+    L.or_sphere_edge_fluxes.argtypes = [vp, ctypes.c_double, dp, dp]
     L.or_single_grid_periodic.argtypes = [ctypes.POINTER(_Params), ctypes.c_int, dp,
                                           ctypes.c_double, ctypes.c_double, ctypes.c_int]
     L.or_mc_phi.restype = ctypes.c_double
@@ -128,6 +129,10 @@ def params(domain: int, mx: int, mbc: int, lmin: int, lmax: int, velocity,
         p.vel[0] = float(velocity[1])
     elif velocity[0] == "rotation":
         p.vel_kind = VEL_ROTATION
+        for k in range(3):
+            p.vel[k] = float(velocity[1 + k])
+    elif velocity[0] == "deform":  # Sec. 5.3: (kappa, T, T_f)
+        p.vel_kind = VEL_DEFORM
         for k in range(3):
             p.vel[k] = float(velocity[1 + k])
     else:
@@ -272,6 +277,16 @@ class Forest:
         out = np.zeros((len(self), self.mx, self.mx))
         lib().or_get_kappa(self.h, _dptr(out))
         return out
+
+    def edge_fluxes(self, t: float = 0.0):
+        """Edge volume fluxes at time t over the extended index range:
+        x-edges (n, S, S+1) [row j, edge i - 1/2] and y-edges (n, S+1, S)
+        [edge j - 1/2, column i], both with index -mbc at 0."""
+        S = self.S
+        px = np.zeros((len(self), S, S + 1))
+        py = np.zeros((len(self), S + 1, S))
+        lib().or_sphere_edge_fluxes(self.h, t, _dptr(px), _dptr(py))
+        return px, py
 
     def set_velocity_scale(self, s: float):
         """Scale every edge speed (the parameter of the velocity-scale gradient)."""

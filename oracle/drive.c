@@ -35,6 +35,10 @@ void or_advance_leaf(or_forest* F, int p, double t, double dt) {
   const or_leaf* a = &F->lv[p];
   size_t S2 = (size_t)F->S * F->S, S = (size_t)F->S;
   if (F->P.domain == OR_SPHERE) {
+    /* a time-dependent streamfunction: the fluxes of the step's half time */
+    if (F->P.vel_kind == OR_VEL_DEFORM)
+      or_sphere_psi_fluxes(a, &F->P, t + 0.5 * dt, F->phix + p * (S + 1) * S,
+                           F->phiy + p * S * (S + 1));
     or_claw_step_capacity(&F->P, F->q + p * S2, F->P.mx, F->P.mbc, dt, F->kappa + p * S2,
                           F->phix + p * (S + 1) * S, F->phiy + p * S * (S + 1));
     return;

@@ -145,12 +145,17 @@ or_forest* or_create(const or_params* P, int n, const int* leaves) {
     or_set_error("bad level range");
     return NULL;
   }
+  if (P->vel_kind == OR_VEL_DEFORM &&
+      (P->domain != OR_SPHERE || !(P->vel[1] != 0.0) || !(P->vel[2] != 0.0))) {
+    or_set_error("the deformational velocity is for the sphere, with nonzero T and T_f");
+    return NULL;
+  }
   if (P->domain == OR_SPHERE && P->reflux) {
     or_set_error("refluxing is built for the square domains");
     return NULL;
   }
-  if (P->domain == OR_SPHERE && P->vel_kind != OR_VEL_ROTATION) {
-    or_set_error("the sphere takes the solid-body rotation velocity");
+  if (P->domain == OR_SPHERE && P->vel_kind != OR_VEL_ROTATION && P->vel_kind != OR_VEL_DEFORM) {
+    or_set_error("the sphere takes the solid-body rotation or the deformational velocity");
     return NULL;
   }
   or_forest* F = (or_forest*)calloc(1, sizeof(or_forest));
@@ -186,9 +191,16 @@ void or_update_metrics(or_forest* F) {
   F->phiy = (double*)malloc(sizeof(double) * n * S * (S + 1));
   double scale = F->P.vel_scale != 0.0 ? F->P.vel_scale : 1.0;
   double om[3] = {scale * F->P.vel[0], scale * F->P.vel[1], scale * F->P.vel[2]};
-  for (int p = 0; p < F->n; ++p)
+  const int deform = F->P.vel_kind == OR_VEL_DEFORM;
+  if (deform) om[0] = om[1] = om[2] = 0.0;
+  for (int p = 0; p < F->n; ++p) {
     or_sphere_metrics(&F->lv[p], F->P.mx, F->P.mbc, om, F->kappa + p * S * S,
                       F->phix + p * (S + 1) * S, F->phiy + p * S * (S + 1));
+    /* time-dependent fluxes: those of t = 0 until a step sets its own */
+    if (deform)
+      or_sphere_psi_fluxes(&F->lv[p], &F->P, 0.0, F->phix + p * (S + 1) * S,
+                           F->phiy + p * S * (S + 1));
+  }
 }
 
 void or_destroy(or_forest* F) {

@@ -36,6 +36,10 @@ void or_sphere_box(const or_leaf* a, int LF, long lo[3], long hi[3]);
 void or_sphere_point(int b, double x, double y, double X[3]);
 void or_sphere_metrics(const or_leaf* a, int mx, int mbc, const double* omega, double* kappa,
                        double* phix, double* phiy);
+/* the edge volume fluxes of a leaf from the streamfunction of P at time t
+ * (OR_VEL_DEFORM): phi = difference of psi between the edge's end points */
+void or_sphere_psi_fluxes(const or_leaf* a, const or_params* P, double t, double* phix,
+                          double* phiy);
 void or_claw_step_capacity(const or_params* P, double* q, int mx, int mbc, double dt,
                            const double* kappa, const double* phix, const double* phiy);
 /* (re)compute the metric terms of every leaf (sphere only) */

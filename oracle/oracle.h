@@ -17,6 +17,12 @@
  * that face, summed over the face's fine cells and the fine substeps.  Pinned
  * by first-order closed forms and by exact conservation of mass.
  *
+ * The sphere's deformational flow (OR_VEL_DEFORM, Sec. 5.3) takes its edge
+ * volume fluxes from the time-dependent streamfunction at each step's half
+ * time.  Pinned against the published velocity components of that flow, the
+ * solid-body rotation it reduces to at half period, and the return of a
+ * tracer after one period.
+ *
  * Parity unpinned (checked only against the same stated reading): the
  * multirate time interpolation of coarse data, the fill of the corner ghost
  * block at three-valent cube corners, and the capacity form on the sphere.
@@ -29,7 +35,8 @@ extern "C" {
 #endif
 
 enum { OR_WALLS = 0, OR_PERIODIC = 1, OR_SPHERE = 2 };
-enum { OR_VEL_CONST = 0, OR_VEL_SWIRL = 1, OR_VEL_ROTATION = 2 /* sphere: vel[0..2] = omega */ };
+enum { OR_VEL_CONST = 0, OR_VEL_SWIRL = 1, OR_VEL_ROTATION = 2 /* sphere: vel[0..2] = omega */,
+       OR_VEL_DEFORM = 3 /* sphere: vel[0..2] = kappa, T, T_f of the Sec. 5.3 streamfunction */ };
 
 #define OR_MAXLEV 18
 
@@ -104,6 +111,11 @@ int or_adjoint_multirate(or_forest* F, int ncoarse, double t0, double dt_coarse,
  * (n x mx x mx x 3) and the cell capacities (n x mx x mx) */
 void or_sphere_centres(const or_forest* F, double* xyz);
 void or_get_kappa(const or_forest* F, double* kappa);
+
+/* cubed sphere: the edge volume fluxes of every leaf at time t (leaf order;
+ * per leaf (S+1)*S x-edges then S*(S+1) y-edges over the extended range, as
+ * or_sphere_metrics lays them out) */
+void or_sphere_edge_fluxes(const or_forest* F, double t, double* phix, double* phiy);
 
 /* one uniform periodic N x N grid, used to check the forest against it */
 int or_single_grid_periodic(const or_params* P, int N, double* q, double t0,

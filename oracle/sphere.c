@@ -162,6 +162,54 @@ void or_sphere_metrics(const or_leaf* a, int mx, int mbc, const double* omega, d
   free(X);
 }
 
+/* Sec. 5.3's deformational streamfunction at unit-sphere point X, time t:
+ *   psi = k sin^2(rho - 2 pi t/T) cos^2(theta) cos(pi t/T) - 2 pi sin(theta)/T_f
+ * with longitude rho and latitude theta of X; since X = cos(theta)(cos rho,
+ * sin rho) + sin(theta) e_z, sin(rho - a) cos(theta) = Y cos a - X sin a and
+ * sin(theta) = Z (no angle is formed: smooth at the poles).  The velocity is
+ * e_r x grad psi, as for the rotation, whose psi is -omega . X. */
+static double deform_psi(const or_params* P, double t, const double* X) {
+  double k = P->vel[0], T = P->vel[1], Tf = P->vel[2];
+  double a = 2.0 * M_PI * t / T;
+  double s = X[1] * cos(a) - X[0] * sin(a);
+  double scale = P->vel_scale != 0.0 ? P->vel_scale : 1.0;
+  return scale * (k * s * s * cos(M_PI * t / T) - 2.0 * M_PI * X[2] / Tf);
+}
+
+void or_sphere_psi_fluxes(const or_leaf* a, const or_params* P, double t, double* phix,
+                          double* phiy) {
+  int mx = P->mx, mbc = P->mbc, S = mx + 2 * mbc, SN = S + 1;
+  double h = 1.0 / ldexp((double)mx, a->l);
+  double* psi = (double*)malloc(sizeof(double) * (size_t)SN * SN);
+  for (int j = 0; j < SN; ++j)
+    for (int i = 0; i < SN; ++i) {
+      double X[3];
+      double x = ((double)a->x * mx + (i - mbc)) * h, y = ((double)a->y * mx + (j - mbc)) * h;
+      or_sphere_point(a->b, x, y, X);
+      psi[j * SN + i] = deform_psi(P, t, X);
+    }
+  /* the rotation's orientation: x-edge psi(bottom) - psi(top), y-edge
+   * psi(right) - psi(left) (for psi = -omega . X these are omega . (X_top -
+   * X_bottom) and omega . (X_left - X_right)) */
+  for (int j = 0; j < S; ++j)
+    for (int i = 0; i < SN; ++i) phix[j * SN + i] = psi[j * SN + i] - psi[(j + 1) * SN + i];
+  for (int j = 0; j < SN; ++j)
+    for (int i = 0; i < S; ++i) phiy[j * S + i] = psi[j * SN + i + 1] - psi[j * SN + i];
+  free(psi);
+}
+
+void or_sphere_edge_fluxes(const or_forest* F, double t, double* phix, double* phiy) {
+  size_t S = (size_t)F->S;
+  for (int p = 0; p < F->n; ++p) {
+    if (F->P.vel_kind == OR_VEL_DEFORM) {
+      or_sphere_psi_fluxes(&F->lv[p], &F->P, t, phix + p * (S + 1) * S, phiy + p * S * (S + 1));
+    } else {
+      memcpy(phix + p * (S + 1) * S, F->phix + p * (S + 1) * S, sizeof(double) * (S + 1) * S);
+      memcpy(phiy + p * S * (S + 1), F->phiy + p * S * (S + 1), sizeof(double) * S * (S + 1));
+    }
+  }
+}
+
 /* Capacity-form wave-propagation step of one patch (the flat step with cell
  * capacities kappa and edge volume fluxes phi in place of h^2 and h s):
  *   W = Q_R - Q_L, F = phi+ Q_L + phi- Q_R + Ft,

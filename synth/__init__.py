@@ -30,7 +30,7 @@ import numpy as np
 
 __all__ = [
     "Gaussians", "Disc", "SquarePulse", "Workload", "uniform_periodic",
-    "swirl", "ensemble", "adjoint_target", "smooth_periodic", "cell_centres",
+    "swirl", "ensemble", "adjoint_target", "smooth_periodic", "cell_centres", "sphere_deform",
     "evaluate", "random_field", "time_step",
 ]
 
@@ -79,6 +79,7 @@ class Workload:
     indicator: str = "gradient"  # regrid indicator: "gradient" | "maxmin" (Sec. 5.1)
     smooth: bool = False         # smooth grading of the target levels (Sec. 3.3)
     reflux: bool = False         # conservative coarse/fine correction (off in the paper)
+    dt_lmin: Optional[float] = None  # fixed time step of level lmin (else from the CFL number)
 
 
 def _rng(seed: int) -> np.random.Generator:
@@ -192,6 +193,28 @@ def sphere(seed: int = 0, lmin: int = 1, lmax: int = 7, mx: int = 32) -> Workloa
         t_final=1.0, regrid_every=4, seed=seed)
 
 
+def sphere_deform(seed: int = 0, lmin: int = 2, lmax: int = 4, mx: int = 32) -> Workload:
+    """The paper's cubed-sphere run (Sec. 5.3) in synthetic form: the
+    deformational streamfunction with kappa = 2, T = 0.5, T_f = 5, run to
+    t = 0.5 with the fixed level-lmin step 2.5e-3 (halved per finer level),
+    moving two slotted cylinders (radius 0.5, on the equator around
+    longitudes 5 pi / 6 and 7 pi / 6, slots opening to the north; the centres
+    are nudged by a seeded few hundredths of a radian)."""
+    g = _rng(seed)
+    parts = []
+    for lon in (5.0 * np.pi / 6.0, 7.0 * np.pi / 6.0):
+        lon = lon + g.uniform(-0.02, 0.02)
+        lat = g.uniform(-0.02, 0.02)
+        c = np.array([np.cos(lat) * np.cos(lon), np.cos(lat) * np.sin(lon), np.sin(lat)])
+        north = np.array([-np.sin(lat) * np.cos(lon), -np.sin(lat) * np.sin(lon), np.cos(lat)])
+        parts.append(SlottedCylinder(c, north))
+    return Workload(
+        name=f"cubed sphere deformational flow levels {lmin}-{lmax} mx={mx}", domain="sphere",
+        mx=mx, mbc=2, lmin=lmin, lmax=lmax, velocity=("deform", 2.0, 0.5, 5.0), limiter="mc",
+        transverse=2, cfl=0.9, parts=parts, t_final=0.5, regrid_every=1,
+        indicator="maxmin", tau_refine=0.25, tau_coarsen=0.001, dt_lmin=2.5e-3, seed=seed)
+
+
 def evaluate_sphere(w: Workload, X: np.ndarray) -> np.ndarray:
     """Initial field of a sphere workload at unit vectors X (..., 3)."""
     X = np.asarray(X, dtype=np.float64)
@@ -290,8 +313,14 @@ def time_step(w: Workload, lmax: Optional[int] = None):
     shared by both implementations, not part of either.
     """
     L = w.lmax if lmax is None else lmax
+    if w.dt_lmin is not None:  # a fixed step of the coarsest level
+        n = int(round(w.t_final / w.dt_lmin))
+        return n, w.t_final / n
     h_f = 1.0 / (w.mx * 2 ** L)
-    if w.velocity[0] == "rotation":
+    if w.velocity[0] == "deform":  # speed <= kappa + 2 pi / |T_f|
+        h_f = 0.7 * (np.pi / 2) / (w.mx * 2 ** L)
+        smax = abs(w.velocity[1]) + 2.0 * np.pi / abs(w.velocity[3])
+    elif w.velocity[0] == "rotation":
         # unit sphere: a block spans pi/2 radians; the smallest equiangular
         # cell side is about 0.7 of the nominal one; speed <= |omega|
         h_f = 0.7 * (np.pi / 2) / (w.mx * 2 ** L)
