@@ -165,37 +165,41 @@ void or_sphere_metrics(const or_leaf* a, int mx, int mbc, const double* omega, d
 /* Sec. 5.3's deformational streamfunction at unit-sphere point X, time t:
  *   psi = k sin^2(rho - 2 pi t/T) cos^2(theta) cos(pi t/T) - 2 pi sin(theta)/T_f
  * with longitude rho and latitude theta of X; since X = cos(theta)(cos rho,
- * sin rho) + sin(theta) e_z, sin(rho - a) cos(theta) = Y cos a - X sin a and
- * sin(theta) = Z (no angle is formed: smooth at the poles).  The velocity is
- * e_r x grad psi, as for the rotation, whose psi is -omega . X. */
-static double deform_psi(const or_params* P, double t, const double* X) {
+ * sin rho) + sin(theta) e_z, sin(rho - a) cos(theta) = Y cos a - X sin a =: s
+ * and sin(theta) = Z (no angle is formed: smooth at the poles).  The velocity
+ * is e_r x grad psi, as for the rotation, whose psi is -omega . X.  An edge's
+ * flux is psi(b) - psi(a) = k c (s_b - s_a)(s_b + s_a) - (2 pi/T_f)(Z_b - Z_a)
+ * (c = cos(pi t/T)), formed from the end points' differences: psi is O(1),
+ * the flux O(h). */
+static double deform_flux(const or_params* P, double t, const double* A, const double* B) {
   double k = P->vel[0], T = P->vel[1], Tf = P->vel[2];
-  double a = 2.0 * M_PI * t / T;
-  double s = X[1] * cos(a) - X[0] * sin(a);
+  double a = 2.0 * M_PI * t / T, ca = cos(a), sa = sin(a);
   double scale = P->vel_scale != 0.0 ? P->vel_scale : 1.0;
-  return scale * (k * s * s * cos(M_PI * t / T) - 2.0 * M_PI * X[2] / Tf);
+  double ds = (B[1] - A[1]) * ca - (B[0] - A[0]) * sa;
+  double ss = (B[1] + A[1]) * ca - (B[0] + A[0]) * sa;
+  return scale * (k * cos(M_PI * t / T) * (ds * ss) - 2.0 * M_PI / Tf * (B[2] - A[2]));
 }
 
 void or_sphere_psi_fluxes(const or_leaf* a, const or_params* P, double t, double* phix,
                           double* phiy) {
   int mx = P->mx, mbc = P->mbc, S = mx + 2 * mbc, SN = S + 1;
   double h = 1.0 / ldexp((double)mx, a->l);
-  double* psi = (double*)malloc(sizeof(double) * (size_t)SN * SN);
+  double* X = (double*)malloc(sizeof(double) * 3 * (size_t)SN * SN);
   for (int j = 0; j < SN; ++j)
     for (int i = 0; i < SN; ++i) {
-      double X[3];
       double x = ((double)a->x * mx + (i - mbc)) * h, y = ((double)a->y * mx + (j - mbc)) * h;
-      or_sphere_point(a->b, x, y, X);
-      psi[j * SN + i] = deform_psi(P, t, X);
+      or_sphere_point(a->b, x, y, X + 3 * (j * SN + i));
     }
+#define N(i, j) (X + 3 * ((j) * SN + (i)))
   /* the rotation's orientation: x-edge psi(bottom) - psi(top), y-edge
    * psi(right) - psi(left) (for psi = -omega . X these are omega . (X_top -
    * X_bottom) and omega . (X_left - X_right)) */
   for (int j = 0; j < S; ++j)
-    for (int i = 0; i < SN; ++i) phix[j * SN + i] = psi[j * SN + i] - psi[(j + 1) * SN + i];
+    for (int i = 0; i < SN; ++i) phix[j * SN + i] = deform_flux(P, t, N(i, j + 1), N(i, j));
   for (int j = 0; j < SN; ++j)
-    for (int i = 0; i < S; ++i) phiy[j * S + i] = psi[j * SN + i + 1] - psi[j * SN + i];
-  free(psi);
+    for (int i = 0; i < S; ++i) phiy[j * S + i] = deform_flux(P, t, N(i, j), N(i + 1, j));
+#undef N
+  free(X);
 }
 
 void or_sphere_edge_fluxes(const or_forest* F, double t, double* phix, double* phiy) {
