@@ -46,7 +46,7 @@ typedef enum {
 
 typedef enum { FC_F32 = 0, FC_F64 = 1 } fc_dtype;
 typedef enum { FC_DOMAIN_WALLS = 0, FC_DOMAIN_PERIODIC = 1, FC_DOMAIN_SPHERE = 2 } fc_domain;
-typedef enum { FC_VEL_CONST = 0, FC_VEL_SWIRL = 1, FC_VEL_ROTATION = 2 } fc_velocity;
+typedef enum { FC_VEL_CONST = 0, FC_VEL_SWIRL = 1, FC_VEL_ROTATION = 2, FC_VEL_DEFORM = 3 } fc_velocity;
 
 /* Problem description (Sec. 2; Sec. 5.1 "Problem setup").
  *   domain      unit square with walls, periodic unit square, or cubed sphere.
@@ -67,6 +67,18 @@ typedef enum { FC_VEL_CONST = 0, FC_VEL_SWIRL = 1, FC_VEL_ROTATION = 2 } fc_velo
  *   vel_kind    FC_VEL_CONST: (u, v) = (vel[0], vel[1]);
  *               FC_VEL_SWIRL: streamfunction sin^2(pi x) sin^2(pi y)
  *               cos(pi t / T) / pi with T = vel[0];
+ *               FC_VEL_DEFORM (sphere only, Sec. 5.3's run): the time-
+ *               dependent streamfunction psi = k sin^2(rho - 2 pi t/T)
+ *               cos^2(theta) cos(pi t/T) - 2 pi sin(theta)/T_f (longitude
+ *               rho, latitude theta; k, T, T_f = vel[0], vel[1], vel[2], T
+ *               and T_f nonzero), velocity e_r x grad psi; before each
+ *               level substep (and global step) the edge volume fluxes of
+ *               the level's patches are recomputed for its half time as
+ *               psi differences between the edges' end points, formed as
+ *               k c (s_b - s_a)(s_b + s_a) - (2 pi/T_f)(Z_b - Z_a) with
+ *               s = Y cos(2 pi t/T) - X sin(2 pi t/T), c = cos(pi t/T),
+ *               from the grid corners kept per patch (3 (mx+5)^2 doubles);
+ *               times the velocity scale.
  *               FC_VEL_ROTATION (sphere only): solid-body rotation
  *               u = omega x X, omega = (vel[0], vel[1], vel[2]).  The sphere
  *               runs the capacity form: FP64 metrics per patch (cell

@@ -12,7 +12,7 @@ STATUS = {0: "FC_OK", 1: "FC_ERR_INVALID_ARG", 2: "FC_ERR_PRECONDITION", 3: "FC_
           4: "FC_ERR_CUDA", 5: "FC_ERR_TIMEOUT", 6: "FC_ERR_STATE"}
 F32, F64 = 0, 1
 WALLS, PERIODIC, SPHERE = 0, 1, 2
-VEL_CONST, VEL_SWIRL, VEL_ROTATION = 0, 1, 2
+VEL_CONST, VEL_SWIRL, VEL_ROTATION, VEL_DEFORM = 0, 1, 2, 3
 
 # every function that include/fc.h declares, with (restype, argtypes)
 _vp, _ip, _dp = ctypes.c_void_p, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)

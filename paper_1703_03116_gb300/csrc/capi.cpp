@@ -178,6 +178,7 @@ struct fc_forest {
   int forced_variant = -1, forced_warps = 4;
   double vel_scale = 1.0;                 // multiplies every edge speed
   double* d_metric = nullptr;             // cubed sphere: FP64 metric blocks per patch
+  double* d_corner = nullptr;             // deformational flow: grid corners per patch
   void* lam[2] = {nullptr, nullptr};      // adjoint tiles (patch-store layout), lazily allocated
   void* madj[3] = {nullptr, nullptr, nullptr};  // multirate adjoint: current, previous, qT tiles
   void* mio = nullptr;                    // multirate adjoint: lam in field layout (graph input)
@@ -332,24 +333,47 @@ void free_device(fc_forest* F) {
   dfree(F->msnap);
   F->msnap_bytes = 0;
   dfree(F->d_metric);
+  dfree(F->d_corner);
 }
 
 // cubed sphere: (re)compute the metric blocks of the current layout for the
 // rotation vector times the velocity scale (synchronous); after a regrid the
-// kept patches copy theirs from the old layout (rm, old: device)
+// kept patches copy theirs from the old layout (rm, old: device).  The
+// deformational flow keeps every patch's grid corners instead of fixed edge
+// fluxes (its fluxes are refreshed per substep): all patches are computed.
 fc_status update_metrics(fc_forest* F, const RemapEntry* rm = nullptr,
                          const double* old = nullptr) {
   const HostForest& H = F->host;
   if (H.desc.domain != FC_DOMAIN_SPHERE) return FC_OK;
   const int n = H.npatch();
   const int S = H.desc.mx + 2 * kMbc;
+  const bool deform = H.desc.vel_kind == FC_VEL_DEFORM;
   dfree(F->d_metric);
+  dfree(F->d_corner);
   if (dmalloc(&F->d_metric, (size_t)n * metric_stride(S)) != cudaSuccess)
     return fail(FC_ERR_OOM, "metric allocation failed");
-  const double w[3] = {F->vel_scale * H.desc.vel[0], F->vel_scale * H.desc.vel[1],
-                       F->vel_scale * H.desc.vel[2]};
-  FC_CUDA(launch_sphere_metrics(F->d_meta, n, H.desc.mx, w, F->d_metric, rm, old,
+  if (deform && dmalloc(&F->d_corner, (size_t)n * 3 * (S + 1) * (S + 1)) != cudaSuccess)
+    return fail(FC_ERR_OOM, "corner allocation failed");
+  double w[3] = {F->vel_scale * H.desc.vel[0], F->vel_scale * H.desc.vel[1],
+                 F->vel_scale * H.desc.vel[2]};
+  if (deform) {
+    w[0] = w[1] = w[2] = 0.0;
+    rm = nullptr;
+    old = nullptr;
+  }
+  FC_CUDA(launch_sphere_metrics(F->d_meta, n, H.desc.mx, w, F->d_metric, rm, old, F->d_corner,
                                 g_alloc_stream));
+  return FC_OK;
+}
+
+// the deformational flow: the edge fluxes of level L's patches for the
+// substep t -> t + dt (a: its update's arguments, whose time they share)
+fc_status deform_fluxes(fc_forest* F, int p0, int p1, const AdvArgs& a, cudaStream_t s) {
+  const fc_forest_desc& d = F->host.desc;
+  if (d.vel_kind != FC_VEL_DEFORM || p1 <= p0) return FC_OK;
+  const double kc = d.vel[0] * F->vel_scale, rot = 2.0 * M_PI / d.vel[2] * F->vel_scale;
+  FC_CUDA(launch_deform_fluxes(p0, p1, d.mx, F->d_corner, F->d_metric, kc, d.vel[1], rot,
+                               a.t_half, a.t0_dev, a.t_off, s));
   return FC_OK;
 }
 
@@ -683,6 +707,10 @@ fc_status advance_level_t(fc_forest* F, int L, double t, double dt, cudaStream_t
       F->pre_ok[L] = true;
     }
     {
+      const fc_status fs = deform_fluxes(F, p0, p1, a, s);
+      if (fs != FC_OK) return fs;
+    }
+    {
       Timed tm(F, 0, s, advance_bytes(F, p1 - p0));
       FC_CUDA(launch_advance(D, p0, p1, a, F->d_err, s));
     }
@@ -767,10 +795,15 @@ fc_status check_desc(const fc_forest_desc* d) {
       d->domain != FC_DOMAIN_SPHERE)
     return fail(FC_ERR_INVALID_ARG, "bad domain");
   if (d->vel_kind != FC_VEL_CONST && d->vel_kind != FC_VEL_SWIRL &&
-      d->vel_kind != FC_VEL_ROTATION)
+      d->vel_kind != FC_VEL_ROTATION && d->vel_kind != FC_VEL_DEFORM)
     return fail(FC_ERR_INVALID_ARG, "bad velocity kind");
-  if ((d->domain == FC_DOMAIN_SPHERE) != (d->vel_kind == FC_VEL_ROTATION))
-    return fail(FC_ERR_INVALID_ARG, "the cubed sphere takes the solid-body rotation, and only it");
+  if ((d->domain == FC_DOMAIN_SPHERE) !=
+      (d->vel_kind == FC_VEL_ROTATION || d->vel_kind == FC_VEL_DEFORM))
+    return fail(FC_ERR_INVALID_ARG,
+                "the cubed sphere takes the solid-body rotation or the deformational flow, and "
+                "only they");
+  if (d->vel_kind == FC_VEL_DEFORM && !(d->vel[1] != 0.0 && d->vel[2] != 0.0))
+    return fail(FC_ERR_INVALID_ARG, "the deformational flow needs nonzero T and T_f");
   if (d->vel_kind == FC_VEL_SWIRL && !(d->vel[0] != 0.0))
     return fail(FC_ERR_INVALID_ARG, "swirl period must be nonzero");
   if (d->order < 1 || d->order > 2 || d->limiter < 0 || d->limiter > 1 || d->transverse < 0 ||
@@ -1455,6 +1488,7 @@ fc_status fc_step_global(fc_forest* F, double t, double dt, void* stream) {
     const int p0 = H.lev_start[L], p1 = H.lev_start[L + 1];
     if (p1 <= p0) continue;
     const AdvArgs a = adv_args(F, L, t, dt, p1 - p0);
+    if ((st = deform_fluxes(F, p0, p1, a, s)) != FC_OK) return st;
     Timed tm(F, 0, s, advance_bytes(F, p1 - p0));
     cudaError_t e = F->esize == 4 ? launch_advance(Df, p0, p1, a, F->d_err, s)
                                   : launch_advance(Dd, p0, p1, a, F->d_err, s);
@@ -1728,6 +1762,7 @@ fc_status fc_tag_regrid(fc_forest* F, double tau_refine, double tau_coarsen,
   F->d_err = G->d_err;
   F->d_t0 = G->d_t0;
   F->d_metric = G->d_metric;
+  F->d_corner = G->d_corner;
   for (int l = 0; l <= kMaxLevel; ++l) F->cur[l] = 0;
   reset_times(F);
   delete G;  // its device pointers now belong to F

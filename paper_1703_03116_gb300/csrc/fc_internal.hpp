@@ -484,9 +484,19 @@ uint64_t& launch_counter();
 // the stream function -omega . X (Sec. 5.3 mapped grids).  With a remap list
 // (rm, device, one entry per patch), RM_COPY patches copy their block from
 // old_metric (same omega) instead.
+// With corner_out set, every patch's grid corners (three planes of
+// (mx+5)^2 unit-sphere components) are also written there.
 cudaError_t launch_sphere_metrics(const PatchMeta* meta, int npatch, int mx, const double* omega,
                                   double* metric, const RemapEntry* rm, const double* old_metric,
-                                  cudaStream_t s);
+                                  double* corner_out, cudaStream_t s);
+
+// The deformational flow (FC_VEL_DEFORM): the edge volume fluxes of the
+// metric blocks of patches [p0, p1) for time t (t0_dev ? *t0_dev + t_off :
+// t_half) from their kept corners; coefficients already scaled:
+// kc = k * scale, rot = 2 pi / T_f * scale.
+cudaError_t launch_deform_fluxes(int p0, int p1, int mx, const double* corner, double* metric,
+                                 double kc, double T, double rot, double t_half,
+                                 const double* t0_dev, double t_off, cudaStream_t s);
 
 // fc_mass_noalloc's kernels (scratch in a file-scope device array)
 cudaError_t noalloc_mass(const void* q, int dtype, int mx, int nleaves, const int* level,

@@ -17,6 +17,14 @@
 // The metrics of a patch cover its ghost cells too (the patch's own mapping
 // extended past its block), are computed in FP64 once per layout, and are
 // stored per patch in the order kappa, phi_x, phi_y (metric_stride doubles).
+//
+// The deformational flow of Sec. 5.3 has a time-dependent streamfunction
+// psi = k sin^2(rho - 2 pi t/T) cos^2(theta) cos(pi t/T) - 2 pi sin(theta)/T_f.
+// With s = Y cos a - X sin a (a = 2 pi t/T), which is sin(rho - a) cos(theta),
+// and sin(theta) = Z, psi = k c s^2 - (2 pi/T_f) Z (c = cos(pi t/T)); an edge
+// flux psi(b) - psi(a) = k c (s_b - s_a)(s_b + s_a) - (2 pi/T_f)(Z_b - Z_a) is
+// again formed from the end points' differences.  Its fluxes are refreshed
+// for each substep's half time from the corners kept per patch.
 #include <cmath>
 
 #include "device_util.cuh"
@@ -49,7 +57,8 @@ __device__ __forceinline__ double tri_area(const double* a, const double* b, con
 __global__ void __launch_bounds__(256) metrics_kernel(const PatchMeta* meta, int npatch, int mx,
                                                       double w0, double w1, double w2,
                                                       double* metric, const RemapEntry* rm,
-                                                      const double* old_metric) {
+                                                      const double* old_metric,
+                                                      double* corner_out) {
   extern __shared__ double Xs[];
   const int S = mx + 2 * kMbc, SN = S + 1;
   double* X0 = Xs;
@@ -79,6 +88,12 @@ __global__ void __launch_bounds__(256) metrics_kernel(const PatchMeta* meta, int
       X0[k] = P[0] / len;
       X1[k] = P[1] / len;
       X2[k] = P[2] / len;
+      if (corner_out) {
+        double* C = corner_out + (size_t)p * 3 * SN * SN;
+        C[k] = X0[k];
+        C[SN * SN + k] = X1[k];
+        C[2 * SN * SN + k] = X2[k];
+      }
     }
     __syncthreads();
     double* K = metric + (size_t)p * metric_stride(S);
@@ -119,11 +134,57 @@ __global__ void __launch_bounds__(256) metrics_kernel(const PatchMeta* meta, int
   }
 }
 
+// one CTA per patch of [p0, p1): phi_x, phi_y of its metric block at time t
+__global__ void __launch_bounds__(256) deform_fluxes_kernel(int p0, int p1, int mx,
+                                                            const double* __restrict__ corner,
+                                                            double* metric, double kc, double T,
+                                                            double rot, double t_half,
+                                                            const double* t0_dev, double t_off) {
+  const double t = t0_dev ? *t0_dev + t_off : t_half;
+  const double a = 2.0 * M_PI * t / T;
+  const double ca = cos(a), sa = sin(a), kcc = kc * cos(M_PI * t / T);
+  const int S = mx + 2 * kMbc, SN = S + 1;
+  for (int p = p0 + blockIdx.x; p < p1; p += gridDim.x) {
+    const double* X0 = corner + (size_t)p * 3 * SN * SN;
+    const double* X1 = X0 + SN * SN;
+    const double* X2 = X1 + SN * SN;
+    double* PX = metric + (size_t)p * metric_stride(S) + S * S;
+    double* PY = PX + S * SN;
+    // psi(corner kb) - psi(corner ka)
+    auto dpsi = [&](int ka, int kb) -> double {
+      const double ds = (X1[kb] - X1[ka]) * ca - (X0[kb] - X0[ka]) * sa;
+      const double ss = (X1[kb] + X1[ka]) * ca - (X0[kb] + X0[ka]) * sa;
+      return kcc * (ds * ss) - rot * (X2[kb] - X2[ka]);
+    };
+    for (int k = threadIdx.x; k < S * SN; k += blockDim.x) {
+      // x-edge i-1/2 of row j: psi(corner (i, j)) - psi(corner (i, j+1))
+      const int i = k % SN, j = k / SN;
+      PX[k] = dpsi((j + 1) * SN + i, j * SN + i);
+    }
+    for (int k = threadIdx.x; k < SN * S; k += blockDim.x) {
+      // y-edge j-1/2 of column i: psi(corner (i+1, j)) - psi(corner (i, j))
+      const int i = k % S, j = k / S;
+      PY[k] = dpsi(j * SN + i, j * SN + i + 1);
+    }
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_deform_fluxes(int p0, int p1, int mx, const double* corner, double* metric,
+                                 double kc, double T, double rot, double t_half,
+                                 const double* t0_dev, double t_off, cudaStream_t s) {
+  if (p1 <= p0) return cudaSuccess;
+  const int grid = p1 - p0 < 65535 * 8 ? p1 - p0 : 65535 * 8;
+  deform_fluxes_kernel<<<grid, 256, 0, s>>>(p0, p1, mx, corner, metric, kc, T, rot, t_half,
+                                            t0_dev, t_off);
+  ++launch_counter();
+  return cudaGetLastError();
+}
 
 cudaError_t launch_sphere_metrics(const PatchMeta* meta, int npatch, int mx, const double* omega,
                                   double* metric, const RemapEntry* rm, const double* old_metric,
-                                  cudaStream_t s) {
+                                  double* corner_out, cudaStream_t s) {
   if (npatch <= 0) return cudaSuccess;
   const int SN = mx + 2 * kMbc + 1;
   const size_t smem = sizeof(double) * 3 * (size_t)SN * SN;
@@ -137,7 +198,7 @@ cudaError_t launch_sphere_metrics(const PatchMeta* meta, int npatch, int mx, con
   if (smem > 64 * 1024) return cudaErrorInvalidValue;
   const int grid = npatch < 65535 * 8 ? npatch : 65535 * 8;
   metrics_kernel<<<grid, 256, smem, s>>>(meta, npatch, mx, omega[0], omega[1], omega[2], metric,
-                                         rm, old_metric);
+                                         rm, old_metric, corner_out);
   ++launch_counter();
   return cudaGetLastError();
 }

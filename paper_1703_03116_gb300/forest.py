@@ -29,6 +29,10 @@ def make_desc(domain: int = _lib.WALLS, mx: int = 32, lmin: int = 2, lmax: int =
         d.vel_kind = _lib.VEL_ROTATION
         for k in range(3):
             d.vel[k] = float(velocity[1 + k])
+    elif velocity[0] == "deform":  # Sec. 5.3: (k, T, T_f)
+        d.vel_kind = _lib.VEL_DEFORM
+        for k in range(3):
+            d.vel[k] = float(velocity[1 + k])
     else:
         raise ValueError(f"unknown velocity {velocity!r}")
     d.order, d.limiter, d.transverse = order, limiter, transverse

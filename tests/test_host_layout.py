@@ -241,3 +241,16 @@ def test_reflux_option_checked():
                      velocity=("rotation", 0.0, 0.0, 1.0), reflux=1)
     with pytest.raises(fc.FcError, match="INVALID_ARG"):
         fc.layout_check(s, fc.uniform_leaves(0, nblocks=6))
+
+
+def test_deformational_flow_option_checked():
+    """The deformational flow is for the sphere, with nonzero T and T_f."""
+    lv = fc.uniform_leaves(1, nblocks=6)
+    d = fc.make_desc(domain=fc.SPHERE, mx=8, lmin=1, lmax=2, velocity=("deform", 2.0, 0.5, 5.0))
+    fc.layout_check(d, lv)
+    d0 = fc.make_desc(domain=fc.SPHERE, mx=8, lmin=1, lmax=2, velocity=("deform", 2.0, 0.0, 5.0))
+    with pytest.raises(fc.FcError, match="INVALID_ARG"):
+        fc.layout_check(d0, lv)
+    sq = fc.make_desc(domain=fc.PERIODIC, mx=8, lmin=1, lmax=2, velocity=("deform", 2.0, 0.5, 5.0))
+    with pytest.raises(fc.FcError, match="INVALID_ARG"):
+        fc.layout_check(sq, fc.uniform_leaves(1))
