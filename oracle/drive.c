@@ -34,17 +34,17 @@ static double cell_h(const or_forest* F, int l) { return 1.0 / ldexp((double)F->
 void or_advance_leaf(or_forest* F, int p, double t, double dt) {
   const or_leaf* a = &F->lv[p];
   size_t S2 = (size_t)F->S * F->S, S = (size_t)F->S;
+  double* bf = (F->P.reflux && F->bflux) ? F->bflux + ((size_t)p * 2 + F->fslot) * 4 * F->P.mx
+                                          : NULL;
   if (F->P.domain == OR_SPHERE) {
     /* a time-dependent streamfunction: the fluxes of the step's half time */
     if (F->P.vel_kind == OR_VEL_DEFORM)
       or_sphere_psi_fluxes(a, &F->P, t + 0.5 * dt, F->phix + p * (S + 1) * S,
                            F->phiy + p * S * (S + 1));
     or_claw_step_capacity(&F->P, F->q + p * S2, F->P.mx, F->P.mbc, dt, F->kappa + p * S2,
-                          F->phix + p * (S + 1) * S, F->phiy + p * S * (S + 1));
+                          F->phix + p * (S + 1) * S, F->phiy + p * S * (S + 1), bf);
     return;
   }
-  double* bf = (F->P.reflux && F->bflux) ? F->bflux + ((size_t)p * 2 + F->fslot) * 4 * F->P.mx
-                                          : NULL;
   or_claw_step_flux(&F->P, F->q + p * S2, F->P.mx, F->P.mbc, cell_h(F, a->l), dt, t,
                     (long)a->x * F->P.mx, (long)a->y * F->P.mx, bf);
 }
@@ -59,70 +59,110 @@ static void flux_store(or_forest* F) {
   F->nbflux = F->n;
 }
 
+/* the leaf across a face and the cell it holds at a point there: located from
+ * the point at depth d beyond the face and the point one cell of that leaf
+ * deeper (cell: that leaf's cell width), whose step gives the leaf's face on
+ * the shared edge (g: 0 -x, 1 +x, 2 -y, 3 +y) and the cell's index along it.
+ * Returns the leaf or -1; with cell = 0 only the leaf is located. */
+static int across(const or_forest* F, const or_leaf* a, int dir, double along, double d,
+                  double cell, int* g, int* jn) {
+  const int mx = F->P.mx;
+  const double h = cell_h(F, a->l);
+  const double x0 = a->x * mx * h, y0 = a->y * mx * h, x1 = x0 + mx * h, y1 = y0 + mx * h;
+  int leaf[2], ix[2], iy[2];
+  for (int c = 0; c < 2; ++c) {
+    double dd = d + c * cell, x, y;
+    if (dir < 2) {
+      x = dir == 0 ? x0 - dd : x1 + dd;
+      y = y0 + along;
+    } else {
+      x = x0 + along;
+      y = dir == 2 ? y0 - dd : y1 + dd;
+    }
+    int b = a->b;
+    leaf[c] = or_locate(F, a->f, &b, &x, &y);
+    if (leaf[c] < 0) return -1;
+    const or_leaf* n = &F->lv[leaf[c]];
+    double hn = cell_h(F, n->l);
+    ix[c] = (int)floor(x / hn) - n->x * mx;
+    iy[c] = (int)floor(y / hn) - n->y * mx;
+  }
+  if (leaf[0] != leaf[1]) return -1;
+  if (cell == 0.0) return leaf[0]; /* the leaf only */
+  int di = ix[1] - ix[0], dj = iy[1] - iy[0];
+  if (di == 1 && dj == 0) *g = 0;
+  else if (di == -1 && dj == 0) *g = 1;
+  else if (di == 0 && dj == 1) *g = 2;
+  else if (di == 0 && dj == -1) *g = 3;
+  else return -1;
+  *jn = *g < 2 ? iy[0] : ix[0];
+  return leaf[0];
+}
+
 /*
  * Refluxing of level L (Berger and Colella's correction; the paper's scheme
- * has none).  Over one level-L update of length dt, a coarse cell next to a
- * face whose other side is finer took the flux Fc that its own update
- * computed; mass leaves the fine side through the same face by the fine
- * fluxes, time dt_f over faces of length h/2 each.  The coarse cell exchanges
- * Fc for the fine fluxes' average Fbar = w * sum over the face's two fine cells
- * and the fine substeps (w = 1/4 with two substeps of dt/2, 1/2 with one
- * substep of dt), by q += (dt/h) (Fc - Fbar) on a face in +x or +y and
- * q += (dt/h) (Fbar - Fc) on a face in -x or -y.  The fine neighbours are
- * found by locating the centres of the fine cells across the face.  Faces are
- * corrected in the order -x, +x, -y, +y (a corner cell takes two).
+ * has none), after one level-L update of length dt whose face fluxes are in
+ * slot cslot.  With s_f = -1 on a -x or -y face and +1 on a +x or +y face, a
+ * cell's update took out = s_f F through each face.  Across a face whose
+ * other side is finer, the fine side's fluxes are the ones kept: the coarse
+ * cell's outflow becomes out' = -w sum s_g F_fine over the two fine cells
+ * across it and the nfs fine substeps (g the fine leaf's face on that edge;
+ * w = (fine dt / dt) times the length ratio of a fine face for fluxes per
+ * unit length -- 1/4 and 1/2 on the square with two substeps or one --, or
+ * fine dt / dt for the sphere's volume fluxes), by q += c (out - out'), c =
+ * dt/h on the square, dt/kappa of the cell on the sphere.  Across a cube
+ * edge between two leaves of the same level (each side computes that edge's
+ * flux from its own ghost cells), the side on the block of lower index keeps
+ * its flux and the other takes out' = -s_g F_nb of the same substep.  Leaves
+ * across are found by locating points beyond the face.  Faces are corrected
+ * in the order -x, +x, -y, +y (a corner cell takes two).
  */
-static void reflux_level(or_forest* F, int L, double dt, int cslot, int nfs, double w) {
+static void reflux_level(or_forest* F, int L, double dt, int cslot, int nfs, double wt) {
   const int mx = F->P.mx;
+  const int sphere = F->P.domain == OR_SPHERE;
   const size_t S2 = (size_t)F->S * F->S, fs = 4 * (size_t)mx;
-  const double h = cell_h(F, L), nu = dt / h;
+  const double h = cell_h(F, L);
+  const double w = sphere ? wt : 0.5 * wt;
   for (int p = 0; p < F->n; ++p) {
     const or_leaf* a = &F->lv[p];
     if (a->l != L) continue;
     double* Q = F->q + p * S2;
-    const double x0 = a->x * mx * h, y0 = a->y * mx * h, x1 = x0 + mx * h, y1 = y0 + mx * h;
     for (int dir = 0; dir < 4; ++dir)
       for (int k = 0; k < mx; ++k) {
-        /* the centres of the two fine cells across the face from coarse cell k */
-        double px[2], py[2];
-        for (int c = 0; c < 2; ++c) {
-          double along = (k + 0.25 + 0.5 * c) * h;
-          if (dir < 2) {
-            px[c] = dir == 0 ? x0 - 0.25 * h : x1 + 0.25 * h;
-            py[c] = y0 + along;
-          } else {
-            px[c] = x0 + along;
-            py[c] = dir == 2 ? y0 - 0.25 * h : y1 + 0.25 * h;
-          }
-        }
-        double fsum = 0.0;
-        int ok = 1;
-        double pair[2][2];
-        for (int c = 0; c < 2 && ok; ++c) {
-          int b = a->b;
-          double x = px[c], y = py[c];
-          int pf = or_locate(F, a->f, &b, &x, &y);
-          if (pf < 0 || F->lv[pf].l != L + 1) {
-            ok = 0;
-            break;
-          }
-          const or_leaf* fl = &F->lv[pf];
-          double hf = 0.5 * h;
-          int jf = dir < 2 ? (int)floor(y / hf) - fl->y * mx : (int)floor(x / hf) - fl->x * mx;
-          int ff = dir ^ 1; /* the fine leaf's face on the shared edge */
+        const double sf = (dir & 1) ? 1.0 : -1.0;
+        int g, jn;
+        double target;
+        /* the level across: at a quarter cell beyond the face, a fine cell's
+         * centre, or inside a same-size or coarser cell */
+        int pn = across(F, a, dir, (k + 0.5) * h, 0.25 * h, 0.0, &g, &jn);
+        if (pn < 0) continue;
+        if (F->lv[pn].l == L + 1) {
+          /* the two fine cells across coarse cell k */
+          int g1, j1;
+          int pn1 = across(F, a, dir, (k + 0.75) * h, 0.25 * h, 0.5 * h, &g1, &j1);
+          int g0, j0;
+          int pn0 = across(F, a, dir, (k + 0.25) * h, 0.25 * h, 0.5 * h, &g0, &j0);
+          if (pn0 != pn || pn1 != pn || g0 != g1) continue;
+          g = g0;
+          double fsum = 0.0;
           for (int s = 0; s < nfs; ++s)
-            pair[s][c] = F->bflux[((size_t)pf * 2 + s) * fs + (size_t)ff * mx + jf];
+            fsum += F->bflux[((size_t)pn * 2 + s) * fs + (size_t)g * mx + j0] +
+                    F->bflux[((size_t)pn * 2 + s) * fs + (size_t)g * mx + j1];
+          const double sg = (g & 1) ? 1.0 : -1.0;
+          target = -sg * (w * fsum);
+        } else if (F->lv[pn].l == L && sphere && F->lv[pn].b != a->b && F->lv[pn].b < a->b) {
+          pn = across(F, a, dir, (k + 0.5) * h, 0.5 * h, h, &g, &jn);
+          if (pn < 0) continue;
+          const double sg = (g & 1) ? 1.0 : -1.0;
+          target = -sg * F->bflux[((size_t)pn * 2 + cslot) * fs + (size_t)g * mx + jn];
+        } else {
+          continue;
         }
-        if (!ok) continue;
-        for (int s = 0; s < nfs; ++s) fsum += pair[s][0] + pair[s][1];
-        const double Fbar = w * fsum;
-        const double Fc = F->bflux[((size_t)p * 2 + cslot) * fs + (size_t)dir * mx + k];
-        int i = dir == 0 ? 0 : dir == 1 ? mx - 1 : k;
-        int j = dir == 2 ? 0 : dir == 3 ? mx - 1 : k;
-        if (dir == 0 || dir == 2)
-          Q[OR_IDX(F, i, j)] += nu * (Fbar - Fc);
-        else
-          Q[OR_IDX(F, i, j)] += nu * (Fc - Fbar);
+        const double out = sf * F->bflux[((size_t)p * 2 + cslot) * fs + (size_t)dir * mx + k];
+        const int i = dir == 0 ? 0 : dir == 1 ? mx - 1 : k;
+        const int j = dir == 2 ? 0 : dir == 3 ? mx - 1 : k;
+        const double c = sphere ? dt / F->kappa[p * S2 + OR_IDX(F, i, j)] : dt / h;
+        Q[OR_IDX(F, i, j)] += c * (out - target);
       }
   }
 }
@@ -134,8 +174,8 @@ int or_step_global(or_forest* F, double t, double dt) {
   flux_store(F);
   F->fslot = 0;
   for (int p = 0; p < F->n; ++p) or_advance_leaf(F, p, t, dt);
-  if (F->P.reflux) /* every level took one step of dt: one fine substep */
-    for (int L = F->P.lmin; L < F->P.lmax; ++L) reflux_level(F, L, dt, 0, 1, 0.5);
+  if (F->P.reflux) /* every level took one step of dt: one fine step of the same dt */
+    for (int L = F->P.lmin; L <= F->P.lmax; ++L) reflux_level(F, L, dt, 0, 1, 1.0);
   return 0;
 }
 
@@ -152,9 +192,9 @@ static int mr_level(or_forest* F, int L, double t, double dt, double alpha) {
   if (L < F->P.lmax) {
     if (mr_level(F, L + 1, t, 0.5 * dt, 0.0)) return -1;
     if (mr_level(F, L + 1, t + 0.5 * dt, 0.5 * dt, 0.5)) return -1;
-    /* both fine substeps of this step are done: two slots of dt/2 */
-    if (F->P.reflux) reflux_level(F, L, dt, slot, 2, 0.25);
   }
+  /* after both finer substeps of this step (two slots of dt/2) */
+  if (F->P.reflux) reflux_level(F, L, dt, slot, 2, 0.5);
   return 0;
 }
 

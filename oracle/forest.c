@@ -150,10 +150,6 @@ or_forest* or_create(const or_params* P, int n, const int* leaves) {
     or_set_error("the deformational velocity is for the sphere, with nonzero T and T_f");
     return NULL;
   }
-  if (P->domain == OR_SPHERE && P->reflux) {
-    or_set_error("refluxing is built for the square domains");
-    return NULL;
-  }
   if (P->domain == OR_SPHERE && P->vel_kind != OR_VEL_ROTATION && P->vel_kind != OR_VEL_DEFORM) {
     or_set_error("the sphere takes the solid-body rotation or the deformational velocity");
     return NULL;

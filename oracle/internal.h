@@ -41,7 +41,8 @@ void or_sphere_metrics(const or_leaf* a, int mx, int mbc, const double* omega, d
 void or_sphere_psi_fluxes(const or_leaf* a, const or_params* P, double t, double* phix,
                           double* phiy);
 void or_claw_step_capacity(const or_params* P, double* q, int mx, int mbc, double dt,
-                           const double* kappa, const double* phix, const double* phiy);
+                           const double* kappa, const double* phix, const double* phiy,
+                           double* bflux);
 /* (re)compute the metric terms of every leaf (sphere only) */
 void or_update_metrics(or_forest* F);
 

@@ -14,8 +14,11 @@
  * Refluxing (or_params.reflux) is not in the paper: it is the standard
  * correction of Berger and Colella (J. Comput. Phys. 82, 1989), which replaces
  * the flux a coarse cell used at a coarse/fine face by the fine fluxes through
- * that face, summed over the face's fine cells and the fine substeps.  Pinned
- * by first-order closed forms and by exact conservation of mass.
+ * that face, summed over the face's fine cells and the fine substeps.  On the
+ * cubed sphere it also makes the fluxes through cube edges single-valued (the
+ * block of lower index keeps its flux, the other side takes it).  Pinned by
+ * first-order closed forms, by exact conservation of mass, and by the
+ * constant state where all fluxes of a step share one velocity field.
  *
  * The sphere's deformational flow (OR_VEL_DEFORM, Sec. 5.3) takes its edge
  * volume fluxes from the time-dependent streamfunction at each step's half
@@ -53,8 +56,9 @@ typedef struct {
   double vel_scale; /* every edge speed is multiplied by this (0 is read as 1) */
   int indicator;   /* regrid indicator: 0 max |grad q| / 2, 1 max q - min q (Sec. 5.1) */
   int smooth;      /* 1: smooth grading of target levels before refining (Sec. 3.3) */
-  int reflux;      /* 1: conservative correction of coarse cells at coarse/fine faces (square
-                      domains; an extension: the paper's scheme has none) */
+  int reflux;      /* 1: conservative correction of coarse cells at coarse/fine faces and, on
+                      the sphere, of one side of every cube edge (an extension: the paper's
+                      scheme has none) */
 } or_params;
 
 typedef struct or_forest or_forest;

@@ -222,7 +222,8 @@ void or_sphere_edge_fluxes(const or_forest* F, double t, double* phix, double* p
  *   transverse edges of its cell with 1/2 dt/kappa_cell phi_transverse,
  *   Q -= dt/kappa (F(i+1/2) - F(i-1/2) + G(j+1/2) - G(j-1/2)). */
 void or_claw_step_capacity(const or_params* P, double* q, int mx, int mbc, double dt,
-                           const double* kappa, const double* phix, const double* phiy) {
+                           const double* kappa, const double* phix, const double* phiy,
+                           double* bflux) {
   int S = mx + 2 * mbc, SE = S + 1;
   double* Fa = (double*)calloc((size_t)SE * SE, sizeof(double));
   double* Ga = (double*)calloc((size_t)SE * SE, sizeof(double));
@@ -285,6 +286,14 @@ void or_claw_step_capacity(const or_params* P, double* q, int mx, int mbc, doubl
         FX(i + 1, j - 1) -= 0.5 * dt / K(i, j - 1) * POS(PX(i + 1, j - 1)) * Mf;
         FX(i, j - 1) -= 0.5 * dt / K(i, j - 1) * NEG(PX(i, j - 1)) * Mf;
       }
+    }
+  /* the fluxes through the patch's faces, as the update below uses them */
+  if (bflux)
+    for (int k = 0; k < mx; ++k) {
+      bflux[k] = FX(0, k);
+      bflux[mx + k] = FX(mx, k);
+      bflux[2 * mx + k] = GY(k, 0);
+      bflux[3 * mx + k] = GY(k, mx);
     }
   for (int j = 0; j < mx; ++j)
     for (int i = 0; i < mx; ++i)
