@@ -254,3 +254,32 @@ def test_deformational_flow_option_checked():
     sq = fc.make_desc(domain=fc.PERIODIC, mx=8, lmin=1, lmax=2, velocity=("deform", 2.0, 0.5, 5.0))
     with pytest.raises(fc.FcError, match="INVALID_ARG"):
         fc.layout_check(sq, fc.uniform_leaves(1))
+
+
+@pytest.mark.parametrize("domain", ["walls", "periodic"])
+def test_finer_face_entries_order_their_halves(domain):
+    """Refluxing reads the two finer leaves of a face entry as n0: the half of
+    the face at the coarse leaf's cells 0..mx/2-1 along it, n1: the other
+    half.  Checked on adaptive layouts against the leaves' coordinates."""
+    import dataclasses
+    w = dataclasses.replace(synth.swirl(3, lmin=2, lmax=5, mx=8), domain=domain)
+    lv = oracle.initial_forest(w).leaves()
+    nb = fc.layout_neighbours(desc_for(w), lv)
+    seen = 0
+    for k, (f, b, l, x, y) in enumerate(lv):
+        for r in range(4):
+            kind, n0, n1 = nb[k, r, 0], nb[k, r, 1], nb[k, r, 2]
+            if kind != 2:
+                continue
+            seen += 1
+            m = 1 << (l + 1)
+            for half, n in ((0, n0), (1, n1)):
+                fl = lv[n]
+                assert fl[2] == l + 1
+                if r < 2:  # -x / +x face: the fine column beside it, rows 2y + half
+                    assert fl[4] == 2 * y + half
+                    assert fl[3] == ((2 * x - 1) % m if r == 0 else (2 * x + 2) % m)
+                else:      # -y / +y face: columns 2x + half
+                    assert fl[3] == 2 * x + half
+                    assert fl[4] == ((2 * y - 1) % m if r == 2 else (2 * y + 2) % m)
+    assert seen > 10
