@@ -26,9 +26,15 @@
  * solid-body rotation it reduces to at half period, and the return of a
  * tracer after one period.
  *
- * Parity unpinned (checked only against the same stated reading): the
- * multirate time interpolation of coarse data, the fill of the corner ghost
- * block at three-valent cube corners, and the capacity form on the sphere.
+ * The multirate time interpolation of coarse data is pinned by exactness on
+ * linear data (a linear field translated by a constant velocity through an
+ * adaptive forest).  The capacity form on the sphere is pinned through its
+ * behaviour: capacities tiling the sphere, a rotated tracer landing where
+ * the rotation puts it, convergence, the deformational flow's return.
+ *
+ * Parity unpinned (checked only against the same stated reading): the fill
+ * of the corner ghost block at three-valent cube corners, and the ghost-cell
+ * metrics of a sphere patch (its own mapping extended past its block).
  */
 #ifndef FC_ORACLE_H
 #define FC_ORACLE_H
