@@ -86,6 +86,7 @@ def lib():
     L.or_set_params.argtypes = [vp, ctypes.POINTER(_Params)]
     L.or_sphere_centres.argtypes = [vp, dp]
     L.or_get_kappa.argtypes = [vp, dp]
+    L.or_get_kappa_full.argtypes = [vp, dp]
     L.or_sphere_edge_fluxes.argtypes = [vp, ctypes.c_double, dp, dp]
     L.or_single_grid_periodic.argtypes = [ctypes.POINTER(_Params), ctypes.c_int, dp,
                                           ctypes.c_double, ctypes.c_double, ctypes.c_int]
@@ -276,6 +277,12 @@ class Forest:
         """Cell capacities (spherical areas) of the interior cells, (n, mx, mx)."""
         out = np.zeros((len(self), self.mx, self.mx))
         lib().or_get_kappa(self.h, _dptr(out))
+        return out
+
+    def kappa_full(self) -> np.ndarray:
+        """Cell capacities over the extended range (ghost cells included), (n, S, S)."""
+        out = np.zeros((len(self), self.S, self.S))
+        lib().or_get_kappa_full(self.h, _dptr(out))
         return out
 
     def edge_fluxes(self, t: float = 0.0):

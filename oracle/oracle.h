@@ -32,9 +32,12 @@
  * behaviour: capacities tiling the sphere, a rotated tracer landing where
  * the rotation puts it, convergence, the deformational flow's return.
  *
+ * The metrics of a sphere patch's ghost cells (its own mapping extended past
+ * its block) are pinned like its interior's: capacities against the
+ * solid-angle closed form, edge fluxes against the published velocity.
+ *
  * Parity unpinned (checked only against the same stated reading): the fill
- * of the corner ghost block at three-valent cube corners, and the ghost-cell
- * metrics of a sphere patch (its own mapping extended past its block).
+ * of the corner ghost block at three-valent cube corners.
  */
 #ifndef FC_ORACLE_H
 #define FC_ORACLE_H
@@ -121,6 +124,8 @@ int or_adjoint_multirate(or_forest* F, int ncoarse, double t0, double dt_coarse,
  * (n x mx x mx x 3) and the cell capacities (n x mx x mx) */
 void or_sphere_centres(const or_forest* F, double* xyz);
 void or_get_kappa(const or_forest* F, double* kappa);
+/* the capacities over the extended range, ghost cells included (n x S x S) */
+void or_get_kappa_full(const or_forest* F, double* kappa);
 
 /* cubed sphere: the edge volume fluxes of every leaf at time t (leaf order;
  * per leaf (S+1)*S x-edges then S*(S+1) y-edges over the extended range, as

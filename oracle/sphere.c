@@ -322,6 +322,11 @@ void or_sphere_centres(const or_forest* F, double* xyz) {
   }
 }
 
+void or_get_kappa_full(const or_forest* F, double* kappa) {
+  size_t n = (size_t)F->n * F->S * F->S;
+  for (size_t c = 0; c < n; ++c) kappa[c] = F->kappa ? F->kappa[c] : 0.0;
+}
+
 void or_get_kappa(const or_forest* F, double* kappa) {
   int mx = F->P.mx;
   for (int p = 0; p < F->n; ++p)

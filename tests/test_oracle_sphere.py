@@ -189,3 +189,29 @@ def test_error_after_one_revolution_falls_under_refinement():
     # the mass defect (ghost metrics from each block's own mapping) is a
     # truncation error and also shrinks
     assert drift[1] < 0.6 * drift[0], drift
+
+
+@pytest.mark.parametrize("level", [0, 1, 2, 3])
+def test_capacities_match_the_solid_angle_closed_form(level):
+    """Every capacity over the extended range (ghost cells: the patch's own
+    mapping continued past its block) equals the solid angle of its
+    rectangle [X1, X2] x [Y1, Y2] on the face plane at unit distance,
+    X = tan((x - 1/2) pi/2): F(X2, Y2) - F(X1, Y2) - F(X2, Y1) + F(X1, Y1)
+    with F(X, Y) = arctan(X Y / sqrt(1 + X^2 + Y^2)), evaluated in extended
+    precision (the four O(1) terms cancel to the cell's O(h^2) area)."""
+    mx, mbc = 8, 2
+    S = mx + 2 * mbc
+    F = oracle.Forest(oracle.params(oracle.SPHERE, mx, mbc, level, level,
+                                    ("rotation", 0.0, 0.0, 1.0)),
+                      oracle.uniform_leaves(level, nblocks=6))
+    K = F.kappa_full()
+    ld = np.longdouble
+    for p, (_, _, l, x0, y0) in enumerate(F.leaves()):
+        h = 1.0 / (mx * 2 ** int(l))
+        e = ((x0 * mx + np.arange(S + 1) - mbc) * h).astype(ld)
+        g = ((y0 * mx + np.arange(S + 1) - mbc) * h).astype(ld)
+        X = np.tan((e - ld(0.5)) * ld(np.pi) / ld(2))
+        Y = np.tan((g - ld(0.5)) * ld(np.pi) / ld(2))
+        Fxy = np.arctan(X[None, :] * Y[:, None] / np.sqrt(ld(1) + X[None, :] ** 2 + Y[:, None] ** 2))
+        A = (Fxy[1:, 1:] - Fxy[1:, :-1] - Fxy[:-1, 1:] + Fxy[:-1, :-1]).astype(np.float64)
+        assert np.abs(K[p] - A).max() <= 5e-14 * A.max()

@@ -70,11 +70,13 @@ def _edge_estimate(A, B, C, t):
     return ell * np.sum(_velocity(M, t) * n, -1)
 
 
-def _flux_errors(level, t):
+def _flux_errors(level, t, ghosts=False):
     F = _forest(level)
     px, py = F.edge_fluxes(t)
     N = _corners(F.leaves())
-    a, b = MBC, MBC + MX
+    # interior edges, or every edge of the extended range but the outermost
+    # (whose neighbouring corner for the normal's side lies outside)
+    a, b = (0, MX + 2 * MBC - 1) if ghosts else (MBC, MBC + MX)
     # x-edge (i, j) runs from corner (i, j) to (i, j+1); positive flux toward +x
     wx = _edge_estimate(N[:, a:b, a:b + 1], N[:, a + 1:b + 1, a:b + 1], N[:, a:b, a + 1:b + 2], t)
     # y-edge (i, j) runs from corner (i, j) to (i+1, j); positive flux toward +y
@@ -85,8 +87,11 @@ def _flux_errors(level, t):
 
 
 @pytest.mark.parametrize("t", [0.0, 0.13, 0.41])
-def test_edge_fluxes_follow_the_published_velocity(t):
-    e2, e3 = _flux_errors(2, t), _flux_errors(3, t)
+@pytest.mark.parametrize("ghosts", [False, True])
+def test_edge_fluxes_follow_the_published_velocity(t, ghosts):
+    """(with ghosts: the edges of the ghost cells too, the patch's own mapping
+    extended past its block)"""
+    e2, e3 = _flux_errors(2, t, ghosts), _flux_errors(3, t, ghosts)
     assert e2 < 1e-3
     assert e3 < 0.3 * e2  # second order: about 1/4
 
