@@ -256,6 +256,16 @@ fc_status fc_layout_neighbours(const fc_forest_desc* desc, int nleaves, const in
 fc_status fc_layout_regrid(const fc_forest_desc* desc, int nleaves, const int* leaves,
                            const double* delta, double tau_refine, double tau_coarsen,
                            const int* lmax_per_forest, int cap, int* out_leaves, int* nout);
+/* fc_layout_reflux: what refluxing exchanges (Berger and Colella's
+ * correction, an extension of the paper's scheme), from the neighbour table
+ * and its index transforms.  out: host, nleaves * 4 * mx rows of 5 ints
+ * (kind, leaf across, its face on the shared edge, j0, j1) per leaf (field
+ * order), face (-x, +x, -y, +y) and face cell along the face's axis: kind 1
+ * the leaf across is finer (j0, j1: its cells beside the lower and upper half
+ * of the cell), 2 the leaf across has the same level and lies across a cube
+ * edge on a block of lower index (its flux is the one kept; j0: its cell),
+ * 0 nothing (-1 elsewhere); faces 0 -x, 1 +x, 2 -y, 3 +y. */
+fc_status fc_layout_reflux(const fc_forest_desc* desc, int nleaves, const int* leaves, int* out);
 
 /* Per-phase device timers (the paper's run-time breakdown, Sec. 5: advance,
  * ghost fill, regrid).  While enabled, every kernel launch of a phase is

@@ -87,6 +87,7 @@ def lib():
     L.or_sphere_centres.argtypes = [vp, dp]
     L.or_get_kappa.argtypes = [vp, dp]
     L.or_get_kappa_full.argtypes = [vp, dp]
+    L.or_reflux_pairs.argtypes = [vp, ip]
     L.or_sphere_edge_fluxes.argtypes = [vp, ctypes.c_double, dp, dp]
     L.or_single_grid_periodic.argtypes = [ctypes.POINTER(_Params), ctypes.c_int, dp,
                                           ctypes.c_double, ctypes.c_double, ctypes.c_int]
@@ -277,6 +278,13 @@ class Forest:
         """Cell capacities (spherical areas) of the interior cells, (n, mx, mx)."""
         out = np.zeros((len(self), self.mx, self.mx))
         lib().or_get_kappa(self.h, _dptr(out))
+        return out
+
+    def reflux_pairs(self) -> np.ndarray:
+        """What refluxing exchanges per (leaf, face, face cell): (n, 4, mx, 5) of
+        (kind, leaf across, its face, j0, j1); see or_reflux_pairs."""
+        out = np.zeros((len(self), 4, self.mx, 5), dtype=np.int32)
+        lib().or_reflux_pairs(self.h, _iptr(out))
         return out
 
     def kappa_full(self) -> np.ndarray:

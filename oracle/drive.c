@@ -117,6 +117,58 @@ static int across(const or_forest* F, const or_leaf* a, int dir, double along, d
  * across are found by locating points beyond the face.  Faces are corrected
  * in the order -x, +x, -y, +y (a corner cell takes two).
  */
+/* What refluxing exchanges at coarse face cell k of leaf p, face dir: kind 1
+ * (finer across: leaf *pn's face *g, its cells *j0 and *j1 beside the lower
+ * and upper half of cell k), kind 2 (same level across a cube edge, this side
+ * on the block of higher index: leaf *pn's face *g, cell *j0), else 0. */
+static int reflux_pair(const or_forest* F, int p, int dir, int k, int* pn, int* g, int* j0,
+                       int* j1) {
+  const or_leaf* a = &F->lv[p];
+  const double h = cell_h(F, a->l);
+  int gg, jn;
+  /* the level across: at a quarter cell beyond the face, a fine cell's
+   * centre, or inside a same-size or coarser cell */
+  int n = across(F, a, dir, (k + 0.5) * h, 0.25 * h, 0.0, &gg, &jn);
+  if (n < 0) return 0;
+  if (F->lv[n].l == a->l + 1) {
+    /* the two fine cells across coarse cell k */
+    int g0, g1, i0, i1;
+    int n1 = across(F, a, dir, (k + 0.75) * h, 0.25 * h, 0.5 * h, &g1, &i1);
+    int n0 = across(F, a, dir, (k + 0.25) * h, 0.25 * h, 0.5 * h, &g0, &i0);
+    if (n0 != n || n1 != n || g0 != g1) return 0;
+    *pn = n;
+    *g = g0;
+    *j0 = i0;
+    *j1 = i1;
+    return 1;
+  }
+  if (F->lv[n].l == a->l && F->P.domain == OR_SPHERE && F->lv[n].b < a->b) {
+    n = across(F, a, dir, (k + 0.5) * h, 0.5 * h, h, &gg, &jn);
+    if (n < 0) return 0;
+    *pn = n;
+    *g = gg;
+    *j0 = jn;
+    *j1 = -1;
+    return 2;
+  }
+  return 0;
+}
+
+void or_reflux_pairs(const or_forest* F, int* out) {
+  const int mx = F->P.mx;
+  for (int p = 0; p < F->n; ++p)
+    for (int dir = 0; dir < 4; ++dir)
+      for (int k = 0; k < mx; ++k) {
+        int* o = out + (((size_t)p * 4 + dir) * mx + k) * 5;
+        int pn = -1, g = -1, j0 = -1, j1 = -1;
+        o[0] = reflux_pair(F, p, dir, k, &pn, &g, &j0, &j1);
+        o[1] = o[0] ? pn : -1;
+        o[2] = o[0] ? g : -1;
+        o[3] = o[0] ? j0 : -1;
+        o[4] = o[0] == 1 ? j1 : -1;
+      }
+}
+
 static void reflux_level(or_forest* F, int L, double dt, int cslot, int nfs, double wt) {
   const int mx = F->P.mx;
   const int sphere = F->P.domain == OR_SPHERE;
@@ -130,33 +182,19 @@ static void reflux_level(or_forest* F, int L, double dt, int cslot, int nfs, dou
     for (int dir = 0; dir < 4; ++dir)
       for (int k = 0; k < mx; ++k) {
         const double sf = (dir & 1) ? 1.0 : -1.0;
-        int g, jn;
+        int pn, g, j0, j1;
+        const int kind = reflux_pair(F, p, dir, k, &pn, &g, &j0, &j1);
+        if (!kind) continue;
+        const double sg = (g & 1) ? 1.0 : -1.0;
         double target;
-        /* the level across: at a quarter cell beyond the face, a fine cell's
-         * centre, or inside a same-size or coarser cell */
-        int pn = across(F, a, dir, (k + 0.5) * h, 0.25 * h, 0.0, &g, &jn);
-        if (pn < 0) continue;
-        if (F->lv[pn].l == L + 1) {
-          /* the two fine cells across coarse cell k */
-          int g1, j1;
-          int pn1 = across(F, a, dir, (k + 0.75) * h, 0.25 * h, 0.5 * h, &g1, &j1);
-          int g0, j0;
-          int pn0 = across(F, a, dir, (k + 0.25) * h, 0.25 * h, 0.5 * h, &g0, &j0);
-          if (pn0 != pn || pn1 != pn || g0 != g1) continue;
-          g = g0;
+        if (kind == 1) {
           double fsum = 0.0;
           for (int s = 0; s < nfs; ++s)
             fsum += F->bflux[((size_t)pn * 2 + s) * fs + (size_t)g * mx + j0] +
                     F->bflux[((size_t)pn * 2 + s) * fs + (size_t)g * mx + j1];
-          const double sg = (g & 1) ? 1.0 : -1.0;
           target = -sg * (w * fsum);
-        } else if (F->lv[pn].l == L && sphere && F->lv[pn].b != a->b && F->lv[pn].b < a->b) {
-          pn = across(F, a, dir, (k + 0.5) * h, 0.5 * h, h, &g, &jn);
-          if (pn < 0) continue;
-          const double sg = (g & 1) ? 1.0 : -1.0;
-          target = -sg * F->bflux[((size_t)pn * 2 + cslot) * fs + (size_t)g * mx + jn];
         } else {
-          continue;
+          target = -sg * F->bflux[((size_t)pn * 2 + cslot) * fs + (size_t)g * mx + j0];
         }
         const double out = sf * F->bflux[((size_t)p * 2 + cslot) * fs + (size_t)dir * mx + k];
         const int i = dir == 0 ? 0 : dir == 1 ? mx - 1 : k;

@@ -127,6 +127,13 @@ void or_get_kappa(const or_forest* F, double* kappa);
 /* the capacities over the extended range, ghost cells included (n x S x S) */
 void or_get_kappa_full(const or_forest* F, double* kappa);
 
+/* refluxing's pairing: per leaf, face (-x, +x, -y, +y) and face cell, 5
+ * ints (kind, leaf across, its face on the edge, j0, j1): kind 1 finer
+ * across (j0, j1: its cells beside the lower and upper half of the cell),
+ * 2 same level across a cube edge with this side on the block of higher index
+ * (j0: its cell), 0 none (-1 elsewhere) */
+void or_reflux_pairs(const or_forest* F, int* out);
+
 /* cubed sphere: the edge volume fluxes of every leaf at time t (leaf order;
  * per leaf (S+1)*S x-edges then S*(S+1) y-edges over the extended range, as
  * or_sphere_metrics lays them out) */

@@ -51,6 +51,7 @@ SIGNATURES = {
     "fc_forest_mass": (ctypes.c_int, [_vp, _dp, _vp]),
     "fc_layout_check": (ctypes.c_int, [_DP, ctypes.c_int, _ip]),
     "fc_layout_neighbours": (ctypes.c_int, [_DP, ctypes.c_int, _ip, _ip]),
+    "fc_layout_reflux": (ctypes.c_int, [_DP, ctypes.c_int, _ip, _ip]),
     "fc_layout_regrid": (ctypes.c_int, [_DP, ctypes.c_int, _ip, _dp, ctypes.c_double,
                                         ctypes.c_double, _ip, ctypes.c_int, _ip, _ip]),
     "fc_timers_enable": (ctypes.c_int, [_vp, ctypes.c_int]),

@@ -1813,6 +1813,15 @@ fc_status fc_layout_neighbours(const fc_forest_desc* desc, int nleaves, const in
   return FC_OK;
 }
 
+fc_status fc_layout_reflux(const fc_forest_desc* desc, int nleaves, const int* leaves, int* out) {
+  if (!out) return fail(FC_ERR_INVALID_ARG, "null output");
+  HostForest H;
+  fc_status st = host_layout(desc, nleaves, leaves, &H);
+  if (st != FC_OK) return st;
+  const std::string err = H.reflux_pairs(out);
+  return err.empty() ? FC_OK : fail(FC_ERR_STATE, err);
+}
+
 fc_status fc_layout_regrid(const fc_forest_desc* desc, int nleaves, const int* leaves,
                            const double* delta, double tau_refine, double tau_coarsen,
                            const int* lmax_per_forest, int cap, int* out_leaves, int* nout) {

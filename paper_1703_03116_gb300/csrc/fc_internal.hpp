@@ -258,6 +258,14 @@ struct HostForest {
   // feeds_finer
   std::string neighbour_rows(int kb, int ke);
   std::string work_lists();
+  // Refluxing's pairing, from the neighbour table and its index transforms:
+  // per leaf (field order), face (-x, +x, -y, +y) and face cell k, 5 ints
+  // (kind, leaf across (field index), its face on the shared edge, j0, j1):
+  // kind 1 finer across (j0, j1: its cells beside the lower and upper half
+  // of cell k along this leaf's face), 2 same level across a cube edge with
+  // this leaf on the block of higher index (j0: its cell), 0 none (-1
+  // elsewhere).  Returns an empty string or an error.
+  std::string reflux_pairs(int* out) const;
   // dense leaf lookup (when `dense`): owner[own_off[f] + (b << 2 lo) +
   // (Y << lo) + X] is the leaf covering cell (X, Y) of block b at level
   // lo = own_lo[f], forest f's finest occupied level

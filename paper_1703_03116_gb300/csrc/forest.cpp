@@ -404,6 +404,81 @@ std::string HostForest::neighbour_rows(int kb, int ke) {
   return "";
 }
 
+// the face whose outward normal is (nx, ny): 0 -x, 1 +x, 2 -y, 3 +y
+static int face_of_normal(int nx, int ny) {
+  return nx < 0 ? 0 : nx > 0 ? 1 : ny < 0 ? 2 : 3;
+}
+
+std::string HostForest::reflux_pairs(int* out) const {
+  const int mx = desc.mx;
+  const bool sphere = desc.domain == FC_DOMAIN_SPHERE;
+  for (int k = 0; k < npatch(); ++k) {
+    const Leaf& a = leaves[k];
+    const int p = dev_of[k];
+    const int X0 = a.x * mx, Y0 = a.y * mx;
+    for (int dir = 0; dir < 4; ++dir) {
+      const NbrEntry& e = nbr[(size_t)p * 8 + dir];
+      // the neighbour's outward normal on the shared edge: back along the
+      // direction of travel, in its block's frame
+      int dx, dy;
+      apply_code_host(e.a, kDirX[dir], kDirY[dir], &dx, &dy);
+      const int g = face_of_normal(-dx, -dy);
+      for (int c = 0; c < mx; ++c) {
+        int* o = out + (((size_t)k * 4 + dir) * mx + c) * 5;
+        o[0] = 0;
+        o[1] = o[2] = o[3] = o[4] = -1;
+        // the level-l ghost cell across the face beside cell c
+        const int Ix = dir == 0 ? X0 - 1 : dir == 1 ? X0 + mx : X0 + c;
+        const int Iy = dir == 2 ? Y0 - 1 : dir == 3 ? Y0 + mx : Y0 + c;
+        int u, v;
+        apply_code_host(e.a, Ix, Iy, &u, &v);
+        u += e.fx;
+        v += e.fy;
+        if (e.kind == NB_FINE) {
+          int j[2], leaf = -1;
+          for (int half = 0; half < 2; ++half) {
+            // the fine cell of the ghost cell beside this leaf, at the lower
+            // or upper half of cell c along the face, in this leaf's frame
+            const int ox = dir == 0 ? 1 : dir == 1 ? 0 : half;
+            const int oy = dir == 2 ? 1 : dir == 3 ? 0 : half;
+            int du, dv;
+            apply_code_host(e.a, ox, oy, &du, &dv);
+            const int fx = 2 * u + ((e.a & 2) ? 1 + du : du);
+            const int fy = 2 * v + ((e.a & 4) ? 1 + dv : dv);
+            int n = -1, lx = 0, ly = 0;
+            if (fx / mx == e.x0 && fy / mx == e.y0 && fx >= 0 && fy >= 0) {
+              n = e.n0;
+              lx = fx - e.x0 * mx;
+              ly = fy - e.y0 * mx;
+            } else if (e.n1 >= 0 && fx >= 0 && fy >= 0 && fx / mx == e.x1 && fy / mx == e.y1) {
+              n = e.n1;
+              lx = fx - e.x1 * mx;
+              ly = fy - e.y1 * mx;
+            }
+            if (n < 0 || (leaf >= 0 && n != leaf)) return "reflux pairing: fine cell outside the face's leaves";
+            leaf = n;
+            j[half] = g < 2 ? ly : lx;
+          }
+          o[0] = 1;
+          o[1] = api_of[leaf];
+          o[2] = g;
+          o[3] = j[0];
+          o[4] = j[1];
+        } else if (e.kind == NB_SAME && sphere && leaves[api_of[e.n0]].b < a.b) {
+          const int lx = u - e.x0 * mx, ly = v - e.y0 * mx;
+          if (lx < 0 || lx >= mx || ly < 0 || ly >= mx)
+            return "reflux pairing: ghost cell outside the same-size leaf";
+          o[0] = 2;
+          o[1] = api_of[e.n0];
+          o[2] = g;
+          o[3] = g < 2 ? ly : lx;
+        }
+      }
+    }
+  }
+  return "";
+}
+
 std::string HostForest::work_lists() {
   const int n = npatch();
   list_all.resize(n);

@@ -253,6 +253,15 @@ def layout_neighbours(desc: Desc, leaves) -> np.ndarray:
     return out
 
 
+def layout_reflux(desc: Desc, leaves) -> np.ndarray:
+    """Refluxing's pairing (host): (n, 4, mx, 5) ints (kind, leaf across, its
+    face, j0, j1) per leaf, face and face cell; see fc_layout_reflux."""
+    leaves = _iarr(leaves).reshape(-1, 5)
+    out = np.zeros((len(leaves), 4, desc.mx, 5), dtype=np.int32)
+    check(load().fc_layout_reflux(ctypes.byref(desc), len(leaves), _ip(leaves), _ip(out)))
+    return out
+
+
 def layout_regrid(desc: Desc, leaves, delta, tau_r: float, tau_c: float,
                   lmax_f: Optional[Sequence[int]] = None) -> np.ndarray:
     leaves = _iarr(leaves).reshape(-1, 5)

@@ -172,3 +172,29 @@ def test_input_generator_centres_match_the_oracle():
     w, F = adaptive_sphere(0)
     X = synth.sphere_cell_centres(F.leaves(), w.mx)
     np.testing.assert_allclose(X, F.sphere_centres(), rtol=0, atol=1e-15)
+
+
+@pytest.mark.parametrize("case", ["walls", "periodic", "sphere rotation", "sphere deformational"])
+def test_reflux_pairing_matches_oracle(case):
+    """What refluxing exchanges per face cell (the finer leaf's face and its
+    two cells across, or across a cube edge the same-level leaf's face and
+    cell), from the product's neighbour table and index transforms, equals
+    what the oracle finds by locating points beyond each face."""
+    import dataclasses
+    if case in ("walls", "periodic"):
+        w = dataclasses.replace(synth.swirl(3, lmin=2, lmax=5, mx=8), domain=case)
+    elif case == "sphere rotation":
+        w = synth.sphere(seed=1, lmin=1, lmax=3, mx=8)
+    else:
+        w = synth.sphere_deform(seed=2, lmin=1, lmax=4, mx=8)
+    F = oracle.initial_forest(w)
+    lv = F.leaves()
+    ref = F.reflux_pairs()
+    dom = {"walls": fc.WALLS, "periodic": fc.PERIODIC, "sphere": fc.SPHERE}[w.domain]
+    d = fc.make_desc(domain=dom, mx=w.mx, lmin=w.lmin, lmax=w.lmax, dtype=fc.F64,
+                     velocity=w.velocity)
+    got = fc.layout_reflux(d, lv)
+    assert (ref[..., 0] == 1).sum() > 0
+    if w.domain == "sphere":
+        assert (ref[..., 0] == 2).sum() > 0
+    np.testing.assert_array_equal(got, ref)
