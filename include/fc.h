@@ -104,7 +104,7 @@ typedef struct {
   int limiter;
   int transverse;
   int indicator;  /* regrid indicator: 0 max |grad q| / 2, 1 max q - min q (Sec. 5.1) */
-  int smooth;     /* 1: smooth grading of the target levels (Sec. 3.3; square domains) */
+  int smooth;     /* 1: smooth grading of the target levels (Sec. 3.3) */
   int reflux;     /* 1: refluxing at coarse/fine faces (an extension; square domains) */
 } fc_forest_desc;
 

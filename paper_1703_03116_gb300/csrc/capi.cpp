@@ -811,8 +811,6 @@ fc_status check_desc(const fc_forest_desc* d) {
     return fail(FC_ERR_INVALID_ARG, "bad scheme options");
   if (d->indicator < 0 || d->indicator > 1 || d->smooth < 0 || d->smooth > 1)
     return fail(FC_ERR_INVALID_ARG, "bad regrid policy");
-  if (d->smooth && d->domain == FC_DOMAIN_SPHERE)
-    return fail(FC_ERR_INVALID_ARG, "smooth grading is built for the square domains");
   if (d->reflux < 0 || d->reflux > 1 || (d->reflux && d->domain == FC_DOMAIN_SPHERE))
     return fail(FC_ERR_INVALID_ARG, "refluxing is built for the square domains (reflux 0 or 1)");
   return FC_OK;
