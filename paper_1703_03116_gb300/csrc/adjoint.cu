@@ -31,6 +31,8 @@
 // different levels can run side by side wherever their forward substeps
 // could.
 // The adjoint tiles use the patch-store layout ((mx+4)^2 per patch).
+#include <atomic>
+
 #include "ghost_gather.cuh"
 
 namespace fc {
@@ -619,13 +621,14 @@ cudaError_t adj_advance_level(const DevForest<real>& D, int L, int p0, int p1, d
   // substeps run beside it (1024 threads, one CTA per SM, measured slower
   // once the levels overlapped; 256 too)
   constexpr int NT = MX >= 16 ? 512 : 256;
-  static bool attr = false;
+  // set once per process; concurrent first calls both set it (idempotent)
+  static std::atomic<bool> attr{false};
   constexpr size_t smem = adj_smem<real, MX>();
-  if (!attr) {
+  if (!attr.load(std::memory_order_acquire)) {
     cudaError_t e = cudaFuncSetAttribute(adj_advance_kernel<real, MX, NT>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    attr = true;
+    attr.store(true, std::memory_order_release);
   }
   if (p1 <= p0) return cudaSuccess;
   AdvArgs al{};

@@ -21,6 +21,7 @@
 // transverse increments 1/2 dt/kappa_cell phi^-+ (fluctuation entering that
 // cell), and the update Q -= dt/kappa (F(i+1/2) - F(i-1/2) + G(j+1/2) -
 // G(j-1/2)).
+#include <atomic>
 #include <cstdint>
 
 #include "ghost_gather.cuh"
@@ -277,13 +278,14 @@ constexpr size_t staged_smem() {
 template <typename real, int MX, int NT, bool CAP>
 cudaError_t staged_launch_t(const DevForest<real>& D, int p0, int p1, const AdvArgs& a, int* err,
                             cudaStream_t s) {
-  static bool attr_set = false;
+  // set once per process; concurrent first calls both set it (idempotent)
+  static std::atomic<bool> attr_set{false};
   constexpr size_t smem = staged_smem<real, MX, CAP>();
-  if (!attr_set) {
+  if (!attr_set.load(std::memory_order_acquire)) {
     cudaError_t e = cudaFuncSetAttribute(advance_staged_kernel<real, MX, NT, CAP>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    attr_set = true;
+    attr_set.store(true, std::memory_order_release);
   }
   advance_staged_kernel<real, MX, NT, CAP><<<p1 - p0, NT, smem, s>>>(D, p0, p1, a, err);
   ++launch_counter();

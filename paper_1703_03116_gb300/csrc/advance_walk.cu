@@ -17,6 +17,7 @@
 //  * Tiles arrive by 1D TMA bulk copies (cp.async.bulk + mbarrier), double
 //    buffered per warp: the next group of patches is in flight while the
 //    current one is computed.  Grids are persistent (CTAs loop over groups).
+#include <atomic>
 #include <cstdint>
 
 #include "ghost_gather.cuh"
@@ -267,7 +268,9 @@ __global__ void __launch_bounds__(NW * 32) advance_walk_kernel(DevForest<real> D
 template <typename real, int MX, int NW, bool SWIRL, int NB>
 cudaError_t walk_launch(const DevForest<real>& D, int p0, int p1, const AdvArgs& a, int* err,
                         cudaStream_t s) {
-  static int max_ctas = 0;
+  // computed once per process; concurrent first calls compute the same value
+  static std::atomic<int> max_ctas_once{0};
+  int max_ctas = max_ctas_once.load(std::memory_order_acquire);
   constexpr size_t smem = sizeof(real) * (size_t)NW * warp_reals<real, MX, NB>();
   auto kern = advance_walk_kernel<real, MX, NW, SWIRL, NB>;
   if (max_ctas == 0) {
@@ -280,6 +283,7 @@ cudaError_t walk_launch(const DevForest<real>& D, int p0, int p1, const AdvArgs&
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NW * 32, smem);
     if (e != cudaSuccess) return e;
     max_ctas = nsm * (per_sm > 0 ? per_sm : 1);
+    max_ctas_once.store(max_ctas, std::memory_order_release);
   }
   constexpr int PPW = 32 / MX;
   const int groups = (p1 - p0 + PPW - 1) / PPW;

@@ -25,6 +25,7 @@
 // flux psi(b) - psi(a) = k c (s_b - s_a)(s_b + s_a) - (2 pi/T_f)(Z_b - Z_a) is
 // again formed from the end points' differences.  Its fluxes are refreshed
 // for each substep's half time from the corners kept per patch.
+#include <atomic>
 #include <cmath>
 
 #include "device_util.cuh"
@@ -188,12 +189,13 @@ cudaError_t launch_sphere_metrics(const PatchMeta* meta, int npatch, int mx, con
   if (npatch <= 0) return cudaSuccess;
   const int SN = mx + 2 * kMbc + 1;
   const size_t smem = sizeof(double) * 3 * (size_t)SN * SN;
-  static bool attr_set = false;
-  if (!attr_set) {
+  // set once per process; concurrent first calls both set it (idempotent)
+  static std::atomic<bool> attr_set{false};
+  if (!attr_set.load(std::memory_order_acquire)) {
     cudaError_t e = cudaFuncSetAttribute(metrics_kernel,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
     if (e != cudaSuccess) return e;
-    attr_set = true;
+    attr_set.store(true, std::memory_order_release);
   }
   if (smem > 64 * 1024) return cudaErrorInvalidValue;
   const int grid = npatch < 65535 * 8 ? npatch : 65535 * 8;
