@@ -16,7 +16,7 @@ together -- one launch per level substep covers every forest -- at 32^2 and
 the adjoint (gradient of a final-time misfit over 25 coarse multirate steps).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--mode full|batched|sphere|adjoint]
+                    [--mode full|batched|sphere|sphere_deform|adjoint|sweep]
 
 Multi-GPU (torchrun): each rank advances its own independent forest (seeded
 by rank): weak scaling, no collective on the data path.  Prints one JSON line
@@ -48,6 +48,10 @@ WORKLOAD = ("adaptive swirl forest, levels 2-6, 32x32 patches, mbc 2, walls, MC 
 SPHERE_WORKLOAD = ("cubed sphere (6 trees), levels 1-7, 32x32 patches, mbc 2, solid-body rotation "
                    "|omega| = 2 pi, two cosine bells + slotted cylinder, capacity form, CFL 0.9, "
                    "multirate, regrid every 4 coarse steps")
+SPHERE_DEFORM_WORKLOAD = ("cubed sphere (6 trees), levels 2-6, 32x32 patches, mbc 2, the deformational "
+                          "flow of Sec. 5.3 (kappa 2, T 0.5, T_f 5; fluxes refreshed per substep), two "
+                          "slotted cylinders, dt 2.5e-3 at level 2, multirate, max - min tagging "
+                          "(0.25 / 0.001), regrid every coarse step")
 
 
 def parse():
@@ -59,7 +63,8 @@ def parse():
     ap.add_argument("--dtype", choices=["f32", "f64"], default="f32")
     ap.add_argument("--no-variants", action="store_true", help="skip FP64, batched and CPU legs")
     ap.add_argument("--ensemble", type=int, default=256, help="forests in the batched variant")
-    ap.add_argument("--mode", choices=["full", "batched", "sphere", "adjoint", "sweep"],
+    ap.add_argument("--mode", choices=["full", "batched", "sphere", "sphere_deform", "adjoint",
+                                       "sweep"],
                     default="full",
                     help="batched: time only the ensemble (a case sized for profiling)")
     return ap.parse_args()
@@ -186,7 +191,9 @@ class Runner:
         _, self.dtc = synth.time_step(w, self.lmax)
         domain = {"walls": fc.WALLS, "periodic": fc.PERIODIC, "sphere": fc.SPHERE}[w.domain]
         desc = fc.make_desc(domain=domain, mx=w.mx, lmin=w.lmin, lmax=self.lmax, dtype=dtype,
-                            velocity=w.velocity, nforests=len(workloads))
+                            velocity=w.velocity, nforests=len(workloads),
+                            indicator={"gradient": 0, "maxmin": 1}[w.indicator],
+                            smooth=int(w.smooth))
         self.F = fc.initial_forest(desc, q0_fn(workloads), lmax_f=self.lmax_f,
                                    tau_r=w.tau_refine, tau_c=w.tau_coarsen)
         # pick the patch-update kernel per launch size on this layout (untimed setup)
@@ -451,11 +458,14 @@ def run_ours(args):
         if dist is not None:
             dist.destroy_process_group()
         return
-    if args.mode in ("batched", "sphere"):
+    if args.mode in ("batched", "sphere", "sphere_deform"):
         if args.mode == "batched":
             ws = synth.ensemble(args.ensemble, seed=rank, mx=32)
             label = (f"{args.ensemble} independent swirl forests, levels 2 to 4/5/6, "
                      "32x32 patches")
+        elif args.mode == "sphere_deform":
+            ws = [synth.sphere_deform(seed=rank, lmin=2, lmax=6, mx=32)]
+            label = SPHERE_DEFORM_WORKLOAD
         else:
             ws = [synth.sphere(seed=rank)]
             label = SPHERE_WORKLOAD
