@@ -283,3 +283,31 @@ def test_finer_face_entries_order_their_halves(domain):
                     assert fl[3] == 2 * x + half
                     assert fl[4] == ((2 * y - 1) % m if r == 2 else (2 * y + 2) % m)
     assert seen > 10
+
+
+@pytest.mark.parametrize("domain", ["walls", "periodic"])
+def test_reflux_kernel_indexing_is_the_oracle_pairing(domain):
+    """On the square domains the refluxing kernel pairs coarse face cell k of
+    a finer face with fine leaf n0 (k < mx/2) or n1 (the face entry's two
+    leaves), the fine leaf's opposite face (dir ^ 1) and its cells
+    2k - half*mx and the next.  That indexing, applied to the neighbour
+    table, equals the oracle's geometric pairing."""
+    import dataclasses
+    w = dataclasses.replace(synth.swirl(4, lmin=2, lmax=5, mx=8), domain=domain)
+    F = oracle.initial_forest(w)
+    lv = F.leaves()
+    ref = F.reflux_pairs()
+    nb = fc.layout_neighbours(desc_for(w), lv)
+    mx = w.mx
+    got = np.full_like(ref, -1)
+    got[..., 0] = 0
+    for k in range(len(lv)):
+        for d in range(4):
+            kind, n0, n1 = nb[k, d, 0], nb[k, d, 1], nb[k, d, 2]
+            if kind != 2:
+                continue
+            for c in range(mx):
+                half = 1 if c >= mx // 2 else 0
+                jf = 2 * c - half * mx
+                got[k, d, c] = (1, n1 if half else n0, d ^ 1, jf, jf + 1)
+    np.testing.assert_array_equal(got, ref)
