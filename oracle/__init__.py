@@ -18,6 +18,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SO = os.path.join(_HERE, "liboracle.so")
+_SO_OMP = os.path.join(_HERE, "liboracle_omp.so")  # the same sources, patch loops over threads
 _SRC = ["forest.c", "ghost.c", "claw.c", "drive.c", "adjoint.c", "sphere.c"]
 _HDR = ["oracle.h", "internal.h"]
 
@@ -25,20 +26,23 @@ WALLS, PERIODIC, SPHERE = 0, 1, 2
 VEL_CONST, VEL_SWIRL, VEL_ROTATION, VEL_DEFORM = 0, 1, 2, 3
 
 
-def build(force: bool = False) -> str:
-    """Compile the oracle into liboracle.so (skipped when up to date)."""
+def build(force: bool = False, openmp: bool = False) -> str:
+    """Compile the oracle into liboracle.so (skipped when up to date); with
+    openmp=True the same sources into liboracle_omp.so with -fopenmp, whose
+    patch loops run on all host threads (for the all-cores CPU baseline)."""
+    so = _SO_OMP if openmp else _SO
     srcs = [os.path.join(_HERE, s) for s in _SRC]
     deps = srcs + [os.path.join(_HERE, h) for h in _HDR]
-    if not force and os.path.exists(_SO):
-        so_t = os.path.getmtime(_SO)
+    if not force and os.path.exists(so):
+        so_t = os.path.getmtime(so)
         if all(os.path.getmtime(d) <= so_t for d in deps):
-            return _SO
-    tmp = _SO + f".tmp{os.getpid()}"
+            return so
+    tmp = so + f".tmp{os.getpid()}"
     cmd = ["gcc", "-O2", "-std=gnu11", "-ffp-contract=off", "-fPIC", "-shared",
-           "-Wall", *srcs, "-lm", "-o", tmp]
+           "-Wall", *(["-fopenmp"] if openmp else []), *srcs, "-lm", "-o", tmp]
     subprocess.run(cmd, check=True)
-    os.replace(tmp, _SO)
-    return _SO
+    os.replace(tmp, so)
+    return so
 
 
 class _Params(ctypes.Structure):
@@ -55,14 +59,35 @@ class _Params(ctypes.Structure):
 
 
 _lib = None
+_libs = {}
+
+
+def use_openmp(on: bool = True) -> None:
+    """Select the library that forests created from now on use: the OpenMP
+    build (patch loops on all host threads) or the plain one."""
+    global _lib
+    _lib = _load(on)
+
+
+def threads() -> int:
+    """Host threads the OpenMP build's patch loops use (1 for the plain build)."""
+    if _lib is None or _lib is not _libs.get(True):
+        return 1
+    return int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
 
 
 def lib():
     global _lib
-    if _lib is not None:
-        return _lib
-    build()
-    L = ctypes.CDLL(_SO)
+    if _lib is None:
+        _lib = _load(False)
+    return _lib
+
+
+def _load(openmp: bool):
+    if openmp in _libs:
+        return _libs[openmp]
+    so = build(openmp=openmp)
+    L = ctypes.CDLL(so)
     vp, ip, dp = ctypes.c_void_p, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)
     L.or_create.restype = vp
     L.or_create.argtypes = [ctypes.POINTER(_Params), ctypes.c_int, ip]
@@ -91,12 +116,16 @@ def lib():
     L.or_sphere_edge_fluxes.argtypes = [vp, ctypes.c_double, dp, dp]
     L.or_single_grid_periodic.argtypes = [ctypes.POINTER(_Params), ctypes.c_int, dp,
                                           ctypes.c_double, ctypes.c_double, ctypes.c_int]
+    for f in ("or_u_edge", "or_v_edge"):
+        getattr(L, f).restype = ctypes.c_double
+        getattr(L, f).argtypes = [ctypes.POINTER(_Params), ctypes.c_double, ctypes.c_double,
+                                  ctypes.c_long, ctypes.c_long, ctypes.c_int, ctypes.c_int]
     L.or_mc_phi.restype = ctypes.c_double
     L.or_mc_phi.argtypes = [ctypes.c_double]
     L.or_minmod.restype = ctypes.c_double
     L.or_minmod.argtypes = [ctypes.c_double, ctypes.c_double]
     L.or_last_error.restype = ctypes.c_char_p
-    _lib = L
+    _libs[openmp] = L
     return L
 
 
@@ -157,16 +186,21 @@ class Forest:
 
     def __init__(self, prm: _Params, leaves: np.ndarray):
         self.prm = prm
+        self.L = lib()  # the build (plain or OpenMP) this forest lives in
         leaves = np.ascontiguousarray(leaves, dtype=np.int32).reshape(-1, 5)
-        h = lib().or_create(ctypes.byref(prm), len(leaves), _iptr(leaves))
+        h = self.L.or_create(ctypes.byref(prm), len(leaves), _iptr(leaves))
         if not h:
-            raise OracleError(lib().or_last_error().decode())
+            raise OracleError(self.L.or_last_error().decode())
         self.h = h
+
+    def _check(self, rc: int):
+        if rc != 0:
+            raise OracleError(self.L.or_last_error().decode())
 
     def __del__(self):
         h = getattr(self, "h", None)
         if h:
-            lib().or_destroy(h)
+            self.L.or_destroy(h)
             self.h = None
 
     @property
@@ -178,43 +212,43 @@ class Forest:
         return self.prm.mx + 2 * self.prm.mbc
 
     def __len__(self) -> int:
-        return lib().or_num_leaves(self.h)
+        return self.L.or_num_leaves(self.h)
 
     def leaves(self) -> np.ndarray:
         out = np.zeros((len(self), 5), dtype=np.int32)
-        lib().or_get_leaves(self.h, _iptr(out))
+        self.L.or_get_leaves(self.h, _iptr(out))
         return out
 
     def set_q(self, q: np.ndarray):
         q = np.ascontiguousarray(q, dtype=np.float64).reshape(len(self), self.mx, self.mx)
-        lib().or_set_q(self.h, _dptr(q))
+        self.L.or_set_q(self.h, _dptr(q))
 
     def get_q(self) -> np.ndarray:
         out = np.zeros((len(self), self.mx, self.mx))
-        lib().or_get_q(self.h, _dptr(out))
+        self.L.or_get_q(self.h, _dptr(out))
         return out
 
     def get_q_full(self) -> np.ndarray:
         out = np.zeros((len(self), self.S, self.S))
-        lib().or_get_q_full(self.h, _dptr(out))
+        self.L.or_get_q_full(self.h, _dptr(out))
         return out
 
     def set_q_full(self, q: np.ndarray):
         q = np.ascontiguousarray(q, dtype=np.float64).reshape(len(self), self.S, self.S)
-        lib().or_set_q_full(self.h, _dptr(q))
+        self.L.or_set_q_full(self.h, _dptr(q))
 
     def fill_ghosts(self):
-        _check(lib().or_fill_ghosts(self.h))
+        self._check(self.L.or_fill_ghosts(self.h))
 
     def step_global(self, t: float, dt: float):
-        _check(lib().or_step_global(self.h, t, dt))
+        self._check(self.L.or_step_global(self.h, t, dt))
 
     def step_multirate(self, t: float, dt_coarse: float):
-        _check(lib().or_step_multirate(self.h, t, dt_coarse))
+        self._check(self.L.or_step_multirate(self.h, t, dt_coarse))
 
     def tag(self) -> np.ndarray:
         out = np.zeros(len(self))
-        _check(lib().or_tag(self.h, _dptr(out)))
+        self._check(self.L.or_tag(self.h, _dptr(out)))
         return out
 
     def regrid(self, tau_r: float, tau_c: float,
@@ -224,12 +258,12 @@ class Forest:
         if lmax_f is not None:
             lm_arr = np.ascontiguousarray(lmax_f, dtype=np.int32)
             lm = _iptr(lm_arr)
-        _check(lib().or_regrid(self.h, tau_r, tau_c, lm, _iptr(changed)))
+        self._check(self.L.or_regrid(self.h, tau_r, tau_c, lm, _iptr(changed)))
         return int(changed[0])
 
     def mass(self) -> np.ndarray:
         out = np.zeros(self.prm.nforests)
-        lib().or_mass(self.h, _dptr(out))
+        self.L.or_mass(self.h, _dptr(out))
         return out
 
     def adjoint_global(self, nsteps: int, t0: float, dt: float, q_target: np.ndarray):
@@ -239,7 +273,7 @@ class Forest:
         g = np.zeros_like(qt)
         gs = np.zeros(1)
         loss = np.zeros(1)
-        _check(lib().or_adjoint_global(self.h, nsteps, t0, dt, _dptr(qt), _dptr(g), _dptr(gs),
+        self._check(self.L.or_adjoint_global(self.h, nsteps, t0, dt, _dptr(qt), _dptr(g), _dptr(gs),
                                        _dptr(loss)))
         return float(loss[0]), g, float(gs[0])
 
@@ -247,7 +281,7 @@ class Forest:
         """Adjoint of one global step at the current state: returns (lam_n, dscale)."""
         lam = np.ascontiguousarray(lam, dtype=np.float64).reshape(len(self), self.mx, self.mx).copy()
         ds = np.zeros(1)
-        _check(lib().or_adjoint_step_global(self.h, t, dt, _dptr(lam), _dptr(ds)))
+        self._check(self.L.or_adjoint_step_global(self.h, t, dt, _dptr(lam), _dptr(ds)))
         return lam, float(ds[0])
 
     def adjoint_multirate(self, ncoarse: int, t0: float, dtc: float, q_target: np.ndarray):
@@ -257,7 +291,7 @@ class Forest:
         g = np.zeros_like(qt)
         gs = np.zeros(1)
         loss = np.zeros(1)
-        _check(lib().or_adjoint_multirate(self.h, ncoarse, t0, dtc, _dptr(qt), _dptr(g),
+        self._check(self.L.or_adjoint_multirate(self.h, ncoarse, t0, dtc, _dptr(qt), _dptr(g),
                                           _dptr(gs), _dptr(loss)))
         return float(loss[0]), g, float(gs[0])
 
@@ -265,32 +299,32 @@ class Forest:
         """Adjoint of one coarse multirate step at the current state: (lam_n, dscale)."""
         lam = np.ascontiguousarray(lam, dtype=np.float64).reshape(len(self), self.mx, self.mx).copy()
         ds = np.zeros(1)
-        _check(lib().or_adjoint_step_multirate(self.h, t, dtc, _dptr(lam), _dptr(ds)))
+        self._check(self.L.or_adjoint_step_multirate(self.h, t, dtc, _dptr(lam), _dptr(ds)))
         return lam, float(ds[0])
 
     def sphere_centres(self) -> np.ndarray:
         """Unit-sphere positions of the interior cell centres, (n, mx, mx, 3)."""
         out = np.zeros((len(self), self.mx, self.mx, 3))
-        lib().or_sphere_centres(self.h, _dptr(out))
+        self.L.or_sphere_centres(self.h, _dptr(out))
         return out
 
     def kappa(self) -> np.ndarray:
         """Cell capacities (spherical areas) of the interior cells, (n, mx, mx)."""
         out = np.zeros((len(self), self.mx, self.mx))
-        lib().or_get_kappa(self.h, _dptr(out))
+        self.L.or_get_kappa(self.h, _dptr(out))
         return out
 
     def reflux_pairs(self) -> np.ndarray:
         """What refluxing exchanges per (leaf, face, face cell): (n, 4, mx, 5) of
         (kind, leaf across, its face, j0, j1); see or_reflux_pairs."""
         out = np.zeros((len(self), 4, self.mx, 5), dtype=np.int32)
-        lib().or_reflux_pairs(self.h, _iptr(out))
+        self.L.or_reflux_pairs(self.h, _iptr(out))
         return out
 
     def kappa_full(self) -> np.ndarray:
         """Cell capacities over the extended range (ghost cells included), (n, S, S)."""
         out = np.zeros((len(self), self.S, self.S))
-        lib().or_get_kappa_full(self.h, _dptr(out))
+        self.L.or_get_kappa_full(self.h, _dptr(out))
         return out
 
     def edge_fluxes(self, t: float = 0.0):
@@ -300,13 +334,13 @@ class Forest:
         S = self.S
         px = np.zeros((len(self), S, S + 1))
         py = np.zeros((len(self), S + 1, S))
-        lib().or_sphere_edge_fluxes(self.h, t, _dptr(px), _dptr(py))
+        self.L.or_sphere_edge_fluxes(self.h, t, _dptr(px), _dptr(py))
         return px, py
 
     def set_velocity_scale(self, s: float):
         """Scale every edge speed (the parameter of the velocity-scale gradient)."""
         self.prm.vel_scale = float(s)
-        lib().or_set_params(self.h, ctypes.byref(self.prm))
+        self.L.or_set_params(self.h, ctypes.byref(self.prm))
 
 
 def single_grid_periodic(prm: _Params, q: np.ndarray, t0: float, dt: float,
@@ -315,6 +349,18 @@ def single_grid_periodic(prm: _Params, q: np.ndarray, t0: float, dt: float,
     N = q.shape[0]
     _check(lib().or_single_grid_periodic(ctypes.byref(prm), N, _dptr(q), t0, dt, nsteps))
     return q
+
+
+def edge_speeds(prm: _Params, h: float, t: float, n: int):
+    """Edge speeds of the single-grid scheme at velocity time t on an n x n grid
+    of cell width h: u at the x-edges (i - 1/2, j), shape (n, n + 1) [j, i],
+    and v at the y-edges (i, j - 1/2), shape (n + 1, n) [j, i]."""
+    L = lib()
+    u = np.array([[L.or_u_edge(ctypes.byref(prm), h, t, 0, 0, i, j) for i in range(n + 1)]
+                  for j in range(n)])
+    v = np.array([[L.or_v_edge(ctypes.byref(prm), h, t, 0, 0, i, j) for i in range(n)]
+                  for j in range(n + 1)])
+    return u, v
 
 
 def mc_phi(theta: float) -> float:

@@ -211,6 +211,7 @@ int or_step_global(or_forest* F, double t, double dt) {
   if (or_fill_all(F)) return -1;
   flux_store(F);
   F->fslot = 0;
+  PATCH_LOOP
   for (int p = 0; p < F->n; ++p) or_advance_leaf(F, p, t, dt);
   if (F->P.reflux) /* every level took one step of dt: one fine step of the same dt */
     for (int L = F->P.lmin; L <= F->P.lmax; ++L) reflux_level(F, L, dt, 0, 1, 1.0);
@@ -221,10 +222,11 @@ static int mr_level(or_forest* F, int L, double t, double dt, double alpha) {
   size_t S2 = (size_t)F->S * F->S;
   if (or_fill_level(F, L, alpha)) return -1;
   const int slot = alpha != 0.0; /* the second substep of a pair */
+  F->fslot = slot;
+  PATCH_LOOP
   for (int p = 0; p < F->n; ++p)
     if (F->lv[p].l == L) {
       memcpy(F->qold + p * S2, F->q + p * S2, sizeof(double) * S2);
-      F->fslot = slot;
       or_advance_leaf(F, p, t, dt);
     }
   if (L < F->P.lmax) {

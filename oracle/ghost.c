@@ -158,6 +158,7 @@ static const gmap* classify_all(or_forest* F) {
   int ng = nghost(F);
   gmap* G = (gmap*)malloc(sizeof(gmap) * (size_t)(F->n > 0 ? F->n : 1) * ng);
   int mx = F->P.mx, mbc = F->P.mbc;
+  PATCH_LOOP
   for (int p = 0; p < F->n; ++p) {
     int k = 0;
     for (int j = -mbc; j < mx + mbc; ++j)
@@ -225,20 +226,25 @@ int or_fill_all_snapshot(or_forest* F, double* snapshot) {
     set_ghosts_nan(F, cur[p]);
   }
   /* phase 1: copy and average into coarse ghost regions, all levels */
+  PATCH_LOOP
   for (int p = 0; p < F->n; ++p) {
     fill_regions(F, G, p, cur[p], cur, REL_SAME);
     fill_regions(F, G, p, cur[p], cur, REL_FINE);
   }
   /* phase 2 */
+  PATCH_LOOP
   for (int p = 0; p < F->n; ++p) apply_bc(F, p, cur[p]);
   /* phase 3: interpolate fine ghost regions from a snapshot of phase 2 */
   double* snap = (double*)malloc(sizeof(double) * (S2 * F->n > 0 ? S2 * F->n : 1));
   memcpy(snap, F->q, sizeof(double) * S2 * F->n);
   double** sp = (double**)malloc(sizeof(double*) * (size_t)(F->n > 0 ? F->n : 1));
   for (int p = 0; p < F->n; ++p) sp[p] = snap + p * S2;
+  PATCH_LOOP
   for (int p = 0; p < F->n; ++p) fill_regions(F, G, p, cur[p], sp, REL_COARSE);
   /* phase 4 */
+  PATCH_LOOP
   for (int p = 0; p < F->n; ++p) apply_bc(F, p, cur[p]);
+  PATCH_LOOP
   for (int p = 0; p < F->n; ++p) corner3_fill(F, G, p, cur[p]);
   if (snapshot) memcpy(snapshot, snap, sizeof(double) * S2 * F->n);
   free(sp);
@@ -277,17 +283,22 @@ int or_fill_level(or_forest* F, int L, double alpha) {
       set_ghosts_nan(F, F->q + p * S2);
     }
   }
+  PATCH_LOOP
   for (int p = 0; p < F->n; ++p)
     if (F->lv[p].l == L - 1 || F->lv[p].l == L) {
       fill_regions(F, G, p, srcp[p], srcp, REL_SAME);
       fill_regions(F, G, p, srcp[p], srcp, REL_FINE);
     }
+  PATCH_LOOP
   for (int p = 0; p < F->n; ++p)
     if (F->lv[p].l == L - 1 || F->lv[p].l == L) apply_bc(F, p, srcp[p]);
+  PATCH_LOOP
   for (int p = 0; p < F->n; ++p)
     if (F->lv[p].l == L) fill_regions(F, G, p, srcp[p], srcp, REL_COARSE);
+  PATCH_LOOP
   for (int p = 0; p < F->n; ++p)
     if (F->lv[p].l == L) apply_bc(F, p, srcp[p]);
+  PATCH_LOOP
   for (int p = 0; p < F->n; ++p)
     if (F->lv[p].l == L - 1 || F->lv[p].l == L) corner3_fill(F, G, p, srcp[p]);
   free(srcp);
