@@ -26,6 +26,7 @@
 #ifndef FC_H
 #define FC_H
 
+#include <stddef.h>
 #include <stdint.h>
 
 #ifdef __cplusplus
@@ -91,7 +92,8 @@ typedef enum { FC_VEL_CONST = 0, FC_VEL_SWIRL = 1, FC_VEL_ROTATION = 2, FC_VEL_D
  *   limiter     0 unlimited, 1 MC.
  *   transverse  0 none, 1 fluctuations, 2 fluctuations and corrections.
  *   reflux      0 (the paper's scheme) or 1: conservative correction at
- *               coarse/fine faces (square domains; see fc_step_multirate). */
+ *               coarse/fine faces and, on the cubed sphere, at cube edges
+ *               (see fc_step_multirate). */
 typedef struct {
   int domain;
   int nforests;
@@ -105,7 +107,7 @@ typedef struct {
   int transverse;
   int indicator;  /* regrid indicator: 0 max |grad q| / 2, 1 max q - min q (Sec. 5.1) */
   int smooth;     /* 1: smooth grading of the target levels (Sec. 3.3) */
-  int reflux;     /* 1: refluxing at coarse/fine faces (an extension; square domains) */
+  int reflux;     /* 1: refluxing at coarse/fine faces (an extension) */
 } fc_forest_desc;
 
 /* Create a forest from an explicit leaf list (Sec. 2: quadrants identified
@@ -118,6 +120,41 @@ typedef struct {
 fc_status fc_forest_create(const fc_forest_desc* desc, int nleaves, const int* leaves,
                            fc_forest** out);
 fc_status fc_forest_destroy(fc_forest* forest);
+
+/* Pluggable device allocator.  By default every device allocation of the
+ * library comes from the device's stream-ordered pool (cudaMallocAsync /
+ * cudaFreeAsync on the API call's stream, or the legacy default stream
+ * inside fc_forest_create).  fc_set_allocator routes them all through the
+ * caller's functions instead (e.g. a framework's caching allocator):
+ *   alloc(bytes, stream, user)        returns a device pointer, 256-byte
+ *                                     aligned, usable in stream order on
+ *                                     `stream` (a cudaStream_t as void*), or
+ *                                     NULL (the call then fails FC_ERR_OOM);
+ *   release(ptr, bytes, stream, user) takes back a block, in stream order on
+ *                                     `stream`; bytes is the size asked for.
+ * Both or neither (NULL, NULL restores the pool).  Process-wide; it may be
+ * changed only while no forest exists (FC_ERR_STATE otherwise), so every
+ * block is released through the functions that allocated it.  The library
+ * calls the functions from the thread that calls it, never during a stream
+ * capture of its own. */
+typedef void* (*fc_alloc_fn)(size_t bytes, void* stream, void* user);
+typedef void (*fc_free_fn)(void* ptr, size_t bytes, void* stream, void* user);
+fc_status fc_set_allocator(fc_alloc_fn alloc, fc_free_fn release, void* user);
+
+/* What a forest holds (Sec. 2: the leaves and their levels).
+ *   leaves_per_level[l]  leaves of level l (0 <= l < FC_INFO_LEVELS)
+ *   device_bytes         device memory the forest holds now (store, tables,
+ *                        metrics, adjoint buffers once created)
+ *   graphs               captured coarse steps (forward and adjoint) held
+ *   tuned_buckets        launch-size buckets the autotuner has timed */
+#define FC_INFO_LEVELS 21
+typedef struct {
+  int nleaves, nforests, mx, mbc, lmin, lmax, dtype, domain;
+  int leaves_per_level[FC_INFO_LEVELS];
+  int64_t device_bytes;
+  int graphs, tuned_buckets;
+} fc_info;
+fc_status fc_forest_info(const fc_forest* forest, fc_info* out);
 
 /* Number of leaves, and the leaf list (host, n x 5 ints) in field order. */
 fc_status fc_forest_num_leaves(const fc_forest* forest, int* n);
@@ -159,9 +196,15 @@ fc_status fc_step_global(fc_forest* forest, double t, double dt, void* stream);
  * two fine cells and the two fine substeps): q += (dt/h)(Fc - Fbar) on a +x
  * or +y face, q += (dt/h)(Fbar - Fc) on a -x or -y face, faces in the order
  * -x, +x, -y, +y.  Total mass is then conserved to rounding.  (In
- * fc_step_global the weight is 1/2: one fine step of the same dt.)  Every
- * update runs the staged variant then; fc_advance_level records the fluxes
- * but corrects nothing. */
+ * fc_step_global the weight is 1/2: one fine step of the same dt.)  On the
+ * cubed sphere the fluxes are volume fluxes (the fine side's weight is the
+ * time ratio alone, 1/2 per substep, 1 in fc_step_global), the correction of
+ * a cell is dt / kappa of the cell, and every level substep also exchanges
+ * the fluxes of the cube edges: each side computes an edge's flux from its
+ * own ghost cells, the side on the block of lower index keeps its own, and
+ * a cell on the other side takes it in place of its own (the pairing of
+ * fc_layout_reflux).  Every update runs the staged variant then;
+ * fc_advance_level records the fluxes but corrects nothing. */
 fc_status fc_step_multirate(fc_forest* forest, double t, double dt_coarse, void* stream);
 
 /* Tag and regrid (Sec. 3.1).  Fills ghosts, computes on the device the
@@ -203,6 +246,38 @@ fc_status fc_set_velocity_scale(fc_forest* forest, double scale);
  * rounding order of those sums is not fixed.  Asynchronous on `stream`. */
 fc_status fc_adjoint_step_global(fc_forest* forest, double t, double dt, void* lam,
                                  double* dscale, void* stream);
+
+/* Adjoint of one multirate level substep, fc_advance_level(level, t, dt)
+ * (Sec. 4 local time stepping; the adjoint is an extension for
+ * differentiation with no counterpart in the paper; square domains only).
+ * The forest must hold the state the forward call started from -- the
+ * current states of every level, the older state of level-1 that its time
+ * interpolation reads, and the bookkeeping of the levels' last steps -- as
+ * it stands right before that call; it is not advanced (the substep's ghost
+ * fill is redone in place, which changes no interior value).  With the
+ * substep's map (level's new state) = U(Fill(q_level, q_level+1,
+ * (1 - alpha) q_old(level-1) + alpha q(level-1))):
+ *   lam      device, in/out, field layout: on entry the adjoint of every
+ *            leaf's current state after the call (level's leaves: of its
+ *            new state), on return the adjoint of every leaf's current state
+ *            before it; the transposes of the level's update, of its ghost
+ *            fill (copies, averages, interpolation slopes on the pieces the
+ *            forward state selects) and the newer state's alpha share of the
+ *            time interpolation are added where they belong;
+ *   lam_old  device, nullable, field layout, accumulated: the adjoint of
+ *            each leaf's older state (the state before its level's latest
+ *            step); this call adds the (1 - alpha) share of level-1's time
+ *            interpolation there.  Needed when level > lmin and level-1
+ *            has stepped since the field was set (FC_ERR_INVALID_ARG if then
+ *            NULL).  Chaining these calls in reverse over a coarse step, a
+ *            caller adds lam_old's entries of a level into lam (and clears
+ *            them) right after reversing that level's substep: the older
+ *            state is the state before it;
+ *   dscale   device, one double, accumulated: += lam^T d(new state)/dsigma.
+ * Contributions are atomic adds, so their rounding order is not fixed.
+ * Asynchronous on `stream`. */
+fc_status fc_adjoint_advance(fc_forest* forest, int level, double t, double dt, void* lam,
+                             void* lam_old, double* dscale, void* stream);
 
 /* Adjoint of one coarse multirate step (the coarse-first recursion of
  * fc_step_multirate, Sec. 4): the transpose of every level substep -- the
@@ -267,6 +342,53 @@ fc_status fc_layout_regrid(const fc_forest_desc* desc, int nleaves, const int* l
  * 0 nothing (-1 elsewhere); faces 0 -x, 1 +x, 2 -y, 3 +y. */
 fc_status fc_layout_reflux(const fc_forest_desc* desc, int nleaves, const int* leaves, int* out);
 
+/* Partitioned layouts (Sec. 3: partitioning, parallel ghost filling).
+ *
+ * The leaves, in their field (Morton) order, are split into contiguous ranges
+ * of equal work, a level-l leaf weighing 2^(l - lmin) (its updates per
+ * coarse step); each rank (one process per GPU, or several partitions on
+ * one GPU) holds its own leaves plus its mirrors: the leaves of other ranks
+ * whose interiors its ghost fills read -- face and corner neighbours of its
+ * leaves and, where a neighbour is coarser, that neighbour's same-size and
+ * finer neighbours (its copied and averaged ghosts feed the interpolation;
+ * Proposition 1 keeps the interpolated ones out of reach).  Every layout
+ * array below is in the caller's leaf order.
+ *
+ * fc_layout_partition (host only): part_out[i] = the rank of leaf i.
+ * fc_layout_halo (host only): the mirrors of `rank` under `part`, as
+ *   indices into `leaves`, in field order; mirror_out holds up to nleaves.
+ * fc_forest_create_part: rank's part of the layout, on the device.  Its
+ *   field layout (set_q, get_q, mass, tag, capacity, leaves) covers the
+ *   owned leaves only, in field order; the mirrors are held internally.
+ *   fc_fill_ghosts, fc_advance_level and fc_step_global update the owned
+ *   leaves; after each of them the caller refreshes the mirrors of the
+ *   levels that changed (all levels after fc_step_global and after
+ *   fc_forest_set_q, level l after fc_advance_level(l, ...)): for every
+ *   other rank r, fc_halo_pack(r, level) on the owner and
+ *   fc_halo_unpack(owner, level) on r, moving the packed buffer between
+ *   them (a device copy, a send/receive, ...), before the next step reads
+ *   them.  Stepping every partition this way gives each owned leaf the same
+ *   bits as the unpartitioned forest.  fc_step_multirate, fc_tag_regrid and
+ *   the adjoint return FC_ERR_STATE on a partition (its layout is fixed);
+ *   refluxing is not built for it.
+ * fc_halo_count: patches in the exchange with `peer` for `level` (-1: all
+ *   levels, level-major), sent from this rank and received by it.
+ * fc_halo_pack: device `dst` <- the interiors (mx x mx of the forest's
+ *   dtype each, [patch][j][i]) of this rank's patches that `peer` mirrors,
+ *   from their current states, ordered by field order; async on `stream`.
+ * fc_halo_unpack: the interiors of this rank's mirrors owned by `peer`, in
+ *   the same order, <- device `src` (the peer's packed buffer for this
+ *   rank); async on `stream`. */
+fc_status fc_layout_partition(const fc_forest_desc* desc, int nleaves, const int* leaves,
+                              int nranks, int* part_out);
+fc_status fc_layout_halo(const fc_forest_desc* desc, int nleaves, const int* leaves,
+                         const int* part, int rank, int* nmirror, int* mirror_out);
+fc_status fc_forest_create_part(const fc_forest_desc* desc, int nleaves, const int* leaves,
+                                const int* part, int rank, fc_forest** out);
+fc_status fc_halo_count(const fc_forest* forest, int peer, int level, int* nsend, int* nrecv);
+fc_status fc_halo_pack(const fc_forest* forest, int peer, int level, void* dst, void* stream);
+fc_status fc_halo_unpack(fc_forest* forest, int peer, int level, const void* src, void* stream);
+
 /* Per-phase device timers (the paper's run-time breakdown, Sec. 5: advance,
  * ghost fill, regrid).  While enabled, every kernel launch of a phase is
  * bracketed by CUDA events on its stream.
@@ -276,7 +398,10 @@ fc_status fc_layout_reflux(const fc_forest_desc* desc, int nleaves, const int* l
  * and the algorithmic bytes those launches must move (advance: every patch
  * array read once with ghosts, every interior written once; fill: every
  * filled ghost cell written once and its source read once).  reset != 0
- * clears the phase afterwards. */
+ * clears the phase afterwards.  A coarse multirate step captured while the
+ * timers are on runs its levels one after another on one stream (without
+ * them each level runs on its own branch, the levels overlapping), so every
+ * timed launch has the GPU to itself and its time is that kernel's alone. */
 fc_status fc_timers_enable(fc_forest* forest, int enable);
 
 /* CUDA-graph replay of fc_step_multirate (on by default).  The first coarse
@@ -320,8 +445,30 @@ fc_status fc_autotune(fc_forest* forest, int* report, void* stream);
  * ring first (same results, bit for bit). */
 fc_status fc_set_fused_fill(fc_forest* forest, int enable);
 fc_status fc_set_advance_variant(fc_forest* forest, int variant, int warps);
+
+/* Launch limits (tests and tuning).
+ *   walk_ctas   cap on the persistent walk grid (0: as many CTAs as the SMs
+ *               hold at once); a small cap makes every warp loop over many
+ *               groups of patches through both of its tile buffers.
+ *   wait_polls  polls of the patch-update kernels' bounded wait for their
+ *               tile copies before they give up (negative: the default,
+ *               2^22); 0 makes every such wait give up at once.  A kernel
+ *               that gives up sets the forest's device error word (the next
+ *               synchronising call returns FC_ERR_TIMEOUT and clears it),
+ *               still waits, with the default limit, for the copies it has
+ *               in flight, and leaves its patches not updated.
+ * Captured steps are discarded (they carry the old values). */
+fc_status fc_set_limits(fc_forest* forest, int walk_ctas, int64_t wait_polls);
 fc_status fc_timers_read(fc_forest* forest, int phase, double* ms, int64_t* launches,
                          double* bytes, int reset);
+
+/* Interior cell capacities in field order, nleaves x mx x mx doubles: h^2 on
+ * the square domains (h = 2^-level / mx), the spherical cell area kappa on the
+ * cubed sphere (Sec. 5.3 mapped grids; the FP64 metric the update uses).
+ *   on_device  nonzero: `out` is a device pointer (async on `stream`);
+ *              zero: a host pointer (the call synchronises `stream`). */
+fc_status fc_forest_get_capacity(const fc_forest* forest, double* out, int on_device,
+                                 void* stream);
 
 /* Mass sums without any allocation.
  *
@@ -336,21 +483,33 @@ fc_status fc_timers_read(fc_forest* forest, int phase, double* ms, int64_t* laun
  *
  *   q             device, packed interior field [leaf][j][i] of `dtype`
  *                 (FC_F32 / FC_F64), mx x mx cells per leaf.
+ *   capacity      device, nullable: the cells' capacities in the same
+ *                 layout (doubles, as fc_forest_get_capacity returns them).
+ *                 Null: each cell weighs h^2, h = 2^-level / mx (the square
+ *                 domains; the same bits as fc_forest_mass there).  Given:
+ *                 each cell weighs its capacity (on the cubed sphere the
+ *                 same bits as fc_forest_mass, which sums kappa q).
  *   level         device, nleaves ints: refinement level of each leaf.
- *   forest_start  device, nforests+1 ints: the leaves of forest f are
- *                 [forest_start[f], forest_start[f+1]) in the field order.
- *   out           device, nforests doubles: sum over the forest's leaves of
- *                 h^2 sum(q), h = 2^-level / mx; each leaf is summed in a
- *                 fixed order, then the leaves of a forest in a fixed order.
+ *   forest_start  device, nforests+1 ints with 0 = forest_start[0] <= ... <=
+ *                 forest_start[nforests] = nleaves: the leaves of forest f
+ *                 are [forest_start[f], forest_start[f+1]) in the field
+ *                 order.  Entries outside that contract are clamped into
+ *                 [0, nleaves] on the device (the sums are then of the
+ *                 clamped ranges); no slot outside this call's leaves is read.
+ *   out           device, nforests doubles: each leaf is summed in a fixed
+ *                 order, then the leaves of a forest in a fixed order.
  * nleaves above FC_NOALLOC_MAX_LEAVES is rejected (FC_ERR_INVALID_ARG).
  * Work is enqueued on `stream`; the call does not synchronise.  All calls
  * share the one array: calls whose work overlaps on the GPU (other streams,
  * other threads) race and must be serialised by the caller.  The first call
- * on a device looks up the array's device address with that device current;
- * make that first call before any stream capture. */
+ * on a device looks up the array's device address with that device current
+ * and keeps it for the life of the process; make that first call before any
+ * stream capture, and do not use the call after cudaDeviceReset (or any
+ * other teardown of the device's primary context) in the same process. */
 #define FC_NOALLOC_MAX_LEAVES (1 << 19)
-fc_status fc_mass_noalloc(const void* q, int dtype, int mx, int nleaves, const int* level,
-                          const int* forest_start, int nforests, double* out, void* stream);
+fc_status fc_mass_noalloc(const void* q, const double* capacity, int dtype, int mx, int nleaves,
+                          const int* level, const int* forest_start, int nforests, double* out,
+                          void* stream);
 
 /* Thread-local description of the last failure. */
 const char* fc_last_error(void);

@@ -7,13 +7,13 @@ fails loudly when it has not been built -- there is no CPU fallback.
 from . import _lib
 from ._lib import F32, F64, PERIODIC, SPHERE, WALLS, Desc, FcError, load
 from .forest import (Forest, initial_forest, layout_check, layout_neighbours, layout_reflux,
-                     layout_regrid, make_desc, uniform_leaves)
+                     layout_regrid, make_desc, set_allocator, torch_allocator, uniform_leaves)
 
 load()
 
 __all__ = ["Forest", "Desc", "FcError", "make_desc", "initial_forest", "uniform_leaves",
-           "layout_check", "layout_neighbours", "layout_reflux", "layout_regrid", "F32", "F64", "WALLS",
-           "PERIODIC", "SPHERE"]
+           "layout_check", "layout_neighbours", "layout_reflux", "layout_regrid", "set_allocator",
+           "torch_allocator", "F32", "F64", "WALLS", "PERIODIC", "SPHERE"]
 
 
 def launch_count(reset: bool = False) -> int:

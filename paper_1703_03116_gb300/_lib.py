@@ -14,6 +14,22 @@ F32, F64 = 0, 1
 WALLS, PERIODIC, SPHERE = 0, 1, 2
 VEL_CONST, VEL_SWIRL, VEL_ROTATION, VEL_DEFORM = 0, 1, 2, 3
 
+INFO_LEVELS = 21
+
+# allocator callbacks of fc_set_allocator
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p,
+                           ctypes.c_void_p)
+
+
+class Info(ctypes.Structure):
+    """Mirror of fc_info."""
+    _fields_ = [(n, ctypes.c_int) for n in ("nleaves", "nforests", "mx", "mbc", "lmin", "lmax",
+                                            "dtype", "domain")] + [
+        ("leaves_per_level", ctypes.c_int * INFO_LEVELS), ("device_bytes", ctypes.c_int64),
+        ("graphs", ctypes.c_int), ("tuned_buckets", ctypes.c_int)]
+
+
 # every function that include/fc.h declares, with (restype, argtypes)
 _vp, _ip, _dp = ctypes.c_void_p, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)
 
@@ -63,9 +79,22 @@ SIGNATURES = {
                                               _vp]),
     "fc_adjoint_step_multirate": (ctypes.c_int, [_vp, ctypes.c_double, ctypes.c_double, _vp,
                                                  _vp, _vp]),
-    "fc_mass_noalloc": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp, _vp,
-                                       ctypes.c_int, _vp, _vp]),
+    "fc_adjoint_advance": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                          _vp, _vp, _vp, _vp]),
+    "fc_forest_info": (ctypes.c_int, [_vp, _vp]),
+    "fc_layout_partition": (ctypes.c_int, [_DP, ctypes.c_int, _ip, ctypes.c_int, _ip]),
+    "fc_layout_halo": (ctypes.c_int, [_DP, ctypes.c_int, _ip, _ip, ctypes.c_int, _ip, _ip]),
+    "fc_forest_create_part": (ctypes.c_int, [_DP, ctypes.c_int, _ip, _ip, ctypes.c_int,
+                                             ctypes.POINTER(_vp)]),
+    "fc_halo_count": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, _ip, _ip]),
+    "fc_halo_pack": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, _vp, _vp]),
+    "fc_halo_unpack": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, _vp, _vp]),
+    "fc_set_allocator": (ctypes.c_int, [_vp, _vp, _vp]),
+    "fc_mass_noalloc": (ctypes.c_int, [_vp, _vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp,
+                                       _vp, ctypes.c_int, _vp, _vp]),
+    "fc_forest_get_capacity": (ctypes.c_int, [_vp, _vp, ctypes.c_int, _vp]),
     "fc_set_advance_variant": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int]),
+    "fc_set_limits": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int64]),
     "fc_timers_read": (ctypes.c_int, [_vp, ctypes.c_int, _dp, ctypes.POINTER(ctypes.c_int64),
                                       _dp, ctypes.c_int]),
     "fc_last_error": (ctypes.c_char_p, []),

@@ -144,7 +144,7 @@ __global__ void __launch_bounds__(NT, NT >= 512 ? (sizeof(real) == 4 ? 3 : 2)
     }
     // every thread observes the copy's completion (bounded); the CTA leaves
     // together if any thread gave up
-    const bool landed = mbar_wait(&bar, parity, kWaitLimit);
+    const bool landed = mbar_wait(&bar, parity, a.wait_limit);
     if (!__syncthreads_and(landed)) {
       if (threadIdx.x == 0) atomicOr(err, kErrTimeout);
       mbar_wait(&bar, parity, kWaitLimit);  // let the copy land before leaving

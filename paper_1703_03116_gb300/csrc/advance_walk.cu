@@ -159,7 +159,7 @@ __global__ void __launch_bounds__(NW * 32) advance_walk_kernel(DevForest<real> D
       TxP = sinpi_r(real(2 * (x0 + MX) + 1) * h);
     }
     uint32_t& par = b ? par1 : par0;
-    const bool ok = mbar_wait(&bars[warp][b], par, kWaitLimit);
+    const bool ok = mbar_wait(&bars[warp][b], par, a.wait_limit);
     if (!__all_sync(FULL, ok)) {
       if (lane == 0) atomicOr(err, kErrTimeout);
       // let every copy in flight land before leaving

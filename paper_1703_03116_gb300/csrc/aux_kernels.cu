@@ -132,7 +132,7 @@ template <typename real>
 __global__ void pack_kernel(DevForest<real> D, const int* api_to_dev, real* out, int full) {
   const int mx = D.mx, S = D.S;
   const int per = full ? S * S : mx * mx;
-  const size_t total = (size_t)D.npatch * per;
+  const size_t total = (size_t)D.napi * per;
   for (size_t g = (size_t)blockIdx.x * blockDim.x + threadIdx.x; g < total;
        g += (size_t)gridDim.x * blockDim.x) {
     const int k = (int)(g / per), r = (int)(g % per);
@@ -145,7 +145,7 @@ __global__ void pack_kernel(DevForest<real> D, const int* api_to_dev, real* out,
 template <typename real>
 __global__ void unpack_kernel(DevForest<real> D, const int* api_to_dev, const real* in) {
   const int mx = D.mx, S = D.S;
-  const size_t total = (size_t)D.npatch * mx * mx;
+  const size_t total = (size_t)D.napi * mx * mx;
   for (size_t g = (size_t)blockIdx.x * blockDim.x + threadIdx.x; g < total;
        g += (size_t)gridDim.x * blockDim.x) {
     const int k = (int)(g / (mx * mx)), r = (int)(g % (mx * mx));
@@ -153,6 +153,60 @@ __global__ void unpack_kernel(DevForest<real> D, const int* api_to_dev, const re
     real* Q = D.buf[D.cur[D.meta[p].level]] + (size_t)p * S * S;
     Q[(r / mx + 2) * S + r % mx + 2] = in[g];
   }
+}
+
+// interior capacities in field order: kappa from the metric block on a
+// mapped grid, h^2 on the square domains
+template <typename real>
+__global__ void pack_capacity_kernel(DevForest<real> D, const int* api_to_dev, double* out) {
+  const int mx = D.mx, S = D.S;
+  const size_t total = (size_t)D.napi * mx * mx;
+  for (size_t g = (size_t)blockIdx.x * blockDim.x + threadIdx.x; g < total;
+       g += (size_t)gridDim.x * blockDim.x) {
+    const int k = (int)(g / (mx * mx)), r = (int)(g % (mx * mx));
+    const int p = api_to_dev[k];
+    if (D.metric) {
+      out[g] = D.metric[(size_t)p * metric_stride(S) + (r / mx + 2) * S + r % mx + 2];
+    } else {
+      const double h = ldexp(1.0, -D.meta[p].level) / mx;
+      out[g] = h * h;
+    }
+  }
+}
+
+// halo exchange of a partition: the interiors of the listed patches (local
+// device indices, each read from its level's current state) to a contiguous
+// buffer [k][j][i], and back into the listed mirrors' current states
+template <typename real>
+__global__ void halo_pack_kernel(DevForest<real> D, const int* list, int n, real* out) {
+  const int mx = D.mx, S = D.S;
+  const size_t total = (size_t)n * mx * mx;
+  for (size_t g = (size_t)blockIdx.x * blockDim.x + threadIdx.x; g < total;
+       g += (size_t)gridDim.x * blockDim.x) {
+    const int k = (int)(g / (mx * mx)), r = (int)(g % (mx * mx));
+    const int p = list[k];
+    out[g] = D.buf[D.cur[D.meta[p].level]][(size_t)p * S * S + (r / mx + 2) * S + r % mx + 2];
+  }
+}
+
+template <typename real>
+__global__ void halo_unpack_kernel(DevForest<real> D, const int* list, int n, const real* in) {
+  const int mx = D.mx, S = D.S;
+  const size_t total = (size_t)n * mx * mx;
+  for (size_t g = (size_t)blockIdx.x * blockDim.x + threadIdx.x; g < total;
+       g += (size_t)gridDim.x * blockDim.x) {
+    const int k = (int)(g / (mx * mx)), r = (int)(g % (mx * mx));
+    const int p = list[k];
+    D.buf[D.cur[D.meta[p].level]][(size_t)p * S * S + (r / mx + 2) * S + r % mx + 2] = in[g];
+  }
+}
+
+// dst += src elementwise (n values)
+template <typename real>
+__global__ void add_store_kernel(real* dst, const real* src, size_t n) {
+  for (size_t g = (size_t)blockIdx.x * blockDim.x + threadIdx.x; g < n;
+       g += (size_t)gridDim.x * blockDim.x)
+    dst[g] += src[g];
 }
 
 // ------------------------------------------------------------------ remap
@@ -242,6 +296,53 @@ __global__ void reflux_kernel(DevForest<real> D, int p0, int p1, const real* __r
   }
 }
 
+// Refluxing on the cubed sphere, from the host's pairing (per patch, face
+// and face cell: kind, patch across, its face g on the shared edge, its cells
+// j0, j1): a cell beside a finer patch (kind 1) takes the fine side's volume
+// fluxes summed over nfs substep slots with weight w (the time ratio); a
+// cell on a cube edge whose same-size neighbour lies on a block of lower
+// index (kind 2) takes that neighbour's flux of the same substep.  Fluxes are
+// signed outward on each side; the correction is dt / kappa of the cell.
+// One warp per patch, lane k on face cell k, faces in order (-x, +x, -y, +y).
+template <typename real, int MX>
+__global__ void reflux_pairs_kernel(DevForest<real> D, int p0, int p1,
+                                    const real* __restrict__ bflux, const int* __restrict__ pairs,
+                                    int cslot, int nfs, double w, double dt) {
+  const int lane = threadIdx.x & 31;
+  const int p = p0 + blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (p >= p1) return;  // whole warps leave together
+  const int S = D.S;
+  real* Q = D.buf[D.cur[D.meta[p].level]] + (size_t)p * S * S;
+  const double* K = D.metric + (size_t)p * metric_stride(S);
+  for (int dir = 0; dir < 4; ++dir) {
+    if (lane < MX) {
+      const int* e = pairs + (((size_t)p * 4 + dir) * MX + lane) * 5;
+      const int kind = e[0];
+      if (kind != 0) {
+        const int n = e[1], g = e[2], j0 = e[3], j1 = e[4];
+        const double sg = (g & 1) ? 1.0 : -1.0, sf = (dir & 1) ? 1.0 : -1.0;
+        double target;
+        if (kind == 1) {
+          double fsum = 0.0;
+          for (int s = 0; s < nfs; ++s) {
+            const real* b = bflux + (((size_t)n * 2 + s) * 4 + g) * MX;
+            fsum += double(b[j0]) + double(b[j1]);
+          }
+          target = -sg * (w * fsum);
+        } else {
+          target = -sg * double(bflux[(((size_t)n * 2 + cslot) * 4 + g) * MX + j0]);
+        }
+        const double out = sf * double(bflux[(((size_t)p * 2 + cslot) * 4 + dir) * MX + lane]);
+        const int i = dir == 0 ? 0 : (dir == 1 ? MX - 1 : lane);
+        const int j = dir == 2 ? 0 : (dir == 3 ? MX - 1 : lane);
+        const int o = (j + kMbc) * S + (i + kMbc);
+        Q[o] = real(double(Q[o]) + dt / K[o] * (out - target));
+      }
+    }
+    __syncwarp();
+  }
+}
+
 }  // namespace
 
 template <typename real>
@@ -300,6 +401,37 @@ cudaError_t launch_pack(const DevForest<real>& D, const int* api_to_dev, real* o
 }
 
 template <typename real>
+cudaError_t launch_halo(const DevForest<real>& D, const int* list, int n, real* buf, int pack,
+                        cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  const size_t total = (size_t)n * D.mx * D.mx;
+  const int grid = (int)std::min<size_t>((total + 255) / 256, 1216);
+  if (pack)
+    halo_pack_kernel<real><<<grid, 256, 0, s>>>(D, list, n, buf);
+  else
+    halo_unpack_kernel<real><<<grid, 256, 0, s>>>(D, list, n, buf);
+  ++launch_counter();
+  return cudaGetLastError();
+}
+
+template <typename real>
+cudaError_t launch_add_store(real* dst, const real* src, size_t n, cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  add_store_kernel<real><<<1216, 256, 0, s>>>(dst, src, n);
+  ++launch_counter();
+  return cudaGetLastError();
+}
+
+template <typename real>
+cudaError_t launch_pack_capacity(const DevForest<real>& D, const int* api_to_dev, double* out,
+                                 cudaStream_t s) {
+  if (D.npatch <= 0) return cudaSuccess;
+  pack_capacity_kernel<real><<<1216, 256, 0, s>>>(D, api_to_dev, out);
+  ++launch_counter();
+  return cudaGetLastError();
+}
+
+template <typename real>
 cudaError_t launch_unpack(const DevForest<real>& D, const int* api_to_dev, const real* in,
                           cudaStream_t s) {
   if (D.npatch <= 0) return cudaSuccess;
@@ -317,6 +449,32 @@ cudaError_t launch_remap(const DevForest<real>& Old, const DevForest<real>& New,
   return cudaGetLastError();
 }
 
+template <typename real>
+cudaError_t launch_reflux_pairs(const DevForest<real>& D, int p0, int p1, const real* bflux,
+                                const int* pairs, int cslot, int nfs, double w, double dt,
+                                cudaStream_t s) {
+  if (p1 <= p0) return cudaSuccess;
+  constexpr int kWarps = 4;
+  const int grid = (p1 - p0 + kWarps - 1) / kWarps;
+  switch (D.mx) {
+    case 8:
+      reflux_pairs_kernel<real, 8><<<grid, 32 * kWarps, 0, s>>>(D, p0, p1, bflux, pairs, cslot,
+                                                                 nfs, w, dt);
+      break;
+    case 16:
+      reflux_pairs_kernel<real, 16><<<grid, 32 * kWarps, 0, s>>>(D, p0, p1, bflux, pairs, cslot,
+                                                                  nfs, w, dt);
+      break;
+    case 32:
+      reflux_pairs_kernel<real, 32><<<grid, 32 * kWarps, 0, s>>>(D, p0, p1, bflux, pairs, cslot,
+                                                                  nfs, w, dt);
+      break;
+    default: return cudaErrorInvalidValue;
+  }
+  ++launch_counter();
+  return cudaGetLastError();
+}
+
 #define FC_INSTANTIATE(real)                                                                   \
   template cudaError_t launch_tag<real>(const DevForest<real>&, int, double*, cudaStream_t);        \
   template cudaError_t launch_reflux<real>(const DevForest<real>&, int, int, const real*, int, int, \
@@ -327,6 +485,14 @@ cudaError_t launch_remap(const DevForest<real>& Old, const DevForest<real>& New,
                                          cudaStream_t);                                        \
   template cudaError_t launch_unpack<real>(const DevForest<real>&, const int*, const real*,   \
                                            cudaStream_t);                                      \
+  template cudaError_t launch_add_store<real>(real*, const real*, size_t, cudaStream_t);      \
+  template cudaError_t launch_reflux_pairs<real>(const DevForest<real>&, int, int, const real*, \
+                                                 const int*, int, int, double, double,         \
+                                                 cudaStream_t);                                \
+  template cudaError_t launch_halo<real>(const DevForest<real>&, const int*, int, real*, int,  \
+                                        cudaStream_t);                                         \
+  template cudaError_t launch_pack_capacity<real>(const DevForest<real>&, const int*, double*, \
+                                                  cudaStream_t);                               \
   template cudaError_t launch_remap<real>(const DevForest<real>&, const DevForest<real>&,     \
                                           const RemapEntry*, cudaStream_t);
 

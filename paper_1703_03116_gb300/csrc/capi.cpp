@@ -1,7 +1,10 @@
 // C ABI (include/fc.h): forest lifetime, device store, and the time-stepping
 // scheduler (Alg. 1 fills, global and multirate level substeps, regrid).
 #include <algorithm>
+#include <atomic>
 #include <functional>
+#include <mutex>
+#include <unordered_map>
 #include <tuple>
 #include <cmath>
 #include <cstdio>
@@ -60,21 +63,63 @@ void keep_pool_memory() {
   done_for = dev;
 }
 
-template <typename T>
-cudaError_t dmalloc(T** p, size_t n) {
-  *p = nullptr;
-  if (n == 0) n = 1;
-  return cudaMallocAsync((void**)p, n * sizeof(T), g_alloc_stream);
-}
+// Pluggable device allocator (fc_set_allocator): when set, every device
+// allocation of the library goes through the caller's functions instead of
+// the stream-ordered pool, with the same stream the pool would have used.
+// The sizes of hooked blocks are kept so the free callback receives them.
+struct AllocHook {
+  fc_alloc_fn alloc = nullptr;
+  fc_free_fn release = nullptr;
+  void* user = nullptr;
+};
+AllocHook g_hook;
+std::mutex g_hook_mu;
+std::unordered_map<void*, size_t> g_hook_sizes;
+std::atomic<int> g_live_forests{0};
 
 cudaError_t dmalloc_bytes(void** p, size_t bytes) {
   *p = nullptr;
-  return cudaMallocAsync(p, bytes ? bytes : 1, g_alloc_stream);
+  if (bytes == 0) bytes = 1;
+  if (g_hook.alloc) {
+    void* q = g_hook.alloc(bytes, static_cast<void*>(g_alloc_stream), g_hook.user);
+    if (!q) return cudaErrorMemoryAllocation;
+    std::lock_guard<std::mutex> lock(g_hook_mu);
+    g_hook_sizes[q] = bytes;
+    *p = q;
+    return cudaSuccess;
+  }
+  return cudaMallocAsync(p, bytes, g_alloc_stream);
+}
+
+template <typename T>
+cudaError_t dmalloc(T** p, size_t n) {
+  void* v = nullptr;
+  const cudaError_t e = dmalloc_bytes(&v, (n ? n : 1) * sizeof(T));
+  *p = static_cast<T*>(v);
+  return e;
+}
+
+void dfree_bytes(void* p) {
+  if (!p) return;
+  if (g_hook.release) {
+    size_t bytes = 0;
+    {
+      std::lock_guard<std::mutex> lock(g_hook_mu);
+      auto it = g_hook_sizes.find(p);
+      if (it != g_hook_sizes.end()) {
+        bytes = it->second;
+        g_hook_sizes.erase(it);
+      }
+    }
+    g_hook.release(p, bytes, static_cast<void*>(g_alloc_stream), g_hook.user);
+    return;
+  }
+  cudaFreeAsync(p, g_alloc_stream);
 }
 
 template <typename T>
 void dfree(T*& p) {
-  if (p) cudaFreeAsync((void*)p, g_alloc_stream);
+  dfree_bytes((void*)p);
   p = nullptr;
 }
 
@@ -176,6 +221,8 @@ struct fc_forest {
   };
   Tune tune[32];
   int forced_variant = -1, forced_warps = 4;
+  int walk_ctas = 0;                    // cap on the walk grid (0: residency)
+  uint32_t wait_polls = kWaitLimit;     // polls of the update kernels' bounded waits
   double vel_scale = 1.0;                 // multiplies every edge speed
   double* d_metric = nullptr;             // cubed sphere: FP64 metric blocks per patch
   double* d_corner = nullptr;             // deformational flow: grid corners per patch
@@ -195,6 +242,15 @@ struct fc_forest {
   cudaStream_t cap_stream = nullptr;
   double* d_t0 = nullptr;  // start time of the replayed coarse step
   std::vector<Graph> graphs;
+  // a partition's exchange lists on the device: for each level (kMaxLevel + 1:
+  // all levels, level-major) and rank, the send then the receive list
+  int* d_halo = nullptr;
+  std::vector<size_t> halo_off;  // [((l * nranks + r) * 2 + dir)] offset; count at + 1
+  // refluxing on the cubed sphere: the host pairing per device patch, face
+  // and face cell (kind, patch across, its face, j0, j1), and the levels
+  // that have any pair
+  int* d_pairs = nullptr;
+  bool pair_level[kMaxLevel + 1] = {};
 };
 
 namespace {
@@ -334,6 +390,8 @@ void free_device(fc_forest* F) {
   F->msnap_bytes = 0;
   dfree(F->d_metric);
   dfree(F->d_corner);
+  dfree(F->d_halo);
+  dfree(F->d_pairs);
 }
 
 // cubed sphere: (re)compute the metric blocks of the current layout for the
@@ -463,6 +521,32 @@ fc_status upload(fc_forest* F, bool alloc_store, bool metrics = true) {
     FC_CUDA(dmalloc(&F->d_t0, 1));
     FC_CUDA(cudaMemsetAsync(F->d_t0, 0, sizeof(double), g_alloc_stream));
   }
+  // refluxing on the cubed sphere: the pairing of coarse faces with finer
+  // ones and of the cube edges' two sides, in device order
+  dfree(F->d_pairs);
+  for (bool& b : F->pair_level) b = false;
+  if (H.desc.reflux && H.desc.domain == FC_DOMAIN_SPHERE) {
+    const size_t row = (size_t)4 * H.desc.mx * 5;
+    std::vector<int> field((size_t)n * row), tab((size_t)n * row);
+    const std::string err = H.reflux_pairs(field.data());
+    if (!err.empty()) return fail(FC_ERR_STATE, err);
+    for (int k = 0; k < n; ++k) {
+      const int* src = field.data() + (size_t)k * row;
+      int* dst = tab.data() + (size_t)H.dev_of[k] * row;
+      for (size_t r = 0; r < row; r += 5) {
+        dst[r] = src[r];
+        dst[r + 1] = src[r] ? H.dev_of[src[r + 1]] : -1;
+        dst[r + 2] = src[r + 2];
+        dst[r + 3] = src[r + 3];
+        dst[r + 4] = src[r + 4];
+        if (src[r]) F->pair_level[H.leaves[k].l] = true;
+      }
+    }
+    FC_CUDA(dmalloc(&F->d_pairs, tab.size()));
+    FC_CUDA(cudaMemcpyAsync(F->d_pairs, tab.data(), sizeof(int) * tab.size(),
+                            cudaMemcpyHostToDevice, g_alloc_stream));
+    // (pageable source: the copy has taken the data when it returns)
+  }
   return metrics ? update_metrics(F) : FC_OK;
 }
 
@@ -473,6 +557,7 @@ DevForest<real> dev(const fc_forest* F) {
   D.mx = H.desc.mx;
   D.S = H.desc.mx + 2 * kMbc;
   D.npatch = H.npatch();
+  D.napi = H.napi();
   D.domain = H.desc.domain;
   D.meta = F->d_meta;
   D.nbr = F->d_nbr;
@@ -510,7 +595,8 @@ AdvArgs adv_args(const fc_forest* F, int L, double t, double dt, int n) {
   a.t0_dev = (F->capture_pairs || F->rel_time) ? F->d_t0 : nullptr;
   a.variant = ADV_STAGED;
   a.warps = 4;
-  a.ctas = 0;
+  a.ctas = F->walk_ctas;
+  a.wait_limit = F->wait_polls;
   a.gather = 0;
   a.tlevel = -1;
   a.alpha = 0.0;
@@ -624,7 +710,10 @@ fc_status ensure_streams(fc_forest* F) {
 template <typename real>
 fc_status advance_level_t(fc_forest* F, int L, double t, double dt, cudaStream_t s) {
   const HostForest& H = F->host;
-  const int p0 = H.lev_start[L], p1 = H.lev_start[L + 1];
+  // updated: the level's patches (a partition: its owned ones); held: any
+  // patch of the level here, mirrors included, whose state buffer turns over
+  const int p0 = H.lev_start[L], p1 = H.upd_end(L);
+  const bool held = H.lev_start[L + 1] > p0;
   int tlevel = -1;
   double alpha = 0.0;
   if (L > H.desc.lmin && F->has_old[L - 1] && F->dt_last[L - 1] > 0.0) {
@@ -718,8 +807,8 @@ fc_status advance_level_t(fc_forest* F, int L, double t, double dt, cudaStream_t
       FC_CUDA(cudaEventRecord(F->ev_post[L], s));
       F->post_ok[L] = true;
     }
-    F->cur[L] ^= 1;
   }
+  if (held) F->cur[L] ^= 1;
   F->has_old[L] = true;
   F->t_start[L] = t;
   F->dt_last[L] = dt;
@@ -732,42 +821,60 @@ fc_status advance_level(fc_forest* F, int L, double t, double dt, cudaStream_t s
 }
 
 // refluxing of level L after one of its updates of length dt: with nfs
-// finer substeps of weight w (see fc_step_multirate)
+// finer substeps of weight w (see fc_step_multirate); on the cubed sphere
+// from the host pairing, whose fluxes are volume fluxes (the weight is the
+// time ratio alone, 2 w) and which also exchanges the cube edges' fluxes
+bool reflux_due(const fc_forest* F, int L) {
+  const HostForest& H = F->host;
+  if (!F->bflux || H.lev_start[L + 1] <= H.lev_start[L]) return false;
+  if (F->d_pairs) return F->pair_level[L];
+  return L < H.desc.lmax && H.lev_start[L + 2] > H.lev_start[L + 1];
+}
+
 fc_status reflux_level(fc_forest* F, int L, double dt, int nfs, double w, cudaStream_t s) {
   const HostForest& H = F->host;
   const int p0 = H.lev_start[L], p1 = H.lev_start[L + 1];
-  if (!F->bflux || p1 <= p0 || L >= H.desc.lmax || H.lev_start[L + 2] <= p1) return FC_OK;
-  const double nu = dt / (std::ldexp(1.0, -L) / H.desc.mx);
+  if (!reflux_due(F, L)) return FC_OK;
   Timed tm(F, 3, s, 0.0);
-  const cudaError_t e =
-      F->esize == 4 ? launch_reflux(dev<float>(F), p0, p1, static_cast<const float*>(F->bflux),
-                                    F->bslot[L], nfs, w, nu, s)
-                    : launch_reflux(dev<double>(F), p0, p1, static_cast<const double*>(F->bflux),
-                                    F->bslot[L], nfs, w, nu, s);
+  cudaError_t e;
+  if (F->d_pairs) {
+    e = F->esize == 4
+            ? launch_reflux_pairs(dev<float>(F), p0, p1, static_cast<const float*>(F->bflux),
+                                  F->d_pairs, F->bslot[L], nfs, 2.0 * w, dt, s)
+            : launch_reflux_pairs(dev<double>(F), p0, p1, static_cast<const double*>(F->bflux),
+                                  F->d_pairs, F->bslot[L], nfs, 2.0 * w, dt, s);
+  } else {
+    const double nu = dt / (std::ldexp(1.0, -L) / H.desc.mx);
+    e = F->esize == 4 ? launch_reflux(dev<float>(F), p0, p1, static_cast<const float*>(F->bflux),
+                                      F->bslot[L], nfs, w, nu, s)
+                      : launch_reflux(dev<double>(F), p0, p1,
+                                      static_cast<const double*>(F->bflux), F->bslot[L], nfs, w,
+                                      nu, s);
+  }
   return e == cudaSuccess ? FC_OK : cuda_fail(e, "reflux");
 }
 
 fc_status multirate(fc_forest* F, int L, double t, double dt, cudaStream_t s) {
   fc_status st = advance_level(F, L, t, dt, s);
   if (st != FC_OK) return st;
-  if (L < F->host.desc.lmax) {
+  const int lmax = F->host.desc.lmax;
+  if (L < lmax) {
     if ((st = multirate(F, L + 1, t, 0.5 * dt, s)) != FC_OK) return st;
     if ((st = multirate(F, L + 1, t + 0.5 * dt, 0.5 * dt, s)) != FC_OK) return st;
-    const HostForest& H = F->host;
-    if (F->bflux && H.lev_start[L + 1] > H.lev_start[L]) {
-      // after both finer substeps (their fluxes written, their reads of this
-      // level's states done); on a captured step's level stream, and the
-      // level's post-update event moves past the correction (what the
-      // coarser level and this level's next substep read)
-      if (F->dag_levels) {
-        s = F->lev_stream[L];
-        if (F->post_ok[L + 1]) FC_CUDA(cudaStreamWaitEvent(s, F->ev_post[L + 1], 0));
-      }
-      if ((st = reflux_level(F, L, dt, 2, 0.25, s)) != FC_OK) return st;
-      if (F->dag) {
-        FC_CUDA(cudaEventRecord(F->ev_post[L], s));
-        F->post_ok[L] = true;
-      }
+  }
+  if (reflux_due(F, L)) {
+    // after both finer substeps (their fluxes written, their reads of this
+    // level's states done); on a captured step's level stream, and the
+    // level's post-update event moves past the correction (what the coarser
+    // level and this level's next substep read)
+    if (F->dag_levels) {
+      s = F->lev_stream[L];
+      if (L < lmax && F->post_ok[L + 1]) FC_CUDA(cudaStreamWaitEvent(s, F->ev_post[L + 1], 0));
+    }
+    if ((st = reflux_level(F, L, dt, 2, 0.25, s)) != FC_OK) return st;
+    if (F->dag) {
+      FC_CUDA(cudaEventRecord(F->ev_post[L], s));
+      F->post_ok[L] = true;
     }
   }
   return FC_OK;
@@ -811,8 +918,7 @@ fc_status check_desc(const fc_forest_desc* d) {
     return fail(FC_ERR_INVALID_ARG, "bad scheme options");
   if (d->indicator < 0 || d->indicator > 1 || d->smooth < 0 || d->smooth > 1)
     return fail(FC_ERR_INVALID_ARG, "bad regrid policy");
-  if (d->reflux < 0 || d->reflux > 1 || (d->reflux && d->domain == FC_DOMAIN_SPHERE))
-    return fail(FC_ERR_INVALID_ARG, "refluxing is built for the square domains (reflux 0 or 1)");
+  if (d->reflux < 0 || d->reflux > 1) return fail(FC_ERR_INVALID_ARG, "reflux must be 0 or 1");
   return FC_OK;
 }
 
@@ -828,6 +934,49 @@ uint64_t fc_launch_count(int reset) {
   uint64_t v = launch_counter();
   if (reset) launch_counter() = 0;
   return v;
+}
+
+fc_status fc_set_allocator(fc_alloc_fn alloc, fc_free_fn release, void* user) {
+  if ((alloc == nullptr) != (release == nullptr))
+    return fail(FC_ERR_INVALID_ARG, "fc_set_allocator: give both functions or neither");
+  if (g_live_forests.load() != 0)
+    return fail(FC_ERR_STATE, "fc_set_allocator: forests are alive (destroy them first)");
+  g_hook = AllocHook{alloc, release, user};
+  return FC_OK;
+}
+
+fc_status fc_forest_info(const fc_forest* F, fc_info* out) {
+  if (!F || !out) return fail(FC_ERR_INVALID_ARG, "null argument");
+  const HostForest& H = F->host;
+  std::memset(out, 0, sizeof *out);
+  out->nleaves = H.napi();
+  out->nforests = H.desc.nforests;
+  out->mx = H.desc.mx;
+  out->mbc = H.desc.mbc;
+  out->lmin = H.desc.lmin;
+  out->lmax = H.desc.lmax;
+  out->dtype = H.desc.dtype;
+  out->domain = H.desc.domain;
+  for (int l = 0; l <= kMaxLevel && l < FC_INFO_LEVELS; ++l)
+    out->leaves_per_level[l] = H.lev_start[l + 1] - H.lev_start[l];
+  const size_t S = (size_t)H.desc.mx + 2 * kMbc;
+  const size_t n = (size_t)std::max(H.npatch(), 1);
+  const size_t store = n * S * S * F->esize;
+  size_t bytes = 4 * store;  // two state buffers, the time-interpolated tiles, the stage
+  if (F->bflux) bytes += n * 2 * 4 * H.desc.mx * F->esize;
+  bytes += sizeof(NbrEntry) * n * 8 + sizeof(PatchMeta) * n + 3 * sizeof(double) * n;
+  if (F->d_metric) bytes += sizeof(double) * n * metric_stride((int)S);
+  if (F->d_corner) bytes += sizeof(double) * n * 3 * (S + 1) * (S + 1);
+  for (void* b : F->lam) bytes += b ? store : 0;
+  for (void* b : F->madj) bytes += b ? store : 0;
+  if (F->mio) bytes += n * H.desc.mx * H.desc.mx * F->esize;
+  bytes += F->msnap_bytes;
+  out->device_bytes = (int64_t)bytes;
+  out->graphs = (int)(F->graphs.size() + F->adj_graphs.size());
+  int tuned = 0;
+  for (const auto& t : F->tune) tuned += t.tuned ? 1 : 0;
+  out->tuned_buckets = tuned;
+  return FC_OK;
 }
 
 fc_status fc_forest_create(const fc_forest_desc* desc, int nleaves, const int* leaves,
@@ -860,11 +1009,13 @@ fc_status fc_forest_create(const fc_forest_desc* desc, int nleaves, const int* l
     return st;
   }
   *out = F;
+  g_live_forests.fetch_add(1);
   return FC_OK;
 }
 
 fc_status fc_forest_destroy(fc_forest* F) {
   if (!F) return FC_OK;
+  g_live_forests.fetch_sub(1);
   cudaDeviceSynchronize();
   destroy_timers(F);
   if (F->cap_stream) cudaStreamDestroy(F->cap_stream);
@@ -907,8 +1058,9 @@ fc_status fc_timers_read(fc_forest* F, int phase, double* ms, int64_t* launches,
   return FC_OK;
 }
 
-fc_status fc_mass_noalloc(const void* q, int dtype, int mx, int nleaves, const int* level,
-                          const int* forest_start, int nforests, double* out, void* stream) {
+fc_status fc_mass_noalloc(const void* q, const double* capacity, int dtype, int mx, int nleaves,
+                          const int* level, const int* forest_start, int nforests, double* out,
+                          void* stream) {
   if (!q || !level || !forest_start || !out)
     return fail(FC_ERR_INVALID_ARG, "fc_mass_noalloc: null pointer");
   if (dtype != FC_F32 && dtype != FC_F64)
@@ -919,9 +1071,37 @@ fc_status fc_mass_noalloc(const void* q, int dtype, int mx, int nleaves, const i
     return fail(FC_ERR_INVALID_ARG, "fc_mass_noalloc: nleaves " + std::to_string(nleaves) +
                                         " exceeds FC_NOALLOC_MAX_LEAVES (" +
                                         std::to_string(FC_NOALLOC_MAX_LEAVES) + ")");
-  cudaError_t e = noalloc_mass(q, dtype, mx, nleaves, level, forest_start, nforests, out,
-                               as_stream(stream));
+  cudaError_t e = noalloc_mass(q, capacity, dtype, mx, nleaves, level, forest_start, nforests,
+                               out, as_stream(stream));
   if (e != cudaSuccess) return cuda_fail(e, "fc_mass_noalloc");
+  return FC_OK;
+}
+
+fc_status fc_forest_get_capacity(const fc_forest* F, double* out, int on_device, void* stream) {
+  if (!F || !out) return fail(FC_ERR_INVALID_ARG, "null argument");
+  cudaStream_t s = as_stream(stream);
+  const size_t n = (size_t)F->host.napi() * F->host.desc.mx * F->host.desc.mx;
+  double* dst = out;
+  if (!on_device && F->esize < sizeof(double)) {
+    // the staging buffer holds a float field: stage through a temporary
+    AllocStream alloc_on(s);
+    if (dmalloc(&dst, n) != cudaSuccess) return fail(FC_ERR_OOM, "staging allocation failed");
+  } else if (!on_device) {
+    dst = static_cast<double*>(F->stage);
+  }
+  const cudaError_t e =
+      F->esize == 4 ? launch_pack_capacity(dev<float>(F), F->d_api_to_dev, dst, s)
+                    : launch_pack_capacity(dev<double>(F), F->d_api_to_dev, dst, s);
+  if (e != cudaSuccess) return cuda_fail(e, "pack capacity");
+  if (!on_device) {
+    FC_CUDA(cudaMemcpyAsync(out, dst, n * sizeof(double), cudaMemcpyDeviceToHost, s));
+    if (dst != F->stage) {
+      AllocStream alloc_on(s);
+      dfree(dst);
+    }
+    FC_CUDA(cudaStreamSynchronize(s));
+    return check_device_error(const_cast<fc_forest*>(F), s);
+  }
   return FC_OK;
 }
 
@@ -931,6 +1111,15 @@ fc_status fc_set_advance_variant(fc_forest* F, int variant, int warps) {
   F->forced_variant = variant;
   F->forced_warps = warps;
   destroy_graphs(F);
+  return FC_OK;
+}
+
+fc_status fc_set_limits(fc_forest* F, int walk_ctas, int64_t wait_polls) {
+  if (!F || walk_ctas < 0 || wait_polls > (int64_t)UINT32_MAX)
+    return fail(FC_ERR_INVALID_ARG, "walk_ctas must be >= 0 and wait_polls < 2^32");
+  F->walk_ctas = walk_ctas;
+  F->wait_polls = wait_polls < 0 ? kWaitLimit : (uint32_t)wait_polls;
+  destroy_graphs(F);  // captured launches carry the old values
   return FC_OK;
 }
 
@@ -955,7 +1144,7 @@ fc_status fc_autotune(fc_forest* F, int* report, void* stream) {
   DevForest<double> Dd = dev<double>(F);
   fc_status st = FC_OK;
   for (int L = H.desc.lmin; L <= H.desc.lmax && st == FC_OK; ++L) {
-    const int p0 = H.lev_start[L], p1 = H.lev_start[L + 1];
+    const int p0 = H.lev_start[L], p1 = H.upd_end(L);
     if (p1 <= p0) continue;
     fc_forest::Tune& t = F->tune[size_bucket(p1 - p0)];
     if (t.tuned) continue;
@@ -1351,11 +1540,118 @@ static fc_status adjoint_multirate_t(fc_forest* F, double t0, double dtc, void* 
   return FC_OK;
 }
 
+// Adjoint of one level substep (fc_adjoint_advance): the forward fill of the
+// substep is redone (separate kernels: ghost rings in the store, the coarse
+// neighbours' time-interpolated tiles in qT), then the substep's transposes
+// run on four accumulators in tile layout: the current states' adjoint (the
+// level's entries read and cleared, the finer level's and the coarser
+// level's newer-state shares added), the level's state before the substep,
+// the older states' adjoint and the qT tiles' adjoint.
+template <typename real>
+static fc_status adjoint_advance_t(fc_forest* F, int L, double t, double dt, void* lam,
+                                   void* lam_old, double* dscale, cudaStream_t s) {
+  AllocStream alloc_on(s);
+  const HostForest& H = F->host;
+  const size_t S = (size_t)H.desc.mx + 2 * kMbc;
+  const size_t cells = std::max<size_t>((size_t)H.npatch() * S * S, 1);
+  int tlevel = -1;
+  double alpha = 0.0;
+  if (L > H.desc.lmin && F->has_old[L - 1] && F->dt_last[L - 1] > 0.0) {
+    tlevel = L - 1;
+    alpha = (t - F->t_start[L - 1]) / F->dt_last[L - 1];
+    alpha = std::min(1.0, std::max(0.0, alpha));
+  }
+  if (tlevel >= 0 && !lam_old)
+    return fail(FC_ERR_INVALID_ARG,
+                "fc_adjoint_advance: level-1 is time-interpolated; lam_old is needed");
+  for (auto& b : F->madj)
+    if (!b && dmalloc_bytes(&b, cells * sizeof(real)) != cudaSuccess)
+      return fail(FC_ERR_OOM, "adjoint buffer allocation failed");
+  if (!F->lam[0] && dmalloc_bytes(&F->lam[0], cells * sizeof(real)) != cudaSuccess)
+    return fail(FC_ERR_OOM, "adjoint buffer allocation failed");
+  real* LQ = static_cast<real*>(F->madj[0]);
+  real* LB = static_cast<real*>(F->madj[1]);
+  real* LT = static_cast<real*>(F->madj[2]);
+  real* LO = static_cast<real*>(F->lam[0]);
+  DevForest<real> D = dev<real>(F);
+  const int p0 = H.lev_start[L], p1 = H.lev_start[L + 1];
+  // the substep's forward fill, as fc_advance_level does it with separate fills
+  FillArgs A{F->d_lists + F->off_a[L], (int)H.list_a[L].size(), tlevel, alpha};
+  FillArgs B{F->d_lists + F->off_b[L], (int)H.list_b[L].size(), tlevel, alpha};
+  if (p1 > p0) {
+    FC_CUDA(launch_fill_coarse(D, A, s));
+    FC_CUDA(launch_fill_fine(D, B, s));
+  }
+  for (real* b : {LQ, LB, LT, LO}) FC_CUDA(cudaMemsetAsync(b, 0, cells * sizeof(real), s));
+  DevForest<real> Lv = dev<real>(F);
+  for (int l = 0; l <= kMaxLevel; ++l) Lv.cur[l] = 0;
+  Lv.buf[0] = Lv.buf[1] = LQ;
+  FC_CUDA(launch_unpack(Lv, F->d_api_to_dev, static_cast<const real*>(lam), s));
+  if (lam_old) {
+    Lv.buf[0] = Lv.buf[1] = LO;
+    FC_CUDA(launch_unpack(Lv, F->d_api_to_dev, static_cast<const real*>(lam_old), s));
+  }
+  if (p1 > p0) {
+    AdjSubArgs g{};
+    g.L = L;
+    g.p0 = p0;
+    g.p1 = p1;
+    g.t = t;
+    g.dt = dt;
+    g.t0_dev = nullptr;
+    g.period = H.desc.vel[0];
+    g.scale = F->vel_scale;
+    g.dscale_factor = F->vel_scale != 0.0 ? 1.0 / F->vel_scale : 0.0;
+    g.tlevel = tlevel;
+    g.alpha = alpha;
+    g.list_a = F->d_lists + F->off_a[L];
+    g.na = (int)H.list_a[L].size();
+    g.list_b = F->d_lists + F->off_b[L];
+    g.nb = (int)H.list_b[L].size();
+    g.list_t = F->d_lists + F->off_t[L];
+    g.nt = (int)H.list_t[L].size();
+    AdjAcc<real> c{};
+    c.lam_in = LQ;     // level L's entries: the new state's adjoint, read then cleared
+    c.lam_out = LB;    // level L before the substep
+    c.lam_fine = LQ;   // level L + 1, read at its current state
+    c.lam_new = LQ;    // level L - 1, the newer state of the interpolation
+    c.lam_old = LO;    // level L - 1, the older state
+    c.lamT = LT;
+    Timed tm(F, 3, s, 0.0);
+    FC_CUDA(launch_adjoint_substep(D, g, c, dscale, s));
+  }
+  FC_CUDA(launch_add_store(LQ, LB, cells, s));
+  Lv.buf[0] = Lv.buf[1] = LQ;
+  FC_CUDA(launch_pack(Lv, F->d_api_to_dev, static_cast<real*>(lam), 0, s));
+  if (lam_old) {
+    Lv.buf[0] = Lv.buf[1] = LO;
+    FC_CUDA(launch_pack(Lv, F->d_api_to_dev, static_cast<real*>(lam_old), 0, s));
+  }
+  return FC_OK;
+}
+
 extern "C" {
+
+fc_status fc_adjoint_advance(fc_forest* F, int level, double t, double dt, void* lam,
+                             void* lam_old, double* dscale, void* stream) {
+  if (!F || !lam || !dscale) return fail(FC_ERR_INVALID_ARG, "null argument");
+  if (F->host.partial) return fail(FC_ERR_STATE, "the adjoint is built for whole forests");
+  if (level < F->host.desc.lmin || level > F->host.desc.lmax)
+    return fail(FC_ERR_INVALID_ARG, "level outside [lmin, lmax]");
+  if (!(dt > 0.0)) return fail(FC_ERR_INVALID_ARG, "dt must be positive");
+  if (F->host.desc.domain == FC_DOMAIN_SPHERE)
+    return fail(FC_ERR_INVALID_ARG, "the adjoint is built for the square domains");
+  if (F->host.desc.reflux)
+    return fail(FC_ERR_PRECONDITION, "the adjoint is built without refluxing");
+  cudaStream_t s = as_stream(stream);
+  return F->esize == 4 ? adjoint_advance_t<float>(F, level, t, dt, lam, lam_old, dscale, s)
+                       : adjoint_advance_t<double>(F, level, t, dt, lam, lam_old, dscale, s);
+}
 
 fc_status fc_adjoint_step_multirate(fc_forest* F, double t, double dt_coarse, void* lam,
                                     double* dscale, void* stream) {
   if (!F || !lam || !dscale) return fail(FC_ERR_INVALID_ARG, "null argument");
+  if (F->host.partial) return fail(FC_ERR_STATE, "the adjoint is built for whole forests");
   if (!(dt_coarse > 0.0)) return fail(FC_ERR_INVALID_ARG, "dt must be positive");
   if (F->host.desc.domain == FC_DOMAIN_SPHERE)
     return fail(FC_ERR_INVALID_ARG, "the adjoint is built for the square domains");
@@ -1371,6 +1667,7 @@ fc_status fc_adjoint_step_multirate(fc_forest* F, double t, double dt_coarse, vo
 fc_status fc_adjoint_step_global(fc_forest* F, double t, double dt, void* lam, double* dscale,
                                  void* stream) {
   if (!F || !lam || !dscale) return fail(FC_ERR_INVALID_ARG, "null argument");
+  if (F->host.partial) return fail(FC_ERR_STATE, "the adjoint is built for whole forests");
   if (!(dt > 0.0)) return fail(FC_ERR_INVALID_ARG, "dt must be positive");
   if (F->host.desc.domain == FC_DOMAIN_SPHERE)
     return fail(FC_ERR_INVALID_ARG, "the adjoint is built for the square domains");
@@ -1397,13 +1694,13 @@ fc_status fc_set_graphs(fc_forest* F, int enable) {
 
 fc_status fc_forest_num_leaves(const fc_forest* F, int* n) {
   if (!F || !n) return fail(FC_ERR_INVALID_ARG, "null argument");
-  *n = F->host.npatch();
+  *n = F->host.napi();
   return FC_OK;
 }
 
 fc_status fc_forest_leaves(const fc_forest* F, int* out) {
   if (!F || !out) return fail(FC_ERR_INVALID_ARG, "null argument");
-  for (int k = 0; k < F->host.npatch(); ++k) {
+  for (int k = 0; k < F->host.napi(); ++k) {
     const Leaf& a = F->host.leaves[k];
     out[5 * k] = a.f;
     out[5 * k + 1] = a.b;
@@ -1417,7 +1714,7 @@ fc_status fc_forest_leaves(const fc_forest* F, int* out) {
 fc_status fc_forest_set_q(fc_forest* F, const void* q, int on_device, void* stream) {
   if (!F || !q) return fail(FC_ERR_INVALID_ARG, "null argument");
   cudaStream_t s = as_stream(stream);
-  const size_t bytes = (size_t)F->host.npatch() * F->host.desc.mx * F->host.desc.mx * F->esize;
+  const size_t bytes = (size_t)F->host.napi() * F->host.desc.mx * F->host.desc.mx * F->esize;
   const void* src = q;
   if (!on_device) {
     FC_CUDA(cudaMemcpyAsync(F->stage, q, bytes, cudaMemcpyHostToDevice, s));
@@ -1437,7 +1734,7 @@ static fc_status get_q_impl(const fc_forest* F, void* q, int on_device, void* st
   cudaStream_t s = as_stream(stream);
   const size_t per = full ? (size_t)(F->host.desc.mx + 4) * (F->host.desc.mx + 4)
                           : (size_t)F->host.desc.mx * F->host.desc.mx;
-  const size_t bytes = (size_t)F->host.npatch() * per * F->esize;
+  const size_t bytes = (size_t)F->host.napi() * per * F->esize;
   void* dst = on_device ? q : F->stage;
   cudaError_t e = F->esize == 4
                       ? launch_pack(dev<float>(F), F->d_api_to_dev, (float*)dst, full, s)
@@ -1483,7 +1780,7 @@ fc_status fc_step_global(fc_forest* F, double t, double dt, void* stream) {
   DevForest<float> Df = dev<float>(F);
   DevForest<double> Dd = dev<double>(F);
   for (int L = H.desc.lmin; L <= H.desc.lmax; ++L) {
-    const int p0 = H.lev_start[L], p1 = H.lev_start[L + 1];
+    const int p0 = H.lev_start[L], p1 = H.upd_end(L);  // (a partition: its owned patches)
     if (p1 <= p0) continue;
     const AdvArgs a = adv_args(F, L, t, dt, p1 - p0);
     if ((st = deform_fluxes(F, p0, p1, a, s)) != FC_OK) return st;
@@ -1494,7 +1791,7 @@ fc_status fc_step_global(fc_forest* F, double t, double dt, void* stream) {
   }
   for (int l = 0; l <= kMaxLevel; ++l) F->cur[l] ^= 1;
   // refluxing: every level took one step of dt, one fine step per face
-  for (int L = H.desc.lmin; L < H.desc.lmax && F->bflux; ++L) {
+  for (int L = H.desc.lmin; L <= H.desc.lmax && F->bflux; ++L) {
     F->bslot[L] = 0;
     if ((st = reflux_level(F, L, dt, 1, 0.5, s)) != FC_OK) return st;
   }
@@ -1504,6 +1801,9 @@ fc_status fc_step_global(fc_forest* F, double t, double dt, void* stream) {
 
 fc_status fc_step_multirate(fc_forest* F, double t, double dt_coarse, void* stream) {
   if (!F) return fail(FC_ERR_INVALID_ARG, "null forest");
+  if (F->host.partial)
+    return fail(FC_ERR_STATE, "a partitioned forest steps level by level (fc_advance_level), "
+                              "with a halo exchange after each substep");
   if (!(dt_coarse > 0.0)) return fail(FC_ERR_INVALID_ARG, "dt must be positive");
   cudaStream_t s = as_stream(stream);
   const int lmin = F->host.desc.lmin, lmax = F->host.desc.lmax;
@@ -1531,7 +1831,10 @@ fc_status fc_step_multirate(fc_forest* F, double t, double dt_coarse, void* stre
     }
     F->capture_pairs = &ng.pairs;
     F->dag = true;
-    F->dag_levels = F->fuse;
+    // with the per-launch timers on, the levels run one after another on one
+    // stream, so each timed launch has the GPU to itself (its event pair
+    // measures that kernel, not the levels sharing the SMs with it)
+    F->dag_levels = F->fuse && !F->timing;
     for (int l = 0; l <= kMaxLevel; ++l) {
       F->pre_ok[l] = F->post_ok[l] = false;
       F->lev_forked[l] = false;
@@ -1617,13 +1920,15 @@ fc_status fc_tag(fc_forest* F, double* delta_host, void* stream) {
   std::vector<double> dd(n);
   FC_CUDA(cudaMemcpyAsync(dd.data(), F->d_delta, sizeof(double) * n, cudaMemcpyDeviceToHost, s));
   FC_CUDA(cudaStreamSynchronize(s));
-  for (int k = 0; k < n; ++k) delta_host[k] = dd[F->host.dev_of[k]];
+  for (int k = 0; k < F->host.napi(); ++k) delta_host[k] = dd[F->host.dev_of[k]];
   return FC_OK;
 }
 
 fc_status fc_tag_regrid(fc_forest* F, double tau_refine, double tau_coarsen,
                         const int* lmax_per_forest, int* changed, void* stream) {
   if (!F) return fail(FC_ERR_INVALID_ARG, "null forest");
+  if (F->host.partial)
+    return fail(FC_ERR_STATE, "a partitioned forest keeps its layout (no regrid)");
   cudaStream_t s = as_stream(stream);
   const int n = F->host.npatch();
   std::vector<double> delta(n);
@@ -1761,6 +2066,8 @@ fc_status fc_tag_regrid(fc_forest* F, double tau_refine, double tau_coarsen,
   F->d_t0 = G->d_t0;
   F->d_metric = G->d_metric;
   F->d_corner = G->d_corner;
+  F->d_pairs = G->d_pairs;
+  std::memcpy(F->pair_level, G->pair_level, sizeof F->pair_level);
   for (int l = 0; l <= kMaxLevel; ++l) F->cur[l] = 0;
   reset_times(F);
   delete G;  // its device pointers now belong to F
@@ -1818,6 +2125,163 @@ fc_status fc_layout_reflux(const fc_forest_desc* desc, int nleaves, const int* l
   if (st != FC_OK) return st;
   const std::string err = H.reflux_pairs(out);
   return err.empty() ? FC_OK : fail(FC_ERR_STATE, err);
+}
+
+// field index of each of the caller's leaves (H built from them)
+static std::vector<int> caller_to_field(const HostForest& H, int nleaves, const int* leaves) {
+  std::vector<int> k_of(nleaves);
+  for (int i = 0; i < nleaves; ++i)
+    k_of[i] = H.find(leaves[5 * i], leaves[5 * i + 1], leaves[5 * i + 2], leaves[5 * i + 3],
+                     leaves[5 * i + 4]);
+  return k_of;
+}
+
+// the caller's per-leaf ranks in field order, checked
+static fc_status part_in_field_order(const HostForest& H, int nleaves, const int* leaves,
+                                     const int* part, std::vector<int>* out, int* nranks) {
+  const std::vector<int> k_of = caller_to_field(H, nleaves, leaves);
+  out->assign(nleaves, -1);
+  *nranks = 0;
+  for (int i = 0; i < nleaves; ++i) {
+    if (part[i] < 0) return fail(FC_ERR_INVALID_ARG, "partition: negative rank");
+    (*out)[k_of[i]] = part[i];
+    *nranks = std::max(*nranks, part[i] + 1);
+  }
+  return FC_OK;
+}
+
+fc_status fc_layout_partition(const fc_forest_desc* desc, int nleaves, const int* leaves,
+                              int nranks, int* part_out) {
+  if (!part_out || nranks < 1) return fail(FC_ERR_INVALID_ARG, "bad output or rank count");
+  HostForest H;
+  fc_status st = host_layout(desc, nleaves, leaves, &H);
+  if (st != FC_OK) return st;
+  const std::vector<int> part = partition_ranges(H, nranks);
+  const std::vector<int> k_of = caller_to_field(H, nleaves, leaves);
+  for (int i = 0; i < nleaves; ++i) part_out[i] = part[k_of[i]];
+  return FC_OK;
+}
+
+fc_status fc_layout_halo(const fc_forest_desc* desc, int nleaves, const int* leaves,
+                         const int* part, int rank, int* nmirror, int* mirror_out) {
+  if (!part || !nmirror || !mirror_out) return fail(FC_ERR_INVALID_ARG, "null argument");
+  HostForest H;
+  fc_status st = host_layout(desc, nleaves, leaves, &H);
+  if (st != FC_OK) return st;
+  std::vector<int> pf;
+  int nranks = 0;
+  if ((st = part_in_field_order(H, nleaves, leaves, part, &pf, &nranks)) != FC_OK) return st;
+  if (rank < 0 || rank >= nranks) return fail(FC_ERR_INVALID_ARG, "rank outside the partition");
+  const std::vector<int> m = partition_mirrors(H, pf, rank);
+  // field index -> the caller's index
+  const std::vector<int> k_of = caller_to_field(H, nleaves, leaves);
+  std::vector<int> caller_of(nleaves);
+  for (int i = 0; i < nleaves; ++i) caller_of[k_of[i]] = i;
+  *nmirror = (int)m.size();
+  for (size_t j = 0; j < m.size(); ++j) mirror_out[j] = caller_of[m[j]];
+  return FC_OK;
+}
+
+fc_status fc_forest_create_part(const fc_forest_desc* desc, int nleaves, const int* leaves,
+                                const int* part, int rank, fc_forest** out) {
+  if (!out || !part) return fail(FC_ERR_INVALID_ARG, "null argument");
+  *out = nullptr;
+  if (desc && desc->reflux)
+    return fail(FC_ERR_INVALID_ARG, "a partitioned forest is built without refluxing");
+  HostForest G;
+  fc_status st = host_layout(desc, nleaves, leaves, &G);
+  if (st != FC_OK) return st;
+  std::vector<int> pf;
+  int nranks = 0;
+  if ((st = part_in_field_order(G, nleaves, leaves, part, &pf, &nranks)) != FC_OK) return st;
+  fc_forest* F = new (std::nothrow) fc_forest();
+  if (!F) return fail(FC_ERR_OOM, "host allocation failed");
+  F->esize = desc->dtype == FC_F32 ? 4 : 8;
+  const std::string err = build_partition(G, pf, rank, &F->host);
+  if (!err.empty()) {
+    delete F;
+    return fail(FC_ERR_INVALID_ARG, err);
+  }
+  keep_pool_memory();
+  const HostForest& H = F->host;
+  st = upload(F, true);
+  // the exchange lists, one block: per (level or all, rank) the send list,
+  // then the receive list
+  std::vector<int> lists;
+  F->halo_off.assign((size_t)(kMaxLevel + 2) * nranks * 2 + 1, 0);
+  for (int l = 0; l <= kMaxLevel + 1; ++l)
+    for (int r = 0; r < nranks; ++r)
+      for (int dir = 0; dir < 2; ++dir) {
+        F->halo_off[((size_t)l * nranks + r) * 2 + dir] = lists.size();
+        for (int lv = (l <= kMaxLevel ? l : 0); lv <= (l <= kMaxLevel ? l : kMaxLevel); ++lv) {
+          const std::vector<int>& v = dir == 0 ? H.send[lv][r] : H.recv[lv][r];
+          lists.insert(lists.end(), v.begin(), v.end());
+        }
+      }
+  F->halo_off.back() = lists.size();
+  if (st == FC_OK && dmalloc(&F->d_halo, lists.size()) != cudaSuccess)
+    st = fail(FC_ERR_OOM, "exchange list allocation failed");
+  if (st == FC_OK && !lists.empty() &&
+      cudaMemcpyAsync(F->d_halo, lists.data(), sizeof(int) * lists.size(),
+                      cudaMemcpyHostToDevice, g_alloc_stream) != cudaSuccess)
+    st = cuda_fail(cudaGetLastError(), "exchange lists");
+  if (st == FC_OK && cudaStreamSynchronize(0) != cudaSuccess)
+    st = cuda_fail(cudaGetLastError(), "create");
+  if (st != FC_OK) {
+    free_device(F);
+    cudaStreamSynchronize(0);
+    delete F;
+    return st;
+  }
+  *out = F;
+  g_live_forests.fetch_add(1);
+  return FC_OK;
+}
+
+// one exchange list of a partition: (device pointer, count)
+static fc_status halo_list(const fc_forest* F, int peer, int level, int dir, const int** p,
+                           int* n) {
+  const HostForest& H = F->host;
+  if (!H.partial) return fail(FC_ERR_STATE, "not a partitioned forest");
+  if (peer < 0 || peer >= H.nranks || peer == H.rank)
+    return fail(FC_ERR_INVALID_ARG, "peer must be another rank of the partition");
+  if (level != -1 && (level < 0 || level > kMaxLevel))
+    return fail(FC_ERR_INVALID_ARG, "level must be -1 (all) or a level");
+  const int l = level < 0 ? kMaxLevel + 1 : level;
+  const size_t at = ((size_t)l * H.nranks + peer) * 2 + dir;
+  *p = F->d_halo + F->halo_off[at];
+  *n = (int)(F->halo_off[at + 1] - F->halo_off[at]);
+  return FC_OK;
+}
+
+fc_status fc_halo_count(const fc_forest* F, int peer, int level, int* nsend, int* nrecv) {
+  if (!F || !nsend || !nrecv) return fail(FC_ERR_INVALID_ARG, "null argument");
+  const int* p;
+  fc_status st = halo_list(F, peer, level, 0, &p, nsend);
+  if (st == FC_OK) st = halo_list(F, peer, level, 1, &p, nrecv);
+  return st;
+}
+
+static fc_status halo_move(const fc_forest* F, int peer, int level, void* buf, int pack,
+                           void* stream) {
+  if (!F || !buf) return fail(FC_ERR_INVALID_ARG, "null argument");
+  const int* list;
+  int n = 0;
+  fc_status st = halo_list(F, peer, level, pack ? 0 : 1, &list, &n);
+  if (st != FC_OK) return st;
+  cudaStream_t s = as_stream(stream);
+  const cudaError_t e =
+      F->esize == 4 ? launch_halo(dev<float>(F), list, n, static_cast<float*>(buf), pack, s)
+                    : launch_halo(dev<double>(F), list, n, static_cast<double*>(buf), pack, s);
+  return e == cudaSuccess ? FC_OK : cuda_fail(e, "halo exchange");
+}
+
+fc_status fc_halo_pack(const fc_forest* F, int peer, int level, void* dst, void* stream) {
+  return halo_move(F, peer, level, dst, 1, stream);
+}
+
+fc_status fc_halo_unpack(fc_forest* F, int peer, int level, const void* src, void* stream) {
+  return halo_move(F, peer, level, const_cast<void*>(src), 0, stream);
 }
 
 fc_status fc_layout_regrid(const fc_forest_desc* desc, int nleaves, const int* leaves,

@@ -99,7 +99,6 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint32
   return false;
 }
 
-constexpr uint32_t kWaitLimit = 1u << 22;
 
 // 1D bulk copy global -> shared (TMA), completion counted on `bar`.
 // dst, src 16-byte aligned; bytes a multiple of 16.

@@ -29,7 +29,16 @@ constexpr int kMbc = 2;  // ghost layers built into the kernels
 // (interpolate), outside the physical domain (boundary condition), or the
 // corner region beyond a cube vertex of the cubed sphere, where only three
 // blocks meet and no block holds the diagonal cells (Sec. 2.4).
-enum NbrKind : int { NB_EXTERIOR = 0, NB_SAME = 1, NB_FINE = 2, NB_COARSE = 3, NB_CORNER3 = 4 };
+// NB_ABSENT marks, in one rank's part of a partitioned layout, a region of a
+// mirror patch whose neighbour that rank does not hold: no kernel reads it.
+enum NbrKind : int {
+  NB_EXTERIOR = 0,
+  NB_SAME = 1,
+  NB_FINE = 2,
+  NB_COARSE = 3,
+  NB_CORNER3 = 4,
+  NB_ABSENT = 5
+};
 
 // Region order: faces -x, +x, -y, +y, then corners (-,-), (+,-), (-,+), (+,+).
 constexpr int kDirX[8] = {-1, 1, 0, 0, -1, 1, -1, 1};
@@ -252,6 +261,25 @@ struct HostForest {
   std::vector<int> forest_start;         // leaves of forest f: [forest_start[f], forest_start[f+1])
   std::vector<char> feeds_finer;         // device order: coarser neighbour of a patch one level finer
 
+  // One rank's part of a partitioned layout (Sec. 3, partitioning): `leaves`
+  // holds the owned leaves (field order) followed by the mirrors -- leaves of
+  // other ranks whose interiors the owned leaves' ghost fills read -- and the
+  // device order puts each level's owned patches first: level l's owned
+  // patches are [lev_start[l], own_end[l]).  The field layout of get/set
+  // covers the owned leaves only.
+  bool partial = false;
+  int nowned = 0;
+  int own_end[kMaxLevel + 1] = {0};
+  // halo exchange with each other rank, per level: local device indices of
+  // the owned patches that rank mirrors (send) and of this rank's mirrors
+  // that rank owns (recv), both in the global field order
+  std::vector<std::vector<int>> send[kMaxLevel + 1], recv[kMaxLevel + 1];
+  int nranks = 1, rank = 0;
+  // leaves in the field layout of get/set (all, or the owned ones)
+  int napi() const { return partial ? nowned : (int)leaves.size(); }
+  // end of level l's patches that an update advances
+  int upd_end(int l) const { return partial ? own_end[l] : lev_start[l + 1]; }
+
   // Build everything from `leaves`; returns an empty string or an error.
   std::string build();
   // rows of `nbr` and `meta` for the leaves [kb, ke) (field order); marks
@@ -302,6 +330,22 @@ struct HostForest {
   int npatch() const { return (int)leaves.size(); }
 };
 
+// The mirrors of `rank` in a built layout G under the partition `part` (per
+// leaf of G, field order): the leaves of other ranks whose interiors the
+// ghost fills of rank's leaves read -- their face and corner neighbours and,
+// for a coarser neighbour, its same-size and finer neighbours (whose copies
+// and averages the interpolation reads, Prop. 1) -- as field indices of G in
+// field order.
+std::vector<int> partition_mirrors(const HostForest& G, const std::vector<int>& part, int rank);
+// Contiguous ranges of G's field order weighted by level work (2^(l - lmin)
+// updates per coarse step), one per rank: part[k] for each leaf of G.
+std::vector<int> partition_ranges(const HostForest& G, int nranks);
+// rank's part of G (H: empty): its owned leaves and mirrors, the neighbour
+// rows of G restricted to them, the work lists restricted to what the owned
+// leaves' updates and fills need, and the exchange lists with every rank.
+std::string build_partition(const HostForest& G, const std::vector<int>& part, int rank,
+                            HostForest* H);
+
 // Regrid: new leaf list and remap list (in the new field order).
 std::string regrid_layout(const HostForest& F, const std::vector<double>& delta, double tau_r,
                           double tau_c, const std::vector<int>& lmax_f,
@@ -335,6 +379,7 @@ __host__ __device__ inline void cube_face(int b, int* n, int* ex, int* ey) {
 template <typename real>
 struct DevForest {
   int mx, S, npatch, domain;
+  int napi;  // leaves in the field layout (get/set, mass): npatch, or the owned ones
   const double* metric;  // cubed sphere: metric_stride(S) doubles per patch; else null
   const PatchMeta* meta;
   const NbrEntry* nbr;
@@ -364,7 +409,11 @@ struct AdvArgs {
   const double* t0_dev;
   int variant;  // ADV_STAGED or ADV_WALK
   int warps;    // walk variant: warps per CTA
-  int ctas;     // walk variant: CTAs in the grid (0: one per group of patches)
+  int ctas;     // walk variant: cap on the CTAs in the grid (0: the SMs' residency)
+  // polls of a kernel's bounded wait for its tile copy before it gives up
+  // (FC_ERR_TIMEOUT); the copies in flight are then still awaited with the
+  // default limit before the CTA leaves
+  uint32_t wait_limit;
   // gather != 0: the kernel fills each patch's ghost ring itself (Alg. 1 in
   // shared memory) before the update; coarser neighbours on `tlevel` are
   // read through the time-interpolation buffer
@@ -455,6 +504,8 @@ cudaError_t launch_adjoint_substep(const DevForest<real>& D, const AdjSubArgs& g
 
 // device error word bits
 constexpr int kErrTimeout = 1;
+// polls of a bounded device wait before it gives up (default)
+constexpr uint32_t kWaitLimit = 1u << 22;
 
 template <typename real>
 cudaError_t launch_fill_coarse(const DevForest<real>& D, const FillArgs& A, cudaStream_t s);
@@ -471,6 +522,12 @@ cudaError_t launch_tag(const DevForest<real>& D, int kind, double* delta, cudaSt
 template <typename real>
 cudaError_t launch_reflux(const DevForest<real>& D, int p0, int p1, const real* bflux, int cslot,
                           int nfs, double w, double nu, cudaStream_t s);
+// refluxing on the cubed sphere from the host pairing (pairs: per device
+// patch, face and face cell 5 ints: kind, patch across, its face, j0, j1)
+template <typename real>
+cudaError_t launch_reflux_pairs(const DevForest<real>& D, int p0, int p1, const real* bflux,
+                                const int* pairs, int cslot, int nfs, double w, double dt,
+                                cudaStream_t s);
 template <typename real>
 cudaError_t launch_mass(const DevForest<real>& D, const int* api_to_dev, const int* fstart,
                         int nforests, double* patch_sums, double* out, cudaStream_t s);
@@ -507,7 +564,20 @@ cudaError_t launch_deform_fluxes(int p0, int p1, int mx, const double* corner, d
                                  const double* t0_dev, double t_off, cudaStream_t s);
 
 // fc_mass_noalloc's kernels (scratch in a file-scope device array)
-cudaError_t noalloc_mass(const void* q, int dtype, int mx, int nleaves, const int* level,
-                         const int* fstart, int nforests, double* out, cudaStream_t s);
+cudaError_t noalloc_mass(const void* q, const double* capacity, int dtype, int mx, int nleaves,
+                         const int* level, const int* fstart, int nforests, double* out,
+                         cudaStream_t s);
+// a partition's halo exchange: pack (pack != 0) the interiors of the listed
+// patches into buf, or unpack buf into them
+template <typename real>
+cudaError_t launch_halo(const DevForest<real>& D, const int* list, int n, real* buf, int pack,
+                        cudaStream_t s);
+// dst += src over n values (adjoint accumulators)
+template <typename real>
+cudaError_t launch_add_store(real* dst, const real* src, size_t n, cudaStream_t s);
+// interior cell capacities in field order (h^2, or kappa on the cubed sphere)
+template <typename real>
+cudaError_t launch_pack_capacity(const DevForest<real>& D, const int* api_to_dev, double* out,
+                                 cudaStream_t s);
 
 }  // namespace fc

@@ -769,3 +769,185 @@ std::string regrid_layout(const HostForest& F, const std::vector<double>& delta,
 }
 
 }  // namespace fc
+
+namespace fc {
+
+// ------------------------------------------------------------------ partition
+//
+// Sec. 3 (partitioning): the leaves, in their Morton (field) order, are split
+// into contiguous ranges of equal work, a level-l leaf weighing 2^(l - lmin)
+// (its updates per coarse step).  Each rank holds its own leaves plus the
+// mirrors its ghost fills read; one exchange per level substep refreshes the
+// mirrors from their owners (Sec. 3, parallel ghost filling).
+
+std::vector<int> partition_ranges(const HostForest& G, int nranks) {
+  const int n = G.npatch(), lmin = G.desc.lmin;
+  std::vector<double> cum(n + 1, 0.0);
+  for (int k = 0; k < n; ++k) cum[k + 1] = cum[k] + std::ldexp(1.0, G.leaves[k].l - lmin);
+  const double W = cum[n];
+  std::vector<int> part(n);
+  for (int k = 0; k < n; ++k) {
+    // the rank whose share of the work holds this leaf's midpoint
+    const double mid = 0.5 * (cum[k] + cum[k + 1]);
+    int r = (int)(mid * nranks / W);
+    part[k] = std::min(std::max(r, 0), nranks - 1);
+  }
+  return part;
+}
+
+std::vector<int> partition_mirrors(const HostForest& G, const std::vector<int>& part, int rank) {
+  const int n = G.npatch();
+  std::vector<char> need(n, 0);
+  auto mark = [&](int dev) {
+    if (dev < 0) return;
+    const int k = G.api_of[dev];
+    if (part[k] != rank) need[k] = 1;
+  };
+  for (int k = 0; k < n; ++k) {
+    if (part[k] != rank) continue;
+    const int p = G.dev_of[k];
+    for (int dir = 0; dir < 8; ++dir) {
+      const NbrEntry& e = G.nbr[(size_t)p * 8 + dir];
+      mark(e.n0);
+      mark(e.n1);
+      if (e.kind != NB_COARSE) continue;
+      // the coarse neighbour's ghosts that the interpolation reads come from
+      // its same-size and finer neighbours (copies and averages)
+      for (int d2 = 0; d2 < 8; ++d2) {
+        const NbrEntry& c = G.nbr[(size_t)e.n0 * 8 + d2];
+        if (c.kind == NB_SAME || c.kind == NB_FINE) {
+          mark(c.n0);
+          mark(c.n1);
+        }
+      }
+    }
+  }
+  std::vector<int> out;
+  for (int k = 0; k < n; ++k)
+    if (need[k]) out.push_back(k);
+  return out;
+}
+
+std::string build_partition(const HostForest& G, const std::vector<int>& part, int rank,
+                            HostForest* H) {
+  const int n = G.npatch();
+  int nranks = 0;
+  for (int r : part) nranks = std::max(nranks, r + 1);
+  if (rank < 0 || rank >= nranks) return "rank outside the partition";
+  std::vector<std::vector<int>> mirrors(nranks);
+  for (int r = 0; r < nranks; ++r) mirrors[r] = partition_mirrors(G, part, r);
+  // local leaves: owned (field order), then mirrors (field order)
+  std::vector<int> local;  // G field index of each local leaf
+  for (int k = 0; k < n; ++k)
+    if (part[k] == rank) local.push_back(k);
+  const int nowned = (int)local.size();
+  if (nowned == 0) return "rank owns no leaf";
+  for (int k : mirrors[rank]) local.push_back(k);
+  const int nl = (int)local.size();
+  std::vector<int> loc_of(n, -1);  // G field index -> local field index
+  for (int i = 0; i < nl; ++i) loc_of[local[i]] = i;
+
+  H->desc = G.desc;
+  H->partial = true;
+  H->nowned = nowned;
+  H->nranks = nranks;
+  H->rank = rank;
+  H->dense = false;
+  H->leaves.resize(nl);
+  for (int i = 0; i < nl; ++i) H->leaves[i] = G.leaves[local[i]];
+  H->idx.clear(nl, G.desc.nforests);
+  for (int i = 0; i < nl; ++i) {
+    const Leaf& a = H->leaves[i];
+    H->idx.insert(leaf_key(a.f, a.b, a.l, a.x, a.y), i);
+  }
+  // the field layout covers the owned leaves
+  H->forest_start.assign(G.desc.nforests + 1, 0);
+  for (int i = 0; i < nowned; ++i) H->forest_start[H->leaves[i].f + 1]++;
+  for (int f = 0; f < G.desc.nforests; ++f) H->forest_start[f + 1] += H->forest_start[f];
+  // device order: by level, each level's owned patches first
+  for (int l = 0; l <= kMaxLevel + 1; ++l) H->lev_start[l] = 0;
+  for (const Leaf& a : H->leaves) H->lev_start[a.l + 1]++;
+  for (int l = 1; l <= kMaxLevel + 1; ++l) H->lev_start[l] += H->lev_start[l - 1];
+  H->api_of.assign(nl, 0);
+  H->dev_of.assign(nl, 0);
+  {
+    int next[kMaxLevel + 1];
+    for (int l = 0; l <= kMaxLevel; ++l) next[l] = H->lev_start[l];
+    for (int pass = 0; pass < 2; ++pass)
+      for (int i = pass ? nowned : 0; i < (pass ? nl : nowned); ++i) {
+        const int p = next[H->leaves[i].l]++;
+        H->api_of[p] = i;
+        H->dev_of[i] = p;
+      }
+    // owned patches were placed first: level l's end of them
+    for (int l = 0; l <= kMaxLevel; ++l) H->own_end[l] = H->lev_start[l];
+    for (int i = 0; i < nowned; ++i) H->own_end[H->leaves[i].l]++;
+  }
+  // rows of G restricted to the local leaves; a neighbour not held here
+  // makes the region NB_ABSENT (only mirrors have such regions)
+  H->meta.resize(nl);
+  H->nbr.resize((size_t)nl * 8);
+  H->feeds_finer.assign(nl, 0);
+  auto to_local_dev = [&](int gdev) -> int {
+    if (gdev < 0) return -1;
+    const int i = loc_of[G.api_of[gdev]];
+    return i < 0 ? -1 : H->dev_of[i];
+  };
+  for (int i = 0; i < nl; ++i) {
+    const int gp = G.dev_of[local[i]], p = H->dev_of[i];
+    H->meta[p] = G.meta[gp];
+    for (int dir = 0; dir < 8; ++dir) {
+      NbrEntry e = G.nbr[(size_t)gp * 8 + dir];
+      const bool two = e.n1 >= 0;
+      const int a0 = to_local_dev(e.n0), a1 = to_local_dev(e.n1);
+      if ((e.n0 >= 0 && a0 < 0) || (two && a1 < 0)) {
+        if (i < nowned) return "partition: an owned leaf's neighbour is not held";
+        e.kind = NB_ABSENT;
+        e.n0 = e.n1 = -1;
+      } else {
+        e.n0 = a0;
+        e.n1 = a1;
+      }
+      H->nbr[(size_t)p * 8 + dir] = e;
+      if (i < nowned && e.kind == NB_COARSE) H->feeds_finer[e.n0] = 1;
+    }
+  }
+  // work lists of what the owned leaves' updates and fills touch
+  H->list_all.clear();
+  H->list_coarse_all.clear();
+  for (int p = 0; p < nl; ++p) {
+    const bool own = H->api_of[p] < nowned;
+    if (own || H->feeds_finer[p]) H->list_all.push_back(p);
+    if (own && (H->meta[p].flags & 1)) H->list_coarse_all.push_back(p);
+  }
+  for (int l = 0; l <= kMaxLevel; ++l) {
+    H->list_a[l].clear();
+    H->list_b[l].clear();
+    H->list_t[l].clear();
+    if (l > 0)
+      for (int p = H->lev_start[l - 1]; p < H->lev_start[l]; ++p)
+        if (H->feeds_finer[p]) {
+          H->list_a[l].push_back(p);
+          H->list_t[l].push_back(p);
+        }
+    for (int p = H->lev_start[l]; p < H->own_end[l]; ++p) {
+      H->list_a[l].push_back(p);
+      if (H->meta[p].flags & 1) H->list_b[l].push_back(p);
+    }
+  }
+  // exchange lists with every other rank, per level, in G's field order
+  for (int l = 0; l <= kMaxLevel; ++l) {
+    H->send[l].assign(nranks, {});
+    H->recv[l].assign(nranks, {});
+  }
+  for (int r = 0; r < nranks; ++r) {
+    if (r == rank) continue;
+    for (int k : mirrors[r])
+      if (part[k] == rank) H->send[G.leaves[k].l][r].push_back(H->dev_of[loc_of[k]]);
+    for (int k : mirrors[rank])
+      if (part[k] == r) H->recv[G.leaves[k].l][r].push_back(H->dev_of[loc_of[k]]);
+  }
+  return "";
+}
+
+}  // namespace fc

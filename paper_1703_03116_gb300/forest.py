@@ -142,6 +142,19 @@ class Forest:
         check(fn(self._h, a.ctypes.data_as(ctypes.c_void_p), 0, _stream(stream)))
         return a
 
+    def capacity(self, out=None, stream=None):
+        """Interior cell capacities (n, mx, mx) in FP64: h^2, or kappa on the sphere."""
+        n, mx = len(self), self.mx
+        if out is not None and hasattr(out, "is_cuda") and out.is_cuda:
+            assert out.is_contiguous() and out.numel() == n * mx * mx
+            check(load().fc_forest_get_capacity(self._h, ctypes.c_void_p(out.data_ptr()), 1,
+                                                _stream(stream)))
+            return out
+        a = np.empty((n, mx, mx))
+        check(load().fc_forest_get_capacity(self._h, a.ctypes.data_as(ctypes.c_void_p), 0,
+                                            _stream(stream)))
+        return a
+
     # ----------------------------------------------------------------- stepping
     def fill_ghosts(self, stream=None):
         check(load().fc_fill_ghosts(self._h, _stream(stream)))
@@ -180,6 +193,11 @@ class Forest:
         """Force 0 staged / 1 walk / 2 walk1 for every launch; -1 restores the tuned choice."""
         check(load().fc_set_advance_variant(self._h, variant, warps))
 
+    def set_limits(self, walk_ctas: int = 0, wait_polls: int = -1):
+        """Cap the walk grid (0: residency) and set the update kernels' bounded
+        wait (polls; negative: default) -- see fc_set_limits."""
+        check(load().fc_set_limits(self._h, int(walk_ctas), int(wait_polls)))
+
     def set_velocity_scale(self, scale: float):
         check(load().fc_set_velocity_scale(self._h, float(scale)))
 
@@ -189,6 +207,29 @@ class Forest:
         assert lam.is_cuda and lam.is_contiguous() and dscale.is_cuda
         check(load().fc_adjoint_step_global(self._h, t, dt, ctypes.c_void_p(lam.data_ptr()),
                                             ctypes.c_void_p(dscale.data_ptr()), _stream(stream)))
+
+    def adjoint_advance(self, level: int, t: float, dt: float, lam, lam_old, dscale,
+                        stream=None):
+        """Adjoint of fc_advance_level(level, t, dt) from the state before it:
+        lam (CUDA tensor, field layout) in place; lam_old (same, or None when
+        level-1 is not time-interpolated) accumulates the older states' share;
+        dscale (CUDA float64, 1 element) += the velocity-scale derivative."""
+        assert lam.is_cuda and lam.is_contiguous() and dscale.is_cuda
+        lo = None
+        if lam_old is not None:
+            assert lam_old.is_cuda and lam_old.is_contiguous()
+            lo = ctypes.c_void_p(lam_old.data_ptr())
+        check(load().fc_adjoint_advance(self._h, level, t, dt, ctypes.c_void_p(lam.data_ptr()),
+                                        lo, ctypes.c_void_p(dscale.data_ptr()),
+                                        _stream(stream)))
+
+    def info(self) -> dict:
+        """Leaf counts per level, device bytes held, captured graphs (fc_forest_info)."""
+        i = _lib.Info()
+        check(load().fc_forest_info(self._h, ctypes.byref(i)))
+        out = {n: getattr(i, n) for n, _ in _lib.Info._fields_ if n != "leaves_per_level"}
+        out["leaves_per_level"] = list(i.leaves_per_level)
+        return out
 
     def adjoint_step_multirate(self, t: float, dt_coarse: float, lam, dscale, stream=None):
         """Adjoint of one coarse multirate step from the current state (left
@@ -239,6 +280,50 @@ def initial_forest(desc: Desc, q0: Callable[[np.ndarray], np.ndarray],
         F.tag_regrid(tau_r, tau_c, lmax_f, stream=stream)
     F.set_q(q0(F.leaves()), stream=stream)
     return F
+
+
+_ALLOCATOR = None  # the callbacks in use (kept alive while the library holds them)
+
+
+def set_allocator(alloc=None, release=None) -> None:
+    """Route every device allocation of the library through alloc(bytes, stream)
+    -> int pointer and release(ptr, bytes, stream) (fc_set_allocator); no
+    arguments restores the stream-ordered pool.  Only while no forest exists."""
+    global _ALLOCATOR
+    if alloc is None:
+        check(load().fc_set_allocator(None, None, None))
+        _ALLOCATOR = None
+        return
+
+    def a(nbytes, stream, user):
+        try:
+            return int(alloc(int(nbytes), stream or 0)) or None
+        except Exception:
+            return None
+
+    def r(ptr, nbytes, stream, user):
+        try:
+            release(int(ptr), int(nbytes), stream or 0)
+        except Exception:
+            pass
+
+    cb = (_lib.ALLOC_FN(a), _lib.FREE_FN(r))
+    check(load().fc_set_allocator(ctypes.cast(cb[0], ctypes.c_void_p),
+                                  ctypes.cast(cb[1], ctypes.c_void_p), None))
+    _ALLOCATOR = cb
+
+
+def torch_allocator():
+    """(alloc, release) over torch's CUDA caching allocator, for set_allocator."""
+    import torch
+
+    def alloc(nbytes, stream):
+        return torch.cuda.caching_allocator_alloc(nbytes, torch.cuda.current_device(), stream)
+
+    def release(ptr, nbytes, stream):
+        torch.cuda.caching_allocator_delete(ptr)
+
+    return alloc, release
 
 
 def layout_check(desc: Desc, leaves) -> None:

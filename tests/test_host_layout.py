@@ -228,7 +228,7 @@ def test_regrid_layout_batched_forests_matches_oracle():
 
 
 def test_reflux_option_checked():
-    """Refluxing is built for the square domains, as 0 or 1."""
+    """Refluxing is an option, 0 or 1, on the square domains and the sphere."""
     w = synth.swirl(1, lmin=2, lmax=3, mx=8)
     lv = oracle.initial_forest(w).leaves()
     d = desc_for(w)
@@ -239,8 +239,7 @@ def test_reflux_option_checked():
         fc.layout_check(d, lv)
     s = fc.make_desc(domain=fc.SPHERE, mx=8, lmin=0, lmax=1,
                      velocity=("rotation", 0.0, 0.0, 1.0), reflux=1)
-    with pytest.raises(fc.FcError, match="INVALID_ARG"):
-        fc.layout_check(s, fc.uniform_leaves(0, nblocks=6))
+    fc.layout_check(s, fc.uniform_leaves(0, nblocks=6))
 
 
 def test_deformational_flow_option_checked():
