@@ -46,11 +46,21 @@ typedef enum {
 } fc_status;
 
 typedef enum { FC_F32 = 0, FC_F64 = 1 } fc_dtype;
-typedef enum { FC_DOMAIN_WALLS = 0, FC_DOMAIN_PERIODIC = 1, FC_DOMAIN_SPHERE = 2 } fc_domain;
+typedef enum {
+  FC_DOMAIN_WALLS = 0,
+  FC_DOMAIN_PERIODIC = 1,
+  FC_DOMAIN_SPHERE = 2,
+  FC_DOMAIN_BRICK = 3
+} fc_domain;
 typedef enum { FC_VEL_CONST = 0, FC_VEL_SWIRL = 1, FC_VEL_ROTATION = 2, FC_VEL_DEFORM = 3 } fc_velocity;
 
 /* Problem description (Sec. 2; Sec. 5.1 "Problem setup").
- *   domain      unit square with walls, periodic unit square, or cubed sphere.
+ *   domain      unit square with walls, periodic unit square, cubed sphere, or
+ *               a periodic brick (Sec. 5.1: a brick_nx x brick_ny arrangement
+ *               of unit blocks, each an adaptive quadtree; block
+ *               b = by * brick_nx + bx sits at [bx, bx+1] x [by, by+1], its
+ *               faces meet its neighbours' with the identity orientation,
+ *               and the brick's outer faces are periodic).
  *   nforests    independent forests in one store (a batched ensemble); each
  *               forest of a square domain is one block, each forest of the
  *               cubed sphere six blocks (Sec. 2.4): block b is the face of
@@ -108,6 +118,7 @@ typedef struct {
   int indicator;  /* regrid indicator: 0 max |grad q| / 2, 1 max q - min q (Sec. 5.1) */
   int smooth;     /* 1: smooth grading of the target levels (Sec. 3.3) */
   int reflux;     /* 1: refluxing at coarse/fine faces (an extension) */
+  int brick_nx, brick_ny;  /* FC_DOMAIN_BRICK: blocks per row and column (<= 256 in all) */
 } fc_forest_desc;
 
 /* Create a forest from an explicit leaf list (Sec. 2: quadrants identified

@@ -22,7 +22,7 @@ _SO_OMP = os.path.join(_HERE, "liboracle_omp.so")  # the same sources, patch loo
 _SRC = ["forest.c", "ghost.c", "claw.c", "drive.c", "adjoint.c", "sphere.c"]
 _HDR = ["oracle.h", "internal.h"]
 
-WALLS, PERIODIC, SPHERE = 0, 1, 2
+WALLS, PERIODIC, SPHERE, BRICK = 0, 1, 2, 3
 VEL_CONST, VEL_SWIRL, VEL_ROTATION, VEL_DEFORM = 0, 1, 2, 3
 
 
@@ -54,7 +54,7 @@ class _Params(ctypes.Structure):
         ("order", ctypes.c_int), ("limiter", ctypes.c_int),
         ("transverse", ctypes.c_int), ("vel_scale", ctypes.c_double),
         ("indicator", ctypes.c_int), ("smooth", ctypes.c_int),
-        ("reflux", ctypes.c_int),
+        ("reflux", ctypes.c_int), ("brick", ctypes.c_int * 2),
     ]
 
 
@@ -149,7 +149,7 @@ def _check(rc: int):
 def params(domain: int, mx: int, mbc: int, lmin: int, lmax: int, velocity,
            order: int = 2, limiter: int = 1, transverse: int = 2,
            nforests: int = 1, indicator: int = 0, smooth: int = 0,
-           reflux: int = 0) -> _Params:
+           reflux: int = 0, brick=(1, 1)) -> _Params:
     p = _Params()
     p.domain, p.nforests, p.mx, p.mbc, p.lmin, p.lmax = domain, nforests, mx, mbc, lmin, lmax
     if velocity[0] == "const":
@@ -171,6 +171,7 @@ def params(domain: int, mx: int, mbc: int, lmin: int, lmax: int, velocity,
     p.order, p.limiter, p.transverse = order, limiter, transverse
     p.vel_scale = 1.0
     p.indicator, p.smooth, p.reflux = indicator, smooth, reflux
+    p.brick[0], p.brick[1] = int(brick[0]), int(brick[1])
     return p
 
 
@@ -373,7 +374,7 @@ def minmod(a: float, b: float) -> float:
 
 # ---------------------------------------------------------------- workloads
 
-_DOMAIN = {"walls": WALLS, "periodic": PERIODIC, "sphere": SPHERE}
+_DOMAIN = {"walls": WALLS, "periodic": PERIODIC, "sphere": SPHERE, "brick": BRICK}
 _LIMITER = {"none": (2, 0), "lw": (2, 0), "mc": (2, 1), "first": (1, 0)}
 
 
@@ -386,7 +387,7 @@ def params_for(w, nforests: int = 1, lmax: Optional[int] = None) -> _Params:
                   w.lmax if lmax is None else lmax, w.velocity, order=order,
                   limiter=lim, transverse=w.transverse, nforests=nforests,
                   indicator=_INDICATOR[w.indicator], smooth=int(w.smooth),
-                  reflux=int(w.reflux))
+                  reflux=int(w.reflux), brick=w.brick)
 
 
 def initial_forest(workloads, lmax: Optional[int] = None) -> Forest:
@@ -404,7 +405,7 @@ def initial_forest(workloads, lmax: Optional[int] = None) -> Forest:
     lmax_all = max(w.lmax for w in workloads) if lmax is None else lmax
     prm = params_for(w0, nforests=nf, lmax=lmax_all)
     sphere = w0.domain == "sphere"
-    nb = 6 if sphere else 1
+    nb = 6 if sphere else w0.brick[0] * w0.brick[1] if w0.domain == "brick" else 1
     leaves = np.concatenate([uniform_leaves(w0.lmin, 1, nb) + np.array([f, 0, 0, 0, 0], np.int32)
                              for f in range(nf)])
     F = Forest(prm, leaves)

@@ -95,6 +95,18 @@ int or_locate(const or_forest* F, int f, int* b, double* x, double* y) {
     if (F->P.domain == OR_PERIODIC) {
       *x -= floor(*x);
       *y -= floor(*y);
+    } else if (F->P.domain == OR_BRICK) {
+      /* the point's place in the brick, wrapped periodically, gives its block */
+      const int nx = F->P.brick[0], ny = F->P.brick[1];
+      double X = (*b % nx) + *x, Y = (*b / nx) + *y;
+      X -= nx * floor(X / nx);
+      Y -= ny * floor(Y / ny);
+      int bx = (int)floor(X), by = (int)floor(Y);
+      if (bx >= nx) bx = nx - 1;
+      if (by >= ny) by = ny - 1;
+      *x = X - bx;
+      *y = Y - by;
+      *b = by * nx + bx;
     } else {
       int r = or_sphere_fold(b, x, y);
       if (r != 0) return r; /* -3: beyond a three-valent cube corner */
@@ -127,10 +139,22 @@ int or_touch(const or_forest* F, const or_leaf* a, const or_leaf* c) {
   long ay0 = (long)a->y << (LFINE - a->l), ay1 = (long)(a->y + 1) << (LFINE - a->l);
   long cx0 = (long)c->x << (LFINE - c->l), cx1 = (long)(c->x + 1) << (LFINE - c->l);
   long cy0 = (long)c->y << (LFINE - c->l), cy1 = (long)(c->y + 1) << (LFINE - c->l);
-  int nshift = (F->P.domain == OR_PERIODIC) ? 1 : 0;
+  /* the brick: both squares placed in the brick's frame (block (bx, by) at
+   * (bx R, by R)), the brick's extent being the period */
+  long PX = R, PY = R;
+  if (F->P.domain == OR_BRICK) {
+    const int nx = F->P.brick[0];
+    PX = R * nx;
+    PY = R * F->P.brick[1];
+    ax0 += (a->b % nx) * R, ax1 += (a->b % nx) * R, ay0 += (a->b / nx) * R, ay1 += (a->b / nx) * R;
+    cx0 += (c->b % nx) * R, cx1 += (c->b % nx) * R, cy0 += (c->b / nx) * R, cy1 += (c->b / nx) * R;
+  } else if (a->b != c->b) {
+    return 0;
+  }
+  int nshift = (F->P.domain == OR_PERIODIC || F->P.domain == OR_BRICK) ? 1 : 0;
   for (int sx = -nshift; sx <= nshift; ++sx)
     for (int sy = -nshift; sy <= nshift; ++sy) {
-      long dx = sx * R, dy = sy * R;
+      long dx = sx * PX, dy = sy * PY;
       if (ax0 <= cx1 + dx && cx0 + dx <= ax1 && ay0 <= cy1 + dy && cy0 + dy <= ay1) return 1;
     }
   return 0;

@@ -46,14 +46,14 @@
 extern "C" {
 #endif
 
-enum { OR_WALLS = 0, OR_PERIODIC = 1, OR_SPHERE = 2 };
+enum { OR_WALLS = 0, OR_PERIODIC = 1, OR_SPHERE = 2, OR_BRICK = 3 };
 enum { OR_VEL_CONST = 0, OR_VEL_SWIRL = 1, OR_VEL_ROTATION = 2 /* sphere: vel[0..2] = omega */,
        OR_VEL_DEFORM = 3 /* sphere: vel[0..2] = kappa, T, T_f of the Sec. 5.3 streamfunction */ };
 
 #define OR_MAXLEV 18
 
 typedef struct {
-  int domain;      /* OR_WALLS, OR_PERIODIC, OR_SPHERE */
+  int domain;      /* OR_WALLS, OR_PERIODIC, OR_SPHERE, OR_BRICK */
   int nforests;    /* independent forests (one block each for the square) */
   int mx, mbc;     /* interior cells per side, ghost layers */
   int lmin, lmax;  /* level range of the whole run */
@@ -68,6 +68,9 @@ typedef struct {
   int reflux;      /* 1: conservative correction of coarse cells at coarse/fine faces and, on
                       the sphere, of one side of every cube edge (an extension: the paper's
                       scheme has none) */
+  int brick[2];    /* OR_BRICK (Sec. 5.1): blocks per row and per column; block b covers
+                      [b % brick[0], +1] x [b / brick[0], +1] of the brick, whose outer
+                      faces are periodic */
 } or_params;
 
 typedef struct or_forest or_forest;

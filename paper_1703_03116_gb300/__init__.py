@@ -5,7 +5,7 @@ package only marshals arguments to it.  Importing it loads the library and
 fails loudly when it has not been built -- there is no CPU fallback.
 """
 from . import _lib
-from ._lib import F32, F64, PERIODIC, SPHERE, WALLS, Desc, FcError, load
+from ._lib import BRICK, F32, F64, PERIODIC, SPHERE, WALLS, Desc, FcError, load
 from .forest import (Forest, initial_forest, layout_check, layout_neighbours, layout_reflux,
                      layout_regrid, make_desc, set_allocator, torch_allocator, uniform_leaves)
 
@@ -13,7 +13,7 @@ load()
 
 __all__ = ["Forest", "Desc", "FcError", "make_desc", "initial_forest", "uniform_leaves",
            "layout_check", "layout_neighbours", "layout_reflux", "layout_regrid", "set_allocator",
-           "torch_allocator", "F32", "F64", "WALLS", "PERIODIC", "SPHERE"]
+           "torch_allocator", "F32", "F64", "WALLS", "PERIODIC", "SPHERE", "BRICK"]
 
 
 def launch_count(reset: bool = False) -> int:

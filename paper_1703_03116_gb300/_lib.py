@@ -11,7 +11,7 @@ FC_OK = 0
 STATUS = {0: "FC_OK", 1: "FC_ERR_INVALID_ARG", 2: "FC_ERR_PRECONDITION", 3: "FC_ERR_OOM",
           4: "FC_ERR_CUDA", 5: "FC_ERR_TIMEOUT", 6: "FC_ERR_STATE"}
 F32, F64 = 0, 1
-WALLS, PERIODIC, SPHERE = 0, 1, 2
+WALLS, PERIODIC, SPHERE, BRICK = 0, 1, 2, 3
 VEL_CONST, VEL_SWIRL, VEL_ROTATION, VEL_DEFORM = 0, 1, 2, 3
 
 INFO_LEVELS = 21
@@ -46,6 +46,7 @@ class Desc(ctypes.Structure):
         ("transverse", ctypes.c_int),
         ("indicator", ctypes.c_int), ("smooth", ctypes.c_int),
         ("reflux", ctypes.c_int),
+        ("brick_nx", ctypes.c_int), ("brick_ny", ctypes.c_int),
     ]
 
 

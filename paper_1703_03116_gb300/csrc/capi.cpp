@@ -753,11 +753,12 @@ fc_status advance_level_t(fc_forest* F, int L, double t, double dt, cudaStream_t
       // their coarse ghost regions filled); the update kernel then fills
       // each level-L patch's ghost ring in shared memory itself
       FillArgs A{F->d_lists + F->off_t[L], (int)H.list_t[L].size(), tlevel, alpha};
-      // the second substep of a pair (alpha > 0) waits on the level's first
-      // one; the staged update then computes the coarse cells it reads
-      // itself, so no fill launch sits between the two updates (the
-      // adjoint's replay keeps the filled tiles: it runs the fill)
-      const bool direct = tlevel >= 0 && alpha != 0.0 && a.variant == ADV_STAGED &&
+      // the staged update computes the time-interpolated coarse cells it
+      // reads itself, so no fill launch sits before it on the level's chain
+      // (at alpha = 0 from the coarser level's older state, which its
+      // running update does not write; the adjoint's replay keeps the
+      // filled tiles: it runs the fill)
+      const bool direct = tlevel >= 0 && a.variant == ADV_STAGED &&
                           H.desc.domain != FC_DOMAIN_SPHERE && !F->keep_qT && !F->keep_tiles;
       if (direct) A.ntargets = 0;
       a.direct = direct ? 1 : 0;
@@ -899,8 +900,11 @@ fc_status check_desc(const fc_forest_desc* d) {
   if (d->nforests < 1 || d->nforests > 65535) return fail(FC_ERR_INVALID_ARG, "bad nforests");
   if (d->dtype != FC_F32 && d->dtype != FC_F64) return fail(FC_ERR_INVALID_ARG, "bad dtype");
   if (d->domain != FC_DOMAIN_WALLS && d->domain != FC_DOMAIN_PERIODIC &&
-      d->domain != FC_DOMAIN_SPHERE)
+      d->domain != FC_DOMAIN_SPHERE && d->domain != FC_DOMAIN_BRICK)
     return fail(FC_ERR_INVALID_ARG, "bad domain");
+  if (d->domain == FC_DOMAIN_BRICK &&
+      (d->brick_nx < 1 || d->brick_ny < 1 || d->brick_nx * d->brick_ny > 256))
+    return fail(FC_ERR_INVALID_ARG, "a brick needs 1..256 blocks (brick_nx, brick_ny >= 1)");
   if (d->vel_kind != FC_VEL_CONST && d->vel_kind != FC_VEL_SWIRL &&
       d->vel_kind != FC_VEL_ROTATION && d->vel_kind != FC_VEL_DEFORM)
     return fail(FC_ERR_INVALID_ARG, "bad velocity kind");

@@ -114,13 +114,22 @@ struct Leaf {
   int f, b, l, x, y;
 };
 
+// forest (16 bits), block (8), level (5), x (17), y (18): levels up to 16
+// (x, y < 2^16) and up to 256 blocks
 inline uint64_t leaf_key(int f, int b, int l, int x, int y) {
-  return ((uint64_t)(uint32_t)f << 48) | ((uint64_t)(uint32_t)b << 45) |
-         ((uint64_t)(uint32_t)l << 40) | ((uint64_t)(uint32_t)x << 20) | (uint64_t)(uint32_t)y;
+  return ((uint64_t)(uint32_t)f << 48) | ((uint64_t)(uint32_t)b << 40) |
+         ((uint64_t)(uint32_t)l << 35) | ((uint64_t)(uint32_t)x << 18) | (uint64_t)(uint32_t)y;
 }
 inline Leaf leaf_of_key(uint64_t k) {
-  return Leaf{(int)(k >> 48), (int)((k >> 45) & 7), (int)((k >> 40) & 31), (int)((k >> 20) & 0xFFFFF),
-              (int)(k & 0xFFFFF)};
+  return Leaf{(int)(k >> 48), (int)((k >> 40) & 0xFF), (int)((k >> 35) & 31),
+              (int)((k >> 18) & 0x1FFFF), (int)(k & 0x3FFFF)};
+}
+
+// blocks of one forest: 6 cube faces, a brick's unit blocks, or one square
+inline int num_blocks(const fc_forest_desc& d) {
+  return d.domain == FC_DOMAIN_SPHERE ? 6
+         : d.domain == FC_DOMAIN_BRICK ? d.brick_nx * d.brick_ny
+                                       : 1;
 }
 
 // Leaf key -> int map with open addressing and linear probing (host tables

@@ -67,7 +67,7 @@ void sort_leaves(std::vector<Leaf>* v) {
   for (size_t i = 0; i < v->size(); ++i) (*v)[i] = ks[i].a;
 }
 
-static int nblocks(const fc_forest_desc& d) { return d.domain == FC_DOMAIN_SPHERE ? 6 : 1; }
+static int nblocks(const fc_forest_desc& d) { return num_blocks(d); }
 
 namespace {
 
@@ -171,11 +171,20 @@ bool move_quadrant(const fc_forest_desc& d, int b, int l, int x, int y, int mx, 
   m->corner3 = false;
   if (x >= 0 && x < N && y >= 0 && y < N) return true;
   if (d.domain == FC_DOMAIN_WALLS) return false;
-  if (d.domain == FC_DOMAIN_PERIODIC) {
-    if (x < 0) { m->x = x + N; m->fx = N * mx; }
-    if (x >= N) { m->x = x - N; m->fx = -N * mx; }
-    if (y < 0) { m->y = y + N; m->fy = N * mx; }
-    if (y >= N) { m->y = y - N; m->fy = -N * mx; }
+  if (d.domain == FC_DOMAIN_PERIODIC || d.domain == FC_DOMAIN_BRICK) {
+    // the periodic square wraps onto itself; a brick's block continues into
+    // the next block of its row or column (periodic at the brick's faces),
+    // in the identity orientation with the same level-l cell offsets
+    int dx = 0, dy = 0;
+    if (x < 0) { m->x = x + N; m->fx = N * mx; dx = -1; }
+    if (x >= N) { m->x = x - N; m->fx = -N * mx; dx = 1; }
+    if (y < 0) { m->y = y + N; m->fy = N * mx; dy = -1; }
+    if (y >= N) { m->y = y - N; m->fy = -N * mx; dy = 1; }
+    if (d.domain == FC_DOMAIN_BRICK) {
+      const int nx = d.brick_nx, ny = d.brick_ny;
+      const int bx = b % nx, by = b / nx;
+      m->b = ((by + dy + ny) % ny) * nx + (bx + dx + nx) % nx;
+    }
     return true;
   }
   // cubed sphere: one coordinate out -> fold across that cube edge; both out
@@ -693,7 +702,7 @@ void regrid_range(const HostForest& F, const std::vector<double>& delta, double 
   LeafSet s;
   s.d = &d;
   {
-    const int nb = d.domain == FC_DOMAIN_SPHERE ? 6 : 1;
+    const int nb = num_blocks(d);
     const int fa = k1 > k0 ? F.leaves[k0].f : 0, fb = k1 > k0 ? F.leaves[k1 - 1].f + 1 : 0;
     s.f0 = fa;
     s.lo.assign(fb - fa, 0);

@@ -15,10 +15,12 @@ _NP = {_lib.F32: np.float32, _lib.F64: np.float64}
 def make_desc(domain: int = _lib.WALLS, mx: int = 32, lmin: int = 2, lmax: int = 6,
               dtype: int = _lib.F64, velocity=("swirl", 4.0), order: int = 2,
               limiter: int = 1, transverse: int = 2, nforests: int = 1, mbc: int = 2,
-              indicator: int = 0, smooth: int = 0, reflux: int = 0) -> Desc:
+              indicator: int = 0, smooth: int = 0, reflux: int = 0, brick=(1, 1)) -> Desc:
+    """brick: (blocks per row, blocks per column) of the FC_DOMAIN_BRICK domain."""
     d = Desc()
     d.domain, d.nforests, d.mx, d.mbc, d.lmin, d.lmax, d.dtype = (
         domain, nforests, mx, mbc, lmin, lmax, dtype)
+    d.brick_nx, d.brick_ny = int(brick[0]), int(brick[1])
     if velocity[0] == "const":
         d.vel_kind = _lib.VEL_CONST
         d.vel[0], d.vel[1] = float(velocity[1]), float(velocity[2])
@@ -273,7 +275,8 @@ def initial_forest(desc: Desc, q0: Callable[[np.ndarray], np.ndarray],
 
     ``q0(leaves)`` returns the initial field (n, mx, mx) for a leaf array.
     """
-    nb = 6 if desc.domain == _lib.SPHERE else 1
+    nb = (6 if desc.domain == _lib.SPHERE else
+          desc.brick_nx * desc.brick_ny if desc.domain == _lib.BRICK else 1)
     F = Forest(desc, uniform_leaves(desc.lmin, desc.nforests, nb))
     for _ in range(desc.lmax - desc.lmin):
         F.set_q(q0(F.leaves()), stream=stream)

@@ -57,6 +57,13 @@ class Disc:
 
 
 @dataclasses.dataclass
+class DiscUnion:
+    """1 inside any of the discs (periodic distances in the unit block), else 0."""
+    centres: np.ndarray  # (k, 2)
+    radius: float = 0.3
+
+
+@dataclasses.dataclass
 class Workload:
     """One forest's problem description (parameters only, no numerics)."""
     name: str
@@ -80,6 +87,7 @@ class Workload:
     smooth: bool = False         # smooth grading of the target levels (Sec. 3.3)
     reflux: bool = False         # conservative coarse/fine correction (off in the paper)
     dt_lmin: Optional[float] = None  # fixed time step of level lmin (else from the CFL number)
+    brick: tuple = (1, 1)        # "brick" domain: blocks per row and per column
 
 
 def _rng(seed: int) -> np.random.Generator:
@@ -175,6 +183,27 @@ def _unit(v):
     return v / np.linalg.norm(v)
 
 
+def brick(seed: int = 0, n: int = 1, lmin: int = 4, lmax: int = 7, mx: int = 32,
+          steps: int = 160) -> Workload:
+    """Sec. 5.1's replicated problem: a periodic brick of 2^n x 2^n unit
+    blocks, each an adaptive quadtree holding the same tracer field (1 inside
+    one of five discs of radius 0.3, else 0; the paper shows the discs only
+    in a figure, so their centres are seeded, with periodic distances in the
+    block), the constant velocity (0.5, 0.5) of the streamfunction
+    -(x - y)/2, CFL 0.64 at the finest level, global steps, the spread
+    indicator with tau_r = 0.25, tau_c = 0.001, smooth grading, a regrid
+    every 2^(lmax - lmin) steps."""
+    g = _rng(seed)
+    centres = g.uniform(0.0, 1.0, (5, 2))
+    k = 1 << n
+    return Workload(
+        name=f"brick {k}x{k} levels {lmin}-{lmax} mx={mx}", domain="brick", mx=mx, mbc=2,
+        lmin=lmin, lmax=lmax, velocity=("const", 0.5, 0.5), limiter="mc", transverse=2,
+        cfl=0.64, parts=[DiscUnion(centres, 0.3)], steps=steps,
+        regrid_every=1 << (lmax - lmin), tau_refine=0.25, tau_coarsen=0.001,
+        indicator="maxmin", smooth=True, seed=seed, brick=(k, k))
+
+
 def sphere(seed: int = 0, lmin: int = 1, lmax: int = 7, mx: int = 32) -> Workload:
     """Cubed-sphere workload: solid-body rotation about a seeded axis with
     |omega| = 2 pi (one revolution in t = 1), two cosine bells (great-circle
@@ -254,6 +283,15 @@ def evaluate(w: Workload, x: np.ndarray, y: np.ndarray) -> np.ndarray:
                 dx = np.mod(dx, 1.0)
                 dy = np.mod(dy, 1.0)
             inside = (dx >= 0) & (dx < p.side) & (dy >= 0) & (dy < p.side)
+            q = q + inside.astype(np.float64)
+        elif isinstance(p, DiscUnion):
+            inside = np.zeros(q.shape, dtype=bool)
+            for c in p.centres:
+                dx = x - c[0]
+                dy = y - c[1]
+                dx = dx - np.round(dx)
+                dy = dy - np.round(dy)
+                inside |= (dx * dx + dy * dy) < p.radius * p.radius
             q = q + inside.astype(np.float64)
         elif isinstance(p, Disc):
             dx = x - p.centre[0]

@@ -9,13 +9,14 @@ F64_TOL = 1e-12   # FP64 path: max |gpu - oracle| / max |oracle|
 
 def desc_for(fc, w, dtype, nforests=1, lmax=None):
     order, lim = {"none": (2, 0), "lw": (2, 0), "mc": (2, 1), "first": (1, 0)}[w.limiter]
-    domain = {"walls": fc.WALLS, "periodic": fc.PERIODIC, "sphere": fc.SPHERE}[w.domain]
+    domain = {"walls": fc.WALLS, "periodic": fc.PERIODIC, "sphere": fc.SPHERE,
+              "brick": fc.BRICK}[w.domain]
     return fc.make_desc(domain=domain, mx=w.mx,
                         lmin=w.lmin, lmax=w.lmax if lmax is None else lmax, dtype=dtype,
                         velocity=w.velocity, order=order, limiter=lim,
                         transverse=w.transverse, nforests=nforests,
                         indicator={"gradient": 0, "maxmin": 1}[w.indicator],
-                        smooth=int(w.smooth), reflux=int(w.reflux))
+                        smooth=int(w.smooth), reflux=int(w.reflux), brick=w.brick)
 
 
 def pair(fc, workloads, dtype):

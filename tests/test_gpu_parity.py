@@ -235,19 +235,18 @@ def test_launch_counter_counts_kernels():
     fc.launch_count(reset=True)
     gpu.step_multirate(0.0, 0.01)
     assert fc.launch_count() == 3 * 2 + 2
-    # fused fill: level 2 one update; level 3's first substep the fill of its
-    # level-2 neighbours plus the update, its second the update alone (the
-    # staged update computes the time-interpolated coarse cells it reads)
+    # fused fill: one update per substep (the staged update fills its own
+    # ghosts and computes the time-interpolated coarse cells it reads)
     gpu.fused_fill(True)
     fc.launch_count(reset=True)
     gpu.step_multirate(0.01, 0.01)
-    assert fc.launch_count() == 1 + 2 + 1
+    assert fc.launch_count() == 1 + 1 + 1
     # graph replay: the same kernels plus the one that stores the step time
     gpu.graphs(True)
     for n in range(3):
         fc.launch_count(reset=True)
         gpu.step_multirate(0.01 * (n + 2), 0.01)
-        assert fc.launch_count() == 1 + 2 + 1 + 1
+        assert fc.launch_count() == 1 + 1 + 1 + 1
 
 
 @pytest.mark.parametrize("variant", [0, 1])
