@@ -57,6 +57,19 @@ __global__ void __launch_bounds__(NT, NT >= 512 ? (sizeof(real) == 4 ? 3 : 2)
   __shared__ NbrStage sco[8];  // a.direct: each coarse region's neighbour's entries
   __shared__ real ring[num_ghosts<MX>()];  // ghost values gathered while the tile loads
   __shared__ bool ring_w[num_ghosts<MX>()];
+  // Warp roles when the CTA has warps to spare beyond the ghost ring (mx =
+  // 32): the first NGT threads gather the ghosts while the others already
+  // compute the edges that read interior cells only (x-edges 2..MX-2 and
+  // y-edges 2..MX-2 of the interior rows / columns), taken in warp-sized
+  // chunks from a shared counter that the gathering warps join once their
+  // ghosts are stored; every edge is computed once, by the same formula, so
+  // the results are those of one pass over all edges.
+  constexpr int NGT = (num_ghosts<MX>() + 31) / 32 * 32;
+  constexpr bool SPLIT = NT - NGT >= 128;
+  constexpr int NI = (MX - 3) * MX;           // interior edges per direction
+  constexpr int NCHUNK = (2 * NI + 31) / 32;  // warp-sized chunks of them
+  constexpr int NB = 6 * MX + 2;              // boundary edges per direction
+  __shared__ int chunk_next;
   // capacity form: kappa, phi_x, phi_y of the patch (MS doubles) come first
   const double* Ms = reinterpret_cast<const double*>(smem_raw);
   real* Q = reinterpret_cast<real*>(smem_raw + sizeof(double) * MS);
@@ -80,6 +93,7 @@ __global__ void __launch_bounds__(NT, NT >= 512 ? (sizeof(real) == 4 ? 3 : 2)
 
   if (threadIdx.x == 0) {
     mbar_init(&bar, 1);
+    chunk_next = 0;
     if (swirl) {
       const double t = a.t0_dev ? *a.t0_dev + a.t_off : a.t_half;
       ucoef_s = cospi_ratio<real>(t, a.period) * real(a.sfac);
@@ -97,79 +111,6 @@ __global__ void __launch_bounds__(NT, NT >= 512 ? (sizeof(real) == 4 ? 3 : 2)
       mbar_expect_tx(&bar, bytes + mbytes);
       bulk_load(Q, src, bytes, &bar);
       if (CAP) bulk_load(smem_raw, D.metric + (size_t)p * MS, mbytes, &bar);
-    }
-    if (a.gather) stage_neighbours(D.meta, D.nbr, p, st, threadIdx.x);
-    // streamfunction tables while the tile is in flight:
-    // psi = s(x) s(y) cos(pi t/T)/pi, s = sin^2(pi .); along an edge the
-    // corner difference is s(corner) * sin(pi (z0 + z1)) * sin(pi h)
-    if (swirl) {
-      for (int k = threadIdx.x; k < NV; k += NT) {
-        const real xs = sinpi_r(real(pm.x * MX + k - 1) * h);
-        const real ys = sinpi_r(real(pm.y * MX + k - 1) * h);
-        Sx[k] = xs * xs;
-        Sy[k] = ys * ys;
-        Tx[k] = sinpi_r(real(2 * (pm.x * MX + k - 1) + 1) * h);
-        Ty[k] = sinpi_r(real(2 * (pm.y * MX + k - 1) + 1) * h);
-      }
-    }
-    // Alg. 1 for this patch, its neighbour reads while the tile is in
-    // flight: each thread computes the values of its ghost cells (copied from
-    // same-size or averaged from finer neighbours, interpolated from coarser
-    // ones; every ghost is one of these or exterior) into registers, stored
-    // into the tile once it has landed; then the wall condition (the
-    // exterior ghosts copy cells that are final by then) and, on the sphere,
-    // the corners beyond a cube vertex
-    constexpr int NG = num_ghosts<MX>();
-    if (a.gather) {
-      __syncthreads();  // the patch's entries
-      if (a.direct) {   // the coarse neighbours' entries (8 threads per region)
-        const int r = threadIdx.x >> 3;
-        if (r < 8 && st.e[r].kind == NB_COARSE && st.e[r].lev == a.tlevel)
-          stage_neighbours(D.meta, D.nbr, st.e[r].n0, sco[r], threadIdx.x & 7);
-        __syncthreads();
-      }
-      const real alpha = real(a.alpha);
-#pragma unroll 1
-      for (int k = threadIdx.x; k < NG; k += NT) {
-        int i, j;
-        ghost_ij<MX>(k, i, j);
-        real v;
-        const bool w =
-            copy_or_average<real, MX>(D, st, pm, a.tlevel, alpha, i, j, v) ||
-            (a.direct ? interpolate_direct<real, MX>(D, st, sco, pm, a.tlevel, alpha, i, j, v)
-                      : interpolate<real, MX>(D, st, pm, a.tlevel, i, j, v));
-        ring[k] = w ? v : real(0);
-        ring_w[k] = w;
-      }
-    }
-    // every thread observes the copy's completion (bounded); the CTA leaves
-    // together if any thread gave up
-    const bool landed = mbar_wait(&bar, parity, a.wait_limit);
-    if (!__syncthreads_and(landed)) {
-      if (threadIdx.x == 0) atomicOr(err, kErrTimeout);
-      mbar_wait(&bar, parity, kWaitLimit);  // let the copy land before leaving
-      return;
-    }
-    if (a.gather) {
-      for (int k = threadIdx.x; k < NG; k += NT)  // each thread its own cells
-        if (ring_w[k]) {
-          int i, j;
-          ghost_ij<MX>(k, i, j);
-          Q[(j + kMbc) * S + i + kMbc] = ring[k];
-        }
-      __syncthreads();
-      if (D.domain == FC_DOMAIN_WALLS) {
-        wall_bc<real, MX>(pm, Q, threadIdx.x, NT);
-        __syncthreads();
-      }
-      if (D.domain == FC_DOMAIN_SPHERE) {
-        corner3_fill<real, MX>(st, Q, threadIdx.x, NT);
-        __syncthreads();
-      }
-    }
-    if (a.keep) {  // the adjoint's replay keeps the ghost-filled input tile
-      real* kp = static_cast<real*>(a.keep) + (size_t)(p - a.keep_p0) * S * S;
-      for (int k = threadIdx.x; k < S * S; k += NT) kp[k] = Q[k];
     }
     auto q = [&](int i, int j) -> real { return Q[(j + 2) * S + (i + 2)]; };
     // capacity form: kappa of cell (i,j), flux through x-edge / y-edge (i,j)
@@ -189,31 +130,200 @@ __global__ void __launch_bounds__(NT, NT >= 512 ? (sizeof(real) == 4 ? 3 : 2)
     auto nu_y = [&](int i, int j) -> real {
       return CAP ? dt * (real(0.5) * (real(1) / kap(i, j - 1) + real(1) / kap(i, j))) : nu;
     };
-    // both sweeps: normal flux and fluctuations of every edge
-    for (int e = threadIdx.x; e < 2 * NE; e += NT) {
-      if (e < NE) {
-        const int i = e % (MX + 1), j = e / (MX + 1) - 1;
-        const real s = uvel(i, j);
-        const real sp = s > real(0) ? s : real(0), sm = s < real(0) ? s : real(0);
-        const real qm = q(i - 1, j), q0 = q(i, j);
-        const real W = q0 - qm;
-        const real Wup = s >= real(0) ? qm - q(i - 2, j) : q(i + 1, j) - q0;
-        const real Ft = correction(order, limiter, s, W, Wup, nu_x(i, j));
-        Fn[e] = sp * qm + sm * q0 + Ft;
-        XP[e] = transverse > 1 ? sp * W - Ft : sp * W;
-        XM[e] = transverse > 1 ? sm * W + Ft : sm * W;
-      } else {
-        const int f = e - NE;
-        const int i = f % (MX + 2) - 1, j = f / (MX + 2);
-        const real s = vvel(i, j);
-        const real sp = s > real(0) ? s : real(0), sm = s < real(0) ? s : real(0);
-        const real qm = q(i, j - 1), q0 = q(i, j);
-        const real W = q0 - qm;
-        const real Wup = s >= real(0) ? qm - q(i, j - 2) : q(i, j + 1) - q0;
-        const real Gt = correction(order, limiter, s, W, Wup, nu_y(i, j));
-        Gn[f] = sp * qm + sm * q0 + Gt;
-        YP[f] = transverse > 1 ? sp * W - Gt : sp * W;
-        YM[f] = transverse > 1 ? sm * W + Gt : sm * W;
+    // normal flux and fluctuations of x-edge (i, j) (cells (i-1,j) | (i,j))
+    // and of y-edge (i, j) (cells (i,j-1) | (i,j))
+    auto xedge = [&](int i, int j) {
+      const int e = (j + 1) * (MX + 1) + i;
+      const real s = uvel(i, j);
+      const real sp = s > real(0) ? s : real(0), sm = s < real(0) ? s : real(0);
+      const real qm = q(i - 1, j), q0 = q(i, j);
+      const real W = q0 - qm;
+      const real Wup = s >= real(0) ? qm - q(i - 2, j) : q(i + 1, j) - q0;
+      const real Ft = correction(order, limiter, s, W, Wup, nu_x(i, j));
+      Fn[e] = sp * qm + sm * q0 + Ft;
+      XP[e] = transverse > 1 ? sp * W - Ft : sp * W;
+      XM[e] = transverse > 1 ? sm * W + Ft : sm * W;
+    };
+    auto yedge = [&](int i, int j) {
+      const int f = j * (MX + 2) + (i + 1);
+      const real s = vvel(i, j);
+      const real sp = s > real(0) ? s : real(0), sm = s < real(0) ? s : real(0);
+      const real qm = q(i, j - 1), q0 = q(i, j);
+      const real W = q0 - qm;
+      const real Wup = s >= real(0) ? qm - q(i, j - 2) : q(i, j + 1) - q0;
+      const real Gt = correction(order, limiter, s, W, Wup, nu_y(i, j));
+      Gn[f] = sp * qm + sm * q0 + Gt;
+      YP[f] = transverse > 1 ? sp * W - Gt : sp * W;
+      YM[f] = transverse > 1 ? sm * W + Gt : sm * W;
+    };
+    // streamfunction tables (thread k0 + k for corner node k):
+    // psi = s(x) s(y) cos(pi t/T)/pi, s = sin^2(pi .); along an edge the
+    // corner difference is s(corner) * sin(pi (z0 + z1)) * sin(pi h)
+    auto tables = [&](int k0) {
+      if (!swirl) return;
+      const int k = (int)threadIdx.x - k0;
+      if (k >= 0 && k < NV) {
+        const real xs = sinpi_r(real(pm.x * MX + k - 1) * h);
+        const real ys = sinpi_r(real(pm.y * MX + k - 1) * h);
+        Sx[k] = xs * xs;
+        Sy[k] = ys * ys;
+        Tx[k] = sinpi_r(real(2 * (pm.x * MX + k - 1) + 1) * h);
+        Ty[k] = sinpi_r(real(2 * (pm.y * MX + k - 1) + 1) * h);
+      }
+    };
+    // Alg. 1 for this patch, its neighbour reads while the tile is in
+    // flight: each thread computes the values of its ghost cells (copied from
+    // same-size or averaged from finer neighbours, interpolated from coarser
+    // ones; every ghost is one of these or exterior) into registers, stored
+    // into the tile once it has landed; then the wall condition (the
+    // exterior ghosts copy cells that are final by then) and, on the sphere,
+    // the corners beyond a cube vertex
+    constexpr int NG = num_ghosts<MX>();
+    auto gather = [&](int nthreads) {
+      const real alpha = real(a.alpha);
+#pragma unroll 1
+      for (int k = threadIdx.x; k < NG; k += nthreads) {
+        int i, j;
+        ghost_ij<MX>(k, i, j);
+        real v;
+        const bool w =
+            copy_or_average<real, MX>(D, st, pm, a.tlevel, alpha, i, j, v) ||
+            (a.direct ? interpolate_direct<real, MX>(D, st, sco, pm, a.tlevel, alpha, i, j, v)
+                      : interpolate<real, MX>(D, st, pm, a.tlevel, i, j, v));
+        ring[k] = w ? v : real(0);
+        ring_w[k] = w;
+      }
+    };
+    auto store_ring = [&](int nthreads) {
+      for (int k = threadIdx.x; k < NG; k += nthreads)  // each thread its own cells
+        if (ring_w[k]) {
+          int i, j;
+          ghost_ij<MX>(k, i, j);
+          Q[(j + kMbc) * S + i + kMbc] = ring[k];
+        }
+    };
+    auto stage_direct = [&]() {  // the coarse neighbours' entries (8 threads per region)
+      const int r = threadIdx.x >> 3;
+      if (r < 8 && st.e[r].kind == NB_COARSE && st.e[r].lev == a.tlevel)
+        stage_neighbours(D.meta, D.nbr, st.e[r].n0, sco[r], threadIdx.x & 7);
+    };
+    bool split_done = false;
+    if constexpr (SPLIT) {
+      if (a.gather) {
+        if (threadIdx.x < 8) stage_neighbours(D.meta, D.nbr, p, st, threadIdx.x);
+        tables(NGT);
+        __syncthreads();  // the patch's entries, the tables
+        bool landed;
+        if (threadIdx.x < NGT) {  // gathering warps
+          if (a.direct) {
+            stage_direct();
+            asm volatile("bar.sync 1, %0;" ::"n"(NGT) : "memory");
+          }
+          gather(NGT);
+          landed = mbar_wait(&bar, parity, a.wait_limit);
+          if (landed) store_ring(NGT);
+        } else {
+          landed = mbar_wait(&bar, parity, a.wait_limit);
+        }
+        // interior edges in warp-sized chunks (the gathering warps join late)
+        const unsigned lane = threadIdx.x & 31;
+        if (__all_sync(0xffffffffu, landed)) {
+          for (;;) {
+            int c = 0;
+            if (lane == 0) c = atomicAdd(&chunk_next, 1);
+            c = __shfl_sync(0xffffffffu, c, 0);
+            if (c >= NCHUNK) break;
+            const int t = c * 32 + (int)lane;
+            if (t < NI) {
+              xedge(2 + t % (MX - 3), t / (MX - 3));
+            } else if (t < 2 * NI) {
+              const int u = t - NI;
+              yedge(u % MX, 2 + u / MX);
+            }
+          }
+        }
+        // every thread observes the copy's completion (bounded); the CTA
+        // leaves together if any thread gave up
+        if (!__syncthreads_and(landed)) {
+          if (threadIdx.x == 0) atomicOr(err, kErrTimeout);
+          mbar_wait(&bar, parity, kWaitLimit);  // let the copy land before leaving
+          return;
+        }
+        if (threadIdx.x == 0) chunk_next = 0;  // (its next use is after later barriers)
+        if (D.domain == FC_DOMAIN_WALLS) {
+          wall_bc<real, MX>(pm, Q, threadIdx.x, NT);
+          __syncthreads();
+        }
+        if (D.domain == FC_DOMAIN_SPHERE) {
+          corner3_fill<real, MX>(st, Q, threadIdx.x, NT);
+          __syncthreads();
+        }
+        split_done = true;
+      }
+    }
+    if (!split_done) {
+      if (a.gather) stage_neighbours(D.meta, D.nbr, p, st, threadIdx.x);
+      tables(0);
+      if (a.gather) {
+        __syncthreads();  // the patch's entries
+        if (a.direct) {
+          stage_direct();
+          __syncthreads();
+        }
+        gather(NT);
+      }
+      // every thread observes the copy's completion (bounded); the CTA leaves
+      // together if any thread gave up
+      const bool landed = mbar_wait(&bar, parity, a.wait_limit);
+      if (!__syncthreads_and(landed)) {
+        if (threadIdx.x == 0) atomicOr(err, kErrTimeout);
+        mbar_wait(&bar, parity, kWaitLimit);  // let the copy land before leaving
+        return;
+      }
+      if (a.gather) {
+        store_ring(NT);
+        __syncthreads();
+        if (D.domain == FC_DOMAIN_WALLS) {
+          wall_bc<real, MX>(pm, Q, threadIdx.x, NT);
+          __syncthreads();
+        }
+        if (D.domain == FC_DOMAIN_SPHERE) {
+          corner3_fill<real, MX>(st, Q, threadIdx.x, NT);
+          __syncthreads();
+        }
+      }
+    }
+    if (a.keep) {  // the adjoint's replay keeps the ghost-filled input tile
+      real* kp = static_cast<real*>(a.keep) + (size_t)(p - a.keep_p0) * S * S;
+      for (int k = threadIdx.x; k < S * S; k += NT) kp[k] = Q[k];
+    }
+    if (split_done) {
+      // the edges that read ghost cells: full rows j = -1, MX and the columns
+      // i = 0, 1, MX-1, MX of the interior rows (x); the same for y
+      for (int b = threadIdx.x; b < 2 * NB; b += NT) {
+        const bool y = b >= NB;
+        const int c = y ? b - NB : b;
+        int u, v;  // (along, across) the edge's direction of travel
+        if (c < 2 * (MX + 1)) {
+          u = c % (MX + 1);
+          v = c < MX + 1 ? -1 : MX;
+        } else {
+          const int d = c - 2 * (MX + 1);
+          v = d >> 2;
+          u = (d & 3) < 2 ? (d & 3) : MX - 3 + (d & 3);  // 0, 1, MX-1, MX
+        }
+        if (y) yedge(v, u);  // column i = v, edge j = u
+        else xedge(u, v);    // edge i = u, row j = v
+      }
+    } else {
+      // both sweeps: normal flux and fluctuations of every edge
+      for (int e = threadIdx.x; e < 2 * NE; e += NT) {
+        if (e < NE) {
+          xedge(e % (MX + 1), e / (MX + 1) - 1);
+        } else {
+          const int f = e - NE;
+          yedge(f % (MX + 2) - 1, f / (MX + 2));
+        }
       }
     }
     __syncthreads();
