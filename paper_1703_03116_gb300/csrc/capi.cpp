@@ -752,7 +752,8 @@ fc_status advance_level_t(fc_forest* F, int L, double t, double dt, cudaStream_t
       // coarse neighbours first (their interiors time-interpolated into qT,
       // their coarse ghost regions filled); the update kernel then fills
       // each level-L patch's ghost ring in shared memory itself
-      FillArgs A{F->d_lists + F->off_t[L], (int)H.list_t[L].size(), tlevel, alpha};
+      FillArgs A{F->d_lists + F->off_t[L], (int)H.list_t[L].size(), tlevel, alpha,
+                 F->keep_qT ? 1 : 0};
       // the staged update computes the time-interpolated coarse cells it
       // reads itself, so no fill launch sits before it on the level's chain
       // (at alpha = 0 from the coarser level's older state, which its
@@ -775,7 +776,8 @@ fc_status advance_level_t(fc_forest* F, int L, double t, double dt, cudaStream_t
       a.tlevel = tlevel;
       a.alpha = alpha;
     } else {
-      FillArgs A{F->d_lists + F->off_a[L], (int)H.list_a[L].size(), tlevel, alpha};
+      FillArgs A{F->d_lists + F->off_a[L], (int)H.list_a[L].size(), tlevel, alpha,
+                 F->keep_qT ? 1 : 0};
       {
         Timed tm(F, 1, s, gb * A.ntargets);
         FC_CUDA(launch_fill_coarse(D, A, s));
@@ -1582,7 +1584,7 @@ static fc_status adjoint_advance_t(fc_forest* F, int L, double t, double dt, voi
   DevForest<real> D = dev<real>(F);
   const int p0 = H.lev_start[L], p1 = H.lev_start[L + 1];
   // the substep's forward fill, as fc_advance_level does it with separate fills
-  FillArgs A{F->d_lists + F->off_a[L], (int)H.list_a[L].size(), tlevel, alpha};
+  FillArgs A{F->d_lists + F->off_a[L], (int)H.list_a[L].size(), tlevel, alpha, 1};
   FillArgs B{F->d_lists + F->off_b[L], (int)H.list_b[L].size(), tlevel, alpha};
   if (p1 > p0) {
     FC_CUDA(launch_fill_coarse(D, A, s));

@@ -405,6 +405,11 @@ struct FillArgs {
   int ntargets;
   int tlevel;    // level read/written through the time-interpolated buffer, -1 none
   double alpha;  // time-interpolation weight of the newer state
+  // targets on tlevel: 0 time-interpolates only the interior cells within
+  // two of the patch's edge (all that a finer neighbour's interpolation
+  // stencil reads: the coarse cell beside the shared edge and its
+  // neighbours), 1 the whole interior (the adjoint reads the whole tile)
+  int full_interior;
 };
 
 // Per-launch scalars of the patch update for one level: cell width h,

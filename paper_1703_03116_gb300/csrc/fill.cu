@@ -29,9 +29,28 @@ __global__ void __launch_bounds__(256) fill_coarse_kernel(DevForest<real> D, Fil
     __syncthreads();
     real* Q = patch_ptr((pm.level == A.tlevel) ? D.qT : D.buf[D.cur[pm.level]], p, S);
     if (pm.level == A.tlevel) {
-      for (int k = threadIdx.x; k < MX * MX; k += blockDim.x) {
-        const int i = k % MX, j = k / MX;
-        Q[(j + kMbc) * S + i + kMbc] = src_interior(D, A.tlevel, alpha, p, pm.level, i, j);
+      if (A.full_interior) {
+        for (int k = threadIdx.x; k < MX * MX; k += blockDim.x) {
+          const int i = k % MX, j = k / MX;
+          Q[(j + kMbc) * S + i + kMbc] = src_interior(D, A.tlevel, alpha, p, pm.level, i, j);
+        }
+      } else {
+        // the cells within two of the patch's edge: rows 0, 1, MX-2, MX-1,
+        // then columns 0, 1, MX-2, MX-1 of the rows between
+        constexpr int NR = 4 * MX + 4 * (MX - 4);
+        for (int k = threadIdx.x; k < NR; k += blockDim.x) {
+          int i, j;
+          if (k < 4 * MX) {
+            const int r = k / MX;
+            j = r < 2 ? r : MX - 4 + r;
+            i = k % MX;
+          } else {
+            const int c = (k - 4 * MX) & 3;
+            j = 2 + ((k - 4 * MX) >> 2);
+            i = c < 2 ? c : MX - 4 + c;
+          }
+          Q[(j + kMbc) * S + i + kMbc] = src_interior(D, A.tlevel, alpha, p, pm.level, i, j);
+        }
       }
     }
     for (int k = threadIdx.x; k < num_ghosts<MX>(); k += blockDim.x) {
