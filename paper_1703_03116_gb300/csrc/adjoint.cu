@@ -587,9 +587,13 @@ __global__ void adj_coarse_tiles_kernel(DevForest<real> D, const int* targets, i
                              alpha, threadIdx.x, blockDim.x);
     __syncthreads();
     const size_t base = (size_t)p * S * S;
+    // (the interpolation stencils of the finer level read only the cells
+    // within two of the tile's edge, so most of the tile's adjoint is zero:
+    // those cells add nothing and need no clearing)
     for (int k = threadIdx.x; k < S * S; k += blockDim.x) {
       const int i = k % S - 2, j = k / S - 2;
       const real v = T[k];
+      if (v == real(0)) continue;
       T[k] = real(0);
       if (i >= 0 && i < MX && j >= 0 && j < MX) {  // other CTAs may add here too
         atomicAdd(lam_old + base + k, (real(1) - alpha) * v);

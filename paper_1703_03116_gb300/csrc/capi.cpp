@@ -752,8 +752,7 @@ fc_status advance_level_t(fc_forest* F, int L, double t, double dt, cudaStream_t
       // coarse neighbours first (their interiors time-interpolated into qT,
       // their coarse ghost regions filled); the update kernel then fills
       // each level-L patch's ghost ring in shared memory itself
-      FillArgs A{F->d_lists + F->off_t[L], (int)H.list_t[L].size(), tlevel, alpha,
-                 F->keep_qT ? 1 : 0};
+      FillArgs A{F->d_lists + F->off_t[L], (int)H.list_t[L].size(), tlevel, alpha};
       // the staged update computes the time-interpolated coarse cells it
       // reads itself, so no fill launch sits before it on the level's chain
       // (at alpha = 0 from the coarser level's older state, which its
@@ -776,8 +775,7 @@ fc_status advance_level_t(fc_forest* F, int L, double t, double dt, cudaStream_t
       a.tlevel = tlevel;
       a.alpha = alpha;
     } else {
-      FillArgs A{F->d_lists + F->off_a[L], (int)H.list_a[L].size(), tlevel, alpha,
-                 F->keep_qT ? 1 : 0};
+      FillArgs A{F->d_lists + F->off_a[L], (int)H.list_a[L].size(), tlevel, alpha};
       {
         Timed tm(F, 1, s, gb * A.ntargets);
         FC_CUDA(launch_fill_coarse(D, A, s));

@@ -407,8 +407,8 @@ struct FillArgs {
   double alpha;  // time-interpolation weight of the newer state
   // targets on tlevel: 0 time-interpolates only the interior cells within
   // two of the patch's edge (all that a finer neighbour's interpolation
-  // stencil reads: the coarse cell beside the shared edge and its
-  // neighbours), 1 the whole interior (the adjoint reads the whole tile)
+  // stencil, or its transpose, reads: the coarse cell beside the shared
+  // edge and its neighbours), 1 the whole interior
   int full_interior;
 };
 
