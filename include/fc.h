@@ -153,7 +153,8 @@ typedef void (*fc_free_fn)(void* ptr, size_t bytes, void* stream, void* user);
 fc_status fc_set_allocator(fc_alloc_fn alloc, fc_free_fn release, void* user);
 
 /* What a forest holds (Sec. 2: the leaves and their levels).
- *   leaves_per_level[l]  leaves of level l (0 <= l < FC_INFO_LEVELS)
+ *   nleaves              leaves of the field layout (a partition: its own)
+ *   leaves_per_level[l]  of them, those of level l (0 <= l < FC_INFO_LEVELS)
  *   device_bytes         device memory the forest holds now (store, tables,
  *                        metrics, adjoint buffers once created)
  *   graphs               captured coarse steps (forward and adjoint) held

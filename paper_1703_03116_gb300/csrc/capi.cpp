@@ -963,8 +963,8 @@ fc_status fc_forest_info(const fc_forest* F, fc_info* out) {
   out->lmax = H.desc.lmax;
   out->dtype = H.desc.dtype;
   out->domain = H.desc.domain;
-  for (int l = 0; l <= kMaxLevel && l < FC_INFO_LEVELS; ++l)
-    out->leaves_per_level[l] = H.lev_start[l + 1] - H.lev_start[l];
+  for (int l = 0; l <= kMaxLevel && l < FC_INFO_LEVELS; ++l)  // (a partition: its own leaves)
+    out->leaves_per_level[l] = H.upd_end(l) - H.lev_start[l];
   const size_t S = (size_t)H.desc.mx + 2 * kMbc;
   const size_t n = (size_t)std::max(H.npatch(), 1);
   const size_t store = n * S * S * F->esize;
