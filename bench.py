@@ -197,7 +197,7 @@ class Runner:
         self.F = fc.initial_forest(desc, q0_fn(workloads), lmax_f=self.lmax_f,
                                    tau_r=w.tau_refine, tau_c=w.tau_coarsen)
         # pick the patch-update kernel per launch size on this layout (untimed setup)
-        self.tuning = {int(b): {"variant": ["staged", "walk", "walk1"][v], "warps": k,
+        self.tuning = {int(b): {"variant": ["staged", "walk", "walk1", "band"][v], "warps": k,
                                 "fill": "fused" if fu else "separate", "ns": ns}
                        for b, (v, k, fu, ns) in self.F.autotune().items()}
         self.n = 0
@@ -407,7 +407,7 @@ def granularity_sweep(fc, torch, hbm):
             v, warps, fused, ns = rep[b]
             cells = n * mx * mx
             nbytes = n * ((mx + 4) ** 2 + mx * mx) * 4
-            rows.append({"mx": mx, "patches": n, "variant": ["staged", "walk", "walk1"][v],
+            rows.append({"mx": mx, "patches": n, "variant": ["staged", "walk", "walk1", "band"][v],
                          "warps": warps, "us_per_substep": ns * 1e-3,
                          "cell_updates_per_s": cells / (ns * 1e-9),
                          "hbm_frac": nbytes / (ns * 1e-9) / 1e9 / hbm})

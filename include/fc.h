@@ -215,7 +215,7 @@ fc_status fc_step_global(fc_forest* forest, double t, double dt, void* stream);
  * the fluxes of the cube edges: each side computes an edge's flux from its
  * own ghost cells, the side on the block of lower index keeps its own, and
  * a cell on the other side takes it in place of its own (the pairing of
- * fc_layout_reflux).  Every update runs the staged variant then;
+ * fc_layout_reflux).  Every update runs the staged or band variant then;
  * fc_advance_level records the fluxes but corrects nothing. */
 fc_status fc_step_multirate(fc_forest* forest, double t, double dt_coarse, void* stream);
 
@@ -428,12 +428,21 @@ fc_status fc_set_graphs(fc_forest* forest, int enable);
 
 /* Patch-update kernel variants: 0 "staged" (one CTA per patch, the whole
  * tile in shared memory, every thread on every phase -- low latency for
- * launches of few patches) and 1 "walk" (lanes own patch columns and walk
+ * launches of few patches), 1 "walk" (lanes own patch columns and walk
  * the rows with warp shuffles, tiles double-buffered per warp by TMA, a
- * persistent grid of `warps`-warp CTAs -- fewest instructions per cell) and
- * 2 (walk1: the walk with one tile buffer per warp, twice the warps per SM).
+ * persistent grid of `warps`-warp CTAs -- fewest instructions per cell),
+ * 2 (walk1: the walk with one tile buffer per warp, twice the warps per SM)
+ * and 3 "band" (one CTA of `warps` warps per patch, each warp walking a band
+ * of rows as the walk does: mx^2 / (32 warps) rows a band, at least one;
+ * planar grids, with refluxing).  Where a variant lacks what the forest
+ * needs (walk: refluxing; walk and band: the cubed sphere's capacity form)
+ * the launch runs staged.
  *
- * fc_autotune times every candidate (staged; walk with 2, 4, 8 warps per
+ * Untuned launch sizes run walk from 1024 patches up, below that band with
+ * 8 warps (staged on the cubed sphere).
+ *
+ * fc_autotune times every candidate (staged; band with 4 or 8 warps;
+ * walk with 2, 4, 8 warps per
  * CTA; walk1 with 4 or 8; each with the level's ghosts filled inside the update kernel or by
  * separate fill kernels) as a whole level substep of the current layout,
  * eight substeps replayed from one CUDA graph as in a captured step (walk
@@ -446,7 +455,8 @@ fc_status fc_set_graphs(fc_forest* forest, int enable);
  * Synchronous.
  *
  * fc_set_advance_variant forces a variant for every launch (variant -1
- * restores the tuned/heuristic choice); warps is 2, 4 or 8. */
+ * restores the tuned/heuristic choice); warps is 2, 4 or 8, or 16 for band
+ * (FC_ERR_INVALID_ARG otherwise). */
 fc_status fc_autotune(fc_forest* forest, int* report, void* stream);
 
 /* Fused ghost fill in multirate substeps (on by default): the patch-update

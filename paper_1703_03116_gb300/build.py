@@ -18,7 +18,7 @@ INCLUDE = os.path.join(ROOT, "include")
 OBJDIR = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libfc.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["advance.cu", "advance_walk.cu", "fill.cu", "aux_kernels.cu", "noalloc.cu", "adjoint.cu", "sphere.cu",
+SOURCES = ["advance.cu", "advance_walk.cu", "advance_band.cu", "fill.cu", "aux_kernels.cu", "noalloc.cu", "adjoint.cu", "sphere.cu",
            "forest.cpp", "capi.cpp"]
 
 

@@ -54,7 +54,6 @@ __global__ void __launch_bounds__(NT, NT >= 512 ? (sizeof(real) == 4 ? 3 : 2)
   __shared__ __align__(8) uint64_t bar;
   __shared__ real ucoef_s;
   __shared__ NbrStage st;
-  __shared__ NbrStage sco[8];  // a.direct: each coarse region's neighbour's entries
   __shared__ real ring[num_ghosts<MX>()];  // ghost values gathered while the tile loads
   __shared__ bool ring_w[num_ghosts<MX>()];
   // Warp roles when the CTA has warps to spare beyond the ghost ring (mx =
@@ -94,13 +93,11 @@ __global__ void __launch_bounds__(NT, NT >= 512 ? (sizeof(real) == 4 ? 3 : 2)
   if (threadIdx.x == 0) {
     mbar_init(&bar, 1);
     chunk_next = 0;
-    if (swirl) {
-      const double t = a.t0_dev ? *a.t0_dev + a.t_off : a.t_half;
-      ucoef_s = cospi_ratio<real>(t, a.period) * real(a.sfac);
-    }
   }
   __syncthreads();
-  const real ucoef = swirl ? ucoef_s : real(0);
+  // the swirl coefficient: computed by the last thread (no ghost to gather)
+  // while the first patch's tile is in flight, read after the next barrier
+  real ucoef = real(0);
   uint32_t parity = 0;
   for (int p = p0 + blockIdx.x; p < p1; p += gridDim.x, parity ^= 1) {
     const PatchMeta pm = D.meta[p];
@@ -111,6 +108,10 @@ __global__ void __launch_bounds__(NT, NT >= 512 ? (sizeof(real) == 4 ? 3 : 2)
       mbar_expect_tx(&bar, bytes + mbytes);
       bulk_load(Q, src, bytes, &bar);
       if (CAP) bulk_load(smem_raw, D.metric + (size_t)p * MS, mbytes, &bar);
+    }
+    if (swirl && threadIdx.x == NT - 1 && p == p0 + (int)blockIdx.x) {
+      const double t = a.t0_dev ? *a.t0_dev + a.t_off : a.t_half;
+      ucoef_s = cospi_ratio<real>(t, a.period) * real(a.sfac);
     }
     auto q = [&](int i, int j) -> real { return Q[(j + 2) * S + (i + 2)]; };
     // capacity form: kappa of cell (i,j), flux through x-edge / y-edge (i,j)
@@ -178,50 +179,22 @@ __global__ void __launch_bounds__(NT, NT >= 512 ? (sizeof(real) == 4 ? 3 : 2)
     // into the tile once it has landed; then the wall condition (the
     // exterior ghosts copy cells that are final by then) and, on the sphere,
     // the corners beyond a cube vertex
-    constexpr int NG = num_ghosts<MX>();
     auto gather = [&](int nthreads) {
-      const real alpha = real(a.alpha);
-#pragma unroll 1
-      for (int k = threadIdx.x; k < NG; k += nthreads) {
-        int i, j;
-        ghost_ij<MX>(k, i, j);
-        real v;
-        const bool w =
-            copy_or_average<real, MX>(D, st, pm, a.tlevel, alpha, i, j, v) ||
-            (a.direct ? interpolate_direct<real, MX>(D, st, sco, pm, a.tlevel, alpha, i, j, v)
-                      : interpolate<real, MX>(D, st, pm, a.tlevel, i, j, v));
-        ring[k] = w ? v : real(0);
-        ring_w[k] = w;
-      }
-    };
-    auto store_ring = [&](int nthreads) {
-      for (int k = threadIdx.x; k < NG; k += nthreads)  // each thread its own cells
-        if (ring_w[k]) {
-          int i, j;
-          ghost_ij<MX>(k, i, j);
-          Q[(j + kMbc) * S + i + kMbc] = ring[k];
-        }
-    };
-    auto stage_direct = [&]() {  // the coarse neighbours' entries (8 threads per region)
-      const int r = threadIdx.x >> 3;
-      if (r < 8 && st.e[r].kind == NB_COARSE && st.e[r].lev == a.tlevel)
-        stage_neighbours(D.meta, D.nbr, st.e[r].n0, sco[r], threadIdx.x & 7);
+      gather_ring<real, MX>(D, st, pm, a.tlevel, real(a.alpha), a.direct != 0, ring, ring_w,
+                            threadIdx.x, nthreads);
     };
     bool split_done = false;
     if constexpr (SPLIT) {
       if (a.gather) {
         if (threadIdx.x < 8) stage_neighbours(D.meta, D.nbr, p, st, threadIdx.x);
         tables(NGT);
-        __syncthreads();  // the patch's entries, the tables
+        __syncthreads();  // the patch's entries, the tables, the swirl coefficient
+        ucoef = swirl ? ucoef_s : real(0);
         bool landed;
         if (threadIdx.x < NGT) {  // gathering warps
-          if (a.direct) {
-            stage_direct();
-            asm volatile("bar.sync 1, %0;" ::"n"(NGT) : "memory");
-          }
           gather(NGT);
           landed = mbar_wait(&bar, parity, a.wait_limit);
-          if (landed) store_ring(NGT);
+          if (landed) store_ring<real, MX>(Q, ring, ring_w, threadIdx.x, NGT);
         } else {
           landed = mbar_wait(&bar, parity, a.wait_limit);
         }
@@ -266,10 +239,6 @@ __global__ void __launch_bounds__(NT, NT >= 512 ? (sizeof(real) == 4 ? 3 : 2)
       tables(0);
       if (a.gather) {
         __syncthreads();  // the patch's entries
-        if (a.direct) {
-          stage_direct();
-          __syncthreads();
-        }
         gather(NT);
       }
       // every thread observes the copy's completion (bounded); the CTA leaves
@@ -280,8 +249,9 @@ __global__ void __launch_bounds__(NT, NT >= 512 ? (sizeof(real) == 4 ? 3 : 2)
         mbar_wait(&bar, parity, kWaitLimit);  // let the copy land before leaving
         return;
       }
+      ucoef = swirl ? ucoef_s : real(0);
       if (a.gather) {
-        store_ring(NT);
+        store_ring<real, MX>(Q, ring, ring_w, threadIdx.x, NT);
         __syncthreads();
         if (D.domain == FC_DOMAIN_WALLS) {
           wall_bc<real, MX>(pm, Q, threadIdx.x, NT);
@@ -427,9 +397,12 @@ cudaError_t launch_advance(const DevForest<real>& D, int p0, int p1, const AdvAr
                            cudaStream_t s) {
   if (p1 <= p0) return cudaSuccess;
   // the walk variant has no capacity form and records no face fluxes:
-  // mapped grids and refluxing always run staged
+  // mapped grids run staged, refluxing staged or band
   if ((a.variant == ADV_WALK || a.variant == ADV_WALK1) && !D.metric && !a.bflux)
     return launch_advance_walk(D, p0, p1, a, err, s);
+  // the band variant records face fluxes but has no capacity form either
+  if (a.variant == ADV_BAND && !D.metric && D.domain != FC_DOMAIN_SPHERE)
+    return launch_advance_band(D, p0, p1, a, err, s);
   return launch_advance_staged(D, p0, p1, a, err, s);
 }
 

@@ -21,34 +21,10 @@
 #include <cstdint>
 
 #include "ghost_gather.cuh"
+#include "walk_edge.cuh"
 
 namespace fc {
 namespace {
-
-template <typename real>
-struct Scheme {
-  real nu;    // dt / h
-  real tfac;  // 1/2 dt/h with transverse propagation, else 0
-  real t2;    // 1 when correction waves are propagated transversely, else 0
-  bool order2, mc;
-};
-
-// one edge between cells qb (upwind-left/below) and qc, with the outer
-// neighbours qa (behind qb) and qd (beyond qc): normal flux and the two
-// fluctuations entering the right/upper (P) and left/lower (M) cell
-template <typename real>
-__device__ __forceinline__ void edge(real s, real qa, real qb, real qc, real qd,
-                                     const Scheme<real>& sc, real& Fn, real& P, real& M) {
-  const real sp = fmax(s, real(0)), sm = fmin(s, real(0));
-  const real W = qc - qb;
-  const real Wup = s >= real(0) ? qb - qa : qd - qc;
-  const real as = fabs(s);
-  const real cf = sc.order2 ? real(0.5) * as * (real(1) - sc.nu * as) : real(0);
-  const real Ft = cf * (sc.mc ? mc_limited(W, Wup) : W);
-  Fn = sp * qb + sm * qc + Ft;
-  P = sp * W - sc.t2 * Ft;
-  M = sm * W + sc.t2 * Ft;
-}
 
 template <int MX>
 constexpr int tile_stride() {
@@ -110,12 +86,7 @@ __global__ void __launch_bounds__(NW * 32) advance_walk_kernel(DevForest<real> D
   const real ucoef = SWIRL ? ucoef_s : real(0);
   const real cu = real(D.vel[0]), cv = real(D.vel[1]);
   const real h = real(a.h);
-  Scheme<real> sc;
-  sc.nu = real(a.nu);
-  sc.tfac = D.transverse > 0 ? real(0.5 * a.nu) : real(0);
-  sc.t2 = D.transverse > 1 ? real(1) : real(0);
-  sc.order2 = D.order > 1;
-  sc.mc = D.limiter != 0;
+  const Scheme<real> sc = make_scheme<real>(D.order, D.limiter, D.transverse, a.nu);
 
   const int ngroups = (p1 - p0 + PPW - 1) / PPW;
   const int TW = gridDim.x * NW;

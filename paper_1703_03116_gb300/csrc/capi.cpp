@@ -614,25 +614,30 @@ int size_bucket(int n) {
 
 // the patch-update configuration for a launch of n patches: the autotuned
 // choice when this size was tuned, else walk for launches that fill the GPU
+// and band (staged on the cubed sphere) for the others
 void choose_variant(const fc_forest* F, int n, AdvArgs* a) {
-  if (F->bflux) {  // only the staged update records the face fluxes
-    a->variant = ADV_STAGED;
-    a->warps = 4;
-    return;
-  }
+  const fc_forest::Tune& t = F->tune[size_bucket(n)];
   if (F->forced_variant >= 0) {
     a->variant = F->forced_variant;
     a->warps = F->forced_warps;
-    return;
-  }
-  const fc_forest::Tune& t = F->tune[size_bucket(n)];
-  if (t.tuned) {
+  } else if (t.tuned) {
     a->variant = t.variant;
     a->warps = t.warps;
-    return;
+  } else if (n >= 1024) {
+    a->variant = ADV_WALK;
+    a->warps = F->esize == 4 ? 4 : 2;
+  } else if (F->d_metric || F->host.desc.domain == FC_DOMAIN_SPHERE) {
+    a->variant = ADV_STAGED;
+    a->warps = 4;
+  } else {
+    a->variant = ADV_BAND;
+    a->warps = 8;
   }
-  a->variant = n >= 1024 ? ADV_WALK : ADV_STAGED;
-  a->warps = F->esize == 4 ? 4 : 2;
+  // only the staged and band updates record the face fluxes
+  if (F->bflux && a->variant != ADV_STAGED && a->variant != ADV_BAND) {
+    a->variant = ADV_STAGED;
+    a->warps = 4;
+  }
 }
 
 // device error word -> status (and clear it)
@@ -760,7 +765,7 @@ fc_status advance_level_t(fc_forest* F, int L, double t, double dt, cudaStream_t
       // filled tiles: it runs the fill).  The walk keeps the fill: with one
       // warp per patch, computing those cells in the update measured slower
       // on the ensemble (5.5e10 vs 7.4e10 cell-updates/s)
-      const bool direct = tlevel >= 0 && a.variant == ADV_STAGED &&
+      const bool direct = tlevel >= 0 && (a.variant == ADV_STAGED || a.variant == ADV_BAND) &&
                           H.desc.domain != FC_DOMAIN_SPHERE && !F->keep_qT && !F->keep_tiles;
       if (direct) A.ntargets = 0;
       a.direct = direct ? 1 : 0;
@@ -1112,8 +1117,10 @@ fc_status fc_forest_get_capacity(const fc_forest* F, double* out, int on_device,
 }
 
 fc_status fc_set_advance_variant(fc_forest* F, int variant, int warps) {
-  if (!F || variant < -1 || variant > ADV_WALK1 || (warps != 2 && warps != 4 && warps != 8))
-    return fail(FC_ERR_INVALID_ARG, "variant must be -1, 0, 1 or 2 and warps 2, 4 or 8");
+  const bool warps_ok = warps == 2 || warps == 4 || warps == 8 || (warps == 16 && variant == ADV_BAND);
+  if (!F || variant < -1 || variant > ADV_BAND || !warps_ok)
+    return fail(FC_ERR_INVALID_ARG,
+                "variant must be -1, 0, 1, 2 or 3 and warps 2, 4 or 8 (16 with variant 3)");
   F->forced_variant = variant;
   F->forced_warps = warps;
   destroy_graphs(F);
@@ -1135,8 +1142,11 @@ fc_status fc_autotune(fc_forest* F, int* report, void* stream) {
   const HostForest& H = F->host;
   const struct {
     int variant, warps;
-  } cand[] = {{ADV_STAGED, 4}, {ADV_WALK, 2}, {ADV_WALK, 4}, {ADV_WALK, 8}, {ADV_WALK1, 4},
-              {ADV_WALK1, 8}};
+  // (band with 16 warps is left out: timed a level at a time it can win,
+  // but beside the other levels' branches of a captured step it measured
+  // slower than with 8)
+  } cand[] = {{ADV_STAGED, 4}, {ADV_BAND, 4}, {ADV_BAND, 8},  {ADV_WALK, 2},
+              {ADV_WALK, 4},   {ADV_WALK, 8}, {ADV_WALK1, 4}, {ADV_WALK1, 8}};
   constexpr int ncand = sizeof(cand) / sizeof(cand[0]);
   cudaEvent_t e0, e1;
   FC_CUDA(cudaEventCreate(&e0));
@@ -1161,10 +1171,15 @@ fc_status fc_autotune(fc_forest* F, int* report, void* stream) {
       const auto& c = cand[c2 % ncand];
       const int fused = c2 / ncand;
       if (fused && !F->fuse) continue;
-      if (c.variant != ADV_STAGED && F->d_metric) continue;  // no capacity form in walk
+      // no capacity form in walk or band
+      if (c.variant != ADV_STAGED && (F->d_metric || H.desc.domain == FC_DOMAIN_SPHERE)) continue;
+      const bool walk = c.variant == ADV_WALK || c.variant == ADV_WALK1;
+      if (walk && F->bflux) continue;  // (it would run staged)
       // below two patches per SM the walk's warps mostly idle: staged has
       // measured about twice as fast there (graph-replayed substeps)
-      if (c.variant != ADV_STAGED && p1 - p0 < 2 * nsm) continue;
+      if (walk && p1 - p0 < 2 * nsm) continue;
+      // a band of one row recomputes three rows of x-edges
+      if (c.variant == ADV_BAND && H.desc.mx * H.desc.mx < 64 * c.warps) continue;
       a.variant = c.variant;
       a.warps = c.warps;
       a.gather = fused;

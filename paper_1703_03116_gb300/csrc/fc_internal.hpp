@@ -421,8 +421,8 @@ struct AdvArgs {
   double h, nu, sfac, period, t_half, t_off;
   double dt;  // time step (capacity form: dt / kappa per cell)
   const double* t0_dev;
-  int variant;  // ADV_STAGED or ADV_WALK
-  int warps;    // walk variant: warps per CTA
+  int variant;  // AdvVariant
+  int warps;    // walk and band variants: warps per CTA
   int ctas;     // walk variant: cap on the CTAs in the grid (0: the SMs' residency)
   // polls of a kernel's bounded wait for its tile copy before it gives up
   // (FC_ERR_TIMEOUT); the copies in flight are then still awaited with the
@@ -453,11 +453,16 @@ struct AdvArgs {
 // walk   -- lanes own patch columns and walk the rows, one warp per patch
 //           (fewest instructions per cell; the throughput choice), tiles
 //           double-buffered per warp;
-// walk1  -- the walk with one tile buffer per warp (twice the warps per SM).
-enum AdvVariant : int { ADV_STAGED = 0, ADV_WALK = 1, ADV_WALK1 = 2 };
+// walk1  -- the walk with one tile buffer per warp (twice the warps per SM);
+// band   -- one CTA per patch whose warps each walk a band of rows as the
+//           walk does (low latency at few instructions per cell).
+enum AdvVariant : int { ADV_STAGED = 0, ADV_WALK = 1, ADV_WALK1 = 2, ADV_BAND = 3 };
 
 template <typename real>
 cudaError_t launch_advance_walk(const DevForest<real>& D, int p0, int p1, const AdvArgs& a,
+                                int* err, cudaStream_t s);
+template <typename real>
+cudaError_t launch_advance_band(const DevForest<real>& D, int p0, int p1, const AdvArgs& a,
                                 int* err, cudaStream_t s);
 
 cudaError_t launch_set_time(double* t0_dev, double t0, cudaStream_t s);

@@ -51,40 +51,37 @@ __device__ __forceinline__ real src_interior(const DevForest<real>& D, int tleve
   return D.buf[c][o];
 }
 
-// Ghost (i, j) of the owner (layout pm) from a same-size or finer neighbour.
-// Returns false when the region is not of that kind (or the entry is malformed).
+// Ghost (i, j) of the owner (layout pm) from a same-size or finer neighbour,
+// e being the entry of the ghost's face/corner region (the neighbours' level
+// and positions travel in it).  Returns false when the region is not of
+// that kind (or the entry is malformed).
 template <typename real, int MX>
-__device__ __forceinline__ bool copy_or_average(const DevForest<real>& D, const NbrStage& st,
-                                                const PatchMeta& pm, int tlevel, real alpha,
-                                                int i, int j, real& v) {
-  const int r = region_of<MX>(i, j);
-  const NbrEntry& e = st.e[r];
+__device__ __forceinline__ bool copy_or_average_entry(const DevForest<real>& D, const NbrEntry& e,
+                                                      const PatchMeta& pm, int tlevel, real alpha,
+                                                      int i, int j, real& v) {
   if (e.kind != NB_SAME && e.kind != NB_FINE) return false;
   const int2 Ip = apply_a(e.a, pm.x * MX + i, pm.y * MX + j);
   const int gx = Ip.x + e.fx, gy = Ip.y + e.fy;
   if (e.kind == NB_SAME) {
-    const PatchMeta& nm = st.m0[r];
-    const int lx = gx - nm.x * MX, ly = gy - nm.y * MX;
+    const int lx = gx - e.x0 * MX, ly = gy - e.y0 * MX;
     if (lx < 0 || lx >= MX || ly < 0 || ly >= MX) return false;
-    v = src_interior(D, tlevel, alpha, e.n0, nm.level, lx, ly);
+    v = src_interior(D, tlevel, alpha, e.n0, e.lev, lx, ly);
     return true;
   }
   int n = e.n0;
-  const PatchMeta* nm = &st.m0[r];
-  int lx = 2 * gx - nm->x * MX, ly = 2 * gy - nm->y * MX;
+  int lx = 2 * gx - e.x0 * MX, ly = 2 * gy - e.y0 * MX;
   if (lx < 0 || lx >= MX || ly < 0 || ly >= MX) {
     if (e.n1 < 0) return false;
     n = e.n1;
-    nm = &st.m1[r];
-    lx = 2 * gx - nm->x * MX;
-    ly = 2 * gy - nm->y * MX;
+    lx = 2 * gx - e.x1 * MX;
+    ly = 2 * gy - e.y1 * MX;
     if (lx < 0 || lx >= MX || ly < 0 || ly >= MX) return false;
   }
   // the four fine cells, in the neighbour's frame: (0,0), (1,0), (0,1), (1,1)
   real s[4];
 #pragma unroll
   for (int q = 0; q < 4; ++q)
-    s[q] = src_interior(D, tlevel, alpha, n, nm->level, lx + (q & 1), ly + (q >> 1));
+    s[q] = src_interior(D, tlevel, alpha, n, e.lev, lx + (q & 1), ly + (q >> 1));
   if (D.metric) {  // mapped grid: weighted by the fine cells' areas
     const double* K = D.metric + (size_t)n * metric_stride(D.S) + (ly + kMbc) * D.S + lx + kMbc;
     const double k0 = K[0], k1 = K[1], k2 = K[D.S], k3 = K[D.S + 1];
@@ -94,6 +91,15 @@ __device__ __forceinline__ bool copy_or_average(const DevForest<real>& D, const 
   }
   v = real(0.25) * (((s[0] + s[1]) + s[2]) + s[3]);
   return true;
+}
+
+// the same from the owner's staged entries
+template <typename real, int MX>
+__device__ __forceinline__ bool copy_or_average(const DevForest<real>& D, const NbrStage& st,
+                                                const PatchMeta& pm, int tlevel, real alpha,
+                                                int i, int j, real& v) {
+  return copy_or_average_entry<real, MX>(D, st.e[region_of<MX>(i, j)], pm, tlevel, alpha, i, j,
+                                         v);
 }
 
 // Ghost (i, j) of the owner from its coarser neighbour; the coarse patch is
@@ -124,17 +130,18 @@ __device__ __forceinline__ bool interpolate(const DevForest<real>& D, const NbrS
 
 // The value the coarse-neighbour fill of a multirate substep (phases 1-2 at
 // tlevel and alpha, then the wall condition) leaves in cell (i, j) of the
-// time-interpolated tile of patch c (on tlevel; sc: its staged entries, cm:
-// its level and position): the interior (1 - alpha) q_old + alpha q_new,
+// time-interpolated tile of patch c (on tlevel; cm: its level and
+// position): the interior (1 - alpha) q_old + alpha q_new,
 // ghosts copied from same-size or averaged from finer neighbours, exterior
 // ghosts from the cell the wall condition clamps them to; any other ghost
 // keeps what the tile holds (that fill leaves it alone).  An update that
 // computes the few coarse cells its interpolation reads this way needs no
-// fill launch before it.  Not for the cubed sphere (its corner rule).
+// fill launch before it.  Not for the cubed sphere (its corner rule).  A
+// ghost of c reads c's entry for its region from the table itself: only the
+// stencils that leave c's interior wait for that read.
 template <typename real, int MX>
-__device__ __forceinline__ real coarse_cell(const DevForest<real>& D, const NbrStage& sc,
-                                            const PatchMeta& cm, int c, int tlevel, real alpha,
-                                            int i, int j) {
+__device__ __forceinline__ real coarse_cell(const DevForest<real>& D, const PatchMeta& cm, int c,
+                                            int tlevel, real alpha, int i, int j) {
   constexpr int S = MX + 4;
   if (D.domain == FC_DOMAIN_WALLS) {
     const int N = MX << cm.level;
@@ -146,17 +153,16 @@ __device__ __forceinline__ real coarse_cell(const DevForest<real>& D, const NbrS
   if (i >= 0 && i < MX && j >= 0 && j < MX)
     return src_interior(D, tlevel, alpha, c, cm.level, i, j);
   real v;
-  if (copy_or_average<real, MX>(D, sc, cm, tlevel, alpha, i, j, v)) return v;
+  const NbrEntry e = D.nbr[(size_t)c * 8 + region_of<MX>(i, j)];
+  if (copy_or_average_entry<real, MX>(D, e, cm, tlevel, alpha, i, j, v)) return v;
   return D.qT[(size_t)c * S * S + (j + kMbc) * S + i + kMbc];
 }
 
 // interpolate(), reading a coarse neighbour on tlevel through coarse_cell
-// (sco[r]: the staged entries of region r's coarse neighbour)
 template <typename real, int MX>
 __device__ __forceinline__ bool interpolate_direct(const DevForest<real>& D, const NbrStage& st,
-                                                   const NbrStage* sco, const PatchMeta& pm,
-                                                   int tlevel, real alpha, int i, int j,
-                                                   real& v) {
+                                                   const PatchMeta& pm, int tlevel, real alpha,
+                                                   int i, int j, real& v) {
   const int r = region_of<MX>(i, j);
   const NbrEntry& e = st.e[r];
   if (e.kind != NB_COARSE) return false;
@@ -168,15 +174,51 @@ __device__ __forceinline__ bool interpolate_direct(const DevForest<real>& D, con
   if (ic < 0 || ic >= MX || jc < 0 || jc >= MX) return false;
   const real dx = (gx & 1) ? real(1) : real(-1);
   const real dy = (gy & 1) ? real(1) : real(-1);
-  const NbrStage& sc = sco[r];
   auto C = [&](int di, int dj) {
-    return coarse_cell<real, MX>(D, sc, nm, e.n0, tlevel, alpha, ic + di, jc + dj);
+    return coarse_cell<real, MX>(D, nm, e.n0, tlevel, alpha, ic + di, jc + dj);
   };
   const real q0 = C(0, 0);
   const real sx = minmod(C(1, 0) - q0, q0 - C(-1, 0));
   const real sy = minmod(C(0, 1) - q0, q0 - C(0, -1));
   v = q0 + real(0.25) * (sx * dx + sy * dy);
   return true;
+}
+
+// The neighbour reads of Alg. 1 for one patch (its copy/average and
+// interpolation rules), made while the patch's own tile is still in flight:
+// slot k of ring / ring_w gets ghost k's value and whether a rule set it (an
+// exterior ghost is left to the wall condition).  Threads tid, stride nt.
+// direct: coarse neighbours on tlevel are read through coarse_cell.
+template <typename real, int MX>
+__device__ __forceinline__ void gather_ring(const DevForest<real>& D, const NbrStage& st,
+                                            const PatchMeta& pm, int tlevel, real alpha,
+                                            bool direct, real* ring, bool* ring_w, int tid,
+                                            int nt) {
+#pragma unroll 1
+  for (int k = tid; k < num_ghosts<MX>(); k += nt) {
+    int i, j;
+    ghost_ij<MX>(k, i, j);
+    real v;
+    const bool w =
+        copy_or_average<real, MX>(D, st, pm, tlevel, alpha, i, j, v) ||
+        (direct ? interpolate_direct<real, MX>(D, st, pm, tlevel, alpha, i, j, v)
+                : interpolate<real, MX>(D, st, pm, tlevel, i, j, v));
+    ring[k] = w ? v : real(0);
+    ring_w[k] = w;
+  }
+}
+
+// the gathered ghosts into the landed tile Q (each thread its own slots)
+template <typename real, int MX>
+__device__ __forceinline__ void store_ring(real* Q, const real* ring, const bool* ring_w, int tid,
+                                           int nt) {
+  constexpr int S = MX + 4;
+  for (int k = tid; k < num_ghosts<MX>(); k += nt)
+    if (ring_w[k]) {
+      int i, j;
+      ghost_ij<MX>(k, i, j);
+      Q[(j + kMbc) * S + i + kMbc] = ring[k];
+    }
 }
 
 // walls: exterior ghosts of the owner's array Q (threads tid, stride nt)
@@ -217,14 +259,14 @@ __device__ __forceinline__ void corner3_fill(const NbrStage& st, real* Q, int ti
 
 // The whole of Alg. 1 for one patch into array Q (shared or global):
 // copy/average, boundary condition, interpolation, boundary condition.
-// `sync` orders the phases across the cooperating threads.  sco non-null:
+// `sync` orders the phases across the cooperating threads.  direct:
 // coarse neighbours on tlevel are read through coarse_cell (no fill of
 // their tiles ran for this substep).
 template <typename real, int MX, class Sync>
 __device__ __forceinline__ void fill_patch_ghosts(const DevForest<real>& D, const NbrStage& st,
                                                   const PatchMeta& pm, int tlevel, real alpha,
                                                   real* Q, int tid, int nt, Sync sync,
-                                                  const NbrStage* sco = nullptr) {
+                                                  bool direct = false) {
   constexpr int S = MX + 4;
   for (int k = tid; k < num_ghosts<MX>(); k += nt) {
     int i, j;
@@ -241,8 +283,8 @@ __device__ __forceinline__ void fill_patch_ghosts(const DevForest<real>& D, cons
     int i, j;
     ghost_ij<MX>(k, i, j);
     real v;
-    if (sco ? interpolate_direct<real, MX>(D, st, sco, pm, tlevel, alpha, i, j, v)
-            : interpolate<real, MX>(D, st, pm, tlevel, i, j, v))
+    if (direct ? interpolate_direct<real, MX>(D, st, pm, tlevel, alpha, i, j, v)
+               : interpolate<real, MX>(D, st, pm, tlevel, i, j, v))
       Q[(j + kMbc) * S + i + kMbc] = v;
   }
   sync();

@@ -192,7 +192,8 @@ class Forest:
         return {b: tuple(int(v) for v in rep[b]) for b in range(32) if rep[b, 0] >= 0}
 
     def set_advance_variant(self, variant: int, warps: int = 4):
-        """Force 0 staged / 1 walk / 2 walk1 for every launch; -1 restores the tuned choice."""
+        """Force 0 staged / 1 walk / 2 walk1 / 3 band for every launch; -1
+        restores the tuned choice (warps 2, 4, 8; 16 for band)."""
         check(load().fc_set_advance_variant(self._h, variant, warps))
 
     def set_limits(self, walk_ctas: int = 0, wait_polls: int = -1):

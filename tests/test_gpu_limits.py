@@ -49,7 +49,7 @@ def test_walk_persistent_loop_matches_oracle(ctas, variant, mx):
         assert err <= tol
 
 
-@pytest.mark.parametrize("variant", [0, 1, 2])
+@pytest.mark.parametrize("variant", [0, 1, 2, 3])
 def test_bounded_wait_gives_up_then_recovers(variant):
     w = synth.swirl(2, lmin=2, lmax=4, mx=16)
     _, dtc = synth.time_step(w)

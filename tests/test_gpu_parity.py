@@ -249,7 +249,7 @@ def test_launch_counter_counts_kernels():
         assert fc.launch_count() == 1 + 1 + 1 + 1
 
 
-@pytest.mark.parametrize("variant", [0, 1])
+@pytest.mark.parametrize("variant", [0, 1, 3])
 def test_fused_fill_matches_separate_fills_bitwise(variant):
     w = synth.swirl(9, lmin=2, lmax=5, mx=16)
     _, dtc = synth.time_step(w)
@@ -341,11 +341,13 @@ def test_timers_count_every_replay_across_regrids():
     assert launches == expect and ms > 0 and nbytes > 0
 
 
-@pytest.mark.parametrize("variant,warps", [(0, 4), (1, 2), (1, 4), (1, 8), (2, 4), (2, 8)])
+@pytest.mark.parametrize("variant,warps", [(0, 4), (1, 2), (1, 4), (1, 8), (2, 4), (2, 8),
+                                           (3, 2), (3, 4), (3, 8), (3, 16)])
 @pytest.mark.parametrize("mx", [8, 16, 32])
 def test_advance_variants_match_oracle(variant, warps, mx):
-    """Both patch-update kernels (staged; walk with 2/4/8 warps per CTA) on
-    an adaptive swirl forest, FP64 and FP32, against the oracle."""
+    """Every patch-update kernel (staged; walk with 2/4/8 warps per CTA;
+    walk1; band with 1 to 16 rows a band) on an adaptive swirl forest, FP64
+    and FP32, against the oracle."""
     w = synth.swirl(8, lmin=2, lmax=4 if mx == 32 else 5, mx=mx)
     _, dtc = synth.time_step(w)
     for dtype, tol in ((fc.F64, F64_TOL), (fc.F32, 1e-4)):
@@ -362,12 +364,15 @@ def test_advance_variants_match_oracle(variant, warps, mx):
 @pytest.mark.parametrize("scheme", [dict(limiter="none"), dict(limiter="first"),
                                     dict(transverse=1), dict(domain="periodic"),
                                     dict(velocity=("const", -0.7, 0.45))])
-def test_walk_variant_scheme_options(scheme):
+@pytest.mark.parametrize("variant", [1, 3])
+def test_row_walk_variants_scheme_options(scheme, variant):
+    """The scheme's options (limiter, transverse terms, boundaries, constant
+    velocity of either sign) in the row-walking kernels (walk, band)."""
     w = synth.swirl(4, lmin=2, lmax=4, mx=16)
     for k, v in scheme.items():
         setattr(w, k, v)
     ref, gpu = pair(fc, w, fc.F64)
-    gpu.set_advance_variant(1, 4)
+    gpu.set_advance_variant(variant, 4)
     dt = 0.45 / (16 * 16)
     for n in range(4):
         ref.step_global(n * dt, dt)
@@ -381,7 +386,7 @@ def test_autotune_then_parity():
     ref, gpu = pair(fc, ws, fc.F64)
     rep = gpu.autotune()
     assert len(rep) >= 2
-    assert all(v[0] in (0, 1) and v[2] in (0, 1) and v[3] > 0 for v in rep.values())
+    assert all(v[0] in (0, 1, 2, 3) and v[2] in (0, 1) and v[3] > 0 for v in rep.values())
     for n in range(2):
         ref.step_multirate(n * dtc, dtc)
         gpu.step_multirate(n * dtc, dtc)

@@ -69,13 +69,24 @@ def test_partitioned_multirate_is_bitwise_the_whole_forest(kind, nparts):
         vp.close()
 
 
-@pytest.mark.parametrize("variant", [0, 1])
+@pytest.mark.parametrize("variant", [0, 1, 3])
 def test_partitioned_global_steps_are_bitwise_the_whole_forest(variant):
     w, lv, whole, vp = _pair("walls", fc.F64, 3, variant)
     dt = 0.9 / (16 * 2 ** 5)
     for n in range(4):
         whole.step_global(n * dt, dt)
         vp.step_global(n * dt, dt)
+    np.testing.assert_array_equal(vp.get_q(), whole.get_q())
+    vp.close()
+
+
+@pytest.mark.parametrize("kind", ["walls", "periodic"])
+def test_partitioned_band_multirate_is_bitwise_the_whole_forest(kind):
+    w, lv, whole, vp = _pair(kind, fc.F32, 3, 3)
+    _, dtc = synth.time_step(w)
+    for n in range(2):
+        whole.step_multirate(n * dtc, dtc)
+        vp.step_multirate(n * dtc, dtc)
     np.testing.assert_array_equal(vp.get_q(), whole.get_q())
     vp.close()
 

@@ -28,16 +28,21 @@ def _w(domain="periodic", velocity=("swirl", 4.0), seed=2, lmin=2, lmax=4, mx=8)
     ("walls", ("swirl", 4.0), 16, 4),
     ("periodic", ("swirl", 4.0), 32, 5),
 ])
-def test_multirate_matches_oracle(domain, velocity, mx, lmax):
+@pytest.mark.parametrize("variant", [-1, 3])
+def test_multirate_matches_oracle(domain, velocity, mx, lmax, variant):
+    """Default update (staged) and the band update, which records the face
+    fluxes too."""
     w = _w(domain, velocity, mx=mx, lmax=lmax)
     _, dtc = synth.time_step(w)
     for dtype, tol in ((fc.F64, F64_TOL), (fc.F32, 1e-4)):
         ref, gpu = pair(fc, w, dtype)
+        gpu.set_advance_variant(variant, 8)
         for n in range(3):
             ref.step_multirate(n * dtc, dtc)
             gpu.step_multirate(n * dtc, dtc)
         err = relerr(gpu.get_q(), ref.get_q())
-        print(f"reflux multirate {domain} mx={mx} dtype {dtype}: rel err {err:.2e}")
+        print(f"reflux multirate {domain} mx={mx} variant {variant} dtype {dtype}: "
+              f"rel err {err:.2e}")
         assert err <= tol
 
 
@@ -52,7 +57,8 @@ def test_global_steps_match_oracle():
 
 
 @pytest.mark.parametrize("mode", ["multirate", "global"])
-def test_mass_conserved_to_rounding(mode):
+@pytest.mark.parametrize("variant", [-1, 3])
+def test_mass_conserved_to_rounding(mode, variant):
     """FP64: total mass after the steps equals the initial mass to rounding,
     where without the correction it drifts (the forest has coarse/fine faces)."""
     drift = {}
@@ -61,6 +67,7 @@ def test_mass_conserved_to_rounding(mode):
         _, dtc = synth.time_step(w)
         dt = dtc if mode == "multirate" else dtc / 2 ** (w.lmax - w.lmin)
         _, gpu = pair(fc, w, fc.F64)
+        gpu.set_advance_variant(variant, 4)
         m0 = gpu.mass().sum()
         for n in range(4):
             (gpu.step_multirate if mode == "multirate" else gpu.step_global)(n * dt, dt)
