@@ -63,6 +63,11 @@ def parse():
     ap.add_argument("--dtype", choices=["f32", "f64"], default="f32")
     ap.add_argument("--no-variants", action="store_true", help="skip FP64, batched and CPU legs")
     ap.add_argument("--ensemble", type=int, default=256, help="forests in the batched variant")
+    ap.add_argument("--variant", default="auto",
+                    help="update kernel of the headline (and --mode batched) forest: auto "
+                         "(autotuned per launch size), or NAME[:WARPS] with NAME staged, walk, "
+                         "walk1 or band -- e.g. to profile the kernels a default run's tuning "
+                         "chose (a profiler distorts the tuner's timings)")
     ap.add_argument("--mode", choices=["full", "batched", "sphere", "sphere_deform", "adjoint",
                                        "sweep"],
                     default="full",
@@ -182,7 +187,7 @@ def peaks():
 class Runner:
     """One forest (or ensemble) on this rank's GPU, stepped coarse step by coarse step."""
 
-    def __init__(self, fc, torch, workloads, dtype):
+    def __init__(self, fc, torch, workloads, dtype, variant="auto"):
         self.fc, self.torch, self.ws = fc, torch, workloads
         w = workloads[0]
         self.w = w
@@ -196,10 +201,17 @@ class Runner:
                             smooth=int(w.smooth))
         self.F = fc.initial_forest(desc, q0_fn(workloads), lmax_f=self.lmax_f,
                                    tau_r=w.tau_refine, tau_c=w.tau_coarsen)
-        # pick the patch-update kernel per launch size on this layout (untimed setup)
-        self.tuning = {int(b): {"variant": ["staged", "walk", "walk1", "band"][v], "warps": k,
-                                "fill": "fused" if fu else "separate", "ns": ns}
-                       for b, (v, k, fu, ns) in self.F.autotune().items()}
+        names = ["staged", "walk", "walk1", "band"]
+        if variant != "auto":  # one kernel for every launch
+            name, _, warps = variant.partition(":")
+            warps = int(warps or 4)
+            self.F.set_advance_variant(names.index(name), warps)
+            self.tuning = {"all": {"variant": name, "warps": warps, "fill": "fused"}}
+        else:
+            # pick the patch-update kernel per launch size on this layout (untimed setup)
+            self.tuning = {int(b): {"variant": names[v], "warps": k,
+                                    "fill": "fused" if fu else "separate", "ns": ns}
+                           for b, (v, k, fu, ns) in self.F.autotune().items()}
         self.n = 0
 
     def updates(self) -> int:
@@ -257,33 +269,36 @@ def measure(runner, steps, warmup, flush_buf, clock_index):
                 step_ms_max=max(step_ms) if step_ms else None)
 
 
-# DRAM bytes per patch advance of the staged FP32 update at mx = 32, from one
-# ncu capture of the 62 update launches of two timed coarse steps of the swirl
-# forest (10196 patch advances: 87.3 MB read, nothing written back -- the new
-# interiors stay in the 129 MB L2 -- so 8564 B per patch against 9280 B
-# algorithmic).  Reported while the kernel's sources are the ones captured
-# (their hash) and every timed launch is staged, else null.
-STAGED_DRAM_PER_PATCH = {(4, 32): 8564.0}
-STAGED_SOURCES = ("advance.cu", "ghost_gather.cuh", "device_util.cuh")
-STAGED_SOURCES_SHA = "899dfe1067ebf238"
+# DRAM bytes per patch advance of an update kernel at (element size, mx),
+# from one ncu capture of every update launch of two timed coarse steps of the
+# swirl forest (band, FP32, 32^2: 62 launches, 10196 patch advances, 86.7 MB
+# read and nothing written back -- the new interiors stay in the 129 MB L2 --
+# so 8508 B per patch against 9280 B algorithmic).  Reported while the
+# kernel's sources are the ones captured (their hash) and every timed launch
+# runs that kernel, else null.
+DRAM_PER_PATCH = {("band", 4, 32): 8508.0}
+KERNEL_SOURCES = {"band": ('advance_band.cu', 'ghost_gather.cuh', 'device_util.cuh', 'walk_edge.cuh', 'fc_internal.hpp')}
+KERNEL_SOURCES_SHA = {"band": "d6eebc2650898761"}
 
 
-def staged_sources_sha():
+def sources_sha(variant):
     h = hashlib.sha256()
-    for f in STAGED_SOURCES:
+    for f in KERNEL_SOURCES[variant]:
         with open(os.path.join(ROOT, "paper_1703_03116_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 
 
-def staged_traffic(phase, tuning, esize, mx):
+def measured_traffic(phase, tuning, esize, mx):
     """DRAM bytes per advance launch from the captured per-patch figure (the
     launches' patch counts from their algorithmic bytes), or None."""
-    per = STAGED_DRAM_PER_PATCH.get((esize, mx))
     ms, n, nbytes = phase
-    if per is None or not tuning or n <= 0 or staged_sources_sha() != STAGED_SOURCES_SHA:
+    variants = {t["variant"] for t in tuning.values()} if tuning else set()
+    if n <= 0 or len(variants) != 1:
         return None
-    if any(t["variant"] != "staged" for t in tuning.values()):
+    v = variants.pop()
+    per = DRAM_PER_PATCH.get((v, esize, mx))
+    if per is None or sources_sha(v) != KERNEL_SOURCES_SHA[v]:
         return None
     patches_per_launch = nbytes / n / (((mx + 4) ** 2 + mx * mx) * esize)
     return per * patches_per_launch
@@ -469,7 +484,8 @@ def run_ours(args):
         else:
             ws = [synth.sphere(seed=rank)]
             label = SPHERE_WORKLOAD
-        b = measure(Runner(fc, torch, ws, dtype), args.steps, args.warmup, flush_buf, local)
+        b = measure(Runner(fc, torch, ws, dtype, args.variant), args.steps, args.warmup,
+                    flush_buf, local)
         line = {"metric": METRIC, "value": reduce(float(b["updates"]), SUM) /
                 (reduce(b["ms"], MAX) * 1e-3), "unit": METRIC, "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": b["ms"] / args.steps,
@@ -484,7 +500,7 @@ def run_ours(args):
         if dist is not None:
             dist.destroy_process_group()
         return
-    run = Runner(fc, torch, [rank_workload(rank)], dtype)
+    run = Runner(fc, torch, [rank_workload(rank)], dtype, args.variant)
     torch.cuda.synchronize()
     if dist is not None:
         dist.barrier()
@@ -539,7 +555,7 @@ def run_ours(args):
                    "parallelism": f"independent forest per GPU x{world}"},
         "clocks": r["clocks"], "e2e": e2e, "gpu_launches": r["launches"],
         "roofline": roofline_of(r["phases"]["advance"], hbm, peak_src,
-                                staged_traffic(r["phases"]["advance"], r["tuning"],
+                                measured_traffic(r["phases"]["advance"], r["tuning"],
                                                4 if dtype == fc.F32 else 8, synth.swirl(seed=0).mx)),
         "phases_ms": {k: v[0] for k, v in r["phases"].items()} | {"step_total": r["ms"]},
         "autotune": r["tuning"],

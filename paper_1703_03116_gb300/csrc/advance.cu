@@ -180,8 +180,9 @@ __global__ void __launch_bounds__(NT, NT >= 512 ? (sizeof(real) == 4 ? 3 : 2)
     // exterior ghosts copy cells that are final by then) and, on the sphere,
     // the corners beyond a cube vertex
     auto gather = [&](int nthreads) {
-      gather_ring<real, MX>(D, st, pm, a.tlevel, real(a.alpha), a.direct != 0, ring, ring_w,
-                            threadIdx.x, nthreads);
+      gather_ring<real, MX>(
+          D, [&](int r) -> const NbrEntry& { return st.e[r]; }, pm, a.tlevel, real(a.alpha),
+          a.direct != 0, ring, ring_w, threadIdx.x, nthreads);
     };
     bool split_done = false;
     if constexpr (SPLIT) {

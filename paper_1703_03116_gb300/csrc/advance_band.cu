@@ -62,7 +62,6 @@ __global__ void __launch_bounds__(band_threads<real, MX, R>(), band_min_blocks<r
   __shared__ __align__(128) real Q[S * S];
   __shared__ __align__(8) uint64_t bar;
   __shared__ real ucoef_s;
-  __shared__ NbrStage st;
   __shared__ real ring[NG];    // ghost values gathered while the tile loads
   __shared__ bool ring_w[NG];
   // streamfunction tables over corner nodes k = 0..MX+2 (index k - 1):
@@ -77,8 +76,8 @@ __global__ void __launch_bounds__(band_threads<real, MX, R>(), band_min_blocks<r
   const int tid = threadIdx.x;
   const int li = tid % MX;  // column of this lane
   const int r0 = (tid / MX) * R;  // first row of this lane's band
-  // thread 0 initialises the copy barrier and issues the copies itself; the
-  // other threads first wait on it after the patch's entry barrier below
+  // thread 0 initialises the copy barrier, issues the copies and waits for
+  // them; the other threads touch the barrier only after a CTA barrier
   if (tid == 0) mbar_init(&bar, 1);
   const real cu = real(D.vel[0]), cv = real(D.vel[1]);
   const real h = real(a.h);
@@ -96,12 +95,11 @@ __global__ void __launch_bounds__(band_threads<real, MX, R>(), band_min_blocks<r
       bulk_load(Q, src, bytes, &bar);
     }
     // the swirl coefficient, by the last thread (it gathers at most one
-    // ghost, the staging threads none); read after the barriers below
+    // ghost); read after the barrier below
     if (SWIRL && tid == NT - 1 && p == p0 + (int)blockIdx.x) {
       const double t = a.t0_dev ? *a.t0_dev + a.t_off : a.t_half;
       ucoef_s = cospi_ratio<real>(t, a.period) * real(a.sfac);
     }
-    if (a.gather && tid < 8) stage_neighbours(D.meta, D.nbr, p, st, tid);
     if (SWIRL) {  // the tables, while the tile is in flight
       for (int k = tid; k < 4 * NV; k += NT) {
         const int tb = k / NV, c = k % NV;
@@ -116,18 +114,21 @@ __global__ void __launch_bounds__(band_threads<real, MX, R>(), band_min_blocks<r
         (tb == 0 ? Sx : tb == 1 ? Sy : tb == 2 ? Tx : Ty)[c] = v;
       }
     }
-    __syncthreads();  // the patch's entries; the copy barrier initialised
+    // each gathering thread reads the entry of its ghost's region from the
+    // table itself: no staging pass, no barrier before the gather
     if (a.gather)
-      gather_ring<real, MX>(D, st, pm, a.tlevel, real(a.alpha), a.direct != 0, ring, ring_w, tid,
-                            NT);
-    // every thread observes the copy's completion (bounded); the CTA leaves
-    // together if any thread gave up
-    const bool landed = mbar_wait(&bar, parity, a.wait_limit);
+      gather_ring<real, MX>(
+          D, [&](int r) { return D.nbr[(size_t)p * 8 + r]; }, pm, a.tlevel, real(a.alpha),
+          a.direct != 0, ring, ring_w, tid, NT);
+    // thread 0 observes the copy's completion (bounded), the others after the
+    // barrier (at once); the CTA leaves together if it gave up
+    const bool landed = tid == 0 ? mbar_wait(&bar, parity, a.wait_limit) : true;
     if (!__syncthreads_and(landed)) {
       if (tid == 0) atomicOr(err, kErrTimeout);
       mbar_wait(&bar, parity, kWaitLimit);  // let the copy land before leaving
       return;
     }
+    if (tid != 0) mbar_wait(&bar, parity, kWaitLimit);
     if (a.gather) {
       store_ring<real, MX>(Q, ring, ring_w, tid, NT);
       __syncthreads();

@@ -102,24 +102,22 @@ __device__ __forceinline__ bool copy_or_average(const DevForest<real>& D, const 
                                          v);
 }
 
-// Ghost (i, j) of the owner from its coarser neighbour; the coarse patch is
-// read through the interpolation buffer when it lies on `tlevel`.
+// Ghost (i, j) of the owner from its coarser neighbour (e: the entry of the
+// ghost's region); the coarse patch is read through the interpolation buffer
+// when it lies on `tlevel`.
 template <typename real, int MX>
-__device__ __forceinline__ bool interpolate(const DevForest<real>& D, const NbrStage& st,
-                                            const PatchMeta& pm, int tlevel, int i, int j,
-                                            real& v) {
+__device__ __forceinline__ bool interpolate_entry(const DevForest<real>& D, const NbrEntry& e,
+                                                  const PatchMeta& pm, int tlevel, int i, int j,
+                                                  real& v) {
   constexpr int S = MX + 4;
-  const int r = region_of<MX>(i, j);
-  const NbrEntry& e = st.e[r];
   if (e.kind != NB_COARSE) return false;
   const int2 Ip = apply_a(e.a, pm.x * MX + i, pm.y * MX + j);
   const int gx = Ip.x + e.fx, gy = Ip.y + e.fy;
-  const PatchMeta& nm = st.m0[r];
-  const int ic = (gx >> 1) - nm.x * MX, jc = (gy >> 1) - nm.y * MX;
+  const int ic = (gx >> 1) - e.x0 * MX, jc = (gy >> 1) - e.y0 * MX;
   if (ic < 0 || ic >= MX || jc < 0 || jc >= MX) return false;
   const real dx = (gx & 1) ? real(1) : real(-1);
   const real dy = (gy & 1) ? real(1) : real(-1);
-  const real* C = patch_ptr(nm.level == tlevel ? D.qT : D.buf[D.cur[nm.level]], e.n0, S) +
+  const real* C = patch_ptr(e.lev == tlevel ? D.qT : D.buf[D.cur[e.lev]], e.n0, S) +
                   (jc + kMbc) * S + ic + kMbc;
   const real q0 = C[0];
   const real sx = minmod(C[1] - q0, q0 - C[-1]);
@@ -128,21 +126,31 @@ __device__ __forceinline__ bool interpolate(const DevForest<real>& D, const NbrS
   return true;
 }
 
+// the same from the owner's staged entries
+template <typename real, int MX>
+__device__ __forceinline__ bool interpolate(const DevForest<real>& D, const NbrStage& st,
+                                            const PatchMeta& pm, int tlevel, int i, int j,
+                                            real& v) {
+  return interpolate_entry<real, MX>(D, st.e[region_of<MX>(i, j)], pm, tlevel, i, j, v);
+}
+
 // The value the coarse-neighbour fill of a multirate substep (phases 1-2 at
 // tlevel and alpha, then the wall condition) leaves in cell (i, j) of the
 // time-interpolated tile of patch c (on tlevel; cm: its level and
-// position): the interior (1 - alpha) q_old + alpha q_new,
-// ghosts copied from same-size or averaged from finer neighbours, exterior
-// ghosts from the cell the wall condition clamps them to; any other ghost
-// keeps what the tile holds (that fill leaves it alone).  An update that
-// computes the few coarse cells its interpolation reads this way needs no
-// fill launch before it.  Not for the cubed sphere (its corner rule).  A
-// ghost of c reads c's entry for its region from the table itself: only the
-// stencils that leave c's interior wait for that read.
+// position): the interior (1 - alpha) q_old + alpha q_new, ghosts copied
+// from same-size or averaged from finer neighbours, exterior ghosts from the
+// cell the wall condition clamps them to; any other ghost keeps what the
+// tile holds (that fill leaves it alone).  An update that computes the few
+// coarse cells its interpolation reads this way needs no fill launch before
+// it.  Not for the cubed sphere (its corner rule).
+//
+// Split in two: coarse_cell_interior applies the wall condition's clamp and
+// says whether the cell is interior (then src_interior reads it); a ghost
+// of c is coarse_ghost, which reads c's entry for its region from the table
+// itself, so only the stencils that leave c's interior wait for that read.
 template <typename real, int MX>
-__device__ __forceinline__ real coarse_cell(const DevForest<real>& D, const PatchMeta& cm, int c,
-                                            int tlevel, real alpha, int i, int j) {
-  constexpr int S = MX + 4;
+__device__ __forceinline__ bool coarse_cell_interior(const DevForest<real>& D,
+                                                     const PatchMeta& cm, int& i, int& j) {
   if (D.domain == FC_DOMAIN_WALLS) {
     const int N = MX << cm.level;
     const int gx = cm.x * MX + i, gy = cm.y * MX + j;
@@ -150,47 +158,76 @@ __device__ __forceinline__ real coarse_cell(const DevForest<real>& D, const Patc
     if (ox) i = gx < 0 ? 0 : MX - 1;
     if (oy) j = gy < 0 ? 0 : MX - 1;
   }
-  if (i >= 0 && i < MX && j >= 0 && j < MX)
-    return src_interior(D, tlevel, alpha, c, cm.level, i, j);
+  return i >= 0 && i < MX && j >= 0 && j < MX;
+}
+
+template <typename real, int MX>
+__device__ __forceinline__ real coarse_ghost(const DevForest<real>& D, const PatchMeta& cm, int c,
+                                             int tlevel, real alpha, int i, int j) {
+  constexpr int S = MX + 4;
   real v;
   const NbrEntry e = D.nbr[(size_t)c * 8 + region_of<MX>(i, j)];
   if (copy_or_average_entry<real, MX>(D, e, cm, tlevel, alpha, i, j, v)) return v;
   return D.qT[(size_t)c * S * S + (j + kMbc) * S + i + kMbc];
 }
 
-// interpolate(), reading a coarse neighbour on tlevel through coarse_cell
+// interpolate_entry(), reading a coarse neighbour on tlevel through the
+// cells the coarse-neighbour fill would leave (above): the stencil's
+// interior cells are read together first, then any ghost of the coarse
+// patch (the same values in any order)
+template <typename real, int MX>
+__device__ __forceinline__ bool interpolate_direct_entry(const DevForest<real>& D,
+                                                         const NbrEntry& e, const PatchMeta& pm,
+                                                         int tlevel, real alpha, int i, int j,
+                                                         real& v) {
+  if (e.kind != NB_COARSE) return false;
+  if (e.lev != tlevel) return interpolate_entry<real, MX>(D, e, pm, tlevel, i, j, v);
+  const int2 Ip = apply_a(e.a, pm.x * MX + i, pm.y * MX + j);
+  const int gx = Ip.x + e.fx, gy = Ip.y + e.fy;
+  const int ic = (gx >> 1) - e.x0 * MX, jc = (gy >> 1) - e.y0 * MX;
+  if (ic < 0 || ic >= MX || jc < 0 || jc >= MX) return false;
+  const real dx = (gx & 1) ? real(1) : real(-1);
+  const real dy = (gy & 1) ? real(1) : real(-1);
+  const PatchMeta cm{e.lev, e.x0, e.y0, 0, 0, 0};
+  // stencil cells (0,0), (+1,0), (-1,0), (0,+1), (0,-1)
+  int ci[5], cj[5];
+  bool in[5];
+  real c[5];
+#pragma unroll
+  for (int m = 0; m < 5; ++m) {
+    ci[m] = ic + (m == 1 ? 1 : m == 2 ? -1 : 0);
+    cj[m] = jc + (m == 3 ? 1 : m == 4 ? -1 : 0);
+    in[m] = coarse_cell_interior<real, MX>(D, cm, ci[m], cj[m]);
+    c[m] = in[m] ? src_interior(D, tlevel, alpha, e.n0, e.lev, ci[m], cj[m]) : real(0);
+  }
+#pragma unroll
+  for (int m = 0; m < 5; ++m)
+    if (!in[m]) c[m] = coarse_ghost<real, MX>(D, cm, e.n0, tlevel, alpha, ci[m], cj[m]);
+  const real q0 = c[0];
+  const real sx = minmod(c[1] - q0, q0 - c[2]);
+  const real sy = minmod(c[3] - q0, q0 - c[4]);
+  v = q0 + real(0.25) * (sx * dx + sy * dy);
+  return true;
+}
+
+// the same from the owner's staged entries
 template <typename real, int MX>
 __device__ __forceinline__ bool interpolate_direct(const DevForest<real>& D, const NbrStage& st,
                                                    const PatchMeta& pm, int tlevel, real alpha,
                                                    int i, int j, real& v) {
-  const int r = region_of<MX>(i, j);
-  const NbrEntry& e = st.e[r];
-  if (e.kind != NB_COARSE) return false;
-  const PatchMeta& nm = st.m0[r];
-  if (nm.level != tlevel) return interpolate<real, MX>(D, st, pm, tlevel, i, j, v);
-  const int2 Ip = apply_a(e.a, pm.x * MX + i, pm.y * MX + j);
-  const int gx = Ip.x + e.fx, gy = Ip.y + e.fy;
-  const int ic = (gx >> 1) - nm.x * MX, jc = (gy >> 1) - nm.y * MX;
-  if (ic < 0 || ic >= MX || jc < 0 || jc >= MX) return false;
-  const real dx = (gx & 1) ? real(1) : real(-1);
-  const real dy = (gy & 1) ? real(1) : real(-1);
-  auto C = [&](int di, int dj) {
-    return coarse_cell<real, MX>(D, nm, e.n0, tlevel, alpha, ic + di, jc + dj);
-  };
-  const real q0 = C(0, 0);
-  const real sx = minmod(C(1, 0) - q0, q0 - C(-1, 0));
-  const real sy = minmod(C(0, 1) - q0, q0 - C(0, -1));
-  v = q0 + real(0.25) * (sx * dx + sy * dy);
-  return true;
+  return interpolate_direct_entry<real, MX>(D, st.e[region_of<MX>(i, j)], pm, tlevel, alpha, i,
+                                            j, v);
 }
 
 // The neighbour reads of Alg. 1 for one patch (its copy/average and
 // interpolation rules), made while the patch's own tile is still in flight:
 // slot k of ring / ring_w gets ghost k's value and whether a rule set it (an
-// exterior ghost is left to the wall condition).  Threads tid, stride nt.
-// direct: coarse neighbours on tlevel are read through coarse_cell.
-template <typename real, int MX>
-__device__ __forceinline__ void gather_ring(const DevForest<real>& D, const NbrStage& st,
+// exterior ghost is left to the wall condition).  entry_of(r) gives the
+// entry of face/corner region r (staged in shared memory, or read from the
+// table).  Threads tid, stride nt.  direct: coarse neighbours on tlevel are
+// read through the cells their fill would leave (interpolate_direct_entry).
+template <typename real, int MX, class EntryOf>
+__device__ __forceinline__ void gather_ring(const DevForest<real>& D, EntryOf entry_of,
                                             const PatchMeta& pm, int tlevel, real alpha,
                                             bool direct, real* ring, bool* ring_w, int tid,
                                             int nt) {
@@ -198,11 +235,12 @@ __device__ __forceinline__ void gather_ring(const DevForest<real>& D, const NbrS
   for (int k = tid; k < num_ghosts<MX>(); k += nt) {
     int i, j;
     ghost_ij<MX>(k, i, j);
+    const NbrEntry e = entry_of(region_of<MX>(i, j));
     real v;
     const bool w =
-        copy_or_average<real, MX>(D, st, pm, tlevel, alpha, i, j, v) ||
-        (direct ? interpolate_direct<real, MX>(D, st, pm, tlevel, alpha, i, j, v)
-                : interpolate<real, MX>(D, st, pm, tlevel, i, j, v));
+        copy_or_average_entry<real, MX>(D, e, pm, tlevel, alpha, i, j, v) ||
+        (direct ? interpolate_direct_entry<real, MX>(D, e, pm, tlevel, alpha, i, j, v)
+                : interpolate_entry<real, MX>(D, e, pm, tlevel, i, j, v));
     ring[k] = w ? v : real(0);
     ring_w[k] = w;
   }
@@ -260,8 +298,8 @@ __device__ __forceinline__ void corner3_fill(const NbrStage& st, real* Q, int ti
 // The whole of Alg. 1 for one patch into array Q (shared or global):
 // copy/average, boundary condition, interpolation, boundary condition.
 // `sync` orders the phases across the cooperating threads.  direct:
-// coarse neighbours on tlevel are read through coarse_cell (no fill of
-// their tiles ran for this substep).
+// coarse neighbours on tlevel are read through the cells their fill would
+// leave (no fill of their tiles ran for this substep).
 template <typename real, int MX, class Sync>
 __device__ __forceinline__ void fill_patch_ghosts(const DevForest<real>& D, const NbrStage& st,
                                                   const PatchMeta& pm, int tlevel, real alpha,

@@ -1,7 +1,7 @@
 """CPU checks of the measurement arithmetic in bench.py: the unit count of a
 coarse step, the roofline fraction, and when the captured DRAM traffic is
 reported (only for the kernel sources it was captured on, only when every
-timed launch ran the staged update)."""
+timed launch ran the kernel it was captured for)."""
 import numpy as np
 
 import bench
@@ -21,14 +21,18 @@ def test_roofline_of_is_bytes_over_time():
     assert r["traffic"] is None and r["bound"] == "hbm" and r["unit"] == "GB/s"
 
 
-def test_staged_traffic_follows_the_captured_sources(monkeypatch):
+def test_measured_traffic_follows_the_captured_sources(monkeypatch):
     per_patch = (36 * 36 + 32 * 32) * 4.0
     phase = (1.0, 4, 4 * 50 * per_patch)     # 4 launches of 50 patches each
-    staged = {0: {"variant": "staged"}}
-    monkeypatch.setattr(bench, "STAGED_SOURCES_SHA", bench.staged_sources_sha())
-    t = bench.staged_traffic(phase, staged, 4, 32)
-    assert abs(t - bench.STAGED_DRAM_PER_PATCH[(4, 32)] * 50) < 1e-6
-    assert bench.staged_traffic(phase, {0: {"variant": "walk"}}, 4, 32) is None
-    assert bench.staged_traffic(phase, staged, 8, 32) is None    # no capture for FP64
-    monkeypatch.setattr(bench, "STAGED_SOURCES_SHA", "0" * 16)
-    assert bench.staged_traffic(phase, staged, 4, 32) is None   # sources changed since
+    band = {0: {"variant": "band"}, 5: {"variant": "band"}}
+    monkeypatch.setitem(bench.KERNEL_SOURCES_SHA, "band", bench.sources_sha("band"))
+    t = bench.measured_traffic(phase, band, 4, 32)
+    assert abs(t - bench.DRAM_PER_PATCH[("band", 4, 32)] * 50) < 1e-6
+    assert bench.measured_traffic(phase, {"all": {"variant": "band"}}, 4, 32) == t
+    mixed = {0: {"variant": "band"}, 5: {"variant": "walk"}}
+    assert bench.measured_traffic(phase, mixed, 4, 32) is None
+    assert bench.measured_traffic(phase, {0: {"variant": "walk"}}, 4, 32) is None
+    assert bench.measured_traffic(phase, band, 8, 32) is None    # no capture for FP64
+    monkeypatch.setitem(bench.KERNEL_SOURCES_SHA, "band", "0" * 16)
+    assert bench.measured_traffic(phase, band, 4, 32) is None   # sources changed since
+
