@@ -227,6 +227,267 @@ __device__ void adj_copy_patch(const NbrStage& st, const PatchMeta& pm, real* L,
   }
 }
 
+// One edge's transpose: e is the forward edge at speed s between cells a, b,
+// c, d along its normal (qb, qc the middle two); lF, lP, lM the adjoints of
+// its normal flux and of the fluctuations it sends into c's and b's side.
+// Returns the four cells' adjoint contributions and, in ds, the derivative
+// with respect to the edge speed times the speed.
+template <typename real>
+struct EdgeAdj {
+  real a, b, c, d, ds;
+};
+
+template <typename real>
+__device__ __forceinline__ EdgeAdj<real> edge_transpose(const EdgeFw<real>& e, int transverse,
+                                                       real s, real qb, real qc, real lF,
+                                                       real lP, real lM) {
+  const real sp = s > real(0) ? s : real(0), sm = s < real(0) ? s : real(0);
+  const real ip = s > real(0) ? real(1) : real(0), im = s < real(0) ? real(1) : real(0);
+  real lFt = lF, lW = 0, lWup = 0, ds = 0;
+  if (transverse > 0) {
+    lW += sp * lP + sm * lM;
+    ds += lP * ip * e.W + lM * im * e.W;
+    if (transverse > 1) lFt += -lP + lM;
+  }
+  EdgeAdj<real> o;
+  o.b = sp * lF;
+  o.c = sm * lF;
+  ds += lF * (ip * qb + im * qc);
+  lW += e.c * e.dW * lFt;
+  lWup += e.c * e.dWup * lFt;
+  ds += lFt * e.dc * e.lim;
+  o.c += lW;
+  o.b -= lW;
+  o.a = real(0);
+  o.d = real(0);
+  if (e.up) {
+    o.b += lWup;
+    o.a = -lWup;
+  } else {
+    o.d = lWup;
+    o.c -= lWup;
+  }
+  o.ds = ds * s;
+  return o;
+}
+
+template <typename real>
+__device__ __forceinline__ real pos(real s) { return s > real(0) ? s : real(0); }
+template <typename real>
+__device__ __forceinline__ real neg(real s) { return s < real(0) ? s : real(0); }
+
+// Transpose of the update of one patch (its final fluxes, their transverse
+// increments and every edge), as a row walk: thread tid's lane li owns
+// column li of the band of R rows starting at r0 = (tid / MX) R and walks
+// rows r0 - 1 .. r0 + R, recomputing the forward edges it needs from the
+// tile Q (x-edge (li, j) and y-edge (li, j + 1) at row j), taking the
+// neighbouring column's values by shuffles, and transposing the x-edges of
+// rows [r0, r0 + R) and the y-edges of rows [r0, r0 + R) (band 0 also the
+// x-edges of row -1, the last band those of row MX and its y-edges).  The
+// contributions to a cell's adjoint gather in a four-row register window of
+// the lane's column and reach LQ (zeroed) by one shared atomic add per cell
+// and band; ghost columns take theirs directly.  The edges of column MX (x)
+// and of ghost columns -1 and MX (y) are side_transpose's.  LN: adjoint of
+// the new interior; XMe[j + 1]: forward M of x-edge (MX, j); YPm[j], YMm[j]:
+// forward P, M of y-edge (-1, j).  Returns the lane's share of sum ds.
+template <typename real, int MX, int R, class UV, class VV>
+__device__ __forceinline__ real band_transpose(const real* Q, real* LQ, const real* LN,
+                                               const real* XMe, const real* YPm, const real* YMm,
+                                               int order, int limiter, int transverse, real nu,
+                                               real hn, UV uvel, VV vvel, int tid) {
+  constexpr int S = MX + 4;
+  constexpr unsigned FULL = 0xffffffffu;
+  const int li = tid % MX, r0 = (tid / MX) * R, r1 = r0 + R;
+  const bool last = r1 == MX;
+  auto q = [&](int i, int j) -> real { return Q[(j + kMbc) * S + i + kMbc]; };
+  auto ln = [&](int j) -> real { return (j >= 0 && j < MX) ? LN[j * MX + li] : real(0); };
+  auto flush = [&](int row, real v) {
+    if (row >= -kMbc && row <= MX + 1) atomicAdd(&LQ[(row + kMbc) * S + li + kMbc], v);
+  };
+  real dsum = 0;
+  real A0 = 0, A1 = 0, A2 = 0, A3 = 0;  // contributions to rows j-2 .. j+1
+  real qa = q(li, r0 - 2), qb = q(li, r0 - 1), qc = q(li, r0), qd = 0;
+  real ln_cur = ln(r0 - 1);
+  real v_cur = r0 - 1 >= 0 ? vvel(li, r0 - 1) : real(0);
+  real lGf_cur = r0 - 1 >= 0 ? nu * (ln_cur - ln(r0 - 2)) : real(0);
+  real YP_prev = 0, X_prev = 0, lY_prev = 0;
+  EdgeFw<real> ey{};  // forward y-edge (li, j)
+#pragma unroll(R <= 8 ? R + 2 : 2)
+  for (int it = 0; it < R + 2; ++it) {
+    const int j = r0 - 1 + it;
+    const bool xrow = (j >= r0 && j < r1) || j == -1 || (last && j == MX);
+    const bool yrow = (j >= r0 && j < r1) || (last && j == MX);
+    if (j + 2 <= MX + 1) qd = q(li, j + 2);
+    // forward: x-edge (li, j), y-edge (li, j + 1)
+    const real su = uvel(li, j);
+    const EdgeFw<real> ex =
+        edge_fw(order, limiter, transverse, su, q(li - 2, j), q(li - 1, j), qb, q(li + 1, j), nu);
+    real vn = 0;
+    EdgeFw<real> eyn{};
+    if (j + 1 <= MX) {
+      vn = vvel(li, j + 1);
+      eyn = edge_fw(order, limiter, transverse, vn, qa, qb, qc, qd, nu);
+    }
+    // adjoints of the final fluxes and of the fluctuation sums
+    const real ln_next = ln(j + 1);
+    const real lGf_next = j + 1 <= MX ? nu * (ln_next - ln_cur) : real(0);  // y-edge (li, j+1)
+    real ln_left = __shfl_up_sync(FULL, ln_cur, 1, MX);
+    if (li == 0) ln_left = real(0);
+    const bool frow = j >= 0 && j < MX;
+    const real lFf = frow ? nu * (ln_cur - ln_left) : real(0);  // x-edge (li, j)
+    real lFf_r = __shfl_down_sync(FULL, lFf, 1, MX);            // x-edge (li+1, j)
+    real su_r = __shfl_down_sync(FULL, su, 1, MX);
+    if (li == MX - 1) {
+      lFf_r = frow ? -nu * ln_cur : real(0);
+      su_r = uvel(MX, j);
+    }
+    const real lY = frow ? -hn * (pos(su_r) * lFf_r + neg(su) * lFf) : real(0);  // Y(li, j)
+    const real lX = -hn * (pos(vn) * lGf_next + (j >= 0 ? neg(v_cur) * lGf_cur : real(0)));
+    real lX_l = __shfl_up_sync(FULL, lX, 1, MX);  // X(li-1, j)
+    if (li == 0) lX_l = real(0);
+    // forward fluctuation sums X(li, j), Y(li, j), Y(li-1, j)
+    real XM_r = __shfl_down_sync(FULL, ex.M, 1, MX);
+    if (li == MX - 1) XM_r = XMe[j + 1];
+    const real X = ex.P + XM_r;
+    const real Y = YP_prev + eyn.M;
+    real Y_l = __shfl_up_sync(FULL, Y, 1, MX);
+    if (li == 0) Y_l = frow ? YPm[j] + YMm[j + 1] : real(0);
+    // x-edge (li, j)
+    EdgeAdj<real> ox =
+        edge_transpose(ex, transverse, su, q(li - 1, j), qb, lFf, transverse > 0 ? lX : real(0),
+                       transverse > 0 ? lX_l : real(0));
+    if (!xrow) ox = EdgeAdj<real>{0, 0, 0, 0, 0};
+    dsum += ox.ds;
+    if (transverse > 0 && xrow && frow) dsum -= hn * (pos(su) * Y_l + neg(su) * Y) * lFf;
+    real T = ox.c;
+    {
+      const real b1 = __shfl_down_sync(FULL, ox.b, 1, MX);
+      const real a2 = __shfl_down_sync(FULL, ox.a, 2, MX);
+      const real d1 = __shfl_up_sync(FULL, ox.d, 1, MX);
+      if (li + 1 < MX) T += b1;
+      if (li + 2 < MX) T += a2;
+      if (li >= 1) T += d1;
+    }
+    if (xrow) {  // contributions to the ghost columns
+      if (li == 0) {
+        atomicAdd(&LQ[(j + kMbc) * S + 0], ox.a);
+        atomicAdd(&LQ[(j + kMbc) * S + 1], ox.b);
+      }
+      if (li == 1) atomicAdd(&LQ[(j + kMbc) * S + 1], ox.a);
+      if (li == MX - 1) atomicAdd(&LQ[(j + kMbc) * S + MX + kMbc], ox.d);
+    }
+    // y-edge (li, j)
+    if (yrow) {
+      const EdgeAdj<real> oy =
+          edge_transpose(ey, transverse, v_cur, qa, qb, lGf_cur,
+                         transverse > 0 && j < MX ? lY : real(0),
+                         transverse > 0 && j > 0 ? lY_prev : real(0));
+      dsum += oy.ds;
+      if (transverse > 0) dsum -= hn * (pos(v_cur) * X_prev + neg(v_cur) * X) * lGf_cur;
+      A0 += oy.a;
+      A1 += oy.b;
+      A2 += oy.c;
+      A3 += oy.d;
+    }
+    A2 += T;
+    if (j >= r0 && j < r1) A2 += ln_cur;  // the update's identity part
+    flush(j - 2, A0);
+    A0 = A1;
+    A1 = A2;
+    A2 = A3;
+    A3 = real(0);
+    X_prev = X;
+    lY_prev = lY;
+    ey = eyn;
+    YP_prev = eyn.P;
+    v_cur = vn;
+    lGf_cur = lGf_next;
+    ln_cur = ln_next;
+    qa = qb;
+    qb = qc;
+    qc = qd;
+  }
+  const int jl = r0 + R;  // the last row walked
+  flush(jl - 1, A0);
+  flush(jl, A1);
+  flush(jl + 1, A2);
+  return dsum;
+}
+
+// The edges band_transpose leaves: x-edge (MX, j), j in [-1, MX], and the
+// y-edges of ghost columns -1 and MX, j in [0, MX] (threads tid, stride
+// nt, one edge each, contributions by shared atomic adds).  Returns the
+// threads' share of sum ds.
+template <typename real, int MX, class UV, class VV>
+__device__ __forceinline__ real side_transpose(const real* Q, real* LQ, const real* LN, int order,
+                                               int limiter, int transverse, real nu, real hn,
+                                               UV uvel, VV vvel, int tid, int nt) {
+  constexpr int S = MX + 4;
+  auto q = [&](int i, int j) -> real { return Q[(j + kMbc) * S + i + kMbc]; };
+  auto ln = [&](int i, int j) -> real {
+    return (i >= 0 && i < MX && j >= 0 && j < MX) ? LN[j * MX + i] : real(0);
+  };
+  auto add = [&](int i, int j, real v) { atomicAdd(&LQ[(j + kMbc) * S + i + kMbc], v); };
+  // adjoints of the final fluxes of x-edge (i, j) and y-edge (i, j)
+  auto lFf = [&](int i, int j) -> real {
+    return (j >= 0 && j < MX) ? nu * (ln(i, j) - ln(i - 1, j)) : real(0);
+  };
+  auto lGf = [&](int i, int j) -> real {
+    return (i >= 0 && i < MX && j >= 0 && j <= MX) ? nu * (ln(i, j) - ln(i, j - 1)) : real(0);
+  };
+  auto yedge = [&](int c, int j) {
+    return edge_fw(order, limiter, transverse, vvel(c, j), q(c, j - 2), q(c, j - 1), q(c, j),
+                   q(c, j + 1), nu);
+  };
+  real dsum = 0;
+  for (int k = tid; k < 3 * MX + 4; k += nt) {
+    if (k < MX + 2) {  // x-edge (MX, j): its P enters no updated cell; M enters (MX-1, j)
+      const int j = k - 1;
+      const real s = uvel(MX, j);
+      const EdgeFw<real> e = edge_fw(order, limiter, transverse, s, q(MX - 2, j), q(MX - 1, j),
+                                     q(MX, j), q(MX + 1, j), nu);
+      const real lF = lFf(MX, j);
+      real lM = 0;
+      if (transverse > 0)
+        lM = -hn * ((j + 1 <= MX ? pos(vvel(MX - 1, j + 1)) * lGf(MX - 1, j + 1) : real(0)) +
+                    (j >= 0 ? neg(vvel(MX - 1, j)) * lGf(MX - 1, j) : real(0)));
+      const EdgeAdj<real> o = edge_transpose(e, transverse, s, q(MX - 1, j), q(MX, j), lF,
+                                             real(0), lM);
+      add(MX - 2, j, o.a);
+      add(MX - 1, j, o.b);
+      add(MX, j, o.c);
+      add(MX + 1, j, o.d);
+      dsum += o.ds;
+      if (transverse > 0 && j >= 0 && j < MX) {  // its transverse increment's speed
+        const real Yl = yedge(MX - 1, j).P + yedge(MX - 1, j + 1).M;
+        const real Yr = yedge(MX, j).P + yedge(MX, j + 1).M;
+        dsum -= hn * (pos(s) * Yl + neg(s) * Yr) * lF;
+      }
+    } else {  // y-edge (c, j) of ghost column c = -1 or MX (no flux of its own updates a cell)
+      const bool right = k >= 2 * MX + 3;
+      const int j = k - (right ? 2 * MX + 3 : MX + 2);
+      const int c = right ? MX : -1;
+      const real s = vvel(c, j);
+      const EdgeFw<real> e = yedge(c, j);
+      // adjoint of Y(c, r): from x-edge (0, r)'s u+ (c = -1) or (MX, r)'s u- (c = MX)
+      auto lY = [&](int r) -> real {
+        if (r < 0 || r >= MX) return real(0);
+        return right ? -hn * neg(uvel(MX, r)) * lFf(MX, r) : -hn * pos(uvel(0, r)) * lFf(0, r);
+      };
+      const real lP = transverse > 0 ? lY(j) : real(0);
+      const real lM = transverse > 0 ? lY(j - 1) : real(0);
+      const EdgeAdj<real> o =
+          edge_transpose(e, transverse, s, q(c, j - 1), q(c, j), real(0), lP, lM);
+      add(c, j - 2, o.a);
+      add(c, j - 1, o.b);
+      add(c, j, o.c);
+      add(c, j + 1, o.d);
+      dsum += o.ds;
+    }
+  }
+  return dsum;
+}
+
 // Where the update transpose of a multirate substep also transposes its
 // patches' ghost fill (the level's Alg. 1, reversed: interpolation from the
 // coarse tiles into lamT, then copies and averages into the accumulators of
@@ -246,26 +507,28 @@ struct AdjGhosts {
 // ghost ring of the input tile's adjoint is transposed through the level's
 // ghost fill at once (g), and its interior is added to lam_out's (other
 // levels' and neighbours' transposes add there too).
-template <typename real, int MX, int NT>
-__global__ void __launch_bounds__(NT) adj_advance_kernel(DevForest<real> D, AdvArgs a,
+// (FP32 at mx = 32: two CTAs of 384 threads per SM, so a finest level's
+// patches run in one wave)
+template <typename real, int MX, int R, int NT, int NS>
+__global__ void __launch_bounds__(NT, sizeof(real) == 4 && NT >= 384 ? 2 : 1)
+    adj_advance_kernel(DevForest<real> D, AdvArgs a,
                                                          real* lam_in, real* lam_out,
                                                          double* dscale, double dfac, int p0,
                                                          int p1, const real* tiles, int tiles_p0,
                                                          int acc, AdjGhosts<real> g) {
   constexpr int S = MX + 4;
-  constexpr int NE = (MX + 1) * (MX + 2);
   constexpr int NV = MX + 3;
+  constexpr int NW = MX * MX / R;  // threads that walk a band of R rows; NS more take the side edges
+  static_assert(MX % R == 0 && NW + NS == NT && NW % 32 == 0 && NS % 32 == 0,
+                "bands of R rows and the side edges, whole warps");
   extern __shared__ __align__(16) unsigned char smem_raw[];
   real* Q = reinterpret_cast<real*>(smem_raw);
   real* LQ = Q + S * S;       // adjoint of the input tile
   real* LN = LQ + S * S;      // adjoint of the new interior (MX*MX)
-  real* LF = LN + MX * MX;    // adjoint of x-edge normal flux / final flux
-  real* LG = LF + NE;         // same for y-edges
-  real* YS = LG + NE;         // forward y-fluctuation into each cell column -1..MX, rows 0..MX-1
-  real* XS = YS + (MX + 2) * MX;  // forward x-fluctuation into cells, columns 0..MX-1, rows -1..MX
-  real* LY = XS + MX * (MX + 2);  // adjoint of Y
-  real* LX = LY + (MX + 2) * MX;  // adjoint of X
-  real* Sx = LX + MX * (MX + 2);
+  real* XMe = LN + MX * MX;   // forward M of x-edge (MX, j) at [j + 1]
+  real* YPm = XMe + MX + 2;   // forward P, M of y-edge (-1, j)
+  real* YMm = YPm + MX + 1;
+  real* Sx = YMm + MX + 1;
   real* Sy = Sx + NV;
   real* Tx = Sy + NV;
   real* Ty = Tx + NV;
@@ -276,12 +539,13 @@ __global__ void __launch_bounds__(NT) adj_advance_kernel(DevForest<real> D, AdvA
   const bool swirl = D.vel_kind == FC_VEL_SWIRL;
   const real cu = real(D.vel[0]), cv = real(D.vel[1]);
   const real nu = real(a.nu), hn = real(0.5 * a.nu), h = real(a.h);
-  if (threadIdx.x == 0 && swirl) {
-    const double t = a.t0_dev ? *a.t0_dev + a.t_off : a.t_half;  // graph replay: time on device
+  // the swirl coefficient, by the last thread while the first patch's data
+  // load (graph replay: the time is on the device); read after the barrier
+  if (threadIdx.x == NT - 1 && swirl) {
+    const double t = a.t0_dev ? *a.t0_dev + a.t_off : a.t_half;
     ucoef_s = cospi_ratio<real>(t, a.period) * real(a.sfac);
   }
-  __syncthreads();
-  const real ucoef = swirl ? ucoef_s : real(0);
+  real ucoef = real(0);
   // velocity-scale derivative: per-thread partial sums in the field's
   // precision (FP64 arithmetic is scarce on this GPU), FP64 from the block
   // reduction on
@@ -293,183 +557,77 @@ __global__ void __launch_bounds__(NT) adj_advance_kernel(DevForest<real> D, AdvA
                             : D.buf[D.cur[pm.level]] + (size_t)p * S * S;
     real* lin = lam_in + (size_t)p * S * S;
     if (acc) stage_neighbours(D.meta, D.nbr, p, st, threadIdx.x);
-    for (int k = threadIdx.x; k < S * S; k += NT) {
-      Q[k] = src[k];
-      LQ[k] = real(0);
+    // every load of a thread is issued before any is used
+    constexpr int NQ = (S * S + NT - 1) / NT, NL = (MX * MX + NT - 1) / NT;
+    real vq[NQ], vl[NL];
+#pragma unroll
+    for (int u = 0; u < NQ; ++u) {
+      const int k = (int)threadIdx.x + u * NT;
+      vq[u] = k < S * S ? src[k] : real(0);
     }
-    for (int k = threadIdx.x; k < MX * MX; k += NT) {
-      const int o = (k / MX + 2) * S + (k % MX) + 2;
-      LN[k] = lin[o];
-      if (acc) lin[o] = real(0);  // consumed: the buffer's next state starts from zero
+#pragma unroll
+    for (int u = 0; u < NL; ++u) {
+      const int k = (int)threadIdx.x + u * NT;
+      vl[u] = k < MX * MX ? lin[(k / MX + 2) * S + (k % MX) + 2] : real(0);
     }
-    if (swirl)
-      for (int k = threadIdx.x; k < NV; k += NT) {
-        const real xs = sinpi_r(real(pm.x * MX + k - 1) * h);
-        const real ys = sinpi_r(real(pm.y * MX + k - 1) * h);
-        Sx[k] = xs * xs;
-        Sy[k] = ys * ys;
-        Tx[k] = sinpi_r(real(2 * (pm.x * MX + k - 1) + 1) * h);
-        Ty[k] = sinpi_r(real(2 * (pm.y * MX + k - 1) + 1) * h);
+    if (swirl)  // the tables, one entry a thread
+      for (int k = threadIdx.x; k < 4 * NV; k += NT) {
+        const int tb = k / NV, c = k % NV;
+        const int z = (tb & 1 ? pm.y : pm.x) * MX + c - 1;
+        real v;
+        if (tb < 2) {
+          v = sinpi_r(real(z) * h);
+          v *= v;
+        } else {
+          v = sinpi_r(real(2 * z + 1) * h);
+        }
+        (tb == 0 ? Sx : tb == 1 ? Sy : tb == 2 ? Tx : Ty)[c] = v;
       }
+#pragma unroll
+    for (int u = 0; u < NQ; ++u) {
+      const int k = (int)threadIdx.x + u * NT;
+      if (k < S * S) {
+        Q[k] = vq[u];
+        LQ[k] = real(0);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < NL; ++u) {
+      const int k = (int)threadIdx.x + u * NT;
+      if (k < MX * MX) {
+        LN[k] = vl[u];
+        if (acc) lin[(k / MX + 2) * S + (k % MX) + 2] = real(0);  // consumed: next state from zero
+      }
+    }
     __syncthreads();
+    ucoef = swirl ? ucoef_s : real(0);
     auto q = [&](int i, int j) -> real { return Q[(j + 2) * S + (i + 2)]; };
     auto lq = [&](int i, int j) -> real* { return &LQ[(j + 2) * S + (i + 2)]; };
     auto uvel = [&](int i, int j) -> real { return swirl ? ucoef * Sx[i + 1] * Ty[j + 1] : cu; };
     auto vvel = [&](int i, int j) -> real { return swirl ? -ucoef * Sy[j + 1] * Tx[i + 1] : cv; };
-    auto ln = [&](int i, int j) -> real {
-      return (i >= 0 && i < MX && j >= 0 && j < MX) ? LN[j * MX + i] : real(0);
-    };
-    auto xe = [](int i, int j) { return (j + 1) * (MX + 1) + i; };
-    auto ye = [](int i, int j) { return j * (MX + 2) + (i + 1); };
-    // forward transverse inputs: Y(c, j) for c in [-1,MX], j in [0,MX); X(i, r) for i in [0,MX), r in [-1,MX]
-    for (int k = threadIdx.x; k < 2 * (MX + 2) * MX; k += NT) {
-      if (k < (MX + 2) * MX) {
-        const int c = k % (MX + 2) - 1, j = k / (MX + 2);
-        real Y = 0;
-        for (int r = j; r <= j + 1; ++r) {  // y-edges (c, j) [P into (c,j)] and (c, j+1) [M into (c,j)]
-          const real s = vvel(c, r);
-          const EdgeFw<real> e =
-              edge_fw(order, limiter, transverse, s, q(c, r - 2), q(c, r - 1), q(c, r), q(c, r + 1), nu);
-          Y += (r == j) ? e.P : e.M;
-        }
-        YS[k] = Y;
+    // the side quantities the band walk reads, then the walk (rows of
+    // bands) and the edges beside it (columns MX and -1)
+    for (int k = threadIdx.x; k < 2 * MX + 3; k += NT) {
+      if (k < MX + 2) {
+        const int j = k - 1;
+        XMe[k] = edge_fw(order, limiter, transverse, uvel(MX, j), q(MX - 2, j), q(MX - 1, j),
+                         q(MX, j), q(MX + 1, j), nu)
+                     .M;
       } else {
-        const int f = k - (MX + 2) * MX;
-        const int i = f % MX, r = f / MX - 1;
-        real X = 0;
-        for (int c = i; c <= i + 1; ++c) {
-          const real s = uvel(c, r);
-          const EdgeFw<real> e =
-              edge_fw(order, limiter, transverse, s, q(c - 2, r), q(c - 1, r), q(c, r), q(c + 1, r), nu);
-          X += (c == i) ? e.P : e.M;
-        }
-        XS[f] = X;
-      }
-    }
-    // transpose of the update: Q_new = Q - nu dF - nu dG
-    for (int k = threadIdx.x; k < 2 * NE; k += NT) {
-      if (k < NE) {
-        const int i = k % (MX + 1), j = k / (MX + 1) - 1;  // x-edge (i, j)
-        LF[k] = (j >= 0 && j < MX) ? nu * (ln(i, j) - ln(i - 1, j)) : real(0);
-      } else {
-        const int f = k - NE;
-        const int i = f % (MX + 2) - 1, j = f / (MX + 2);  // y-edge (i, j)
-        LG[f] = (i >= 0 && i < MX) ? nu * (ln(i, j) - ln(i, j - 1)) : real(0);
-      }
-    }
-    for (int k = threadIdx.x; k < MX * MX; k += NT) LQ[(k / MX + 2) * S + (k % MX) + 2] += LN[k];
-    __syncthreads();
-    // transpose of the transverse increments: F = Fn - nu/2 (u+ Y(i-1) + u- Y(i)), G likewise
-    if (transverse > 0) {
-      for (int k = threadIdx.x; k < 2 * (MX + 2) * MX; k += NT) {
-        if (k < (MX + 2) * MX) {  // adjoint of Y(c, j): used by x-edges (c+1, j) [u+] and (c, j) [u-]
-          const int c = k % (MX + 2) - 1, j = k / (MX + 2);
-          real l = 0;
-          if (c + 1 <= MX) {
-            const real s = uvel(c + 1, j);
-            l -= hn * (s > real(0) ? s : real(0)) * LF[xe(c + 1, j)];
-          }
-          if (c >= 0) {
-            const real s = uvel(c, j);
-            l -= hn * (s < real(0) ? s : real(0)) * LF[xe(c, j)];
-          }
-          LY[k] = l;
-        } else {  // adjoint of X(i, r): used by y-edges (i, r+1) [v+] and (i, r) [v-]
-          const int f = k - (MX + 2) * MX;
-          const int i = f % MX, r = f / MX - 1;
-          real l = 0;
-          if (r + 1 <= MX) {
-            const real s = vvel(i, r + 1);
-            l -= hn * (s > real(0) ? s : real(0)) * LG[ye(i, r + 1)];
-          }
-          if (r >= 0) {
-            const real s = vvel(i, r);
-            l -= hn * (s < real(0) ? s : real(0)) * LG[ye(i, r)];
-          }
-          LX[f] = l;
-        }
-      }
-      // speed derivative of the transverse coefficients (their own edges' speeds)
-      for (int k = threadIdx.x; k < 2 * MX * (MX + 1); k += NT) {
-        if (k < MX * (MX + 1)) {
-          const int i = k % (MX + 1), j = k / (MX + 1);
-          const real s = uvel(i, j);
-          const real yl = YS[j * (MX + 2) + i], yr = YS[j * (MX + 2) + i + 1];  // Y(i-1,j), Y(i,j)
-          dsum -= hn * ((s > real(0) ? s : real(0)) * yl + (s < real(0) ? s : real(0)) * yr) *
-                  LF[xe(i, j)];
-        } else {
-          const int f = k - MX * (MX + 1);
-          const int i = f % MX, j = f / MX;
-          const real s = vvel(i, j);
-          const real xb = XS[j * MX + i], xt = XS[(j + 1) * MX + i];  // X(i,j-1), X(i,j)
-          dsum -= hn * ((s > real(0) ? s : real(0)) * xb + (s < real(0) ? s : real(0)) * xt) *
-                  LG[ye(i, j)];
-        }
+        const int j = k - (MX + 2);
+        const EdgeFw<real> e = edge_fw(order, limiter, transverse, vvel(-1, j), q(-1, j - 2),
+                                       q(-1, j - 1), q(-1, j), q(-1, j + 1), nu);
+        YPm[j] = e.P;
+        YMm[j] = e.M;
       }
     }
     __syncthreads();
-    // transpose of every edge: x-edges (i, j), i in [0,MX], j in [-1,MX]
-    for (int k = threadIdx.x; k < 2 * NE; k += NT) {
-      const bool xdir = k < NE;
-      int i, j;
-      real s, lF, lP = 0, lM = 0;
-      if (xdir) {
-        i = k % (MX + 1);
-        j = k / (MX + 1) - 1;
-        s = uvel(i, j);
-        lF = LF[k];
-        if (transverse > 0) {
-          if (i < MX) lP = LX[(j + 1) * MX + i];        // P enters cell (i, j): X(i, j)
-          if (i > 0) lM = LX[(j + 1) * MX + i - 1];     // M enters cell (i-1, j): X(i-1, j)
-        }
-      } else {
-        const int f = k - NE;
-        i = f % (MX + 2) - 1;
-        j = f / (MX + 2);
-        s = vvel(i, j);
-        lF = LG[f];
-        if (transverse > 0) {
-          if (j < MX) lP = LY[j * (MX + 2) + i + 1];      // P enters (i, j): Y(i, j)
-          if (j > 0) lM = LY[(j - 1) * (MX + 2) + i + 1];  // M enters (i, j-1): Y(i, j-1)
-        }
-      }
-      // cells a (behind b), b, c, d (beyond c) along the edge normal
-      real qa, qb, qc, qd;
-      real *la, *lb, *lc, *ld;
-      if (xdir) {
-        qa = q(i - 2, j); qb = q(i - 1, j); qc = q(i, j); qd = q(i + 1, j);
-        la = lq(i - 2, j); lb = lq(i - 1, j); lc = lq(i, j); ld = lq(i + 1, j);
-      } else {
-        qa = q(i, j - 2); qb = q(i, j - 1); qc = q(i, j); qd = q(i, j + 1);
-        la = lq(i, j - 2); lb = lq(i, j - 1); lc = lq(i, j); ld = lq(i, j + 1);
-      }
-      const EdgeFw<real> e = edge_fw(order, limiter, transverse, s, qa, qb, qc, qd, nu);
-      const real sp = s > real(0) ? s : real(0), sm = s < real(0) ? s : real(0);
-      const real ip = s > real(0) ? real(1) : real(0), im = s < real(0) ? real(1) : real(0);
-      real lFt = lF, lW = 0, lWup = 0;
-      real ds = 0;
-      if (transverse > 0) {
-        lW += sp * lP + sm * lM;
-        ds += lP * ip * e.W + lM * im * e.W;
-        if (transverse > 1) lFt += -lP + lM;
-      }
-      atomicAdd(lb, sp * lF);
-      atomicAdd(lc, sm * lF);
-      ds += lF * (ip * qb + im * qc);
-      lW += e.c * e.dW * lFt;
-      lWup += e.c * e.dWup * lFt;
-      ds += lFt * e.dc * e.lim;
-      atomicAdd(lc, lW);
-      atomicAdd(lb, -lW);
-      if (e.up) {
-        atomicAdd(lb, lWup);
-        atomicAdd(la, -lWup);
-      } else {
-        atomicAdd(ld, lWup);
-        atomicAdd(lc, -lWup);
-      }
-      dsum += ds * s;
-    }
+    if (threadIdx.x < NW)
+      dsum += band_transpose<real, MX, R>(Q, LQ, LN, XMe, YPm, YMm, order, limiter, transverse, nu,
+                                          hn, uvel, vvel, threadIdx.x);
+    else
+      dsum += side_transpose<real, MX>(Q, LQ, LN, order, limiter, transverse, nu, hn, uvel, vvel,
+                                       threadIdx.x - NW, NS);
     __syncthreads();
     // transpose of the second wall-BC pass
     if (D.domain == FC_DOMAIN_WALLS) {
@@ -606,8 +764,7 @@ __global__ void adj_coarse_tiles_kernel(DevForest<real> D, const int* targets, i
 
 template <typename real, int MX>
 constexpr size_t adj_smem() {
-  return sizeof(real) * (size_t)(2 * (MX + 4) * (MX + 4) + MX * MX + 2 * (MX + 1) * (MX + 2) +
-                                 4 * (MX + 2) * MX + 4 * (MX + 3));
+  return sizeof(real) * (size_t)(2 * (MX + 4) * (MX + 4) + MX * MX + 3 * MX + 4 + 4 * (MX + 3));
 }
 
 inline int grid_for(int n) { return n < 1 ? 1 : (n < 65535 * 8 ? n : 65535 * 8); }
@@ -620,16 +777,16 @@ cudaError_t adj_advance_level(const DevForest<real>& D, int L, int p0, int p1, d
                               const double* t0_dev = nullptr, const real* tiles = nullptr,
                               int tiles_p0 = 0, int acc = 0,
                               AdjGhosts<real> g = AdjGhosts<real>{}) {
-  // a whole CTA per patch, 512 threads at mx = 32: two CTAs per SM hold a
-  // finest level's patches in one wave while the coarser levels' reversed
-  // substeps run beside it (1024 threads, one CTA per SM, measured slower
-  // once the levels overlapped; 256 too)
-  constexpr int NT = MX >= 16 ? 512 : 256;
+  // a whole CTA per patch whose warps walk bands of R rows (4 at mx = 32,
+  // 2 below) while more warps transpose the side edges
+  constexpr int R = MX == 32 ? 4 : 2;
+  constexpr int NS = (3 * MX + 4 + 31) / 32 * 32;  // a thread per side edge
+  constexpr int NT = MX * MX / R + NS;
   // set once per process; concurrent first calls both set it (idempotent)
   static std::atomic<bool> attr{false};
   constexpr size_t smem = adj_smem<real, MX>();
   if (!attr.load(std::memory_order_acquire)) {
-    cudaError_t e = cudaFuncSetAttribute(adj_advance_kernel<real, MX, NT>,
+    cudaError_t e = cudaFuncSetAttribute(adj_advance_kernel<real, MX, R, NT, NS>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     attr.store(true, std::memory_order_release);
@@ -643,8 +800,8 @@ cudaError_t adj_advance_level(const DevForest<real>& D, int L, int p0, int p1, d
   al.t_off = t + 0.5 * dt;  // with t0_dev: t is relative to the replayed step's start
   al.t0_dev = t0_dev;
   al.sfac = D.vel_kind == FC_VEL_SWIRL ? scale * sin(M_PI * al.h) / (M_PI * al.h) : 0.0;
-  adj_advance_kernel<real, MX, NT><<<p1 - p0, NT, smem, s>>>(D, al, lam_in, lam_out, dscale, dfac,
-                                                               p0, p1, tiles, tiles_p0, acc, g);
+  adj_advance_kernel<real, MX, R, NT, NS><<<p1 - p0, NT, smem, s>>>(
+      D, al, lam_in, lam_out, dscale, dfac, p0, p1, tiles, tiles_p0, acc, g);
   ++launch_counter();
   return cudaGetLastError();
 }
