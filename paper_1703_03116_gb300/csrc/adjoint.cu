@@ -725,38 +725,54 @@ __global__ void adj_copy_kernel(DevForest<real> D, real* lam) {
 // lam_new; finer ones, on level L, into lam) and of the time interpolation
 // of their interiors; their lamT tiles are cleared
 template <typename real, int MX>
-__global__ void adj_coarse_tiles_kernel(DevForest<real> D, const int* targets, int n, real* lam,
-                                        real* lam_old, real* lam_new, int tlevel, real alpha,
-                                        real* lamT) {
-  constexpr int S = MX + 4;
+__global__ void __launch_bounds__(256) adj_coarse_tiles_kernel(DevForest<real> D,
+                                                               const int* targets, int n,
+                                                               real* lam, real* lam_old,
+                                                               real* lam_new, int tlevel,
+                                                               real alpha, real* lamT) {
+  constexpr int S = MX + 4, NT = 256, NQ = (S * S + NT - 1) / NT;
   __shared__ NbrStage st;
+  __shared__ real L[S * S];  // the tile's adjoint, staged
   const bool walls = D.domain == FC_DOMAIN_WALLS;
+  const int tid = threadIdx.x;
   for (int t = blockIdx.x; t < n; t += gridDim.x) {
     const int p = targets[t];
-    stage_neighbours(D.meta, D.nbr, p, st, threadIdx.x);
+    stage_neighbours(D.meta, D.nbr, p, st, tid);
     const PatchMeta pm = D.meta[p];
     real* T = lamT + (size_t)p * S * S;
+    // the whole tile in (every load issued before any is used); it is left
+    // cleared for its next use (the interpolation stencils of the finer
+    // level read only the cells within two of the tile's edge, so most of
+    // it is zero and needs no store)
+    real v[NQ];
+#pragma unroll
+    for (int u = 0; u < NQ; ++u) {
+      const int k = tid + u * NT;
+      v[u] = k < S * S ? T[k] : real(0);
+    }
+#pragma unroll
+    for (int u = 0; u < NQ; ++u) {
+      const int k = tid + u * NT;
+      if (k < S * S) {
+        L[k] = v[u];
+        if (v[u] != real(0)) T[k] = real(0);
+      }
+    }
     __syncthreads();
     if (walls) {
-      adj_bc_patch<real, MX>(pm, T, threadIdx.x, blockDim.x);
+      adj_bc_patch<real, MX>(pm, L, tid, NT);
       __syncthreads();
     }
-    adj_copy_patch<real, MX>(st, pm, T, AdjTargets<real>{lam, lam, lam_old, lam_new}, tlevel,
-                             alpha, threadIdx.x, blockDim.x);
+    adj_copy_patch<real, MX>(st, pm, L, AdjTargets<real>{lam, lam, lam_old, lam_new}, tlevel,
+                             alpha, tid, NT);
     __syncthreads();
     const size_t base = (size_t)p * S * S;
-    // (the interpolation stencils of the finer level read only the cells
-    // within two of the tile's edge, so most of the tile's adjoint is zero:
-    // those cells add nothing and need no clearing)
-    for (int k = threadIdx.x; k < S * S; k += blockDim.x) {
-      const int i = k % S - 2, j = k / S - 2;
-      const real v = T[k];
-      if (v == real(0)) continue;
-      T[k] = real(0);
-      if (i >= 0 && i < MX && j >= 0 && j < MX) {  // other CTAs may add here too
-        atomicAdd(lam_old + base + k, (real(1) - alpha) * v);
-        if (alpha != real(0)) atomicAdd(lam_new + base + k, alpha * v);
-      }
+    for (int k = tid; k < MX * MX; k += NT) {  // other CTAs may add here too
+      const int o = (k / MX + kMbc) * S + k % MX + kMbc;
+      const real w = L[o];
+      if (w == real(0)) continue;
+      atomicAdd(lam_old + base + o, (real(1) - alpha) * w);
+      if (alpha != real(0)) atomicAdd(lam_new + base + o, alpha * w);
     }
     __syncthreads();
   }
