@@ -338,7 +338,7 @@ def roofline_fp64_alu(phase, mx, sm_mhz):
                            f"{sm_mhz:.0f} MHz"}
 
 
-def adjoint_cost(fc, torch, flush_buf, ncoarse: int = 25):
+def adjoint_cost(fc, torch, flush_buf, ncoarse: int = 25, variant: str = "auto"):
     """Forward vs gradient cost of the adjoint workload: the swirl forest
     frozen after its initial regrid, 25 coarse multirate steps (400
     finest-level substeps), FP32, sqrt(N) checkpoints; L = 1/2 |q_N -
@@ -351,7 +351,11 @@ def adjoint_cost(fc, torch, flush_buf, ncoarse: int = 25):
     desc = fc.make_desc(domain=fc.WALLS, mx=w.mx, lmin=w.lmin, lmax=w.lmax, dtype=fc.F32,
                         velocity=w.velocity)
     F = fc.initial_forest(desc, q0_fn([w]), tau_r=w.tau_refine, tau_c=w.tau_coarsen)
-    F.autotune()
+    if variant == "auto":
+        F.autotune()
+    else:  # one update kernel for every launch (see --variant)
+        name, _, warps = variant.partition(":")
+        F.set_advance_variant(["staged", "walk", "walk1", "band"].index(name), int(warps or 4))
     leaves = F.leaves()
     dev = flush_buf.device
     q0 = torch.tensor(q0_fn([w])(leaves), dtype=torch.float32, device=dev)
@@ -468,7 +472,7 @@ def run_ours(args):
         return
     if args.mode == "adjoint":  # the adjoint cost alone (a case sized for profiling)
         if rank == 0:
-            print(json.dumps({"variants": {"adjoint": adjoint_cost(fc, torch, flush_buf)}}),
+            print(json.dumps({"variants": {"adjoint": adjoint_cost(fc, torch, flush_buf, variant=args.variant)}}),
                   flush=True)
         if dist is not None:
             dist.destroy_process_group()
