@@ -434,12 +434,12 @@ fc_status fc_set_graphs(fc_forest* forest, int enable);
  * 2 (walk1: the walk with one tile buffer per warp, twice the warps per SM)
  * and 3 "band" (one CTA of `warps` warps per patch, each warp walking a band
  * of rows as the walk does: mx^2 / (32 warps) rows a band, at least one;
- * planar grids, with refluxing).  Where a variant lacks what the forest
- * needs (walk: refluxing; walk and band: the cubed sphere's capacity form)
- * the launch runs staged.
+ * with refluxing and the cubed sphere's capacity form).  Where the walk
+ * lacks what the forest needs (refluxing, the capacity form) the launch
+ * runs staged.
  *
- * Untuned launch sizes run walk from 1024 patches up, below that band with
- * 8 warps (staged on the cubed sphere).
+ * Untuned launch sizes run walk from 1024 patches up on planar grids, band
+ * with 8 warps otherwise.
  *
  * fc_autotune times every candidate (staged; band with 4 or 8 warps;
  * walk with 2, 4, 8 warps per

@@ -398,12 +398,11 @@ cudaError_t launch_advance(const DevForest<real>& D, int p0, int p1, const AdvAr
                            cudaStream_t s) {
   if (p1 <= p0) return cudaSuccess;
   // the walk variant has no capacity form and records no face fluxes:
-  // mapped grids run staged, refluxing staged or band
+  // mapped grids and refluxing run staged or band
   if ((a.variant == ADV_WALK || a.variant == ADV_WALK1) && !D.metric && !a.bflux)
     return launch_advance_walk(D, p0, p1, a, err, s);
-  // the band variant records face fluxes but has no capacity form either
-  if (a.variant == ADV_BAND && !D.metric && D.domain != FC_DOMAIN_SPHERE)
-    return launch_advance_band(D, p0, p1, a, err, s);
+  // the band variant records face fluxes and has the capacity form
+  if (a.variant == ADV_BAND) return launch_advance_band(D, p0, p1, a, err, s);
   return launch_advance_staged(D, p0, p1, a, err, s);
 }
 

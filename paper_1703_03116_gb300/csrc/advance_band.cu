@@ -19,8 +19,9 @@
 // column); and the fluctuations of the y-edges of ghost columns -1 and MX.
 // Then the bands run with no further CTA barrier.
 //
-// Planar grids only (the capacity form runs staged).  Refluxing: the final
-// fluxes through the patch's faces are recorded as the staged variant does.
+// Refluxing: the final fluxes through the patch's faces are recorded as the
+// staged variant does.
+#include <atomic>
 #include <cstdint>
 
 #include "ghost_gather.cuh"
@@ -48,10 +49,19 @@ constexpr int band_min_blocks() {
              : 1;
 }
 
-template <typename real, int MX, int R, bool SWIRL>
+// CAP: the capacity form of the cubed sphere (Sec. 5.3) -- the patch's FP64
+// metric block (kappa, phi_x, phi_y) arrives in dynamic shared memory by a
+// second bulk copy; edge speeds are the edge volume fluxes phi, the
+// correction's dt/h is dt (1/kappa_L + 1/kappa_R)/2, a fluctuation's
+// transverse increment is scaled by dt/2 over the area of the cell it
+// enters, and the update by dt over the cell's area.
+template <typename real, int MX, int R, bool SWIRL, bool CAP>
 __global__ void __launch_bounds__(band_threads<real, MX, R>(), band_min_blocks<real, MX, R>())
     advance_band_kernel(DevForest<real> D, int p0, int p1, AdvArgs a, int* err) {
   constexpr int S = MX + 4;
+  constexpr int MS = CAP ? metric_stride(S) : 0;
+  constexpr uint32_t mbytes = sizeof(double) * MS;
+  extern __shared__ __align__(16) double Ms[];  // CAP: kappa, phi_x, phi_y
   constexpr int NT = band_threads<real, MX, R>();
   constexpr int NW = MX * MX / R;  // threads that walk a band
   constexpr int NV = MX + 3;  // corner nodes -1..MX+1 of a row or column
@@ -82,7 +92,18 @@ __global__ void __launch_bounds__(band_threads<real, MX, R>(), band_min_blocks<r
   const real cu = real(D.vel[0]), cv = real(D.vel[1]);
   const real h = real(a.h);
   const Scheme<real> sc = make_scheme<real>(D.order, D.limiter, D.transverse, a.nu);
+  const real dt = real(a.dt), tdt = D.transverse > 0 ? real(0.5 * a.dt) : real(0);
   auto q = [&](int i, int j) -> real { return Q[(j + kMbc) * S + (i + kMbc)]; };
+  // capacity form: 1/kappa of cell (i, j), volume flux of x-edge (i, j) /
+  // y-edge (i, j), and an edge's correction dt/h from its two cells
+  auto ik = [&](int i, int j) -> real { return real(1) / real(Ms[(j + kMbc) * S + i + kMbc]); };
+  auto phx = [&](int i, int j) -> real {
+    return real(Ms[S * S + (j + kMbc) * (S + 1) + i + kMbc]);
+  };
+  auto phy = [&](int i, int j) -> real {
+    return real(Ms[S * S + S * (S + 1) + (j + kMbc) * S + i + kMbc]);
+  };
+  auto nu_e = [&](real ika, real ikb) -> real { return dt * (real(0.5) * (ika + ikb)); };
 
   uint32_t parity = 0;
   for (int p = p0 + blockIdx.x; p < p1; p += gridDim.x, parity ^= 1) {
@@ -91,8 +112,9 @@ __global__ void __launch_bounds__(band_threads<real, MX, R>(), band_min_blocks<r
     real* dst = D.buf[D.cur[pm.level] ^ 1] + (size_t)p * S * S;
     if (tid == 0) {
       fence_proxy_async();
-      mbar_expect_tx(&bar, bytes);
+      mbar_expect_tx(&bar, bytes + mbytes);
       bulk_load(Q, src, bytes, &bar);
+      if (CAP) bulk_load(Ms, D.metric + (size_t)p * MS, mbytes, &bar);
     }
     // the swirl coefficient, by the last thread (it gathers at most one
     // ghost); read after the barrier below
@@ -136,6 +158,11 @@ __global__ void __launch_bounds__(band_threads<real, MX, R>(), band_min_blocks<r
         wall_bc<real, MX>(pm, Q, tid, NT);
         __syncthreads();
       }
+      if (CAP && D.domain == FC_DOMAIN_SPHERE) {  // corners beyond a cube vertex
+        corner3_fill_k<real, MX>([&](int r) { return D.nbr[(size_t)p * 8 + r].kind; }, Q, tid,
+                                 NT);
+        __syncthreads();
+      }
     }
     if (a.keep) {  // the adjoint's replay keeps the ghost-filled input tile
       real* kp = static_cast<real*>(a.keep) + (size_t)(p - a.keep_p0) * S * S;
@@ -148,8 +175,9 @@ __global__ void __launch_bounds__(band_threads<real, MX, R>(), band_min_blocks<r
       real Fn, P, M;
       if (k < MX + 2) {
         const int r = k - 1;
-        const real s = SWIRL ? ucoef * Sx[MX + 1] * Ty[r + 1] : cu;
-        edge(s, q(MX - 2, r), q(MX - 1, r), q(MX, r), q(MX + 1, r), sc, Fn, P, M);
+        const real s = CAP ? phx(MX, r) : SWIRL ? ucoef * Sx[MX + 1] * Ty[r + 1] : cu;
+        const real nu = CAP ? nu_e(ik(MX - 1, r), ik(MX, r)) : sc.nu;
+        edge(s, q(MX - 2, r), q(MX - 1, r), q(MX, r), q(MX + 1, r), nu, sc, Fn, P, M);
         FeN[k] = Fn;
         FeU[k] = s;
         XMe[k] = M;
@@ -157,8 +185,9 @@ __global__ void __launch_bounds__(band_threads<real, MX, R>(), band_min_blocks<r
         const bool right = k >= 2 * MX + 3;
         const int r = k - (right ? 2 * MX + 3 : MX + 2);
         const int c = right ? MX : -1;
-        const real s = SWIRL ? -ucoef * Sy[r + 1] * Tx[c + 1] : cv;
-        edge(s, q(c, r - 2), q(c, r - 1), q(c, r), q(c, r + 1), sc, Fn, P, M);
+        const real s = CAP ? phy(c, r) : SWIRL ? -ucoef * Sy[r + 1] * Tx[c + 1] : cv;
+        const real nu = CAP ? nu_e(ik(c, r - 1), ik(c, r)) : sc.nu;
+        edge(s, q(c, r - 2), q(c, r - 1), q(c, r), q(c, r + 1), nu, sc, Fn, P, M);
         (right ? YPp : YPm)[r] = P;
         (right ? YMp : YMm)[r] = M;
       }
@@ -173,14 +202,20 @@ __global__ void __launch_bounds__(band_threads<real, MX, R>(), band_min_blocks<r
       const real Sx_i = SWIRL ? Sx[li + 1] : real(0), Tx_i = SWIRL ? Tx[li + 1] : real(0);
       real qa = q(li, r0 - 2), qb = q(li, r0 - 1), qc = q(li, r0), qd = 0;
       real X_prev = 0, Gn_cur = 0, v_cur = 0, YP_cur = 0, Gf_prev = 0, dF_prev = 0;
+      // capacity form: 1/kappa of this column's cells in rows r-1, r
+      real ik_prev = CAP ? ik(li, r0 - 2) : real(0), ik_cur = CAP ? ik(li, r0 - 1) : real(0);
 #pragma unroll(R <= 8 ? R + 2 : 2)
       for (int it = 0; it < R + 2; ++it) {
         const int r = r0 - 1 + it;
         if (it <= R) qd = q(li, r + 2);
+        const real ik_next = CAP && it <= R ? ik(li, r + 1) : real(0);
+        real ik_left = CAP ? __shfl_up_sync(FULL, ik_cur, 1, MX) : real(0);  // cell (li-1, r)
+        if (CAP && li == 0) ik_left = ik(-1, r);
         // x-edge (li, r): cells (li-1, r) | (li, r)
-        const real su = SWIRL ? ucoef * Sx_i * Ty[r + 1] : cu;
+        const real su = CAP ? phx(li, r) : SWIRL ? ucoef * Sx_i * Ty[r + 1] : cu;
         real Fn_r, XP_r, XM_r;
-        edge(su, q(li - 2, r), q(li - 1, r), qb, q(li + 1, r), sc, Fn_r, XP_r, XM_r);
+        edge(su, q(li - 2, r), q(li - 1, r), qb, q(li + 1, r),
+             CAP ? nu_e(ik_left, ik_cur) : sc.nu, sc, Fn_r, XP_r, XM_r);
         real XMn = __shfl_down_sync(FULL, XM_r, 1, MX);
         if (li == MX - 1) XMn = XMe[r + 1];
         const real X_r = XP_r + XMn;  // x-fluctuation into cell (li, r)
@@ -188,13 +223,17 @@ __global__ void __launch_bounds__(band_threads<real, MX, R>(), band_min_blocks<r
         // next band's
         real Gn_n = 0, YP_n = 0, YM_n = 0, v_n = 0;
         if (it <= R) {
-          v_n = SWIRL ? -ucoef * Sy[r + 2] * Tx_i : cv;
-          edge(v_n, qa, qb, qc, qd, sc, Gn_n, YP_n, YM_n);
+          v_n = CAP ? phy(li, r + 1) : SWIRL ? -ucoef * Sy[r + 2] * Tx_i : cv;
+          edge(v_n, qa, qb, qc, qd, CAP ? nu_e(ik_cur, ik_next) : sc.nu, sc, Gn_n, YP_n, YM_n);
         }
         // final flux at y-edge (li, r)
         real Gf_r = 0;
         if (it >= 1) {
-          Gf_r = Gn_cur - sc.tfac * (fmax(v_cur, real(0)) * X_prev + fmin(v_cur, real(0)) * X_r);
+          if (CAP)
+            Gf_r = Gn_cur - tdt * (fmax(v_cur, real(0)) * X_prev * ik_prev +
+                                   fmin(v_cur, real(0)) * X_r * ik_cur);
+          else
+            Gf_r = Gn_cur - sc.tfac * (fmax(v_cur, real(0)) * X_prev + fmin(v_cur, real(0)) * X_r);
           if (bf && r == 0) bf[2 * MX + li] = Gf_r;
           if (bf && r == MX) bf[3 * MX + li] = Gf_r;
         }
@@ -204,12 +243,18 @@ __global__ void __launch_bounds__(band_threads<real, MX, R>(), band_min_blocks<r
           const real Y_r = YP_cur + YM_n;  // y-fluctuation into cell (li, r)
           real Yl = __shfl_up_sync(FULL, Y_r, 1, MX);
           if (li == 0) Yl = YPm[r] + YMm[r + 1];
-          const real Ff = Fn_r - sc.tfac * (fmax(su, real(0)) * Yl + fmin(su, real(0)) * Y_r);
+          const real Ff =
+              CAP ? Fn_r - tdt * (fmax(su, real(0)) * Yl * ik_left + fmin(su, real(0)) * Y_r * ik_cur)
+                  : Fn_r - sc.tfac * (fmax(su, real(0)) * Yl + fmin(su, real(0)) * Y_r);
           real Fr = __shfl_down_sync(FULL, Ff, 1, MX);
           if (li == MX - 1) {
             const real ue = FeU[r + 1];
-            Fr = FeN[r + 1] -
-                 sc.tfac * (fmax(ue, real(0)) * Y_r + fmin(ue, real(0)) * (YPp[r] + YMp[r + 1]));
+            if (CAP)
+              Fr = FeN[r + 1] - tdt * (fmax(ue, real(0)) * Y_r * ik_cur +
+                                       fmin(ue, real(0)) * (YPp[r] + YMp[r + 1]) * ik(MX, r));
+            else
+              Fr = FeN[r + 1] - sc.tfac * (fmax(ue, real(0)) * Y_r +
+                                           fmin(ue, real(0)) * (YPp[r] + YMp[r + 1]));
           }
           dF_r = Fr - Ff;
           if (bf && li == 0) bf[r] = Ff;
@@ -217,7 +262,9 @@ __global__ void __launch_bounds__(band_threads<real, MX, R>(), band_min_blocks<r
         }
         // conservative update of cell (li, r-1)
         if (it >= 2)
-          dst[(r + 1) * S + (li + kMbc)] = qa - sc.nu * dF_prev - sc.nu * (Gf_r - Gf_prev);
+          dst[(r + 1) * S + (li + kMbc)] =
+              CAP ? qa - dt * ik_prev * (dF_prev + (Gf_r - Gf_prev))
+                  : qa - sc.nu * dF_prev - sc.nu * (Gf_r - Gf_prev);
         X_prev = X_r;
         Gn_cur = Gn_n;
         v_cur = v_n;
@@ -227,17 +274,29 @@ __global__ void __launch_bounds__(band_threads<real, MX, R>(), band_min_blocks<r
         qa = qb;
         qb = qc;
         qc = qd;
+        ik_prev = ik_cur;
+        ik_cur = ik_next;
       }
     }
     __syncthreads();  // the next patch's copy overwrites the tile
   }
 }
 
-template <typename real, int MX, int R, bool SWIRL>
+template <typename real, int MX, int R, bool SWIRL, bool CAP>
 cudaError_t band_launch_t(const DevForest<real>& D, int p0, int p1, const AdvArgs& a, int* err,
                           cudaStream_t s) {
-  advance_band_kernel<real, MX, R, SWIRL>
-      <<<p1 - p0, band_threads<real, MX, R>(), 0, s>>>(D, p0, p1, a, err);
+  constexpr size_t dyn = CAP ? sizeof(double) * (size_t)metric_stride(MX + 4) : 0;
+  auto kern = advance_band_kernel<real, MX, R, SWIRL, CAP>;
+  if (CAP) {  // set once per process; concurrent first calls both set it (idempotent)
+    static std::atomic<bool> attr_set{false};
+    if (!attr_set.load(std::memory_order_acquire)) {
+      cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)dyn);
+      if (e != cudaSuccess) return e;
+      attr_set.store(true, std::memory_order_release);
+    }
+  }
+  kern<<<p1 - p0, band_threads<real, MX, R>(), dyn, s>>>(D, p0, p1, a, err);
   ++launch_counter();
   return cudaGetLastError();
 }
@@ -245,8 +304,10 @@ cudaError_t band_launch_t(const DevForest<real>& D, int p0, int p1, const AdvArg
 template <typename real, int MX, int R>
 cudaError_t band_launch(const DevForest<real>& D, int p0, int p1, const AdvArgs& a, int* err,
                         cudaStream_t s) {
-  if (D.vel_kind == FC_VEL_SWIRL) return band_launch_t<real, MX, R, true>(D, p0, p1, a, err, s);
-  return band_launch_t<real, MX, R, false>(D, p0, p1, a, err, s);
+  if (D.metric) return band_launch_t<real, MX, R, false, true>(D, p0, p1, a, err, s);
+  if (D.vel_kind == FC_VEL_SWIRL)
+    return band_launch_t<real, MX, R, true, false>(D, p0, p1, a, err, s);
+  return band_launch_t<real, MX, R, false, false>(D, p0, p1, a, err, s);
 }
 
 }  // namespace

@@ -614,7 +614,7 @@ int size_bucket(int n) {
 
 // the patch-update configuration for a launch of n patches: the autotuned
 // choice when this size was tuned, else walk for launches that fill the GPU
-// and band (staged on the cubed sphere) for the others
+// (planar grids) and band for the others
 void choose_variant(const fc_forest* F, int n, AdvArgs* a) {
   const fc_forest::Tune& t = F->tune[size_bucket(n)];
   if (F->forced_variant >= 0) {
@@ -623,12 +623,9 @@ void choose_variant(const fc_forest* F, int n, AdvArgs* a) {
   } else if (t.tuned) {
     a->variant = t.variant;
     a->warps = t.warps;
-  } else if (n >= 1024) {
-    a->variant = ADV_WALK;
+  } else if (n >= 1024 && !F->d_metric && F->host.desc.domain != FC_DOMAIN_SPHERE) {
+    a->variant = ADV_WALK;  // (it has no capacity form)
     a->warps = F->esize == 4 ? 4 : 2;
-  } else if (F->d_metric || F->host.desc.domain == FC_DOMAIN_SPHERE) {
-    a->variant = ADV_STAGED;
-    a->warps = 4;
   } else {
     a->variant = ADV_BAND;
     a->warps = 8;
@@ -1171,9 +1168,9 @@ fc_status fc_autotune(fc_forest* F, int* report, void* stream) {
       const auto& c = cand[c2 % ncand];
       const int fused = c2 / ncand;
       if (fused && !F->fuse) continue;
-      // no capacity form in walk or band
-      if (c.variant != ADV_STAGED && (F->d_metric || H.desc.domain == FC_DOMAIN_SPHERE)) continue;
       const bool walk = c.variant == ADV_WALK || c.variant == ADV_WALK1;
+      // no capacity form in walk
+      if (walk && (F->d_metric || H.desc.domain == FC_DOMAIN_SPHERE)) continue;
       if (walk && F->bflux) continue;  // (it would run staged)
       // below two patches per SM the walk's warps mostly idle: staged has
       // measured about twice as fast there (graph-replayed substeps)

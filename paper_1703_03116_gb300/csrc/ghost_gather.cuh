@@ -280,12 +280,12 @@ __device__ __forceinline__ void wall_bc(const PatchMeta& pm, real* Q, int tid, i
 // stated reading of Sec. 2.4): each of the 2 x 2 corner ghosts takes the mean
 // of the two edge ghosts in its row and column next to the patch, once the
 // edge ghosts are final.  Threads tid, stride nt.
-template <typename real, int MX>
-__device__ __forceinline__ void corner3_fill(const NbrStage& st, real* Q, int tid, int nt) {
+template <typename real, int MX, class KindOf>
+__device__ __forceinline__ void corner3_fill_k(KindOf kind_of, real* Q, int tid, int nt) {
   constexpr int S = MX + 4;
   for (int k = tid; k < 16; k += nt) {
     const int r = 4 + (k >> 2);
-    if (st.e[r].kind != NB_CORNER3) continue;
+    if (kind_of(r) != NB_CORNER3) continue;
     // corners (-,-), (+,-), (-,+), (+,+)
     const int i = (r & 1) ? MX + (k & 1) : -2 + (k & 1);
     const int j = (r & 2) ? MX + ((k >> 1) & 1) : -2 + ((k >> 1) & 1);
@@ -293,6 +293,12 @@ __device__ __forceinline__ void corner3_fill(const NbrStage& st, real* Q, int ti
     Q[(j + kMbc) * S + i + kMbc] =
         real(0.5) * (Q[(jc + kMbc) * S + i + kMbc] + Q[(j + kMbc) * S + ic + kMbc]);
   }
+}
+
+// the same with the owner's staged entries
+template <typename real, int MX>
+__device__ __forceinline__ void corner3_fill(const NbrStage& st, real* Q, int tid, int nt) {
+  corner3_fill_k<real, MX>([&](int r) { return st.e[r].kind; }, Q, tid, nt);
 }
 
 // The whole of Alg. 1 for one patch into array Q (shared or global):

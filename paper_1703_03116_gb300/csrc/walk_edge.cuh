@@ -32,19 +32,26 @@ __device__ __forceinline__ Scheme<real> make_scheme(int order, int limiter, int 
 
 // one edge between cells qb (upwind-left/below) and qc, with the outer
 // neighbours qa (behind qb) and qd (beyond qc): normal flux and the two
-// fluctuations entering the right/upper (P) and left/lower (M) cell
+// fluctuations entering the right/upper (P) and left/lower (M) cell; nu the
+// edge's dt/h in the correction (capacity form: dt (1/kappa_b + 1/kappa_c)/2)
 template <typename real>
-__device__ __forceinline__ void edge(real s, real qa, real qb, real qc, real qd,
+__device__ __forceinline__ void edge(real s, real qa, real qb, real qc, real qd, real nu,
                                      const Scheme<real>& sc, real& Fn, real& P, real& M) {
   const real sp = fmax(s, real(0)), sm = fmin(s, real(0));
   const real W = qc - qb;
   const real Wup = s >= real(0) ? qb - qa : qd - qc;
   const real as = fabs(s);
-  const real cf = sc.order2 ? real(0.5) * as * (real(1) - sc.nu * as) : real(0);
+  const real cf = sc.order2 ? real(0.5) * as * (real(1) - nu * as) : real(0);
   const real Ft = cf * (sc.mc ? mc_limited(W, Wup) : W);
   Fn = sp * qb + sm * qc + Ft;
   P = sp * W - sc.t2 * Ft;
   M = sm * W + sc.t2 * Ft;
+}
+
+template <typename real>
+__device__ __forceinline__ void edge(real s, real qa, real qb, real qc, real qd,
+                                     const Scheme<real>& sc, real& Fn, real& P, real& M) {
+  edge(s, qa, qb, qc, qd, sc.nu, sc, Fn, P, M);
 }
 
 }  // namespace fc

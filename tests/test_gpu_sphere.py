@@ -68,16 +68,20 @@ def test_global_steps(dtype, tol):
 
 
 @pytest.mark.parametrize("mx,lmax", [(8, 4), (16, 4), (32, 3)])
-def test_multirate(mx, lmax):
+@pytest.mark.parametrize("variant,warps", [(-1, 4), (0, 4), (3, 4), (3, 16)])
+def test_multirate(mx, lmax, variant, warps):
+    """The capacity-form update of every kernel that has one: the default
+    (band, 8 warps), staged, band with 4 and 16 warps."""
     w = sphere(4, lmax=lmax, mx=mx)
     _, dtc = synth.time_step(w)
     for dtype, tol in ((fc.F64, F64_TOL), (fc.F32, 2e-4)):
         ref, gpu = pair(fc, w, dtype)
+        gpu.set_advance_variant(variant, warps)
         for s in range(2):
             ref.step_multirate(s * dtc, dtc)
             gpu.step_multirate(s * dtc, dtc)
         err = relerr(gpu.get_q(), ref.get_q())
-        print(f"sphere multirate mx={mx} dtype={dtype}: rel err {err:.2e}")
+        print(f"sphere multirate mx={mx} variant {variant}/{warps} dtype={dtype}: rel err {err:.2e}")
         assert err <= tol
         m_gpu, m_ref = gpu.mass()[0], ref.mass()[0]
         assert abs(m_gpu - m_ref) <= (1e-12 if dtype == fc.F64 else 1e-5) * abs(m_ref)

@@ -19,17 +19,20 @@ fc = pytest.importorskip("paper_1703_03116_gb300")
 
 
 @pytest.mark.parametrize("mx,lmin,lmax", [(8, 1, 3), (16, 1, 3), (32, 2, 3)])
-def test_multirate_matches_oracle(mx, lmin, lmax):
+@pytest.mark.parametrize("variant", [-1, 0])
+def test_multirate_matches_oracle(mx, lmin, lmax, variant):
+    """Default update (band) and staged under the refreshed fluxes."""
     w = synth.sphere_deform(seed=1, lmin=lmin, lmax=lmax, mx=mx)
     dtc = w.dt_lmin
     for dtype, tol in ((fc.F64, F64_TOL), (fc.F32, 2e-4)):
         ref, gpu = pair(fc, w, dtype)
+        gpu.set_advance_variant(variant, 8)
         for s in range(2):
             t = 0.2 + s * dtc
             ref.step_multirate(t, dtc)
             gpu.step_multirate(t, dtc)
         err = relerr(gpu.get_q(), ref.get_q())
-        print(f"deform multirate mx={mx} dtype {dtype}: rel err {err:.2e}")
+        print(f"deform multirate mx={mx} variant {variant} dtype {dtype}: rel err {err:.2e}")
         assert err <= tol
 
 

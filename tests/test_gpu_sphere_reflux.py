@@ -37,17 +37,21 @@ def _dt(w):
 
 @pytest.mark.parametrize("name", sorted(SPHERES))
 @pytest.mark.parametrize("mx", [8, 16, 32])
-def test_sphere_reflux_multirate_matches_oracle(name, mx):
+@pytest.mark.parametrize("variant", [-1, 0])
+def test_sphere_reflux_multirate_matches_oracle(name, mx, variant):
+    """Default update (band) and staged, both recording the face fluxes."""
     w = dataclasses.replace(SPHERES[name](mx), reflux=True)
     dtc = _dt(w)
     t0 = 0.2 if name == "deformational" else 0.0
     for dtype, tol in ((fc.F64, F64_TOL), (fc.F32, 2e-4)):
         ref, gpu = pair(fc, w, dtype)
+        gpu.set_advance_variant(variant, 8)
         for n in range(2):
             ref.step_multirate(t0 + n * dtc, dtc)
             gpu.step_multirate(t0 + n * dtc, dtc)
         err = relerr(gpu.get_q(), ref.get_q())
-        print(f"sphere reflux multirate {name} mx={mx} dtype {dtype}: rel err {err:.2e}")
+        print(f"sphere reflux multirate {name} mx={mx} variant {variant} dtype {dtype}: "
+              f"rel err {err:.2e}")
         assert err <= tol
 
 
