@@ -143,8 +143,24 @@ __global__ void __launch_bounds__(NW * 32) advance_walk_kernel(DevForest<real> D
     if (a.gather) {  // Alg. 1 for this segment's patch, into the tile's ghost ring
       stage_neighbours(D.meta, D.nbr, pc, nst[warp][seg], li);
       __syncwarp();
-      fill_patch_ghosts<real, MX>(D, nst[warp][seg], pm, a.tlevel, real(a.alpha), T, li, MX,
-                                  []() { __syncwarp(); });
+      // every ghost by its own rule in one pass (the phases of Alg. 1 write
+      // different ghosts, and an interpolation reads the coarse patch, not
+      // this tile), then the wall condition once: the bits of the phased fill
+      const NbrStage& ns = nst[warp][seg];
+      for (int k = li; k < num_ghosts<MX>(); k += MX) {
+        int i, j;
+        ghost_ij<MX>(k, i, j);
+        const NbrEntry& e = ns.e[region_of<MX>(i, j)];
+        real v;
+        if (copy_or_average_entry<real, MX>(D, e, pm, a.tlevel, real(a.alpha), i, j, v) ||
+            interpolate_entry<real, MX>(D, e, pm, a.tlevel, i, j, v))
+          T[(j + kMbc) * S + i + kMbc] = v;
+      }
+      __syncwarp();
+      if (D.domain == FC_DOMAIN_WALLS) {
+        wall_bc<real, MX>(pm, T, li, MX);
+        __syncwarp();
+      }
     }
     if (a.keep && valid) {  // the adjoint's replay keeps the ghost-filled input tile
       real* kp = static_cast<real*>(a.keep) + (size_t)(p - a.keep_p0) * TILE;

@@ -301,43 +301,4 @@ __device__ __forceinline__ void corner3_fill(const NbrStage& st, real* Q, int ti
   corner3_fill_k<real, MX>([&](int r) { return st.e[r].kind; }, Q, tid, nt);
 }
 
-// The whole of Alg. 1 for one patch into array Q (shared or global):
-// copy/average, boundary condition, interpolation, boundary condition.
-// `sync` orders the phases across the cooperating threads.  direct:
-// coarse neighbours on tlevel are read through the cells their fill would
-// leave (no fill of their tiles ran for this substep).
-template <typename real, int MX, class Sync>
-__device__ __forceinline__ void fill_patch_ghosts(const DevForest<real>& D, const NbrStage& st,
-                                                  const PatchMeta& pm, int tlevel, real alpha,
-                                                  real* Q, int tid, int nt, Sync sync,
-                                                  bool direct = false) {
-  constexpr int S = MX + 4;
-  for (int k = tid; k < num_ghosts<MX>(); k += nt) {
-    int i, j;
-    ghost_ij<MX>(k, i, j);
-    real v;
-    if (copy_or_average<real, MX>(D, st, pm, tlevel, alpha, i, j, v))
-      Q[(j + kMbc) * S + i + kMbc] = v;
-  }
-  sync();
-  const bool walls = D.domain == FC_DOMAIN_WALLS;
-  if (walls) wall_bc<real, MX>(pm, Q, tid, nt);
-  sync();
-  for (int k = tid; k < num_ghosts<MX>(); k += nt) {
-    int i, j;
-    ghost_ij<MX>(k, i, j);
-    real v;
-    if (direct ? interpolate_direct<real, MX>(D, st, pm, tlevel, alpha, i, j, v)
-               : interpolate<real, MX>(D, st, pm, tlevel, i, j, v))
-      Q[(j + kMbc) * S + i + kMbc] = v;
-  }
-  sync();
-  if (walls) wall_bc<real, MX>(pm, Q, tid, nt);
-  sync();
-  if (D.domain == FC_DOMAIN_SPHERE) {
-    corner3_fill<real, MX>(st, Q, tid, nt);
-    sync();
-  }
-}
-
 }  // namespace fc
