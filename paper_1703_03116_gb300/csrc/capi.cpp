@@ -755,24 +755,29 @@ fc_status advance_level_t(fc_forest* F, int L, double t, double dt, cudaStream_t
       // their coarse ghost regions filled); the update kernel then fills
       // each level-L patch's ghost ring in shared memory itself
       FillArgs A{F->d_lists + F->off_t[L], (int)H.list_t[L].size(), tlevel, alpha};
-      // the staged update computes the time-interpolated coarse cells it
-      // reads itself, so no fill launch sits before it on the level's chain
-      // (at alpha = 0 from the coarser level's older state, which its
-      // running update does not write; the adjoint's replay keeps the
-      // filled tiles: it runs the fill).  The walk keeps the fill: with one
-      // warp per patch, computing those cells in the update measured slower
-      // on the ensemble (5.5e10 vs 7.4e10 cell-updates/s)
+      // the staged and band updates compute the time-interpolated coarse
+      // cells they read themselves, so no fill launch sits before them on
+      // the level's chain (at alpha = 0 from the coarser level's older
+      // state, which its running update does not write); in the adjoint's
+      // replay they also store those cells in the kept time-interpolated
+      // tiles, all the reverse reads of them.  The walk keeps the fill: with
+      // one warp per patch, computing those cells in the update measured
+      // slower on the ensemble (5.5e10 vs 7.4e10 cell-updates/s)
       const bool direct = tlevel >= 0 && (a.variant == ADV_STAGED || a.variant == ADV_BAND) &&
-                          H.desc.domain != FC_DOMAIN_SPHERE && !F->keep_qT && !F->keep_tiles;
+                          H.desc.domain != FC_DOMAIN_SPHERE;
       if (direct) A.ntargets = 0;
       a.direct = direct ? 1 : 0;
+      if (direct && F->keep_qT) {
+        a.keep_t = F->keep_qT;
+        a.keep_t_p0 = H.lev_start[L - 1];
+      }
       // (inside a captured step this runs on the level's own stream, after
       // the waits above: see fc_forest::dag_levels)
       {
         Timed tm(F, 1, s, gb * A.ntargets);
         FC_CUDA(launch_fill_coarse(D, A, s));
       }
-      FC_CUDA(keep_coarse_tiles(F, L, s));
+      if (!direct) FC_CUDA(keep_coarse_tiles(F, L, s));
       a.gather = 1;
       a.tlevel = tlevel;
       a.alpha = alpha;

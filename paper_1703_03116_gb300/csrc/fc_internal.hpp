@@ -442,6 +442,11 @@ struct AdvArgs {
   // cells its interpolation reads as that fill would (no fill launch before
   // it on the critical path)
   int direct;
+  // direct with keep_t set (the adjoint's replay): the coarse cells the
+  // interpolation computes are also stored in the kept time-interpolated
+  // tiles, keep_t + (patch - keep_t_p0) tiles, as the fill would leave them
+  void* keep_t;
+  int keep_t_p0;
   // refluxing: each patch's final fluxes through its faces go to
   // bflux + ((p * 2 + bslot) * 4 + face) * mx (faces -x, +x, -y, +y; null: off)
   void* bflux;

@@ -174,12 +174,16 @@ __device__ __forceinline__ real coarse_ghost(const DevForest<real>& D, const Pat
 // interpolate_entry(), reading a coarse neighbour on tlevel through the
 // cells the coarse-neighbour fill would leave (above): the stencil's
 // interior cells are read together first, then any ghost of the coarse
-// patch (the same values in any order)
+// patch (the same values in any order).  keep_t non-null: each stencil cell
+// is also stored where that fill would have left it in the coarse patch's
+// tile at keep_t + (patch - keep_t_p0) tiles (the adjoint's replay keeps
+// what the interpolation read; several writers store the same value)
 template <typename real, int MX>
 __device__ __forceinline__ bool interpolate_direct_entry(const DevForest<real>& D,
                                                          const NbrEntry& e, const PatchMeta& pm,
                                                          int tlevel, real alpha, int i, int j,
-                                                         real& v) {
+                                                         real& v, real* keep_t = nullptr,
+                                                         int keep_t_p0 = 0) {
   if (e.kind != NB_COARSE) return false;
   if (e.lev != tlevel) return interpolate_entry<real, MX>(D, e, pm, tlevel, i, j, v);
   const int2 Ip = apply_a(e.a, pm.x * MX + i, pm.y * MX + j);
@@ -203,6 +207,15 @@ __device__ __forceinline__ bool interpolate_direct_entry(const DevForest<real>& 
 #pragma unroll
   for (int m = 0; m < 5; ++m)
     if (!in[m]) c[m] = coarse_ghost<real, MX>(D, cm, e.n0, tlevel, alpha, ci[m], cj[m]);
+  if (keep_t) {
+    constexpr int S = MX + 4;
+    real* K = keep_t + (size_t)(e.n0 - keep_t_p0) * S * S;
+#pragma unroll
+    for (int m = 0; m < 5; ++m) {  // at the cell's own place (an exterior one unclamped)
+      const int oi = ic + (m == 1 ? 1 : m == 2 ? -1 : 0), oj = jc + (m == 3 ? 1 : m == 4 ? -1 : 0);
+      K[(oj + kMbc) * S + oi + kMbc] = c[m];
+    }
+  }
   const real q0 = c[0];
   const real sx = minmod(c[1] - q0, q0 - c[2]);
   const real sy = minmod(c[3] - q0, q0 - c[4]);
@@ -225,12 +238,14 @@ __device__ __forceinline__ bool interpolate_direct(const DevForest<real>& D, con
 // exterior ghost is left to the wall condition).  entry_of(r) gives the
 // entry of face/corner region r (staged in shared memory, or read from the
 // table).  Threads tid, stride nt.  direct: coarse neighbours on tlevel are
-// read through the cells their fill would leave (interpolate_direct_entry).
+// read through the cells their fill would leave (interpolate_direct_entry;
+// keep_t, keep_t_p0: where it also stores them).
 template <typename real, int MX, class EntryOf>
 __device__ __forceinline__ void gather_ring(const DevForest<real>& D, EntryOf entry_of,
                                             const PatchMeta& pm, int tlevel, real alpha,
                                             bool direct, real* ring, bool* ring_w, int tid,
-                                            int nt) {
+                                            int nt, real* keep_t = nullptr,
+                                            int keep_t_p0 = 0) {
 #pragma unroll 1
   for (int k = tid; k < num_ghosts<MX>(); k += nt) {
     int i, j;
@@ -239,7 +254,8 @@ __device__ __forceinline__ void gather_ring(const DevForest<real>& D, EntryOf en
     real v;
     const bool w =
         copy_or_average_entry<real, MX>(D, e, pm, tlevel, alpha, i, j, v) ||
-        (direct ? interpolate_direct_entry<real, MX>(D, e, pm, tlevel, alpha, i, j, v)
+        (direct ? interpolate_direct_entry<real, MX>(D, e, pm, tlevel, alpha, i, j, v, keep_t,
+                                                     keep_t_p0)
                 : interpolate_entry<real, MX>(D, e, pm, tlevel, i, j, v));
     ring[k] = w ? v : real(0);
     ring_w[k] = w;
