@@ -341,7 +341,8 @@ def roofline_fp64_alu(phase, mx, sm_mhz):
 def adjoint_cost(fc, torch, flush_buf, ncoarse: int = 25, variant: str = "auto"):
     """Forward vs gradient cost of the adjoint workload: the swirl forest
     frozen after its initial regrid, 25 coarse multirate steps (400
-    finest-level substeps), FP32, sqrt(N) checkpoints; L = 1/2 |q_N -
+    finest-level substeps), FP32, every step recorded by the forward pass
+    (and, for comparison, sqrt(N) checkpoints); L = 1/2 |q_N -
     q_target|^2 (target: the run from the shifted disc), gradients with
     respect to q0 and the velocity scale.  Also the adjoint of one coarse step
     alone against the forward coarse step."""
@@ -373,17 +374,18 @@ def adjoint_cost(fc, torch, flush_buf, ncoarse: int = 25, variant: str = "auto")
         return e0.elapsed_time(e1)
 
     times = {}
-    for name in ("warm-up", "forward", "forward+backward"):
+    for name, tape in (("warm-up", "forward"), ("warm-up", "recompute"), ("forward", "auto"),
+                       ("forward+backward", "forward"), ("recompute", "recompute")):
         q = q0.clone().requires_grad_(name != "forward")
         s = torch.ones((), dtype=torch.float32, device=dev, requires_grad=name != "forward")
 
         def run():
-            qN = advect(q, s, F, 0.0, dtc, ncoarse, multirate=True)
+            qN = advect(q, s, F, 0.0, dtc, ncoarse, multirate=True, tape=tape)
             loss = 0.5 * ((qN - qt) ** 2).sum()
             if name != "forward":
                 loss.backward()
         times[name] = timed(run)
-    fwd, both = times["forward"], times["forward+backward"]
+    fwd, both, rec = times["forward"], times["forward+backward"], times["recompute"]
     # one coarse step: forward vs its adjoint (which replays the forward once)
     F.set_q(q0)
     lam = (q0 - qt).contiguous()
@@ -395,13 +397,23 @@ def adjoint_cost(fc, torch, flush_buf, ncoarse: int = 25, variant: str = "auto")
     torch.cuda.nvtx.range_push("adjoint_steps")  # lets a profiler select these steps
     t_adj = timed(lambda: [F.adjoint_step_multirate(0.0, dtc, lam, ds) for _ in range(K)]) / K
     torch.cuda.nvtx.range_pop()
+    # the same step recorded, then reversed from its tape
+    F.set_q(q0)
+    t_rec = timed(lambda: [F.step_multirate_record(k * dtc, dtc, k) for k in range(K)]) / K
+    t_rev = timed(lambda: [F.adjoint_step_multirate_taped(k * dtc, dtc, k, lam, ds)
+                           for k in range(K - 1, -1, -1)]) / K
     return {"workload": f"swirl forest frozen after the initial regrid ({len(leaves)} patches), "
-                        f"{ncoarse} coarse multirate steps = {ncoarse * 16} finest substeps, FP32, "
-                        "sqrt(N) checkpoints",
+                        f"{ncoarse} coarse multirate steps = {ncoarse * 16} finest substeps, FP32; "
+                        "gradient: every step recorded by the forward pass, reversed from its "
+                        "tape (gradient_recompute_ms: sqrt(N) checkpoints, each segment "
+                        "recomputed and recorded in the backward)",
             "forward_ms": fwd, "gradient_ms": both - fwd,
             "gradient_over_forward": (both - fwd) / fwd,
+            "gradient_recompute_ms": rec - fwd, "gradient_recompute_over_forward": (rec - fwd) / fwd,
             "coarse_step_forward_ms": t_fwd, "coarse_step_adjoint_ms": t_adj,
             "adjoint_step_over_forward_step": t_adj / t_fwd,
+            "coarse_step_recorded_ms": t_rec, "coarse_step_reverse_from_tape_ms": t_rev,
+            "reverse_from_tape_over_forward_step": t_rev / t_fwd,
             "forward_cell_updates_per_s": updates / (fwd * 1e-3)}
 
 

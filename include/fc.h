@@ -241,7 +241,9 @@ fc_status fc_tag_regrid(fc_forest* forest, double tau_refine, double tau_coarsen
 fc_status fc_tag(fc_forest* forest, double* delta_host, void* stream);
 
 /* Velocity scale sigma: every edge speed is multiplied by sigma (default 1).
- * It is the scalar parameter of the adjoint's velocity derivative. */
+ * It is the scalar parameter of the adjoint's velocity derivative.  A new
+ * value drops the captured steps and tapes (their kernels carry the scale)
+ * and synchronizes the device; setting the current value changes nothing. */
 fc_status fc_set_velocity_scale(fc_forest* forest, double scale);
 
 /* Adjoint of one global time step (the transposes of Alg. 1 and of the
@@ -312,6 +314,34 @@ fc_status fc_adjoint_advance(fc_forest* forest, int level, double t, double dt, 
  * (synchronous). */
 fc_status fc_adjoint_step_multirate(fc_forest* forest, double t, double dt_coarse, void* lam,
                                     double* dscale, void* stream);
+
+/* The same adjoint in two halves, for a caller that steps forward again
+ * anyway (a checkpointed gradient recomputing a segment of steps):
+ * fc_step_multirate_record is fc_step_multirate (the same kernels, the same
+ * result bits) that also keeps in tape `slot` what the reverse of the step
+ * reads -- each level substep's ghost-filled input tiles and the
+ * time-interpolated coarse cells its interpolation used -- and
+ * fc_adjoint_step_multirate_taped is the reverse alone, from that tape,
+ * with lam and dscale as in fc_adjoint_step_multirate; it neither reads nor
+ * changes the forest's state, so a segment recorded forward is reversed in
+ * any order of slots.  t and dt_coarse of the reverse are those the step
+ * was recorded with (FC_ERR_STATE when the slot holds no step of that
+ * length, or was recorded before the layout or the captured steps last
+ * changed: a regrid, fc_set_advance_variant, fc_set_limits, ...).
+ *   slot  0 <= slot < FC_MAX_TAPE_SLOTS (FC_ERR_INVALID_ARG otherwise).
+ * Device memory per slot: the kept tiles of fc_adjoint_step_multirate
+ * (without its copy of the start state), held until fc_tape_release or the
+ * forest's destruction.  Square domains only, no refluxing (as
+ * fc_adjoint_step_multirate).  Work runs on `stream`: the record is
+ * asynchronous, as fc_step_multirate (a device error shows at the next call
+ * that reads the error word); the reverse ends by reading the device error
+ * word (synchronous). */
+#define FC_MAX_TAPE_SLOTS 64
+fc_status fc_step_multirate_record(fc_forest* forest, double t, double dt_coarse, int slot,
+                                   void* stream);
+fc_status fc_adjoint_step_multirate_taped(fc_forest* forest, double t, double dt_coarse, int slot,
+                                          void* lam, double* dscale, void* stream);
+fc_status fc_tape_release(fc_forest* forest);
 
 /* Total mass per forest, sum over leaves of h^2 sum(q) (on the sphere
  * sum(kappa q)), accumulated in FP64

@@ -80,6 +80,11 @@ SIGNATURES = {
                                               _vp]),
     "fc_adjoint_step_multirate": (ctypes.c_int, [_vp, ctypes.c_double, ctypes.c_double, _vp,
                                                  _vp, _vp]),
+    "fc_step_multirate_record": (ctypes.c_int, [_vp, ctypes.c_double, ctypes.c_double,
+                                                ctypes.c_int, _vp]),
+    "fc_adjoint_step_multirate_taped": (ctypes.c_int, [_vp, ctypes.c_double, ctypes.c_double,
+                                                       ctypes.c_int, _vp, _vp, _vp]),
+    "fc_tape_release": (ctypes.c_int, [_vp]),
     "fc_adjoint_advance": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_double, ctypes.c_double,
                                           _vp, _vp, _vp, _vp]),
     "fc_forest_info": (ctypes.c_int, [_vp, _vp]),

@@ -232,12 +232,28 @@ struct fc_forest {
   double* d_ds = nullptr;                 // multirate adjoint: the step's dscale (graph output)
   void* msnap = nullptr;                  // multirate adjoint: the start state, then the filled
   size_t msnap_bytes = 0;                 // tiles of every substep
+  // an adjoint coarse step (mode 0: replay and reverse), a recorded
+  // forward coarse step (1: fc_step_multirate_record into tape `slot`) or
+  // the reverse of a recorded one (2: fc_adjoint_step_multirate_taped)
   struct AdjGraph {
     cudaGraphExec_t exec = nullptr;
     double dt = 0.0;
     int cur[kMaxLevel + 1] = {0};
+    int cur_after[kMaxLevel + 1] = {0};  // mode 1: the buffer parities it leaves
+    int mode = 0, slot = -1;
     uint64_t kernels = 0;
   };
+  // tapes of recorded forward coarse steps: per slot the kept tiles of every
+  // substep (the pool layout of the adjoint step without its start state),
+  // the step's length and the buffer parities it started from
+  struct Tape {
+    void* pool = nullptr;
+    size_t bytes = 0;
+    bool valid = false;
+    double dt = 0.0;
+    int cur0[kMaxLevel + 1] = {0};  // the buffer parities the step started from
+  };
+  std::vector<Tape> tapes;
   std::vector<AdjGraph> adj_graphs;       // captured adjoint coarse steps, valid for one layout
   cudaStream_t cap_stream = nullptr;
   double* d_t0 = nullptr;  // start time of the replayed coarse step
@@ -333,6 +349,7 @@ void destroy_graphs(fc_forest* F) {
   F->adj_graphs.clear();
   for (auto& x : F->stale) cudaGraphExecDestroy(x);
   F->stale.clear();
+  for (auto& t : F->tapes) t.valid = false;  // recorded with the graphs' launches
 }
 
 // after a regrid: the captured steps are stale; untimed ones are kept for
@@ -388,6 +405,8 @@ void free_device(fc_forest* F) {
   dfree(F->d_ds);
   dfree(F->msnap);
   F->msnap_bytes = 0;
+  for (auto& t : F->tapes) dfree(t.pool);
+  F->tapes.clear();
   dfree(F->d_metric);
   dfree(F->d_corner);
   dfree(F->d_halo);
@@ -984,6 +1003,7 @@ fc_status fc_forest_info(const fc_forest* F, fc_info* out) {
   for (void* b : F->madj) bytes += b ? store : 0;
   if (F->mio) bytes += n * H.desc.mx * H.desc.mx * F->esize;
   bytes += F->msnap_bytes;
+  for (const auto& t : F->tapes) bytes += t.bytes;
   out->device_bytes = (int64_t)bytes;
   out->graphs = (int)(F->graphs.size() + F->adj_graphs.size());
   int tuned = 0;
@@ -1261,6 +1281,7 @@ fc_status fc_autotune(fc_forest* F, int* report, void* stream) {
 
 fc_status fc_set_velocity_scale(fc_forest* F, double scale) {
   if (!F || !(scale == scale)) return fail(FC_ERR_INVALID_ARG, "bad velocity scale");
+  if (scale == F->vel_scale) return FC_OK;  // the captured steps and tapes stay valid
   F->vel_scale = scale;
   destroy_graphs(F);
   FC_CUDA(cudaDeviceSynchronize());  // no launch may still read the old metrics
@@ -1316,9 +1337,14 @@ static fc_status adjoint_step_t(fc_forest* F, double t, double dt, void* lam, do
 // parity) as a CUDA graph and replayed; the step's start time, lam and
 // dscale pass through device buffers of the forest.  The forest is left at
 // the step's start state.
+//
+// mode 1 captures the replay alone, as a recorded forward step: it keeps the
+// same tiles in tape `slot` (no start state saved) and leaves the forest at
+// the step's end state; mode 2 captures the reverse alone, from that tape.
 template <typename real>
 static fc_status capture_adjoint_multirate(fc_forest* F, double dtc, cudaStream_t cs,
-                                           fc_forest::AdjGraph* out) {
+                                           fc_forest::AdjGraph* out, int mode = 0,
+                                           int slot = -1) {
   const HostForest& H = F->host;
   const int lmin = H.desc.lmin, lmax = H.desc.lmax;
   const size_t S2 = (size_t)(H.desc.mx + 2 * kMbc) * (H.desc.mx + 2 * kMbc);
@@ -1355,7 +1381,7 @@ static fc_status capture_adjoint_multirate(fc_forest* F, double dtc, cudaStream_
       FC_CUDA(cudaEventCreateWithFlags(&F->ev_rev[k], cudaEventDisableTiming));
   }
   const size_t store = cells * sizeof(real);
-  size_t need = 2 * store;  // the start state: both stores
+  size_t need = mode == 0 ? 2 * store : 0;  // the start state: both stores
   for (auto& u : subs) {
     u.offq = need;
     need += (size_t)(H.lev_start[u.L + 1] - H.lev_start[u.L]) * tile;
@@ -1370,14 +1396,24 @@ static fc_status capture_adjoint_multirate(fc_forest* F, double dtc, cudaStream_
                      cudaSuccess)
     return fail(FC_ERR_OOM, "adjoint buffer allocation failed");
   if (!F->d_ds) FC_CUDA(dmalloc(&F->d_ds, 1));
-  if (need > F->msnap_bytes) {
+  fc_forest::Tape* tape = mode != 0 ? &F->tapes[slot] : nullptr;
+  if (mode == 0 && need > F->msnap_bytes) {
     dfree(F->msnap);
     F->msnap_bytes = 0;
     if (dmalloc_bytes(&F->msnap, need) != cudaSuccess)
       return fail(FC_ERR_OOM, "adjoint state allocation failed");
     F->msnap_bytes = need;
   }
-  char* pool = static_cast<char*>(F->msnap);
+  if (mode == 1 && need > tape->bytes) {
+    dfree(tape->pool);
+    tape->bytes = 0;
+    if (dmalloc_bytes(&tape->pool, need) != cudaSuccess)
+      return fail(FC_ERR_OOM, "tape allocation failed");
+    tape->bytes = need;
+  }
+  if (mode == 2 && need > tape->bytes)
+    return fail(FC_ERR_STATE, "the tape does not hold this layout's step");
+  char* pool = static_cast<char*>(mode == 0 ? F->msnap : tape->pool);
   real* LQ = static_cast<real*>(F->madj[0]);
   real* LO = static_cast<real*>(F->madj[1]);
   real* LT = static_cast<real*>(F->madj[2]);
@@ -1397,37 +1433,49 @@ static fc_status capture_adjoint_multirate(fc_forest* F, double dtc, cudaStream_
     auto cp = [&](void* dst, const void* src, size_t n) {
       if (e == cudaSuccess && n > 0) e = cudaMemcpyAsync(dst, src, n, cudaMemcpyDeviceToDevice, cs);
     };
-    auto tiles = [&](void* base, int p) { return static_cast<char*>(base) + (size_t)p * tile; };
-    cp(pool, F->buf[0], store);
-    cp(pool + store, F->buf[1], store);
-    // forward replay through the forward's own level substeps (fused gather,
-    // fills forked where their inputs are final), keeping what the reverse
-    // reads: each update's ghost-filled input tiles and the coarse tiles
-    reset_times(F);
-    F->dag = true;
-    F->dag_levels = F->fuse;  // each level on its own stream, as in a captured step
-    F->rel_time = true;
-    for (int l = 0; l <= kMaxLevel; ++l) {
-      F->pre_ok[l] = F->post_ok[l] = false;
-      F->lev_forked[l] = false;
+    if (mode == 0) {
+      cp(pool, F->buf[0], store);
+      cp(pool + store, F->buf[1], store);
     }
-    if (e == cudaSuccess) e = cudaEventRecord(F->ev_start, cs);
-    for (auto& u : subs) {
-      std::copy(F->cur, F->cur + kMaxLevel + 1, u.cur);
-      F->keep_tiles = pool + u.offq;
-      F->keep_qT = u.L > lmin ? pool + u.offt : nullptr;
-      if (e == cudaSuccess && replay_st == FC_OK) replay_st = advance_level(F, u.L, u.t, u.dt, cs);
+    if (mode == 2) {  // the parities the recorded step saw: each held level turns over
+      int c[kMaxLevel + 1];
+      std::copy(F->cur, F->cur + kMaxLevel + 1, c);
+      for (auto& u : subs) {
+        std::copy(c, c + kMaxLevel + 1, u.cur);
+        if (H.lev_start[u.L + 1] > H.lev_start[u.L]) c[u.L] ^= 1;
+      }
     }
-    for (int l = 0; l <= kMaxLevel; ++l)  // the level streams rejoin before the reverse sweep
-      if (F->lev_forked[l]) {
-        if (e == cudaSuccess) e = cudaEventRecord(F->ev_fill[l], F->lev_stream[l]);
-        if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, F->ev_fill[l], 0);
+    if (mode != 2) {
+      // forward replay through the forward's own level substeps (fused gather,
+      // fills forked where their inputs are final), keeping what the reverse
+      // reads: each update's ghost-filled input tiles and the coarse tiles
+      reset_times(F);
+      F->dag = true;
+      F->dag_levels = F->fuse;  // each level on its own stream, as in a captured step
+      F->rel_time = true;
+      for (int l = 0; l <= kMaxLevel; ++l) {
+        F->pre_ok[l] = F->post_ok[l] = false;
         F->lev_forked[l] = false;
       }
-    F->dag = false;
-    F->dag_levels = false;
-    F->rel_time = false;
-    F->keep_tiles = F->keep_qT = nullptr;
+      if (e == cudaSuccess) e = cudaEventRecord(F->ev_start, cs);
+      for (auto& u : subs) {
+        std::copy(F->cur, F->cur + kMaxLevel + 1, u.cur);
+        F->keep_tiles = pool + u.offq;
+        F->keep_qT = u.L > lmin ? pool + u.offt : nullptr;
+        if (e == cudaSuccess && replay_st == FC_OK) replay_st = advance_level(F, u.L, u.t, u.dt, cs);
+      }
+      for (int l = 0; l <= kMaxLevel; ++l)  // the level streams rejoin before the reverse sweep
+        if (F->lev_forked[l]) {
+          if (e == cudaSuccess) e = cudaEventRecord(F->ev_fill[l], F->lev_stream[l]);
+          if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, F->ev_fill[l], 0);
+          F->lev_forked[l] = false;
+        }
+      F->dag = false;
+      F->dag_levels = false;
+      F->rel_time = false;
+      F->keep_tiles = F->keep_qT = nullptr;
+    }
+    if (mode == 1) return e;  // a recorded forward step: the state advanced
     if (e == cudaSuccess) e = cudaMemsetAsync(LQ, 0, cells * sizeof(real), cs);
     if (e == cudaSuccess) e = cudaMemsetAsync(LO, 0, cells * sizeof(real), cs);
     if (e == cudaSuccess) e = cudaMemsetAsync(LT, 0, cells * sizeof(real), cs);
@@ -1508,8 +1556,10 @@ static fc_status capture_adjoint_multirate(fc_forest* F, double dtc, cudaStream_
     // each level's adjoint of the step's start state is in buf[par[l]]
     for (int l = 0; l <= kMaxLevel; ++l) Lv.cur[l] = par[l];
     if (e == cudaSuccess) e = launch_pack(Lv, F->d_api_to_dev, static_cast<real*>(F->mio), 0, cs);
-    cp(F->buf[0], pool, store);
-    cp(F->buf[1], pool + store, store);
+    if (mode == 0) {
+      cp(F->buf[0], pool, store);
+      cp(F->buf[1], pool + store, store);
+    }
     return e;
   };
   const cudaError_t eb = body();
@@ -1517,6 +1567,7 @@ static fc_status capture_adjoint_multirate(fc_forest* F, double dtc, cudaStream_
   const cudaError_t ee = cudaStreamEndCapture(cs, &graph);
   out->kernels = launch_counter() - launches_before;  // counted when replayed
   launch_counter() = launches_before;
+  std::copy(F->cur, F->cur + kMaxLevel + 1, out->cur_after);
   std::copy(cur0, cur0 + kMaxLevel + 1, F->cur);
   F->timing = timing;
   reset_times(F);
@@ -1532,6 +1583,8 @@ static fc_status capture_adjoint_multirate(fc_forest* F, double dtc, cudaStream_
   cudaGraphDestroy(graph);
   if (ei != cudaSuccess) return cuda_fail(ei, "cudaGraphInstantiate");
   out->dt = dtc;
+  out->mode = mode;
+  out->slot = slot;
   std::copy(cur0, cur0 + kMaxLevel + 1, out->cur);
   return FC_OK;
 }
@@ -1542,12 +1595,12 @@ static fc_status adjoint_multirate_t(fc_forest* F, double t0, double dtc, void* 
   AllocStream alloc_on(s);  // buffers first allocated here are ordered before the replay on s
   fc_forest::AdjGraph* g = nullptr;
   for (auto& c : F->adj_graphs)
-    if (c.dt == dtc && std::equal(c.cur, c.cur + kMaxLevel + 1, F->cur)) g = &c;
+    if (c.mode == 0 && c.dt == dtc && std::equal(c.cur, c.cur + kMaxLevel + 1, F->cur)) g = &c;
   if (!g) {
     if (!F->cap_stream)
       FC_CUDA(cudaStreamCreateWithFlags(&F->cap_stream, cudaStreamNonBlocking));
     fc_forest::AdjGraph ng;
-    fc_status st = capture_adjoint_multirate<real>(F, dtc, F->cap_stream, &ng);
+    fc_status st = capture_adjoint_multirate<real>(F, dtc, F->cap_stream, &ng, 0, -1);
     if (st != FC_OK) return st;
     F->adj_graphs.push_back(ng);
     g = &F->adj_graphs.back();
@@ -1560,6 +1613,84 @@ static fc_status adjoint_multirate_t(fc_forest* F, double t0, double dtc, void* 
   FC_CUDA(cudaMemcpyAsync(lam, F->mio, nbytes, cudaMemcpyDeviceToDevice, s));
   FC_CUDA(launch_add_double(dscale, F->d_ds, s));
   reset_times(F);  // the state is the step's start state again
+  return FC_OK;
+}
+
+// the graph of `mode` (1: record, 2: reverse) for tape `slot` at this step
+// length and buffer parity, captured on first use
+template <typename real>
+static fc_status tape_graph(fc_forest* F, double dtc, int mode, int slot,
+                            fc_forest::AdjGraph** out) {
+  fc_forest::AdjGraph* g = nullptr;
+  for (auto& c : F->adj_graphs)
+    if (c.mode == mode && c.slot == slot && c.dt == dtc &&
+        std::equal(c.cur, c.cur + kMaxLevel + 1, F->cur))
+      g = &c;
+  if (!g) {
+    if (!F->cap_stream)
+      FC_CUDA(cudaStreamCreateWithFlags(&F->cap_stream, cudaStreamNonBlocking));
+    fc_forest::AdjGraph ng;
+    const fc_status st = capture_adjoint_multirate<real>(F, dtc, F->cap_stream, &ng, mode, slot);
+    if (st != FC_OK) return st;
+    F->adj_graphs.push_back(ng);
+    g = &F->adj_graphs.back();
+  }
+  *out = g;
+  return FC_OK;
+}
+
+// a coarse multirate step that also keeps, in tape `slot`, what the reverse
+// of the step reads
+template <typename real>
+static fc_status record_multirate_t(fc_forest* F, double t0, double dtc, int slot,
+                                    cudaStream_t s) {
+  AllocStream alloc_on(s);  // the tape's memory is ordered before the step on s
+  if ((int)F->tapes.size() <= slot) F->tapes.resize(slot + 1);
+  fc_forest::Tape& tp = F->tapes[slot];
+  tp.valid = false;
+  fc_forest::AdjGraph* g = nullptr;
+  const fc_status st = tape_graph<real>(F, dtc, 1, slot, &g);
+  if (st != FC_OK) return st;
+  std::copy(F->cur, F->cur + kMaxLevel + 1, tp.cur0);
+  FC_CUDA(launch_set_time(F->d_t0, t0, s));
+  FC_CUDA(cudaGraphLaunch(g->exec, s));
+  launch_counter() += g->kernels;
+  std::copy(g->cur_after, g->cur_after + kMaxLevel + 1, F->cur);
+  const int lmin = F->host.desc.lmin, lmax = F->host.desc.lmax;
+  for (int L = lmin; L <= lmax; ++L) {  // as a coarse step leaves them
+    const double dtl = std::ldexp(dtc, -(L - lmin));
+    F->has_old[L] = true;
+    F->dt_last[L] = dtl;
+    F->t_start[L] = t0 + dtc - dtl;
+  }
+  tp.valid = true;
+  tp.dt = dtc;
+  return FC_OK;
+}
+
+// the adjoint of the step recorded in tape `slot` (its reverse alone)
+template <typename real>
+static fc_status adjoint_taped_t(fc_forest* F, double t0, double dtc, int slot, void* lam,
+                                 double* dscale, cudaStream_t s) {
+  AllocStream alloc_on(s);
+  if (slot >= (int)F->tapes.size() || !F->tapes[slot].valid || F->tapes[slot].dt != dtc)
+    return fail(FC_ERR_STATE,
+                "no step of this length recorded in the slot since the layout or the "
+                "captured steps last changed");
+  int cur_now[kMaxLevel + 1];
+  std::copy(F->cur, F->cur + kMaxLevel + 1, cur_now);
+  std::copy(F->tapes[slot].cur0, F->tapes[slot].cur0 + kMaxLevel + 1, F->cur);
+  fc_forest::AdjGraph* g = nullptr;
+  const fc_status st = tape_graph<real>(F, dtc, 2, slot, &g);
+  std::copy(cur_now, cur_now + kMaxLevel + 1, F->cur);
+  if (st != FC_OK) return st;
+  const size_t nbytes = (size_t)F->host.npatch() * F->host.desc.mx * F->host.desc.mx * sizeof(real);
+  FC_CUDA(cudaMemcpyAsync(F->mio, lam, nbytes, cudaMemcpyDeviceToDevice, s));
+  FC_CUDA(launch_set_time(F->d_t0, t0, s));
+  FC_CUDA(cudaGraphLaunch(g->exec, s));
+  launch_counter() += g->kernels;
+  FC_CUDA(cudaMemcpyAsync(lam, F->mio, nbytes, cudaMemcpyDeviceToDevice, s));
+  FC_CUDA(launch_add_double(dscale, F->d_ds, s));
   return FC_OK;
 }
 
@@ -1685,6 +1816,58 @@ fc_status fc_adjoint_step_multirate(fc_forest* F, double t, double dt_coarse, vo
                                : adjoint_multirate_t<double>(F, t, dt_coarse, lam, dscale, s);
   if (st != FC_OK) return st;
   return check_device_error(F, s);
+}
+
+// the checks the multirate adjoint's entry points share
+static fc_status adjoint_preconditions(const fc_forest* F, double dt) {
+  if (F->host.partial) return fail(FC_ERR_STATE, "the adjoint is built for whole forests");
+  if (!(dt > 0.0)) return fail(FC_ERR_INVALID_ARG, "dt must be positive");
+  if (F->host.desc.domain == FC_DOMAIN_SPHERE)
+    return fail(FC_ERR_INVALID_ARG, "the adjoint is built for the square domains");
+  if (F->host.desc.reflux)
+    return fail(FC_ERR_PRECONDITION, "the adjoint is built without refluxing");
+  return FC_OK;
+}
+
+fc_status fc_step_multirate_record(fc_forest* F, double t, double dt_coarse, int slot,
+                                   void* stream) {
+  if (!F) return fail(FC_ERR_INVALID_ARG, "null forest");
+  if (slot < 0 || slot >= FC_MAX_TAPE_SLOTS)
+    return fail(FC_ERR_INVALID_ARG, "tape slot out of range");
+  const fc_status pre = adjoint_preconditions(F, dt_coarse);
+  if (pre != FC_OK) return pre;
+  cudaStream_t s = as_stream(stream);
+  return F->esize == 4 ? record_multirate_t<float>(F, t, dt_coarse, slot, s)
+                       : record_multirate_t<double>(F, t, dt_coarse, slot, s);
+}
+
+fc_status fc_adjoint_step_multirate_taped(fc_forest* F, double t, double dt_coarse, int slot,
+                                          void* lam, double* dscale, void* stream) {
+  if (!F || !lam || !dscale) return fail(FC_ERR_INVALID_ARG, "null argument");
+  if (slot < 0 || slot >= FC_MAX_TAPE_SLOTS)
+    return fail(FC_ERR_INVALID_ARG, "tape slot out of range");
+  const fc_status pre = adjoint_preconditions(F, dt_coarse);
+  if (pre != FC_OK) return pre;
+  cudaStream_t s = as_stream(stream);
+  const fc_status st =
+      F->esize == 4 ? adjoint_taped_t<float>(F, t, dt_coarse, slot, lam, dscale, s)
+                    : adjoint_taped_t<double>(F, t, dt_coarse, slot, lam, dscale, s);
+  if (st != FC_OK) return st;
+  return check_device_error(F, s);
+}
+
+fc_status fc_tape_release(fc_forest* F) {
+  if (!F) return fail(FC_ERR_INVALID_ARG, "null forest");
+  for (auto it = F->adj_graphs.begin(); it != F->adj_graphs.end();)
+    if (it->mode != 0) {
+      if (it->exec) cudaGraphExecDestroy(it->exec);
+      it = F->adj_graphs.erase(it);
+    } else {
+      ++it;
+    }
+  for (auto& t : F->tapes) dfree(t.pool);
+  F->tapes.clear();
+  return FC_OK;
 }
 
 fc_status fc_adjoint_step_global(fc_forest* F, double t, double dt, void* lam, double* dscale,

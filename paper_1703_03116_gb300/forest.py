@@ -244,6 +244,25 @@ class Forest:
                                                ctypes.c_void_p(dscale.data_ptr()),
                                                _stream(stream)))
 
+    def step_multirate_record(self, t: float, dt_coarse: float, slot: int, stream=None):
+        """fc_step_multirate that also keeps, in tape `slot`, what the step's
+        reverse reads (see adjoint_step_multirate_taped)."""
+        check(load().fc_step_multirate_record(self._h, t, dt_coarse, slot, _stream(stream)))
+
+    def adjoint_step_multirate_taped(self, t: float, dt_coarse: float, slot: int, lam, dscale,
+                                     stream=None):
+        """Adjoint of the coarse step recorded in tape `slot` (the state is
+        neither read nor changed): lam and dscale as in adjoint_step_multirate."""
+        assert lam.is_cuda and lam.is_contiguous() and dscale.is_cuda
+        check(load().fc_adjoint_step_multirate_taped(self._h, t, dt_coarse, slot,
+                                                     ctypes.c_void_p(lam.data_ptr()),
+                                                     ctypes.c_void_p(dscale.data_ptr()),
+                                                     _stream(stream)))
+
+    def release_tapes(self):
+        """Free the tapes of recorded steps."""
+        check(load().fc_tape_release(self._h))
+
     def fused_fill(self, enable: bool = True):
         """Multirate substeps fill each patch's ghosts inside the update kernel (default on)."""
         check(load().fc_set_fused_fill(self._h, 1 if enable else 0))

@@ -159,6 +159,94 @@ def test_gpu_multirate_adjoint_step_matches_oracle_fp64(mx, lmax):
     np.testing.assert_array_equal(back.cpu().numpy(), q0)
 
 
+@pytest.mark.parametrize("mx,lmax", [(8, 4), (16, 4), (32, 3)])
+def test_recorded_step_and_taped_reverse_fp64(mx, lmax):
+    """fc_step_multirate_record is fc_step_multirate (the same bits) and the
+    taped reverse equals the oracle's adjoint of the step, for steps
+    recorded into several slots and reversed in any order."""
+    w, ref, q0, qt = _case(mx, lmax)
+    dtc = 0.9 / (mx * 2 ** lmax) * 2 ** (lmax - 2)
+    plain = fc.Forest(desc_for(fc, w, fc.F64), ref.leaves())
+    rec = fc.Forest(desc_for(fc, w, fc.F64), ref.leaves())
+    plain.set_q(q0)
+    rec.set_q(q0)
+    states = [q0]
+    for k in range(3):
+        plain.step_multirate(0.3 + k * dtc, dtc)
+        rec.step_multirate_record(0.3 + k * dtc, dtc, k)
+        np.testing.assert_array_equal(rec.get_q(), plain.get_q())
+        states.append(plain.get_q())
+    for k in (1, 2, 0):  # any order of the slots
+        o = oracle.initial_forest(w)
+        o.set_q(states[k])
+        lam0 = synth.random_field(q0.shape, seed=20 + k) - 0.5
+        lam_ref, ds_ref = o.adjoint_step_multirate(0.3 + k * dtc, dtc, lam0)
+        lam = _tensor(lam0, torch.float64)
+        ds = torch.zeros(1, dtype=torch.float64, device=DEV)
+        rec.adjoint_step_multirate_taped(0.3 + k * dtc, dtc, k, lam, ds)
+        err = relerr(lam.cpu().numpy(), lam_ref)
+        print(f"taped reverse mx={mx} slot {k}: rel err {err:.2e}")
+        assert err <= 1e-12
+        assert abs(float(ds) - ds_ref) <= 1e-12 * abs(ds_ref)
+    # the reverses left the recorded forest where its forward steps did
+    np.testing.assert_array_equal(rec.get_q(), states[3])
+
+
+@pytest.mark.parametrize("dtype,tol", [("f64", 1e-12), ("f32", 1e-5)])
+def test_forward_tape_and_recompute_give_the_same_gradient(dtype, tol):
+    """advect's two multirate strategies -- every step recorded by the
+    forward pass, or sqrt(N) checkpoints recomputed and recorded segment by
+    segment -- give the same gradients (to the atomics' rounding order)."""
+    w, ref, q0, qt = _case(16, 4)
+    dtc = 0.9 / (16 * 2 ** 4) * 4
+    F = fc.Forest(desc_for(fc, w, fc.F64 if dtype == "f64" else fc.F32), ref.leaves())
+    tdt = torch.float64 if dtype == "f64" else torch.float32
+    grads = {}
+    for tape in ("forward", "recompute"):
+        q = _tensor(q0, tdt).requires_grad_(True)
+        s = torch.ones((), dtype=tdt, device=DEV, requires_grad=True)
+        qN = advect(q, s, F, 0.1, dtc, 6, multirate=True, tape=tape)
+        loss = 0.5 * ((qN - _tensor(qt, tdt)) ** 2).sum()
+        loss.backward()
+        grads[tape] = (q.grad.cpu().numpy(), float(s.grad))
+    err = relerr(grads["forward"][0], grads["recompute"][0])
+    print(f"tape vs recompute {dtype}: q0 gradient {err:.2e}")
+    assert err <= tol
+    assert abs(grads["forward"][1] - grads["recompute"][1]) <= tol * abs(grads["recompute"][1])
+    # a later taped run takes the forest's tapes: the first backward refuses
+    q1 = _tensor(q0, tdt).requires_grad_(True)
+    s1 = torch.ones((), dtype=tdt, device=DEV, requires_grad=True)
+    a = advect(q1, s1, F, 0.1, dtc, 3, multirate=True, tape="forward")
+    b = advect(q1, s1, F, 0.1, dtc, 3, multirate=True, tape="forward")
+    b.sum().backward(retain_graph=True)
+    with pytest.raises(RuntimeError):
+        a.sum().backward()
+
+
+def test_taped_reverse_refuses_what_was_not_recorded():
+    w, ref, q0, qt = _case(16, 4)
+    dtc = 0.9 / (16 * 2 ** 4) * 4
+    F = fc.Forest(desc_for(fc, w, fc.F64), ref.leaves())
+    F.set_q(q0)
+    lam = _tensor(q0, torch.float64)
+    ds = torch.zeros(1, dtype=torch.float64, device=DEV)
+    with pytest.raises(fc.FcError) as e:  # nothing recorded
+        F.adjoint_step_multirate_taped(0.0, dtc, 0, lam, ds)
+    assert e.value.status == 6  # FC_ERR_STATE
+    F.step_multirate_record(0.0, dtc, 0)
+    with pytest.raises(fc.FcError) as e:  # recorded with another step length
+        F.adjoint_step_multirate_taped(0.0, 0.5 * dtc, 0, lam, ds)
+    assert e.value.status == 6
+    with pytest.raises(fc.FcError) as e:
+        F.step_multirate_record(0.0, dtc, 64)  # past FC_MAX_TAPE_SLOTS
+    assert e.value.status == 1  # FC_ERR_INVALID_ARG
+    F.set_advance_variant(0, 4)  # the captured steps changed: the tape is stale
+    with pytest.raises(fc.FcError) as e:
+        F.adjoint_step_multirate_taped(0.0, dtc, 0, lam, ds)
+    assert e.value.status == 6
+    F.release_tapes()
+
+
 @pytest.mark.parametrize("dtype,tol", [("f64", 1e-10), ("f32", 1e-3)])
 def test_autograd_multirate_gradient_matches_oracle(dtype, tol):
     w, ref, q0, qt = _case(8, 4)
