@@ -128,6 +128,10 @@ void dfree(T*& p) {
 struct fc_forest {
   HostForest host;
   size_t esize = 8;
+  // one allocation (store) holds the two state buffers, the
+  // time-interpolation tiles qT, the refluxing fluxes and the device staging
+  // for host copies, in that order
+  void* store = nullptr;
   void* buf[2] = {nullptr, nullptr};
   void* qT = nullptr;
   void* stage = nullptr;  // device staging for host copies
@@ -378,7 +382,7 @@ void destroy_timers(fc_forest* F) {
 
 void free_tables(fc_forest* F) {
   dfree(F->d_tables);
-  dfree(F->d_nbr);
+  F->d_nbr = nullptr;
   F->d_meta = nullptr;
   F->d_lists = nullptr;
   F->d_api_to_dev = nullptr;
@@ -389,11 +393,8 @@ void free_tables(fc_forest* F) {
 }
 
 void free_device(fc_forest* F) {
-  dfree(F->buf[0]);
-  dfree(F->buf[1]);
-  dfree(F->qT);
-  dfree(F->stage);
-  dfree(F->bflux);
+  dfree(F->store);
+  F->buf[0] = F->buf[1] = F->qT = F->stage = F->bflux = nullptr;
   free_tables(F);
   dfree(F->d_remap);
   dfree(F->d_err);
@@ -462,26 +463,23 @@ fc_status upload(fc_forest* F, bool alloc_store, bool metrics = true) {
   const size_t S = (size_t)H.desc.mx + 2 * kMbc;
   const size_t cells = (size_t)n * S * S;
   if (alloc_store) {
-    for (int b = 0; b < 2; ++b) {
-      dfree(F->buf[b]);
-      if (dmalloc_bytes(&F->buf[b], std::max<size_t>(cells, 1) * F->esize) != cudaSuccess)
-        return fail(FC_ERR_OOM, "device store allocation failed");
-      FC_CUDA(cudaMemsetAsync(F->buf[b], 0, std::max<size_t>(cells, 1) * F->esize,
-                              g_alloc_stream));
-    }
-    dfree(F->qT);
-    dfree(F->stage);
-    if (dmalloc_bytes(&F->qT, std::max<size_t>(cells, 1) * F->esize) != cudaSuccess ||
-        dmalloc_bytes(&F->stage, std::max<size_t>(cells, 1) * F->esize) != cudaSuccess)
+    // buf[0], buf[1], qT, bflux zeroed (one memset), then stage; each part
+    // 16-byte aligned
+    dfree(F->store);
+    F->buf[0] = F->buf[1] = F->qT = F->stage = F->bflux = nullptr;
+    const size_t tb = (std::max<size_t>(cells, 1) * F->esize + 15) & ~(size_t)15;
+    const size_t fb =
+        H.desc.reflux ? ((size_t)std::max(n, 1) * 2 * 4 * H.desc.mx * F->esize + 15) & ~(size_t)15
+                      : 0;
+    if (dmalloc_bytes(&F->store, 4 * tb + fb) != cudaSuccess)
       return fail(FC_ERR_OOM, "device store allocation failed");
-    FC_CUDA(cudaMemsetAsync(F->qT, 0, std::max<size_t>(cells, 1) * F->esize, g_alloc_stream));
-    dfree(F->bflux);
-    if (H.desc.reflux) {
-      const size_t nb = (size_t)std::max(n, 1) * 2 * 4 * H.desc.mx * F->esize;
-      if (dmalloc_bytes(&F->bflux, nb) != cudaSuccess)
-        return fail(FC_ERR_OOM, "device flux store allocation failed");
-      FC_CUDA(cudaMemsetAsync(F->bflux, 0, nb, g_alloc_stream));
-    }
+    char* base = static_cast<char*>(F->store);
+    F->buf[0] = base;
+    F->buf[1] = base + tb;
+    F->qT = base + 2 * tb;
+    F->bflux = fb ? base + 3 * tb : nullptr;
+    F->stage = base + 3 * tb + fb;
+    FC_CUDA(cudaMemsetAsync(F->store, 0, 3 * tb + fb, g_alloc_stream));
   }
   free_tables(F);
   // every work list, concatenated
@@ -498,8 +496,8 @@ fc_status upload(fc_forest* F, bool alloc_store, bool metrics = true) {
     F->off_t[l] = lists.size();
     lists.insert(lists.end(), H.list_t[l].begin(), H.list_t[l].end());
   }
-  // one block: the uploaded tables, then the device-written scratch (each
-  // part 16-byte aligned)
+  // one block: the uploaded tables, the neighbour table, then the
+  // device-written scratch (each part 16-byte aligned)
   const int nf = H.desc.nforests;
   size_t off = 0;
   const auto part = [&](size_t bytes) {
@@ -510,6 +508,7 @@ fc_status upload(fc_forest* F, bool alloc_store, bool metrics = true) {
   const size_t o_meta = part(sizeof(PatchMeta) * n), o_lists = part(sizeof(int) * lists.size()),
                o_api = part(sizeof(int) * n), o_fstart = part(sizeof(int) * (nf + 1));
   const size_t uploaded = off;
+  const size_t o_nbr = part(sizeof(NbrEntry) * n * 8);  // its own copy, from the host table
   const size_t o_sums = part(sizeof(double) * n), o_mass = part(sizeof(double) * nf),
                o_delta = part(sizeof(double) * n);
   std::vector<char> host(uploaded, 0);
@@ -526,7 +525,7 @@ fc_status upload(fc_forest* F, bool alloc_store, bool metrics = true) {
   F->d_patch_sums = reinterpret_cast<double*>(base + o_sums);
   F->d_mass = reinterpret_cast<double*>(base + o_mass);
   F->d_delta = reinterpret_cast<double*>(base + o_delta);
-  FC_CUDA(dmalloc(&F->d_nbr, (size_t)n * 8));
+  F->d_nbr = reinterpret_cast<NbrEntry*>(base + o_nbr);
   // (host sources are pageable: each copy has taken its data when it returns)
   FC_CUDA(cudaMemcpyAsync(F->d_tables, host.data(), uploaded, cudaMemcpyHostToDevice,
                           g_alloc_stream));
@@ -2136,6 +2135,7 @@ fc_status fc_tag_regrid(fc_forest* F, double tau_refine, double tau_coarsen,
   if (F->host.partial)
     return fail(FC_ERR_STATE, "a partitioned forest keeps its layout (no regrid)");
   cudaStream_t s = as_stream(stream);
+  host_pool_arm();  // the host workers wake while the tag waits on the device
   const int n = F->host.npatch();
   std::vector<double> delta(n);
   fc_status st = fc_tag(F, delta.data(), stream);
@@ -2184,7 +2184,7 @@ fc_status fc_tag_regrid(fc_forest* F, double tau_refine, double tau_coarsen,
   std::vector<RemapEntry> rm(N.npatch());
   // each entry reads the two layouts' tables only: host threads take ranges
   std::vector<char> orphan(16, 0);
-  parallel_chunks(N.npatch(), 8192, [&](int pb, int pe, int tid) {
+  parallel_chunks(N.npatch(), 128, [&](int pb, int pe, int tid) {
     for (int p = pb; p < pe; ++p) {
       const Leaf& a = N.leaves[N.api_of[p]];
       RemapEntry e{RM_COPY, {-1, -1, -1, -1}, 0, 0};
@@ -2249,6 +2249,7 @@ fc_status fc_tag_regrid(fc_forest* F, double tau_refine, double tau_coarsen,
   retire_graphs(F);
   free_device(F);
   F->host = std::move(G->host);
+  F->store = G->store;
   std::memcpy(F->buf, G->buf, sizeof F->buf);
   F->qT = G->qT;
   F->stage = G->stage;

@@ -6,6 +6,7 @@
 #include <climits>
 #include <cstddef>
 #include <cstdint>
+#include <functional>
 #include <memory>
 #include <new>
 #include <string>
@@ -88,22 +89,32 @@ struct UninitAlloc : std::allocator<T> {
   }
 };
 
-// Run fn(begin, end, thread) over [0, n) split into even contiguous chunks on
-// host threads (one chunk, on the calling thread, when n is small).
+// Host worker threads for the layout builds (leaf maps, neighbour rows,
+// remap lists).  host_pool_run(n, chunks, fn) runs fn(begin, end, slot) over
+// [0, n) split into `chunks` contiguous pieces, each taken by whichever
+// thread claims it first; slot (0 the caller, 1..15 a worker) names the
+// thread, which may run several pieces.  The caller claims pieces too, so a
+// call completes even if no worker joins (a worker that has claimed a piece
+// finishes it; nothing waits on a worker that has not).  host_pool_arm()
+// wakes a few workers ahead of parallel work: they poll for pieces for about
+// a millisecond before they sleep again (a regrid arms them before its tag
+// waits on the device, so they are awake when its tables are built).  One
+// call at a time per process: a concurrent call runs on its caller alone.
+// In a child process forked after the workers started, every call runs on
+// the caller.
+void host_pool_arm();
+void host_pool_run(int n, int chunks, const std::function<void(int, int, int)>& fn);
+
+// Run fn(begin, end, slot) over [0, n) on host threads in pieces of at least
+// min_per_piece items (on the calling thread alone when n is small).
 template <class Fn>
-inline void parallel_chunks(int n, int min_per_thread, Fn fn) {
-  const int hw = (int)std::max(1u, std::thread::hardware_concurrency());
-  const int nt = std::max(1, std::min(std::min(hw, 16), n / std::max(1, min_per_thread)));
-  if (nt <= 1) {
+inline void parallel_chunks(int n, int min_per_piece, Fn fn) {
+  const int pieces = n / std::max(1, min_per_piece);
+  if (pieces <= 1) {
     fn(0, n, 0);
     return;
   }
-  std::vector<std::thread> th;
-  for (int t = 0; t < nt; ++t) {
-    const int b = (int)((long)n * t / nt), e = (int)((long)n * (t + 1) / nt);
-    th.emplace_back([=]() { fn(b, e, t); });
-  }
-  for (auto& x : th) x.join();
+  host_pool_run(n, std::min(pieces, 64), std::function<void(int, int, int)>(fn));
 }
 
 struct PatchMeta {

@@ -11,14 +11,151 @@
 // the two patches.
 // Sec. 3.1: tagged grids are refined, quiet families of four siblings are
 // coarsened, and 2:1 balancing may add refinement.
+#include <unistd.h>
+
 #include <algorithm>
+#include <atomic>
+#include <chrono>
 #include <cmath>
+#include <condition_variable>
 #include <cstdio>
+#include <mutex>
 #include <thread>
 
 #include "fc_internal.hpp"
 
 namespace fc {
+
+// ------------------------------------------------------------------ host pool
+
+namespace {
+
+int64_t now_ns() {
+  return std::chrono::duration_cast<std::chrono::nanoseconds>(
+             std::chrono::steady_clock::now().time_since_epoch())
+      .count();
+}
+
+// The workers and the one open job.  A job is open while `gen` is odd; its
+// fields are written before it opens and read by a worker only after it
+// has announced itself in `active` and seen the job still open, and the
+// caller closes the job and waits for `active` to drain before it returns,
+// so no worker touches a job's function after its call has returned.
+struct HostPool {
+  static constexpr int kSpinners = 3;     // workers that arm() keeps polling
+  static constexpr int64_t kPollNs = 1000000;  // how long they poll
+  int workers = 0;
+  pid_t pid = 0;
+  std::mutex sleep_mu, run_mu;
+  std::condition_variable wake_spin, wake_all;  // the polling workers; every worker
+  std::atomic<uint64_t> gen{0};
+  std::atomic<int> next{0}, done{0}, active{0};
+  std::atomic<int64_t> poll_until{0};
+  int n = 0, chunks = 0;
+  const std::function<void(int, int, int)>* fn = nullptr;
+
+  bool open() const { return gen.load() & 1; }
+
+  // claim and run pieces of the open job g; returns when none is left
+  void take(uint64_t g, int slot);
+
+  void worker(int slot) {
+    const bool spinner = slot <= kSpinners;
+    for (;;) {
+      {
+        std::unique_lock<std::mutex> lk(sleep_mu);
+        if (spinner)
+          wake_spin.wait(lk, [&] { return open() || now_ns() < poll_until.load(); });
+        else
+          wake_all.wait(lk, [&] { return open(); });
+      }
+      do {
+        const uint64_t g = gen.load();
+        if (g & 1)
+          take(g, slot);
+        else
+          std::this_thread::yield();
+      } while (spinner ? now_ns() < poll_until.load() : open());
+    }
+  }
+
+  void start() {
+    pid = getpid();
+    const int hw = (int)std::max(1u, std::thread::hardware_concurrency());
+    workers = std::min(15, hw - 1);
+    // the workers live as long as the process (the pool is never freed, so
+    // a worker never outlives what it reads)
+    for (int w = 1; w <= workers; ++w) std::thread([this, w] { worker(w); }).detach();
+  }
+
+  void extend_poll() {
+    poll_until.store(now_ns() + kPollNs);
+    { std::lock_guard<std::mutex> lk(sleep_mu); }
+    wake_spin.notify_all();
+  }
+};
+
+// set while this thread runs a piece: a nested call runs on its caller
+thread_local bool t_in_piece = false;
+
+void HostPool::take(uint64_t g, int slot) {
+  active.fetch_add(1);
+  if (gen.load() == g) {
+    t_in_piece = true;
+    for (int c = next.fetch_add(1); c < chunks; c = next.fetch_add(1)) {
+      (*fn)((int)((long)n * c / chunks), (int)((long)n * (c + 1) / chunks), slot);
+      done.fetch_add(1);
+    }
+    t_in_piece = false;
+  }
+  active.fetch_sub(1);
+}
+
+HostPool* host_pool() {
+  static HostPool* p = [] {
+    HostPool* q = new HostPool();
+    q->start();
+    return q;
+  }();
+  return p;
+}
+
+}  // namespace
+
+void host_pool_arm() {
+  HostPool* P = host_pool();
+  if (P->workers > 0 && P->pid == getpid()) P->extend_poll();
+}
+
+void host_pool_run(int n, int chunks, const std::function<void(int, int, int)>& fn) {
+  HostPool* P = host_pool();
+  std::unique_lock<std::mutex> one(P->run_mu, std::defer_lock);
+  if (!t_in_piece) (void)one.try_lock();
+  if (!one.owns_lock() || P->workers == 0 || P->pid != getpid() || chunks <= 1) {
+    for (int c = 0; c < std::max(1, chunks); ++c)
+      fn((int)((long)n * c / std::max(1, chunks)), (int)((long)n * (c + 1) / std::max(1, chunks)),
+         0);
+    return;
+  }
+  P->n = n;
+  P->chunks = chunks;
+  P->fn = &fn;
+  P->next.store(0);
+  P->done.store(0);
+  {
+    std::lock_guard<std::mutex> lk(P->sleep_mu);
+    P->gen.fetch_add(1);  // open
+  }
+  P->wake_spin.notify_all();
+  P->wake_all.notify_all();
+  P->poll_until.store(std::max(P->poll_until.load(), now_ns() + HostPool::kPollNs));
+  const uint64_t g = P->gen.load();
+  P->take(g, 0);
+  while (P->done.load() < chunks) std::this_thread::yield();
+  P->gen.fetch_add(1);  // close
+  while (P->active.load() > 0) std::this_thread::yield();
+  P->fn = nullptr;
+}
 
 static uint64_t spread_bits(uint32_t v) {
   uint64_t x = v;
@@ -315,7 +452,7 @@ std::string HostForest::build() {
   // take contiguous ranges of leaves in field order, so one thread's lookups
   // stay within a few forests
   std::vector<std::string> row_err(16);
-  parallel_chunks(n, 8192, [&](int kb, int ke, int tid) {
+  parallel_chunks(n, 64, [&](int kb, int ke, int tid) {
     const std::string e = neighbour_rows(kb, ke);
     if (!e.empty()) row_err[tid] = e;
   });

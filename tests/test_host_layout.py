@@ -310,3 +310,35 @@ def test_reflux_kernel_indexing_is_the_oracle_pairing(domain):
                 jf = 2 * c - half * mx
                 got[k, d, c] = (1, n1 if half else n0, d ^ 1, jf, jf + 1)
     np.testing.assert_array_equal(got, ref)
+
+
+@pytest.mark.filterwarnings("ignore:This process .* is multi-threaded")
+def test_tables_built_on_host_threads_concurrently_and_after_fork():
+    """The neighbour tables are built in pieces by a pool of host threads.
+    Calls from several threads at once (one takes the pool, the others run
+    on their callers) and a call in a forked child (whose pool has no
+    threads) all give the table of a lone call."""
+    import multiprocessing as mp
+    import threading
+
+    w = synth.swirl(4, lmin=2, lmax=6, mx=8)
+    lv = oracle.initial_forest(w).leaves()
+    assert len(lv) >= 256  # several pieces
+    d = desc_for(w)
+    want = fc.layout_neighbours(d, lv)
+    got = [None] * 6
+
+    def run(i):
+        for _ in range(20):
+            got[i] = fc.layout_neighbours(d, lv)
+
+    th = [threading.Thread(target=run, args=(i,)) for i in range(len(got))]
+    for t in th:
+        t.start()
+    for t in th:
+        t.join()
+    for g in got:
+        np.testing.assert_array_equal(g, want)
+    ctx = mp.get_context("fork")
+    with ctx.Pool(1) as pool:
+        np.testing.assert_array_equal(pool.apply(fc.layout_neighbours, (d, lv)), want)
