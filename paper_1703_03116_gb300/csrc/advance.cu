@@ -181,7 +181,7 @@ __global__ void __launch_bounds__(NT, NT >= 512 ? (sizeof(real) == 4 ? 3 : 2)
     // the corners beyond a cube vertex
     auto gather = [&](int nthreads) {
       gather_ring<real, MX>(
-          D, [&](int r) -> const NbrEntry& { return st.e[r]; }, pm, a.tlevel, real(a.alpha),
+          D, [&](int r) -> const NbrEntry& { return st.e[r]; }, p, pm, a.tlevel, real(a.alpha),
           a.direct != 0, ring, ring_w, threadIdx.x, nthreads, static_cast<real*>(a.keep_t),
           a.keep_t_p0);
     };

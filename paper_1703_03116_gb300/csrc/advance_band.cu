@@ -140,7 +140,7 @@ __global__ void __launch_bounds__(band_threads<real, MX, R>(), band_min_blocks<r
     // table itself: no staging pass, no barrier before the gather
     if (a.gather)
       gather_ring<real, MX>(
-          D, [&](int r) { return D.nbr[(size_t)p * 8 + r]; }, pm, a.tlevel, real(a.alpha),
+          D, [&](int r) { return D.nbr[(size_t)p * 8 + r]; }, p, pm, a.tlevel, real(a.alpha),
           a.direct != 0, ring, ring_w, tid, NT, static_cast<real*>(a.keep_t), a.keep_t_p0);
     // thread 0 observes the copy's completion (bounded), the others after the
     // barrier (at once); the CTA leaves together if it gave up

@@ -83,6 +83,10 @@ cudaError_t dmalloc_bytes(void** p, size_t bytes) {
   if (g_hook.alloc) {
     void* q = g_hook.alloc(bytes, static_cast<void*>(g_alloc_stream), g_hook.user);
     if (!q) return cudaErrorMemoryAllocation;
+    if (reinterpret_cast<uintptr_t>(q) & 255) {  // the kernels' bulk copies and vector reads
+      g_hook.release(q, bytes, static_cast<void*>(g_alloc_stream), g_hook.user);
+      return cudaErrorMemoryAllocation;
+    }
     std::lock_guard<std::mutex> lock(g_hook_mu);
     g_hook_sizes[q] = bytes;
     *p = q;
@@ -781,8 +785,7 @@ fc_status advance_level_t(fc_forest* F, int L, double t, double dt, cudaStream_t
       // tiles, all the reverse reads of them.  The walk keeps the fill: with
       // one warp per patch, computing those cells in the update measured
       // slower on the ensemble (5.5e10 vs 7.4e10 cell-updates/s)
-      const bool direct = tlevel >= 0 && (a.variant == ADV_STAGED || a.variant == ADV_BAND) &&
-                          H.desc.domain != FC_DOMAIN_SPHERE;
+      const bool direct = tlevel >= 0 && (a.variant == ADV_STAGED || a.variant == ADV_BAND);
       if (direct) A.ntargets = 0;
       a.direct = direct ? 1 : 0;
       if (direct && F->keep_qT) {
@@ -2183,8 +2186,10 @@ fc_status fc_tag_regrid(fc_forest* F, double tau_refine, double tau_coarsen,
   const HostForest& N = G->host;
   std::vector<RemapEntry> rm(N.npatch());
   // each entry reads the two layouts' tables only: host threads take ranges
+  // of large layouts (below some thousands of patches one thread measured
+  // faster: the tables would have to move between cores)
   std::vector<char> orphan(16, 0);
-  parallel_chunks(N.npatch(), 128, [&](int pb, int pe, int tid) {
+  parallel_chunks(N.npatch(), 8192, [&](int pb, int pe, int tid) {
     for (int p = pb; p < pe; ++p) {
       const Leaf& a = N.leaves[N.api_of[p]];
       RemapEntry e{RM_COPY, {-1, -1, -1, -1}, 0, 0};

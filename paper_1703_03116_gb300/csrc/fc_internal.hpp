@@ -64,7 +64,19 @@ struct NbrEntry {
   // the neighbours' level and quadrant coordinates, copied here so a
   // kernel gathering ghosts reads one table instead of two dependent ones
   int lev, x0, y0, x1, y1, pad;
+  // A coarser neighbour c (NB_COARSE): where the coarse-neighbour fill
+  // takes the ghosts of c that the interpolation of this region reads, so a
+  // kernel computing them needs no read of c's entries.  The ghosts of c
+  // next to the owner are averages of the owner's own cells; up to two
+  // others, each (src[k], code[k]): code bits 0-5 and 6-11 the ghost's
+  // indices in c plus one, 12-17 and 18-23 the source cell (the first of a
+  // 2 x 2 block) in patch src[k], 24-25 the rule (1 copy, 2 average of the
+  // block, 3 keep the time-interpolated tile's value); bit 28 of code[0]:
+  // every ghost of c read is the owner's or one of these two (else, or when
+  // code[0] is 0, the kernel reads c's entries).
+  int src[2], code[2];
 };
+constexpr int kSrcComplete = 1 << 28;
 
 // Allocator whose construct without arguments leaves trivially constructible
 // elements uninitialised: host tables that are written in full (by host
@@ -305,6 +317,9 @@ struct HostForest {
   // rows of `nbr` and `meta` for the leaves [kb, ke) (field order); marks
   // feeds_finer
   std::string neighbour_rows(int kb, int ke);
+  // the coarse neighbours' ghost sources (NbrEntry::src, code) of the rows
+  // of leaves [kb, ke), from the finished table
+  void coarse_sources(int kb, int ke);
   std::string work_lists();
   // Refluxing's pairing, from the neighbour table and its index transforms:
   // per leaf (field order), face (-x, +x, -y, +y) and face cell k, 5 ints

@@ -142,7 +142,10 @@ __device__ __forceinline__ bool interpolate(const DevForest<real>& D, const NbrS
 // cell the wall condition clamps them to; any other ghost keeps what the
 // tile holds (that fill leaves it alone).  An update that computes the few
 // coarse cells its interpolation reads this way needs no fill launch before
-// it.  Not for the cubed sphere (its corner rule).
+// it.  The interpolation's stencil is centred in c's interior, so it reads
+// c's face ghosts at most, never the corners (on the cubed sphere, the
+// corners beyond a cube vertex are the only ghosts that fill computes from
+// other ghosts).
 //
 // Split in two: coarse_cell_interior applies the wall condition's clamp and
 // says whether the cell is interior (then src_interior reads it); a ghost
@@ -171,6 +174,61 @@ __device__ __forceinline__ real coarse_ghost(const DevForest<real>& D, const Pat
   return D.qT[(size_t)c * S * S + (j + kMbc) * S + i + kMbc];
 }
 
+// The value the coarse-neighbour fill gives ghost (ci, cj) of patch c by a
+// rule of NbrEntry::code (1 copy of cell (lx, ly) of patch n, on tlevel; 2
+// average of the 2 x 2 block at (lx, ly) of patch n, one level finer than
+// tlevel, area-weighted on a mapped grid; 3 the tile's value): the
+// arithmetic of copy_or_average_entry and coarse_ghost.
+template <typename real, int MX>
+__device__ __forceinline__ real fill_rule(const DevForest<real>& D, int tlevel, real alpha,
+                                          int rule, int n, int lx, int ly, int c, int ci,
+                                          int cj) {
+  constexpr int S = MX + 4;
+  if (rule == 1) return src_interior(D, tlevel, alpha, n, tlevel, lx, ly);
+  if (rule == 3) return D.qT[(size_t)c * S * S + (cj + kMbc) * S + ci + kMbc];
+  real s[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q)
+    s[q] = src_interior(D, tlevel, alpha, n, tlevel + 1, lx + (q & 1), ly + (q >> 1));
+  if (D.metric) {
+    const double* K = D.metric + (size_t)n * metric_stride(D.S) + (ly + kMbc) * D.S + lx + kMbc;
+    const double k0 = K[0], k1 = K[1], k2 = K[D.S], k3 = K[D.S + 1];
+    return real((((k0 * double(s[0]) + k1 * double(s[1])) + k2 * double(s[2])) +
+                 k3 * double(s[3])) /
+                (((k0 + k1) + k2) + k3));
+  }
+  return real(0.25) * (((s[0] + s[1]) + s[2]) + s[3]);
+}
+
+// Ghost (ci, cj) of coarse neighbour c (entry e of the owner p's region r,
+// ghost (i, j) of the owner) as the coarse-neighbour fill leaves it, from
+// the sources the host found for the region (NbrEntry::src, code): one of
+// the two listed ghosts, or the block of the owner's cells beside the
+// ghost's coarse cell (region r a face, the list complete), else from c's
+// own entry (coarse_ghost).  No read waits on c's table.
+template <typename real, int MX>
+__device__ __forceinline__ real coarse_ghost_at(const DevForest<real>& D, const NbrEntry& e,
+                                                const PatchMeta& cm, int p, int owner_level,
+                                                int tlevel, real alpha, int i, int j, int ci,
+                                                int cj) {
+  const int key = (ci + 1) | ((cj + 1) << 6);
+#pragma unroll
+  for (int q = 0; q < 2; ++q) {
+    const int code = e.code[q], rule = (code >> 24) & 3;
+    if (rule && (code & 0xFFF) == key)
+      return fill_rule<real, MX>(D, tlevel, alpha, rule, e.src[q], (code >> 12) & 63,
+                                 (code >> 18) & 63, e.n0, ci, cj);
+  }
+  const int r = region_of<MX>(i, j);
+  if ((e.code[0] & kSrcComplete) && r < 4) {
+    const int bi = r == 0 ? 0 : r == 1 ? MX - 2 : (i & ~1);
+    const int bj = r == 2 ? 0 : r == 3 ? MX - 2 : (j & ~1);
+    (void)owner_level;  // (one level finer than tlevel: fill_rule's average)
+    return fill_rule<real, MX>(D, tlevel, alpha, 2, p, bi, bj, e.n0, ci, cj);
+  }
+  return coarse_ghost<real, MX>(D, cm, e.n0, tlevel, alpha, ci, cj);
+}
+
 // interpolate_entry(), reading a coarse neighbour on tlevel through the
 // cells the coarse-neighbour fill would leave (above): the stencil's
 // interior cells are read together first, then any ghost of the coarse
@@ -182,7 +240,8 @@ template <typename real, int MX>
 __device__ __forceinline__ bool interpolate_direct_entry(const DevForest<real>& D,
                                                          const NbrEntry& e, const PatchMeta& pm,
                                                          int tlevel, real alpha, int i, int j,
-                                                         real& v, real* keep_t = nullptr,
+                                                         real& v, int p,
+                                                         real* keep_t = nullptr,
                                                          int keep_t_p0 = 0) {
   if (e.kind != NB_COARSE) return false;
   if (e.lev != tlevel) return interpolate_entry<real, MX>(D, e, pm, tlevel, i, j, v);
@@ -206,7 +265,8 @@ __device__ __forceinline__ bool interpolate_direct_entry(const DevForest<real>& 
   }
 #pragma unroll
   for (int m = 0; m < 5; ++m)
-    if (!in[m]) c[m] = coarse_ghost<real, MX>(D, cm, e.n0, tlevel, alpha, ci[m], cj[m]);
+    if (!in[m])
+      c[m] = coarse_ghost_at<real, MX>(D, e, cm, p, pm.level, tlevel, alpha, i, j, ci[m], cj[m]);
   if (keep_t) {
     constexpr int S = MX + 4;
     real* K = keep_t + (size_t)(e.n0 - keep_t_p0) * S * S;
@@ -226,10 +286,10 @@ __device__ __forceinline__ bool interpolate_direct_entry(const DevForest<real>& 
 // the same from the owner's staged entries
 template <typename real, int MX>
 __device__ __forceinline__ bool interpolate_direct(const DevForest<real>& D, const NbrStage& st,
-                                                   const PatchMeta& pm, int tlevel, real alpha,
-                                                   int i, int j, real& v) {
+                                                   const PatchMeta& pm, int p, int tlevel,
+                                                   real alpha, int i, int j, real& v) {
   return interpolate_direct_entry<real, MX>(D, st.e[region_of<MX>(i, j)], pm, tlevel, alpha, i,
-                                            j, v);
+                                            j, v, p);
 }
 
 // The neighbour reads of Alg. 1 for one patch (its copy/average and
@@ -237,11 +297,11 @@ __device__ __forceinline__ bool interpolate_direct(const DevForest<real>& D, con
 // slot k of ring / ring_w gets ghost k's value and whether a rule set it (an
 // exterior ghost is left to the wall condition).  entry_of(r) gives the
 // entry of face/corner region r (staged in shared memory, or read from the
-// table).  Threads tid, stride nt.  direct: coarse neighbours on tlevel are
+// table) of patch p.  Threads tid, stride nt.  direct: coarse neighbours on tlevel are
 // read through the cells their fill would leave (interpolate_direct_entry;
 // keep_t, keep_t_p0: where it also stores them).
 template <typename real, int MX, class EntryOf>
-__device__ __forceinline__ void gather_ring(const DevForest<real>& D, EntryOf entry_of,
+__device__ __forceinline__ void gather_ring(const DevForest<real>& D, EntryOf entry_of, int p,
                                             const PatchMeta& pm, int tlevel, real alpha,
                                             bool direct, real* ring, bool* ring_w, int tid,
                                             int nt, real* keep_t = nullptr,
@@ -254,8 +314,8 @@ __device__ __forceinline__ void gather_ring(const DevForest<real>& D, EntryOf en
     real v;
     const bool w =
         copy_or_average_entry<real, MX>(D, e, pm, tlevel, alpha, i, j, v) ||
-        (direct ? interpolate_direct_entry<real, MX>(D, e, pm, tlevel, alpha, i, j, v, keep_t,
-                                                     keep_t_p0)
+        (direct ? interpolate_direct_entry<real, MX>(D, e, pm, tlevel, alpha, i, j, v, p,
+                                                     keep_t, keep_t_p0)
                 : interpolate_entry<real, MX>(D, e, pm, tlevel, i, j, v));
     ring[k] = w ? v : real(0);
     ring_w[k] = w;
