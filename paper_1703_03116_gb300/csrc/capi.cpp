@@ -2170,17 +2170,22 @@ fc_status fc_tag_regrid(fc_forest* F, double tau_refine, double tau_coarsen,
   // by its upload: the new layout's build reuses their memory
   G->host.nbr.swap(F->host.nbr);
   G->host.meta.swap(F->host.meta);
-  err = G->host.build();
-  if (!err.empty()) {
-    delete G;
-    return fail(FC_ERR_STATE, "regrid produced an invalid layout: " + err);
-  }
-  st = upload(G, true, false);
-  if (st != FC_OK) {
+  // the forest's error word and step-time word carry over to the new layout
+  // (G borrows them until it takes F's place)
+  G->d_err = F->d_err;
+  G->d_t0 = F->d_t0;
+  const auto abandon = [&](fc_status why) {  // G's own memory goes, F stays as it was
+    G->d_err = nullptr;
+    G->d_t0 = nullptr;
     free_device(G);
     delete G;
-    return st;
-  }
+    return why;
+  };
+  err = G->host.build();
+  if (!err.empty())
+    return abandon(fail(FC_ERR_STATE, "regrid produced an invalid layout: " + err));
+  st = upload(G, true, false);
+  if (st != FC_OK) return abandon(st);
   // remap list in G's device order
   const HostForest& O = F->host;
   const HostForest& N = G->host;
@@ -2219,39 +2224,30 @@ fc_status fc_tag_regrid(fc_forest* F, double tau_refine, double tau_coarsen,
     }
   });
   for (char o : orphan)
-    if (o) {
-      free_device(G);
-      delete G;
-      return fail(FC_ERR_STATE, "regrid: new leaf has neither an old parent nor children");
-    }
+    if (o) return abandon(fail(FC_ERR_STATE, "regrid: new leaf has neither an old parent nor children"));
   int kept = 0;
   for (const RemapEntry& e : rm) kept += e.kind == RM_COPY;
   const int created = N.npatch() - kept;
   dfree(G->d_remap);
-  if (dmalloc(&G->d_remap, rm.size()) != cudaSuccess) {
-    free_device(G);
-    delete G;
-    return fail(FC_ERR_OOM, "remap list allocation failed");
-  }
-  FC_CUDA(cudaMemcpyAsync(G->d_remap, rm.data(), sizeof(RemapEntry) * rm.size(),
-                          cudaMemcpyHostToDevice, s));
+  if (dmalloc(&G->d_remap, rm.size()) != cudaSuccess)
+    return abandon(fail(FC_ERR_OOM, "remap list allocation failed"));
+  cudaError_t e = cudaMemcpyAsync(G->d_remap, rm.data(), sizeof(RemapEntry) * rm.size(),
+                                  cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) return abandon(cuda_fail(e, "remap list copy"));
   if (F->d_metric) {  // the new layout's metrics: kept patches copy theirs
     st = update_metrics(G, G->d_remap, F->d_metric);
-    if (st != FC_OK) {
-      free_device(G);
-      delete G;
-      return st;
-    }
+    if (st != FC_OK) return abandon(st);
   }
-  cudaError_t e;
   {
     Timed tm(F, 2, s, 2.0 * (double)N.npatch() * N.desc.mx * N.desc.mx * F->esize);
     e = F->esize == 4 ? launch_remap(dev<float>(F), dev<float>(G), G->d_remap, s)
                       : launch_remap(dev<double>(F), dev<double>(G), G->d_remap, s);
   }
-  if (e != cudaSuccess) return cuda_fail(e, "remap");
+  if (e != cudaSuccess) return abandon(cuda_fail(e, "remap"));
   // swap contents: F takes G's layout and store; captured steps are stale
   retire_graphs(F);
+  F->d_err = nullptr;  // (G holds them)
+  F->d_t0 = nullptr;
   free_device(F);
   F->host = std::move(G->host);
   F->store = G->store;
