@@ -131,6 +131,10 @@ void dfree(T*& p) {
 
 struct fc_forest {
   HostForest host;
+  // the tables of the layout before the current one, whose memory the next
+  // regrid's build writes its rows into
+  std::vector<NbrEntry, UninitAlloc<NbrEntry>> spare_nbr;
+  std::vector<PatchMeta, UninitAlloc<PatchMeta>> spare_meta;
   size_t esize = 8;
   // one allocation (store) holds the two state buffers, the
   // time-interpolation tiles qT, the refluxing fluxes and the device staging
@@ -2166,10 +2170,11 @@ fc_status fc_tag_regrid(fc_forest* F, double tau_refine, double tau_coarsen,
   G->esize = F->esize;
   G->vel_scale = F->vel_scale;  // the sphere's metrics carry it
   G->host.leaves = nl;
-  // the old layout's host neighbour table and patch records were read once,
-  // by its upload: the new layout's build reuses their memory
-  G->host.nbr.swap(F->host.nbr);
-  G->host.meta.swap(F->host.meta);
+  // the new layout's build carries over the rows of the old one that it
+  // keeps (the old tables are read, not reused; the memory of the tables
+  // before them is)
+  G->host.nbr.swap(F->spare_nbr);
+  G->host.meta.swap(F->spare_meta);
   // the forest's error word and step-time word carry over to the new layout
   // (G borrows them until it takes F's place)
   G->d_err = F->d_err;
@@ -2181,7 +2186,7 @@ fc_status fc_tag_regrid(fc_forest* F, double tau_refine, double tau_coarsen,
     delete G;
     return why;
   };
-  err = G->host.build();
+  err = G->host.build(&F->host);
   if (!err.empty())
     return abandon(fail(FC_ERR_STATE, "regrid produced an invalid layout: " + err));
   st = upload(G, true, false);
@@ -2249,6 +2254,8 @@ fc_status fc_tag_regrid(fc_forest* F, double tau_refine, double tau_coarsen,
   F->d_err = nullptr;  // (G holds them)
   F->d_t0 = nullptr;
   free_device(F);
+  F->spare_nbr.swap(F->host.nbr);  // the next regrid's build writes here
+  F->spare_meta.swap(F->host.meta);
   F->host = std::move(G->host);
   F->store = G->store;
   std::memcpy(F->buf, G->buf, sizeof F->buf);

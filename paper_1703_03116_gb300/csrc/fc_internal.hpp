@@ -313,13 +313,17 @@ struct HostForest {
   int upd_end(int l) const { return partial ? own_end[l] : lev_start[l + 1]; }
 
   // Build everything from `leaves`; returns an empty string or an error.
-  std::string build();
+  // prev (optional): the layout this one replaces (a regrid), built and
+  // unchanged since; the rows of leaves it held whose neighbours it held too
+  // are its rows with the patch indices renumbered (the same rows a full
+  // build computes: a row depends only on the leaves it names).
+  std::string build(const HostForest* prev = nullptr);
   // rows of `nbr` and `meta` for the leaves [kb, ke) (field order); marks
   // feeds_finer
   std::string neighbour_rows(int kb, int ke);
   // the coarse neighbours' ghost sources (NbrEntry::src, code) of the rows
   // of leaves [kb, ke), from the finished table
-  void coarse_sources(int kb, int ke);
+  void coarse_sources(int kb, int ke, const char* only = nullptr);  // only: rows flagged 1
   std::string work_lists();
   // Refluxing's pairing, from the neighbour table and its index transforms:
   // per leaf (field order), face (-x, +x, -y, +y) and face cell k, 5 ints

@@ -342,7 +342,7 @@ bool move_quadrant(const fc_forest_desc& d, int b, int l, int x, int y, int mx, 
 
 }  // namespace
 
-std::string HostForest::build() {
+std::string HostForest::build(const HostForest* prev) {
   const fc_forest_desc& d = desc;
   const int nb = nblocks(d);
   sort_leaves(&leaves);
@@ -448,17 +448,61 @@ std::string HostForest::build() {
   meta.resize(n);
   nbr.resize((size_t)n * 8);
   feeds_finer.assign(n, 0);
+  // rows carried over from the replaced layout: prev's device index -> ours
+  const bool incr = prev && prev != this && !prev->partial && !partial &&
+                    prev->desc.nforests == d.nforests && prev->desc.mx == d.mx &&
+                    prev->nbr.size() == (size_t)prev->npatch() * 8 &&
+                    prev->meta.size() == (size_t)prev->npatch();
+  std::vector<int> prev_k, dev_map;
+  if (incr) {
+    prev_k.resize(n);
+    dev_map.assign(prev->npatch(), -1);
+    for (int k = 0; k < n; ++k) {
+      const Leaf& a = leaves[k];
+      const int o = prev->find(a.f, a.b, a.l, a.x, a.y);
+      prev_k[k] = o;
+      if (o >= 0) dev_map[prev->dev_of[o]] = dev_of[k];
+    }
+  }
+  // a carried row: every patch it names (neighbours, ghost sources) still a
+  // leaf; false leaves the row to be computed
+  const auto carry = [&](int k) {
+    const int o = prev_k[k];
+    if (o < 0) return false;
+    const int op = prev->dev_of[o], p = dev_of[k];
+    NbrEntry row[8];
+    for (int dir = 0; dir < 8; ++dir) {
+      NbrEntry e = prev->nbr[(size_t)op * 8 + dir];
+      for (int* id : {&e.n0, &e.n1, &e.src[0], &e.src[1]})
+        if (*id >= 0 && (*id = dev_map[*id]) < 0) return false;
+      row[dir] = e;
+    }
+    for (int dir = 0; dir < 8; ++dir) {
+      nbr[(size_t)p * 8 + dir] = row[dir];
+      if (row[dir].kind == NB_COARSE)  // (several threads may store the same byte)
+        __atomic_store_n(&feeds_finer[row[dir].n0], (char)1, __ATOMIC_RELAXED);
+    }
+    meta[p] = prev->meta[op];
+    return true;
+  };
   // the rows are independent (each reads the leaf tables only): host threads
   // take contiguous ranges of leaves in field order, so one thread's lookups
   // stay within a few forests
   std::vector<std::string> row_err(16);
+  std::vector<char> fresh(n, 1);  // rows computed here (their ghost sources too)
   parallel_chunks(n, 64, [&](int kb, int ke, int tid) {
-    const std::string e = neighbour_rows(kb, ke);
-    if (!e.empty()) row_err[tid] = e;
+    for (int k = kb; k < ke; ++k) {
+      if (incr && carry(k)) {
+        fresh[k] = 0;
+        continue;
+      }
+      const std::string e = neighbour_rows(k, k + 1);
+      if (!e.empty()) row_err[tid] = e;
+    }
   });
   for (const auto& e : row_err)
     if (!e.empty()) return e;
-  parallel_chunks(n, 64, [&](int kb, int ke, int) { coarse_sources(kb, ke); });
+  parallel_chunks(n, 64, [&](int kb, int ke, int) { coarse_sources(kb, ke, fresh.data()); });
   // work lists
   return work_lists();
 }
@@ -558,7 +602,7 @@ std::string HostForest::neighbour_rows(int kb, int ke) {
 // each (its face entries: copy from a same-size neighbour, average of a
 // finer one's 2 x 2 block; a coarser one leaves the tile's value).  The
 // stencil and the wall clamp are the kernel's (interpolate_direct_entry).
-void HostForest::coarse_sources(int kb, int ke) {
+void HostForest::coarse_sources(int kb, int ke, const char* only) {
   const fc_forest_desc& d = desc;
   const int mx = d.mx;
   const bool walls = d.domain == FC_DOMAIN_WALLS;
@@ -569,6 +613,7 @@ void HostForest::coarse_sources(int kb, int ke) {
     return 4 + (dx > 0 ? 1 : 0) + (dy > 0 ? 2 : 0);
   };
   for (int k = kb; k < ke; ++k) {
+    if (only && !only[k]) continue;
     const int p = dev_of[k];
     const Leaf& o = leaves[k];
     for (int r = 0; r < 8; ++r) {
@@ -662,11 +707,14 @@ void HostForest::coarse_sources(int kb, int ke) {
           }
           if (!own) complete = false;
         }
+      if (!complete) {  // (no list: nothing named, so a carried row never waits on it)
+        src[0] = src[1] = -1;
+        code[0] = code[1] = 0;
+      }
       e.src[0] = src[0];
       e.src[1] = src[1];
       e.code[0] = code[0] | (complete ? kSrcComplete : 0);
       e.code[1] = code[1];
-      if (!complete) e.code[0] = e.code[1] = 0;
     }
   }
 }
