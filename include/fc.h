@@ -158,13 +158,22 @@ fc_status fc_set_allocator(fc_alloc_fn alloc, fc_free_fn release, void* user);
  *   device_bytes         device memory the forest holds now (store, tables,
  *                        metrics, adjoint buffers once created)
  *   graphs               captured coarse steps (forward and adjoint) held
- *   tuned_buckets        launch-size buckets the autotuner has timed */
+ *   tuned_buckets        launch-size buckets the autotuner has timed
+ *   coarse_entries       face/corner regions of the layout filled from a
+ *                        coarser neighbour
+ *   coarse_unlisted      of them, those whose coarse neighbour's ghosts the
+ *                        update must look up in that neighbour's own table
+ *                        entries (the ghosts it reads are not all listed in
+ *                        the region's entry: a slower read chain, same
+ *                        values).  Reading these two synchronises the
+ *                        device (the table is read back). */
 #define FC_INFO_LEVELS 21
 typedef struct {
   int nleaves, nforests, mx, mbc, lmin, lmax, dtype, domain;
   int leaves_per_level[FC_INFO_LEVELS];
   int64_t device_bytes;
   int graphs, tuned_buckets;
+  int coarse_entries, coarse_unlisted;
 } fc_info;
 fc_status fc_forest_info(const fc_forest* forest, fc_info* out);
 

@@ -27,7 +27,8 @@ class Info(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int) for n in ("nleaves", "nforests", "mx", "mbc", "lmin", "lmax",
                                             "dtype", "domain")] + [
         ("leaves_per_level", ctypes.c_int * INFO_LEVELS), ("device_bytes", ctypes.c_int64),
-        ("graphs", ctypes.c_int), ("tuned_buckets", ctypes.c_int)]
+        ("graphs", ctypes.c_int), ("tuned_buckets", ctypes.c_int),
+        ("coarse_entries", ctypes.c_int), ("coarse_unlisted", ctypes.c_int)]
 
 
 # every function that include/fc.h declares, with (restype, argtypes)

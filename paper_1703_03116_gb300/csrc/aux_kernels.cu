@@ -513,6 +513,130 @@ cudaError_t launch_add_double(double* dst, const double* src, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+// Sec. 2.3 (interpolation) with the coarse neighbours' time-interpolated
+// cells computed where they are read: for each region of a patch filled
+// from a coarser neighbour c (entry e), the ghosts of c that the
+// interpolation stencils of the region's ghosts reach beyond the owner's own
+// cells, and the rule of c's coarse-neighbour fill for each (from c's face
+// entries: copy of a same-size neighbour's cell, average of a finer one's
+// 2 x 2 block; a coarser one leaves the tile's value) -- NbrEntry::src and
+// code, one thread an entry, written in place (a thread writes its entry's
+// src and code and reads only other fields of the entries).  The stencil and
+// the wall clamp are interpolate_direct_entry's.  The four ghosts of an
+// aligned 2 x 2 group share their coarse cell, its stencil and their block
+// of the owner, so one stands for all; along a face only the two end groups
+// are visited: a group between them has its stencil inside c but towards
+// the owner, where c's ghost is the average of the owner's block beside it,
+// as each end group shows for its own.
+__global__ void coarse_sources_kernel(NbrEntry* nbr, const PatchMeta* meta, int n, int mx,
+                                      int walls) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n * 8) return;
+  const int p = t >> 3, r = t & 7;
+  NbrEntry& e = nbr[t];
+  if (e.kind != NB_COARSE) return;
+  const PatchMeta o = meta[p];
+  const int c = e.n0;
+  const int dxr = r == 0 || r == 4 || r == 6 ? -1 : r == 1 || r == 5 || r == 7 ? 1 : 0;
+  const int dyr = r == 2 || r == 4 || r == 5 ? -1 : r == 3 || r == 6 || r == 7 ? 1 : 0;
+  const int i0 = dxr < 0 ? -2 : dxr > 0 ? mx : 0, i1 = dxr == 0 ? mx : i0 + 2;
+  const int j0 = dyr < 0 ? -2 : dyr > 0 ? mx : 0, j1 = dyr == 0 ? mx : j0 + 2;
+  const int step_i = r < 4 && dxr == 0 ? mx - 2 : 2, step_j = r < 4 && dyr == 0 ? mx - 2 : 2;
+  auto region = [mx](int i, int j) {
+    const int dx = i < 0 ? -1 : (i >= mx ? 1 : 0), dy = j < 0 ? -1 : (j >= mx ? 1 : 0);
+    if (dy == 0) return dx < 0 ? 0 : 1;
+    if (dx == 0) return dy < 0 ? 2 : 3;
+    return 4 + (dx > 0 ? 1 : 0) + (dy > 0 ? 2 : 0);
+  };
+  int ext = 0, cc[2] = {0, 0}, src[2] = {-1, -1}, code[2] = {0, 0};
+  bool complete = true;
+  for (int j = j0; j < j1 && complete; j += step_j)
+    for (int i = i0; i < i1 && complete; i += step_i) {
+      bool own = r >= 4;  // a face's group has the owner's block among its reads
+      const int2 I = apply_a(e.a, o.x * mx + i, o.y * mx + j);
+      const int gx = I.x + e.fx, gy = I.y + e.fy;
+      const int ic = (gx >> 1) - e.x0 * mx, jc = (gy >> 1) - e.y0 * mx;
+      if (ic < 0 || ic >= mx || jc < 0 || jc >= mx) continue;  // not interpolated
+      for (int m = 1; m < 5 && complete; ++m) {
+        int ci = ic + (m == 1 ? 1 : m == 2 ? -1 : 0), cj = jc + (m == 3 ? 1 : m == 4 ? -1 : 0);
+        if (walls) {  // the exterior ghosts of c are its clamped cells
+          const int N = mx << e.lev, X = e.x0 * mx + ci, Y = e.y0 * mx + cj;
+          if (X < 0 || X >= N) ci = X < 0 ? 0 : mx - 1;
+          if (Y < 0 || Y >= N) cj = Y < 0 ? 0 : mx - 1;
+        }
+        if (ci >= 0 && ci < mx && cj >= 0 && cj < mx) continue;  // c's interior
+        const NbrEntry& f = nbr[(size_t)c * 8 + region(ci, cj)];  // c's fill of (ci, cj)
+        int rule = 3, sp = -1, lx = 0, ly = 0;
+        if (f.kind == NB_SAME || f.kind == NB_FINE) {
+          const int2 H = apply_a(f.a, e.x0 * mx + ci, e.y0 * mx + cj);
+          const int hx = H.x + f.fx, hy = H.y + f.fy;
+          if (f.kind == NB_SAME) {
+            rule = 1;
+            sp = f.n0;
+            lx = hx - f.x0 * mx;
+            ly = hy - f.y0 * mx;
+          } else {
+            rule = 2;
+            sp = f.n0;
+            lx = 2 * hx - f.x0 * mx;
+            ly = 2 * hy - f.y0 * mx;
+            if (lx < 0 || lx >= mx || ly < 0 || ly >= mx) {
+              sp = f.n1;
+              lx = 2 * hx - f.x1 * mx;
+              ly = 2 * hy - f.y1 * mx;
+            }
+          }
+          if (sp < 0 || lx < 0 || lx >= mx || ly < 0 || ly >= mx) {
+            complete = false;  // (a malformed entry: the update reads c's)
+            break;
+          }
+        }
+        // next to the owner: a block of its own cells, the one the update
+        // takes (region r a face; the block beside the ghost's coarse cell,
+        // towards the owner)
+        if (rule == 2 && sp == p && r < 4) {
+          const int bi = r == 0 ? 0 : r == 1 ? mx - 2 : (i & ~1);
+          const int bj = r == 2 ? 0 : r == 3 ? mx - 2 : (j & ~1);
+          if (lx == bi && ly == bj) {
+            own = true;
+            continue;
+          }
+        }
+        const int key = (ci + 1) | ((cj + 1) << 6);
+        int slot = -1;
+        for (int q = 0; q < ext; ++q)
+          if (cc[q] == key) slot = q;
+        if (slot < 0) {
+          if (ext == 2) {
+            complete = false;
+            break;
+          }
+          slot = ext++;
+          cc[slot] = key;
+          src[slot] = sp;
+          code[slot] = key | (lx << 12) | (ly << 18) | (rule << 24);
+        }
+      }
+      if (!own) complete = false;
+    }
+  if (!complete) {  // no list: the update reads c's entries
+    src[0] = src[1] = -1;
+    code[0] = code[1] = 0;
+  }
+  e.src[0] = src[0];
+  e.src[1] = src[1];
+  e.code[0] = code[0] | (complete ? kSrcComplete : 0);
+  e.code[1] = code[1];
+}
+
+cudaError_t launch_coarse_sources(NbrEntry* nbr, const PatchMeta* meta, int n, int mx, int walls,
+                                  cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  coarse_sources_kernel<<<(n * 8 + 255) / 256, 256, 0, s>>>(nbr, meta, n, mx, walls);
+  ++launch_counter();
+  return cudaGetLastError();
+}
+
 // Stores the start time of a replayed coarse step in device memory (one
 // thread); kernels captured in a graph read it there.
 cudaError_t launch_set_time(double* t0_dev, double t0, cudaStream_t s) {

@@ -539,6 +539,9 @@ fc_status upload(fc_forest* F, bool alloc_store, bool metrics = true) {
                           g_alloc_stream));
   FC_CUDA(cudaMemcpyAsync(F->d_nbr, H.nbr.data(), sizeof(NbrEntry) * n * 8,
                           cudaMemcpyHostToDevice, g_alloc_stream));
+  // the coarse neighbours' ghost sources, on the device (the host goes on)
+  FC_CUDA(launch_coarse_sources(F->d_nbr, F->d_meta, n, H.desc.mx,
+                                H.desc.domain == FC_DOMAIN_WALLS ? 1 : 0, g_alloc_stream));
   if (!F->d_err) {
     FC_CUDA(dmalloc(&F->d_err, 1));
     FC_CUDA(cudaMemsetAsync(F->d_err, 0, sizeof(int), g_alloc_stream));
@@ -1015,6 +1018,17 @@ fc_status fc_forest_info(const fc_forest* F, fc_info* out) {
   int tuned = 0;
   for (const auto& t : F->tune) tuned += t.tuned ? 1 : 0;
   out->tuned_buckets = tuned;
+  if (F->d_nbr && H.npatch() > 0) {  // the ghost sources the device wrote
+    std::vector<NbrEntry> rows((size_t)H.npatch() * 8);
+    FC_CUDA(cudaDeviceSynchronize());
+    FC_CUDA(cudaMemcpy(rows.data(), F->d_nbr, sizeof(NbrEntry) * rows.size(),
+                       cudaMemcpyDeviceToHost));
+    for (const NbrEntry& e : rows)
+      if (e.kind == NB_COARSE) {
+        ++out->coarse_entries;
+        out->coarse_unlisted += (e.code[0] & kSrcComplete) ? 0 : 1;
+      }
+  }
   return FC_OK;
 }
 

@@ -66,9 +66,10 @@ struct NbrEntry {
   int lev, x0, y0, x1, y1, pad;
   // A coarser neighbour c (NB_COARSE): where the coarse-neighbour fill
   // takes the ghosts of c that the interpolation of this region reads, so a
-  // kernel computing them needs no read of c's entries.  The ghosts of c
-  // next to the owner are averages of the owner's own cells; up to two
-  // others, each (src[k], code[k]): code bits 0-5 and 6-11 the ghost's
+  // kernel computing them needs no read of c's entries (written on the
+  // device after each upload, launch_coarse_sources; -1 and 0 on the host).
+  // The ghosts of c next to the owner are averages of the owner's own cells;
+  // up to two others, each (src[k], code[k]): code bits 0-5 and 6-11 the ghost's
   // indices in c plus one, 12-17 and 18-23 the source cell (the first of a
   // 2 x 2 block) in patch src[k], 24-25 the rule (1 copy, 2 average of the
   // block, 3 keep the time-interpolated tile's value); bit 28 of code[0]:
@@ -321,9 +322,6 @@ struct HostForest {
   // rows of `nbr` and `meta` for the leaves [kb, ke) (field order); marks
   // feeds_finer
   std::string neighbour_rows(int kb, int ke);
-  // the coarse neighbours' ghost sources (NbrEntry::src, code) of the rows
-  // of leaves [kb, ke), from the finished table
-  void coarse_sources(int kb, int ke, const char* only = nullptr);  // only: rows flagged 1
   std::string work_lists();
   // Refluxing's pairing, from the neighbour table and its index transforms:
   // per leaf (field order), face (-x, +x, -y, +y) and face cell k, 5 ints
@@ -596,6 +594,12 @@ cudaError_t launch_remap(const DevForest<real>& Old, const DevForest<real>& New,
                          const RemapEntry* rm, cudaStream_t s);
 
 uint64_t& launch_counter();
+
+// The coarse neighbours' ghost sources (NbrEntry::src, code) of a layout's
+// neighbour table in device memory (n patches, mx, walls: the square
+// domain with walls), in place.
+cudaError_t launch_coarse_sources(NbrEntry* nbr, const PatchMeta* meta, int n, int mx, int walls,
+                                  cudaStream_t s);
 
 // Cubed-sphere metric blocks of patches [0, npatch) for the solid-body
 // rotation omega (already scaled): equiangular gnomonic mapping of each

@@ -464,8 +464,8 @@ std::string HostForest::build(const HostForest* prev) {
       if (o >= 0) dev_map[prev->dev_of[o]] = dev_of[k];
     }
   }
-  // a carried row: every patch it names (neighbours, ghost sources) still a
-  // leaf; false leaves the row to be computed
+  // a carried row: every patch it names still a leaf; false leaves the row
+  // to be computed
   const auto carry = [&](int k) {
     const int o = prev_k[k];
     if (o < 0) return false;
@@ -473,7 +473,7 @@ std::string HostForest::build(const HostForest* prev) {
     NbrEntry row[8];
     for (int dir = 0; dir < 8; ++dir) {
       NbrEntry e = prev->nbr[(size_t)op * 8 + dir];
-      for (int* id : {&e.n0, &e.n1, &e.src[0], &e.src[1]})
+      for (int* id : {&e.n0, &e.n1})
         if (*id >= 0 && (*id = dev_map[*id]) < 0) return false;
       row[dir] = e;
     }
@@ -489,20 +489,15 @@ std::string HostForest::build(const HostForest* prev) {
   // take contiguous ranges of leaves in field order, so one thread's lookups
   // stay within a few forests
   std::vector<std::string> row_err(16);
-  std::vector<char> fresh(n, 1);  // rows computed here (their ghost sources too)
   parallel_chunks(n, 64, [&](int kb, int ke, int tid) {
     for (int k = kb; k < ke; ++k) {
-      if (incr && carry(k)) {
-        fresh[k] = 0;
-        continue;
-      }
+      if (incr && carry(k)) continue;
       const std::string e = neighbour_rows(k, k + 1);
       if (!e.empty()) row_err[tid] = e;
     }
   });
   for (const auto& e : row_err)
     if (!e.empty()) return e;
-  parallel_chunks(n, 64, [&](int kb, int ke, int) { coarse_sources(kb, ke, fresh.data()); });
   // work lists
   return work_lists();
 }
@@ -593,130 +588,6 @@ std::string HostForest::neighbour_rows(int kb, int ke) {
     }
   }
   return "";
-}
-
-// Sec. 2.3 (interpolation) with the coarse neighbours' time-interpolated
-// cells computed where they are read: for each region of a leaf filled from a
-// coarser neighbour c, the ghosts of c that the interpolation stencils of
-// the region's ghosts reach, and the rule of c's coarse-neighbour fill for
-// each (its face entries: copy from a same-size neighbour, average of a
-// finer one's 2 x 2 block; a coarser one leaves the tile's value).  The
-// stencil and the wall clamp are the kernel's (interpolate_direct_entry).
-void HostForest::coarse_sources(int kb, int ke, const char* only) {
-  const fc_forest_desc& d = desc;
-  const int mx = d.mx;
-  const bool walls = d.domain == FC_DOMAIN_WALLS;
-  auto region = [mx](int i, int j) {
-    const int dx = i < 0 ? -1 : (i >= mx ? 1 : 0), dy = j < 0 ? -1 : (j >= mx ? 1 : 0);
-    if (dy == 0) return dx < 0 ? 0 : 1;
-    if (dx == 0) return dy < 0 ? 2 : 3;
-    return 4 + (dx > 0 ? 1 : 0) + (dy > 0 ? 2 : 0);
-  };
-  for (int k = kb; k < ke; ++k) {
-    if (only && !only[k]) continue;
-    const int p = dev_of[k];
-    const Leaf& o = leaves[k];
-    for (int r = 0; r < 8; ++r) {
-      NbrEntry& e = nbr[(size_t)p * 8 + r];
-      if (e.kind != NB_COARSE) continue;
-      const int c = e.n0;
-      // the ghosts of the region: rows / columns -2, -1 or mx, mx + 1
-      const int i0 = kDirX[r] < 0 ? -2 : kDirX[r] > 0 ? mx : 0;
-      const int i1 = kDirX[r] == 0 ? mx : i0 + 2;
-      const int j0 = kDirY[r] < 0 ? -2 : kDirY[r] > 0 ? mx : 0;
-      const int j1 = kDirY[r] == 0 ? mx : j0 + 2;
-      int ext = 0, cc[2] = {0, 0}, src[2] = {-1, -1}, code[2] = {0, 0};
-      bool complete = true;
-      // The four ghosts of an aligned 2 x 2 group share their coarse cell,
-      // its stencil and their block of the owner: one of them stands for all.
-      // Along a face only the two end groups are visited: a group between
-      // them has its stencil inside c but towards the owner, where c's
-      // ghost is the average of the owner's block beside it (c's face next
-      // to the owner holds the owner and its sibling, one level finer), as
-      // each end group shows for its own.
-      const int step_i = r < 4 && kDirX[r] == 0 ? mx - 2 : 2;
-      const int step_j = r < 4 && kDirY[r] == 0 ? mx - 2 : 2;
-      for (int j = j0; j < j1 && complete; j += step_j)
-        for (int i = i0; i < i1 && complete; i += step_i) {
-          bool own = r >= 4;  // a face's group has the owner's block among its reads
-          int u, v;
-          apply_code_host(e.a, o.x * mx + i, o.y * mx + j, &u, &v);
-          const int gx = u + e.fx, gy = v + e.fy;
-          const int ic = (gx >> 1) - e.x0 * mx, jc = (gy >> 1) - e.y0 * mx;
-          if (ic < 0 || ic >= mx || jc < 0 || jc >= mx) continue;  // not interpolated
-          for (int m = 1; m < 5; ++m) {
-            int ci = ic + (m == 1 ? 1 : m == 2 ? -1 : 0), cj = jc + (m == 3 ? 1 : m == 4 ? -1 : 0);
-            if (walls) {  // the exterior ghosts of c are its clamped cells
-              const int N = mx << e.lev, X = e.x0 * mx + ci, Y = e.y0 * mx + cj;
-              if (X < 0 || X >= N) ci = X < 0 ? 0 : mx - 1;
-              if (Y < 0 || Y >= N) cj = Y < 0 ? 0 : mx - 1;
-            }
-            if (ci >= 0 && ci < mx && cj >= 0 && cj < mx) continue;  // c's interior
-            // c's fill of its ghost (ci, cj)
-            const NbrEntry& f = nbr[(size_t)c * 8 + region(ci, cj)];
-            int rule = 3, sp = -1, lx = 0, ly = 0;
-            if (f.kind == NB_SAME || f.kind == NB_FINE) {
-              apply_code_host(f.a, e.x0 * mx + ci, e.y0 * mx + cj, &u, &v);
-              const int hx = u + f.fx, hy = v + f.fy;
-              if (f.kind == NB_SAME) {
-                rule = 1;
-                sp = f.n0;
-                lx = hx - f.x0 * mx;
-                ly = hy - f.y0 * mx;
-              } else {
-                rule = 2;
-                sp = f.n0;
-                lx = 2 * hx - f.x0 * mx;
-                ly = 2 * hy - f.y0 * mx;
-                if (lx < 0 || lx >= mx || ly < 0 || ly >= mx) {
-                  sp = f.n1;
-                  lx = 2 * hx - f.x1 * mx;
-                  ly = 2 * hy - f.y1 * mx;
-                }
-              }
-              if (sp < 0 || lx < 0 || lx >= mx || ly < 0 || ly >= mx) {
-                complete = false;  // (a malformed entry: the kernel reads c's)
-                break;
-              }
-            }
-            // next to the owner: a block of its own cells, the one the
-            // kernel takes (region r a face; the block beside the ghost's
-            // coarse cell, towards the owner)
-            if (rule == 2 && sp == p && r < 4) {
-              const int bi = r == 0 ? 0 : r == 1 ? mx - 2 : (i & ~1);
-              const int bj = r == 2 ? 0 : r == 3 ? mx - 2 : (j & ~1);
-              if (lx == bi && ly == bj) {
-                own = true;
-                continue;
-              }
-            }
-            const int key = (ci + 1) | ((cj + 1) << 6);
-            int slot = -1;
-            for (int q = 0; q < ext; ++q)
-              if (cc[q] == key) slot = q;
-            if (slot < 0) {
-              if (ext == 2) {
-                complete = false;
-                break;
-              }
-              slot = ext++;
-              cc[slot] = key;
-              src[slot] = sp;
-              code[slot] = key | (lx << 12) | (ly << 18) | (rule << 24);
-            }
-          }
-          if (!own) complete = false;
-        }
-      if (!complete) {  // (no list: nothing named, so a carried row never waits on it)
-        src[0] = src[1] = -1;
-        code[0] = code[1] = 0;
-      }
-      e.src[0] = src[0];
-      e.src[1] = src[1];
-      e.code[0] = code[0] | (complete ? kSrcComplete : 0);
-      e.code[1] = code[1];
-    }
-  }
 }
 
 // the face whose outward normal is (nx, ny): 0 -x, 1 +x, 2 -y, 3 +y
@@ -1223,13 +1094,7 @@ std::string build_partition(const HostForest& G, const std::vector<int>& part, i
         e.n0 = a0;
         e.n1 = a1;
       }
-      // a coarse neighbour's ghost sources, where held (else the kernel
-      // reads the coarse neighbour's entries)
-      for (int q = 0; q < 2; ++q) {
-        e.src[q] = e.src[q] >= 0 ? to_local_dev(e.src[q]) : -1;
-        if (((e.code[q] >> 24) & 3) && ((e.code[q] >> 24) & 3) != 3 && e.src[q] < 0)
-          e.code[0] = e.code[1] = 0;
-      }
+
       H->nbr[(size_t)p * 8 + dir] = e;
       if (i < nowned && e.kind == NB_COARSE) H->feeds_finer[e.n0] = 1;
     }

@@ -183,3 +183,40 @@ def test_allocator_cannot_change_while_a_forest_lives():
         fc.set_allocator(alloc, lambda p, n, s: release(p, n, s))
     F.close()
     fc.set_allocator()  # no forest: accepted
+
+
+@pytest.mark.parametrize("domain", ["walls", "periodic", "sphere", "brick"])
+@pytest.mark.parametrize("mx", [8, 32])
+def test_every_coarse_region_lists_its_coarse_ghosts(domain, mx):
+    """The update reads the ghosts of a coarser neighbour that its
+    interpolation reaches from sources listed in the region's entry (written
+    on the device after each upload); a region whose list is incomplete
+    falls back to the coarse neighbour's own entries (same values, a longer
+    read chain).  On random graded layouts of every domain kind, and after a
+    regrid of the swirl forest, no region falls back."""
+    rng = np.random.default_rng(5)
+    nb = {"walls": 1, "periodic": 1, "sphere": 6, "brick": 4}[domain]
+    dom = {"walls": fc.WALLS, "periodic": fc.PERIODIC, "sphere": fc.SPHERE, "brick": fc.BRICK}[domain]
+    vel = ("rotation", 0.0, 0.0, 1.0) if domain == "sphere" else ("swirl", 1.0)
+    kw = {"brick": (2, 2)} if domain == "brick" else {}  # noqa: E501
+    desc = fc.make_desc(domain=dom, mx=mx, lmin=1, lmax=5, dtype=fc.F32, velocity=vel, **kw)
+    lv = fc.uniform_leaves(1, 1, nb)
+    for _ in range(6):
+        lv = fc.layout_regrid(desc, lv, rng.random(len(lv)), 0.55, 0.1)
+    F = fc.Forest(desc, lv)
+    i = F.info()
+    assert i["coarse_entries"] > 0 and i["coarse_unlisted"] == 0, i
+
+
+def test_swirl_forest_lists_its_coarse_ghosts_after_regrids():
+    w = synth.swirl(0)
+    ref = oracle.initial_forest(w)
+    F = fc.Forest(desc_for(fc, w, fc.F32), ref.leaves())
+    F.set_q(ref.get_q())
+    _, dtc = synth.time_step(w)
+    for n in range(8):
+        F.step_multirate(n * dtc, dtc)
+        if (n + 1) % 4 == 0:
+            F.tag_regrid(w.tau_refine, w.tau_coarsen)
+            i = F.info()
+            assert i["coarse_entries"] > 0 and i["coarse_unlisted"] == 0, i
