@@ -202,15 +202,14 @@ __device__ __forceinline__ real fill_rule(const DevForest<real>& D, int tlevel, 
 
 // Ghost (ci, cj) of coarse neighbour c (entry e of the owner p's region r,
 // ghost (i, j) of the owner) as the coarse-neighbour fill leaves it, from
-// the sources the host found for the region (NbrEntry::src, code): one of
-// the two listed ghosts, or the block of the owner's cells beside the
-// ghost's coarse cell (region r a face, the list complete), else from c's
-// own entry (coarse_ghost).  No read waits on c's table.
+// the sources listed in the region's entry (NbrEntry::src, code): one of the
+// two listed ghosts, or the block of the owner's cells beside the ghost's
+// coarse cell (region r a face, the list complete), else from c's own entry
+// (coarse_ghost).  Only that last case waits on a read of c's table.
 template <typename real, int MX>
 __device__ __forceinline__ real coarse_ghost_at(const DevForest<real>& D, const NbrEntry& e,
-                                                const PatchMeta& cm, int p, int owner_level,
-                                                int tlevel, real alpha, int i, int j, int ci,
-                                                int cj) {
+                                                const PatchMeta& cm, int p, int tlevel,
+                                                real alpha, int i, int j, int ci, int cj) {
   const int key = (ci + 1) | ((cj + 1) << 6);
 #pragma unroll
   for (int q = 0; q < 2; ++q) {
@@ -223,7 +222,6 @@ __device__ __forceinline__ real coarse_ghost_at(const DevForest<real>& D, const 
   if ((e.code[0] & kSrcComplete) && r < 4) {
     const int bi = r == 0 ? 0 : r == 1 ? MX - 2 : (i & ~1);
     const int bj = r == 2 ? 0 : r == 3 ? MX - 2 : (j & ~1);
-    (void)owner_level;  // (one level finer than tlevel: fill_rule's average)
     return fill_rule<real, MX>(D, tlevel, alpha, 2, p, bi, bj, e.n0, ci, cj);
   }
   return coarse_ghost<real, MX>(D, cm, e.n0, tlevel, alpha, ci, cj);
@@ -231,8 +229,9 @@ __device__ __forceinline__ real coarse_ghost_at(const DevForest<real>& D, const 
 
 // interpolate_entry(), reading a coarse neighbour on tlevel through the
 // cells the coarse-neighbour fill would leave (above): the stencil's
-// interior cells are read together first, then any ghost of the coarse
-// patch (the same values in any order).  keep_t non-null: each stencil cell
+// interior cells, then any ghost of the coarse patch from the sources the
+// region's entry lists (coarse_ghost_at), all issued before any is used (the
+// same values in any order); p is the owner.  keep_t non-null: each stencil cell
 // is also stored where that fill would have left it in the coarse patch's
 // tile at keep_t + (patch - keep_t_p0) tiles (the adjoint's replay keeps
 // what the interpolation read; several writers store the same value)
@@ -266,7 +265,7 @@ __device__ __forceinline__ bool interpolate_direct_entry(const DevForest<real>& 
 #pragma unroll
   for (int m = 0; m < 5; ++m)
     if (!in[m])
-      c[m] = coarse_ghost_at<real, MX>(D, e, cm, p, pm.level, tlevel, alpha, i, j, ci[m], cj[m]);
+      c[m] = coarse_ghost_at<real, MX>(D, e, cm, p, tlevel, alpha, i, j, ci[m], cj[m]);
   if (keep_t) {
     constexpr int S = MX + 4;
     real* K = keep_t + (size_t)(e.n0 - keep_t_p0) * S * S;
@@ -297,9 +296,9 @@ __device__ __forceinline__ bool interpolate_direct(const DevForest<real>& D, con
 // slot k of ring / ring_w gets ghost k's value and whether a rule set it (an
 // exterior ghost is left to the wall condition).  entry_of(r) gives the
 // entry of face/corner region r (staged in shared memory, or read from the
-// table) of patch p.  Threads tid, stride nt.  direct: coarse neighbours on tlevel are
-// read through the cells their fill would leave (interpolate_direct_entry;
-// keep_t, keep_t_p0: where it also stores them).
+// table) of patch p.  Threads tid, stride nt.  direct: coarse neighbours on
+// tlevel are read through the cells their fill would leave
+// (interpolate_direct_entry; keep_t, keep_t_p0: where it also stores them).
 template <typename real, int MX, class EntryOf>
 __device__ __forceinline__ void gather_ring(const DevForest<real>& D, EntryOf entry_of, int p,
                                             const PatchMeta& pm, int tlevel, real alpha,
