@@ -2131,7 +2131,9 @@ fc_status fc_tag(fc_forest* F, double* delta_host, void* stream) {
   if (!F || !delta_host) return fail(FC_ERR_INVALID_ARG, "null argument");
   cudaStream_t s = as_stream(stream);
   const int kind = F->host.desc.indicator;
-  if (kind == 0) {  // central differences read the first ghost layer
+  {  // Alg. 1 first: central differences read the first ghost layer, and a
+     // regrid's new children interpolate from their parent's cells with its
+     // ghosts (the update kernels keep ghosts in shared memory only)
     const fc_status st = fill_all(F, s);
     if (st != FC_OK) return st;
   }

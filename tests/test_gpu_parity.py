@@ -391,3 +391,43 @@ def test_autotune_then_parity():
         ref.step_multirate(n * dtc, dtc)
         gpu.step_multirate(n * dtc, dtc)
     assert relerr(gpu.get_q(), ref.get_q()) <= F64_TOL
+
+
+def _smooth_field(leaves, mx):
+    """1 + sin(2 pi x) cos(2 pi y) / 2 at the cell centres of each leaf: a
+    field that is nowhere constant."""
+    lv = np.asarray(leaves)
+    n = len(lv)
+    h = 1.0 / (mx * 2.0 ** lv[:, 2])
+    i = np.arange(mx) + 0.5
+    x = (lv[:, 3, None] * mx + i[None, :]) * h[:, None]
+    y = (lv[:, 4, None] * mx + i[None, :]) * h[:, None]
+    return (1.0 + 0.5 * np.sin(2 * np.pi * x)[:, None, :] *
+            np.cos(2 * np.pi * y)[:, :, None]).reshape(n, mx, mx)
+
+
+@pytest.mark.parametrize("indicator", ["gradient", "maxmin"])
+def test_regrid_interpolates_new_children_with_filled_ghosts(indicator):
+    """New children take Eq. ghost_fine interpolation from their parent's
+    cells, the stencil reaching the parent's first ghost layer at its edges:
+    with either indicator the regrid fills the ghosts first, so on a field
+    that is nowhere constant the remapped field equals the oracle's."""
+    w = synth.swirl(3, lmin=2, lmax=4, mx=16)
+    w.indicator = indicator
+    ref, gpu = pair(fc, w, fc.F64)
+    q = _smooth_field(ref.leaves(), w.mx)
+    ref.set_q(q)
+    gpu.set_q(q)
+    _, dtc = synth.time_step(w)
+    ref.step_multirate(0.0, dtc)
+    gpu.step_multirate(0.0, dtc)
+    # a threshold in the widest gap between the middle indicators (no leaf
+    # within rounding of it)
+    d = np.sort(ref.tag())
+    k = len(d) // 4 + int(np.argmax(np.diff(d[len(d) // 4: 3 * len(d) // 4])))
+    tau_r = 0.5 * (d[k] + d[k + 1])
+    assert d[k + 1] - d[k] > 1e-9 * d[-1]
+    assert ref.regrid(tau_r, -1.0) > 0
+    gpu.tag_regrid(tau_r, -1.0)
+    np.testing.assert_array_equal(gpu.leaves(), ref.leaves())
+    assert relerr(gpu.get_q(), ref.get_q()) <= F64_TOL
