@@ -342,3 +342,35 @@ def test_tables_built_on_host_threads_concurrently_and_after_fork():
     ctx = mp.get_context("fork")
     with ctx.Pool(1) as pool:
         np.testing.assert_array_equal(pool.apply(fc.layout_neighbours, (d, lv)), want)
+
+
+def test_large_ensemble_rows_equal_each_forest_built_alone():
+    """The rows of a large ensemble (built in many pieces on the host worker
+    pool) are, forest by forest, the rows of that forest built alone with
+    its patch indices shifted: forests never touch, and the pieces are
+    independent."""
+    rng = np.random.default_rng(9)
+    nf = 24
+    d1 = fc.make_desc(domain=fc.PERIODIC, mx=8, lmin=2, lmax=6, dtype=fc.F32,
+                      velocity=("swirl", 1.0), nforests=1)
+    dn = fc.make_desc(domain=fc.PERIODIC, mx=8, lmin=2, lmax=6, dtype=fc.F32,
+                      velocity=("swirl", 1.0), nforests=nf)
+    parts = []
+    for f in range(nf):
+        lv = fc.uniform_leaves(2, 1, 1)
+        for _ in range(4):
+            lv = fc.layout_regrid(d1, lv, rng.random(len(lv)), 0.5, 0.1)
+        lv = np.asarray(lv).copy()
+        parts.append(lv)
+    allv = np.concatenate([np.column_stack([np.full(len(p), f), p[:, 1:]])
+                           for f, p in enumerate(parts)]).astype(np.int32)
+    assert len(allv) > 8192  # several pieces of the pool
+    big = fc.layout_neighbours(dn, allv)
+    off = 0
+    for f, p in enumerate(parts):
+        one = fc.layout_neighbours(d1, p).copy()
+        shifted = one.copy()
+        for c in (1, 2):  # neighbour indices (field order) move by the forest's offset
+            shifted[:, :, c] = np.where(one[:, :, c] >= 0, one[:, :, c] + off, -1)
+        np.testing.assert_array_equal(big[off: off + len(p)], shifted)
+        off += len(p)
