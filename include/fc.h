@@ -189,6 +189,15 @@ fc_status fc_forest_get_q(const fc_forest* forest, void* q, int on_device, void*
 /* Whole patch arrays with ghosts, (mx+2mbc)^2 per leaf, [leaf][j][i]. */
 fc_status fc_forest_get_q_full(const fc_forest* forest, void* q, int on_device, void* stream);
 
+/* Test aid, an executable Prop. 1 (Sec. 2.3: every cell the update's stencil
+ * reads is set by a rule of Alg. 1 first): writes `value` (NaN, say) into
+ * every ghost cell of the forest's two state buffers and into every cell of
+ * its time-interpolation tiles, enqueued on `stream`.  Interiors are left
+ * alone, so the next steps must give the same results as without the call;
+ * an update that read such a cell before a rule wrote it would carry the
+ * value into its result. */
+fc_status fc_forest_poison(fc_forest* forest, double value, void* stream);
+
 /* Alg. 1 (update_ghost, Sec. 2.3) on every level: copy from same-size
  * neighbours (Eq. transform), average from fine neighbours (Eq.
  * ghost_coarse), physical boundary conditions, interpolation from coarse

@@ -73,6 +73,7 @@ SIGNATURES = {
     "fc_layout_regrid": (ctypes.c_int, [_DP, ctypes.c_int, _ip, _dp, ctypes.c_double,
                                         ctypes.c_double, _ip, ctypes.c_int, _ip, _ip]),
     "fc_timers_enable": (ctypes.c_int, [_vp, ctypes.c_int]),
+    "fc_forest_poison": (ctypes.c_int, [_vp, ctypes.c_double, _vp]),
     "fc_set_graphs": (ctypes.c_int, [_vp, ctypes.c_int]),
     "fc_autotune": (ctypes.c_int, [_vp, _ip, _vp]),
     "fc_set_fused_fill": (ctypes.c_int, [_vp, ctypes.c_int]),

@@ -155,6 +155,24 @@ __global__ void unpack_kernel(DevForest<real> D, const int* api_to_dev, const re
   }
 }
 
+// Test aid (an executable Prop. 1): value into every ghost cell of both
+// state buffers and every cell of the time-interpolation tiles -- the cells
+// a rule of Alg. 1 must write before any update may read them.
+template <typename real>
+__global__ void poison_kernel(DevForest<real> D, real value) {
+  const int mx = D.mx, S = D.S;
+  const size_t total = (size_t)D.npatch * S * S;
+  for (size_t g = (size_t)blockIdx.x * blockDim.x + threadIdx.x; g < total;
+       g += (size_t)gridDim.x * blockDim.x) {
+    const int r = (int)(g % ((size_t)S * S)), i = r % S - kMbc, j = r / S - kMbc;
+    D.qT[g] = value;
+    if (i < 0 || i >= mx || j < 0 || j >= mx) {
+      D.buf[0][g] = value;
+      D.buf[1][g] = value;
+    }
+  }
+}
+
 // interior capacities in field order: kappa from the metric block on a
 // mapped grid, h^2 on the square domains
 template <typename real>
@@ -392,6 +410,14 @@ cudaError_t launch_mass(const DevForest<real>& D, const int* api_to_dev, const i
 }
 
 template <typename real>
+cudaError_t launch_poison(const DevForest<real>& D, double value, cudaStream_t s) {
+  if (D.npatch <= 0) return cudaSuccess;
+  poison_kernel<real><<<1216, 256, 0, s>>>(D, real(value));
+  ++launch_counter();
+  return cudaGetLastError();
+}
+
+template <typename real>
 cudaError_t launch_pack(const DevForest<real>& D, const int* api_to_dev, real* out, int full,
                         cudaStream_t s) {
   if (D.npatch <= 0) return cudaSuccess;
@@ -494,7 +520,8 @@ cudaError_t launch_reflux_pairs(const DevForest<real>& D, int p0, int p1, const 
   template cudaError_t launch_pack_capacity<real>(const DevForest<real>&, const int*, double*, \
                                                   cudaStream_t);                               \
   template cudaError_t launch_remap<real>(const DevForest<real>&, const DevForest<real>&,     \
-                                          const RemapEntry*, cudaStream_t);
+                                          const RemapEntry*, cudaStream_t);                      \
+  template cudaError_t launch_poison<real>(const DevForest<real>&, double, cudaStream_t);
 
 FC_INSTANTIATE(float)
 FC_INSTANTIATE(double)

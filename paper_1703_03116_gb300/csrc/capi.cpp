@@ -1978,6 +1978,14 @@ fc_status fc_forest_get_q(const fc_forest* F, void* q, int on_device, void* stre
   return get_q_impl(F, q, on_device, stream, 0);
 }
 
+fc_status fc_forest_poison(fc_forest* F, double value, void* stream) {
+  if (!F) return fail(FC_ERR_INVALID_ARG, "null forest");
+  cudaStream_t s = as_stream(stream);
+  const cudaError_t e = F->esize == 4 ? launch_poison(dev<float>(F), value, s)
+                                      : launch_poison(dev<double>(F), value, s);
+  return e == cudaSuccess ? FC_OK : cuda_fail(e, "poison");
+}
+
 fc_status fc_forest_get_q_full(const fc_forest* F, void* q, int on_device, void* stream) {
   return get_q_impl(F, q, on_device, stream, 1);
 }

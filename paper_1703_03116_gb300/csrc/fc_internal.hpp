@@ -592,6 +592,8 @@ cudaError_t launch_unpack(const DevForest<real>& D, const int* api_to_dev, const
 template <typename real>
 cudaError_t launch_remap(const DevForest<real>& Old, const DevForest<real>& New,
                          const RemapEntry* rm, cudaStream_t s);
+template <typename real>
+cudaError_t launch_poison(const DevForest<real>& D, double value, cudaStream_t s);
 
 uint64_t& launch_counter();
 

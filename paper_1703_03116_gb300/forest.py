@@ -131,6 +131,11 @@ class Forest:
             check(load().fc_forest_set_q(self._h, a.ctypes.data_as(ctypes.c_void_p), 0,
                                          _stream(stream)))
 
+    def poison(self, value: float, stream=None):
+        """Test aid (fc_forest_poison): value into every ghost cell of both
+        state buffers and every time-interpolation tile cell."""
+        check(load().fc_forest_poison(self._h, float(value), _stream(stream)))
+
     def get_q(self, out=None, stream=None, full: bool = False):
         """Interior (or, with full=True, ghost-including) field, host or device."""
         n = len(self)
