@@ -279,7 +279,7 @@ def measure(runner, steps, warmup, flush_buf, clock_index):
 # and every timed launch runs that kernel, else null.
 DRAM_PER_PATCH = {("band", 4, 32): 8734.0}
 KERNEL_SOURCES = {"band": ('advance_band.cu', 'ghost_gather.cuh', 'device_util.cuh', 'walk_edge.cuh', 'fc_internal.hpp')}
-KERNEL_SOURCES_SHA = {"band": "57ce1aba8bdc04a1"}
+KERNEL_SOURCES_SHA = {"band": "16d2b9fd61c0685d"}
 
 
 def sources_sha(variant):
